@@ -1,0 +1,179 @@
+"""Seeded synthetic inputs: surface densities, their analytic slopes, and grids.
+
+This module generates inputs only. It holds none of the force method's
+arithmetic (no kernel integrals, transforms or sums) and is shared by the
+tests, the oracle comparisons and the benchmark so that both sides of every
+comparison see the same arrays.
+
+Conventions: arrays are row-major [y][x]; cell (j, i) of a patch with origin
+(x0, y0) and cell width h has centre (x0 + (i + 1/2) h, y0 + (j + 1/2) h).
+
+Disks (Section 3 of Tseng, Shang & Yen for D_2; the others are the workloads
+of the benchmark configurations):
+* D_2:   sigma0 (1 - R^2/alpha^2)^{3/2} for R < alpha, else 0.
+* Kuzmin: a M / (2 pi (R^2 + a^2)^{3/2}).
+* two-armed logarithmic spiral: Kuzmin(a) (1 + A cos(2 theta - ln(R) / tan 15deg)).
+* exponential: exp(-R / r0).
+"""
+import math
+
+import numpy as np
+
+
+# ---------------------------------------------------------------- geometry --
+
+def cell_centres(nx, ny, x0, y0, h):
+    """Centre coordinates (X, Y), each [ny, nx], of a uniform patch."""
+    x = x0 + (np.arange(nx) + 0.5) * h
+    y = y0 + (np.arange(ny) + 0.5) * h
+    return np.meshgrid(x, y)
+
+
+def unit_grid(n):
+    """A uniform n-by-n grid on [-1, 1]^2: returns (nx, ny, x0, y0, h)."""
+    return (n, n, -1.0, -1.0, 2.0 / n)
+
+
+def centred_nested_patches(base_n, nlevels, cells_per_level=None):
+    """Nested, centred ratio-2 patches: level l covers [-2^-l, 2^-l]^2.
+
+    Level 0 is base_n^2 cells on [-1, 1]^2; every finer level has the same number
+    of cells per side (cells_per_level, default base_n), i.e. half the extent at
+    half the cell width. Returns a list of (nx, ny, x0, y0, h).
+    """
+    n = base_n if cells_per_level is None else cells_per_level
+    out = []
+    for lev in range(nlevels):
+        h = (2.0 / base_n) / (2 ** lev)
+        nl = base_n if lev == 0 else n
+        half = nl * h / 2.0
+        out.append((nl, nl, -half, -half, h))
+    return out
+
+
+def covered_mask(patches, level):
+    """Boolean [ny, nx] mask of cells of patch `level` covered by patch `level+1`."""
+    nx, ny, x0, y0, h = patches[level]
+    mask = np.zeros((ny, nx), dtype=bool)
+    if level + 1 < len(patches):
+        fx, fy, fx0, fy0, fh = patches[level + 1]
+        i0 = int(round((fx0 - x0) / h))
+        j0 = int(round((fy0 - y0) / h))
+        i1 = i0 + int(round(fx * fh / h))
+        j1 = j0 + int(round(fy * fh / h))
+        mask[j0:j1, i0:i1] = True
+    return mask
+
+
+# ------------------------------------------------------------------ disks --
+
+def d2_sigma(X, Y, alpha, sigma0=1.0, xc=0.0, yc=0.0):
+    """D_2 surface density and its analytic gradient (sigma, dsdx, dsdy)."""
+    dx = X - xc
+    dy = Y - yc
+    q = 1.0 - (dx * dx + dy * dy) / (alpha * alpha)
+    inside = q > 0.0
+    qp = np.where(inside, q, 0.0)
+    s = sigma0 * qp ** 1.5
+    g = -3.0 * sigma0 * np.sqrt(qp) / (alpha * alpha)
+    return s, g * dx, g * dy
+
+
+def d22_sigma(X, Y, alpha, sigma0=1.0):
+    """Two D_2 disks centred at (0, 0.5) and (0, -0.5) (Section 3)."""
+    a = d2_sigma(X, Y, alpha, sigma0, 0.0, 0.5)
+    b = d2_sigma(X, Y, alpha, sigma0, 0.0, -0.5)
+    return tuple(p + q for p, q in zip(a, b))
+
+
+def kuzmin_sigma(X, Y, a, M=1.0):
+    """Kuzmin surface density and its analytic gradient."""
+    q = X * X + Y * Y + a * a
+    s = a * M / (2.0 * math.pi * q ** 1.5)
+    g = -3.0 * s / q
+    return s, g * X, g * Y
+
+
+def spiral_sigma(X, Y, a, amp, pitch_deg=15.0, M=1.0):
+    """Kuzmin(a) modulated by a two-armed logarithmic spiral, with its gradient."""
+    s, sx, sy = kuzmin_sigma(X, Y, a, M)
+    R2 = X * X + Y * Y
+    R = np.sqrt(R2)
+    th = np.arctan2(Y, X)
+    k = 1.0 / math.tan(math.radians(pitch_deg))
+    ph = 2.0 * th - k * np.log(R)
+    c = np.cos(ph)
+    sn = np.sin(ph)
+    # d(ph)/dx = 2 d(theta)/dx - k x / R^2 = (-2 y - k x) / R^2 ; d(ph)/dy = (2 x - k y) / R^2
+    dphx = (-2.0 * Y - k * X) / R2
+    dphy = (2.0 * X - k * Y) / R2
+    m = 1.0 + amp * c
+    return s * m, sx * m - s * amp * sn * dphx, sy * m - s * amp * sn * dphy
+
+
+def exponential_sigma(X, Y, r0):
+    """exp(-R / r0) and its gradient (undefined at R = 0, never a cell centre here)."""
+    R = np.hypot(X, Y)
+    s = np.exp(-R / r0)
+    g = -s / (r0 * R)
+    return s, g * X, g * Y
+
+
+# --------------------------------------------------------- configurations --
+
+def kuzmin_64(a=0.2):
+    """64^2 grid on [-1,1]^2, Kuzmin a = 0.2, G = M = 1."""
+    nx, ny, x0, y0, h = unit_grid(64)
+    X, Y = cell_centres(nx, ny, x0, y0, h)
+    s, sx, sy = kuzmin_sigma(X, Y, a)
+    return dict(geom=(nx, ny, x0, y0, h), sigma=s, dx=sx, dy=sy, X=X, Y=Y)
+
+
+def spiral_1024(seed=2, n=1024, a=0.1, amp=0.1, noise=1e-3):
+    """n^2 grid on [-1,1]^2: Kuzmin(a) x (1 + amp cos(2 theta - ln R / tan 15deg)) + U(-noise, noise).
+
+    The noise is absolute, drawn from numpy's PCG64 with the given seed; the
+    analytic gradient returned ignores the noise.
+    """
+    nx, ny, x0, y0, h = unit_grid(n)
+    X, Y = cell_centres(nx, ny, x0, y0, h)
+    s, sx, sy = spiral_sigma(X, Y, a, amp)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = s + rng.uniform(-noise, noise, size=s.shape)
+    return dict(geom=(nx, ny, x0, y0, h), sigma=s, dx=sx, dy=sy, X=X, Y=Y)
+
+
+def exponential_hierarchy(base_n=256, nlevels=3, r0=0.1):
+    """Centred nested ratio-2 patches of base_n^2 cells each, sigma = exp(-R/r0).
+
+    Covered cells (those refined by the next level) hold sigma = slopes = 0.
+    Returns dict(patches=[...], sigma=[...], dx=[...], dy=[...], leaf=[...]).
+    """
+    patches = centred_nested_patches(base_n, nlevels)
+    sig, sxs, sys_, leaf = [], [], [], []
+    for lev, (nx, ny, x0, y0, h) in enumerate(patches):
+        X, Y = cell_centres(nx, ny, x0, y0, h)
+        s, sx, sy = exponential_sigma(X, Y, r0)
+        cov = covered_mask(patches, lev)
+        for a in (s, sx, sy):
+            a[cov] = 0.0
+        sig.append(s)
+        sxs.append(sx)
+        sys_.append(sy)
+        leaf.append(~cov)
+    return dict(patches=patches, sigma=sig, dx=sxs, dy=sys_, leaf=leaf)
+
+
+def batch_sizes(count=64, lo=64, hi=512, seed=4):
+    """Grid sizes N = round(exp U(ln lo, ln hi)) and disk parameters, seeded."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=count))).astype(int)
+    a = rng.uniform(0.05, 0.3, size=count)
+    amp = rng.uniform(0.0, 0.2, size=count)
+    return ns, a, amp
+
+
+def random_fields(ny, nx, seed, scale=1.0):
+    """Seeded uniform random sigma, dx, dy in [-scale, scale] (parity inputs)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return tuple(rng.uniform(-scale, scale, size=(ny, nx)) for _ in range(3))
