@@ -1,0 +1,416 @@
+"""Benchmark of the thin-disk self-gravity force solve on GB300.
+
+Workload (one "step" = one force solve through the C ABI): the uniform
+1024 x 1024 grid on [-1,1]^2 with the two-armed spiral Kuzmin disk
+(a = 0.1, amplitude 0.1, pitch 15 deg) plus seeded uniform noise +-1e-3,
+FP32 fields and transforms, FP64-built kernel spectra, central-difference
+slopes, zero padding to 2048 x 2048. The L2 cache is flushed (a 512 MB
+write) before every timed solve; each solve is timed with CUDA events on the
+stream it runs on.
+
+Reported: value = solves/s (whole job, N ranks), p50/p99 latency per solve,
+target-cells/s, the plain FP64 per-solve path on the same GPU, the relative L2
+force error of the FP32 path against the FP64 path, a roofline entry for the
+dominant kernel, the end-to-end rate through the host-buffer entry point, and
+the FP64 CPU oracle timed on the host cores on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload amr3]
+
+Multi-GPU (torchrun): every rank solves its own independent stream of
+problems (replicas, no collective on the data path); the slowest rank's time
+sets the rate.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "force solves/sec and target-cells/sec (p50/p99 latency) vs FP64 plain, ≤1e-5 rel err"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------- workloads --
+
+def workload_spiral():
+    from paper_2001_02765_gb300 import workloads as W
+    case = W.spiral_1024(seed=2)
+    nx, ny, x0, y0, h = case["geom"]
+    return {
+        "name": "uniform 1024x1024 spiral Kuzmin disk (a=0.1, m=2 amplitude 0.1, pitch 15 deg, noise 1e-3), "
+                "central slopes, FFT on 2048x2048 padded grid",
+        "patches": [(0, nx, ny, x0, y0, h)], "slope_mode": 1,
+        "sigma": case["sigma"].ravel(), "dx": None, "dy": None, "targets": nx * ny,
+        "config": {"workload": "spiral_1024_fft", "grid": [nx, ny], "padded": [2048, 2048], "precision": "fp32",
+                   "slopes": "central", "l2": "flushed before every solve (512 MB write)"},
+    }
+
+
+def workload_amr3():
+    from paper_2001_02765_gb300 import workloads as W
+    case = W.exponential_hierarchy(256, 3, 0.1)
+    patches = [(lev,) + p for lev, p in enumerate(case["patches"])]
+    cat = lambda a: np.concatenate([x.ravel() for x in a])
+    nleaf = int(sum(m.sum() for m in case["leaf"]))
+    return {
+        "name": "AMR 3 levels x 256^2 (ratio 2, centred nested), exponential disk exp(-R/0.1), caller slopes",
+        "patches": patches, "slope_mode": 2, "sigma": cat(case["sigma"]), "dx": cat(case["dx"]),
+        "dy": cat(case["dy"]), "targets": nleaf,
+        "config": {"workload": "amr3_exponential", "levels": 3, "cells_per_level": [256, 256], "leaves": nleaf,
+                   "precision": "fp32", "slopes": "caller",
+                   "l2": "flushed before every solve (512 MB write)"},
+    }
+
+
+WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3}
+
+
+# ----------------------------------------------------------------- oracle --
+
+class OracleSample:
+    """The FP64 plain direct sum (the oracle) on a seeded sample of leaf targets
+    of a workload; the leaf list is prepared once."""
+
+    def __init__(self, wl):
+        from oracle import amr as oamr
+        from oracle.fftconv import central_slopes
+        patches = wl["patches"]
+        sig, off = [], 0
+        for p in patches:
+            sig.append(np.asarray(wl["sigma"][off:off + p[1] * p[2]], np.float64).reshape(p[2], p[1]))
+            off += p[1] * p[2]
+        if wl["slope_mode"] == 1:
+            sx, sy = central_slopes(sig[0], patches[0][5])
+            sxs, sys_ = [sx], [sy]
+        elif wl["slope_mode"] == 2:
+            sxs, sys_, off = [], [], 0
+            for p in patches:
+                n = p[1] * p[2]
+                sxs.append(np.asarray(wl["dx"][off:off + n], np.float64).reshape(p[2], p[1]))
+                sys_.append(np.asarray(wl["dy"][off:off + n], np.float64).reshape(p[2], p[1]))
+                off += n
+        else:
+            sxs = sys_ = None
+        leaves = oamr.leaf_cells(oamr.make_patches(patches))
+        k, j, i = leaves["patch"], leaves["j"], leaves["i"]
+
+        def g(f):
+            return np.concatenate([f[q][j[k == q], i[k == q]] for q in range(len(patches))])
+
+        self.s0 = g(sig)
+        self.sx = g(sxs) if sxs is not None else None
+        self.sy = g(sys_) if sys_ is not None else None
+        self.cells = (leaves["xl"], leaves["xr"], leaves["yd"], leaves["yu"])
+        self.tx, self.ty = leaves["xc"], leaves["yc"]
+        self.total_targets = wl["targets"]
+        self.rng = np.random.Generator(np.random.PCG64(77))
+
+    def run(self, sample_targets, nthreads=0):
+        """Returns (solves/s, target-cells/s, seconds, threads, description)."""
+        from oracle.direct import direct_force, max_threads
+        tsel = self.rng.choice(self.tx.size, sample_targets, replace=False)
+        t0 = time.perf_counter()
+        direct_force(self.cells, self.s0, self.sx, self.sy, self.tx[tsel], self.ty[tsel], nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        threads = nthreads or max_threads()
+        tps = sample_targets / dt
+        return (tps / self.total_targets, tps, dt, threads,
+                "%d seeded leaf targets of the full workload, plain FP64 direct sum over all sources" % sample_targets)
+
+
+# -------------------------------------------------------------- GPU arm --
+
+def run_gpu(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2001_02765_gb300 import sg
+
+    wl = WORKLOADS[args.workload]()
+    dt = torch.float32
+    plan = sg.Plan(wl["patches"], precision="fp32", slope_mode=wl["slope_mode"])
+    sg.sg_plan_set_timing(plan.handle, True)
+    stream = torch.cuda.Stream()
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    sigma, dxs, dys = dev(wl["sigma"]), dev(wl["dx"]), dev(wl["dy"])
+    fx = torch.empty_like(sigma)
+    fy = torch.empty_like(sigma)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def solve():
+        with torch.cuda.stream(stream):
+            plan.force(sigma, dxs, dys, fx, fy, stream=stream)
+
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        solve()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = {k: [] for k in sg.STAGE_NAMES}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+            solve()
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+            t = sg.sg_plan_get_timing(plan.handle)  # waits for this solve's events
+            for name, v in t.items():
+                stage_ms[name].append(v)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    per = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(per)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    solves = args.steps * world
+    value = solves / (total_ms / 1e3)
+    p50 = float(np.percentile(per, 50))
+    p99 = float(np.percentile(per, 99))
+
+    # FP64 plain per-solve path on the same GPU, and the FP32 error against it
+    plan64 = sg.Plan(wl["patches"], precision="fp64", slope_mode=wl["slope_mode"])
+    d64 = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32).astype(np.float64)).cuda()
+    s64, dx64, dy64 = d64(wl["sigma"]), d64(wl["dx"]), d64(wl["dy"])
+    g64 = plan64.force(s64, dx64, dy64)
+    torch.cuda.synchronize()
+    ff = [x.double() for x in (fx, fy)]
+    num = torch.sum((ff[0] - g64[0]) ** 2) + torch.sum((ff[1] - g64[1]) ** 2)
+    den = torch.sum(g64[0] ** 2) + torch.sum(g64[1] ** 2)
+    rel_err = float(torch.sqrt(num / den))
+    n64 = max(3, min(args.steps, 10))
+    e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
+    for k in range(n64):
+        flush.fill_(1.0)
+        e64[k][0].record()
+        plan64.force(s64, dx64, dy64, g64[0], g64[1])
+        e64[k][1].record()
+    torch.cuda.synchronize()
+    fp64_ms = statistics.median([a.elapsed_time(b) for a, b in e64])
+    plan64.close()
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    hs = torch.from_numpy(np.ascontiguousarray(wl["sigma"], np.float32)).pin_memory()
+    hdx = torch.from_numpy(np.ascontiguousarray(wl["dx"], np.float32)).pin_memory() if wl["dx"] is not None else None
+    hdy = torch.from_numpy(np.ascontiguousarray(wl["dy"], np.float32)).pin_memory() if wl["dy"] is not None else None
+    hfx = torch.empty(plan.ncells, dtype=dt).pin_memory()
+    hfy = torch.empty(plan.ncells, dtype=dt).pin_memory()
+    sg.sg_plan_set_timing(plan.handle, False)
+    for _ in range(2):
+        plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)  # copies in, solve, copies out, waits
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    nbytes = plan.ncells * 4
+    h2d = nbytes * (3 if wl["dx"] is not None else 1)
+    d2h = 2 * nbytes
+
+    # roofline of the dominant kernel
+    stage_mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
+    dom = max(stage_mean, key=stage_mean.get)
+    peak, peak_kind = _peaks()
+    info = plan.info
+    alg = algorithmic_bytes(wl, info, dom)
+    achieved = alg / (stage_mean[dom] * 1e-3) / 1e9 if stage_mean[dom] > 0 else 0.0
+    plan.close()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(wl["config"], parallelism="replicas" if world > 1 else "single"),
+        "target_cells_per_s": value * wl["targets"],
+        "latency_ms": {"p50": p50, "p99": p99},
+        "fp64_plain": {"solves_per_s": 1e3 / fp64_ms * world, "ms_per_solve": fp64_ms},
+        "rel_err_vs_fp64": rel_err,
+        "stage_ms": stage_mean,
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes": alg, "peak_source": peak_kind},
+        "e2e": {"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * launches_per_solve(wl),
+        "clocks": clk.summary(),
+        "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        sps, tps, secs, thr, what = OracleSample(wl).run(args.cpu_targets)
+        line["cpu_baseline"] = {"value": sps, "unit": "solves/s", "cores": thr, "kind": "oracle", "sample": what,
+                                "target_cells_per_s": tps, "seconds": secs}
+    print(json.dumps(line), flush=True)
+
+
+def launches_per_solve(wl):
+    n = len(wl["patches"])
+    return 3 * n + (2 if n > 1 else 0)
+
+
+def algorithmic_bytes(wl, info, stage):
+    """Bytes a stage must move per solve (see the design notes): FP32 complex
+    intermediates of (P/2+1) x ny bins per field, spectra planes, inputs, outputs."""
+    es = 4
+    total = 0
+    nf = 1 if wl["slope_mode"] == 0 else 3
+    for p in wl["patches"]:
+        nx, ny = p[1], p[2]
+        px = 64
+        while px < 2 * nx - 1:
+            px *= 2
+        py = 64
+        while py < 2 * ny - 1:
+            py *= 2
+        qx, qy = px // 2 + 1, py // 2 + 1
+        inputs = nx * ny * es * (1 if wl["slope_mode"] != 2 else 3)
+        if stage == "row_fwd":
+            total += inputs + nf * qx * ny * 2 * es
+        elif stage == "col_conv":
+            total += nf * qx * ny * 2 * es + 6 * qx * qy * es + 2 * qx * ny * 2 * es
+        elif stage == "row_inv":
+            total += 2 * qx * ny * 2 * es + 2 * nx * ny * es
+    if stage in ("corner_weights", "cross_direct"):
+        total = info["ncells"] * es * 3
+    return total
+
+
+# ---------------------------------------------------------- reference arm --
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]()
+    orc = OracleSample(wl)
+    for _ in range(args.warmup):
+        orc.run(8)
+    times, tps_all, thr, what = [], [], 0, ""
+    for _ in range(args.steps):
+        sps, tps, secs, thr, what = orc.run(args.ref_targets)
+        times.append(secs)
+        tps_all.append(tps)
+    tps = args.steps * args.ref_targets / sum(times)
+    value = tps / wl["targets"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(wl["config"], precision="fp64", parallelism="host cores"),
+        "target_cells_per_s": tps,
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": thr, "kind": "oracle",
+                         "sample": "each step: " + what},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="spiral1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-targets", type=int, default=2048)
+    ap.add_argument("--ref-targets", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

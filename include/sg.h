@@ -1,0 +1,202 @@
+/*
+ * sg.h -- C ABI of the thin-disk self-gravity library (GB300, sm_103a).
+ *
+ * The library computes the in-plane gravitational force (Fx, Fy) at the centre
+ * of every leaf cell of an infinitesimally thin disk whose surface density is
+ * piecewise linear on rectangular cells (Tseng, Shang & Yen, Section 2):
+ *
+ *   sigma_i(x, y) = sigma0_i + deltax_i (x - xc_i) + deltay_i (y - yc_i)   (Eq. eqnGamma)
+ *   Fx(t) = G sum_i [sigma0_i K^{x,0}_i(t) + deltax_i K^{x,x}_i(t) + deltay_i K^{x,y}_i(t)]
+ *   Fy(t) = G sum_i [sigma0_i K^{y,0}_i(t) + deltax_i K^{y,x}_i(t) + deltay_i K^{y,y}_i(t)]
+ *
+ * with the closed-form cell integrals of (xbar - x)/r^3 and (ybar - y)/r^3 listed
+ * in Section 2 (z = 0), including the coincident-line form for targets on a
+ * source edge line. The force is attractive (points towards mass).
+ *
+ * Grids are sets of patches: uniform blocks of square cells. A single patch is
+ * a uniform grid; several patches on refinement levels 0, 1, 2, ... (ratio 2,
+ * Section 3 and Fig. 1) form an AMR hierarchy whose leaves are the cells not
+ * covered by a patch of the next level. Pairs of cells in the same patch are
+ * summed as a zero-padded FFT convolution; pairs in different patches by a
+ * direct sum over cell corners. Both give the sum above to rounding.
+ *
+ * Conventions
+ *  - Every entry point returns an sg_status; no exception or signal crosses
+ *    the ABI. sg_strerror() names a status.
+ *  - Field arrays (sigma, deltax, deltay, Fx, Fy) are per-patch dense arrays,
+ *    row-major [y][x] (cell (j, i) of a patch has centre
+ *    (x0 + (i + 1/2) h, y0 + (j + 1/2) h)), concatenated in patch order;
+ *    element type double for SG_FP64 plans and float for SG_FP32 plans.
+ *    Values at covered (non-leaf) cells are ignored on input and unspecified
+ *    on output.
+ *  - The caller owns every field buffer. A plan owns its device memory
+ *    (kernel spectra, geometry tables, scratch) until sg_plan_destroy.
+ *  - A plan is bound to the CUDA device that was current at sg_plan_create and
+ *    must be used with that device current. A plan is not thread-safe: calls on
+ *    one plan must not overlap (they share the plan's scratch).
+ *  - Streams are passed as opaque pointers (a cudaStream_t; NULL is the legacy
+ *    default stream). Work is enqueued and the call returns without waiting.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,      /* invalid argument or geometry */
+    SG_ENOMEM = 2,      /* a device or host allocation failed */
+    SG_EBUDGET = 3,     /* the plan would exceed the caller's device-memory budget */
+    SG_ECUDA = 4,       /* a CUDA runtime call failed */
+    SG_ETIMEOUT = 5,    /* a bounded wait ran out */
+    SG_EBUSY = 6,       /* the request is still running */
+    SG_ECANCELLED = 7,  /* the request was cancelled */
+    SG_ENOTFOUND = 8    /* unknown ticket */
+} sg_status;
+
+typedef enum {
+    SG_FP64 = 0,        /* FP64 fields, FP64 transforms and sums */
+    SG_FP32 = 1         /* FP32 fields and transforms with FP64-built kernel spectra;
+                           compensated (FP64) accumulation across direct-sum tiles */
+} sg_precision;
+
+typedef enum {
+    SG_SLOPES_NONE = 0,     /* order-0: deltax = deltay = 0 (first-order accurate) */
+    SG_SLOPES_CENTRAL = 1,  /* deltax, deltay by central differences on the patch,
+                               neighbours outside the patch counting as zero
+                               (single-patch geometries only) */
+    SG_SLOPES_CALLER = 2    /* deltax, deltay supplied by the caller */
+} sg_slope_mode;
+
+typedef struct {
+    int level;          /* refinement level, 0 = coarsest */
+    int nx, ny;         /* cells along x and y, each >= 1 */
+    double x0, y0;      /* lower-left corner of the patch */
+    double h;           /* cell width (square cells) */
+} sg_patch;
+
+typedef struct {
+    int npatches;               /* >= 1 */
+    const sg_patch *patches;    /* sorted by level; level-0 patches first */
+    double G;                   /* gravitational constant */
+    int slope_mode;             /* an sg_slope_mode */
+} sg_geom;
+
+typedef struct {
+    int npatches;
+    int64_t ncells;             /* total cells over all patches (field array length) */
+    int64_t nleaves;            /* leaf cells (targets) */
+    int64_t cross_pairs;        /* leaf-target x leaf-source pairs summed directly */
+    int64_t device_bytes;       /* device memory held by the plan */
+    int64_t scratch_bytes;      /* of which per-call scratch */
+    int max_pad;                /* largest padded FFT length */
+} sg_plan_info;
+
+typedef struct sg_plan sg_plan;
+
+/*
+ * Check a geometry without touching a GPU. Rules: every patch has nx, ny >= 1
+ * and h > 0; level-0 patches share one lattice of cell width h0 and do not
+ * overlap; a patch of level l+1 has h = h_l / 2, lies inside one level-l patch,
+ * starts on that patch's cell lattice and covers whole parent cells (even nx,
+ * ny); patches of one level do not overlap; at most 12 levels; the lattice of
+ * the finest level's half-cells spans at most 2^23 units per axis; a single
+ * patch has at most 2048 cells per side. slope_mode SG_SLOPES_CENTRAL needs a
+ * single patch. Returns SG_OK or SG_EINVAL.
+ */
+sg_status sg_geom_validate(const sg_geom *geom);
+
+/*
+ * Create a plan: validate the geometry, allocate the plan's device memory,
+ * generate the FP64 kernel tables of every patch (Section 2 closed forms),
+ * transform them into kernel spectra, and build the cross-patch target and
+ * corner-tile lists. Device work runs on the legacy default stream and is
+ * complete when the call returns.
+ *   geom        geometry (host memory, read during the call only)
+ *   prec        SG_FP64 or SG_FP32
+ *   hbm_budget  maximum device bytes the plan may hold (0 = no limit);
+ *               SG_EBUDGET if exceeded
+ *   out         receives the plan handle (unchanged on error)
+ * Errors: SG_EINVAL (geometry, precision, null pointer), SG_EBUDGET,
+ * SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_plan_create(const sg_geom *geom, sg_precision prec, size_t hbm_budget, sg_plan **out);
+
+/* Release a plan and its device memory (synchronises the device first). NULL is a no-op. */
+sg_status sg_plan_destroy(sg_plan *plan);
+
+/* Sizes and counts of a plan (host memory). */
+sg_status sg_plan_get_info(const sg_plan *plan, sg_plan_info *out);
+
+/*
+ * Host-only estimate of the device bytes sg_plan_create would hold for this
+ * geometry and precision (written to *bytes). SG_EINVAL for an invalid geometry.
+ */
+sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes);
+
+/*
+ * Copy one FP64 kernel table of patch `patch` to host memory, regenerated on
+ * the device: which = 0..5 selects K^{x,0}, K^{x,x}, K^{x,y}, K^{y,0},
+ * K^{y,x}, K^{y,y} (Section 2). Entry [n + ny - 1][m + nx - 1] (row-major,
+ * (2 nx - 1) x (2 ny - 1) doubles) holds the integral over a source cell whose
+ * centre is offset by (m h, n h) from the target centre, in physical units
+ * (K^{.,0} dimensionless, the others proportional to h).
+ *   host_out  caller-owned host buffer of n doubles; n must be >= (2nx-1)(2ny-1)
+ * Synchronous. Errors: SG_EINVAL, SG_ECUDA.
+ */
+sg_status sg_kernel_tables(const sg_plan *plan, int patch, int which, double *host_out, size_t n);
+
+/*
+ * Enqueue one force solve on `stream`.
+ *   sigma       device pointer, ncells elements (sigma0 per cell)
+ *   deltax/y    device pointers, ncells elements each; read only for
+ *               SG_SLOPES_CALLER, otherwise may be NULL
+ *   fx, fy      device pointers, ncells elements each, written at leaf cells
+ * Pointers must be aligned to their element size. Input and output buffers must
+ * not overlap. The call returns once the work is enqueued; the caller
+ * synchronises the stream before reading fx, fy.
+ * Errors: SG_EINVAL (null plan or pointer, wrong device current), SG_ECUDA.
+ */
+sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
+                   void *fx, void *fy, void *stream);
+
+/*
+ * The same solve with HOST buffers: copies the inputs to the plan's device
+ * staging buffers, runs sg_force on `stream`, copies Fx, Fy back and waits for
+ * the stream. Host buffers may be pageable or pinned (pinned is faster).
+ * Errors: as sg_force, plus SG_ENOMEM if the staging buffers cannot be allocated.
+ */
+sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
+                        void *fx, void *fy, void *stream);
+
+/*
+ * Per-stage device timers (tracing). With timing enabled, every sg_force on the
+ * plan records CUDA events around each kernel on the call's stream;
+ * sg_plan_get_timing waits for the last call's events and writes the summed
+ * milliseconds of its stages to ms[0..5]: 0 row transforms (forward), 1 column
+ * transforms with the spectral multiply, 2 row transforms (inverse), 3 corner
+ * weights, 4 cross-patch direct sum, 5 composite AMR sources. n must be >= 6.
+ * Timing adds two event records per stage; it is off by default.
+ */
+sg_status sg_plan_set_timing(sg_plan *plan, int enable);
+sg_status sg_plan_get_timing(sg_plan *plan, double *ms, int n);
+
+/* Static, human-readable name of a status. */
+const char *sg_strerror(sg_status status);
+
+/* Message of the last error reported on the calling thread ("" if none). */
+const char *sg_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int sg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

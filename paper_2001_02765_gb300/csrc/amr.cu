@@ -1,0 +1,131 @@
+// Composite sources of an AMR hierarchy.
+//
+// The force of Eq. eqnXforce2 sums the piecewise-linear density of the leaf
+// cells. The same function is the telescoping sum over patches of
+//   S_0 = f_0                                  on level-0 patches,
+//   S_l = f_l - P(f_{l-1})                     on a patch of level l >= 1,
+// where f_l is the level-l data with every covered cell filled by the
+// restriction of its four children, and P(f_{l-1}) is the parent's linear
+// function evaluated on the children (exact: a linear function restricted to a
+// child cell is linear, same slopes, value at the child centre). At any point
+// the sum telescopes to the leaf density there, so summing the closed-form
+// integrals over the S_l of every patch gives the leaf sum exactly. The gain is
+// numerical: S_l (l >= 1) is the difference between two representations of the
+// same density and is small, and f_0 has no hole, so no corner weight along a
+// patch boundary is of the size of the density itself.
+//
+// Restriction (any choice cancels in the sum; this one is the least-squares
+// linear fit of the four children over the parent cell of width H):
+//   sigma0 = mean(sigma0_k)
+//   deltax = (3 / (4 H)) (sum_right sigma0_k - sum_left sigma0_k) + (1/16) sum deltax_k
+//   deltay = (3 / (4 H)) (sum_top sigma0_k - sum_bottom sigma0_k) + (1/16) sum deltay_k
+// It is exact for linear data.
+#include "common.cuh"
+
+namespace {
+
+// Fill the cells of patch p: leaves copy the input, covered cells restrict
+// their children's filled values (already written: patches run finest first).
+template <typename T>
+__global__ void k_fill(sg_patch_dev p, const int4 *__restrict__ cov, const int *__restrict__ cov_child,
+                       const sg_patch_dev *__restrict__ pd, const T *__restrict__ sigma, const T *__restrict__ dx,
+                       const T *__restrict__ dy, T *__restrict__ s)
+{
+    const int64_t n = (int64_t)p.nx * p.ny;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % p.nx), j = (int)(e / p.nx);
+        const int64_t o = p.cell_off + e;
+        int c = -1;
+        for (int k = 0; k < p.ncov; ++k) {
+            const int4 r = cov[p.cov_off + k];
+            if (i >= r.x && i < r.z && j >= r.y && j < r.w) {
+                c = k;
+                break;
+            }
+        }
+        double s0, sx, sy;
+        if (c < 0) {
+            s0 = (double)sigma[o];
+            sx = dx ? (double)dx[o] : 0.0;
+            sy = dy ? (double)dy[o] : 0.0;
+        } else {
+            const int4 r = cov[p.cov_off + c];
+            const sg_patch_dev q = pd[cov_child[p.cov_off + c]];
+            const int ci = 2 * (i - r.x), cj = 2 * (j - r.y);
+            double sum = 0, right = 0, top = 0, gx = 0, gy = 0;
+            for (int b = 0; b < 2; ++b) {
+                for (int a = 0; a < 2; ++a) {
+                    const int64_t oc = q.cell_off + (int64_t)(cj + b) * q.nx + (ci + a);
+                    const double v = (double)s[oc];
+                    sum += v;
+                    right += a ? v : -v;
+                    top += b ? v : -v;
+                    gx += (double)s[oc + q.ncells_plane];
+                    gy += (double)s[oc + 2 * q.ncells_plane];
+                }
+            }
+            s0 = 0.25 * sum;
+            sx = 0.75 / p.h * right + gx / 16.0;
+            sy = 0.75 / p.h * top + gy / 16.0;
+        }
+        s[o] = (T)s0;
+        s[o + p.ncells_plane] = (T)sx;
+        s[o + 2 * p.ncells_plane] = (T)sy;
+    }
+}
+
+// Replace the filled values of patch q (level >= 1) by q - P(parent), in place.
+template <typename T>
+__global__ void k_defect(sg_patch_dev q, sg_patch_dev p, T *__restrict__ s)
+{
+    const int64_t n = (int64_t)q.nx * q.ny;
+    const int64_t P = q.ncells_plane;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % q.nx), j = (int)(e / q.nx);
+        const int64_t o = q.cell_off + e;
+        const int64_t op = p.cell_off + (int64_t)(q.pj0 + j / 2) * p.nx + (q.pi0 + i / 2);
+        const double ox = ((i & 1) - 0.5) * q.h, oy = ((j & 1) - 0.5) * q.h;
+        const double px = (double)s[op + P], py = (double)s[op + 2 * P];
+        const double pv = (double)s[op] + px * ox + py * oy;
+        s[o] = (T)((double)s[o] - pv);
+        s[o + P] = (T)((double)s[o + P] - px);
+        s[o + 2 * P] = (T)((double)s[o + 2 * P] - py);
+    }
+}
+
+template <typename T>
+sg_status prepare_t(sg_plan *plan, const void *sigma, const void *dx, const void *dy, cudaStream_t st)
+{
+    T *s = (T *)plan->sfield;
+    const bool slopes = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    for (int k = plan->npatches - 1; k >= 0; --k) {
+        const sg_patch_dev &d = plan->pp[k].d;
+        const int64_t n = (int64_t)d.nx * d.ny;
+        int grid = (int)((n + 255) / 256);
+        if (grid > 4096) grid = 4096;
+        k_fill<T><<<grid, 256, 0, st>>>(d, plan->cov_rects, plan->cov_child, plan->patch_dev, (const T *)sigma,
+                                        slopes ? (const T *)dx : nullptr, slopes ? (const T *)dy : nullptr, s);
+        SG_CUDA_TRY(cudaGetLastError());
+    }
+    for (int k = plan->npatches - 1; k >= 0; --k) {
+        const sg_patch_dev &d = plan->pp[k].d;
+        if (d.parent < 0) continue;
+        const int64_t n = (int64_t)d.nx * d.ny;
+        int grid = (int)((n + 255) / 256);
+        if (grid > 4096) grid = 4096;
+        k_defect<T><<<grid, 256, 0, st>>>(d, plan->pp[d.parent].d, s);
+        SG_CUDA_TRY(cudaGetLastError());
+    }
+    return SG_OK;
+}
+
+}  // namespace
+
+sg_status sg_amr_prepare(sg_plan *plan, const void *sigma, const void *dx, const void *dy, cudaStream_t st)
+{
+    sg_timing_begin(plan, SG_STAGE_COMPOSITE, st);
+    sg_status r = plan->prec == SG_FP64 ? prepare_t<double>(plan, sigma, dx, dy, st)
+                                        : prepare_t<float>(plan, sigma, dx, dy, st);
+    sg_timing_end(plan, SG_STAGE_COMPOSITE, st);
+    return r;
+}

@@ -1,0 +1,691 @@
+// Host side of the C ABI: geometry analysis, plan construction, entry points.
+#include "common.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+// ------------------------------------------------------------------ errors --
+
+static thread_local char g_last_error[256] = "";
+
+void sg_set_last_cuda_error(cudaError_t e, const char *what)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
+
+static void set_error(const char *msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+// ------------------------------------------------------------------ timing --
+
+struct sg_timing {
+    std::vector<cudaEvent_t> pool;      // created on demand, reused
+    std::vector<int> stage;             // stage of each recorded (begin, end) pair
+    int used = 0;                       // events used by the last solve
+    int open = -1;                      // index of the pending begin event
+};
+
+static cudaEvent_t timing_event(sg_timing *t)
+{
+    if (t->used == (int)t->pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        t->pool.push_back(e);
+    }
+    return t->pool[t->used++];
+}
+
+void sg_timing_reset(sg_plan *plan)
+{
+    if (!plan->timing) return;
+    plan->timing->used = 0;
+    plan->timing->stage.clear();
+    plan->timing->open = -1;
+}
+
+void sg_timing_begin(sg_plan *plan, int stage, cudaStream_t st)
+{
+    sg_timing *t = plan->timing;
+    if (!t) return;
+    cudaEvent_t e = timing_event(t);
+    if (!e) return;
+    cudaEventRecord(e, st);
+    t->open = t->used - 1;
+    t->stage.push_back(stage);
+}
+
+void sg_timing_end(sg_plan *plan, int stage, cudaStream_t st)
+{
+    sg_timing *t = plan->timing;
+    if (!t || t->open < 0) return;
+    cudaEvent_t e = timing_event(t);
+    if (!e) return;
+    cudaEventRecord(e, st);
+    t->open = -1;
+    (void)stage;
+}
+
+// --------------------------------------------------------- geometry analysis --
+
+namespace {
+
+struct geom_info {
+    int n = 0;
+    int lmax = 0;
+    double h0 = 0, X0 = 0, Y0 = 0, lambda = 0;
+    std::vector<int> parent, ox, oy, step;
+    std::vector<std::vector<int4>> cov;       // per patch, covered rectangles in its cells
+    std::vector<std::vector<int>> cov_child;  // per patch, the child patch of each rectangle
+    std::vector<std::vector<uint8_t>> leaf;   // per patch, leaf mask [ny][nx]
+    std::vector<int64_t> nleaf, cell_off;
+    int64_t ncells = 0, nleaves = 0, cross_pairs = 0;
+};
+
+bool near_int(double x, long long *out)
+{
+    const double r = nearbyint(x);
+    if (fabs(x - r) > 1e-9 * (fabs(x) > 1.0 ? fabs(x) : 1.0)) return false;
+    if (out) *out = (long long)r;
+    return true;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+sg_status fail(const char *msg)
+{
+    set_error(msg);
+    return SG_EINVAL;
+}
+
+sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
+{
+    if (!g) return fail("geometry is NULL");
+    if (g->npatches < 1 || !g->patches) return fail("geometry has no patches");
+    if (!isfinite(g->G)) return fail("G is not finite");
+    if (g->slope_mode < SG_SLOPES_NONE || g->slope_mode > SG_SLOPES_CALLER) return fail("unknown slope mode");
+    const int n = g->npatches;
+    const sg_patch *P = g->patches;
+    gi.n = n;
+    if (g->slope_mode == SG_SLOPES_CENTRAL && n != 1) return fail("central slopes need a single patch");
+    if (P[0].level != 0) return fail("the first patch must be on level 0");
+    for (int k = 0; k < n; ++k) {
+        if (P[k].nx < 1 || P[k].ny < 1 || P[k].nx > SG_MAX_PATCH_SIDE || P[k].ny > SG_MAX_PATCH_SIDE)
+            return fail("patch size out of range [1, 2048]");
+        if (!finite_pos(P[k].h) || !isfinite(P[k].x0) || !isfinite(P[k].y0)) return fail("patch origin or h invalid");
+        if (P[k].level < 0 || P[k].level >= SG_MAX_LEVELS) return fail("patch level out of range");
+        if (k > 0 && P[k].level < P[k - 1].level) return fail("patches are not sorted by level");
+        if (P[k].level > gi.lmax) gi.lmax = P[k].level;
+    }
+    gi.h0 = P[0].h;
+    gi.X0 = P[0].x0;
+    gi.Y0 = P[0].y0;
+    for (int k = 0; k < n; ++k) {
+        const double want = gi.h0 / (double)(1 << P[k].level);
+        if (fabs(P[k].h - want) > 1e-12 * want) return fail("cell width must halve per level");
+        if (P[k].level == 0) {
+            if (P[k].x0 < gi.X0) gi.X0 = P[k].x0;
+            if (P[k].y0 < gi.Y0) gi.Y0 = P[k].y0;
+        }
+    }
+    gi.lambda = gi.h0 / (double)(1LL << (gi.lmax + 1));
+    gi.parent.assign(n, -1);
+    gi.ox.assign(n, 0);
+    gi.oy.assign(n, 0);
+    gi.step.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+        long long ix, iy;
+        if (!near_int((P[k].x0 - gi.X0) / gi.lambda, &ix) || !near_int((P[k].y0 - gi.Y0) / gi.lambda, &iy))
+            return fail("patch origin is off the lattice");
+        const long long st = 1LL << (gi.lmax - P[k].level + 1);
+        if (ix + (long long)P[k].nx * st > (1LL << 23) || iy + (long long)P[k].ny * st > (1LL << 23))
+            return fail("hierarchy spans more than 2^23 finest half-cells");
+        gi.ox[k] = (int)ix;
+        gi.oy[k] = (int)iy;
+        gi.step[k] = (int)st;
+    }
+    // alignment, nesting and overlap, on the lattice
+    for (int k = 0; k < n; ++k) {
+        const int L = P[k].level;
+        const long long x0 = gi.ox[k], y0 = gi.oy[k];
+        const long long x1 = x0 + (long long)P[k].nx * gi.step[k], y1 = y0 + (long long)P[k].ny * gi.step[k];
+        if (L == 0) {
+            if (x0 % gi.step[k] || y0 % gi.step[k]) return fail("level-0 patches are not on one lattice");
+        } else {
+            if (P[k].nx % 2 || P[k].ny % 2) return fail("refined patches need even cell counts");
+            int par = -1;
+            for (int q = 0; q < n; ++q) {
+                if (P[q].level != L - 1) continue;
+                const long long px0 = gi.ox[q], py0 = gi.oy[q];
+                const long long px1 = px0 + (long long)P[q].nx * gi.step[q], py1 = py0 + (long long)P[q].ny * gi.step[q];
+                if (x0 >= px0 && x1 <= px1 && y0 >= py0 && y1 <= py1) {
+                    par = q;
+                    break;
+                }
+            }
+            if (par < 0) return fail("a refined patch does not lie inside one patch of the level below");
+            if ((x0 - gi.ox[par]) % gi.step[par] || (y0 - gi.oy[par]) % gi.step[par])
+                return fail("a refined patch does not start on its parent's cell lattice");
+            gi.parent[k] = par;
+        }
+        for (int q = 0; q < k; ++q) {
+            if (P[q].level != L) continue;
+            const long long qx0 = gi.ox[q], qy0 = gi.oy[q];
+            const long long qx1 = qx0 + (long long)P[q].nx * gi.step[q], qy1 = qy0 + (long long)P[q].ny * gi.step[q];
+            if (x0 < qx1 && qx0 < x1 && y0 < qy1 && qy0 < y1) return fail("patches of one level overlap");
+        }
+    }
+    // covered rectangles, leaves
+    gi.cov.assign(n, {});
+    gi.cov_child.assign(n, {});
+    gi.nleaf.assign(n, 0);
+    gi.cell_off.assign(n, 0);
+    if (build_masks) gi.leaf.assign(n, {});
+    for (int k = 0; k < n; ++k) {
+        if (gi.parent[k] >= 0) {
+            const int p = gi.parent[k];
+            int4 r;
+            r.x = (gi.ox[k] - gi.ox[p]) / gi.step[p];
+            r.y = (gi.oy[k] - gi.oy[p]) / gi.step[p];
+            r.z = r.x + P[k].nx / 2;
+            r.w = r.y + P[k].ny / 2;
+            gi.cov[p].push_back(r);
+            gi.cov_child[p].push_back(k);
+        }
+    }
+    gi.ncells = 0;
+    gi.nleaves = 0;
+    for (int k = 0; k < n; ++k) {
+        gi.cell_off[k] = gi.ncells;
+        gi.ncells += (int64_t)P[k].nx * P[k].ny;
+        int64_t covered = 0;
+        for (const int4 &r : gi.cov[k]) covered += (int64_t)(r.z - r.x) * (r.w - r.y);
+        gi.nleaf[k] = (int64_t)P[k].nx * P[k].ny - covered;
+        gi.nleaves += gi.nleaf[k];
+        if (build_masks) {
+            gi.leaf[k].assign((size_t)P[k].nx * P[k].ny, 1);
+            for (const int4 &r : gi.cov[k])
+                for (int j = r.y; j < r.w; ++j)
+                    for (int i = r.x; i < r.z; ++i) gi.leaf[k][(size_t)j * P[k].nx + i] = 0;
+        }
+    }
+    gi.cross_pairs = 0;
+    for (int k = 0; k < n; ++k) gi.cross_pairs += gi.nleaf[k] * (gi.nleaves - gi.nleaf[k]);
+    return SG_OK;
+}
+
+size_t elem_size(sg_precision prec) { return prec == SG_FP64 ? 8 : 4; }
+
+// corner tiles of every patch (the composite sources cover whole patches)
+void build_tiles(const sg_geom *g, const geom_info &gi, std::vector<sg_tile_desc> &tiles, std::vector<int> &first,
+                 std::vector<int> &count)
+{
+    first.assign(gi.n, 0);
+    count.assign(gi.n, 0);
+    for (int k = 0; k < gi.n; ++k) {
+        const sg_patch &p = g->patches[k];
+        first[k] = (int)tiles.size();
+        const int ntx = (p.nx + 1 + SG_TILE_X - 1) / SG_TILE_X, nty = (p.ny + 1 + SG_TILE_Y - 1) / SG_TILE_Y;
+        for (int b = 0; b < nty; ++b) {
+            for (int a = 0; a < ntx; ++a) {
+                const int ci0 = a * SG_TILE_X, cj0 = b * SG_TILE_Y;
+                sg_tile_desc t;
+                memset(&t, 0, sizeof(t));
+                t.patch = k;
+                t.ci0 = ci0;
+                t.cj0 = cj0;
+                t.step = gi.step[k];
+                t.ox = gi.ox[k] + ci0 * gi.step[k];
+                t.oy = gi.oy[k] + cj0 * gi.step[k];
+                tiles.push_back(t);
+            }
+        }
+        count[k] = (int)tiles.size() - first[k];
+    }
+}
+
+int choose_nsplit(int nblocks, int ntiles, int nsm)
+{
+    if (nblocks <= 0) return 1;
+    int s = (2 * nsm + nblocks - 1) / nblocks;
+    const int cap = ntiles / 4 > 1 ? ntiles / 4 : 1;
+    if (s > cap) s = cap;
+    if (s < 1) s = 1;
+    return s;
+}
+
+struct sizes {
+    int64_t spectra = 0, twiddles = 0, work = 0, direct = 0, geometry = 0;
+    int max_pad = SG_MIN_PAD;
+    int64_t total() const { return spectra + twiddles + work + direct + geometry; }
+};
+
+sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int ntiles, int nblocks, int nsplit)
+{
+    sizes s;
+    const size_t es = elem_size(prec);
+    int64_t work = 0;
+    for (int k = 0; k < gi.n; ++k) {
+        const int px = sg_pad_length(g->patches[k].nx), py = sg_pad_length(g->patches[k].ny);
+        if (px > s.max_pad) s.max_pad = px;
+        if (py > s.max_pad) s.max_pad = py;
+        s.spectra += 6LL * (px / 2 + 1) * (py / 2 + 1) * (int64_t)es;
+        const int64_t w = 5LL * (px / 2 + 1) * g->patches[k].ny * (int64_t)(2 * es);
+        if (w > work) work = w;
+    }
+    s.work = work;
+    for (int L = SG_MIN_PAD; L <= s.max_pad; L <<= 1) s.twiddles += (int64_t)L * (16 + 8);
+    if (gi.n > 1) {
+        s.direct = 3 * gi.ncells * (int64_t)es + (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
+                   gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
+                   (nsplit > 1 ? (int64_t)nsplit * gi.nleaves * 16 : 0);
+    }
+    s.geometry = (int64_t)gi.n * (int64_t)sizeof(sg_patch_dev) + 16 * (int64_t)gi.n;
+    return s;
+}
+
+int count_blocks(const geom_info &gi)
+{
+    if (gi.n <= 1) return 0;
+    int64_t b = 0;
+    for (int k = 0; k < gi.n; ++k) b += (gi.nleaf[k] + SG_DIRECT_THREADS - 1) / SG_DIRECT_THREADS;
+    return (int)b;
+}
+
+template <typename X>
+sg_status dev_alloc(sg_plan *plan, X **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) return SG_OK;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sg_set_last_cuda_error(e, "cudaMalloc");
+        return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
+    }
+    plan->device_bytes += (int64_t)bytes;
+    return SG_OK;
+}
+
+void plan_free(sg_plan *plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    if (plan->timing) {
+        for (cudaEvent_t e : plan->timing->pool) cudaEventDestroy(e);
+        delete plan->timing;
+    }
+    if (plan->pp) {
+        for (int k = 0; k < plan->npatches; ++k) cudaFree(plan->pp[k].spectra);
+    }
+    cudaFree(plan->twiddles);
+    cudaFree(plan->cov_rects);
+    cudaFree(plan->cov_child);
+    cudaFree(plan->sfield);
+    cudaFree(plan->work_fwd);
+    cudaFree(plan->work_inv);
+    cudaFree(plan->tiles);
+    cudaFree(plan->tile_w32);
+    cudaFree(plan->tile_w64);
+    cudaFree(plan->targets);
+    cudaFree(plan->blocks);
+    cudaFree(plan->patch_dev);
+    cudaFree(plan->partial);
+    cudaFree(plan->stage_in);
+    cudaFree(plan->stage_out);
+    delete[] plan->pp;
+    delete[] plan->patches_host;
+    delete plan;
+}
+
+sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan **out)
+{
+    geom_info gi;
+    SG_TRY(analyse(g, gi, true));
+    std::vector<sg_tile_desc> tiles;
+    std::vector<int> tfirst, tcount;
+    if (gi.n > 1) build_tiles(g, gi, tiles, tfirst, tcount);
+    int dev = 0, nsm = 152;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    SG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int nblocks = count_blocks(gi);
+    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), nsm);
+    const sizes sz = plan_sizes(g, gi, prec, (int)tiles.size(), nblocks, nsplit);
+    if (budget && (size_t)sz.total() > budget) {
+        set_error("plan exceeds the device-memory budget");
+        return SG_EBUDGET;
+    }
+
+    sg_plan *plan = new (std::nothrow) sg_plan();
+    if (!plan) return SG_ENOMEM;
+    memset(plan, 0, sizeof(*plan));
+    plan->device = dev;
+    plan->prec = prec;
+    plan->geom = *g;
+    plan->npatches = gi.n;
+    plan->patches_host = new (std::nothrow) sg_patch[gi.n];
+    plan->pp = new (std::nothrow) sg_patch_plan[gi.n];
+    if (!plan->patches_host || !plan->pp) {
+        plan_free(plan);
+        return SG_ENOMEM;
+    }
+    memcpy(plan->patches_host, g->patches, sizeof(sg_patch) * gi.n);
+    plan->geom.patches = plan->patches_host;
+    plan->ncells = gi.ncells;
+    plan->nleaves = gi.nleaves;
+    plan->cross_pairs = gi.cross_pairs;
+    plan->max_pad = sz.max_pad;
+    plan->lattice_unit = gi.lambda;
+    plan->lattice_x0 = gi.X0;
+    plan->lattice_y0 = gi.Y0;
+    plan->nsplit = nsplit;
+
+    sg_status st = SG_OK;
+    const size_t es = elem_size(prec);
+    // covered rectangles
+    std::vector<int4> cov_all;
+    std::vector<int> cov_child_all;
+    std::vector<sg_patch_dev> pdev(gi.n);
+    for (int k = 0; k < gi.n && st == SG_OK; ++k) {
+        sg_patch_plan &pp = plan->pp[k];
+        memset(&pp, 0, sizeof(pp));
+        pp.geom = g->patches[k];
+        sg_patch_dev &d = pp.d;
+        d.nx = g->patches[k].nx;
+        d.ny = g->patches[k].ny;
+        d.px = sg_pad_length(d.nx);
+        d.py = sg_pad_length(d.ny);
+        d.cell_off = gi.cell_off[k];
+        d.h = g->patches[k].h;
+        d.ox = gi.ox[k];
+        d.oy = gi.oy[k];
+        d.step = gi.step[k];
+        d.ncov = (int)gi.cov[k].size();
+        d.cov_off = (int)cov_all.size();
+        for (const int4 &r : gi.cov[k]) cov_all.push_back(r);
+        for (int c : gi.cov_child[k]) cov_child_all.push_back(c);
+        d.parent = gi.parent[k];
+        d.pi0 = d.parent >= 0 ? (gi.ox[k] - gi.ox[d.parent]) / gi.step[d.parent] : 0;
+        d.pj0 = d.parent >= 0 ? (gi.oy[k] - gi.oy[d.parent]) / gi.step[d.parent] : 0;
+        d.ncells_plane = gi.ncells;
+        if (gi.n > 1) {
+            pp.tile_first = tfirst[k];
+            pp.tile_count = tcount[k];
+        }
+        pdev[k] = d;
+        st = dev_alloc(plan, &pp.spectra, 6 * (size_t)(d.px / 2 + 1) * (d.py / 2 + 1) * es);
+    }
+    plan->ncov_total = (int)cov_all.size();
+    if (st == SG_OK) st = dev_alloc(plan, &plan->cov_rects, (cov_all.empty() ? 1 : cov_all.size()) * sizeof(int4));
+    if (st == SG_OK && !cov_all.empty())
+        st = cudaMemcpy(plan->cov_rects, cov_all.data(), cov_all.size() * sizeof(int4), cudaMemcpyHostToDevice) ==
+                     cudaSuccess ? SG_OK : SG_ECUDA;
+    if (st == SG_OK) st = dev_alloc(plan, &plan->cov_child, (cov_child_all.empty() ? 1 : cov_child_all.size()) * sizeof(int));
+    if (st == SG_OK && !cov_child_all.empty())
+        st = cudaMemcpy(plan->cov_child, cov_child_all.data(), cov_child_all.size() * sizeof(int),
+                        cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
+    if (st == SG_OK && gi.n > 1) {
+        st = dev_alloc(plan, &plan->sfield, 3 * (size_t)gi.ncells * es);
+        plan->scratch_bytes += 3 * gi.ncells * (int64_t)es;
+    }
+    if (st == SG_OK) st = dev_alloc(plan, &plan->patch_dev, gi.n * sizeof(sg_patch_dev));
+    if (st == SG_OK)
+        st = cudaMemcpy(plan->patch_dev, pdev.data(), gi.n * sizeof(sg_patch_dev), cudaMemcpyHostToDevice) == cudaSuccess
+                 ? SG_OK : SG_ECUDA;
+    // transform scratch, sized for the largest patch
+    int64_t wf = 0, wi = 0;
+    for (int k = 0; k < gi.n; ++k) {
+        const int64_t q = (int64_t)(pdev[k].px / 2 + 1) * pdev[k].ny * (int64_t)(2 * es);
+        if (3 * q > wf) wf = 3 * q;
+        if (2 * q > wi) wi = 2 * q;
+    }
+    if (st == SG_OK) st = dev_alloc(plan, &plan->work_fwd, (size_t)wf);
+    if (st == SG_OK) st = dev_alloc(plan, &plan->work_inv, (size_t)wi);
+    plan->scratch_bytes = wf + wi;
+    // cross-patch direct sum
+    if (st == SG_OK && gi.n > 1 && !tiles.empty()) {
+        plan->ntiles = (int)tiles.size();
+        st = dev_alloc(plan, &plan->tiles, tiles.size() * sizeof(sg_tile_desc));
+        if (st == SG_OK)
+            st = cudaMemcpy(plan->tiles, tiles.data(), tiles.size() * sizeof(sg_tile_desc), cudaMemcpyHostToDevice) ==
+                         cudaSuccess ? SG_OK : SG_ECUDA;
+        const size_t nw = (size_t)plan->ntiles * SG_TILE_N;
+        if (st == SG_OK) {
+            if (prec == SG_FP64) st = dev_alloc(plan, &plan->tile_w64, nw * sizeof(sg_dvec4));
+            else st = dev_alloc(plan, &plan->tile_w32, nw * sizeof(float4));
+            plan->scratch_bytes += (int64_t)nw * 4 * (int64_t)es;
+        }
+        // targets: every leaf, row-major per patch, blocks of SG_DIRECT_THREADS
+        std::vector<int4> tg;
+        std::vector<sg_target_block> blocks;
+        tg.reserve((size_t)gi.nleaves);
+        for (int k = 0; k < gi.n; ++k) {
+            const sg_patch &p = g->patches[k];
+            int in_block = 0;
+            for (int j = 0; j < p.ny; ++j) {
+                for (int i = 0; i < p.nx; ++i) {
+                    if (!gi.leaf[k][(size_t)j * p.nx + i]) continue;
+                    if (in_block == 0) {
+                        sg_target_block b;
+                        b.patch = k;
+                        b.first = (int)tg.size();
+                        b.count = 0;
+                        b.pad = 0;
+                        blocks.push_back(b);
+                    }
+                    int4 t;
+                    t.x = gi.ox[k] + (2 * i + 1) * (gi.step[k] / 2);
+                    t.y = gi.oy[k] + (2 * j + 1) * (gi.step[k] / 2);
+                    t.z = (int)(gi.cell_off[k] + (int64_t)j * p.nx + i);
+                    t.w = k;
+                    tg.push_back(t);
+                    blocks.back().count++;
+                    if (++in_block == SG_DIRECT_THREADS) in_block = 0;
+                }
+            }
+        }
+        plan->ntargets = (int)tg.size();
+        plan->nblocks = (int)blocks.size();
+        if (st == SG_OK) st = dev_alloc(plan, &plan->targets, tg.size() * sizeof(int4));
+        if (st == SG_OK)
+            st = cudaMemcpy(plan->targets, tg.data(), tg.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess
+                     ? SG_OK : SG_ECUDA;
+        if (st == SG_OK) st = dev_alloc(plan, &plan->blocks, blocks.size() * sizeof(sg_target_block));
+        if (st == SG_OK)
+            st = cudaMemcpy(plan->blocks, blocks.data(), blocks.size() * sizeof(sg_target_block),
+                            cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
+        if (st == SG_OK && nsplit > 1) {
+            st = dev_alloc(plan, &plan->partial, (size_t)nsplit * tg.size() * 2 * sizeof(double));
+            plan->scratch_bytes += (int64_t)nsplit * (int64_t)tg.size() * 16;
+        }
+    }
+    if (st == SG_OK) st = sg_twiddles_build(plan);
+    if (st == SG_OK) st = sg_tables_build(plan);
+    if (st == SG_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            sg_set_last_cuda_error(e, "sg_plan_create");
+            st = SG_ECUDA;
+        }
+    }
+    if (st != SG_OK) {
+        plan_free(plan);
+        return st;
+    }
+    *out = plan;
+    return SG_OK;
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+
+// --------------------------------------------------------------- the C ABI --
+
+extern "C" {
+
+sg_status sg_geom_validate(const sg_geom *geom)
+{
+    geom_info gi;
+    return analyse(geom, gi, false);
+}
+
+sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes)
+{
+    if (!bytes || (prec != SG_FP64 && prec != SG_FP32)) return SG_EINVAL;
+    geom_info gi;
+    SG_TRY(analyse(geom, gi, true));
+    std::vector<sg_tile_desc> tiles;
+    std::vector<int> tf, tc;
+    if (gi.n > 1) build_tiles(geom, gi, tiles, tf, tc);
+    const int nblocks = count_blocks(gi);
+    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152);
+    *bytes = plan_sizes(geom, gi, prec, (int)tiles.size(), nblocks, nsplit).total();
+    return SG_OK;
+}
+
+sg_status sg_plan_create(const sg_geom *geom, sg_precision prec, size_t hbm_budget, sg_plan **out)
+{
+    if (!out || (prec != SG_FP64 && prec != SG_FP32)) return fail("invalid precision or output pointer");
+    return plan_build(geom, prec, hbm_budget, out);
+}
+
+sg_status sg_plan_destroy(sg_plan *plan)
+{
+    plan_free(plan);
+    return SG_OK;
+}
+
+sg_status sg_plan_get_info(const sg_plan *plan, sg_plan_info *out)
+{
+    if (!plan || !out) return SG_EINVAL;
+    out->npatches = plan->npatches;
+    out->ncells = plan->ncells;
+    out->nleaves = plan->nleaves;
+    out->cross_pairs = plan->cross_pairs;
+    out->device_bytes = plan->device_bytes;
+    out->scratch_bytes = plan->scratch_bytes;
+    out->max_pad = plan->max_pad;
+    return SG_OK;
+}
+
+sg_status sg_kernel_tables(const sg_plan *plan, int patch, int which, double *host_out, size_t n)
+{
+    return sg_tables_copy(plan, patch, which, host_out, n);
+}
+
+sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
+                   void *stream)
+{
+    if (!plan || !sigma || !fx || !fy) return fail("null plan or field pointer");
+    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
+    const size_t es = elem_size(plan->prec);
+    if (!aligned(sigma, es) || !aligned(fx, es) || !aligned(fy, es) || (caller && (!aligned(deltax, es) || !aligned(deltay, es))))
+        return fail("misaligned field pointer");
+    int dev = -1;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) return fail("the plan's device is not current");
+    cudaStream_t st = (cudaStream_t)stream;
+    sg_timing_reset(plan);
+    const void *dx = caller ? deltax : nullptr, *dy = caller ? deltay : nullptr;
+    if (plan->npatches == 1) return sg_uniform_solve(plan, 0, sigma, dx, dy, fx, fy, st);
+    // AMR: composite sources, same-patch FFT convolutions, cross-patch direct sum
+    SG_TRY(sg_amr_prepare(plan, sigma, dx, dy, st));
+    const char *S = (const char *)plan->sfield;
+    const size_t plane = (size_t)plan->ncells * es;
+    for (int k = 0; k < plan->npatches; ++k) SG_TRY(sg_uniform_solve(plan, k, S, S + plane, S + 2 * plane, fx, fy, st));
+    SG_TRY(sg_cross_solve(plan, S, S + plane, S + 2 * plane, fx, fy, st));
+    return SG_OK;
+}
+
+sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
+                        void *stream)
+{
+    if (!plan || !sigma || !fx || !fy) return fail("null plan or field pointer");
+    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
+    int dev = -1;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) return fail("the plan's device is not current");
+    const size_t bytes = (size_t)plan->ncells * elem_size(plan->prec);
+    if (!plan->stage_in) {
+        SG_TRY(dev_alloc(plan, &plan->stage_in, 3 * bytes));
+        sg_status s = dev_alloc(plan, &plan->stage_out, 2 * bytes);
+        if (s != SG_OK) {
+            cudaFree(plan->stage_in);
+            plan->stage_in = nullptr;
+            plan->device_bytes -= (int64_t)(3 * bytes);
+            return s;
+        }
+        plan->stage_bytes = bytes;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char *in = (char *)plan->stage_in, *out = (char *)plan->stage_out;
+    SG_CUDA_TRY(cudaMemcpyAsync(in, sigma, bytes, cudaMemcpyHostToDevice, st));
+    if (caller) {
+        SG_CUDA_TRY(cudaMemcpyAsync(in + bytes, deltax, bytes, cudaMemcpyHostToDevice, st));
+        SG_CUDA_TRY(cudaMemcpyAsync(in + 2 * bytes, deltay, bytes, cudaMemcpyHostToDevice, st));
+    }
+    SG_TRY(sg_force(plan, in, caller ? in + bytes : nullptr, caller ? in + 2 * bytes : nullptr, out, out + bytes, stream));
+    SG_CUDA_TRY(cudaMemcpyAsync(fx, out, bytes, cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaMemcpyAsync(fy, out + bytes, bytes, cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
+sg_status sg_plan_set_timing(sg_plan *plan, int enable)
+{
+    if (!plan) return SG_EINVAL;
+    if (enable && !plan->timing) {
+        plan->timing = new (std::nothrow) sg_timing();
+        if (!plan->timing) return SG_ENOMEM;
+    } else if (!enable && plan->timing) {
+        cudaDeviceSynchronize();
+        for (cudaEvent_t e : plan->timing->pool) cudaEventDestroy(e);
+        delete plan->timing;
+        plan->timing = nullptr;
+    }
+    return SG_OK;
+}
+
+sg_status sg_plan_get_timing(sg_plan *plan, double *ms, int n)
+{
+    if (!plan || !ms || n < SG_NSTAGES) return SG_EINVAL;
+    for (int i = 0; i < SG_NSTAGES; ++i) ms[i] = 0.0;
+    sg_timing *t = plan->timing;
+    if (!t) return SG_EINVAL;
+    for (size_t k = 0; k < t->stage.size(); ++k) {
+        const int b = 2 * (int)k, e = b + 1;
+        if (e >= t->used) break;
+        SG_CUDA_TRY(cudaEventSynchronize(t->pool[e]));
+        float v = 0.f;
+        SG_CUDA_TRY(cudaEventElapsedTime(&v, t->pool[b], t->pool[e]));
+        ms[t->stage[k]] += v;
+    }
+    return SG_OK;
+}
+
+const char *sg_strerror(sg_status s)
+{
+    switch (s) {
+    case SG_OK: return "ok";
+    case SG_EINVAL: return "invalid argument";
+    case SG_ENOMEM: return "out of memory";
+    case SG_EBUDGET: return "device-memory budget exceeded";
+    case SG_ECUDA: return "CUDA error";
+    case SG_ETIMEOUT: return "timed out";
+    case SG_EBUSY: return "busy";
+    case SG_ECANCELLED: return "cancelled";
+    case SG_ENOTFOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+const char *sg_last_error(void) { return g_last_error; }
+
+int sg_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// Common definitions of the thin-disk self-gravity library (device and host).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "sg.h"
+
+#define SG_CUDA_TRY(expr)                                  \
+    do {                                                   \
+        cudaError_t sg_e_ = (expr);                        \
+        if (sg_e_ != cudaSuccess) {                        \
+            sg_set_last_cuda_error(sg_e_, #expr);          \
+            return SG_ECUDA;                               \
+        }                                                  \
+    } while (0)
+
+#define SG_TRY(expr)                                       \
+    do {                                                   \
+        sg_status sg_s_ = (expr);                          \
+        if (sg_s_ != SG_OK) return sg_s_;                  \
+    } while (0)
+
+void sg_set_last_cuda_error(cudaError_t e, const char *what);
+
+// ------------------------------------------------------------ complex math --
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <typename T> using cplx_t = typename cplx_of<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(decltype(C::x) re, decltype(C::x) im)
+{
+    C c;
+    c.x = re;
+    c.y = im;
+    return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
+{
+    return cmake<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+
+// 32-byte aligned FP64 4-vector (corner weights of FP64 plans)
+struct __align__(32) sg_dvec4 {
+    double x, y, z, w;
+};
+
+// ------------------------------------------------------------- plan layout --
+
+// Largest padded FFT length handled by the transform kernels.
+#define SG_MAX_PAD 4096
+#define SG_MIN_PAD 64
+#define SG_MAX_PATCH_SIDE 2048
+#define SG_MAX_LEVELS 12
+
+// Corner tiles of the cross-patch direct sum: TILE_X x TILE_Y corners.
+#define SG_TILE_X 16
+#define SG_TILE_Y 16
+#define SG_TILE_N (SG_TILE_X * SG_TILE_Y)
+// Leaf targets per CTA of the direct sum.
+#define SG_DIRECT_THREADS 256
+
+struct sg_tile_desc {
+    int patch;          // source patch
+    int ox, oy;         // lattice coordinates of corner (0, 0) of the tile
+    int step;           // corner spacing in lattice units
+    int ci0, cj0;       // first corner index (i, j) of the tile in its patch
+    int pad0, pad1;
+};
+
+struct sg_target_block {
+    int patch;          // patch of every target in the block
+    int first;          // first index into the target arrays
+    int count;          // targets in the block (<= SG_DIRECT_THREADS)
+    int pad;
+};
+
+struct sg_patch_dev {
+    int nx, ny;
+    int px, py;         // padded FFT lengths
+    int64_t cell_off;   // offset of the patch in the field arrays
+    double h;
+    int ox, oy;         // lattice coordinates of the patch's lower-left corner
+    int step;           // cell width in lattice units
+    int ncov;           // covered rectangles (child patch footprints) in cells
+    int cov_off;        // first covered rectangle in the plan's list
+    int parent;         // parent patch (-1 on level 0)
+    int pi0, pj0;       // offset of this patch in its parent's cells
+    int64_t ncells_plane;  // plane stride of the 3-field composite source arrays (= total cells)
+};
+
+struct sg_patch_plan {
+    sg_patch geom;
+    sg_patch_dev d;
+    // device buffers owned by the plan
+    void *spectra;      // 6 planes [(px/2+1) x (py/2+1)] of T (quarter spectra, scaled)
+    // tile range of this patch in the tile list
+    int tile_first, tile_count;
+};
+
+struct sg_plan {
+    int device;
+    sg_precision prec;
+    sg_geom geom;
+    int npatches;
+    sg_patch *patches_host;
+    sg_patch_plan *pp;
+    int64_t ncells;
+    int64_t nleaves;
+    int64_t cross_pairs;
+    int64_t device_bytes;
+    int64_t scratch_bytes;
+    int max_pad;
+    double lattice_unit;            // lambda: half of the finest cell width
+    double lattice_x0, lattice_y0;  // physical position of lattice coordinate 0
+
+    // twiddle tables exp(-2 pi i k / L), k < L, for each power of two L in
+    // [SG_MIN_PAD, max_pad]: FP64 copies then FP32 copies, back to back
+    void *twiddles;
+    int64_t tw64_off[16];           // byte offsets, indexed by log2 L
+    int64_t tw32_off[16];
+
+    // covered rectangles, int4 (i0, j0, i1, j1) in cell units of the parent patch,
+    // and the child patch that covers each
+    int4 *cov_rects;
+    int *cov_child;
+    int ncov_total;
+
+    // composite source fields of an AMR plan, 3 x ncells of T: the filled level
+    // data on level 0 and the fine-minus-prolonged-coarse difference on finer patches
+    void *sfield;
+
+    // uniform-transform scratch, sized for the largest patch
+    void *work_fwd;                 // 3 x (px/2+1) x ny complex
+    void *work_inv;                 // 2 x (px/2+1) x ny complex
+
+    // cross-patch direct sum
+    int ntiles;
+    sg_tile_desc *tiles;            // device
+    float4 *tile_w32;               // device, ntiles x SG_TILE_N x (B, X, Y, 0) weights (FP32 plans)
+    sg_dvec4 *tile_w64;              // the same in FP64 (FP64 plans)
+    int nsplit;                     // source-tile ranges per target block
+    double *partial;                // device, nsplit x ntargets x 2 (nsplit > 1 only)
+    int ntargets;
+    int4 *targets;                  // device: (lattice x, lattice y, output index, patch)
+    int nblocks;
+    sg_target_block *blocks;        // device
+    sg_patch_dev *patch_dev;        // device copy of every patch's sg_patch_dev
+
+    // host staging for sg_force_host
+    void *stage_in, *stage_out;
+    size_t stage_bytes;
+
+    // per-stage device timers of the last solve (NULL when timing is off)
+    struct sg_timing *timing;
+};
+
+// Stages timed by sg_plan_get_timing.
+enum { SG_STAGE_ROW_FWD = 0, SG_STAGE_COL_CONV = 1, SG_STAGE_ROW_INV = 2, SG_STAGE_WEIGHTS = 3,
+       SG_STAGE_DIRECT = 4, SG_STAGE_COMPOSITE = 5, SG_NSTAGES = 6 };
+
+// Record the start / end of a stage on a stream (no-op when timing is off).
+void sg_timing_begin(sg_plan *plan, int stage, cudaStream_t st);
+void sg_timing_end(sg_plan *plan, int stage, cudaStream_t st);
+void sg_timing_reset(sg_plan *plan);
+
+// ---------------------------------------------------------- host functions --
+
+sg_status sg_tables_build(sg_plan *plan);     // tables + spectra of every patch
+sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host_out, size_t n);
+sg_status sg_twiddles_build(sg_plan *plan);
+sg_status sg_uniform_solve(sg_plan *plan, int patch, const void *sigma, const void *dx, const void *dy,
+                           void *fx, void *fy, cudaStream_t st);
+sg_status sg_cross_solve(sg_plan *plan, const void *sigma, const void *dx, const void *dy,
+                         void *fx, void *fy, cudaStream_t st);
+sg_status sg_amr_prepare(sg_plan *plan, const void *sigma, const void *dx, const void *dy, cudaStream_t st);
+
+static inline int sg_ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+static inline int sg_pad_length(int n)
+{
+    int p = SG_MIN_PAD;
+    while (p < 2 * n - 1) p <<= 1;
+    return p;
+}

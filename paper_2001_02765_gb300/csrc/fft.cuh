@@ -1,0 +1,156 @@
+// Shared-memory Stockham FFT for power-of-two lengths, executed by a whole CTA.
+//
+// NB independent sequences of length L lie back to back in shared memory
+// (element k of sequence s at logical index s * L + k, see spad below). Each stage of radix R reads the
+// R inputs of every butterfly into registers, synchronises, applies the
+// twiddles and a radix-R DFT in registers and writes the outputs to their
+// auto-sorted positions, then synchronises again; one buffer therefore serves
+// every stage. Radix 8 is used while at least 8 points remain per sub-transform,
+// then one radix-4 or radix-2 stage.
+//
+// Stage with span NS (product of the radices before it) and radix R, for the
+// butterfly j in [0, L/R) of a sequence, k = j mod NS:
+//     v_r = x[j + r L/R] * W_{NS R}^{r k},   r = 0..R-1
+//     X = DFT_R(v)
+//     y[(j / NS) NS R + k + r NS] = X_r
+// (the Stockham auto-sort formulation; the output is in natural order).
+//
+// Twiddles come from a table tw[k] = exp(-2 pi i k / L), k < L, built in FP64
+// on the device; W_{NS R}^{r k} = tw[r k L / (NS R)]. The inverse transform
+// uses the conjugates and is not normalised.
+//
+// Shared-memory layout: element i of the batch is stored at spad(i), which
+// inserts one padding element every 16 (8-byte complex) or 8 (16-byte complex)
+// elements so that the strided stores of the early stages fall in distinct
+// banks (for a warp, about 1.1x the conflict-free wavefront count instead of
+// 2x). Every access to an FFT buffer goes through spad; spad_size(n) is the
+// number of elements a buffer holding n logical elements needs.
+#pragma once
+
+#include "common.cuh"
+
+template <typename C>
+__host__ __device__ __forceinline__ constexpr int spad(int i)
+{
+    return sizeof(C) == 8 ? i + (i >> 4) : i + (i >> 3);
+}
+
+template <typename C>
+__host__ __device__ __forceinline__ constexpr int spad_size(int n)
+{
+    return spad<C>(n - 1) + 1;
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ C twiddle(const C *__restrict__ tw, int idx)
+{
+    C w = __ldg(&tw[idx]);
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// multiply by -i (forward) or +i (inverse)
+template <typename C, bool INV>
+__device__ __forceinline__ C rot90(C a)
+{
+    return INV ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft2(C &a, C &b)
+{
+    C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft4(C &v0, C &v1, C &v2, C &v3)
+{
+    C t0 = cadd(v0, v2), t1 = csub(v0, v2);
+    C t2 = cadd(v1, v3), t3 = rot90<C, INV>(csub(v1, v3));
+    v0 = cadd(t0, t2);
+    v2 = csub(t0, t2);
+    v1 = cadd(t1, t3);
+    v3 = csub(t1, t3);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft8(C *v)
+{
+    using T = decltype(C::x);
+    const T s = (T)0.70710678118654752440;  // 1/sqrt(2)
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<C, INV>(e0, e1, e2, e3);
+    dft4<C, INV>(o0, o1, o2, o3);
+    // o_k *= W8^k, W8 = exp(-+ 2 pi i / 8)
+    C w1 = INV ? cmake<C>(s * (o1.x - o1.y), s * (o1.x + o1.y)) : cmake<C>(s * (o1.x + o1.y), s * (o1.y - o1.x));
+    C w2 = rot90<C, INV>(o2);
+    C w3 = INV ? cmake<C>(-s * (o3.x + o3.y), s * (o3.x - o3.y)) : cmake<C>(s * (o3.y - o3.x), -s * (o3.x + o3.y));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, w1);
+    v[5] = csub(e1, w1);
+    v[2] = cadd(e2, w2);
+    v[6] = csub(e2, w2);
+    v[3] = cadd(e3, w3);
+    v[7] = csub(e3, w3);
+}
+
+template <typename C, int L, int NB, int THREADS, int NS, int R, bool INV>
+__device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
+{
+    constexpr int NBF = NB * (L / R);            // butterflies in the stage
+    constexpr int PER = (NBF + THREADS - 1) / THREADS;
+    C v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * THREADS;
+        if (NBF % THREADS == 0 || b < NBF) {
+            const int seq = b / (L / R), j = b % (L / R);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = buf[spad<C>(seq * L + j + r * (L / R))];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * THREADS;
+        if (NBF % THREADS == 0 || b < NBF) {
+            const int seq = b / (L / R), j = b % (L / R);
+            const int k = j % NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], twiddle<C, INV>(tw, r * k * (L / (NS * R))));
+            }
+            if constexpr (R == 8) dft8<C, INV>(v[p]);
+            else if constexpr (R == 4) dft4<C, INV>(v[p][0], v[p][1], v[p][2], v[p][3]);
+            else dft2<C, INV>(v[p][0], v[p][1]);
+            const int base = seq * L + (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[spad<C>(base + r * NS)] = v[p][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <typename C, int L, int NB, int THREADS, int NS, bool INV>
+__device__ __forceinline__ void fft_stages(C *buf, const C *__restrict__ tw)
+{
+    if constexpr (NS < L) {
+        constexpr int REM = L / NS;
+        constexpr int R = REM >= 8 ? 8 : REM;
+        fft_stage<C, L, NB, THREADS, NS, R, INV>(buf, tw);
+        fft_stages<C, L, NB, THREADS, NS * R, INV>(buf, tw);
+    }
+}
+
+// FFT of NB sequences of length L in shared memory by THREADS threads.
+// Must be called by every thread of the CTA (it synchronises). The caller
+// synchronises before the call so that the inputs are visible.
+template <typename C, int L, int NB, int THREADS, bool INV>
+__device__ __forceinline__ void fft_batch(C *buf, const C *__restrict__ tw)
+{
+    fft_stages<C, L, NB, THREADS, 1, INV>(buf, tw);
+}

@@ -1,0 +1,337 @@
+// Uniform-patch force as a zero-padded 2-D FFT convolution (introduction and
+// conclusion of Tseng, Shang & Yen; the uniform-grid route of Yen et al. 2012).
+//
+// For a patch of nx x ny cells padded to Px x Py (powers of two, P >= 2n - 1):
+//   1. k_row_fwd : per row j < ny, the three input fields (sigma0, deltax,
+//                  deltay; the slopes either read or formed by central
+//                  differences on the fly, covered cells masked to zero) are
+//                  real-to-complex transformed along x, two rows per complex
+//                  FFT, and the Px/2+1 bins are written transposed:
+//                  work_fwd[f][kx][j].
+//   2. k_col_conv: per bin column kx, each field's column (ny values, zero
+//                  padded to Py) is transformed along y, multiplied with the
+//                  kernel spectra and accumulated into Fx^, Fy^ in registers:
+//                    Fx^ = sigma^ (i a) + deltax^ b + deltay^ (s c)
+//                    Fy^ = sigma^ (i s d) + deltay^ e + deltax^ (s f)
+//                  (s = -1 for ky > Py/2: those planes are odd in ky); both are
+//                  transformed back along y and the first ny rows written:
+//                  work_inv[o][kx][j].
+//   3. k_row_inv : per row j < ny, the two half spectra are inverse transformed
+//                  along x (two rows per complex FFT) and the first nx values
+//                  written to Fx, Fy. The spectra already carry G / (Px Py).
+// Every transform is the shared-memory Stockham FFT of fft.cuh.
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace {
+
+template <typename T>
+struct field_src {
+    const T *sigma, *dx, *dy;
+    int nx, ny;
+    T inv2h;
+    int mode;          // sg_slope_mode
+    const int4 *cov;   // covered rectangles (i0, j0, i1, j1), cells of this patch
+    int ncov;
+};
+
+template <typename T>
+__device__ __forceinline__ bool covered(const field_src<T> &s, int j, int i)
+{
+    for (int c = 0; c < s.ncov; ++c) {
+        const int4 r = __ldg(&s.cov[c]);
+        if (i >= r.x && i < r.z && j >= r.y && j < r.w) return true;
+    }
+    return false;
+}
+
+template <typename T>
+__device__ __forceinline__ T sigma_at(const field_src<T> &s, int j, int i)
+{
+    if (i < 0 || i >= s.nx || j < 0 || j >= s.ny) return (T)0;
+    return s.sigma[(int64_t)j * s.nx + i];
+}
+
+template <typename T>
+__device__ __forceinline__ T field_value(const field_src<T> &s, int f, int j, int i)
+{
+    if (j >= s.ny || i >= s.nx) return (T)0;
+    if (s.ncov && covered(s, j, i)) return (T)0;
+    const int64_t o = (int64_t)j * s.nx + i;
+    if (f == 0) return s.sigma[o];
+    if (s.mode == SG_SLOPES_CALLER) return f == 1 ? s.dx[o] : s.dy[o];
+    // central differences, zero beyond the patch edge
+    if (f == 1) return (sigma_at(s, j, i + 1) - sigma_at(s, j, i - 1)) * s.inv2h;
+    return (sigma_at(s, j + 1, i) - sigma_at(s, j - 1, i)) * s.inv2h;
+}
+
+// ---------------------------------------------------------------- kernels --
+
+template <typename T, int PX, int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T> *__restrict__ work,
+                                                     const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int RB = 2 * NB;
+    constexpr int QX = PX / 2 + 1;
+    const int f = blockIdx.y;
+    const int j0 = blockIdx.x * RB;
+    const int ny = src.ny;
+
+    // two rows per complex sequence: z = row(2s) + i row(2s+1)
+    for (int e = threadIdx.x; e < NB * PX; e += THREADS) {
+        const int s = e / PX, i = e % PX;
+        const int ja = j0 + 2 * s;
+        const T a = field_value(src, f, ja, i);
+        const T b = field_value(src, f, ja + 1, i);
+        buf[spad<C>(e)] = cmake<C>(a, b);
+    }
+    __syncthreads();
+    fft_batch<C, PX, NB, THREADS, false>(buf, tw);
+
+    // unpack: A[k] = (Z[k] + conj Z[-k]) / 2, B[k] = (Z[k] - conj Z[-k]) / 2i
+    const T half = (T)0.5;
+    for (int e = threadIdx.x; e < QX * RB; e += THREADS) {
+        const int kx = e / RB, r = e % RB;
+        const int j = j0 + r;
+        if (j >= ny) continue;
+        const int s = r >> 1;
+        const C z = buf[spad<C>(s * PX + kx)];
+        const C w = buf[spad<C>(s * PX + ((PX - kx) & (PX - 1)))];
+        C out;
+        if ((r & 1) == 0) out = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
+        else out = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
+        work[((int64_t)f * QX + kx) * ny + j] = out;
+    }
+}
+
+// resident CTAs per SM asked of the register allocator (spill-free choices)
+template <typename T, int PY>
+constexpr int col_min_blocks() { return sizeof(T) == 4 ? (PY == 2048 ? 3 : (PY == 4096 ? 1 : 2)) : 1; }
+
+template <typename T, int PY, int CB, int THREADS>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv(const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv,
+                                                      const T *__restrict__ spec, int ny, int qx, int nf,
+                                                      const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int EPT = CB * PY / THREADS;
+    constexpr int QY = PY / 2 + 1;
+    const int kx0 = blockIdx.x * CB;
+    const int64_t qplane = (int64_t)qx * QY;
+
+    C accx[EPT], accy[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+
+    for (int f = 0; f < nf; ++f) {
+        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+            const int c = e / PY, j = e % PY;
+            const int kx = kx0 + c;
+            buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
+        }
+        __syncthreads();
+        fft_batch<C, PY, CB, THREADS, false>(buf, tw);
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int e = threadIdx.x + q * THREADS;
+            const int c = e / PY, ky = e % PY;
+            const int kx = kx0 + c;
+            if (kx >= qx) continue;
+            const bool lower = ky <= PY / 2;
+            const int kq = lower ? ky : PY - ky;
+            const T sg = lower ? (T)1 : (T)-1;
+            const int64_t si = (int64_t)kx * QY + kq;
+            const C X = buf[spad<C>(e)];
+            if (f == 0) {
+                const T a = __ldg(&spec[0 * qplane + si]);
+                const T d = sg * __ldg(&spec[3 * qplane + si]);
+                accx[q] = cmake<C>(-a * X.y, a * X.x);
+                accy[q] = cmake<C>(-d * X.y, d * X.x);
+            } else if (f == 1) {
+                const T b = __ldg(&spec[1 * qplane + si]);
+                const T ff = sg * __ldg(&spec[5 * qplane + si]);
+                accx[q] = cmake<C>(accx[q].x + b * X.x, accx[q].y + b * X.y);
+                accy[q] = cmake<C>(accy[q].x + ff * X.x, accy[q].y + ff * X.y);
+            } else {
+                const T cc = sg * __ldg(&spec[2 * qplane + si]);
+                const T ee = __ldg(&spec[4 * qplane + si]);
+                accx[q] = cmake<C>(accx[q].x + cc * X.x, accx[q].y + cc * X.y);
+                accy[q] = cmake<C>(accy[q].x + ee * X.x, accy[q].y + ee * X.y);
+            }
+        }
+        __syncthreads();
+    }
+
+    for (int o = 0; o < 2; ++o) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
+        __syncthreads();
+        fft_batch<C, PY, CB, THREADS, true>(buf, tw);
+        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+            const int c = e / PY, j = e % PY;
+            const int kx = kx0 + c;
+            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = buf[spad<C>(e)];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int PX, int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict__ work_inv, T *__restrict__ fx,
+                                                     T *__restrict__ fy, int nx, int ny, const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int RB = 2 * NB;
+    constexpr int QX = PX / 2 + 1;
+    const int o = blockIdx.y;
+    const int j0 = blockIdx.x * RB;
+    const C *w = work_inv + (int64_t)o * QX * ny;
+    T *out = o == 0 ? fx : fy;
+
+    // Z[k] = A[k] + i B[k] over the full length, from the half spectra of rows 2s, 2s+1
+    for (int e = threadIdx.x; e < NB * QX; e += THREADS) {
+        const int s = e % NB, k = e / NB;
+        const int ja = j0 + 2 * s;
+        C a = ja < ny ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
+        C b = ja + 1 < ny ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
+        if (k == 0 || k == PX / 2) {
+            a.y = (T)0;
+            b.y = (T)0;
+        }
+        buf[spad<C>(s * PX + k)] = cmake<C>(a.x - b.y, a.y + b.x);
+        if (k > 0 && k < PX / 2) buf[spad<C>(s * PX + PX - k)] = cmake<C>(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+    }
+    __syncthreads();
+    fft_batch<C, PX, NB, THREADS, true>(buf, tw);
+    for (int e = threadIdx.x; e < NB * PX; e += THREADS) {
+        const int s = e / PX, i = e % PX;
+        if (i >= nx) continue;
+        const int ja = j0 + 2 * s;
+        const C z = buf[spad<C>(e)];
+        if (ja < ny) out[(int64_t)ja * nx + i] = z.x;
+        if (ja + 1 < ny) out[(int64_t)(ja + 1) * nx + i] = z.y;
+    }
+}
+
+// ------------------------------------------------------------ launch shapes --
+
+constexpr int row_nb(int px) { return px >= 4096 ? 2 : (4096 / px < 2 ? 2 : 4096 / px); }
+constexpr int col_cb(int py) { return py >= 2048 ? 1 : 2048 / py; }
+constexpr int col_threads(int py) { return col_cb(py) * py / 8; }
+constexpr int ROW_THREADS = 256;
+
+template <typename T, int PX>
+sg_status launch_rows_fwd(const field_src<T> &src, cplx_t<T> *work, int nf, const cplx_t<T> *tw, cudaStream_t st)
+{
+    constexpr int NB = row_nb(PX);
+    const size_t smem = (size_t)spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
+    auto kern = k_row_fwd<T, PX, NB, ROW_THREADS>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((src.ny + 2 * NB - 1) / (2 * NB), nf);
+    kern<<<grid, ROW_THREADS, smem, st>>>(src, work, tw);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+template <typename T, int PX>
+sg_status launch_rows_inv(const cplx_t<T> *work, T *fx, T *fy, int nx, int ny, const cplx_t<T> *tw, cudaStream_t st)
+{
+    constexpr int NB = row_nb(PX);
+    const size_t smem = (size_t)spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
+    auto kern = k_row_inv<T, PX, NB, ROW_THREADS>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((ny + 2 * NB - 1) / (2 * NB), 2);
+    kern<<<grid, ROW_THREADS, smem, st>>>(work, fx, fy, nx, ny, tw);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+template <typename T, int PY>
+sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf, const cplx_t<T> *tw,
+                      cudaStream_t st)
+{
+    constexpr int CB = col_cb(PY);
+    constexpr int THREADS = col_threads(PY);
+    const size_t smem = (size_t)spad_size<cplx_t<T>>(CB * PY) * sizeof(cplx_t<T>);
+    auto kern = k_col_conv<T, PY, CB, THREADS>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((qx + CB - 1) / CB);
+    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, ny, qx, nf, tw);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+#define SG_PAD_SWITCH(P, CALL)                 \
+    switch (P) {                               \
+    case 64: { constexpr int PP = 64; CALL; } break;     \
+    case 128: { constexpr int PP = 128; CALL; } break;   \
+    case 256: { constexpr int PP = 256; CALL; } break;   \
+    case 512: { constexpr int PP = 512; CALL; } break;   \
+    case 1024: { constexpr int PP = 1024; CALL; } break; \
+    case 2048: { constexpr int PP = 2048; CALL; } break; \
+    case 4096: { constexpr int PP = 4096; CALL; } break; \
+    default: return SG_EINVAL;                 \
+    }
+
+template <typename T>
+sg_status uniform_solve_t(sg_plan *plan, int p, const void *sigma, const void *dx, const void *dy, void *fx, void *fy,
+                          cudaStream_t st)
+{
+    using C = cplx_t<T>;
+    const sg_patch_plan &pp = plan->pp[p];
+    const sg_patch_dev &d = pp.d;
+    const int64_t off = d.cell_off;
+    field_src<T> src;
+    src.sigma = (const T *)sigma + off;
+    src.dx = dx ? (const T *)dx + off : nullptr;
+    src.dy = dy ? (const T *)dy + off : nullptr;
+    src.nx = d.nx;
+    src.ny = d.ny;
+    src.inv2h = (T)(0.5 / d.h);
+    src.mode = plan->geom.slope_mode;
+    src.cov = plan->cov_rects + d.cov_off;
+    src.ncov = d.ncov;
+    if (plan->npatches > 1) {
+        // AMR: the composite source fields (three planes, no covered cells to mask)
+        const T *S = (const T *)plan->sfield;
+        src.sigma = S + off;
+        src.dx = S + plan->ncells + off;
+        src.dy = S + 2 * plan->ncells + off;
+        src.mode = SG_SLOPES_CALLER;
+        src.ncov = 0;
+    }
+    const int nf = src.mode == SG_SLOPES_NONE ? 1 : 3;
+    const int qx = d.px / 2 + 1;
+    C *wf = (C *)plan->work_fwd;
+    C *wi = (C *)plan->work_inv;
+    const int64_t *twoff = sizeof(T) == 8 ? plan->tw64_off : plan->tw32_off;
+    const C *twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.px)]);
+    const C *twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.py)]);
+    T *ox = (T *)fx + off, *oy = (T *)fy + off;
+    sg_timing_begin(plan, SG_STAGE_ROW_FWD, st);
+    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_fwd<T, PP>(src, wf, nf, twx, st))));
+    sg_timing_end(plan, SG_STAGE_ROW_FWD, st);
+    sg_timing_begin(plan, SG_STAGE_COL_CONV, st);
+    SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, st))));
+    sg_timing_end(plan, SG_STAGE_COL_CONV, st);
+    sg_timing_begin(plan, SG_STAGE_ROW_INV, st);
+    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, oy, d.nx, d.ny, twx, st))));
+    sg_timing_end(plan, SG_STAGE_ROW_INV, st);
+    return SG_OK;
+}
+
+}  // namespace
+
+sg_status sg_uniform_solve(sg_plan *plan, int patch, const void *sigma, const void *dx, const void *dy, void *fx,
+                           void *fy, cudaStream_t st)
+{
+    if (plan->prec == SG_FP64) return uniform_solve_t<double>(plan, patch, sigma, dx, dy, fx, fy, st);
+    return uniform_solve_t<float>(plan, patch, sigma, dx, dy, fx, fy, st);
+}

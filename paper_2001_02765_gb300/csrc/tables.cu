@@ -1,0 +1,273 @@
+// Kernel tables and kernel spectra (FP64, one-off per plan).
+//
+// For a uniform patch of square cells the cell integrals of Section 2 depend
+// only on the integer offset (m, n) = (source - target) / h:
+//   K^{x,0}(m,n) = -dd ln(v + r)                      (scale-free)
+//   K^{x,x}(m,n) = -m h K^{x,0} + dd[v ln(u + r)]     (proportional to h)
+//   K^{x,y}(m,n) = -n h K^{x,0} - dd r
+//   K^{y,.}(m,n) = K^{x,.}(n,m) with x and y exchanged
+// over the cell u in [(m-1/2)h, (m+1/2)h], v in [(n-1/2)h, (n+1/2)h].
+//
+// The tables are evaluated in FP64 from algebraically identical forms that
+// avoid cancellation at large offsets: ln(v + r) - ln|u| = asinh(v/|u|), whose
+// u-independent part cancels in the double difference, and first differences
+//   asinh(a) - asinh(b) = asinh((a - b)(a + b) / (a sqrt(1 + b^2) + b sqrt(1 + a^2)))   (a >= b >= 0)
+//   r(u2, v) - r(u1, v) = (u2 - u1)(u2 + u1) / (r(u2, v) + r(u1, v))
+// so that only the outer difference cancels. Parities (K^{x,0} odd in m and
+// even in n, K^{x,x} even-even, K^{x,y} odd-odd) are imposed exactly.
+//
+// Spectra: the correlation F[t] = sum_s q[s] K[s - t] is a convolution with
+// Kr[e] = K[-e]; Kr is placed on the padded Px x Py grid (index e mod P, zero
+// outside |m| <= nx-1, |n| <= ny-1) and transformed with the shared-memory FFT.
+// By parity the transforms of the x0 and y0 tables are imaginary and the other
+// four real, so pairs are packed into one complex transform and the planes
+//   a = Im Kr^x0, b = Re Kr^xx, c = Re Kr^xy, d = Im Kr^y0, e = Re Kr^yy, f = Re Kr^yx
+// are stored for kx in [0, Px/2], ky in [0, Py/2] (the rest follows by parity),
+// scaled by G / (Px Py) and by h for the order-1 planes.
+#include "common.cuh"
+#include "fft.cuh"
+
+#include <math.h>
+
+// asinh(a) - asinh(b) for a >= b >= 0 given d = a - b computed without rounding loss.
+__device__ __forceinline__ double asinh_diff(double a, double b, double d)
+{
+    return asinh(d * (a + b) / (a * sqrt(1.0 + b * b) + b * sqrt(1.0 + a * a)));
+}
+
+// asinh(t2 / s) - asinh(t1 / s), t2 - t1 = 1, s > 0.
+__device__ __forceinline__ double asinh_span(double t1, double t2, double s)
+{
+    if (t1 >= 0.0) return asinh_diff(t2 / s, t1 / s, 1.0 / s);
+    if (t2 <= 0.0) return asinh_diff(-t1 / s, -t2 / s, 1.0 / s);
+    return asinh(t2 / s) + asinh(-t1 / s);
+}
+
+// unit-cell tables for m, n >= 0 (parity applied by the caller)
+struct k3 {
+    double x0, xx, xy;
+};
+
+__device__ k3 unit_kernels_pos(int m, int n)
+{
+    k3 k;
+    const double u1 = m - 0.5, u2 = m + 0.5, v1 = n - 0.5, v2 = n + 0.5;
+    // K^{x,0} = -dd asinh(v/|u|) = Dv(u1) - Dv(u2), Dv(u) = asinh(v2/u) - asinh(v1/u)
+    if (m == 0) {
+        k.x0 = 0.0;
+    } else {
+        k.x0 = asinh_span(v1, v2, u1) - asinh_span(v1, v2, u2);
+    }
+    // dd[v asinh(u/|v|)] = v2 Du(v2) - v1 Du(v1), Du(v) = asinh(u2/|v|) - asinh(u1/|v|)
+    const double psi = v2 * asinh_span(u1, u2, fabs(v2)) - v1 * asinh_span(u1, u2, fabs(v1));
+    k.xx = -(double)m * k.x0 + psi;
+    // dd r = Dr(v2) - Dr(v1), Dr(v) = r(u2,v) - r(u1,v) = (u2 + u1) / (r(u2,v) + r(u1,v))
+    if (m == 0 || n == 0) {
+        k.xy = 0.0;
+    } else {
+        const double r22 = sqrt(u2 * u2 + v2 * v2), r12 = sqrt(u1 * u1 + v2 * v2);
+        const double r21 = sqrt(u2 * u2 + v1 * v1), r11 = sqrt(u1 * u1 + v1 * v1);
+        const double ddr = (u2 + u1) / (r22 + r12) - (u2 + u1) / (r21 + r11);
+        k.xy = -(double)n * k.x0 - ddr;
+    }
+    return k;
+}
+
+// All six unit-h kernels at offset (m, n).
+__device__ void unit_kernels(int m, int n, double *out6)
+{
+    const int am = m < 0 ? -m : m, an = n < 0 ? -n : n;
+    const double sm = m < 0 ? -1.0 : 1.0, sn = n < 0 ? -1.0 : 1.0;
+    k3 a = unit_kernels_pos(am, an);   // x-family at (|m|, |n|)
+    k3 b = unit_kernels_pos(an, am);   // x-family at (|n|, |m|) -> y-family at (m, n)
+    out6[0] = sm * a.x0;               // K^{x,0}: odd in m, even in n
+    out6[1] = a.xx;                    // K^{x,x}: even-even
+    out6[2] = sm * sn * a.xy;          // K^{x,y}: odd-odd
+    out6[3] = sn * b.x0;               // K^{y,0}(m,n) = K^{x,0}(n,m)
+    out6[4] = sm * sn * b.xy;          // K^{y,x}(m,n) = K^{x,y}(n,m)
+    out6[5] = b.xx;                    // K^{y,y}(m,n) = K^{x,x}(n,m)
+}
+
+// Unwrapped table of one kernel, physical units, [(2ny-1)][(2nx-1)].
+__global__ void k_table_unwrapped(double *out, int nx, int ny, double h, int which)
+{
+    const int w = 2 * nx - 1, hgt = 2 * ny - 1;
+    const int64_t total = (int64_t)w * hgt;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int col = (int)(e % w), row = (int)(e / w);
+        double k6[6];
+        unit_kernels(col - (nx - 1), row - (ny - 1), k6);
+        const double scale = (which == 0 || which == 3) ? 1.0 : h;
+        out[e] = scale * k6[which];
+    }
+}
+
+// Wrapped correlation kernels packed in pairs: z0 = Kr^x0 + i Kr^y0,
+// z1 = Kr^xx + i Kr^xy, z2 = Kr^yy + i Kr^yx, each [py][px].
+__global__ void k_tables_wrapped(double2 *z, int nx, int ny, int px, int py)
+{
+    const int64_t plane = (int64_t)px * py;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % px), b = (int)(e / px);
+        const int ex = a < px / 2 ? a : a - px;
+        const int ey = b < py / 2 ? b : b - py;
+        const int m = -ex, n = -ey;  // Kr[e] = K[-e]
+        double k6[6] = {0, 0, 0, 0, 0, 0};
+        if (m <= nx - 1 && m >= -(nx - 1) && n <= ny - 1 && n >= -(ny - 1)) unit_kernels(m, n, k6);
+        z[e] = make_double2(k6[0], k6[3]);
+        z[plane + e] = make_double2(k6[1], k6[2]);
+        z[2 * plane + e] = make_double2(k6[5], k6[4]);
+    }
+}
+
+// In-place complex FFT along rows (stride 1) or columns (stride = row length)
+// of `count` sequences of length L, one sequence per CTA, FP64.
+template <int L>
+__global__ void __launch_bounds__(L / 8 >= 64 ? L / 8 : 64) k_fft_lines(double2 *data, int64_t seq_stride, int64_t elem_stride,
+                                                                          const double2 *__restrict__ tw)
+{
+    constexpr int THREADS = L / 8 >= 64 ? L / 8 : 64;
+    extern __shared__ double2 buf[];
+    double2 *base = data + blockIdx.x * seq_stride;
+    for (int k = threadIdx.x; k < L; k += THREADS) buf[spad<double2>(k)] = base[k * elem_stride];
+    __syncthreads();
+    fft_batch<double2, L, 1, THREADS, false>(buf, tw);
+    for (int k = threadIdx.x; k < L; k += THREADS) base[k * elem_stride] = buf[spad<double2>(k)];
+}
+
+template <typename T>
+__global__ void k_extract_spectra(const double2 *z, T *planes, int px, int py, double scale0, double scale1)
+{
+    const int qx = px / 2 + 1, qy = py / 2 + 1;
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(e / qy), ky = (int)(e % qy);  // planes are [kx][ky]
+        const int64_t src = (int64_t)ky * px + kx;          // z is [ky][kx]
+        const double2 z0 = z[src], z1 = z[plane + src], z2 = z[2 * plane + src];
+        // z0 = Kx0^ + i Ky0^ = i a + i (i d) = -d + i a
+        planes[0 * qplane + e] = (T)(scale0 * z0.y);   // a
+        planes[3 * qplane + e] = (T)(-scale0 * z0.x);  // d
+        // z1 = Kxx^ + i Kxy^ = b + i c ; z2 = Kyy^ + i Kyx^ = e + i f
+        planes[1 * qplane + e] = (T)(scale1 * z1.x);   // b
+        planes[2 * qplane + e] = (T)(scale1 * z1.y);   // c
+        planes[4 * qplane + e] = (T)(scale1 * z2.x);   // e
+        planes[5 * qplane + e] = (T)(scale1 * z2.y);   // f
+    }
+}
+
+__global__ void k_twiddles(double2 *tw64, float2 *tw32, int L)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)k / (double)L, &s, &c);
+        tw64[k] = make_double2(c, s);
+        if (tw32) tw32[k] = make_float2((float)c, (float)s);
+    }
+}
+
+static sg_status launch_fft_lines(double2 *data, int L, int count, int64_t seq_stride, int64_t elem_stride,
+                                  const double2 *tw)
+{
+    switch (L) {
+#define SG_CASE(LL)                                                                                           \
+    case LL:                                                                                                  \
+        SG_CUDA_TRY(cudaFuncSetAttribute(k_fft_lines<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                         (int)(spad_size<double2>(LL) * sizeof(double2))));                   \
+        k_fft_lines<LL><<<count, (LL / 8 >= 64 ? LL / 8 : 64), spad_size<double2>(LL) * sizeof(double2)>>>(   \
+            data, seq_stride, elem_stride, tw);                                                               \
+        break;
+        SG_CASE(64) SG_CASE(128) SG_CASE(256) SG_CASE(512) SG_CASE(1024) SG_CASE(2048) SG_CASE(4096)
+#undef SG_CASE
+    default:
+        return SG_EINVAL;
+    }
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+// Twiddle tables: FP64 for every power of two in [SG_MIN_PAD, max_pad], then
+// FP32 copies of each (read by FP32 plans), back to back.
+sg_status sg_twiddles_build(sg_plan *plan)
+{
+    int64_t off = 0;
+    for (int L = SG_MIN_PAD; L <= plan->max_pad; L <<= 1) {
+        plan->tw64_off[sg_ilog2(L)] = off;
+        off += (int64_t)L * sizeof(double2);
+    }
+    for (int L = SG_MIN_PAD; L <= plan->max_pad; L <<= 1) {
+        plan->tw32_off[sg_ilog2(L)] = off;
+        off += (int64_t)L * sizeof(float2);
+    }
+    SG_CUDA_TRY(cudaMalloc(&plan->twiddles, (size_t)off));
+    plan->device_bytes += off;
+    for (int L = SG_MIN_PAD; L <= plan->max_pad; L <<= 1) {
+        double2 *t64 = (double2 *)((char *)plan->twiddles + plan->tw64_off[sg_ilog2(L)]);
+        float2 *t32 = (float2 *)((char *)plan->twiddles + plan->tw32_off[sg_ilog2(L)]);
+        k_twiddles<<<(L + 255) / 256, 256>>>(t64, t32, L);
+        SG_CUDA_TRY(cudaGetLastError());
+    }
+    return SG_OK;
+}
+
+sg_status sg_tables_build(sg_plan *plan)
+{
+    // one temporary of the largest padded patch, three complex planes
+    int64_t maxplane = 0;
+    for (int p = 0; p < plan->npatches; ++p) {
+        const sg_patch_dev &d = plan->pp[p].d;
+        int64_t pl = (int64_t)d.px * d.py;
+        if (pl > maxplane) maxplane = pl;
+    }
+    double2 *z = nullptr;
+    SG_CUDA_TRY(cudaMalloc(&z, (size_t)(3 * maxplane * sizeof(double2))));
+    sg_status st = SG_OK;
+    for (int p = 0; p < plan->npatches && st == SG_OK; ++p) {
+        sg_patch_plan &pp = plan->pp[p];
+        const int px = pp.d.px, py = pp.d.py;
+        const int64_t plane = (int64_t)px * py;
+        k_tables_wrapped<<<1024, 256>>>(z, pp.d.nx, pp.d.ny, px, py);
+        if (cudaGetLastError() != cudaSuccess) { st = SG_ECUDA; break; }
+        const double2 *twx = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(px)]);
+        const double2 *twy = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(py)]);
+        for (int q = 0; q < 3 && st == SG_OK; ++q) {
+            double2 *zq = z + q * plane;
+            st = launch_fft_lines(zq, px, py, px, 1, twx);       // rows
+            if (st == SG_OK) st = launch_fft_lines(zq, py, px, 1, px, twy);   // columns
+        }
+        if (st != SG_OK) break;
+        const double scale0 = plan->geom.G / ((double)px * (double)py);
+        const double scale1 = scale0 * pp.d.h;
+        if (plan->prec == SG_FP64)
+            k_extract_spectra<double><<<1024, 256>>>(z, (double *)pp.spectra, px, py, scale0, scale1);
+        else
+            k_extract_spectra<float><<<1024, 256>>>(z, (float *)pp.spectra, px, py, scale0, scale1);
+        if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(z);
+    if (st != SG_OK) return st;
+    if (e != cudaSuccess) {
+        sg_set_last_cuda_error(e, "sg_tables_build");
+        return SG_ECUDA;
+    }
+    return SG_OK;
+}
+
+sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host_out, size_t n)
+{
+    if (!plan || !host_out || patch < 0 || patch >= plan->npatches || which < 0 || which > 5) return SG_EINVAL;
+    const sg_patch_dev &d = plan->pp[patch].d;
+    const size_t need = (size_t)(2 * d.nx - 1) * (size_t)(2 * d.ny - 1);
+    if (n < need) return SG_EINVAL;
+    double *tmp = nullptr;
+    SG_CUDA_TRY(cudaMalloc(&tmp, need * sizeof(double)));
+    k_table_unwrapped<<<1024, 256>>>(tmp, d.nx, d.ny, d.h, which);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, tmp, need * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        sg_set_last_cuda_error(e, "sg_kernel_tables");
+        return SG_ECUDA;
+    }
+    return SG_OK;
+}

@@ -1,0 +1,290 @@
+"""Python binding of the C ABI in include/sg.h (argument marshalling only).
+
+Every step of a solve runs in the CUDA library libsg.so; this module converts
+arguments and checks status codes. Loading fails loudly (SgLibraryMissing) when
+the library has not been built: there is no fallback implementation.
+
+Low-level names mirror the C entry points (sg_plan_create, sg_force, ...);
+``Plan`` is a small convenience wrapper that takes torch tensors (PyTorch is
+used for device memory and streams only).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsg.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_EBUDGET, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_ECANCELLED, SG_ENOTFOUND = range(9)
+SG_FP64, SG_FP32 = 0, 1
+SG_SLOPES_NONE, SG_SLOPES_CENTRAL, SG_SLOPES_CALLER = 0, 1, 2
+KERNEL_NAMES = ("x0", "xx", "xy", "y0", "yx", "yy")
+
+
+class SgLibraryMissing(ImportError):
+    pass
+
+
+class SgError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = "%s failed: %s (%d)" % (where, strerror(status), status)
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
+
+
+class sg_patch(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("h", ctypes.c_double)]
+
+
+class sg_geom(ctypes.Structure):
+    _fields_ = [("npatches", ctypes.c_int), ("patches", ctypes.POINTER(sg_patch)),
+                ("G", ctypes.c_double), ("slope_mode", ctypes.c_int)]
+
+
+class sg_plan_info(ctypes.Structure):
+    _fields_ = [("npatches", ctypes.c_int), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
+                ("cross_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("scratch_bytes", ctypes.c_int64), ("max_pad", ctypes.c_int)]
+
+
+# name -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_SIGNATURES = {
+    "sg_geom_validate": (ctypes.c_int, [ctypes.POINTER(sg_geom)]),
+    "sg_plan_create": (ctypes.c_int, [ctypes.POINTER(sg_geom), ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)]),
+    "sg_plan_destroy": (ctypes.c_int, [_VP]),
+    "sg_plan_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(sg_plan_info)]),
+    "sg_plan_bytes": (ctypes.c_int, [ctypes.POINTER(sg_geom), ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "sg_kernel_tables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
+    "sg_force": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_force_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "sg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sg_last_error": (ctypes.c_char_p, []),
+    "sg_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+def exported_names():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIGNATURES)
+
+
+def load(path=None):
+    """Load libsg.so (once). Raises SgLibraryMissing if it is not built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise SgLibraryMissing("CUDA library %s is not built; run __graft_entry__.build() "
+                               "(python -m paper_2001_02765_gb300.build)" % p)
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def strerror(status):
+    try:
+        return load().sg_strerror(int(status)).decode()
+    except SgLibraryMissing:
+        return "status %d" % status
+
+
+def last_error():
+    return load().sg_last_error().decode()
+
+
+def _check(status, where):
+    if status != SG_OK:
+        raise SgError(status, where, last_error())
+
+
+def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER):
+    """patches: iterable of (level, nx, ny, x0, y0, h). Returns (sg_geom, keepalive array)."""
+    patches = list(patches)
+    arr = (sg_patch * len(patches))(*[sg_patch(int(p[0]), int(p[1]), int(p[2]), float(p[3]), float(p[4]), float(p[5]))
+                                      for p in patches])
+    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode))
+    return g, arr
+
+
+def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER):
+    g, _keep = make_geom(patches, G, slope_mode)
+    return load().sg_geom_validate(ctypes.byref(g))
+
+
+def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER):
+    g, _keep = make_geom(patches, G, slope_mode)
+    out = ctypes.c_int64(0)
+    _check(load().sg_plan_bytes(ctypes.byref(g), int(precision), ctypes.byref(out)), "sg_plan_bytes")
+    return int(out.value)
+
+
+def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0):
+    g, _keep = make_geom(patches, G, slope_mode)
+    h = _VP()
+    _check(load().sg_plan_create(ctypes.byref(g), int(precision), int(hbm_budget), ctypes.byref(h)), "sg_plan_create")
+    return h.value
+
+
+def sg_plan_destroy(handle):
+    if handle:
+        _check(load().sg_plan_destroy(handle), "sg_plan_destroy")
+
+
+def sg_plan_get_info(handle):
+    info = sg_plan_info()
+    _check(load().sg_plan_get_info(handle, ctypes.byref(info)), "sg_plan_get_info")
+    return {k: getattr(info, k) for k, _ in sg_plan_info._fields_}
+
+
+def sg_kernel_tables(handle, patch, which, nx, ny):
+    n = (2 * nx - 1) * (2 * ny - 1)
+    out = np.empty(n, dtype=np.float64)
+    _check(load().sg_kernel_tables(handle, int(patch), int(which),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n), "sg_kernel_tables")
+    return out.reshape(2 * ny - 1, 2 * nx - 1)
+
+
+def sg_force(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
+    """Raw device pointers (ints); enqueues one solve on the stream."""
+    _check(load().sg_force(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr, stream_ptr or None),
+           "sg_force")
+
+
+def sg_force_host(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
+    """Raw host pointers (ints); synchronous."""
+    _check(load().sg_force_host(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr,
+                                stream_ptr or None), "sg_force_host")
+
+
+STAGE_NAMES = ("row_fwd", "col_conv", "row_inv", "corner_weights", "cross_direct", "composite")
+
+
+def sg_plan_set_timing(handle, enable):
+    _check(load().sg_plan_set_timing(handle, int(bool(enable))), "sg_plan_set_timing")
+
+
+def sg_plan_get_timing(handle):
+    ms = (ctypes.c_double * len(STAGE_NAMES))()
+    _check(load().sg_plan_get_timing(handle, ms, len(STAGE_NAMES)), "sg_plan_get_timing")
+    return dict(zip(STAGE_NAMES, list(ms)))
+
+
+def sg_version():
+    return int(load().sg_version())
+
+
+# ------------------------------------------------------------ convenience --
+
+class Plan:
+    """A plan for one geometry; fields are torch tensors on the current CUDA device.
+
+    patches: list of (level, nx, ny, x0, y0, h); fields are the per-patch
+    row-major arrays concatenated (length ``ncells``).
+    """
+
+    def __init__(self, patches, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0):
+        self.patches = [tuple(p) for p in patches]
+        self.precision = SG_FP32 if precision in ("fp32", SG_FP32) else SG_FP64
+        self.slope_mode = slope_mode
+        self.G = G
+        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget)
+        self.info = sg_plan_get_info(self.handle)
+
+    @property
+    def ncells(self):
+        return self.info["ncells"]
+
+    @property
+    def dtype_name(self):
+        return "float32" if self.precision == SG_FP32 else "float64"
+
+    def close(self):
+        if self.handle:
+            sg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def kernel_table(self, patch, which):
+        p = self.patches[patch]
+        w = KERNEL_NAMES.index(which) if isinstance(which, str) else int(which)
+        return sg_kernel_tables(self.handle, patch, w, p[1], p[2])
+
+    def _torch_dtype(self):
+        import torch
+        return torch.float32 if self.precision == SG_FP32 else torch.float64
+
+    def empty_fields(self, n=2):
+        import torch
+        return [torch.empty(self.ncells, dtype=self._torch_dtype(), device="cuda") for _ in range(n)]
+
+    def force(self, sigma, dx=None, dy=None, fx=None, fy=None, stream=None):
+        """Enqueue a solve on `stream` (default: torch's current stream); returns (fx, fy)."""
+        import torch
+        dt = self._torch_dtype()
+        for t in (sigma, dx, dy, fx, fy):
+            if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() != self.ncells):
+                raise ValueError("fields must be contiguous %s CUDA tensors of %d elements" % (dt, self.ncells))
+        if fx is None:
+            fx = torch.empty_like(sigma)
+        if fy is None:
+            fy = torch.empty_like(sigma)
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        sg_force(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
+                 dy.data_ptr() if dy is not None else 0, fx.data_ptr(), fy.data_ptr(), st)
+        return fx, fy
+
+    def force_host(self, sigma, dx=None, dy=None, fx=None, fy=None, stream=None):
+        """Solve from host arrays (numpy, or pinned torch CPU tensors); returns host (fx, fy)."""
+        npdt = np.float32 if self.precision == SG_FP32 else np.float64
+
+        def host_ptr(a):
+            if a is None:
+                return 0, None
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=npdt).ravel()
+                return a.ctypes.data, a
+            return a.data_ptr(), a  # torch CPU tensor
+
+        ps, ks = host_ptr(sigma)
+        pdx, kdx = host_ptr(dx)
+        pdy, kdy = host_ptr(dy)
+        if fx is None:
+            fx = np.empty(self.ncells, dtype=npdt)
+        if fy is None:
+            fy = np.empty(self.ncells, dtype=npdt)
+        pfx, _ = host_ptr(fx) if not isinstance(fx, np.ndarray) else (fx.ctypes.data, fx)
+        pfy, _ = host_ptr(fy) if not isinstance(fy, np.ndarray) else (fy.ctypes.data, fy)
+        st = 0
+        if stream is not None:
+            st = stream.cuda_stream
+        sg_force_host(self.handle, ps, pdx, pdy, pfx, pfy, st)
+        return fx, fy
+
+    def split(self, flat):
+        """Split a flat field array into per-patch [ny, nx] views."""
+        out, off = [], 0
+        for p in self.patches:
+            n = p[1] * p[2]
+            out.append(flat[off:off + n].reshape(p[2], p[1]))
+            off += n
+        return out

@@ -173,6 +173,34 @@ def batch_sizes(count=64, lo=64, hi=512, seed=4):
     return ns, a, amp
 
 
+def bumps_on_patches(patches, seed, nbumps=6):
+    """Seeded smooth density: a sum of Gaussian bumps (random centres in
+    [-0.6, 0.6]^2, widths in [0.08, 0.3], amplitudes in [0.2, 1]) at the cell
+    centres of every patch, with its analytic gradient. Returns lists
+    (sigma, dx, dy) of per-patch [ny, nx] arrays."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cx = rng.uniform(-0.6, 0.6, nbumps)
+    cy = rng.uniform(-0.6, 0.6, nbumps)
+    w = rng.uniform(0.08, 0.3, nbumps)
+    a = rng.uniform(0.2, 1.0, nbumps)
+    sig, gx, gy = [], [], []
+    for p in patches:
+        nx, ny, x0, y0, h = p[-5:]
+        X, Y = cell_centres(nx, ny, x0, y0, h)
+        s = np.zeros_like(X)
+        sx = np.zeros_like(X)
+        sy = np.zeros_like(X)
+        for k in range(nbumps):
+            e = a[k] * np.exp(-((X - cx[k]) ** 2 + (Y - cy[k]) ** 2) / (2 * w[k] ** 2))
+            s += e
+            sx += -e * (X - cx[k]) / w[k] ** 2
+            sy += -e * (Y - cy[k]) / w[k] ** 2
+        sig.append(s)
+        gx.append(sx)
+        gy.append(sy)
+    return sig, gx, gy
+
+
 def random_fields(ny, nx, seed, scale=1.0):
     """Seeded uniform random sigma, dx, dy in [-scale, scale] (parity inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed))

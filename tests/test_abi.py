@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports what include/sg.h declares; host-only calls (no GPU)."""
+import pytest
+
+from paper_2001_02765_gb300 import sg
+from paper_2001_02765_gb300 import workloads as W
+from tests._lib import ensure_built, header_functions
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ensure_built()
+
+
+def test_header_declares_binding_names():
+    assert header_functions() == sg.exported_names()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_strerror(lib):
+    assert sg.sg_version() >= 100
+    assert sg.strerror(sg.SG_EINVAL) == "invalid argument"
+    assert sg.strerror(99) == "unknown status"
+
+
+def test_validate_uniform_and_nested(lib):
+    assert sg.sg_geom_validate([(0,) + W.unit_grid(64)]) == sg.SG_OK
+    pat = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(256, 3))]
+    assert sg.sg_geom_validate(pat) == sg.SG_OK
+    t10 = [(0, 4, 4, 0.0, 0.0, 0.25), (1, 2, 2, 0.25, 0.25, 0.125), (1, 2, 2, 0.5, 0.5, 0.125),
+           (2, 2, 2, 0.25, 0.375, 0.0625), (2, 2, 2, 0.375, 0.25, 0.0625)]
+    assert sg.sg_geom_validate(t10) == sg.SG_OK
+
+
+@pytest.mark.parametrize("bad, why", [
+    ([], "no patches"),
+    ([(0, 0, 4, 0.0, 0.0, 0.1)], "empty patch"),
+    ([(0, 4096, 4, 0.0, 0.0, 0.1)], "too large"),
+    ([(0, 4, 4, 0.0, 0.0, -0.1)], "negative h"),
+    ([(1, 4, 4, 0.0, 0.0, 0.1)], "first patch not level 0"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (1, 4, 4, 0.2, 0.2, 0.06)], "h not halved"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (1, 3, 4, 0.2, 0.2, 0.05)], "odd refined size"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (1, 4, 4, 0.25, 0.2, 0.05)], "off the parent lattice"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (1, 20, 4, 0.2, 0.2, 0.05)], "outside the parent"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (1, 4, 4, 0.2, 0.2, 0.05), (1, 4, 4, 0.3, 0.2, 0.05)], "same-level overlap"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (0, 8, 8, 0.4, 0.0, 0.1)], "level-0 overlap"),
+    ([(0, 8, 8, 0.0, 0.0, 0.1), (0, 8, 8, 0.85, 0.0, 0.1)], "level-0 off lattice"),
+])
+def test_validate_rejects(lib, bad, why):
+    assert sg.sg_geom_validate(bad) == sg.SG_EINVAL, why
+
+
+def test_validate_rejects_central_slopes_on_amr(lib):
+    pat = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))]
+    assert sg.sg_geom_validate(pat, slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_EINVAL
+    assert sg.sg_geom_validate(pat[:1], slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_OK
+
+
+def test_plan_bytes_estimate(lib):
+    one = sg.sg_plan_bytes([(0,) + W.unit_grid(1024)], sg.SG_FP32)
+    two = sg.sg_plan_bytes([(0,) + W.unit_grid(1024)], sg.SG_FP64)
+    assert 40e6 < one < 200e6 and 1.8 < two / one < 2.2
+    amr = sg.sg_plan_bytes([(lev,) + p for lev, p in enumerate(W.centred_nested_patches(256, 3))], sg.SG_FP32)
+    assert amr > 0
+    with pytest.raises(sg.SgError):
+        sg.sg_plan_bytes([(0, 0, 0, 0.0, 0.0, 1.0)])
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(sg.SgLibraryMissing):
+        sg.load(str(tmp_path / "libsg.so"))

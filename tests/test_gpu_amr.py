@@ -1,0 +1,154 @@
+"""Parity of the CUDA AMR path (per-patch FFT + cross-patch corner-form direct sum)
+with the oracle's plain leaf-pair sum. Tolerances as for the uniform path:
+relative L2 over all leaf targets, 1e-12 (FP64 plans) and 1e-5 (FP32 plans) on
+smooth densities (disks, Gaussian bumps).
+
+Rough densities (independent uniform noise in every cell) are a stress case for
+FP32: the cross-patch sum adds O(1) corner weights times kernel terms whose
+FP32 evaluation error is ~2^-22 each, so the error grows like
+2^-22 sqrt(corners) |w| / |F|; for the 16^2-per-level hierarchies below this
+predicts ~1e-5 and the bound used is 5e-5."""
+import numpy as np
+import pytest
+
+from oracle import amr as oamr
+from oracle.norms import rel_l2
+from paper_2001_02765_gb300 import workloads as W
+from tests._lib import concat_dev, ensure_built, gather_leaves
+
+pytestmark = pytest.mark.gpu
+
+TABLE10 = [(0, 4, 4, 0.0, 0.0, 0.25), (1, 2, 2, 0.25, 0.25, 0.125), (1, 2, 2, 0.5, 0.5, 0.125),
+           (2, 2, 2, 0.25, 0.375, 0.0625), (2, 2, 2, 0.375, 0.25, 0.0625)]
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+    assert torch.cuda.is_available()
+    ensure_built()
+    from paper_2001_02765_gb300 import sg as mod
+    return mod
+
+
+def _fields(patches, seed, positive=False):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = 0.0 if positive else -1.0
+    sig = [rng.uniform(lo, 1, (p[2], p[1])) for p in patches]
+    sx = [rng.uniform(-1, 1, (p[2], p[1])) for p in patches]
+    sy = [rng.uniform(-1, 1, (p[2], p[1])) for p in patches]
+    return sig, sx, sy
+
+
+def _run(sg, patches, prec, mode, sig, sx, sy, G=1.0):
+    import torch
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan = sg.Plan(patches, precision=prec, slope_mode=mode, G=G)
+    a = concat_dev(sig, dt)
+    b = concat_dev(sx, dt) if mode == sg.SG_SLOPES_CALLER else None
+    c = concat_dev(sy, dt) if mode == sg.SG_SLOPES_CALLER else None
+    fx, fy = plan.force(a, b, c)
+    torch.cuda.synchronize()
+    return plan, fx.cpu().numpy(), fy.cpu().numpy()
+
+
+def _check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None):
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan, fx, fy = _run(sg, patches, prec, mode, sig, sx, sy, G)
+    r = lambda a: [np.asarray(x, dt).astype(np.float64) for x in a]
+    use_slopes = mode == sg.SG_SLOPES_CALLER
+    leaves, rx, ry = oamr.amr_direct_force(oamr.make_patches(patches), r(sig), r(sx) if use_slopes else None,
+                                           r(sy) if use_slopes else None, G=G, target_index=target_index)
+    if target_index is not None:
+        leaves = {k: v[target_index] for k, v in leaves.items()}
+    gx = gather_leaves(plan, fx, leaves)
+    gy = gather_leaves(plan, fy, leaves)
+    plan.close()
+    err = rel_l2(gx, gy, rx, ry)
+    assert err < tol, err
+    return err
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("mode", [0, 2])
+def test_nested_three_levels(sg, prec, tol, mode):
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))]
+    sig, sx, sy = W.bumps_on_patches(patches, 3)
+    _check(sg, patches, prec, mode, sig, sx, sy, tol, G=2.5)
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 5e-5)])
+def test_nested_three_levels_rough(sg, prec, tol):
+    """Independent noise in every cell (see the module docstring for the FP32 bound)."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))]
+    sig, sx, sy = _fields(patches, 3, positive=True)
+    _check(sg, patches, prec, 2, sig, sx, sy, tol, G=2.5)
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_table10_hierarchy(sg, prec, tol):
+    """Fig. 1 / Table 10: two patches per refined level, 28 leaves."""
+    sig, sx, sy = _fields(TABLE10, 8, positive=True)
+    _check(sg, TABLE10, prec, 2, sig, sx, sy, tol)
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_ragged_off_centre_patches(sg, prec, tol):
+    """Non-square, off-centre patches whose sizes are not tile multiples."""
+    patches = [(0, 37, 29, -1.0, -0.8, 0.05), (1, 22, 14, -0.6, -0.3, 0.025), (1, 6, 8, 0.2, 0.1, 0.025),
+               (2, 10, 12, -0.5, -0.25, 0.0125)]
+    assert sg.sg_geom_validate(patches) == sg.SG_OK
+    sig, sx, sy = W.bumps_on_patches(patches, 17)
+    _check(sg, patches, prec, 2, sig, sx, sy, tol)
+
+
+def test_refinement_invariance_on_gpu(sg):
+    """A fine patch carrying the coarse linear reconstruction leaves the force at
+    the coarse leaves equal to the uniform coarse force (FP64)."""
+    import torch
+    n = 16
+    nx, ny, x0, y0, h = W.unit_grid(n)
+    s, sx, sy = W.random_fields(n, n, seed=21)
+    fine = np.zeros((16, 16)), np.zeros((16, 16)), np.zeros((16, 16))
+    for J in range(16):
+        for I in range(16):
+            pj, pi = 4 + J // 2, 4 + I // 2
+            fine[0][J, I] = s[pj, pi] + sx[pj, pi] * (I % 2 - 0.5) * h / 2 + sy[pj, pi] * (J % 2 - 0.5) * h / 2
+            fine[1][J, I] = sx[pj, pi]
+            fine[2][J, I] = sy[pj, pi]
+    patches = [(0, nx, ny, x0, y0, h), (1, 16, 16, -0.5, -0.5, h / 2)]
+    plan, fx, fy = _run(sg, patches, "fp64", 2, [s, fine[0]], [sx, fine[1]], [sy, fine[2]])
+    uni, ux, uy = _run(sg, patches[:1], "fp64", 2, [s], [sx], [sy])
+    leaf = np.ones((n, n), bool)
+    leaf[4:12, 4:12] = False
+    ax = fx[:n * n].reshape(n, n)[leaf]
+    ay = fy[:n * n].reshape(n, n)[leaf]
+    assert rel_l2(ax, ay, ux.reshape(n, n)[leaf], uy.reshape(n, n)[leaf]) < 1e-12
+    plan.close()
+    uni.close()
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_exponential_hierarchy_full_size_sampled(sg, prec, tol):
+    """Three 256^2 levels on [-1,1]^2, [-.5,.5]^2, [-.25,.25]^2, exp(-R/0.1),
+    analytic slopes: 192 seeded leaf targets vs the plain leaf-pair sum."""
+    case = W.exponential_hierarchy(256, 3, 0.1)
+    patches = [(lev,) + p for lev, p in enumerate(case["patches"])]
+    nleaf = sum(int(m.sum()) for m in case["leaf"])
+    rng = np.random.Generator(np.random.PCG64(31))
+    idx = np.sort(rng.choice(nleaf, 192, replace=False))
+    _check(sg, patches, prec, 2, case["sigma"], case["dx"], case["dy"], tol, target_index=idx)
+
+
+def test_covered_cells_are_ignored(sg):
+    """Garbage in covered cells must not change any leaf result."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))]
+    sig, sx, sy = _fields(patches, 5, positive=True)
+    _, a, b = _run(sg, patches, "fp64", 2, sig, sx, sy)
+    sig2 = [x.copy() for x in sig]
+    sig2[0][4:12, 4:12] = 1e6
+    plan, c, d = _run(sg, patches, "fp64", 2, sig2, sx, sy)
+    leaves = oamr.leaf_cells(oamr.make_patches(patches))
+    assert np.allclose(gather_leaves(plan, a, leaves), gather_leaves(plan, c, leaves), rtol=1e-13, atol=1e-13)
+    plan.close()
