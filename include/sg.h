@@ -186,6 +186,35 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
 sg_status sg_plan_set_timing(sg_plan *plan, int enable);
 sg_status sg_plan_get_timing(sg_plan *plan, double *ms, int n);
 
+/*
+ * Allocation-free direct force sum on one uniform grid, FP32. The paper has no
+ * counterpart for this entry point: it computes the same sum as sg_force on a
+ * single nx x ny patch with caller slopes (or order 0 when deltax and deltay
+ * are both NULL), by direct summation over the grid corners, for callers that
+ * cannot let a library allocate device memory (an application that owns the
+ * whole device budget and passes libraries only its own buffers, or a
+ * time-step loop that must not pay cudaMalloc's latency and implicit
+ * synchronisation). No plan is needed and nothing is allocated: the one
+ * intermediate (the corner weights, 16 bytes per corner) lives in a fixed
+ * array compiled into the library, sized for at most 512 x 512 cells
+ * (513^2 corners, 4.2 MB), which every GPU that loads the library holds until
+ * the process exits.
+ *   nx, ny      cells, 1..512 each (SG_EINVAL beyond, with sg_last_error set)
+ *   h, G        cell width (> 0) and gravitational constant
+ *   sigma, deltax, deltay, fx, fy
+ *               caller-owned device arrays of nx*ny floats, row-major [y][x];
+ *               deltax and deltay both NULL or both non-NULL
+ *   stream      cudaStream_t (NULL = legacy default stream); the call enqueues
+ *               two kernels and returns
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call shares the array and overwrites what it uses, so calls
+ * whose work overlaps on the GPU race and give wrong results; serialise them
+ * (one stream, or events between streams). Cost O((nx ny)^2).
+ */
+sg_status sg_direct_force_static(int nx, int ny, double h, double G, const float *sigma, const float *deltax,
+                                 const float *deltay, float *fx, float *fy, void *stream);
+
 /* Static, human-readable name of a status. */
 const char *sg_strerror(sg_status status);
 

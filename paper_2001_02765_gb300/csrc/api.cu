@@ -17,7 +17,9 @@ void sg_set_last_cuda_error(cudaError_t e, const char *what)
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
 }
 
-static void set_error(const char *msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+void sg_set_last_error_message(const char *msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+static void set_error(const char *msg) { sg_set_last_error_message(msg); }
 
 // ------------------------------------------------------------------ timing --
 

@@ -23,6 +23,7 @@
     } while (0)
 
 void sg_set_last_cuda_error(cudaError_t e, const char *what);
+void sg_set_last_error_message(const char *msg);
 
 // ------------------------------------------------------------ complex math --
 

@@ -64,6 +64,8 @@ _SIGNATURES = {
     "sg_force_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "sg_direct_force_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sg_last_error": (ctypes.c_char_p, []),
     "sg_version": (ctypes.c_int, []),
@@ -182,6 +184,12 @@ def sg_plan_get_timing(handle):
     ms = (ctypes.c_double * len(STAGE_NAMES))()
     _check(load().sg_plan_get_timing(handle, ms, len(STAGE_NAMES)), "sg_plan_get_timing")
     return dict(zip(STAGE_NAMES, list(ms)))
+
+
+def sg_direct_force_static(nx, ny, h, G, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
+    """Raw device pointers (ints) of float32 arrays; allocation-free uniform direct sum."""
+    _check(load().sg_direct_force_static(int(nx), int(ny), float(h), float(G), sigma_ptr, dx_ptr or None,
+                                         dy_ptr or None, fx_ptr, fy_ptr, stream_ptr or None), "sg_direct_force_static")
 
 
 def sg_version():
