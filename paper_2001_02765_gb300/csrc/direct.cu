@@ -93,13 +93,14 @@ __device__ __forceinline__ void tile_pairs_f32(const float4 *__restrict__ w, flo
 #pragma unroll 1
     for (int r = 0; r < SG_TILE_Y; ++r) {
         const float v = fmaf((float)r, st, dv0);
-        const float av = fabsf(v), v2 = v * v;
+        // + 1e-30 keeps q > 0 where a zero-weight padding corner sits on a target
+        const float av = fabsf(v), v2 = fmaf(v, v, 1e-30f);
         const float iv = v == 0.0f ? 0.5f : __frcp_rn(av);
 #pragma unroll
         for (int c = 0; c < SG_TILE_X; ++c) {
             const float4 wc = w[r * SG_TILE_X + c];
             const float u = fmaf((float)c, st, du0);
-            const float q = fmaxf(fmaf(u, u, v2), 1e-30f);
+            const float q = fmaf(u, u, v2);
             const float rr = q * rsqrtf(q);
             const float g0 = copysignf(__log2f((av + rr) * iu[c]), v);
             const float g0y = copysignf(__log2f((fabsf(u) + rr) * iv), u);

@@ -15,9 +15,13 @@
 //     y[(j / NS) NS R + k + r NS] = X_r
 // (the Stockham auto-sort formulation; the output is in natural order).
 //
-// Twiddles come from a table tw[k] = exp(-2 pi i k / L), k < L, built in FP64
-// on the device; W_{NS R}^{r k} = tw[r k L / (NS R)]. The inverse transform
-// uses the conjugates and is not normalised.
+// Twiddles: a compact table per length L holds, for every stage with span
+// NS > 1, the NS values W_{NS R}^k = exp(-2 pi i k / (NS R)), k < NS, built in
+// FP64 on the device (sincospi) and cast for FP32 plans; the stages' tables lie
+// back to back (spans 8, 64, 512, ... so the table of span NS starts at
+// (NS - 8) / 7). A butterfly loads W^k once (consecutive k: a coalesced load)
+// and forms W^{2k} .. W^{7k} by complex products of depth at most 3. The
+// inverse transform uses the conjugates and is not normalised.
 //
 // Shared-memory layout: element i of the batch is stored at spad(i), which
 // inserts one padding element every 16 (8-byte complex) or 8 (16-byte complex)
@@ -47,6 +51,21 @@ __device__ __forceinline__ C twiddle(const C *__restrict__ tw, int idx)
     C w = __ldg(&tw[idx]);
     if (INV) w.y = -w.y;
     return w;
+}
+
+// offset of the stage table of span NS (NS = 8, 64, 512, ...) in the compact table
+__host__ __device__ constexpr int stage_table_offset(int NS) { return (NS - 8) / 7; }
+
+// entries of the compact table of a length-L transform
+__host__ __device__ constexpr int stage_table_size(int L)
+{
+    int total = 0;
+    for (int ns = 1; ns < L;) {
+        const int r = L / ns >= 8 ? 8 : L / ns;
+        if (ns > 1) total += ns;
+        ns *= r;
+    }
+    return total;
 }
 
 // multiply by -i (forward) or +i (inverse)
@@ -120,9 +139,22 @@ __device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
         if (NBF % THREADS == 0 || b < NBF) {
             const int seq = b / (L / R), j = b % (L / R);
             const int k = j % NS;
-            if (NS > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], twiddle<C, INV>(tw, r * k * (L / (NS * R))));
+            if constexpr (NS > 1) {
+                const C w1 = twiddle<C, INV>(tw, stage_table_offset(NS) + k);
+                v[p][1] = cmul(v[p][1], w1);
+                if constexpr (R >= 4) {
+                    const C w2 = cmul(w1, w1);
+                    const C w3 = cmul(w2, w1);
+                    v[p][2] = cmul(v[p][2], w2);
+                    v[p][3] = cmul(v[p][3], w3);
+                    if constexpr (R == 8) {
+                        const C w4 = cmul(w2, w2);
+                        v[p][4] = cmul(v[p][4], w4);
+                        v[p][5] = cmul(v[p][5], cmul(w4, w1));
+                        v[p][6] = cmul(v[p][6], cmul(w3, w3));
+                        v[p][7] = cmul(v[p][7], cmul(w4, w3));
+                    }
+                }
             }
             if constexpr (R == 8) dft8<C, INV>(v[p]);
             else if constexpr (R == 4) dft4<C, INV>(v[p][0], v[p][1], v[p][2], v[p][3]);

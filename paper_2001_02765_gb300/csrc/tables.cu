@@ -155,13 +155,18 @@ __global__ void k_extract_spectra(const double2 *z, T *planes, int px, int py, d
     }
 }
 
+// Compact stage table of a length-L transform: for each stage of span NS > 1
+// and radix R, entries W_{NS R}^k = exp(-2 pi i k / (NS R)), k < NS.
 __global__ void k_twiddles(double2 *tw64, float2 *tw32, int L)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
-        double s, c;
-        sincospi(-2.0 * (double)k / (double)L, &s, &c);
-        tw64[k] = make_double2(c, s);
-        if (tw32) tw32[k] = make_float2((float)c, (float)s);
+    for (int ns = 8, off = 0; ns < L; off += ns, ns *= 8) {
+        const int span = L / ns >= 8 ? 8 * ns : L;  // NS R
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += gridDim.x * blockDim.x) {
+            double s, c;
+            sincospi(-2.0 * (double)k / (double)span, &s, &c);
+            tw64[off + k] = make_double2(c, s);
+            tw32[off + k] = make_float2((float)c, (float)s);
+        }
     }
 }
 
@@ -185,25 +190,25 @@ static sg_status launch_fft_lines(double2 *data, int L, int count, int64_t seq_s
     return SG_OK;
 }
 
-// Twiddle tables: FP64 for every power of two in [SG_MIN_PAD, max_pad], then
-// FP32 copies of each (read by FP32 plans), back to back.
+// Compact twiddle tables (see fft.cuh): FP64 for every power of two in
+// [SG_MIN_PAD, max_pad], then FP32 copies of each (read by FP32 plans).
 sg_status sg_twiddles_build(sg_plan *plan)
 {
     int64_t off = 0;
     for (int L = SG_MIN_PAD; L <= plan->max_pad; L <<= 1) {
         plan->tw64_off[sg_ilog2(L)] = off;
-        off += (int64_t)L * sizeof(double2);
+        off += ((int64_t)stage_table_size(L) * sizeof(double2) + 255) / 256 * 256;
     }
     for (int L = SG_MIN_PAD; L <= plan->max_pad; L <<= 1) {
         plan->tw32_off[sg_ilog2(L)] = off;
-        off += (int64_t)L * sizeof(float2);
+        off += ((int64_t)stage_table_size(L) * sizeof(float2) + 255) / 256 * 256;
     }
     SG_CUDA_TRY(cudaMalloc(&plan->twiddles, (size_t)off));
     plan->device_bytes += off;
     for (int L = SG_MIN_PAD; L <= plan->max_pad; L <<= 1) {
         double2 *t64 = (double2 *)((char *)plan->twiddles + plan->tw64_off[sg_ilog2(L)]);
         float2 *t32 = (float2 *)((char *)plan->twiddles + plan->tw32_off[sg_ilog2(L)]);
-        k_twiddles<<<(L + 255) / 256, 256>>>(t64, t32, L);
+        k_twiddles<<<(L / 8 + 255) / 256, 256>>>(t64, t32, L);
         SG_CUDA_TRY(cudaGetLastError());
     }
     return SG_OK;
