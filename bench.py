@@ -141,6 +141,159 @@ def workload_amr3():
 WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3}
 
 
+# ------------------------------------------------------------ serving run --
+
+def serve_requests(n, seed=5):
+    """Seeded request mix: 70 % uniform grids N = round(exp U(ln 128, ln 2048)),
+    central slopes; 30 % centred nested ratio-2 hierarchies of 1-3 levels with
+    base 128^2 or 256^2, analytic slopes; densities Kuzmin (a ~ U[0.05, 0.3]) or
+    exponential (r0 ~ U[0.05, 0.2]). Returns a list of (key, patches, slope_mode,
+    density) tuples."""
+    from paper_2001_02765_gb300 import workloads as W
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        kuz = rng.uniform() < 0.5
+        par = float(rng.uniform(0.05, 0.3) if kuz else rng.uniform(0.05, 0.2))
+        if rng.uniform() < 0.7:
+            N = int(np.rint(np.exp(rng.uniform(np.log(128), np.log(2048)))))
+            N -= N % 2
+            patches = [(0,) + W.unit_grid(N)]
+            mode = 1
+        else:
+            base = int(rng.choice([128, 256]))
+            lev = int(rng.integers(1, 4))
+            patches = [(k,) + p for k, p in enumerate(W.centred_nested_patches(base, lev))]
+            mode = 2
+        key = (tuple(patches), mode, kuz, round(par, 3))
+        out.append((key, patches, mode, ("kuzmin" if kuz else "exp", round(par, 3))))
+    return out
+
+
+def _serve_inputs(patches, density):
+    from paper_2001_02765_gb300 import workloads as W
+    sig, gx, gy = [], [], []
+    for p in patches:
+        X, Y = W.cell_centres(*p[1:])
+        if density[0] == "kuzmin":
+            a, b, c = W.kuzmin_sigma(X, Y, density[1])
+        else:
+            a, b, c = W.exponential_sigma(X, Y, density[1])
+        sig.append(a.ravel())
+        gx.append(b.ravel())
+        gy.append(c.ravel())
+    return np.concatenate(sig), np.concatenate(gx), np.concatenate(gy)
+
+
+def run_serve(args):
+    """Continuous-batching server on a seeded Poisson request stream."""
+    import torch
+    from paper_2001_02765_gb300 import sg
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    reqs = serve_requests(args.serve_requests, seed=5 + rank)
+    cache = {}
+
+    def prepare(precision):
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        for key, patches, mode, dens in reqs:
+            k = (key, precision)
+            if k in cache:
+                continue
+            plan = sg.Plan(patches, precision=precision, slope_mode=mode)
+            a, b, c = _serve_inputs(patches, dens)
+            dev = lambda v: torch.from_numpy(v).to(dtype=dt, device="cuda")
+            ins = (dev(a), dev(b) if mode == 2 else None, dev(c) if mode == 2 else None)
+            uses = sum(1 for r in reqs if r[0] == key)
+            outs = [(torch.empty_like(ins[0]), torch.empty_like(ins[0])) for _ in range(min(uses, args.serve_inflight))]
+            cache[k] = dict(plan=plan, ins=ins, outs=outs, n=0, targets=plan.info["nleaves"])
+
+    def submit(server, key, precision):
+        c = cache[(key, precision)]
+        fx, fy = c["outs"][c["n"] % len(c["outs"])]
+        c["n"] += 1
+        ins = c["ins"]
+        return sg.sg_submit(server, c["plan"].handle, ins[0].data_ptr(), ins[1].data_ptr() if ins[1] is not None else 0,
+                            ins[2].data_ptr() if ins[2] is not None else 0, fx.data_ptr(), fy.data_ptr())
+
+    prepare("fp32")
+    torch.cuda.synchronize()
+    budget = args.serve_budget_gb << 30
+    server = sg.sg_server_create(budget, args.serve_inflight)
+    # warm-up and closed-loop capacity (everything submitted at once)
+    for key, *_ in reqs[: min(len(reqs), 16)]:
+        sg.sg_wait(server, submit(server, key, "fp32"), 600000.0)
+    t0 = time.perf_counter()
+    tickets = [submit(server, key, "fp32") for key, *_ in reqs]
+    for t in tickets:
+        sg.sg_wait(server, t, 600000.0)
+    capacity = len(reqs) / (time.perf_counter() - t0)
+    # open loop: Poisson arrivals at 0.8 x capacity
+    rate = args.serve_load * capacity
+    rng = np.random.Generator(np.random.PCG64(55))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    sg.sg_server_get_stats(server, reset_latencies=True)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        tickets = []
+        for (key, *_), at in zip(reqs, arrivals):
+            delay = at - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(submit(server, key, "fp32"))
+        for t in tickets:
+            sg.sg_wait(server, t, 600000.0)
+        wall = time.perf_counter() - t0
+    stats = sg.sg_server_get_stats(server)
+    sg.sg_server_destroy(server)
+    value = len(tickets) / wall  # the open-loop requests, all completed
+    targets = sum(cache[(key, "fp32")]["targets"] for key, *_ in reqs)
+
+    # the plain FP64 per-solve path on a time-bounded prefix of the same stream
+    prepare_keys = []
+    t_budget = args.serve_fp64_seconds
+    done64 = 0
+    t64 = 0.0
+    for key, patches, mode, dens in reqs:
+        if t64 > t_budget:
+            break
+        if (key, "fp64") not in cache:
+            sub = [r for r in reqs if r[0] == key][:1]
+            saved = list(reqs)
+            reqs[:] = sub
+            prepare("fp64")
+            reqs[:] = saved
+        c = cache[(key, "fp64")]
+        ins = c["ins"]
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        c["plan"].force(ins[0], ins[1], ins[2], c["outs"][0][0], c["outs"][0][1])
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - a
+        done64 += 1
+    for c in cache.values():
+        c["plan"].close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value * world, "unit": "solves/s", "n_gpus": world, "steps": len(reqs),
+        "warmup": 16, "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve_poisson_mix", "requests": len(reqs), "uniform": "128^2..2048^2 (70%)",
+                   "amr": "1-3 levels, base 128^2/256^2 (30%)", "load": args.serve_load,
+                   "budget_gb": args.serve_budget_gb, "max_inflight": args.serve_inflight, "precision": "fp32"},
+        "target_cells_per_s": targets / wall * world,
+        "latency_ms": {"p50": stats["latency_p50_ms"], "p99": stats["latency_p99_ms"],
+                       "mean": stats["latency_mean_ms"]},
+        "capacity_solves_per_s": capacity, "offered_rate": rate,
+        "peak_bytes": stats["peak_bytes"],
+        "fp64_plain": {"solves_per_s": done64 / t64 if t64 else None, "requests": done64,
+                       "note": "one solve at a time, same stream prefix"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------- oracle --
 
 class OracleSample:
@@ -406,11 +559,19 @@ def main():
     ap.add_argument("--cpu-targets", type=int, default=2048)
     ap.add_argument("--ref-targets", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the request-server workload instead")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-inflight", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-fp64-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_gpu(args)
 

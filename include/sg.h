@@ -92,8 +92,8 @@ typedef struct {
     int64_t ncells;             /* total cells over all patches (field array length) */
     int64_t nleaves;            /* leaf cells (targets) */
     int64_t cross_pairs;        /* leaf-target x leaf-source pairs summed directly */
-    int64_t device_bytes;       /* device memory held by the plan */
-    int64_t scratch_bytes;      /* of which per-call scratch */
+    int64_t device_bytes;       /* device memory held by the plan now */
+    int64_t scratch_bytes;      /* per-call scratch (workspace) of one solve */
     int max_pad;                /* largest padded FFT length */
 } sg_plan_info;
 
@@ -116,7 +116,9 @@ sg_status sg_geom_validate(const sg_geom *geom);
  * generate the FP64 kernel tables of every patch (Section 2 closed forms),
  * transform them into kernel spectra, and build the cross-patch target and
  * corner-tile lists. Device work runs on the legacy default stream and is
- * complete when the call returns.
+ * complete when the call returns. The plan's own per-call scratch
+ * (sg_plan_info.scratch_bytes) is allocated at its first sg_force; the request
+ * server gives each request its own instead.
  *   geom        geometry (host memory, read during the call only)
  *   prec        SG_FP64 or SG_FP32
  *   hbm_budget  maximum device bytes the plan may hold (0 = no limit);
@@ -214,6 +216,64 @@ sg_status sg_plan_get_timing(sg_plan *plan, double *ms, int n);
  */
 sg_status sg_direct_force_static(int nx, int ny, double h, double G, const float *sigma, const float *deltax,
                                  const float *deltay, float *fx, float *fy, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Request server (continuous batching on one GPU; not in the paper).
+ *
+ * sg_submit queues a solve (a plan plus caller-owned device buffers, as for
+ * sg_force) and returns at once. A worker thread admits queued requests in
+ * arrival order while one of max_inflight slots is free and the per-request
+ * workspace (sg_plan_info.scratch_bytes) fits in what remains of hbm_budget
+ * (0 = no limit); each admitted request gets its own workspace from the
+ * server's stream-ordered memory pool and runs on its slot's stream, so
+ * requests arriving while others run start as slots and memory free up and
+ * overlap on the device. Plans stay resident and may be shared by many
+ * requests; a result is bit-for-bit the same alone and in any mix. Completion
+ * is observed on the host (a stream host function); nothing waits on the GPU.
+ * The caller keeps the plan and the buffers alive until the request finished,
+ * and must not destroy a plan with requests in flight. The server is
+ * thread-safe. Latency = completion time of the request's GPU work minus its
+ * submission time (host steady clock).
+ * ------------------------------------------------------------------------ */
+typedef struct sg_server sg_server;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled, rejected;
+    int64_t queued, running;        /* right now */
+    int64_t bytes_in_use, peak_bytes;
+    int64_t latency_count;          /* completed requests the latencies cover */
+    double latency_p50_ms, latency_p99_ms, latency_mean_ms;
+} sg_server_stats;
+
+/* Create a server on the current device. max_inflight: 1..256 concurrent
+ * requests (one stream each). Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+sg_status sg_server_create(size_t hbm_budget, int max_inflight, sg_server **out);
+
+/* Cancel queued requests, wait for running ones, release everything. NULL is a no-op. */
+sg_status sg_server_destroy(sg_server *server);
+
+/* Queue one solve; *ticket identifies it. SG_EBUDGET (rejected) if its workspace
+ * alone exceeds the budget; SG_EINVAL for null pointers, missing caller slopes or
+ * a plan of another device. */
+sg_status sg_submit(sg_server *server, sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
+                    void *fx, void *fy, uint64_t *ticket);
+
+/* Non-blocking. SG_EBUSY while queued or running; SG_OK once finished, with
+ * *result the solve's status (SG_ECANCELLED if cancelled) and *latency_ms its
+ * latency; the ticket is then retired (SG_ENOTFOUND afterwards, or for an
+ * unknown ticket). result and latency_ms may be NULL. */
+sg_status sg_poll(sg_server *server, uint64_t ticket, sg_status *result, double *latency_ms);
+
+/* As sg_poll but waits up to timeout_ms; SG_ETIMEOUT if the request has not
+ * finished by then (it keeps running and can be waited for again). */
+sg_status sg_wait(sg_server *server, uint64_t ticket, double timeout_ms, sg_status *result, double *latency_ms);
+
+/* Cancel a request that has not started (SG_OK); SG_EBUSY if it is running. */
+sg_status sg_cancel(sg_server *server, uint64_t ticket);
+
+/* Counters and latency percentiles over the requests completed so far (the
+ * latency samples are cleared afterwards when reset_latencies != 0). */
+sg_status sg_server_get_stats(sg_server *server, sg_server_stats *out, int reset_latencies);
 
 /* Static, human-readable name of a status. */
 const char *sg_strerror(sg_status status);

@@ -94,9 +94,10 @@ __global__ void k_defect(sg_patch_dev q, sg_patch_dev p, T *__restrict__ s)
 }
 
 template <typename T>
-sg_status prepare_t(sg_plan *plan, const void *sigma, const void *dx, const void *dy, cudaStream_t st)
+sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                    cudaStream_t st)
 {
-    T *s = (T *)plan->sfield;
+    T *s = (T *)ws->sfield;
     const bool slopes = plan->geom.slope_mode == SG_SLOPES_CALLER;
     for (int k = plan->npatches - 1; k >= 0; --k) {
         const sg_patch_dev &d = plan->pp[k].d;
@@ -121,11 +122,12 @@ sg_status prepare_t(sg_plan *plan, const void *sigma, const void *dx, const void
 
 }  // namespace
 
-sg_status sg_amr_prepare(sg_plan *plan, const void *sigma, const void *dx, const void *dy, cudaStream_t st)
+sg_status sg_amr_prepare(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                         cudaStream_t st)
 {
-    sg_timing_begin(plan, SG_STAGE_COMPOSITE, st);
-    sg_status r = plan->prec == SG_FP64 ? prepare_t<double>(plan, sigma, dx, dy, st)
-                                        : prepare_t<float>(plan, sigma, dx, dy, st);
-    sg_timing_end(plan, SG_STAGE_COMPOSITE, st);
+    sg_timing_begin(ws, SG_STAGE_COMPOSITE, st);
+    sg_status r = plan->prec == SG_FP64 ? prepare_t<double>(plan, ws, sigma, dx, dy, st)
+                                        : prepare_t<float>(plan, ws, sigma, dx, dy, st);
+    sg_timing_end(ws, SG_STAGE_COMPOSITE, st);
     return r;
 }

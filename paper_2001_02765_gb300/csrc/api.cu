@@ -40,17 +40,17 @@ static cudaEvent_t timing_event(sg_timing *t)
     return t->pool[t->used++];
 }
 
-void sg_timing_reset(sg_plan *plan)
+void sg_timing_reset(sg_timing *t)
 {
-    if (!plan->timing) return;
-    plan->timing->used = 0;
-    plan->timing->stage.clear();
-    plan->timing->open = -1;
+    if (!t) return;
+    t->used = 0;
+    t->stage.clear();
+    t->open = -1;
 }
 
-void sg_timing_begin(sg_plan *plan, int stage, cudaStream_t st)
+void sg_timing_begin(const sg_workspace *ws, int stage, cudaStream_t st)
 {
-    sg_timing *t = plan->timing;
+    sg_timing *t = ws->timing;
     if (!t) return;
     cudaEvent_t e = timing_event(t);
     if (!e) return;
@@ -59,9 +59,9 @@ void sg_timing_begin(sg_plan *plan, int stage, cudaStream_t st)
     t->stage.push_back(stage);
 }
 
-void sg_timing_end(sg_plan *plan, int stage, cudaStream_t st)
+void sg_timing_end(const sg_workspace *ws, int stage, cudaStream_t st)
 {
-    sg_timing *t = plan->timing;
+    sg_timing *t = ws->timing;
     if (!t || t->open < 0) return;
     cudaEvent_t e = timing_event(t);
     if (!e) return;
@@ -325,16 +325,14 @@ void plan_free(sg_plan *plan)
     cudaFree(plan->twiddles);
     cudaFree(plan->cov_rects);
     cudaFree(plan->cov_child);
-    cudaFree(plan->sfield);
-    cudaFree(plan->work_fwd);
-    cudaFree(plan->work_inv);
+    if (plan->ws) {
+        sg_workspace_free(plan->ws, 0, false);
+        delete plan->ws;
+    }
     cudaFree(plan->tiles);
-    cudaFree(plan->tile_w32);
-    cudaFree(plan->tile_w64);
     cudaFree(plan->targets);
     cudaFree(plan->blocks);
     cudaFree(plan->patch_dev);
-    cudaFree(plan->partial);
     cudaFree(plan->stage_in);
     cudaFree(plan->stage_out);
     delete[] plan->pp;
@@ -428,10 +426,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     if (st == SG_OK && !cov_child_all.empty())
         st = cudaMemcpy(plan->cov_child, cov_child_all.data(), cov_child_all.size() * sizeof(int),
                         cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
-    if (st == SG_OK && gi.n > 1) {
-        st = dev_alloc(plan, &plan->sfield, 3 * (size_t)gi.ncells * es);
-        plan->scratch_bytes += 3 * gi.ncells * (int64_t)es;
-    }
+    if (gi.n > 1) plan->ws_sfield_bytes = 3 * gi.ncells * (int64_t)es;
     if (st == SG_OK) st = dev_alloc(plan, &plan->patch_dev, gi.n * sizeof(sg_patch_dev));
     if (st == SG_OK)
         st = cudaMemcpy(plan->patch_dev, pdev.data(), gi.n * sizeof(sg_patch_dev), cudaMemcpyHostToDevice) == cudaSuccess
@@ -443,9 +438,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         if (3 * q > wf) wf = 3 * q;
         if (2 * q > wi) wi = 2 * q;
     }
-    if (st == SG_OK) st = dev_alloc(plan, &plan->work_fwd, (size_t)wf);
-    if (st == SG_OK) st = dev_alloc(plan, &plan->work_inv, (size_t)wi);
-    plan->scratch_bytes = wf + wi;
+    plan->ws_fwd_bytes = wf;
+    plan->ws_inv_bytes = wi;
     // cross-patch direct sum
     if (st == SG_OK && gi.n > 1 && !tiles.empty()) {
         plan->ntiles = (int)tiles.size();
@@ -454,11 +448,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             st = cudaMemcpy(plan->tiles, tiles.data(), tiles.size() * sizeof(sg_tile_desc), cudaMemcpyHostToDevice) ==
                          cudaSuccess ? SG_OK : SG_ECUDA;
         const size_t nw = (size_t)plan->ntiles * SG_TILE_N;
-        if (st == SG_OK) {
-            if (prec == SG_FP64) st = dev_alloc(plan, &plan->tile_w64, nw * sizeof(sg_dvec4));
-            else st = dev_alloc(plan, &plan->tile_w32, nw * sizeof(float4));
-            plan->scratch_bytes += (int64_t)nw * 4 * (int64_t)es;
-        }
+        plan->ws_tile_bytes = (int64_t)nw * (prec == SG_FP64 ? (int64_t)sizeof(sg_dvec4) : (int64_t)sizeof(float4));
         // targets: every leaf, row-major per patch, blocks of SG_DIRECT_THREADS
         std::vector<int4> tg;
         std::vector<sg_target_block> blocks;
@@ -498,11 +488,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         if (st == SG_OK)
             st = cudaMemcpy(plan->blocks, blocks.data(), blocks.size() * sizeof(sg_target_block),
                             cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
-        if (st == SG_OK && nsplit > 1) {
-            st = dev_alloc(plan, &plan->partial, (size_t)nsplit * tg.size() * 2 * sizeof(double));
-            plan->scratch_bytes += (int64_t)nsplit * (int64_t)tg.size() * 16;
-        }
+        if (nsplit > 1) plan->ws_partial_bytes = (int64_t)nsplit * (int64_t)tg.size() * 2 * (int64_t)sizeof(double);
     }
+    plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
     if (st == SG_OK) st = sg_twiddles_build(plan);
     if (st == SG_OK) st = sg_tables_build(plan);
     if (st == SG_OK) {
@@ -523,6 +511,68 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
+
+// ------------------------------------------------------------- workspaces --
+
+int64_t sg_workspace_bytes(const sg_plan *plan)
+{
+    return plan->ws_fwd_bytes + plan->ws_inv_bytes + plan->ws_sfield_bytes + plan->ws_tile_bytes +
+           plan->ws_partial_bytes;
+}
+
+static sg_status ws_alloc_one(void **p, int64_t bytes, cudaStream_t st, bool async)
+{
+    *p = nullptr;
+    if (bytes <= 0) return SG_OK;
+    cudaError_t e = async ? cudaMallocAsync(p, (size_t)bytes, st) : cudaMalloc(p, (size_t)bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        sg_set_last_cuda_error(e, async ? "cudaMallocAsync" : "cudaMalloc");
+        return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
+    }
+    return SG_OK;
+}
+
+void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async)
+{
+    void *bufs[5] = {ws->work_fwd, ws->work_inv, ws->sfield, ws->tile_w, ws->partial};
+    for (void *b : bufs) {
+        if (!b) continue;
+        if (async) cudaFreeAsync(b, st);
+        else cudaFree(b);
+    }
+    ws->work_fwd = ws->work_inv = ws->sfield = ws->tile_w = nullptr;
+    ws->partial = nullptr;
+}
+
+sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t st, bool async)
+{
+    memset(ws, 0, sizeof(*ws));
+    sg_status r = ws_alloc_one(&ws->work_fwd, plan->ws_fwd_bytes, st, async);
+    if (r == SG_OK) r = ws_alloc_one(&ws->work_inv, plan->ws_inv_bytes, st, async);
+    if (r == SG_OK) r = ws_alloc_one(&ws->sfield, plan->ws_sfield_bytes, st, async);
+    if (r == SG_OK) r = ws_alloc_one(&ws->tile_w, plan->ws_tile_bytes, st, async);
+    if (r == SG_OK) r = ws_alloc_one((void **)&ws->partial, plan->ws_partial_bytes, st, async);
+    if (r != SG_OK) sg_workspace_free(ws, st, async);
+    return r;
+}
+
+sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *deltax, const void *deltay,
+                      void *fx, void *fy, cudaStream_t st)
+{
+    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    const void *dx = caller ? deltax : nullptr, *dy = caller ? deltay : nullptr;
+    if (plan->npatches == 1) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, st);
+    // AMR: composite sources, same-patch FFT convolutions, cross-patch direct sum
+    SG_TRY(sg_amr_prepare(plan, ws, sigma, dx, dy, st));
+    const size_t es = elem_size(plan->prec);
+    const char *S = (const char *)ws->sfield;
+    const size_t plane = (size_t)plan->ncells * es;
+    for (int k = 0; k < plan->npatches; ++k)
+        SG_TRY(sg_uniform_solve(plan, ws, k, S, S + plane, S + 2 * plane, fx, fy, st));
+    return sg_cross_solve(plan, ws, S, S + plane, S + 2 * plane, fx, fy, st);
+}
 
 // --------------------------------------------------------------- the C ABI --
 
@@ -590,17 +640,20 @@ sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const v
     int dev = -1;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != plan->device) return fail("the plan's device is not current");
-    cudaStream_t st = (cudaStream_t)stream;
-    sg_timing_reset(plan);
-    const void *dx = caller ? deltax : nullptr, *dy = caller ? deltay : nullptr;
-    if (plan->npatches == 1) return sg_uniform_solve(plan, 0, sigma, dx, dy, fx, fy, st);
-    // AMR: composite sources, same-patch FFT convolutions, cross-patch direct sum
-    SG_TRY(sg_amr_prepare(plan, sigma, dx, dy, st));
-    const char *S = (const char *)plan->sfield;
-    const size_t plane = (size_t)plan->ncells * es;
-    for (int k = 0; k < plan->npatches; ++k) SG_TRY(sg_uniform_solve(plan, k, S, S + plane, S + 2 * plane, fx, fy, st));
-    SG_TRY(sg_cross_solve(plan, S, S + plane, S + 2 * plane, fx, fy, st));
-    return SG_OK;
+    if (!plan->ws) {
+        sg_workspace *ws = new (std::nothrow) sg_workspace();
+        if (!ws) return SG_ENOMEM;
+        sg_status a = sg_workspace_alloc(plan, ws, 0, false);
+        if (a != SG_OK) {
+            delete ws;
+            return a;
+        }
+        plan->ws = ws;
+        plan->device_bytes += plan->scratch_bytes;
+    }
+    sg_timing_reset(plan->timing);
+    plan->ws->timing = plan->timing;
+    return sg_force_ws(plan, plan->ws, sigma, deltax, deltay, fx, fy, (cudaStream_t)stream);
 }
 
 sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,

@@ -138,13 +138,10 @@ struct sg_plan {
     int *cov_child;
     int ncov_total;
 
-    // composite source fields of an AMR plan, 3 x ncells of T: the filled level
-    // data on level 0 and the fine-minus-prolonged-coarse difference on finer patches
-    void *sfield;
 
-    // uniform-transform scratch, sized for the largest patch
-    void *work_fwd;                 // 3 x (px/2+1) x ny complex
-    void *work_inv;                 // 2 x (px/2+1) x ny complex
+    // per-call scratch sizes (bytes) and the plan's own workspace (used by sg_force)
+    int64_t ws_fwd_bytes, ws_inv_bytes, ws_sfield_bytes, ws_tile_bytes, ws_partial_bytes;
+    struct sg_workspace *ws;
 
     // cross-patch direct sum
     int ntiles;
@@ -163,29 +160,52 @@ struct sg_plan {
     void *stage_in, *stage_out;
     size_t stage_bytes;
 
-    // per-stage device timers of the last solve (NULL when timing is off)
+    // per-stage device timers of the last sg_force (NULL when timing is off)
     struct sg_timing *timing;
 };
+
+// Per-call scratch of a solve. A plan owns one (sg_force); the request server
+// gives every in-flight request its own, so requests on one plan can overlap.
+struct sg_workspace {
+    void *work_fwd;         // uniform-transform scratch: 3 x (px/2+1) x ny complex (largest patch)
+    void *work_inv;         // 2 x (px/2+1) x ny complex
+    void *sfield;           // AMR composite source fields, 3 x ncells of T
+    void *tile_w;           // AMR corner weights, ntiles x SG_TILE_N x 4 of T
+    double *partial;        // AMR split partial sums, nsplit x ntargets x 2 (nsplit > 1)
+    struct sg_timing *timing;  // stage timers, or NULL
+};
+
+// Allocate / free a workspace for a plan. async: stream-ordered allocation on st.
+sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t st, bool async);
+void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async);
+int64_t sg_workspace_bytes(const sg_plan *plan);
+// One solve on an explicit workspace (sg_force uses the plan's own).
+sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                      void *fx, void *fy, cudaStream_t st);
 
 // Stages timed by sg_plan_get_timing.
 enum { SG_STAGE_ROW_FWD = 0, SG_STAGE_COL_CONV = 1, SG_STAGE_ROW_INV = 2, SG_STAGE_WEIGHTS = 3,
        SG_STAGE_DIRECT = 4, SG_STAGE_COMPOSITE = 5, SG_NSTAGES = 6 };
 
 // Record the start / end of a stage on a stream (no-op when timing is off).
-void sg_timing_begin(sg_plan *plan, int stage, cudaStream_t st);
-void sg_timing_end(sg_plan *plan, int stage, cudaStream_t st);
-void sg_timing_reset(sg_plan *plan);
+void sg_timing_begin(const struct sg_workspace *ws, int stage, cudaStream_t st);
+void sg_timing_end(const struct sg_workspace *ws, int stage, cudaStream_t st);
+void sg_timing_reset(struct sg_timing *t);
 
 // ---------------------------------------------------------- host functions --
+
+struct sg_workspace;
+struct sg_timing;
 
 sg_status sg_tables_build(sg_plan *plan);     // tables + spectra of every patch
 sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host_out, size_t n);
 sg_status sg_twiddles_build(sg_plan *plan);
-sg_status sg_uniform_solve(sg_plan *plan, int patch, const void *sigma, const void *dx, const void *dy,
-                           void *fx, void *fy, cudaStream_t st);
-sg_status sg_cross_solve(sg_plan *plan, const void *sigma, const void *dx, const void *dy,
+sg_status sg_uniform_solve(sg_plan *plan, const struct sg_workspace *ws, int patch, const void *sigma, const void *dx,
+                           const void *dy, void *fx, void *fy, cudaStream_t st);
+sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          void *fx, void *fy, cudaStream_t st);
-sg_status sg_amr_prepare(sg_plan *plan, const void *sigma, const void *dx, const void *dy, cudaStream_t st);
+sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                         cudaStream_t st);
 
 static inline int sg_ilog2(int v)
 {

@@ -231,39 +231,39 @@ __global__ void k_cross_reduce(const int4 *__restrict__ targets, int ntargets, i
 }
 
 template <typename T>
-sg_status cross_solve_t(sg_plan *plan, const void *sigma, const void *dx, const void *dy, void *fx, void *fy,
-                        cudaStream_t st)
+sg_status cross_solve_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                        void *fx, void *fy, cudaStream_t st)
 {
     if (plan->ntiles == 0 || plan->ntargets == 0) return SG_OK;
-    T *w = sizeof(T) == 4 ? (T *)plan->tile_w32 : (T *)plan->tile_w64;
+    T *w = (T *)ws->tile_w;
     const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
     int grid_w = (int)((nw + 255) / 256);
     if (grid_w > 65535) grid_w = 65535;
-    sg_timing_begin(plan, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
     k_corner_weights<T><<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, (const T *)sigma,
                                                  (const T *)dx, (const T *)dy, plan->lattice_unit, w);
     SG_CUDA_TRY(cudaGetLastError());
-    sg_timing_end(plan, SG_STAGE_WEIGHTS, st);
-    sg_timing_begin(plan, SG_STAGE_DIRECT, st);
+    sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_DIRECT, st);
     dim3 grid(plan->nblocks, plan->nsplit);
     k_cross_direct<T><<<grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->targets, plan->tiles, plan->ntiles, w,
                                                           plan->nsplit, plan->geom.G, (T *)fx, (T *)fy,
-                                                          plan->partial, plan->ntargets);
+                                                          ws->partial, plan->ntargets);
     SG_CUDA_TRY(cudaGetLastError());
     if (plan->nsplit > 1) {
         k_cross_reduce<T><<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
-                                                                         plan->partial, (T *)fx, (T *)fy);
+                                                                         ws->partial, (T *)fx, (T *)fy);
         SG_CUDA_TRY(cudaGetLastError());
     }
-    sg_timing_end(plan, SG_STAGE_DIRECT, st);
+    sg_timing_end(ws, SG_STAGE_DIRECT, st);
     return SG_OK;
 }
 
 }  // namespace
 
-sg_status sg_cross_solve(sg_plan *plan, const void *sigma, const void *dx, const void *dy, void *fx, void *fy,
-                         cudaStream_t st)
+sg_status sg_cross_solve(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                         void *fx, void *fy, cudaStream_t st)
 {
-    if (plan->prec == SG_FP64) return cross_solve_t<double>(plan, sigma, dx, dy, fx, fy, st);
-    return cross_solve_t<float>(plan, sigma, dx, dy, fx, fy, st);
+    if (plan->prec == SG_FP64) return cross_solve_t<double>(plan, ws, sigma, dx, dy, fx, fy, st);
+    return cross_solve_t<float>(plan, ws, sigma, dx, dy, fx, fy, st);
 }

@@ -281,8 +281,8 @@ sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny,
     }
 
 template <typename T>
-sg_status uniform_solve_t(sg_plan *plan, int p, const void *sigma, const void *dx, const void *dy, void *fx, void *fy,
-                          cudaStream_t st)
+sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const void *sigma, const void *dx,
+                          const void *dy, void *fx, void *fy, cudaStream_t st)
 {
     using C = cplx_t<T>;
     const sg_patch_plan &pp = plan->pp[p];
@@ -300,7 +300,7 @@ sg_status uniform_solve_t(sg_plan *plan, int p, const void *sigma, const void *d
     src.ncov = d.ncov;
     if (plan->npatches > 1) {
         // AMR: the composite source fields (three planes, no covered cells to mask)
-        const T *S = (const T *)plan->sfield;
+        const T *S = (const T *)ws->sfield;
         src.sigma = S + off;
         src.dx = S + plan->ncells + off;
         src.dy = S + 2 * plan->ncells + off;
@@ -309,29 +309,29 @@ sg_status uniform_solve_t(sg_plan *plan, int p, const void *sigma, const void *d
     }
     const int nf = src.mode == SG_SLOPES_NONE ? 1 : 3;
     const int qx = d.px / 2 + 1;
-    C *wf = (C *)plan->work_fwd;
-    C *wi = (C *)plan->work_inv;
+    C *wf = (C *)ws->work_fwd;
+    C *wi = (C *)ws->work_inv;
     const int64_t *twoff = sizeof(T) == 8 ? plan->tw64_off : plan->tw32_off;
     const C *twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.px)]);
     const C *twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.py)]);
     T *ox = (T *)fx + off, *oy = (T *)fy + off;
-    sg_timing_begin(plan, SG_STAGE_ROW_FWD, st);
+    sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
     SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_fwd<T, PP>(src, wf, nf, twx, st))));
-    sg_timing_end(plan, SG_STAGE_ROW_FWD, st);
-    sg_timing_begin(plan, SG_STAGE_COL_CONV, st);
+    sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
+    sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
     SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, st))));
-    sg_timing_end(plan, SG_STAGE_COL_CONV, st);
-    sg_timing_begin(plan, SG_STAGE_ROW_INV, st);
+    sg_timing_end(ws, SG_STAGE_COL_CONV, st);
+    sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
     SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, oy, d.nx, d.ny, twx, st))));
-    sg_timing_end(plan, SG_STAGE_ROW_INV, st);
+    sg_timing_end(ws, SG_STAGE_ROW_INV, st);
     return SG_OK;
 }
 
 }  // namespace
 
-sg_status sg_uniform_solve(sg_plan *plan, int patch, const void *sigma, const void *dx, const void *dy, void *fx,
-                           void *fy, cudaStream_t st)
+sg_status sg_uniform_solve(sg_plan *plan, const sg_workspace *ws, int patch, const void *sigma, const void *dx,
+                           const void *dy, void *fx, void *fy, cudaStream_t st)
 {
-    if (plan->prec == SG_FP64) return uniform_solve_t<double>(plan, patch, sigma, dx, dy, fx, fy, st);
-    return uniform_solve_t<float>(plan, patch, sigma, dx, dy, fx, fy, st);
+    if (plan->prec == SG_FP64) return uniform_solve_t<double>(plan, ws, patch, sigma, dx, dy, fx, fy, st);
+    return uniform_solve_t<float>(plan, ws, patch, sigma, dx, dy, fx, fy, st);
 }

@@ -51,6 +51,14 @@ class sg_plan_info(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_int64), ("max_pad", ctypes.c_int)]
 
 
+class sg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("queued", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("latency_count", ctypes.c_int64), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("latency_mean_ms", ctypes.c_double)]
+
+
 # name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _SIGNATURES = {
@@ -66,6 +74,14 @@ _SIGNATURES = {
     "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "sg_direct_force_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "sg_server_destroy": (ctypes.c_int, [_VP]),
+    "sg_submit": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "sg_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "sg_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "sg_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "sg_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sg_server_stats), ctypes.c_int]),
     "sg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sg_last_error": (ctypes.c_char_p, []),
     "sg_version": (ctypes.c_int, []),
@@ -190,6 +206,51 @@ def sg_direct_force_static(nx, ny, h, G, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_p
     """Raw device pointers (ints) of float32 arrays; allocation-free uniform direct sum."""
     _check(load().sg_direct_force_static(int(nx), int(ny), float(h), float(G), sigma_ptr, dx_ptr or None,
                                          dy_ptr or None, fx_ptr, fy_ptr, stream_ptr or None), "sg_direct_force_static")
+
+
+def sg_server_create(hbm_budget=0, max_inflight=8):
+    h = _VP()
+    _check(load().sg_server_create(int(hbm_budget), int(max_inflight), ctypes.byref(h)), "sg_server_create")
+    return h.value
+
+
+def sg_server_destroy(handle):
+    if handle:
+        _check(load().sg_server_destroy(handle), "sg_server_destroy")
+
+
+def sg_submit(server, plan_handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr):
+    """Queue a solve (raw device pointers). Returns the ticket; raises SgError (e.g. SG_EBUDGET)."""
+    t = ctypes.c_uint64(0)
+    _check(load().sg_submit(server, plan_handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr,
+                            ctypes.byref(t)), "sg_submit")
+    return int(t.value)
+
+
+def sg_poll(server, ticket):
+    """Returns (status, result, latency_ms): status SG_OK when finished, SG_EBUSY, or SG_ENOTFOUND."""
+    res = ctypes.c_int(0)
+    lat = ctypes.c_double(0.0)
+    st = load().sg_poll(server, int(ticket), ctypes.byref(res), ctypes.byref(lat))
+    return st, res.value, lat.value
+
+
+def sg_wait(server, ticket, timeout_ms):
+    """Returns (status, result, latency_ms): status SG_OK, SG_ETIMEOUT or SG_ENOTFOUND."""
+    res = ctypes.c_int(0)
+    lat = ctypes.c_double(0.0)
+    st = load().sg_wait(server, int(ticket), float(timeout_ms), ctypes.byref(res), ctypes.byref(lat))
+    return st, res.value, lat.value
+
+
+def sg_cancel(server, ticket):
+    return load().sg_cancel(server, int(ticket))
+
+
+def sg_server_get_stats(server, reset_latencies=False):
+    out = sg_server_stats()
+    _check(load().sg_server_get_stats(server, ctypes.byref(out), int(bool(reset_latencies))), "sg_server_get_stats")
+    return {k: getattr(out, k) for k, _ in sg_server_stats._fields_}
 
 
 def sg_version():
