@@ -99,6 +99,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def job_rate(local_ms, local_solves):
+    """Whole-job rate of independent replicas: solves summed over ranks divided
+    by the slowest rank's time (max over ranks). Uses the initialised
+    torch.distributed group when there is one (any backend)."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+        n = torch.tensor([float(local_solves)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        local_ms, local_solves = float(t.item()), float(n.item())
+    return local_solves / (local_ms / 1e3), local_ms, local_solves
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -399,13 +415,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     per = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(per)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    solves = args.steps * world
-    value = solves / (total_ms / 1e3)
+    value, total_ms, solves = job_rate(sum(per), args.steps)
     p50 = float(np.percentile(per, 50))
     p99 = float(np.percentile(per, 99))
 
