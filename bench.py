@@ -157,6 +157,95 @@ def workload_amr3():
 WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3}
 
 
+# -------------------------------------------------------------- batch run --
+
+def run_batch(args):
+    """64 independent spiral disks (N log-uniform 64..512, seed 4), one CUDA
+    graph launch per step, versus the same solves launched one by one."""
+    import torch
+    from paper_2001_02765_gb300 import sg
+    from paper_2001_02765_gb300 import workloads as W
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ns, a, amp = W.batch_sizes(count=args.batch_size, lo=64, hi=512, seed=4 + rank)
+
+    def build(precision):
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        plans, ins, outs = [], [], []
+        for k, n in enumerate(ns):
+            patches = [(0,) + W.unit_grid(int(n))]
+            X, Y = W.cell_centres(*patches[0][1:])
+            s, _, _ = W.spiral_sigma(X, Y, a[k], amp[k])
+            plans.append(sg.Plan(patches, precision=precision, slope_mode=sg.SG_SLOPES_CENTRAL))
+            ins.append(torch.from_numpy(s.ravel()).to(dtype=dt, device="cuda"))
+            outs.append((torch.empty_like(ins[-1]), torch.empty_like(ins[-1])))
+        return plans, ins, outs
+
+    plans, ins, outs = build("fp32")
+    batch = sg.sg_batch_create([p.handle for p in plans], [i.data_ptr() for i in ins], [0] * len(ins), [0] * len(ins),
+                               [o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs])
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+            fn()
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [x.elapsed_time(y) for x, y in ev]
+
+    graph = lambda: sg.sg_batch_launch(batch, stream.cuda_stream)
+
+    def one_by_one(pl=plans, i_=ins, o_=outs):
+        for p, i, o in zip(pl, i_, o_):
+            p.force(i, None, None, o[0], o[1], stream=stream)
+
+    timed(graph, args.warmup)
+    timed(one_by_one, args.warmup)
+    with ClockSampler(local) as clk:
+        per = timed(graph, args.steps)
+    per_seq = timed(one_by_one, args.steps)
+    value, total_ms, solves = job_rate(sum(per), args.steps * len(plans))
+    # FP64 plain per-solve path and the FP32 error against it
+    plans64, ins64, outs64 = build("fp64")
+    for p, i, o in zip(plans64, ins64, outs64):
+        p.force(i, None, None, o[0], o[1])
+    graph()
+    torch.cuda.synchronize()
+    num = sum(float(torch.sum((o[0].double() - q[0]) ** 2) + torch.sum((o[1].double() - q[1]) ** 2))
+              for o, q in zip(outs, outs64))
+    den = sum(float(torch.sum(q[0] ** 2) + torch.sum(q[1] ** 2)) for q in outs64)
+    n64 = max(1, min(args.steps, 3))
+    per64 = timed(lambda: one_by_one(plans64, ins64, outs64), n64)
+    sg.sg_batch_destroy(batch)
+    targets = int(sum(int(n) ** 2 for n in ns))
+    for p in plans + plans64:
+        p.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64_graph", "members": len(ns), "sizes": "N = round(exp U(ln 64, ln 512)), seed 4",
+                   "disk": "Kuzmin a~U[.05,.3] x (1 + A cos(2 theta - ln R / tan 15deg)), A~U[0,.2]",
+                   "slopes": "central", "precision": "fp32", "l2": "flushed before every batch (512 MB write)"},
+        "target_cells_per_s": value / len(ns) * targets,
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+        "one_by_one": {"solves_per_s": len(ns) * args.steps / (sum(per_seq) / 1e3)},
+        "fp64_plain": {"solves_per_s": len(ns) * n64 / (sum(per64) / 1e3)},
+        "rel_err_vs_fp64": float(np.sqrt(num / den)),
+        "gpu_launches": args.steps * 3 * len(ns),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ serving run --
 
 def serve_requests(n, seed=5):
@@ -507,7 +596,8 @@ def algorithmic_bytes(wl, info, stage):
     intermediates of (P/2+1) x ny bins per field, spectra planes, inputs, outputs."""
     es = 4
     total = 0
-    nf = 1 if wl["slope_mode"] == 0 else 3
+    # central slopes are formed from sigma's transforms: one field is transformed
+    nf = 3 if wl["slope_mode"] == 2 else 1
     for p in wl["patches"]:
         nx, ny = p[1], p[2]
         px = 64
@@ -570,6 +660,8 @@ def main():
     ap.add_argument("--ref-targets", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true", help="run the request-server workload instead")
+    ap.add_argument("--batch", action="store_true", help="run the graph-captured batch workload instead")
+    ap.add_argument("--batch-size", type=int, default=64)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-inflight", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
@@ -582,6 +674,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.batch:
+        run_batch(args)
     else:
         run_gpu(args)
 

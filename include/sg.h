@@ -218,6 +218,29 @@ sg_status sg_direct_force_static(int nx, int ny, double h, double G, const float
                                  const float *deltay, float *fx, float *fy, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batches (not in the paper): n independent solves bound to their plans and
+ * caller-owned device buffers at creation and captured once into a CUDA graph
+ * with one branch per member (each with its own workspace), so uneven solves
+ * overlap on the device and the whole batch costs one graph launch. The
+ * buffers stay bound: refill them and launch again. Results are bit-for-bit
+ * those of sg_force on the same inputs.
+ * ------------------------------------------------------------------------ */
+typedef struct sg_batch sg_batch;
+
+/* plans, sigma, fx, fy: arrays of n entries; deltax, deltay: arrays of n
+ * entries (entries used for SG_SLOPES_CALLER plans) or NULL. Capture runs on
+ * internal streams; nothing executes until sg_batch_launch. Errors: SG_EINVAL,
+ * SG_ENOMEM, SG_ECUDA. */
+sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma, const void *const *deltax,
+                          const void *const *deltay, void *const *fx, void *const *fy, sg_batch **out);
+
+/* Enqueue the whole batch on `stream` (one graph launch). */
+sg_status sg_batch_launch(sg_batch *batch, void *stream);
+
+/* Release the batch's graph and workspaces (synchronises the device). NULL is a no-op. */
+sg_status sg_batch_destroy(sg_batch *batch);
+
+/* ------------------------------------------------------------------------
  * Request server (continuous batching on one GPU; not in the paper).
  *
  * sg_submit queues a solve (a plan plus caller-owned device buffers, as for

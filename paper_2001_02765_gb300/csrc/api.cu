@@ -320,7 +320,10 @@ void plan_free(sg_plan *plan)
         delete plan->timing;
     }
     if (plan->pp) {
-        for (int k = 0; k < plan->npatches; ++k) cudaFree(plan->pp[k].spectra);
+        for (int k = 0; k < plan->npatches; ++k) {
+            cudaFree(plan->pp[k].spectra);
+            cudaFree(plan->pp[k].phase);
+        }
     }
     cudaFree(plan->twiddles);
     cudaFree(plan->cov_rects);
@@ -416,6 +419,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         }
         pdev[k] = d;
         st = dev_alloc(plan, &pp.spectra, 6 * (size_t)(d.px / 2 + 1) * (d.py / 2 + 1) * es);
+        if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL)
+            st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
     plan->ncov_total = (int)cov_all.size();
     if (st == SG_OK) st = dev_alloc(plan, &plan->cov_rects, (cov_all.empty() ? 1 : cov_all.size()) * sizeof(int4));
@@ -435,7 +440,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     int64_t wf = 0, wi = 0;
     for (int k = 0; k < gi.n; ++k) {
         const int64_t q = (int64_t)(pdev[k].px / 2 + 1) * pdev[k].ny * (int64_t)(2 * es);
-        if (3 * q > wf) wf = 3 * q;
+        // central slopes transform sigma only, plus the two edge columns (2 x py complex)
+        const int64_t f = g->slope_mode == SG_SLOPES_CENTRAL ? q + 2LL * pdev[k].py * (int64_t)(2 * es) : 3 * q;
+        if (f > wf) wf = f;
         if (2 * q > wi) wi = 2 * q;
     }
     plan->ws_fwd_bytes = wf;
@@ -492,6 +499,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     }
     plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
     if (st == SG_OK) st = sg_twiddles_build(plan);
+    if (st == SG_OK) st = sg_phase_build(plan);
     if (st == SG_OK) st = sg_tables_build(plan);
     if (st == SG_OK) {
         cudaError_t e = cudaDeviceSynchronize();

@@ -106,6 +106,7 @@ struct sg_patch_plan {
     sg_patch_dev d;
     // device buffers owned by the plan
     void *spectra;      // 6 planes [(px/2+1) x (py/2+1)] of T (quarter spectra, scaled)
+    void *phase;        // central-slope spectral factors (see fftconv.cu), NULL unless SG_SLOPES_CENTRAL
     // tile range of this patch in the tile list
     int tile_first, tile_count;
 };
@@ -200,6 +201,7 @@ struct sg_timing;
 sg_status sg_tables_build(sg_plan *plan);     // tables + spectra of every patch
 sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host_out, size_t n);
 sg_status sg_twiddles_build(sg_plan *plan);
+sg_status sg_phase_build(sg_plan *plan);     // central-slope factors of every patch
 sg_status sg_uniform_solve(sg_plan *plan, const struct sg_workspace *ws, int patch, const void *sigma, const void *dx,
                            const void *dy, void *fx, void *fy, cudaStream_t st);
 sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,

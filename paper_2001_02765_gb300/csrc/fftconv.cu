@@ -20,6 +20,19 @@
 //                  along x (two rows per complex FFT) and the first nx values
 //                  written to Fx, Fy. The spectra already carry G / (Px Py).
 // Every transform is the shared-memory Stockham FFT of fft.cuh.
+//
+// Central slopes. When deltax, deltay are central differences of sigma with
+// zero outside the patch, their transforms follow from sigma's exactly: along
+// x the stencil (s[i+1] - s[i-1]) / 2h applied to the zero-padded row has the
+// transform i sin(2 pi k / P) / h times sigma's, except that it also puts
+// s[0] / 2h at i = -1 and -s[nx-1] / 2h at i = nx, outside the patch, whose
+// transforms are removed again:
+//   deltax^(kx, ky) = i csin(kx) S - e^{+2 pi i kx/Px}/2h C0(ky) + e^{-2 pi i nx kx/Px}/2h C1(ky)
+//   deltay^(kx, ky) = i rsin(ky) S - e^{+2 pi i ky/Py}/2h R0(kx) + e^{-2 pi i ny ky/Py}/2h R1(kx)
+// with S = sigma^(kx, ky), C0 / C1 the y-transforms of sigma's first / last
+// column (k_edge_cols), R0 / R1 the x-transforms of its first / last row (the
+// column pass reads them from its own input). So only sigma is transformed:
+// one row field and one forward column transform instead of three.
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -220,6 +233,109 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict
     }
 }
 
+// y-transforms of sigma's first and last columns, packed as z = c0 + i c1:
+// edge[k] = C0(k), edge[PY + k] = C1(k), k < PY.
+template <typename T, int PY, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_edge_cols(const T *__restrict__ sigma, int nx, int ny, cplx_t<T> *__restrict__ edge,
+                                                       const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    for (int j = threadIdx.x; j < PY; j += THREADS) {
+        const T a = j < ny ? sigma[(int64_t)j * nx] : (T)0;
+        const T b = j < ny ? sigma[(int64_t)j * nx + nx - 1] : (T)0;
+        buf[spad<C>(j)] = cmake<C>(a, b);
+    }
+    __syncthreads();
+    fft_batch<C, PY, 1, THREADS, false>(buf, tw);
+    const T half = (T)0.5;
+    for (int k = threadIdx.x; k < PY; k += THREADS) {
+        const C z = buf[spad<C>(k)];
+        const C w = buf[spad<C>((PY - k) & (PY - 1))];
+        edge[k] = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
+        edge[PY + k] = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
+    }
+}
+
+// Column pass for central slopes: one forward transform (sigma), the slope
+// spectra formed per bin (see the header comment), two inverse transforms.
+template <typename T, int PY, int CB, int THREADS>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv_central(
+    const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv, const T *__restrict__ spec,
+    const cplx_t<T> *__restrict__ edge, const T *__restrict__ phase, int ny, int qx, const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    __shared__ C rows[CB][2];  // R0, R1 of each column
+    constexpr int EPT = CB * PY / THREADS;
+    constexpr int QY = PY / 2 + 1;
+    const int kx0 = blockIdx.x * CB;
+    const int64_t qplane = (int64_t)qx * QY;
+    const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
+    const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
+
+    for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+        const int c = e / PY, j = e % PY;
+        const int kx = kx0 + c;
+        buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    if (threadIdx.x < CB) {
+        rows[threadIdx.x][0] = buf[spad<C>(threadIdx.x * PY)];
+        rows[threadIdx.x][1] = buf[spad<C>(threadIdx.x * PY + ny - 1)];
+    }
+    __syncthreads();
+    fft_batch<C, PY, CB, THREADS, false>(buf, tw);
+
+    C accx[EPT], accy[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        const int e = threadIdx.x + q * THREADS;
+        const int c = e / PY, ky = e % PY;
+        const int kx = kx0 + c;
+        accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+        if (kx >= qx) continue;
+        const bool lower = ky <= PY / 2;
+        const int kq = lower ? ky : PY - ky;
+        const T sg = lower ? (T)1 : (T)-1;
+        const int64_t si = (int64_t)kx * QY + kq;
+        const C S = buf[spad<C>(e)];
+        // slope spectra
+        const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
+        const C e1 = cmake<C>(__ldg(&ce1[2 * kx]), __ldg(&ce1[2 * kx + 1]));
+        const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
+        const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
+        const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
+        const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
+        const C X = csub(cadd(cmake<C>(-cs * S.y, cs * S.x), cmul(e2, c1)), cmul(e1, c0));
+        const C Y = csub(cadd(cmake<C>(-rs * S.y, rs * S.x), cmul(f2, rows[c][1])), cmul(f1, rows[c][0]));
+        const T a = __ldg(&spec[0 * qplane + si]);
+        const T b = __ldg(&spec[1 * qplane + si]);
+        const T cc = sg * __ldg(&spec[2 * qplane + si]);
+        const T d = sg * __ldg(&spec[3 * qplane + si]);
+        const T ee = __ldg(&spec[4 * qplane + si]);
+        const T ff = sg * __ldg(&spec[5 * qplane + si]);
+        accx[q] = cmake<C>(-a * S.y + b * X.x + cc * Y.x, a * S.x + b * X.y + cc * Y.y);
+        accy[q] = cmake<C>(-d * S.y + ee * Y.x + ff * X.x, d * S.x + ee * Y.y + ff * X.y);
+    }
+    __syncthreads();
+
+    for (int o = 0; o < 2; ++o) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
+        __syncthreads();
+        fft_batch<C, PY, CB, THREADS, true>(buf, tw);
+        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+            const int c = e / PY, j = e % PY;
+            const int kx = kx0 + c;
+            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = buf[spad<C>(e)];
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ launch shapes --
 
 constexpr int row_nb(int px) { return px >= 4096 ? 2 : (4096 / px < 2 ? 2 : 4096 / px); }
@@ -264,6 +380,33 @@ sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny,
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((qx + CB - 1) / CB);
     kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, ny, qx, nf, tw);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+template <typename T, int PY>
+sg_status launch_cols_central(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge, const T *phase,
+                              int ny, int qx, const cplx_t<T> *tw, cudaStream_t st)
+{
+    constexpr int CB = col_cb(PY);
+    constexpr int THREADS = col_threads(PY);
+    const size_t smem = (size_t)spad_size<cplx_t<T>>(CB * PY) * sizeof(cplx_t<T>);
+    auto kern = k_col_conv_central<T, PY, CB, THREADS>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((qx + CB - 1) / CB);
+    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, edge, phase, ny, qx, tw);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+template <typename T, int PY>
+sg_status launch_edge_cols(const T *sigma, int nx, int ny, cplx_t<T> *edge, const cplx_t<T> *tw, cudaStream_t st)
+{
+    constexpr int THREADS = PY / 8 >= 64 ? PY / 8 : 64;
+    const size_t smem = (size_t)spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
+    auto kern = k_edge_cols<T, PY, THREADS>;
+    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<1, THREADS, smem, st>>>(sigma, nx, ny, edge, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -315,11 +458,22 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     const C *twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.px)]);
     const C *twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.py)]);
     T *ox = (T *)fx + off, *oy = (T *)fy + off;
+    const bool central = src.mode == SG_SLOPES_CENTRAL && pp.phase;
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
-    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_fwd<T, PP>(src, wf, nf, twx, st))));
+    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_fwd<T, PP>(src, wf, central ? 1 : nf, twx, st))));
+    if (central) {
+        C *edge = wf + (int64_t)qx * d.ny;  // after sigma's row transforms
+        SG_PAD_SWITCH(d.py, SG_TRY((launch_edge_cols<T, PP>(src.sigma, d.nx, d.ny, edge, twy, st))));
+    }
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
-    SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, st))));
+    if (central) {
+        const C *edge = wf + (int64_t)qx * d.ny;
+        SG_PAD_SWITCH(d.py, SG_TRY((launch_cols_central<T, PP>(wf, wi, (const T *)pp.spectra, edge,
+                                                                (const T *)pp.phase, d.ny, qx, twy, st))));
+    } else {
+        SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, st))));
+    }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
     SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, oy, d.nx, d.ny, twx, st))));

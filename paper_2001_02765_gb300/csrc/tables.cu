@@ -258,6 +258,49 @@ sg_status sg_tables_build(sg_plan *plan)
     return SG_OK;
 }
 
+// Central-slope factors of a patch (see fftconv.cu), in the plan precision:
+//   csin[kx] = sin(2 pi kx / Px) / h,  ce1[kx] = e^{+2 pi i kx / Px} / 2h,  ce2[kx] = e^{-2 pi i nx kx / Px} / 2h
+// for kx in [0, Px/2], and the same along y for ky in [0, Py) (rsin, re1, re2).
+// Layout: csin[qx] ce1[qx] ce2[qx] rsin[py] re1[py] re2[py], complex entries as (re, im).
+template <typename T>
+__global__ void k_phase(T *out, int nx, int ny, int px, int py, double h)
+{
+    const int qx = px / 2 + 1;
+    T *csin = out, *ce1 = out + qx, *ce2 = out + 3 * qx;
+    T *rsin = out + 5 * qx, *re1 = rsin + py, *re2 = rsin + 3 * py;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < qx + py; k += gridDim.x * blockDim.x) {
+        const bool col = k < qx;
+        const int kk = col ? k : k - qx;
+        const int P = col ? px : py, n = col ? nx : ny;
+        double s1, c1, s2, c2;
+        sincospi(2.0 * (double)kk / (double)P, &s1, &c1);
+        // e^{-2 pi i n k / P}: reduce n k mod P first so the argument stays small
+        sincospi(-2.0 * (double)(((long long)n * kk) % P) / (double)P, &s2, &c2);
+        T *sn = col ? csin : rsin, *e1 = col ? ce1 : re1, *e2 = col ? ce2 : re2;
+        sn[kk] = (T)(s1 / h);
+        e1[2 * kk] = (T)(c1 / (2.0 * h));
+        e1[2 * kk + 1] = (T)(s1 / (2.0 * h));
+        e2[2 * kk] = (T)(c2 / (2.0 * h));
+        e2[2 * kk + 1] = (T)(s2 / (2.0 * h));
+    }
+}
+
+sg_status sg_phase_build(sg_plan *plan)
+{
+    for (int p = 0; p < plan->npatches; ++p) {
+        sg_patch_plan &pp = plan->pp[p];
+        if (!pp.phase) continue;
+        const sg_patch_dev &d = pp.d;
+        const int n = d.px / 2 + 1 + d.py;
+        if (plan->prec == SG_FP64)
+            k_phase<double><<<(n + 255) / 256, 256>>>((double *)pp.phase, d.nx, d.ny, d.px, d.py, d.h);
+        else
+            k_phase<float><<<(n + 255) / 256, 256>>>((float *)pp.phase, d.nx, d.ny, d.px, d.py, d.h);
+        SG_CUDA_TRY(cudaGetLastError());
+    }
+    return SG_OK;
+}
+
 sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host_out, size_t n)
 {
     if (!plan || !host_out || patch < 0 || patch >= plan->npatches || which < 0 || which > 5) return SG_EINVAL;

@@ -74,6 +74,11 @@ _SIGNATURES = {
     "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "sg_direct_force_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                       ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                       ctypes.POINTER(_VP)]),
+    "sg_batch_launch": (ctypes.c_int, [_VP, _VP]),
+    "sg_batch_destroy": (ctypes.c_int, [_VP]),
     "sg_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
     "sg_server_destroy": (ctypes.c_int, [_VP]),
     "sg_submit": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
@@ -206,6 +211,25 @@ def sg_direct_force_static(nx, ny, h, G, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_p
     """Raw device pointers (ints) of float32 arrays; allocation-free uniform direct sum."""
     _check(load().sg_direct_force_static(int(nx), int(ny), float(h), float(G), sigma_ptr, dx_ptr or None,
                                          dy_ptr or None, fx_ptr, fy_ptr, stream_ptr or None), "sg_direct_force_static")
+
+
+def sg_batch_create(plan_handles, sigma_ptrs, dx_ptrs, dy_ptrs, fx_ptrs, fy_ptrs):
+    """Bind n solves (raw device pointers; dx/dy entries 0 where unused) into one graph."""
+    n = len(plan_handles)
+    arr = lambda v: (_VP * n)(*[x or None for x in v])
+    h = _VP()
+    _check(load().sg_batch_create(n, arr(plan_handles), arr(sigma_ptrs), arr(dx_ptrs), arr(dy_ptrs), arr(fx_ptrs),
+                                  arr(fy_ptrs), ctypes.byref(h)), "sg_batch_create")
+    return h.value
+
+
+def sg_batch_launch(batch, stream_ptr=0):
+    _check(load().sg_batch_launch(batch, stream_ptr or None), "sg_batch_launch")
+
+
+def sg_batch_destroy(batch):
+    if batch:
+        _check(load().sg_batch_destroy(batch), "sg_batch_destroy")
 
 
 def sg_server_create(hbm_budget=0, max_inflight=8):

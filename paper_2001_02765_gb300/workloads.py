@@ -95,27 +95,31 @@ def kuzmin_sigma(X, Y, a, M=1.0):
 
 
 def spiral_sigma(X, Y, a, amp, pitch_deg=15.0, M=1.0):
-    """Kuzmin(a) modulated by a two-armed logarithmic spiral, with its gradient."""
+    """Kuzmin(a) modulated by a two-armed logarithmic spiral, with its gradient.
+
+    The spiral phase is undefined at R = 0; a cell centred there (odd grids)
+    gets the unmodulated Kuzmin value and gradient."""
     s, sx, sy = kuzmin_sigma(X, Y, a, M)
     R2 = X * X + Y * Y
-    R = np.sqrt(R2)
+    origin = R2 == 0.0
+    R2s = np.where(origin, 1.0, R2)
     th = np.arctan2(Y, X)
     k = 1.0 / math.tan(math.radians(pitch_deg))
-    ph = 2.0 * th - k * np.log(R)
-    c = np.cos(ph)
-    sn = np.sin(ph)
+    ph = 2.0 * th - k * 0.5 * np.log(R2s)
+    c = np.where(origin, 0.0, np.cos(ph))
+    sn = np.where(origin, 0.0, np.sin(ph))
     # d(ph)/dx = 2 d(theta)/dx - k x / R^2 = (-2 y - k x) / R^2 ; d(ph)/dy = (2 x - k y) / R^2
-    dphx = (-2.0 * Y - k * X) / R2
-    dphy = (2.0 * X - k * Y) / R2
+    dphx = (-2.0 * Y - k * X) / R2s
+    dphy = (2.0 * X - k * Y) / R2s
     m = 1.0 + amp * c
     return s * m, sx * m - s * amp * sn * dphx, sy * m - s * amp * sn * dphy
 
 
 def exponential_sigma(X, Y, r0):
-    """exp(-R / r0) and its gradient (undefined at R = 0, never a cell centre here)."""
+    """exp(-R / r0) and its gradient (the cusp at R = 0 gets gradient 0)."""
     R = np.hypot(X, Y)
     s = np.exp(-R / r0)
-    g = -s / (r0 * R)
+    g = np.where(R > 0.0, -s / (r0 * np.where(R > 0.0, R, 1.0)), 0.0)
     return s, g * X, g * Y
 
 
