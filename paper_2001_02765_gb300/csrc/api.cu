@@ -273,7 +273,7 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
         const int px = sg_pad_length(g->patches[k].nx), py = sg_pad_length(g->patches[k].ny);
         if (px > s.max_pad) s.max_pad = px;
         if (py > s.max_pad) s.max_pad = py;
-        s.spectra += 6LL * (px / 2 + 1) * (py / 2 + 1) * (int64_t)es;
+        s.spectra += 6LL * (px / 2 + 1) * sg_spec_stride(py) * (int64_t)es;
         const int64_t w = 5LL * (px / 2 + 1) * g->patches[k].ny * (int64_t)(2 * es);
         if (w > work) work = w;
     }
@@ -418,7 +418,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             pp.tile_count = tcount[k];
         }
         pdev[k] = d;
-        st = dev_alloc(plan, &pp.spectra, 6 * (size_t)(d.px / 2 + 1) * (d.py / 2 + 1) * es);
+        st = dev_alloc(plan, &pp.spectra, 6 * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
         if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL)
             st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
@@ -544,7 +544,12 @@ static sg_status ws_alloc_one(void **p, int64_t bytes, cudaStream_t st, bool asy
 
 void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async)
 {
-    void *bufs[5] = {ws->work_fwd, ws->work_inv, ws->sfield, ws->tile_w, ws->partial};
+    if (ws->aux) cudaStreamDestroy(ws->aux);
+    if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
+    if (ws->ev_join) cudaEventDestroy(ws->ev_join);
+    ws->aux = nullptr;
+    ws->ev_fork = ws->ev_join = nullptr;
+    void *bufs[6] = {ws->work_fwd, ws->work_inv, ws->sfield, ws->tile_w, ws->partial, ws->err};
     for (void *b : bufs) {
         if (!b) continue;
         if (async) cudaFreeAsync(b, st);
@@ -552,6 +557,7 @@ void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async)
     }
     ws->work_fwd = ws->work_inv = ws->sfield = ws->tile_w = nullptr;
     ws->partial = nullptr;
+    ws->err = nullptr;
 }
 
 sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t st, bool async)
@@ -562,6 +568,20 @@ sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t
     if (r == SG_OK) r = ws_alloc_one(&ws->sfield, plan->ws_sfield_bytes, st, async);
     if (r == SG_OK) r = ws_alloc_one(&ws->tile_w, plan->ws_tile_bytes, st, async);
     if (r == SG_OK) r = ws_alloc_one((void **)&ws->partial, plan->ws_partial_bytes, st, async);
+    if (r == SG_OK) r = ws_alloc_one((void **)&ws->err, 16, st, async);
+    if (r == SG_OK) {
+        cudaError_t e = async ? cudaMemsetAsync(ws->err, 0, 16, st) : cudaMemset(ws->err, 0, 16);
+        if (e != cudaSuccess) r = SG_ECUDA;
+    }
+    if (r == SG_OK && !async && plan->geom.slope_mode == SG_SLOPES_CENTRAL) {
+        // side stream for the edge-column transform of the central-slope path
+        if (cudaStreamCreateWithFlags(&ws->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            r = SG_ECUDA;
+        }
+    }
     if (r != SG_OK) sg_workspace_free(ws, st, async);
     return r;
 }
@@ -580,6 +600,20 @@ sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, 
     for (int k = 0; k < plan->npatches; ++k)
         SG_TRY(sg_uniform_solve(plan, ws, k, S, S + plane, S + 2 * plane, fx, fy, st));
     return sg_cross_solve(plan, ws, S, S + plane, S + 2 * plane, fx, fy, st);
+}
+
+// Reads and clears the device error word of the plan's workspace (synchronises).
+static sg_status check_device_error(sg_plan *plan)
+{
+    if (!plan->ws || !plan->ws->err) return SG_OK;
+    int e = 0;
+    SG_CUDA_TRY(cudaMemcpy(&e, plan->ws->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        SG_CUDA_TRY(cudaMemset(plan->ws->err, 0, sizeof(int)));
+        sg_set_last_error_message("a bounded wait for a bulk copy ran out in a kernel");
+        return SG_ETIMEOUT;
+    }
+    return SG_OK;
 }
 
 // --------------------------------------------------------------- the C ABI --
@@ -696,7 +730,7 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
     SG_CUDA_TRY(cudaMemcpyAsync(fx, out, bytes, cudaMemcpyDeviceToHost, st));
     SG_CUDA_TRY(cudaMemcpyAsync(fy, out + bytes, bytes, cudaMemcpyDeviceToHost, st));
     SG_CUDA_TRY(cudaStreamSynchronize(st));
-    return SG_OK;
+    return check_device_error(plan);
 }
 
 sg_status sg_plan_set_timing(sg_plan *plan, int enable)
@@ -728,7 +762,7 @@ sg_status sg_plan_get_timing(sg_plan *plan, double *ms, int n)
         SG_CUDA_TRY(cudaEventElapsedTime(&v, t->pool[b], t->pool[e]));
         ms[t->stage[k]] += v;
     }
-    return SG_OK;
+    return check_device_error(plan);
 }
 
 const char *sg_strerror(sg_status s)

@@ -105,7 +105,7 @@ struct sg_patch_plan {
     sg_patch geom;
     sg_patch_dev d;
     // device buffers owned by the plan
-    void *spectra;      // 6 planes [(px/2+1) x (py/2+1)] of T (quarter spectra, scaled)
+    void *spectra;      // 6 planes [(px/2+1) x sg_spec_stride(py)] of T (quarter spectra, scaled)
     void *phase;        // central-slope spectral factors (see fftconv.cu), NULL unless SG_SLOPES_CENTRAL
     // tile range of this patch in the tile list
     int tile_first, tile_count;
@@ -173,7 +173,12 @@ struct sg_workspace {
     void *sfield;           // AMR composite source fields, 3 x ncells of T
     void *tile_w;           // AMR corner weights, ntiles x SG_TILE_N x 4 of T
     double *partial;        // AMR split partial sums, nsplit x ntargets x 2 (nsplit > 1)
+    int *err;               // device error word: nonzero after a bounded wait in a kernel ran out
     struct sg_timing *timing;  // stage timers, or NULL
+    // optional side stream for independent work of one solve (fork/join by events);
+    // NULL runs that work on the solve's stream
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_join;
 };
 
 // Allocate / free a workspace for a plan. async: stream-ordered allocation on st.
@@ -215,6 +220,10 @@ static inline int sg_ilog2(int v)
     while ((1 << l) < v) ++l;
     return l;
 }
+
+// Row stride of the spectra planes: (Py/2 + 1) rounded up to 4 entries so that
+// every row starts on a 16-byte boundary (bulk copies need it).
+static inline __host__ __device__ int sg_spec_stride(int py) { return ((py / 2 + 1) + 3) & ~3; }
 
 static inline int sg_pad_length(int n)
 {

@@ -117,7 +117,10 @@ __device__ __forceinline__ void dft8(C *v)
     v[7] = csub(e3, w3);
 }
 
-template <typename C, int L, int NB, int THREADS, int NS, int R, bool INV>
+// IN_HALF: the first stage takes the inputs at logical positions >= L/2 as
+// zero without reading them (zero padding to at least twice the data length).
+// OUT_HALF: the last stage writes only the outputs at positions < L/2.
+template <typename C, int L, int NB, int THREADS, int NS, int R, bool INV, bool IN_HALF = false, bool OUT_HALF = false>
 __device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
 {
     constexpr int NBF = NB * (L / R);            // butterflies in the stage
@@ -129,7 +132,10 @@ __device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
         if (NBF % THREADS == 0 || b < NBF) {
             const int seq = b / (L / R), j = b % (L / R);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[p][r] = buf[spad<C>(seq * L + j + r * (L / R))];
+            for (int r = 0; r < R; ++r) {
+                if (IN_HALF && NS == 1 && r >= R / 2) v[p][r] = cmake<C>(0, 0);
+                else v[p][r] = buf[spad<C>(seq * L + j + r * (L / R))];
+            }
         }
     }
     __syncthreads();
@@ -161,28 +167,33 @@ __device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
             else dft2<C, INV>(v[p][0], v[p][1]);
             const int base = seq * L + (j / NS) * NS * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[spad<C>(base + r * NS)] = v[p][r];
+            for (int r = 0; r < R; ++r) {
+                if (OUT_HALF && NS * R == L && r >= R / 2) continue;  // position k + r NS >= L/2
+                buf[spad<C>(base + r * NS)] = v[p][r];
+            }
         }
     }
     __syncthreads();
 }
 
-template <typename C, int L, int NB, int THREADS, int NS, bool INV>
+template <typename C, int L, int NB, int THREADS, int NS, bool INV, bool IN_HALF, bool OUT_HALF>
 __device__ __forceinline__ void fft_stages(C *buf, const C *__restrict__ tw)
 {
     if constexpr (NS < L) {
         constexpr int REM = L / NS;
         constexpr int R = REM >= 8 ? 8 : REM;
-        fft_stage<C, L, NB, THREADS, NS, R, INV>(buf, tw);
-        fft_stages<C, L, NB, THREADS, NS * R, INV>(buf, tw);
+        fft_stage<C, L, NB, THREADS, NS, R, INV, IN_HALF, OUT_HALF>(buf, tw);
+        fft_stages<C, L, NB, THREADS, NS * R, INV, IN_HALF, OUT_HALF>(buf, tw);
     }
 }
 
 // FFT of NB sequences of length L in shared memory by THREADS threads.
 // Must be called by every thread of the CTA (it synchronises). The caller
-// synchronises before the call so that the inputs are visible.
-template <typename C, int L, int NB, int THREADS, bool INV>
+// synchronises before the call so that the inputs are visible. With IN_HALF
+// the inputs at positions >= L/2 are taken as zero (and need not be written);
+// with OUT_HALF only the outputs at positions < L/2 are produced.
+template <typename C, int L, int NB, int THREADS, bool INV, bool IN_HALF = false, bool OUT_HALF = false>
 __device__ __forceinline__ void fft_batch(C *buf, const C *__restrict__ tw)
 {
-    fft_stages<C, L, NB, THREADS, 1, INV>(buf, tw);
+    fft_stages<C, L, NB, THREADS, 1, INV, IN_HALF, OUT_HALF>(buf, tw);
 }

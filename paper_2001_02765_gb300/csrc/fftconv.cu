@@ -35,6 +35,7 @@
 // one row field and one forward column transform instead of three.
 #include "common.cuh"
 #include "fft.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -93,16 +94,16 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T>
     const int j0 = blockIdx.x * RB;
     const int ny = src.ny;
 
-    // two rows per complex sequence: z = row(2s) + i row(2s+1)
-    for (int e = threadIdx.x; e < NB * PX; e += THREADS) {
-        const int s = e / PX, i = e % PX;
+    // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
+    for (int e = threadIdx.x; e < NB * (PX / 2); e += THREADS) {
+        const int s = e / (PX / 2), i = e % (PX / 2);
         const int ja = j0 + 2 * s;
         const T a = field_value(src, f, ja, i);
         const T b = field_value(src, f, ja + 1, i);
-        buf[spad<C>(e)] = cmake<C>(a, b);
+        buf[spad<C>(s * PX + i)] = cmake<C>(a, b);
     }
     __syncthreads();
-    fft_batch<C, PX, NB, THREADS, false>(buf, tw);
+    fft_batch<C, PX, NB, THREADS, false, true>(buf, tw);
 
     // unpack: A[k] = (Z[k] + conj Z[-k]) / 2, B[k] = (Z[k] - conj Z[-k]) / 2i
     const T half = (T)0.5;
@@ -120,6 +121,43 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T>
     }
 }
 
+// Shared-memory layout of the column kernels: the padded FFT buffer, then the
+// kernel spectra of the CTA's columns, [CB][6][sg_spec_stride(PY)] of T, which
+// one thread fetches with 1-D bulk copies (TMA) at kernel start so that they
+// arrive while the forward transform runs.
+template <typename T, int PY, int CB>
+__host__ __device__ constexpr int col_buf_bytes() { return (spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15; }
+template <typename T, int PY, int CB>
+__host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * 6 * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
+
+template <typename T, int PY, int CB>
+__device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec, int kx0, int qx, uint64_t *bar)
+{
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    const int ncol = qx - kx0 < CB ? qx - kx0 : CB;
+    const int64_t qplane = (int64_t)qx * QS;
+    mbar_arrive_expect_tx(bar, (uint32_t)(ncol * 6 * QS * sizeof(T)));
+    for (int c = 0; c < ncol; ++c)
+        for (int p = 0; p < 6; ++p)
+            bulk_copy_g2s(ssp + (c * 6 + p) * QS, spec + p * qplane + (int64_t)(kx0 + c) * QS, QS * sizeof(T), bar);
+}
+
+// Bounded wait for the spectra; on timeout records the error, gives the copies
+// one more bounded wait and tells the CTA to return (uniformly).
+__device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err)
+{
+    const bool ok = mbar_wait_bounded(bar, 0, SG_MBAR_MAX_TRIES);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(bar, 0, SG_MBAR_MAX_TRIES);
+        }
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
 // resident CTAs per SM asked of the register allocator (spill-free choices)
 template <typename T, int PY>
 constexpr int col_min_blocks() { return sizeof(T) == 4 ? (PY == 2048 ? 3 : (PY == 4096 ? 1 : 2)) : 1; }
@@ -127,15 +165,19 @@ constexpr int col_min_blocks() { return sizeof(T) == 4 ? (PY == 2048 ? 3 : (PY =
 template <typename T, int PY, int CB, int THREADS>
 __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv(const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv,
                                                       const T *__restrict__ spec, int ny, int qx, int nf,
-                                                      const cplx_t<T> *__restrict__ tw)
+                                                      const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
+    __shared__ uint64_t bar;
     constexpr int EPT = CB * PY / THREADS;
-    constexpr int QY = PY / 2 + 1;
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int kx0 = blockIdx.x * CB;
-    const int64_t qplane = (int64_t)qx * QY;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
 
     C accx[EPT], accy[EPT];
 #pragma unroll
@@ -145,10 +187,12 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
         for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
             const int c = e / PY, j = e % PY;
             const int kx = kx0 + c;
+            if (j >= PY / 2) continue;  // taken as zero by the first stage
             buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
         }
         __syncthreads();
-        fft_batch<C, PY, CB, THREADS, false>(buf, tw);
+        fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
+        if (f == 0 && !spectra_ready(&bar, err)) return;
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             const int e = threadIdx.x + q * THREADS;
@@ -158,21 +202,21 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
             const bool lower = ky <= PY / 2;
             const int kq = lower ? ky : PY - ky;
             const T sg = lower ? (T)1 : (T)-1;
-            const int64_t si = (int64_t)kx * QY + kq;
+            const T *sp = ssp + c * 6 * QS + kq;
             const C X = buf[spad<C>(e)];
             if (f == 0) {
-                const T a = __ldg(&spec[0 * qplane + si]);
-                const T d = sg * __ldg(&spec[3 * qplane + si]);
+                const T a = sp[0 * QS];
+                const T d = sg * sp[3 * QS];
                 accx[q] = cmake<C>(-a * X.y, a * X.x);
                 accy[q] = cmake<C>(-d * X.y, d * X.x);
             } else if (f == 1) {
-                const T b = __ldg(&spec[1 * qplane + si]);
-                const T ff = sg * __ldg(&spec[5 * qplane + si]);
+                const T b = sp[1 * QS];
+                const T ff = sg * sp[5 * QS];
                 accx[q] = cmake<C>(accx[q].x + b * X.x, accx[q].y + b * X.y);
                 accy[q] = cmake<C>(accy[q].x + ff * X.x, accy[q].y + ff * X.y);
             } else {
-                const T cc = sg * __ldg(&spec[2 * qplane + si]);
-                const T ee = __ldg(&spec[4 * qplane + si]);
+                const T cc = sg * sp[2 * QS];
+                const T ee = sp[4 * QS];
                 accx[q] = cmake<C>(accx[q].x + cc * X.x, accx[q].y + cc * X.y);
                 accy[q] = cmake<C>(accy[q].x + ee * X.x, accy[q].y + ee * X.y);
             }
@@ -184,7 +228,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
 #pragma unroll
         for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
         __syncthreads();
-        fft_batch<C, PY, CB, THREADS, true>(buf, tw);
+        fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
         for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
             const int c = e / PY, j = e % PY;
             const int kx = kx0 + c;
@@ -222,7 +266,7 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict
         if (k > 0 && k < PX / 2) buf[spad<C>(s * PX + PX - k)] = cmake<C>(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
     }
     __syncthreads();
-    fft_batch<C, PX, NB, THREADS, true>(buf, tw);
+    fft_batch<C, PX, NB, THREADS, true, false, true>(buf, tw);
     for (int e = threadIdx.x; e < NB * PX; e += THREADS) {
         const int s = e / PX, i = e % PX;
         if (i >= nx) continue;
@@ -242,13 +286,13 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(const T *__restrict__ sig
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    for (int j = threadIdx.x; j < PY; j += THREADS) {
+    for (int j = threadIdx.x; j < PY / 2; j += THREADS) {  // positions >= PY/2 are zero
         const T a = j < ny ? sigma[(int64_t)j * nx] : (T)0;
         const T b = j < ny ? sigma[(int64_t)j * nx + nx - 1] : (T)0;
         buf[spad<C>(j)] = cmake<C>(a, b);
     }
     __syncthreads();
-    fft_batch<C, PY, 1, THREADS, false>(buf, tw);
+    fft_batch<C, PY, 1, THREADS, false, true>(buf, tw);
     const T half = (T)0.5;
     for (int k = threadIdx.x; k < PY; k += THREADS) {
         const C z = buf[spad<C>(k)];
@@ -263,22 +307,28 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(const T *__restrict__ sig
 template <typename T, int PY, int CB, int THREADS>
 __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv_central(
     const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv, const T *__restrict__ spec,
-    const cplx_t<T> *__restrict__ edge, const T *__restrict__ phase, int ny, int qx, const cplx_t<T> *__restrict__ tw)
+    const cplx_t<T> *__restrict__ edge, const T *__restrict__ phase, int ny, int qx, const cplx_t<T> *__restrict__ tw,
+    int *err)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
+    __shared__ uint64_t bar;
     __shared__ C rows[CB][2];  // R0, R1 of each column
     constexpr int EPT = CB * PY / THREADS;
-    constexpr int QY = PY / 2 + 1;
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int kx0 = blockIdx.x * CB;
-    const int64_t qplane = (int64_t)qx * QY;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
     const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
     const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
 
     for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
         const int c = e / PY, j = e % PY;
         const int kx = kx0 + c;
+        if (j >= PY / 2) continue;  // taken as zero by the first stage
         buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
     }
     __syncthreads();
@@ -287,7 +337,8 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
         rows[threadIdx.x][1] = buf[spad<C>(threadIdx.x * PY + ny - 1)];
     }
     __syncthreads();
-    fft_batch<C, PY, CB, THREADS, false>(buf, tw);
+    fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
+    if (!spectra_ready(&bar, err)) return;
 
     C accx[EPT], accy[EPT];
 #pragma unroll
@@ -300,7 +351,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
         const bool lower = ky <= PY / 2;
         const int kq = lower ? ky : PY - ky;
         const T sg = lower ? (T)1 : (T)-1;
-        const int64_t si = (int64_t)kx * QY + kq;
+        const T *sp = ssp + c * 6 * QS + kq;
         const C S = buf[spad<C>(e)];
         // slope spectra
         const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
@@ -311,12 +362,12 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
         const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
         const C X = csub(cadd(cmake<C>(-cs * S.y, cs * S.x), cmul(e2, c1)), cmul(e1, c0));
         const C Y = csub(cadd(cmake<C>(-rs * S.y, rs * S.x), cmul(f2, rows[c][1])), cmul(f1, rows[c][0]));
-        const T a = __ldg(&spec[0 * qplane + si]);
-        const T b = __ldg(&spec[1 * qplane + si]);
-        const T cc = sg * __ldg(&spec[2 * qplane + si]);
-        const T d = sg * __ldg(&spec[3 * qplane + si]);
-        const T ee = __ldg(&spec[4 * qplane + si]);
-        const T ff = sg * __ldg(&spec[5 * qplane + si]);
+        const T a = sp[0 * QS];
+        const T b = sp[1 * QS];
+        const T cc = sg * sp[2 * QS];
+        const T d = sg * sp[3 * QS];
+        const T ee = sp[4 * QS];
+        const T ff = sg * sp[5 * QS];
         accx[q] = cmake<C>(-a * S.y + b * X.x + cc * Y.x, a * S.x + b * X.y + cc * Y.y);
         accy[q] = cmake<C>(-d * S.y + ee * Y.x + ff * X.x, d * S.x + ee * Y.y + ff * X.y);
     }
@@ -326,7 +377,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
 #pragma unroll
         for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
         __syncthreads();
-        fft_batch<C, PY, CB, THREADS, true>(buf, tw);
+        fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
         for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
             const int c = e / PY, j = e % PY;
             const int kx = kx0 + c;
@@ -338,7 +389,9 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
 
 // ------------------------------------------------------------ launch shapes --
 
+// row sequences (two rows each) per CTA: forward and inverse passes measured separately
 constexpr int row_nb(int px) { return px >= 4096 ? 2 : (4096 / px < 2 ? 2 : 4096 / px); }
+constexpr int row_nb_inv(int px) { return px >= 4096 ? 2 : (px == 2048 ? 4 : 4096 / px); }
 constexpr int col_cb(int py) { return py >= 2048 ? 1 : 2048 / py; }
 constexpr int col_threads(int py) { return col_cb(py) * py / 8; }
 constexpr int ROW_THREADS = 256;
@@ -359,7 +412,7 @@ sg_status launch_rows_fwd(const field_src<T> &src, cplx_t<T> *work, int nf, cons
 template <typename T, int PX>
 sg_status launch_rows_inv(const cplx_t<T> *work, T *fx, T *fy, int nx, int ny, const cplx_t<T> *tw, cudaStream_t st)
 {
-    constexpr int NB = row_nb(PX);
+    constexpr int NB = row_nb_inv(PX);
     const size_t smem = (size_t)spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
     auto kern = k_row_inv<T, PX, NB, ROW_THREADS>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -371,30 +424,30 @@ sg_status launch_rows_inv(const cplx_t<T> *work, T *fx, T *fy, int nx, int ny, c
 
 template <typename T, int PY>
 sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf, const cplx_t<T> *tw,
-                      cudaStream_t st)
+                      int *err, cudaStream_t st)
 {
     constexpr int CB = col_cb(PY);
     constexpr int THREADS = col_threads(PY);
-    const size_t smem = (size_t)spad_size<cplx_t<T>>(CB * PY) * sizeof(cplx_t<T>);
+    const size_t smem = (size_t)col_smem_bytes<T, PY, CB>();
     auto kern = k_col_conv<T, PY, CB, THREADS>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((qx + CB - 1) / CB);
-    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, ny, qx, nf, tw);
+    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, ny, qx, nf, tw, err);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
 template <typename T, int PY>
 sg_status launch_cols_central(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge, const T *phase,
-                              int ny, int qx, const cplx_t<T> *tw, cudaStream_t st)
+                              int ny, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st)
 {
     constexpr int CB = col_cb(PY);
     constexpr int THREADS = col_threads(PY);
-    const size_t smem = (size_t)spad_size<cplx_t<T>>(CB * PY) * sizeof(cplx_t<T>);
+    const size_t smem = (size_t)col_smem_bytes<T, PY, CB>();
     auto kern = k_col_conv_central<T, PY, CB, THREADS>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((qx + CB - 1) / CB);
-    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, edge, phase, ny, qx, tw);
+    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, edge, phase, ny, qx, tw, err);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -460,19 +513,28 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     T *ox = (T *)fx + off, *oy = (T *)fy + off;
     const bool central = src.mode == SG_SLOPES_CENTRAL && pp.phase;
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
-    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_fwd<T, PP>(src, wf, central ? 1 : nf, twx, st))));
     if (central) {
+        // the edge-column transform is independent of the row pass: run it beside it
         C *edge = wf + (int64_t)qx * d.ny;  // after sigma's row transforms
-        SG_PAD_SWITCH(d.py, SG_TRY((launch_edge_cols<T, PP>(src.sigma, d.nx, d.ny, edge, twy, st))));
+        cudaStream_t es = st;
+        if (ws->aux) {
+            SG_CUDA_TRY(cudaEventRecord(ws->ev_fork, st));
+            SG_CUDA_TRY(cudaStreamWaitEvent(ws->aux, ws->ev_fork, 0));
+            es = ws->aux;
+        }
+        SG_PAD_SWITCH(d.py, SG_TRY((launch_edge_cols<T, PP>(src.sigma, d.nx, d.ny, edge, twy, es))));
+        if (ws->aux) SG_CUDA_TRY(cudaEventRecord(ws->ev_join, ws->aux));
     }
+    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_fwd<T, PP>(src, wf, central ? 1 : nf, twx, st))));
+    if (central && ws->aux) SG_CUDA_TRY(cudaStreamWaitEvent(st, ws->ev_join, 0));
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
     if (central) {
         const C *edge = wf + (int64_t)qx * d.ny;
         SG_PAD_SWITCH(d.py, SG_TRY((launch_cols_central<T, PP>(wf, wi, (const T *)pp.spectra, edge,
-                                                                (const T *)pp.phase, d.ny, qx, twy, st))));
+                                                                (const T *)pp.phase, d.ny, qx, twy, ws->err, st))));
     } else {
-        SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, st))));
+        SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, ws->err, st))));
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);

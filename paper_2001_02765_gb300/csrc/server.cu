@@ -110,9 +110,11 @@ bool start(sg_server *s, sg_request *r)
     sg_status a = SG_OK;
     {
         const sg_plan *p = r->plan;
-        int64_t sizes[5] = {p->ws_fwd_bytes, p->ws_inv_bytes, p->ws_sfield_bytes, p->ws_tile_bytes, p->ws_partial_bytes};
-        void **dst[5] = {&r->ws.work_fwd, &r->ws.work_inv, &r->ws.sfield, &r->ws.tile_w, (void **)&r->ws.partial};
-        for (int k = 0; k < 5 && a == SG_OK; ++k) {
+        int64_t sizes[6] = {p->ws_fwd_bytes, p->ws_inv_bytes, p->ws_sfield_bytes, p->ws_tile_bytes,
+                            p->ws_partial_bytes, 16};
+        void **dst[6] = {&r->ws.work_fwd, &r->ws.work_inv, &r->ws.sfield, &r->ws.tile_w, (void **)&r->ws.partial,
+                         (void **)&r->ws.err};
+        for (int k = 0; k < 6 && a == SG_OK; ++k) {
             if (sizes[k] <= 0) continue;
             if (cudaMallocFromPoolAsync(dst[k], (size_t)sizes[k], s->pool, st) != cudaSuccess) {
                 cudaGetLastError();
@@ -121,6 +123,7 @@ bool start(sg_server *s, sg_request *r)
             }
         }
     }
+    if (a == SG_OK && cudaMemsetAsync(r->ws.err, 0, 16, st) != cudaSuccess) a = SG_ECUDA;
     if (a != SG_OK) {
         sg_workspace_free(&r->ws, st, true);
         return false;

@@ -138,10 +138,14 @@ __global__ void __launch_bounds__(L / 8 >= 64 ? L / 8 : 64) k_fft_lines(double2 
 template <typename T>
 __global__ void k_extract_spectra(const double2 *z, T *planes, int px, int py, double scale0, double scale1)
 {
-    const int qx = px / 2 + 1, qy = py / 2 + 1;
-    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
+    const int qx = px / 2 + 1, qy = py / 2 + 1, qs = sg_spec_stride(py);
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qs;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(e / qy), ky = (int)(e % qy);  // planes are [kx][ky]
+        const int kx = (int)(e / qs), ky = (int)(e % qs);  // planes are [kx][ky], row stride qs
+        if (ky >= qy) {
+            for (int c = 0; c < 6; ++c) planes[c * qplane + e] = (T)0;
+            continue;
+        }
         const int64_t src = (int64_t)ky * px + kx;          // z is [ky][kx]
         const double2 z0 = z[src], z1 = z[plane + src], z2 = z[2 * plane + src];
         // z0 = Kx0^ + i Ky0^ = i a + i (i d) = -d + i a
