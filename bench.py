@@ -40,12 +40,17 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 def _peaks():
+    """(HBM GB/s, its source, FP32 non-tensor TFLOP/s, its source). The FP32
+    peak is derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x the maximum SM
+    clock recorded in MEASURED_PEAKS.json (2070 MHz on this pool)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        hbm, src = float(p["hbm_gbs"]), "measured"
+        mhz = float(p.get("sm_max_mhz", 2070.0))
     except Exception:
-        return 6800.0, "fallback"
+        hbm, src, mhz = 6800.0, "fallback", 2070.0
+    return hbm, src, 152 * 128 * 2 * mhz * 1e6 / 1e12, "derived: 152 SM x 128 lanes x 2 x %.0f MHz" % mhz
 
 
 class ClockSampler:
@@ -552,10 +557,13 @@ def run_gpu(args):
     # roofline of the dominant kernel
     stage_mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(stage_mean, key=stage_mean.get)
-    peak, peak_kind = _peaks()
+    hbm_peak, hbm_src, fp32_peak, fp32_src = _peaks()
     info = plan.info
     alg = algorithmic_bytes(wl, info, dom)
-    achieved = alg / (stage_mean[dom] * 1e-3) / 1e9 if stage_mean[dom] > 0 else 0.0
+    flops = algorithmic_flops(wl, info, dom)
+    secs = stage_mean[dom] * 1e-3
+    tflops = flops / secs / 1e12 if secs > 0 else 0.0
+    gbs = alg / secs / 1e9 if secs > 0 else 0.0
     plan.close()
 
     if rank != 0:
@@ -570,9 +578,11 @@ def run_gpu(args):
         "fp64_plain": {"solves_per_s": 1e3 / fp64_ms * world, "ms_per_solve": fp64_ms},
         "rel_err_vs_fp64": rel_err,
         "stage_ms": stage_mean,
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "algorithmic_bytes": alg, "peak_source": peak_kind},
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": tflops / fp32_peak, "traffic": TRAFFIC.get((args.workload, dom)),
+                     "algorithmic_flops": flops, "peak_source": fp32_src,
+                     "hbm": {"algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                             "frac": gbs / hbm_peak, "peak_source": hbm_src}},
         "e2e": {"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches_per_solve(wl),
@@ -584,6 +594,42 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": sps, "unit": "solves/s", "cores": thr, "kind": "oracle", "sample": what,
                                 "target_cells_per_s": tps, "seconds": secs}
     print(json.dumps(line), flush=True)
+
+
+# DRAM bytes (read + write) per launch of a stage's kernel from the ncu capture
+# of the current kernel build (see profiles/); None when not captured for it.
+TRAFFIC = {("spiral1024", "col_conv"): 33.8e6 + 0.03e6}
+
+
+def algorithmic_flops(wl, info, stage):
+    """Conventional flop counts: 5 L log2 L per complex FFT of length L, plus
+    the spectral multiply-adds (8 flops per field per bin; about 60 per bin for
+    the central-slope spectrum); the direct sum counts 28 FP32 operations per
+    target-corner pair (FMA = 2)."""
+    import math
+    total = 0.0
+    for p in wl["patches"]:
+        nx, ny = p[1], p[2]
+        px = 64
+        while px < 2 * nx - 1:
+            px *= 2
+        py = 64
+        while py < 2 * ny - 1:
+            py *= 2
+        qx = px // 2 + 1
+        fft_x = 5.0 * px * math.log2(px)
+        fft_y = 5.0 * py * math.log2(py)
+        central = wl["slope_mode"] == 1
+        nfwd = 1 if wl["slope_mode"] != 2 else 3
+        if stage == "row_fwd":
+            total += nfwd * (ny / 2) * fft_x + (fft_y if central else 0)
+        elif stage == "col_conv":
+            total += qx * ((nfwd + 2) * fft_y + (60 if central else 8 * nfwd) * py)
+        elif stage == "row_inv":
+            total += ny * fft_x  # two outputs, two rows per transform
+    if stage == "cross_direct":
+        total = 28.0 * info["cross_pairs"]
+    return total
 
 
 def launches_per_solve(wl):
