@@ -114,3 +114,73 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * Off the plane (targets at height z != 0; Section 2, the antiderivatives with
+ * the arctan terms): with r = sqrt(u^2 + v^2 + z^2),
+ *   K^{x,0} = -dd ln(v + r),  K^{x,x} = (x - xc) K^{x,0} + dd[v ln(u + r) - |z| atan(u v / (|z| r))],
+ *   K^{x,y} = (y - yc) K^{x,0} - dd r, the y-family with u <-> v, and
+ *   K^{z,0} = -dd atan(u v / (z r)),  K^{z,x} = (x - xc) K^{z,0} - z K^{x,0},
+ *   K^{z,y} = (y - yc) K^{z,0} - z K^{y,0};
+ * F = G sum_i [sigma0_i K^{.,0} + deltax_i K^{.,x} + deltay_i K^{.,y}] for . = x, y, z.
+ */
+static double ln_s_plus_rz(double t, double s, double z)
+{
+    double r = sqrt(t * t + s * s + z * z);
+    if (s >= 0.0) return log(s + r);
+    return log(t * t + z * z) - log(r - s);
+}
+
+int oracle_direct_force3(long ns, const double *xl, const double *xr, const double *yd, const double *yu,
+                         const double *s0, const double *sx, const double *sy,
+                         long nt, const double *tx, const double *ty, double z, double G,
+                         double *fx, double *fy, double *fz, int nthreads)
+{
+    if (z == 0.0) return 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const double az = fabs(z);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long t = 0; t < nt; ++t) {
+        double ax = 0.0, ay = 0.0, azs = 0.0;
+        for (long i = 0; i < ns; ++i) {
+            double us[2] = { xl[i] - tx[t], xr[i] - tx[t] };
+            double vs[2] = { yd[i] - ty[t], yu[i] - ty[t] };
+            double ddlv = 0, ddlu = 0, ddvlu = 0, ddulv = 0, ddr = 0, ddat = 0;
+            for (int a = 0; a < 2; ++a) {
+                for (int b = 0; b < 2; ++b) {
+                    double sgn = (a == b) ? 1.0 : -1.0;
+                    double u = us[a], v = vs[b];
+                    double r = sqrt(u * u + v * v + z * z);
+                    double lv = ln_s_plus_rz(u, v, z);   /* ln(v + r) */
+                    double lu = ln_s_plus_rz(v, u, z);   /* ln(u + r) */
+                    ddlv += sgn * lv;
+                    ddlu += sgn * lu;
+                    ddvlu += sgn * v * lu;
+                    ddulv += sgn * u * lv;
+                    ddr += sgn * r;
+                    ddat += sgn * atan(u * v / (az * r));
+                }
+            }
+            double xc = 0.5 * (xl[i] + xr[i]), yc = 0.5 * (yd[i] + yu[i]);
+            double kx0 = -ddlv, ky0 = -ddlu, kz0 = (z > 0 ? -1.0 : 1.0) * ddat;
+            double kxx = (tx[t] - xc) * kx0 + ddvlu - az * ddat;
+            double kxy = (ty[t] - yc) * kx0 - ddr;
+            double kyx = (tx[t] - xc) * ky0 - ddr;
+            double kyy = (ty[t] - yc) * ky0 + ddulv - az * ddat;
+            double kzx = (tx[t] - xc) * kz0 - z * kx0;
+            double kzy = (ty[t] - yc) * kz0 - z * ky0;
+            double a0 = s0[i], bx = sx ? sx[i] : 0.0, by = sy ? sy[i] : 0.0;
+            ax += a0 * kx0 + bx * kxx + by * kxy;
+            ay += a0 * ky0 + bx * kyx + by * kyy;
+            azs += a0 * kz0 + bx * kzx + by * kzy;
+        }
+        fx[t] = G * ax;
+        fy[t] = G * ay;
+        fz[t] = G * azs;
+    }
+    return 0;
+}

@@ -33,6 +33,9 @@ def _load():
                                             ctypes.c_long, dp, dp, ctypes.c_double, dp, dp, ctypes.c_int]
         lib.oracle_direct_force.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_direct_force3.argtypes = [ctypes.c_long, dp, dp, dp, dp, dp, dp, dp, ctypes.c_long, dp, dp,
+                                             ctypes.c_double, ctypes.c_double, dp, dp, dp, ctypes.c_int]
+        lib.oracle_direct_force3.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -98,3 +101,39 @@ def uniform_direct_force(sigma, dx, dy, h, x0=-1.0, y0=-1.0, G=1.0, targets=None
     ty = y0 + (tj + 0.5) * h
     fx, fy = direct_force(cells, sigma, dx, dy, tx, ty, G=G, nthreads=nthreads)
     return fx.reshape(shape), fy.reshape(shape)
+
+
+def direct_force3(cells, s0, sx, sy, tx, ty, z, G=1.0, nthreads=0):
+    """Fx, Fy, Fz at targets (tx, ty, z), z != 0, by the plain sum over cells."""
+    lib = _load()
+    xl, xr, yd, yu = [np.ascontiguousarray(c, dtype=np.float64).ravel() for c in cells]
+    s0 = np.ascontiguousarray(s0, dtype=np.float64).ravel()
+    sx = None if sx is None else np.ascontiguousarray(sx, dtype=np.float64).ravel()
+    sy = None if sy is None else np.ascontiguousarray(sy, dtype=np.float64).ravel()
+    tx = np.ascontiguousarray(tx, dtype=np.float64).ravel()
+    ty = np.ascontiguousarray(ty, dtype=np.float64).ravel()
+    out = [np.zeros(tx.size) for _ in range(3)]
+    st = lib.oracle_direct_force3(xl.size, _ptr(xl), _ptr(xr), _ptr(yd), _ptr(yu), _ptr(s0), _ptr(sx), _ptr(sy),
+                                  tx.size, _ptr(tx), _ptr(ty), float(z), float(G), _ptr(out[0]), _ptr(out[1]),
+                                  _ptr(out[2]), int(nthreads))
+    if st != 0:
+        raise ValueError("direct_force3 needs z != 0")
+    return tuple(out)
+
+
+def uniform_direct_force3(sigma, dx, dy, h, z, x0=-1.0, y0=-1.0, G=1.0, targets=None, nthreads=0):
+    """Off-plane direct sum on a uniform grid (layout as uniform_direct_force)."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    ny, nx = sigma.shape
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny))
+    xl = x0 + I * h
+    yd = y0 + J * h
+    if targets is None:
+        tj, ti = J.ravel(), I.ravel()
+        shape = sigma.shape
+    else:
+        tj, ti = (np.asarray(a).ravel() for a in targets)
+        shape = np.asarray(targets[0]).shape
+    f = direct_force3((xl, xl + h, yd, yd + h), sigma, dx, dy, x0 + (ti + 0.5) * h, y0 + (tj + 0.5) * h, z, G=G,
+                      nthreads=nthreads)
+    return tuple(a.reshape(shape) for a in f)

@@ -51,3 +51,13 @@ def kuzmin_force_xy(x, y, a, M=1.0, G=1.0):
     y = np.asarray(y, np.float64)
     s = -G * M / (x * x + y * y + a * a) ** 1.5
     return s * x, s * y
+
+
+def kuzmin_force_xyz(x, y, z, a, M=1.0, G=1.0):
+    """Kuzmin disk off the plane: Phi = -G M / sqrt(R^2 + (a + |z|)^2), so
+    F = -grad Phi = -G M (x, y, sgn(z) (a + |z|)) / (R^2 + (a + |z|)^2)^{3/2}."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    b = a + abs(z)
+    s = -G * M / (x * x + y * y + b * b) ** 1.5
+    return s * x, s * y, s * np.sign(z) * b

@@ -13,7 +13,7 @@ grids (after Yen et al. 2012). The FFT itself is numpy's (a library routine).
 """
 import numpy as np
 
-from .kernels import offset_tables
+from .kernels import offset_tables, offset_tables_z
 
 
 def _wrap_correlation_kernel(table, py, px):
@@ -77,3 +77,29 @@ def central_slopes(sigma, h):
     dx = (p[1:-1, 2:] - p[1:-1, :-2]) / (2.0 * h)
     dy = (p[2:, 1:-1] - p[:-2, 1:-1]) / (2.0 * h)
     return dx, dy
+
+
+def uniform_fft_force3(sigma, dx, dy, h, z, G=1.0, pad=None):
+    """Fx, Fy, Fz at height z != 0 above every cell centre, by zero-padded FFT
+    with the nine off-plane kernel tables."""
+    sigma = np.asarray(sigma, dtype=np.float64)
+    ny, nx = sigma.shape
+    py, px = pad if pad is not None else (2 * ny, 2 * nx)
+    tabs = offset_tables_z(nx, ny, h, z)
+
+    def spec(a):
+        return np.fft.rfft2(a, s=(py, px))
+
+    def kspec(name):
+        return np.fft.rfft2(_wrap_correlation_kernel(tabs[name], py, px))
+
+    fields = [(spec(sigma), "0")]
+    if dx is not None:
+        fields.append((spec(np.asarray(dx, np.float64)), "x"))
+    if dy is not None:
+        fields.append((spec(np.asarray(dy, np.float64)), "y"))
+    out = []
+    for comp in ("x", "y", "z"):
+        acc = sum(f * kspec(comp + k) for f, k in fields)
+        out.append(G * np.fft.irfft2(acc, s=(py, px))[:ny, :nx])
+    return tuple(out)

@@ -130,3 +130,67 @@ def offset_tables(mx, my, h=1.0):
     n = np.arange(-(my - 1), my, dtype=np.float64)
     M, Nn = np.meshgrid(m, n)
     return cell_kernels(0.0, 0.0, (M - 0.5) * h, (M + 0.5) * h, (Nn - 0.5) * h, (Nn + 0.5) * h)
+
+
+# ----------------------------------------------------------- off the plane --
+#
+# Targets at height z != 0 above the disk plane (Section 2, the antiderivative
+# list with the arctan terms; the printed "sgn(x) x y" is read as u v, and the
+# z-family as below). With r = sqrt(u^2 + v^2 + z^2):
+#   K^{x,0} = -dd ln(v + r)
+#   K^{x,x} = (x - xc) K^{x,0} + dd[v ln(u + r) - |z| atan(u v / (|z| r))]
+#   K^{x,y} = (y - yc) K^{x,0} - dd r
+#   (y-family with u <-> v)
+#   K^{z,0} = integral of (zbar - z) / r^3 over the cell = -dd atan(u v / (z r))
+#   K^{z,x} = (x - xc) K^{z,0} - z K^{x,0}
+#   K^{z,y} = (y - yc) K^{z,0} - z K^{y,0}
+# so that F_z = G sum_i [sigma0_i K^{z,0}_i + deltax_i K^{z,x}_i + deltay_i K^{z,y}_i]
+# (attractive: towards the plane). The paper's z-family differs from these by
+# the overall sign convention discussed for the in-plane force.
+
+def _ln_s_plus_rz(t, s, z):
+    """ln(s + sqrt(t^2 + s^2 + z^2)) for z != 0 (never singular)."""
+    t, s = np.broadcast_arrays(np.asarray(t, np.float64), np.asarray(s, np.float64))
+    r = np.sqrt(t * t + s * s + z * z)
+    out = np.empty(t.shape, dtype=np.float64)
+    pos = s >= 0.0
+    out[pos] = np.log(s[pos] + r[pos])
+    neg = ~pos
+    out[neg] = np.log(t[neg] ** 2 + z * z) - np.log(r[neg] - s[neg])
+    return out
+
+
+def cell_kernels_z(x, y, z, xl, xr, yd, yu):
+    """All nine cell integrals at height z != 0: keys x0 xx xy y0 yx yy z0 zx zy."""
+    if z == 0.0:
+        raise ValueError("cell_kernels_z needs z != 0 (use cell_kernels in the plane)")
+    x, y, xl, xr, yd, yu = np.broadcast_arrays(*[np.asarray(a, np.float64) for a in (x, y, xl, xr, yd, yu)])
+    u1, u2, v1, v2 = xl - x, xr - x, yd - y, yu - y
+    xc = 0.5 * (xl + xr)
+    yc = 0.5 * (yd + yu)
+    az = abs(z)
+    rr = lambda u, v: np.sqrt(u * u + v * v + z * z)
+    kx0 = -_dd(lambda u, v: _ln_s_plus_rz(u, v, z), u1, u2, v1, v2)
+    ky0 = -_dd(lambda u, v: _ln_s_plus_rz(v, u, z), u1, u2, v1, v2)
+    solid = _dd(lambda u, v: np.arctan(u * v / (az * rr(u, v))), u1, u2, v1, v2)
+    ddr = _dd(rr, u1, u2, v1, v2)
+    kz0 = -np.sign(z) * solid
+    return {
+        "x0": kx0,
+        "xx": (x - xc) * kx0 + _dd(lambda u, v: v * _ln_s_plus_rz(v, u, z), u1, u2, v1, v2) - az * solid,
+        "xy": (y - yc) * kx0 - ddr,
+        "y0": ky0,
+        "yx": (x - xc) * ky0 - ddr,
+        "yy": (y - yc) * ky0 + _dd(lambda u, v: u * _ln_s_plus_rz(u, v, z), u1, u2, v1, v2) - az * solid,
+        "z0": kz0,
+        "zx": (x - xc) * kz0 - z * kx0,
+        "zy": (y - yc) * kz0 - z * ky0,
+    }
+
+
+def offset_tables_z(mx, my, h, z):
+    """Nine kernel tables of a uniform grid at height z (layout of offset_tables)."""
+    m = np.arange(-(mx - 1), mx, dtype=np.float64)
+    n = np.arange(-(my - 1), my, dtype=np.float64)
+    M, Nn = np.meshgrid(m, n)
+    return cell_kernels_z(0.0, 0.0, z, (M - 0.5) * h, (M + 0.5) * h, (Nn - 0.5) * h, (Nn + 0.5) * h)
