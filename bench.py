@@ -159,7 +159,18 @@ def workload_amr3():
     }
 
 
-WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3}
+def workload_offplane():
+    """The spiral 1024^2 disk with the targets one cell width above the plane
+    (Fx, Fy, Fz; off-plane kernels with the arctan terms), central slopes."""
+    wl = workload_spiral()
+    h = wl["patches"][0][5]
+    wl["z"] = h
+    wl["name"] = wl["name"] + ", targets at z = h above the plane"
+    wl["config"] = dict(wl["config"], workload="spiral_1024_offplane", z=h, outputs="Fx Fy Fz")
+    return wl
+
+
+WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3, "offplane": workload_offplane}
 
 
 # -------------------------------------------------------------- batch run --
@@ -471,18 +482,25 @@ def run_gpu(args):
 
     wl = WORKLOADS[args.workload]()
     dt = torch.float32
-    plan = sg.Plan(wl["patches"], precision="fp32", slope_mode=wl["slope_mode"])
+    zt = wl.get("z", 0.0)
+    plan = sg.Plan(wl["patches"], precision="fp32", slope_mode=wl["slope_mode"], z=zt)
     sg.sg_plan_set_timing(plan.handle, True)
     stream = torch.cuda.Stream()
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     sigma, dxs, dys = dev(wl["sigma"]), dev(wl["dx"]), dev(wl["dy"])
     fx = torch.empty_like(sigma)
     fy = torch.empty_like(sigma)
+    fz = torch.empty_like(sigma) if zt else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def solve():
         with torch.cuda.stream(stream):
-            plan.force(sigma, dxs, dys, fx, fy, stream=stream)
+            if zt:
+                sg.sg_force3(plan.handle, sigma.data_ptr(), dxs.data_ptr() if dxs is not None else 0,
+                             dys.data_ptr() if dys is not None else 0, fx.data_ptr(), fy.data_ptr(), fz.data_ptr(),
+                             stream.cuda_stream)
+            else:
+                plan.force(sigma, dxs, dys, fx, fy, stream=stream)
 
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -514,21 +532,24 @@ def run_gpu(args):
     p99 = float(np.percentile(per, 99))
 
     # FP64 plain per-solve path on the same GPU, and the FP32 error against it
-    plan64 = sg.Plan(wl["patches"], precision="fp64", slope_mode=wl["slope_mode"])
+    plan64 = sg.Plan(wl["patches"], precision="fp64", slope_mode=wl["slope_mode"], z=zt)
     d64 = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32).astype(np.float64)).cuda()
     s64, dx64, dy64 = d64(wl["sigma"]), d64(wl["dx"]), d64(wl["dy"])
-    g64 = plan64.force(s64, dx64, dy64)
+    g64 = plan64.force3(s64, dx64, dy64) if zt else plan64.force(s64, dx64, dy64)
     torch.cuda.synchronize()
-    ff = [x.double() for x in (fx, fy)]
-    num = torch.sum((ff[0] - g64[0]) ** 2) + torch.sum((ff[1] - g64[1]) ** 2)
-    den = torch.sum(g64[0] ** 2) + torch.sum(g64[1] ** 2)
+    ff = [x.double() for x in ((fx, fy, fz) if zt else (fx, fy))]
+    num = sum(torch.sum((a - b) ** 2) for a, b in zip(ff, g64))
+    den = sum(torch.sum(b ** 2) for b in g64)
     rel_err = float(torch.sqrt(num / den))
     n64 = max(3, min(args.steps, 10))
     e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
     for k in range(n64):
         flush.fill_(1.0)
         e64[k][0].record()
-        plan64.force(s64, dx64, dy64, g64[0], g64[1])
+        if zt:
+            plan64.force3(s64, dx64, dy64)
+        else:
+            plan64.force(s64, dx64, dy64, g64[0], g64[1])
         e64[k][1].record()
     torch.cuda.synchronize()
     fp64_ms = statistics.median([a.elapsed_time(b) for a, b in e64])
@@ -541,18 +562,20 @@ def run_gpu(args):
     hfx = torch.empty(plan.ncells, dtype=dt).pin_memory()
     hfy = torch.empty(plan.ncells, dtype=dt).pin_memory()
     sg.sg_plan_set_timing(plan.handle, False)
-    for _ in range(2):
-        plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)
-    e2e_ms = 0.0
-    for k in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)  # copies in, solve, copies out, waits
-        e2e_ms += 1e3 * (time.perf_counter() - t0)
-    nbytes = plan.ncells * 4
-    h2d = nbytes * (3 if wl["dx"] is not None else 1)
-    d2h = 2 * nbytes
+    e2e_ms, h2d, d2h = None, 0, 0
+    if not zt:  # the host entry point returns Fx, Fy
+        for _ in range(2):
+            plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)
+        e2e_ms = 0.0
+        for k in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)  # copies in, solve, copies out, waits
+            e2e_ms += 1e3 * (time.perf_counter() - t0)
+        nbytes = plan.ncells * 4
+        h2d = nbytes * (3 if wl["dx"] is not None else 1)
+        d2h = 2 * nbytes
 
     # roofline of the dominant kernel
     stage_mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
@@ -583,8 +606,8 @@ def run_gpu(args):
                      "algorithmic_flops": flops, "peak_source": fp32_src,
                      "hbm": {"algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
                              "frac": gbs / hbm_peak, "peak_source": hbm_src}},
-        "e2e": {"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                 "d2h_bytes_per_step": d2h} if e2e_ms else None),
         "gpu_launches": args.steps * launches_per_solve(wl),
         "clocks": clk.summary(),
         "wall_s": wall,

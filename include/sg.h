@@ -85,6 +85,9 @@ typedef struct {
     const sg_patch *patches;    /* sorted by level; level-0 patches first */
     double G;                   /* gravitational constant */
     int slope_mode;             /* an sg_slope_mode */
+    double z;                   /* height of the targets above the disk plane; 0 = in the plane.
+                                   z != 0 (off-plane forces, Section 2 with the arctan terms)
+                                   needs a single patch and sg_force3 */
 } sg_geom;
 
 typedef struct {
@@ -144,7 +147,8 @@ sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes);
 /*
  * Copy one FP64 kernel table of patch `patch` to host memory, regenerated on
  * the device: which = 0..5 selects K^{x,0}, K^{x,x}, K^{x,y}, K^{y,0},
- * K^{y,x}, K^{y,y} (Section 2). Entry [n + ny - 1][m + nx - 1] (row-major,
+ * K^{y,x}, K^{y,y} (Section 2); for plans with z != 0 also 6..8 = K^{z,0},
+ * K^{z,x}, K^{z,y}. Entry [n + ny - 1][m + nx - 1] (row-major,
  * (2 nx - 1) x (2 ny - 1) doubles) holds the integral over a source cell whose
  * centre is offset by (m h, n h) from the target centre, in physical units
  * (K^{.,0} dimensionless, the others proportional to h).
@@ -154,7 +158,7 @@ sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes);
 sg_status sg_kernel_tables(const sg_plan *plan, int patch, int which, double *host_out, size_t n);
 
 /*
- * Enqueue one force solve on `stream`.
+ * Enqueue one force solve on `stream` (plans with z == 0; use sg_force3 for z != 0).
  *   sigma       device pointer, ncells elements (sigma0 per cell)
  *   deltax/y    device pointers, ncells elements each; read only for
  *               SG_SLOPES_CALLER, otherwise may be NULL
@@ -166,6 +170,19 @@ sg_status sg_kernel_tables(const sg_plan *plan, int patch, int which, double *ho
  */
 sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
                    void *fx, void *fy, void *stream);
+
+/*
+ * Fx, Fy and Fz (enqueued on `stream`, buffers as for sg_force plus fz).
+ * For a plan with z != 0 (one patch) the targets are the points (xc, yc, z)
+ * above the cell centres and all three components come from the off-plane cell
+ * integrals (Section 2): K^{z,0} = integral of (zbar - z)/r^3 = -dd atan(uv/(z r)),
+ * K^{z,x} = (x - xc) K^{z,0} - z K^{x,0}, K^{z,y} = (y - yc) K^{z,0} - z K^{y,0}.
+ * For a z = 0 plan Fx, Fy are those of sg_force and Fz is the limit from
+ * above the plane, -2 pi G sigma0 of the target's own cell (the other cells'
+ * normal forces vanish in the plane). Errors: as sg_force.
+ */
+sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
+                    void *fz, void *stream);
 
 /*
  * The same solve with HOST buffers: copies the inputs to the plan's device

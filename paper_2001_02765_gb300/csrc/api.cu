@@ -107,6 +107,8 @@ sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
     if (!g) return fail("geometry is NULL");
     if (g->npatches < 1 || !g->patches) return fail("geometry has no patches");
     if (!isfinite(g->G)) return fail("G is not finite");
+    if (!isfinite(g->z)) return fail("z is not finite");
+    if (g->z != 0.0 && g->npatches != 1) return fail("off-plane forces (z != 0) need a single patch");
     if (g->slope_mode < SG_SLOPES_NONE || g->slope_mode > SG_SLOPES_CALLER) return fail("unknown slope mode");
     const int n = g->npatches;
     const sg_patch *P = g->patches;
@@ -273,7 +275,7 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
         const int px = sg_pad_length(g->patches[k].nx), py = sg_pad_length(g->patches[k].ny);
         if (px > s.max_pad) s.max_pad = px;
         if (py > s.max_pad) s.max_pad = py;
-        s.spectra += 6LL * (px / 2 + 1) * sg_spec_stride(py) * (int64_t)es;
+        s.spectra += (g->z != 0.0 ? 9LL : 6LL) * (px / 2 + 1) * sg_spec_stride(py) * (int64_t)es;
         const int64_t w = 5LL * (px / 2 + 1) * g->patches[k].ny * (int64_t)(2 * es);
         if (w > work) work = w;
     }
@@ -418,8 +420,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             pp.tile_count = tcount[k];
         }
         pdev[k] = d;
-        st = dev_alloc(plan, &pp.spectra, 6 * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
-        if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL)
+        const int nplanes = g->z != 0.0 ? 9 : 6;
+        st = dev_alloc(plan, &pp.spectra, nplanes * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
+        if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0)
             st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
     plan->ncov_total = (int)cov_all.size();
@@ -440,10 +443,12 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     int64_t wf = 0, wi = 0;
     for (int k = 0; k < gi.n; ++k) {
         const int64_t q = (int64_t)(pdev[k].px / 2 + 1) * pdev[k].ny * (int64_t)(2 * es);
-        // central slopes transform sigma only, plus the two edge columns (2 x py complex)
-        const int64_t f = g->slope_mode == SG_SLOPES_CENTRAL ? q + 2LL * pdev[k].py * (int64_t)(2 * es) : 3 * q;
+        // central slopes (in the plane) transform sigma only, plus the two edge columns (2 x py complex)
+        const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0;
+        const int64_t f = central ? q + 2LL * pdev[k].py * (int64_t)(2 * es) : 3 * q;
+        const int nout = g->z != 0.0 ? 3 : 2;
         if (f > wf) wf = f;
-        if (2 * q > wi) wi = 2 * q;
+        if (nout * q > wi) wi = nout * q;
     }
     plan->ws_fwd_bytes = wf;
     plan->ws_inv_bytes = wi;
@@ -587,18 +592,18 @@ sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t
 }
 
 sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *deltax, const void *deltay,
-                      void *fx, void *fy, cudaStream_t st)
+                      void *fx, void *fy, cudaStream_t st, void *fz)
 {
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
     const void *dx = caller ? deltax : nullptr, *dy = caller ? deltay : nullptr;
-    if (plan->npatches == 1) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, st);
+    if (plan->npatches == 1) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, fz, st);
     // AMR: composite sources, same-patch FFT convolutions, cross-patch direct sum
     SG_TRY(sg_amr_prepare(plan, ws, sigma, dx, dy, st));
     const size_t es = elem_size(plan->prec);
     const char *S = (const char *)ws->sfield;
     const size_t plane = (size_t)plan->ncells * es;
     for (int k = 0; k < plan->npatches; ++k)
-        SG_TRY(sg_uniform_solve(plan, ws, k, S, S + plane, S + 2 * plane, fx, fy, st));
+        SG_TRY(sg_uniform_solve(plan, ws, k, S, S + plane, S + 2 * plane, fx, fy, nullptr, st));
     return sg_cross_solve(plan, ws, S, S + plane, S + 2 * plane, fx, fy, st);
 }
 
@@ -614,6 +619,43 @@ static sg_status check_device_error(sg_plan *plan)
         return SG_ETIMEOUT;
     }
     return SG_OK;
+}
+
+template <typename T>
+__global__ void k_fz_plane(const T *__restrict__ sigma, T *__restrict__ fz, int64_t n, double c)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        fz[i] = (T)(c * (double)sigma[i]);
+}
+
+// Validation, the plan's own workspace (allocated at the first call), timers, solve.
+static sg_status force_common(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
+                              void *fy, void *fz, void *stream)
+{
+    if (!plan || !sigma || !fx || !fy) return fail("null plan or field pointer");
+    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
+    const size_t es = elem_size(plan->prec);
+    if (!aligned(sigma, es) || !aligned(fx, es) || !aligned(fy, es) || (fz && !aligned(fz, es)) ||
+        (caller && (!aligned(deltax, es) || !aligned(deltay, es))))
+        return fail("misaligned field pointer");
+    int dev = -1;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) return fail("the plan's device is not current");
+    if (!plan->ws) {
+        sg_workspace *ws = new (std::nothrow) sg_workspace();
+        if (!ws) return SG_ENOMEM;
+        sg_status a = sg_workspace_alloc(plan, ws, 0, false);
+        if (a != SG_OK) {
+            delete ws;
+            return a;
+        }
+        plan->ws = ws;
+        plan->device_bytes += plan->scratch_bytes;
+    }
+    sg_timing_reset(plan->timing);
+    plan->ws->timing = plan->timing;
+    return sg_force_ws(plan, plan->ws, sigma, deltax, deltay, fx, fy, (cudaStream_t)stream, fz);
 }
 
 // --------------------------------------------------------------- the C ABI --
@@ -673,29 +715,25 @@ sg_status sg_kernel_tables(const sg_plan *plan, int patch, int which, double *ho
 sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
                    void *stream)
 {
-    if (!plan || !sigma || !fx || !fy) return fail("null plan or field pointer");
-    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
-    if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
-    const size_t es = elem_size(plan->prec);
-    if (!aligned(sigma, es) || !aligned(fx, es) || !aligned(fy, es) || (caller && (!aligned(deltax, es) || !aligned(deltay, es))))
-        return fail("misaligned field pointer");
-    int dev = -1;
-    SG_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev != plan->device) return fail("the plan's device is not current");
-    if (!plan->ws) {
-        sg_workspace *ws = new (std::nothrow) sg_workspace();
-        if (!ws) return SG_ENOMEM;
-        sg_status a = sg_workspace_alloc(plan, ws, 0, false);
-        if (a != SG_OK) {
-            delete ws;
-            return a;
-        }
-        plan->ws = ws;
-        plan->device_bytes += plan->scratch_bytes;
-    }
-    sg_timing_reset(plan->timing);
-    plan->ws->timing = plan->timing;
-    return sg_force_ws(plan, plan->ws, sigma, deltax, deltay, fx, fy, (cudaStream_t)stream);
+    return force_common(plan, sigma, deltax, deltay, fx, fy, nullptr, stream);
+}
+
+sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
+                    void *fz, void *stream)
+{
+    if (!plan || !fz) return fail("null plan or fz pointer");
+    if (plan->geom.z != 0.0) return force_common(plan, sigma, deltax, deltay, fx, fy, fz, stream);
+    SG_TRY(force_common(plan, sigma, deltax, deltay, fx, fy, nullptr, stream));
+    // in the plane: Fz from above is -2 pi G sigma0 of the target's own cell
+    const int64_t n = plan->ncells;
+    const double c = -2.0 * 3.14159265358979323846 * plan->geom.G;
+    const int grid = (int)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+    if (plan->prec == SG_FP64)
+        k_fz_plane<double><<<grid, 256, 0, (cudaStream_t)stream>>>((const double *)sigma, (double *)fz, n, c);
+    else
+        k_fz_plane<float><<<grid, 256, 0, (cudaStream_t)stream>>>((const float *)sigma, (float *)fz, n, c);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
 }
 
 sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,

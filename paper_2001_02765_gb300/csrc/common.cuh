@@ -187,7 +187,7 @@ void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async);
 int64_t sg_workspace_bytes(const sg_plan *plan);
 // One solve on an explicit workspace (sg_force uses the plan's own).
 sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
-                      void *fx, void *fy, cudaStream_t st);
+                      void *fx, void *fy, cudaStream_t st, void *fz = nullptr);
 
 // Stages timed by sg_plan_get_timing.
 enum { SG_STAGE_ROW_FWD = 0, SG_STAGE_COL_CONV = 1, SG_STAGE_ROW_INV = 2, SG_STAGE_WEIGHTS = 3,
@@ -208,7 +208,7 @@ sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host
 sg_status sg_twiddles_build(sg_plan *plan);
 sg_status sg_phase_build(sg_plan *plan);     // central-slope factors of every patch
 sg_status sg_uniform_solve(sg_plan *plan, const struct sg_workspace *ws, int patch, const void *sigma, const void *dx,
-                           const void *dy, void *fx, void *fy, cudaStream_t st);
+                           const void *dy, void *fx, void *fy, void *fz, cudaStream_t st);
 sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          void *fx, void *fy, cudaStream_t st);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,

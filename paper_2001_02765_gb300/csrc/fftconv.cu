@@ -127,19 +127,19 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T>
 // arrive while the forward transform runs.
 template <typename T, int PY, int CB>
 __host__ __device__ constexpr int col_buf_bytes() { return (spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15; }
-template <typename T, int PY, int CB>
-__host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * 6 * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
+template <typename T, int PY, int CB, int NPL = 6>
+__host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * NPL * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
 
-template <typename T, int PY, int CB>
+template <typename T, int PY, int CB, int NPL = 6>
 __device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec, int kx0, int qx, uint64_t *bar)
 {
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int ncol = qx - kx0 < CB ? qx - kx0 : CB;
     const int64_t qplane = (int64_t)qx * QS;
-    mbar_arrive_expect_tx(bar, (uint32_t)(ncol * 6 * QS * sizeof(T)));
+    mbar_arrive_expect_tx(bar, (uint32_t)(ncol * NPL * QS * sizeof(T)));
     for (int c = 0; c < ncol; ++c)
-        for (int p = 0; p < 6; ++p)
-            bulk_copy_g2s(ssp + (c * 6 + p) * QS, spec + p * qplane + (int64_t)(kx0 + c) * QS, QS * sizeof(T), bar);
+        for (int p = 0; p < NPL; ++p)
+            bulk_copy_g2s(ssp + (c * NPL + p) * QS, spec + p * qplane + (int64_t)(kx0 + c) * QS, QS * sizeof(T), bar);
 }
 
 // Bounded wait for the spectra; on timeout records the error, gives the copies
@@ -162,7 +162,7 @@ __device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err)
 template <typename T, int PY>
 constexpr int col_min_blocks() { return sizeof(T) == 4 ? (PY == 2048 ? 3 : (PY == 4096 ? 1 : 2)) : 1; }
 
-template <typename T, int PY, int CB, int THREADS>
+template <typename T, int PY, int CB, int THREADS, int NOUT>
 __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv(const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv,
                                                       const T *__restrict__ spec, int ny, int qx, int nf,
                                                       const cplx_t<T> *__restrict__ tw, int *err)
@@ -175,13 +175,16 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
     constexpr int EPT = CB * PY / THREADS;
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int kx0 = blockIdx.x * CB;
+    constexpr int NPL = NOUT == 3 ? 9 : 6;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL>(ssp, spec, kx0, qx, &bar);
 
-    C accx[EPT], accy[EPT];
+    C accx[EPT], accy[EPT], accz[NOUT == 3 ? EPT : 1];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+#pragma unroll
+    for (int q = 0; q < (NOUT == 3 ? EPT : 1); ++q) accz[q] = cmake<C>((T)0, (T)0);
 
     for (int f = 0; f < nf; ++f) {
         for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
@@ -202,31 +205,49 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
             const bool lower = ky <= PY / 2;
             const int kq = lower ? ky : PY - ky;
             const T sg = lower ? (T)1 : (T)-1;
-            const T *sp = ssp + c * 6 * QS + kq;
+            const T *sp = ssp + c * NPL * QS + kq;
             const C X = buf[spad<C>(e)];
             if (f == 0) {
                 const T a = sp[0 * QS];
                 const T d = sg * sp[3 * QS];
                 accx[q] = cmake<C>(-a * X.y, a * X.x);
                 accy[q] = cmake<C>(-d * X.y, d * X.x);
+                if constexpr (NOUT == 3) {
+                    const T g = sp[6 * QS];  // real: sigma^ g
+                    accz[q] = cmake<C>(g * X.x, g * X.y);
+                }
             } else if (f == 1) {
                 const T b = sp[1 * QS];
                 const T ff = sg * sp[5 * QS];
                 accx[q] = cmake<C>(accx[q].x + b * X.x, accx[q].y + b * X.y);
                 accy[q] = cmake<C>(accy[q].x + ff * X.x, accy[q].y + ff * X.y);
+                if constexpr (NOUT == 3) {
+                    const T hh = sp[7 * QS];  // imaginary: deltax^ (i hh)
+                    accz[q] = cmake<C>(accz[q].x - hh * X.y, accz[q].y + hh * X.x);
+                }
             } else {
                 const T cc = sg * sp[2 * QS];
                 const T ee = sp[4 * QS];
                 accx[q] = cmake<C>(accx[q].x + cc * X.x, accx[q].y + cc * X.y);
                 accy[q] = cmake<C>(accy[q].x + ee * X.x, accy[q].y + ee * X.y);
+                if constexpr (NOUT == 3) {
+                    const T kk = sg * sp[8 * QS];  // imaginary, odd in ky: deltay^ (i s kk)
+                    accz[q] = cmake<C>(accz[q].x - kk * X.y, accz[q].y + kk * X.x);
+                }
             }
         }
         __syncthreads();
     }
 
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < NOUT; ++o) {
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
+        for (int q = 0; q < EPT; ++q) {
+            C v = o == 0 ? accx[q] : accy[q];
+            if constexpr (NOUT == 3) {
+                if (o == 2) v = accz[q];
+            }
+            buf[spad<C>(threadIdx.x + q * THREADS)] = v;
+        }
         __syncthreads();
         fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
         for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
@@ -240,7 +261,8 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
 
 template <typename T, int PX, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict__ work_inv, T *__restrict__ fx,
-                                                     T *__restrict__ fy, int nx, int ny, const cplx_t<T> *__restrict__ tw)
+                                                     T *__restrict__ fy, T *__restrict__ fz, int nx, int ny,
+                                                     const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -250,7 +272,7 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict
     const int o = blockIdx.y;
     const int j0 = blockIdx.x * RB;
     const C *w = work_inv + (int64_t)o * QX * ny;
-    T *out = o == 0 ? fx : fy;
+    T *out = o == 0 ? fx : (o == 1 ? fy : fz);
 
     // Z[k] = A[k] + i B[k] over the full length, from the half spectra of rows 2s, 2s+1
     for (int e = threadIdx.x; e < NB * QX; e += THREADS) {
@@ -410,26 +432,27 @@ sg_status launch_rows_fwd(const field_src<T> &src, cplx_t<T> *work, int nf, cons
 }
 
 template <typename T, int PX>
-sg_status launch_rows_inv(const cplx_t<T> *work, T *fx, T *fy, int nx, int ny, const cplx_t<T> *tw, cudaStream_t st)
+sg_status launch_rows_inv(const cplx_t<T> *work, T *fx, T *fy, T *fz, int nx, int ny, const cplx_t<T> *tw,
+                          cudaStream_t st)
 {
     constexpr int NB = row_nb_inv(PX);
     const size_t smem = (size_t)spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
     auto kern = k_row_inv<T, PX, NB, ROW_THREADS>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((ny + 2 * NB - 1) / (2 * NB), 2);
-    kern<<<grid, ROW_THREADS, smem, st>>>(work, fx, fy, nx, ny, tw);
+    dim3 grid((ny + 2 * NB - 1) / (2 * NB), fz ? 3 : 2);
+    kern<<<grid, ROW_THREADS, smem, st>>>(work, fx, fy, fz, nx, ny, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
-template <typename T, int PY>
+template <typename T, int PY, int NOUT>
 sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf, const cplx_t<T> *tw,
                       int *err, cudaStream_t st)
 {
     constexpr int CB = col_cb(PY);
     constexpr int THREADS = col_threads(PY);
-    const size_t smem = (size_t)col_smem_bytes<T, PY, CB>();
-    auto kern = k_col_conv<T, PY, CB, THREADS>;
+    const size_t smem = (size_t)col_smem_bytes<T, PY, CB, NOUT == 3 ? 9 : 6>();
+    auto kern = k_col_conv<T, PY, CB, THREADS, NOUT>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((qx + CB - 1) / CB);
     kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, ny, qx, nf, tw, err);
@@ -478,7 +501,7 @@ sg_status launch_edge_cols(const T *sigma, int nx, int ny, cplx_t<T> *edge, cons
 
 template <typename T>
 sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const void *sigma, const void *dx,
-                          const void *dy, void *fx, void *fy, cudaStream_t st)
+                          const void *dy, void *fx, void *fy, void *fz, cudaStream_t st)
 {
     using C = cplx_t<T>;
     const sg_patch_plan &pp = plan->pp[p];
@@ -511,6 +534,7 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     const C *twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.px)]);
     const C *twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.py)]);
     T *ox = (T *)fx + off, *oy = (T *)fy + off;
+    T *oz = fz ? (T *)fz + off : nullptr;  // off-plane plans only
     const bool central = src.mode == SG_SLOPES_CENTRAL && pp.phase;
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
     if (central) {
@@ -534,11 +558,15 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
         SG_PAD_SWITCH(d.py, SG_TRY((launch_cols_central<T, PP>(wf, wi, (const T *)pp.spectra, edge,
                                                                 (const T *)pp.phase, d.ny, qx, twy, ws->err, st))));
     } else {
-        SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, ws->err, st))));
+        if (oz) {
+            SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP, 3>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, ws->err, st))));
+        } else {
+            SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP, 2>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, ws->err, st))));
+        }
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
-    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, oy, d.nx, d.ny, twx, st))));
+    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, oy, oz, d.nx, d.ny, twx, st))));
     sg_timing_end(ws, SG_STAGE_ROW_INV, st);
     return SG_OK;
 }
@@ -546,8 +574,8 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
 }  // namespace
 
 sg_status sg_uniform_solve(sg_plan *plan, const sg_workspace *ws, int patch, const void *sigma, const void *dx,
-                           const void *dy, void *fx, void *fy, cudaStream_t st)
+                           const void *dy, void *fx, void *fy, void *fz, cudaStream_t st)
 {
-    if (plan->prec == SG_FP64) return uniform_solve_t<double>(plan, ws, patch, sigma, dx, dy, fx, fy, st);
-    return uniform_solve_t<float>(plan, ws, patch, sigma, dx, dy, fx, fy, st);
+    if (plan->prec == SG_FP64) return uniform_solve_t<double>(plan, ws, patch, sigma, dx, dy, fx, fy, fz, st);
+    return uniform_solve_t<float>(plan, ws, patch, sigma, dx, dy, fx, fy, fz, st);
 }

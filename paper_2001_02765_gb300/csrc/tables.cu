@@ -88,17 +88,71 @@ __device__ void unit_kernels(int m, int n, double *out6)
     out6[5] = b.xx;                    // K^{y,y}(m,n) = K^{x,x}(n,m)
 }
 
+// ---- off the plane: unit-h kernels at height zeta = z / h != 0 ----
+//   K^{x,0} = -dd asinh(v / rho_u),  rho_u = sqrt(u^2 + zeta^2)
+//   K^{x,x} = -m K^{x,0} + dd[v asinh(u / rho_v)] - |zeta| dd atan(u v / (|zeta| r))
+//   K^{x,y} = -n K^{x,0} - dd r,  r = sqrt(u^2 + v^2 + zeta^2)
+//   K^{z,0} = -sgn(zeta) dd atan(u v / (|zeta| r)),  K^{z,x} = -m K^{z,0} - zeta K^{x,0}
+// (the u-only and v-only parts of ln(v + r) and v ln(u + r) cancel in the double
+// differences, as in the plane).
+struct k5 {
+    double x0, xx, xy, z0, zx;
+};
+
+__device__ k5 unit_kernels_pos_z(int m, int n, double zeta)
+{
+    const double u1 = m - 0.5, u2 = m + 0.5, v1 = n - 0.5, v2 = n + 0.5;
+    const double z2 = zeta * zeta, az = fabs(zeta);
+    k5 k;
+    k.x0 = m == 0 ? 0.0 : asinh_span(v1, v2, sqrt(u1 * u1 + z2)) - asinh_span(v1, v2, sqrt(u2 * u2 + z2));
+    const double r22 = sqrt(u2 * u2 + v2 * v2 + z2), r12 = sqrt(u1 * u1 + v2 * v2 + z2);
+    const double r21 = sqrt(u2 * u2 + v1 * v1 + z2), r11 = sqrt(u1 * u1 + v1 * v1 + z2);
+    const double solid = atan(u2 * v2 / (az * r22)) - atan(u1 * v2 / (az * r12)) - atan(u2 * v1 / (az * r21)) +
+                         atan(u1 * v1 / (az * r11));
+    const double psi = v2 * asinh_span(u1, u2, sqrt(v2 * v2 + z2)) - v1 * asinh_span(u1, u2, sqrt(v1 * v1 + z2));
+    k.xx = -(double)m * k.x0 + psi - az * solid;
+    if (m == 0 || n == 0) {
+        k.xy = 0.0;
+    } else {
+        const double ddr = (u2 + u1) / (r22 + r12) - (u2 + u1) / (r21 + r11);
+        k.xy = -(double)n * k.x0 - ddr;
+    }
+    k.z0 = (zeta > 0.0 ? -1.0 : 1.0) * solid;
+    k.zx = -(double)m * k.z0 - zeta * k.x0;
+    return k;
+}
+
+// All nine unit-h kernels at offset (m, n), height zeta:
+// x0 xx xy y0 yx yy z0 zx zy.
+__device__ void unit_kernels_z(int m, int n, double zeta, double *out9)
+{
+    const int am = m < 0 ? -m : m, an = n < 0 ? -n : n;
+    const double sm = m < 0 ? -1.0 : 1.0, sn = n < 0 ? -1.0 : 1.0;
+    k5 a = unit_kernels_pos_z(am, an, zeta);
+    k5 b = unit_kernels_pos_z(an, am, zeta);
+    out9[0] = sm * a.x0;
+    out9[1] = a.xx;
+    out9[2] = sm * sn * a.xy;
+    out9[3] = sn * b.x0;
+    out9[4] = sm * sn * b.xy;
+    out9[5] = b.xx;
+    out9[6] = a.z0;          // even in m and n
+    out9[7] = sm * a.zx;     // odd in m, even in n
+    out9[8] = sn * b.zx;     // even in m, odd in n
+}
+
 // Unwrapped table of one kernel, physical units, [(2ny-1)][(2nx-1)].
-__global__ void k_table_unwrapped(double *out, int nx, int ny, double h, int which)
+__global__ void k_table_unwrapped(double *out, int nx, int ny, double h, double zeta, int which)
 {
     const int w = 2 * nx - 1, hgt = 2 * ny - 1;
     const int64_t total = (int64_t)w * hgt;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int col = (int)(e % w), row = (int)(e / w);
-        double k6[6];
-        unit_kernels(col - (nx - 1), row - (ny - 1), k6);
-        const double scale = (which == 0 || which == 3) ? 1.0 : h;
-        out[e] = scale * k6[which];
+        double k9[9];
+        if (zeta == 0.0) unit_kernels(col - (nx - 1), row - (ny - 1), k9);
+        else unit_kernels_z(col - (nx - 1), row - (ny - 1), zeta, k9);
+        const double scale = (which == 0 || which == 3 || which == 6) ? 1.0 : h;
+        out[e] = scale * k9[which];
     }
 }
 
@@ -120,6 +174,26 @@ __global__ void k_tables_wrapped(double2 *z, int nx, int ny, int px, int py)
     }
 }
 
+// Off the plane: five packed planes, z0..z2 as above and
+// z3 = Kr^zx + i Kr^zy, z4 = Kr^z0.
+__global__ void k_tables_wrapped_z(double2 *z, int nx, int ny, int px, int py, double zeta)
+{
+    const int64_t plane = (int64_t)px * py;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % px), b = (int)(e / px);
+        const int ex = a < px / 2 ? a : a - px;
+        const int ey = b < py / 2 ? b : b - py;
+        const int m = -ex, n = -ey;  // Kr[e] = K[-e]
+        double k9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (m <= nx - 1 && m >= -(nx - 1) && n <= ny - 1 && n >= -(ny - 1)) unit_kernels_z(m, n, zeta, k9);
+        z[e] = make_double2(k9[0], k9[3]);
+        z[plane + e] = make_double2(k9[1], k9[2]);
+        z[2 * plane + e] = make_double2(k9[5], k9[4]);
+        z[3 * plane + e] = make_double2(k9[7], k9[8]);
+        z[4 * plane + e] = make_double2(k9[6], 0.0);
+    }
+}
+
 // In-place complex FFT along rows (stride 1) or columns (stride = row length)
 // of `count` sequences of length L, one sequence per CTA, FP64.
 template <int L>
@@ -136,14 +210,14 @@ __global__ void __launch_bounds__(L / 8 >= 64 ? L / 8 : 64) k_fft_lines(double2 
 }
 
 template <typename T>
-__global__ void k_extract_spectra(const double2 *z, T *planes, int px, int py, double scale0, double scale1)
+__global__ void k_extract_spectra(const double2 *z, T *planes, int px, int py, double scale0, double scale1, int nplanes)
 {
     const int qx = px / 2 + 1, qy = py / 2 + 1, qs = sg_spec_stride(py);
     const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qs;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
         const int kx = (int)(e / qs), ky = (int)(e % qs);  // planes are [kx][ky], row stride qs
         if (ky >= qy) {
-            for (int c = 0; c < 6; ++c) planes[c * qplane + e] = (T)0;
+            for (int c = 0; c < nplanes; ++c) planes[c * qplane + e] = (T)0;
             continue;
         }
         const int64_t src = (int64_t)ky * px + kx;          // z is [ky][kx]
@@ -156,6 +230,13 @@ __global__ void k_extract_spectra(const double2 *z, T *planes, int px, int py, d
         planes[2 * qplane + e] = (T)(scale1 * z1.y);   // c
         planes[4 * qplane + e] = (T)(scale1 * z2.x);   // e
         planes[5 * qplane + e] = (T)(scale1 * z2.y);   // f
+        if (nplanes == 9) {
+            // z3 = Kzx^ + i Kzy^ = i hh + i (i kk) = -kk + i hh ; z4 = Kz0^ = g
+            const double2 z3 = z[3 * plane + src], z4 = z[4 * plane + src];
+            planes[6 * qplane + e] = (T)(scale0 * z4.x);   // g
+            planes[7 * qplane + e] = (T)(scale1 * z3.y);   // hh
+            planes[8 * qplane + e] = (T)(-scale1 * z3.x);  // kk
+        }
     }
 }
 
@@ -227,18 +308,21 @@ sg_status sg_tables_build(sg_plan *plan)
         int64_t pl = (int64_t)d.px * d.py;
         if (pl > maxplane) maxplane = pl;
     }
+    const bool offplane = plan->geom.z != 0.0;
+    const int npacked = offplane ? 5 : 3;
     double2 *z = nullptr;
-    SG_CUDA_TRY(cudaMalloc(&z, (size_t)(3 * maxplane * sizeof(double2))));
+    SG_CUDA_TRY(cudaMalloc(&z, (size_t)(npacked * maxplane * sizeof(double2))));
     sg_status st = SG_OK;
     for (int p = 0; p < plan->npatches && st == SG_OK; ++p) {
         sg_patch_plan &pp = plan->pp[p];
         const int px = pp.d.px, py = pp.d.py;
         const int64_t plane = (int64_t)px * py;
-        k_tables_wrapped<<<1024, 256>>>(z, pp.d.nx, pp.d.ny, px, py);
+        if (offplane) k_tables_wrapped_z<<<1024, 256>>>(z, pp.d.nx, pp.d.ny, px, py, plan->geom.z / pp.d.h);
+        else k_tables_wrapped<<<1024, 256>>>(z, pp.d.nx, pp.d.ny, px, py);
         if (cudaGetLastError() != cudaSuccess) { st = SG_ECUDA; break; }
         const double2 *twx = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(px)]);
         const double2 *twy = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(py)]);
-        for (int q = 0; q < 3 && st == SG_OK; ++q) {
+        for (int q = 0; q < npacked && st == SG_OK; ++q) {
             double2 *zq = z + q * plane;
             st = launch_fft_lines(zq, px, py, px, 1, twx);       // rows
             if (st == SG_OK) st = launch_fft_lines(zq, py, px, 1, px, twy);   // columns
@@ -246,10 +330,11 @@ sg_status sg_tables_build(sg_plan *plan)
         if (st != SG_OK) break;
         const double scale0 = plan->geom.G / ((double)px * (double)py);
         const double scale1 = scale0 * pp.d.h;
+        const int nplanes = offplane ? 9 : 6;
         if (plan->prec == SG_FP64)
-            k_extract_spectra<double><<<1024, 256>>>(z, (double *)pp.spectra, px, py, scale0, scale1);
+            k_extract_spectra<double><<<1024, 256>>>(z, (double *)pp.spectra, px, py, scale0, scale1, nplanes);
         else
-            k_extract_spectra<float><<<1024, 256>>>(z, (float *)pp.spectra, px, py, scale0, scale1);
+            k_extract_spectra<float><<<1024, 256>>>(z, (float *)pp.spectra, px, py, scale0, scale1, nplanes);
         if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
     }
     cudaError_t e = cudaDeviceSynchronize();
@@ -307,13 +392,17 @@ sg_status sg_phase_build(sg_plan *plan)
 
 sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host_out, size_t n)
 {
-    if (!plan || !host_out || patch < 0 || patch >= plan->npatches || which < 0 || which > 5) return SG_EINVAL;
+    const int maxw = plan && plan->geom.z != 0.0 ? 8 : 5;
+    if (!plan || !host_out || patch < 0 || patch >= plan->npatches || which < 0 || which > maxw) {
+        sg_set_last_error_message("sg_kernel_tables: no such patch or table (0..5, and 6..8 for z != 0)");
+        return SG_EINVAL;
+    }
     const sg_patch_dev &d = plan->pp[patch].d;
     const size_t need = (size_t)(2 * d.nx - 1) * (size_t)(2 * d.ny - 1);
     if (n < need) return SG_EINVAL;
     double *tmp = nullptr;
     SG_CUDA_TRY(cudaMalloc(&tmp, need * sizeof(double)));
-    k_table_unwrapped<<<1024, 256>>>(tmp, d.nx, d.ny, d.h, which);
+    k_table_unwrapped<<<1024, 256>>>(tmp, d.nx, d.ny, d.h, plan->geom.z / d.h, which);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(host_out, tmp, need * sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(tmp);

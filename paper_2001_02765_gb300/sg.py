@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsg.so")
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_EBUDGET, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_ECANCELLED, SG_ENOTFOUND = range(9)
 SG_FP64, SG_FP32 = 0, 1
 SG_SLOPES_NONE, SG_SLOPES_CENTRAL, SG_SLOPES_CALLER = 0, 1, 2
-KERNEL_NAMES = ("x0", "xx", "xy", "y0", "yx", "yy")
+KERNEL_NAMES = ("x0", "xx", "xy", "y0", "yx", "yy", "z0", "zx", "zy")
 
 
 class SgLibraryMissing(ImportError):
@@ -42,7 +42,7 @@ class sg_patch(ctypes.Structure):
 
 class sg_geom(ctypes.Structure):
     _fields_ = [("npatches", ctypes.c_int), ("patches", ctypes.POINTER(sg_patch)),
-                ("G", ctypes.c_double), ("slope_mode", ctypes.c_int)]
+                ("G", ctypes.c_double), ("slope_mode", ctypes.c_int), ("z", ctypes.c_double)]
 
 
 class sg_plan_info(ctypes.Structure):
@@ -70,6 +70,7 @@ _SIGNATURES = {
     "sg_kernel_tables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "sg_force": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_force_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_force3": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "sg_direct_force_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -135,29 +136,29 @@ def _check(status, where):
         raise SgError(status, where, last_error())
 
 
-def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER):
+def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0):
     """patches: iterable of (level, nx, ny, x0, y0, h). Returns (sg_geom, keepalive array)."""
     patches = list(patches)
     arr = (sg_patch * len(patches))(*[sg_patch(int(p[0]), int(p[1]), int(p[2]), float(p[3]), float(p[4]), float(p[5]))
                                       for p in patches])
-    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode))
+    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode), float(z))
     return g, arr
 
 
-def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER):
-    g, _keep = make_geom(patches, G, slope_mode)
+def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0):
+    g, _keep = make_geom(patches, G, slope_mode, z)
     return load().sg_geom_validate(ctypes.byref(g))
 
 
-def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER):
-    g, _keep = make_geom(patches, G, slope_mode)
+def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0):
+    g, _keep = make_geom(patches, G, slope_mode, z)
     out = ctypes.c_int64(0)
     _check(load().sg_plan_bytes(ctypes.byref(g), int(precision), ctypes.byref(out)), "sg_plan_bytes")
     return int(out.value)
 
 
-def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0):
-    g, _keep = make_geom(patches, G, slope_mode)
+def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0):
+    g, _keep = make_geom(patches, G, slope_mode, z)
     h = _VP()
     _check(load().sg_plan_create(ctypes.byref(g), int(precision), int(hbm_budget), ctypes.byref(h)), "sg_plan_create")
     return h.value
@@ -186,6 +187,12 @@ def sg_force(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
     """Raw device pointers (ints); enqueues one solve on the stream."""
     _check(load().sg_force(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr, stream_ptr or None),
            "sg_force")
+
+
+def sg_force3(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, fz_ptr, stream_ptr=0):
+    """Raw device pointers (ints); enqueues a solve with Fz."""
+    _check(load().sg_force3(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr, fz_ptr,
+                            stream_ptr or None), "sg_force3")
 
 
 def sg_force_host(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
@@ -290,12 +297,13 @@ class Plan:
     row-major arrays concatenated (length ``ncells``).
     """
 
-    def __init__(self, patches, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0):
+    def __init__(self, patches, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0):
         self.patches = [tuple(p) for p in patches]
         self.precision = SG_FP32 if precision in ("fp32", SG_FP32) else SG_FP64
         self.slope_mode = slope_mode
         self.G = G
-        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget)
+        self.z = z
+        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget, z)
         self.info = sg_plan_get_info(self.handle)
 
     @property
@@ -345,6 +353,19 @@ class Plan:
         sg_force(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
                  dy.data_ptr() if dy is not None else 0, fx.data_ptr(), fy.data_ptr(), st)
         return fx, fy
+
+    def force3(self, sigma, dx=None, dy=None, stream=None):
+        """Enqueue a solve with Fz (see sg_force3); returns (fx, fy, fz)."""
+        import torch
+        dt = self._torch_dtype()
+        for t in (sigma, dx, dy):
+            if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() != self.ncells):
+                raise ValueError("fields must be contiguous %s CUDA tensors of %d elements" % (dt, self.ncells))
+        fx, fy, fz = (torch.empty_like(sigma) for _ in range(3))
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        sg_force3(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
+                  dy.data_ptr() if dy is not None else 0, fx.data_ptr(), fy.data_ptr(), fz.data_ptr(), st)
+        return fx, fy, fz
 
     def force_host(self, sigma, dx=None, dy=None, fx=None, fy=None, stream=None):
         """Solve from host arrays (numpy, or pinned torch CPU tensors); returns host (fx, fy)."""
