@@ -58,6 +58,15 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
             batch_free(b);
             return a;
         }
+        // the members already run side by side: keep each member's work on its own branch
+        sg_workspace &w = b->ws[i];
+        if (w.aux) {
+            cudaStreamDestroy(w.aux);
+            cudaEventDestroy(w.ev_fork);
+            cudaEventDestroy(w.ev_join);
+            w.aux = nullptr;
+            w.ev_fork = w.ev_join = nullptr;
+        }
     }
     // capture: root stream -> one branch per member -> join
     std::vector<cudaStream_t> streams(n + 1, nullptr);

@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T>
 }
 
 // Shared-memory layout of the column kernels: the padded FFT buffer, then the
-// kernel spectra of the CTA's columns, [CB][6][sg_spec_stride(PY)] of T, which
-// one thread fetches with 1-D bulk copies (TMA) at kernel start so that they
-// arrive while the forward transform runs.
+// kernel spectra of the CTA's columns, [planes][CB][sg_spec_stride(PY)] of T,
+// which one thread fetches with one 1-D bulk copy (TMA) per plane at kernel
+// start so that they arrive while the forward transform runs.
 template <typename T, int PY, int CB>
 __host__ __device__ constexpr int col_buf_bytes() { return (spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15; }
 template <typename T, int PY, int CB, int NPL = 6>
@@ -137,9 +137,9 @@ __device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec
     const int ncol = qx - kx0 < CB ? qx - kx0 : CB;
     const int64_t qplane = (int64_t)qx * QS;
     mbar_arrive_expect_tx(bar, (uint32_t)(ncol * NPL * QS * sizeof(T)));
-    for (int c = 0; c < ncol; ++c)
-        for (int p = 0; p < NPL; ++p)
-            bulk_copy_g2s(ssp + (c * NPL + p) * QS, spec + p * qplane + (int64_t)(kx0 + c) * QS, QS * sizeof(T), bar);
+    // the CTA's columns are consecutive rows of every plane: one copy per plane
+    for (int p = 0; p < NPL; ++p)
+        bulk_copy_g2s(ssp + p * CB * QS, spec + p * qplane + (int64_t)kx0 * QS, ncol * QS * sizeof(T), bar);
 }
 
 // Bounded wait for the spectra; on timeout records the error, gives the copies
@@ -205,33 +205,33 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
             const bool lower = ky <= PY / 2;
             const int kq = lower ? ky : PY - ky;
             const T sg = lower ? (T)1 : (T)-1;
-            const T *sp = ssp + c * NPL * QS + kq;
+            const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
             const C X = buf[spad<C>(e)];
             if (f == 0) {
-                const T a = sp[0 * QS];
-                const T d = sg * sp[3 * QS];
+                const T a = sp[0 * CB * QS];
+                const T d = sg * sp[3 * CB * QS];
                 accx[q] = cmake<C>(-a * X.y, a * X.x);
                 accy[q] = cmake<C>(-d * X.y, d * X.x);
                 if constexpr (NOUT == 3) {
-                    const T g = sp[6 * QS];  // real: sigma^ g
+                    const T g = sp[6 * CB * QS];  // real: sigma^ g
                     accz[q] = cmake<C>(g * X.x, g * X.y);
                 }
             } else if (f == 1) {
-                const T b = sp[1 * QS];
-                const T ff = sg * sp[5 * QS];
+                const T b = sp[1 * CB * QS];
+                const T ff = sg * sp[5 * CB * QS];
                 accx[q] = cmake<C>(accx[q].x + b * X.x, accx[q].y + b * X.y);
                 accy[q] = cmake<C>(accy[q].x + ff * X.x, accy[q].y + ff * X.y);
                 if constexpr (NOUT == 3) {
-                    const T hh = sp[7 * QS];  // imaginary: deltax^ (i hh)
+                    const T hh = sp[7 * CB * QS];  // imaginary: deltax^ (i hh)
                     accz[q] = cmake<C>(accz[q].x - hh * X.y, accz[q].y + hh * X.x);
                 }
             } else {
-                const T cc = sg * sp[2 * QS];
-                const T ee = sp[4 * QS];
+                const T cc = sg * sp[2 * CB * QS];
+                const T ee = sp[4 * CB * QS];
                 accx[q] = cmake<C>(accx[q].x + cc * X.x, accx[q].y + cc * X.y);
                 accy[q] = cmake<C>(accy[q].x + ee * X.x, accy[q].y + ee * X.y);
                 if constexpr (NOUT == 3) {
-                    const T kk = sg * sp[8 * QS];  // imaginary, odd in ky: deltay^ (i s kk)
+                    const T kk = sg * sp[8 * CB * QS];  // imaginary, odd in ky: deltay^ (i s kk)
                     accz[q] = cmake<C>(accz[q].x - kk * X.y, accz[q].y + kk * X.x);
                 }
             }
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
         const bool lower = ky <= PY / 2;
         const int kq = lower ? ky : PY - ky;
         const T sg = lower ? (T)1 : (T)-1;
-        const T *sp = ssp + c * 6 * QS + kq;
+        const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
         const C S = buf[spad<C>(e)];
         // slope spectra
         const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
@@ -384,12 +384,12 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
         const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
         const C X = csub(cadd(cmake<C>(-cs * S.y, cs * S.x), cmul(e2, c1)), cmul(e1, c0));
         const C Y = csub(cadd(cmake<C>(-rs * S.y, rs * S.x), cmul(f2, rows[c][1])), cmul(f1, rows[c][0]));
-        const T a = sp[0 * QS];
-        const T b = sp[1 * QS];
-        const T cc = sg * sp[2 * QS];
-        const T d = sg * sp[3 * QS];
-        const T ee = sp[4 * QS];
-        const T ff = sg * sp[5 * QS];
+        const T a = sp[0 * CB * QS];
+        const T b = sp[1 * CB * QS];
+        const T cc = sg * sp[2 * CB * QS];
+        const T d = sg * sp[3 * CB * QS];
+        const T ee = sp[4 * CB * QS];
+        const T ff = sg * sp[5 * CB * QS];
         accx[q] = cmake<C>(-a * S.y + b * X.x + cc * Y.x, a * S.x + b * X.y + cc * Y.y);
         accy[q] = cmake<C>(-d * S.y + ee * Y.x + ff * X.x, d * S.x + ee * Y.y + ff * X.y);
     }
