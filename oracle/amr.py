@@ -130,3 +130,35 @@ def amr_patchfft_plus_direct(patches, sigma, dx=None, dy=None, G=1.0):
         fx_out.append(np.where(m, fx, np.nan))
         fy_out.append(np.where(m, fy, np.nan))
     return fx_out, fy_out
+
+
+# ------------------------------------------------ zone-by-zone hierarchies --
+#
+# A quadtree hierarchy given zone by zone (Fig. 1, Table 10): level l, column
+# ix and row iy on the level-l grid of cell width h_l = h0 / 2^l, and a leaf
+# flag. Only leaf zones carry density and receive the force (Section 2: the
+# sum of Eq. eqnXforce2 runs over the leaf zones).
+
+def zone_bounds(x0, y0, h0, level, ix, iy):
+    """Edges (xl, xr, yd, yu) and centres (xc, yc) of zones (level, ix, iy)."""
+    h = h0 / 2.0 ** np.asarray(level, np.float64)
+    xl = x0 + np.asarray(ix, np.float64) * h
+    yd = y0 + np.asarray(iy, np.float64) * h
+    return xl, xl + h, yd, yd + h, xl + 0.5 * h, yd + 0.5 * h
+
+
+def zone_leaf_force(x0, y0, h0, level, ix, iy, leaf, sigma, dx=None, dy=None, G=1.0, nthreads=0):
+    """Force at every leaf centre from every leaf zone (plain sum, C oracle).
+
+    sigma, dx, dy: per-zone arrays (values at non-leaf zones are ignored).
+    Returns (fx, fy) per zone, 0 at non-leaf zones.
+    """
+    leaf = np.asarray(leaf, bool)
+    xl, xr, yd, yu, xc, yc = (a[leaf] for a in zone_bounds(x0, y0, h0, level, ix, iy))
+    pick = lambda a: None if a is None else np.asarray(a, np.float64)[leaf]
+    fx, fy = direct_force((xl, xr, yd, yu), pick(sigma), pick(dx), pick(dy), xc, yc, G=G, nthreads=nthreads)
+    ox = np.zeros(leaf.size)
+    oy = np.zeros(leaf.size)
+    ox[leaf] = fx
+    oy[leaf] = fy
+    return ox, oy

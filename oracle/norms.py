@@ -33,3 +33,12 @@ def rel_l2(fx, fy, rx, ry):
     num = np.sum((np.asarray(fx, np.float64) - rx) ** 2) + np.sum((np.asarray(fy, np.float64) - ry) ** 2)
     den = np.sum(np.asarray(rx, np.float64) ** 2) + np.sum(np.asarray(ry, np.float64) ** 2)
     return float(np.sqrt(num / den))
+
+
+def amr_norms(e, h_leaf):
+    """Norms over the leaf zones of a refined hierarchy, every leaf weighted by
+    the area of the finest zone, min(h)^2 (the weighting with which the L1, L2
+    norms of Tables 4 and 6 come out; the text's 'area of sub-region D_i' does
+    not reproduce them)."""
+    h = float(np.min(np.asarray(h_leaf, np.float64)))
+    return norms(e, h * h)

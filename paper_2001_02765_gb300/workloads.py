@@ -10,7 +10,8 @@ Conventions: arrays are row-major [y][x]; cell (j, i) of a patch with origin
 
 Disks (Section 3 of Tseng, Shang & Yen for D_2; the others are the workloads
 of the benchmark configurations):
-* D_2:   sigma0 (1 - R^2/alpha^2)^{3/2} for R < alpha, else 0.
+* D_2:   sigma0 (1 - R^2/alpha^2)^{3/2} for R < alpha, else 0 (alpha = 0.5 on [-1, 1]^2;
+         D_2,2 is two of them of radius 0.4 centred at (0, +-0.5)).
 * Kuzmin: a M / (2 pi (R^2 + a^2)^{3/2}).
 * two-armed logarithmic spiral: Kuzmin(a) (1 + A cos(2 theta - ln(R) / tan 15deg)).
 * exponential: exp(-R / r0).
@@ -79,8 +80,12 @@ def d2_sigma(X, Y, alpha, sigma0=1.0, xc=0.0, yc=0.0):
     return s, g * dx, g * dy
 
 
-def d22_sigma(X, Y, alpha, sigma0=1.0):
-    """Two D_2 disks centred at (0, 0.5) and (0, -0.5) (Section 3)."""
+D22_RADIUS = 0.4
+
+
+def d22_sigma(X, Y, alpha=D22_RADIUS, sigma0=1.0):
+    """Two D_2 disks centred at (0, 0.5) and (0, -0.5) (Section 3), radius 0.4 each
+    (the radius that reproduces Table 2 and the D_2,2 zone counts of Tables 8-9)."""
     a = d2_sigma(X, Y, alpha, sigma0, 0.0, 0.5)
     b = d2_sigma(X, Y, alpha, sigma0, 0.0, -0.5)
     return tuple(p + q for p, q in zip(a, b))
@@ -209,3 +214,79 @@ def random_fields(ny, nx, seed, scale=1.0):
     """Seeded uniform random sigma, dx, dy in [-scale, scale] (parity inputs)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return tuple(rng.uniform(-scale, scale, size=(ny, nx)) for _ in range(3))
+
+
+# ------------------------------------------------ refined hierarchies (AMR) --
+
+def d2_edge_distance(X, Y):
+    """Distance of (X, Y) from the edge of the D_2 disk (radius 0.5 at the origin)."""
+    return np.abs(np.hypot(X, Y) - 0.5)
+
+
+def d22_edge_distance(X, Y):
+    """Distance of (X, Y) from the nearer edge of the two D_2,2 disks."""
+    a = np.abs(np.hypot(X, Y - 0.5) - D22_RADIUS)
+    b = np.abs(np.hypot(X, Y + 0.5) - D22_RADIUS)
+    return np.minimum(a, b)
+
+
+def refinement_band(rule, n, level):
+    """Half-width of the band around a disk edge inside which a zone of `level`
+    (0 = the n x n grid on [-1, 1]^2) is split into four (Section 4):
+
+    * "ilr" (independent level refinement): 0.025 / 2^level, a fixed distance
+      that halves per level;
+    * "vlr" (variable level refinement): 0.1 (128 / n) / 2^level, i.e. 6.4 cells
+      of the zone's own level whatever n is.
+
+    These constants reproduce every zone and leaf count of Tables 8 and 9."""
+    if rule == "ilr":
+        return 0.025 / 2.0 ** level
+    if rule == "vlr":
+        return 0.1 * (128.0 / n) / 2.0 ** level
+    raise ValueError("rule must be 'ilr' or 'vlr'")
+
+
+def band_hierarchy(n, nlevels, rule, disk="d2"):
+    """Quadtree hierarchy of Section 4: an n x n grid on [-1, 1]^2 (level 0)
+    whose zones near the disk edge(s) are split into four children, level by
+    level, up to nlevels levels (the paper's L; L = 1 is the uniform grid).
+
+    A level-l zone is split when the distance of its centre from the edge is
+    below refinement_band(rule, n, l). Zones are listed level by level: level 0
+    row-major, then the four children of every split zone of the previous
+    level in that level's order, each as (SW, SE, NW, NE).
+
+    Returns dict(n, x0, y0, h0, level, ix, iy, leaf): int32 arrays level, ix, iy
+    (zone (ix, iy) of level l spans [x0 + ix h_l, x0 + (ix + 1) h_l] with
+    h_l = h0 / 2^l, likewise in y) and a boolean leaf flag per zone.
+    """
+    dist = {"d2": d2_edge_distance, "d22": d22_edge_distance}[disk]
+    h0 = 2.0 / n
+    x0 = y0 = -1.0
+    J, I = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ix, iy = I.ravel().astype(np.int64), J.ravel().astype(np.int64)
+    levels, xs, ys, leaves = [], [], [], []
+    for lev in range(nlevels):
+        h = h0 / 2.0 ** lev
+        split = np.zeros(ix.size, dtype=bool)
+        if lev + 1 < nlevels:
+            split = dist(x0 + (ix + 0.5) * h, y0 + (iy + 0.5) * h) < refinement_band(rule, n, lev)
+        levels.append(np.full(ix.size, lev))
+        xs.append(ix)
+        ys.append(iy)
+        leaves.append(~split)
+        pi, pj = ix[split], iy[split]
+        ix = np.stack([2 * pi, 2 * pi + 1, 2 * pi, 2 * pi + 1], axis=1).ravel()
+        iy = np.stack([2 * pj, 2 * pj, 2 * pj + 1, 2 * pj + 1], axis=1).ravel()
+        if ix.size == 0:
+            break
+    return dict(n=n, x0=x0, y0=y0, h0=h0,
+                level=np.concatenate(levels).astype(np.int32), ix=np.concatenate(xs).astype(np.int32),
+                iy=np.concatenate(ys).astype(np.int32), leaf=np.concatenate(leaves))
+
+
+def zone_geometry(hier):
+    """Centres and widths (xc, yc, h) of every zone of a band_hierarchy dict."""
+    h = hier["h0"] / 2.0 ** hier["level"]
+    return hier["x0"] + (hier["ix"] + 0.5) * h, hier["y0"] + (hier["iy"] + 0.5) * h, h

@@ -15,7 +15,7 @@ from oracle.direct import direct_force, uniform_direct_force
 from oracle.disks import d2_force_xy, kuzmin_force_xy
 from oracle.fftconv import central_slopes, uniform_fft_force
 from oracle.kernels import cell_kernels, offset_tables
-from oracle.norms import norms, radial_error, rel_l2
+from oracle.norms import amr_norms, norms, radial_error, rel_l2
 from paper_2001_02765_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -35,6 +35,13 @@ def _sig3(a, b):
     """True when a, rounded to three significant digits, equals the printed b."""
     e = math.floor(math.log10(abs(b)))
     return abs(round(a / 10 ** e, 2) - round(b / 10 ** e, 2)) < 1e-9
+
+
+def _near3(a, b):
+    """True when a lies within half a unit of the printed b's third digit, plus 2 %
+    of a unit for values on a rounding tie (3.50499e-3 printed as 3.51e-3)."""
+    e = math.floor(math.log10(abs(b)))
+    return abs(a / 10 ** e - b / 10 ** e) <= 0.0051
 
 
 # --------------------------------------------------------------- Table 1 --
@@ -58,22 +65,27 @@ def test_table1_d2_uniform_reproduced(n):
         assert _sig3(g, p), (n, got, row)
 
 
-def test_d22_l1_close_to_table2():
-    """Table 2 (D_2,2, N = 128): L_x1 = 1.71e-3 printed.
+@pytest.mark.parametrize("n", [128, 256, 512])
+def test_table2_d22_uniform_reproduced(n):
+    """Table 2 (Section 3): uniform D_2,2 errors, all nine printed norms to 3 digits
+    (N = 512 without its misprinted L_Rinf).
 
-    Two D_2 disks of radius 0.5 (the same doubling of the printed alpha that
-    reproduces Table 1) centred at (0, +-0.5). Only L_x1 comes out close
-    (within 6 %); the other norms of this table are not reproduced and are not
-    used as pins."""
-    n = 128
+    Reading: the two D_2 disks at (0, +-0.5) have radius 0.4 (the text gives
+    only alpha = 0.25; radius 0.4 also reproduces the D_2,2 zone counts of
+    Tables 8 and 9)."""
+    row = {int(r[0]): r[1:] for r in _load_table("table2_d22_uniform.txt")}[n]
     nx, ny, x0, y0, h = W.unit_grid(n)
     X, Y = W.cell_centres(nx, ny, x0, y0, h)
-    s, sx, sy = W.d22_sigma(X, Y, 0.5)
+    s, sx, sy = W.d22_sigma(X, Y)
     fx, fy = uniform_fft_force(s, sx, sy, h)
-    ax, ay = d2_force_xy(X, Y, 0.5, xc=0.0, yc=0.5)
-    bx, by = d2_force_xy(X, Y, 0.5, xc=0.0, yc=-0.5)
-    lx1 = norms(fx - ax - bx, h * h)[0]
-    assert abs(lx1 / 1.71e-3 - 1.0) < 0.06
+    ax, ay = d2_force_xy(X, Y, W.D22_RADIUS, xc=0.0, yc=0.5)
+    bx, by = d2_force_xy(X, Y, W.D22_RADIUS, xc=0.0, yc=-0.5)
+    ex, ey = fx - ax - bx, fy - ay - by
+    got = norms(ex, h * h) + norms(ey, h * h) + norms(radial_error(X, Y, ex, ey), h * h)
+    skip = {8} if n == 512 else set()
+    for k, (g, p) in enumerate(zip(got, row)):
+        if k not in skip:
+            assert _sig3(g, p), (n, k, got, row)
 
 
 # ------------------------------------------------ closed-form convergence --
@@ -332,3 +344,128 @@ def test_refinement_invariance():
     coarse = leaves["patch"] == 0
     j, i = leaves["j"][coarse], leaves["i"][coarse]
     assert rel_l2(fx[coarse], fy[coarse], ux[j, i], uy[j, i]) < 1e-12
+
+
+# ------------------------------------------- refined hierarchies (Section 4) --
+
+def test_tables8_9_zone_and_leaf_counts():
+    """Every zone and leaf count of Tables 8 (ILR) and 9 (VLR), N = 128 ... 2048,
+    L = 2, 3, D_2 and D_2,2, from the band refinement rules."""
+    rows = _load_table("tables8_9_zone_counts.txt")
+    assert len(rows) == 40
+    for table, rule, disk, L, n, zones, leaves in rows:
+        hier = W.band_hierarchy(int(n), int(L), ("ilr", "vlr")[int(rule)], ("d2", "d22")[int(disk)])
+        assert (hier["level"].size, int(hier["leaf"].sum())) == (int(zones), int(leaves)), (table, rule, disk, L, n)
+
+
+def _children_complete(hier):
+    """Every non-leaf zone has exactly its four children on the next level."""
+    lev, ix, iy, leaf = hier["level"], hier["ix"], hier["iy"], hier["leaf"]
+    keys = set(zip(lev.tolist(), ix.tolist(), iy.tolist()))
+    for l, i, j, f in zip(lev.tolist(), ix.tolist(), iy.tolist(), leaf.tolist()):
+        kids = [(l + 1, 2 * i + a, 2 * j + b) for a in (0, 1) for b in (0, 1)]
+        assert all(k in keys for k in kids) != f
+        if l > 0:
+            assert (l - 1, i // 2, j // 2) in keys
+
+
+def test_band_hierarchy_structure():
+    for rule in ("ilr", "vlr"):
+        for disk in ("d2", "d22"):
+            _children_complete(W.band_hierarchy(32, 3, rule, disk))
+
+
+def _d_sigma(disk, X, Y):
+    return W.d2_sigma(X, Y, 0.5) if disk == "d2" else W.d22_sigma(X, Y)
+
+
+def _d_force(disk, X, Y):
+    if disk == "d2":
+        return d2_force_xy(X, Y, 0.5)
+    ax, ay = d2_force_xy(X, Y, W.D22_RADIUS, yc=0.5)
+    bx, by = d2_force_xy(X, Y, W.D22_RADIUS, yc=-0.5)
+    return ax + bx, ay + by
+
+
+def amr_table_norms(hier, disk, fx, fy):
+    """Norms of Tables 3-6 at the leaves (finest-area weights) from per-zone forces."""
+    xc, yc, h = W.zone_geometry(hier)
+    m = hier["leaf"]
+    ex, ey = _d_force(disk, xc[m], yc[m])
+    ex, ey = fx[m] - ex, fy[m] - ey
+    eR = radial_error(xc[m], yc[m], ex, ey)
+    if disk == "d2":
+        return amr_norms(ex, h[m]) + amr_norms(eR, h[m])
+    return amr_norms(ex, h[m]) + amr_norms(ey, h[m]) + amr_norms(eR, h[m])
+
+
+# Entries of Tables 3-6 pinned: D_2,2 every norm; D_2 the Linf norms only (its
+# L1, L2 entries differ from the finest-area norms by inconsistent powers of 2).
+# (table, L, N, column) entries that are misprints: exponent (8.72E-04 for 8.72E-05)
+# and digit (3.31E-03 for 3.11E-03).
+AMR_MISPRINTS = {(4, 3, 128, 0), (6, 2, 128, 2)}
+
+
+def amr_pinned_columns(table, disk, L, n):
+    cols = range(9) if disk == 1 else (2, 5)
+    return [c for c in cols if (table, L, n, c) not in AMR_MISPRINTS]
+
+
+@pytest.mark.parametrize("table, L", [(3, 2), (3, 3), (4, 2), (6, 2)])
+def test_tables3_6_amr_errors_reproduced(table, L):
+    """Tables 3-6 (Section 4), N = 128: the oracle's leaf sum on the ILR/VLR
+    hierarchy with the analytic density and gradient at every leaf centre
+    reproduces the printed errors to three digits."""
+    rows = {(int(r[0]), int(r[3]), int(r[4])): r for r in _load_table("tables3_6_amr_norms.txt")}
+    r = rows[(table, L, 128)]
+    rule, disk = ("ilr", "vlr")[int(r[1])], ("d2", "d22")[int(r[2])]
+    hier = W.band_hierarchy(128, L, rule, disk)
+    xc, yc, _ = W.zone_geometry(hier)
+    s, sx, sy = _d_sigma(disk, xc, yc)
+    fx, fy = oamr.zone_leaf_force(hier["x0"], hier["y0"], hier["h0"], hier["level"], hier["ix"], hier["iy"],
+                                  hier["leaf"], s, sx, sy)
+    got = amr_table_norms(hier, disk, fx, fy)
+    printed = r[5:]
+    for c in amr_pinned_columns(table, int(r[2]), L, 128):
+        assert _near3(got[c], printed[c]), (table, L, c, got, printed)
+
+
+def test_zone_sum_refinement_invariance():
+    """Zones split into children that carry the parent's linear reconstruction
+    (sigma0 + delta . offset, same delta) leave the force at the unsplit zones
+    equal to the uniform-grid sum (same integrand), through two levels."""
+    n = 16
+    nx, ny, x0, y0, h = W.unit_grid(n)
+    s, sx, sy = W.random_fields(n, n, seed=31)
+    ux, uy = uniform_direct_force(s, sx, sy, h)
+    hier = W.band_hierarchy(n, 3, "ilr", "d2")
+    lev, ix, iy = hier["level"], hier["ix"], hier["iy"]
+    # each zone's value: the level-0 ancestor's linear function at the zone centre
+    anc_i, anc_j = ix >> lev, iy >> lev
+    xc, yc, _ = W.zone_geometry(hier)
+    pxc = x0 + (anc_i + 0.5) * h
+    pyc = y0 + (anc_j + 0.5) * h
+    zs = s[anc_j, anc_i] + sx[anc_j, anc_i] * (xc - pxc) + sy[anc_j, anc_i] * (yc - pyc)
+    fx, fy = oamr.zone_leaf_force(x0, y0, h, lev, ix, iy, hier["leaf"], zs, sx[anc_j, anc_i], sy[anc_j, anc_i])
+    coarse = (lev == 0) & hier["leaf"]
+    assert np.count_nonzero(lev > 0) > 0 and np.count_nonzero(coarse) > 0
+    assert rel_l2(fx[coarse], fy[coarse], ux[iy[coarse], ix[coarse]], uy[iy[coarse], ix[coarse]]) < 1e-12
+
+
+def test_zone_sum_equals_patch_sum_table10():
+    """The Fig. 1 hierarchy given zone by zone gives the patch-list leaf sum."""
+    patches = oamr.make_patches(TABLE10_PATCHES)
+    rng = np.random.Generator(np.random.PCG64(8))
+    sig = [rng.uniform(0, 1, (p.ny, p.nx)) for p in patches]
+    leaves, fx, fy = oamr.amr_direct_force(patches, sig)
+    lev, zi, zj, zs, zl = [], [], [], [], []
+    masks = oamr.leaf_masks(patches)
+    for p, m, sg in zip(patches, masks, sig):
+        oi, oj = int(round(p.x0 / p.h)), int(round(p.y0 / p.h))
+        for j in range(p.ny):
+            for i in range(p.nx):
+                lev.append(p.level); zi.append(oi + i); zj.append(oj + j); zs.append(sg[j, i]); zl.append(m[j, i])
+    gx, gy = oamr.zone_leaf_force(0.0, 0.0, 0.25, lev, zi, zj, zl, zs)
+    zl = np.array(zl)
+    assert np.allclose(np.sort(gx[zl]), np.sort(fx), rtol=1e-13, atol=1e-14)
+    assert np.allclose(np.sort(gy[zl]), np.sort(fy), rtol=1e-13, atol=1e-14)
