@@ -88,6 +88,14 @@ typedef struct {
     double z;                   /* height of the targets above the disk plane; 0 = in the plane.
                                    z != 0 (off-plane forces, Section 2 with the arctan terms)
                                    needs a single patch and sg_force3 */
+    const uint8_t *const *masks; /* NULL, or one entry per patch: NULL (every cell of the patch
+                                   exists) or nx*ny bytes, row-major, nonzero where the cell
+                                   exists. Cells that do not exist carry no density and get no
+                                   force (quadtree hierarchies, where a refined region is not a
+                                   rectangle). Rules: on a refined patch existing cells come in
+                                   whole 2 x 2 blocks over an existing parent cell; a parent
+                                   cell with children is not a leaf. Not with z != 0 or
+                                   SG_SLOPES_CENTRAL. Read during sg_plan_create only. */
 } sg_geom;
 
 typedef struct {
@@ -98,6 +106,7 @@ typedef struct {
     int64_t device_bytes;       /* device memory held by the plan now */
     int64_t scratch_bytes;      /* per-call scratch (workspace) of one solve */
     int max_pad;                /* largest padded FFT length */
+    int64_t nzones;             /* zones of a plan made by sg_plan_create_zones, else 0 */
 } sg_plan_info;
 
 typedef struct sg_plan sg_plan;
@@ -110,7 +119,8 @@ typedef struct sg_plan sg_plan;
  * ny); patches of one level do not overlap; at most 12 levels; the lattice of
  * the finest level's half-cells spans at most 2^23 units per axis; a single
  * patch has at most 2048 cells per side. slope_mode SG_SLOPES_CENTRAL needs a
- * single patch. Returns SG_OK or SG_EINVAL.
+ * single patch. Masks, where given, follow the rules stated at sg_geom.masks.
+ * Returns SG_OK or SG_EINVAL.
  */
 sg_status sg_geom_validate(const sg_geom *geom);
 
@@ -233,6 +243,89 @@ sg_status sg_plan_get_timing(sg_plan *plan, double *ms, int n);
  */
 sg_status sg_direct_force_static(int nx, int ny, double h, double G, const float *sigma, const float *deltax,
                                  const float *deltay, float *fx, float *fy, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Zone-by-zone hierarchies (Section 2 and Fig. 1: Berger-Oliger refinement,
+ * each refined zone split into four children; the ILR and VLR hierarchies of
+ * Section 4 are of this kind). A hierarchy is the list of its zones: level l
+ * (0 = the coarsest grid of nx0 x ny0 zones of width h0 with lower-left corner
+ * (x0, y0); the paper's L is l + 1) and the zone's column ix and row iy on the
+ * level-l grid, zone (l, ix, iy) spanning [x0 + ix h_l, x0 + (ix + 1) h_l] x
+ * [y0 + iy h_l, y0 + (iy + 1) h_l] with h_l = h0 / 2^l. A zone is a leaf when
+ * none of its children is listed; the force acts on and is summed over the
+ * leaf zones (Eq. eqnXforce2).
+ *
+ * Rules: 0 <= level < 12, 0 <= ix < nx0 2^level, 0 <= iy < ny0 2^level; no
+ * zone is listed twice; every zone of level >= 1 has its parent
+ * (level - 1, ix / 2, iy / 2) and its three siblings listed; nx0, ny0 >= 1,
+ * h0 > 0, the finest level spans at most 2^22 zones per axis.
+ *
+ * The library lays the zones out as masked patches (one or more per level,
+ * each at most 2048 zones per side and inside one patch of the level below)
+ * and solves them with the same FFT convolutions and cross-patch direct sum
+ * as a patch hierarchy.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int nx0, ny0;               /* level-0 grid, zones per axis */
+    double x0, y0;              /* lower-left corner of the level-0 grid */
+    double h0;                  /* level-0 zone width */
+    int64_t nzones;             /* zones listed, >= 1 */
+    const int32_t *level;       /* [nzones] host arrays */
+    const int32_t *ix;
+    const int32_t *iy;
+} sg_zones;
+
+/*
+ * Create a plan for a zone list (host memory, read during the call only).
+ * G, slope_mode (SG_SLOPES_NONE or SG_SLOPES_CALLER), prec and hbm_budget as
+ * for sg_plan_create. Errors: SG_EINVAL (rules above, with sg_last_error
+ * naming the first offending zone), SG_EBUDGET, SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, sg_precision prec,
+                               size_t hbm_budget, sg_plan **out);
+
+/*
+ * Enqueue one solve of a zone plan on `stream`. sigma, deltax, deltay, fx, fy
+ * are device arrays of nzones elements in the order of the zone list (double
+ * for SG_FP64, float for SG_FP32); deltax, deltay are read for
+ * SG_SLOPES_CALLER only. Values at non-leaf zones are ignored on input; fx, fy
+ * receive the force at every leaf zone and 0 at non-leaf zones.
+ * Errors: SG_EINVAL (not a zone plan, null or misaligned pointer), SG_ECUDA.
+ */
+sg_status sg_force_zones(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
+                         void *fy, void *stream);
+
+/*
+ * Index of every zone in the plan's patch layout (the field arrays of
+ * sg_force): host_out[k] for zone k, n >= nzones. Synchronous.
+ */
+sg_status sg_plan_zone_slots(const sg_plan *plan, int64_t *host_out, int64_t n);
+
+/*
+ * Read zone records of the paper's Table 10 form (Appendix A): one row of
+ * ncols >= 6 doubles per zone, row-major, columns ID, x_c, y_c, L, P, EL
+ * (further columns, the neighbours LN, DN, RN, UN, are not read). IDs are
+ * 1..n in row order; L >= 1 is the paper's level (level = L - 1); P is the
+ * parent's ID (0 on L = 1); EL = 1 marks a leaf. The centre must lie within a
+ * quarter zone width of a zone centre of its level on the grid (nx0, ny0, x0,
+ * y0, h0) (printed centres are rounded). Writes level, ix, iy (caller arrays
+ * of n int32) after checking that every parent is the zone containing its
+ * child one level up and that EL is 1 exactly for the zones nobody names as
+ * parent. Host only. Errors: SG_EINVAL (sg_last_error names the record).
+ */
+sg_status sg_zones_from_records(int64_t n, int ncols, const double *records, int nx0, int ny0, double x0,
+                                double y0, double h0, int32_t *level, int32_t *ix, int32_t *iy);
+
+/*
+ * Links of a valid zone list (host only), the remaining columns of the record
+ * form: parent[k] = 1-based index of zone k's parent (0 on level 0); leaf[k] =
+ * 1 for leaf zones; neighbours[4k + s] for sides s = left, down, right, up =
+ * 1-based index of the zone across that side: the zone of the same level if
+ * listed, else the listed coarser zone containing the point just across the
+ * side's midpoint; 0 at the domain boundary. Any output may be NULL.
+ * Errors: SG_EINVAL.
+ */
+sg_status sg_zones_links(const sg_zones *zones, int64_t *parent, uint8_t *leaf, int64_t *neighbours);
 
 /* ------------------------------------------------------------------------
  * Batches (not in the paper): n independent solves bound to their plans and

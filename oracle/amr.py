@@ -147,16 +147,21 @@ def zone_bounds(x0, y0, h0, level, ix, iy):
     return xl, xl + h, yd, yd + h, xl + 0.5 * h, yd + 0.5 * h
 
 
-def zone_leaf_force(x0, y0, h0, level, ix, iy, leaf, sigma, dx=None, dy=None, G=1.0, nthreads=0):
-    """Force at every leaf centre from every leaf zone (plain sum, C oracle).
+def zone_leaf_force(x0, y0, h0, level, ix, iy, leaf, sigma, dx=None, dy=None, G=1.0, targets=None, nthreads=0):
+    """Force at leaf centres from every leaf zone (plain sum, C oracle).
 
     sigma, dx, dy: per-zone arrays (values at non-leaf zones are ignored).
-    Returns (fx, fy) per zone, 0 at non-leaf zones.
+    targets: optional zone indices (leaf zones) to evaluate; default all leaves.
+    Returns (fx, fy): per zone (0 at non-leaf zones), or per entry of targets.
     """
     leaf = np.asarray(leaf, bool)
-    xl, xr, yd, yu, xc, yc = (a[leaf] for a in zone_bounds(x0, y0, h0, level, ix, iy))
+    xl, xr, yd, yu, xc, yc = zone_bounds(x0, y0, h0, level, ix, iy)
     pick = lambda a: None if a is None else np.asarray(a, np.float64)[leaf]
-    fx, fy = direct_force((xl, xr, yd, yu), pick(sigma), pick(dx), pick(dy), xc, yc, G=G, nthreads=nthreads)
+    tsel = np.nonzero(leaf)[0] if targets is None else np.asarray(targets)
+    fx, fy = direct_force((xl[leaf], xr[leaf], yd[leaf], yu[leaf]), pick(sigma), pick(dx), pick(dy), xc[tsel],
+                          yc[tsel], G=G, nthreads=nthreads)
+    if targets is not None:
+        return fx, fy
     ox = np.zeros(leaf.size)
     oy = np.zeros(leaf.size)
     ox[leaf] = fx

@@ -14,44 +14,43 @@
 // same density and is small, and f_0 has no hole, so no corner weight along a
 // patch boundary is of the size of the density itself.
 //
-// Restriction (any choice cancels in the sum; this one is the least-squares
-// linear fit of the four children over the parent cell of width H):
-//   sigma0 = mean(sigma0_k)
-//   deltax = (3 / (4 H)) (sum_right sigma0_k - sum_left sigma0_k) + (1/16) sum deltax_k
-//   deltay = (3 / (4 H)) (sum_top sigma0_k - sum_bottom sigma0_k) + (1/16) sum deltay_k
-// It is exact for linear data.
+// Restriction (any choice cancels in the sum): sigma0 = mean(sigma0_k) over the
+// four children, and
+//   with caller slopes:  deltax = mean(deltax_k), deltay = mean(deltay_k);
+//   order 0:             the least-squares linear fit over the parent of width H,
+//                        deltax = (3 / (4 H)) (sum_right sigma0_k - sum_left sigma0_k),
+//                        deltay likewise with top and bottom.
+// For smooth data both give the gradient to O(H^2), so the defects S_l are
+// O(H^2). With slopes supplied the children's mean slope stays of the size of
+// the data's slopes even for rough data, where a least-squares slope grows like
+// (jump in sigma) / H and the large slope terms of consecutive levels, which
+// cancel in the sum, would cost digits in the corner-form sum.
 #include "common.cuh"
 
 namespace {
 
 // Fill the cells of patch p: leaves copy the input, covered cells restrict
-// their children's filled values (already written: patches run finest first).
+// their children's filled values (already written: patches run finest first),
+// cells that do not exist get zero.
 template <typename T>
-__global__ void k_fill(sg_patch_dev p, const int4 *__restrict__ cov, const int *__restrict__ cov_child,
-                       const sg_patch_dev *__restrict__ pd, const T *__restrict__ sigma, const T *__restrict__ dx,
-                       const T *__restrict__ dy, T *__restrict__ s)
+__global__ void k_fill(sg_patch_dev p, const int *__restrict__ code, const sg_patch_dev *__restrict__ pd,
+                       const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
+                       T *__restrict__ s)
 {
+    const bool slopes = dx != nullptr;
     const int64_t n = (int64_t)p.nx * p.ny;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % p.nx), j = (int)(e / p.nx);
         const int64_t o = p.cell_off + e;
-        int c = -1;
-        for (int k = 0; k < p.ncov; ++k) {
-            const int4 r = cov[p.cov_off + k];
-            if (i >= r.x && i < r.z && j >= r.y && j < r.w) {
-                c = k;
-                break;
-            }
-        }
-        double s0, sx, sy;
-        if (c < 0) {
+        const int c = code[o];
+        double s0 = 0.0, sx = 0.0, sy = 0.0;
+        if (c == SG_CELL_LEAF) {
             s0 = (double)sigma[o];
             sx = dx ? (double)dx[o] : 0.0;
             sy = dy ? (double)dy[o] : 0.0;
-        } else {
-            const int4 r = cov[p.cov_off + c];
-            const sg_patch_dev q = pd[cov_child[p.cov_off + c]];
-            const int ci = 2 * (i - r.x), cj = 2 * (j - r.y);
+        } else if (c >= 0) {
+            const sg_patch_dev q = pd[c];
+            const int ci = 2 * (i - q.pi0), cj = 2 * (j - q.pj0);
             double sum = 0, right = 0, top = 0, gx = 0, gy = 0;
             for (int b = 0; b < 2; ++b) {
                 for (int a = 0; a < 2; ++a) {
@@ -65,8 +64,8 @@ __global__ void k_fill(sg_patch_dev p, const int4 *__restrict__ cov, const int *
                 }
             }
             s0 = 0.25 * sum;
-            sx = 0.75 / p.h * right + gx / 16.0;
-            sy = 0.75 / p.h * top + gy / 16.0;
+            sx = slopes ? 0.25 * gx : 0.75 / p.h * right;
+            sy = slopes ? 0.25 * gy : 0.75 / p.h * top;
         }
         s[o] = (T)s0;
         s[o + p.ncells_plane] = (T)sx;
@@ -76,13 +75,14 @@ __global__ void k_fill(sg_patch_dev p, const int4 *__restrict__ cov, const int *
 
 // Replace the filled values of patch q (level >= 1) by q - P(parent), in place.
 template <typename T>
-__global__ void k_defect(sg_patch_dev q, sg_patch_dev p, T *__restrict__ s)
+__global__ void k_defect(sg_patch_dev q, sg_patch_dev p, const int *__restrict__ code, T *__restrict__ s)
 {
     const int64_t n = (int64_t)q.nx * q.ny;
     const int64_t P = q.ncells_plane;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e % q.nx), j = (int)(e / q.nx);
         const int64_t o = q.cell_off + e;
+        if (code[o] == SG_CELL_ABSENT) continue;
         const int64_t op = p.cell_off + (int64_t)(q.pj0 + j / 2) * p.nx + (q.pi0 + i / 2);
         const double ox = ((i & 1) - 0.5) * q.h, oy = ((j & 1) - 0.5) * q.h;
         const double px = (double)s[op + P], py = (double)s[op + 2 * P];
@@ -104,7 +104,7 @@ sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, co
         const int64_t n = (int64_t)d.nx * d.ny;
         int grid = (int)((n + 255) / 256);
         if (grid > 4096) grid = 4096;
-        k_fill<T><<<grid, 256, 0, st>>>(d, plan->cov_rects, plan->cov_child, plan->patch_dev, (const T *)sigma,
+        k_fill<T><<<grid, 256, 0, st>>>(d, plan->cell_code, plan->patch_dev, (const T *)sigma,
                                         slopes ? (const T *)dx : nullptr, slopes ? (const T *)dy : nullptr, s);
         SG_CUDA_TRY(cudaGetLastError());
     }
@@ -114,7 +114,7 @@ sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, co
         const int64_t n = (int64_t)d.nx * d.ny;
         int grid = (int)((n + 255) / 256);
         if (grid > 4096) grid = 4096;
-        k_defect<T><<<grid, 256, 0, st>>>(d, plan->pp[d.parent].d, s);
+        k_defect<T><<<grid, 256, 0, st>>>(d, plan->pp[d.parent].d, plan->cell_code, s);
         SG_CUDA_TRY(cudaGetLastError());
     }
     return SG_OK;

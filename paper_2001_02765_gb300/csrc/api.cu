@@ -79,9 +79,8 @@ struct geom_info {
     int lmax = 0;
     double h0 = 0, X0 = 0, Y0 = 0, lambda = 0;
     std::vector<int> parent, ox, oy, step;
-    std::vector<std::vector<int4>> cov;       // per patch, covered rectangles in its cells
-    std::vector<std::vector<int>> cov_child;  // per patch, the child patch of each rectangle
-    std::vector<std::vector<uint8_t>> leaf;   // per patch, leaf mask [ny][nx]
+    std::vector<std::vector<int>> code;       // per patch [ny][nx]: SG_CELL_ABSENT, SG_CELL_LEAF or child patch
+    bool masked = false;                      // some patch has a mask
     std::vector<int64_t> nleaf, cell_off;
     int64_t ncells = 0, nleaves = 0, cross_pairs = 0;
 };
@@ -102,7 +101,7 @@ sg_status fail(const char *msg)
     return SG_EINVAL;
 }
 
-sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
+sg_status analyse(const sg_geom *g, geom_info &gi)
 {
     if (!g) return fail("geometry is NULL");
     if (g->npatches < 1 || !g->patches) return fail("geometry has no patches");
@@ -114,6 +113,10 @@ sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
     const sg_patch *P = g->patches;
     gi.n = n;
     if (g->slope_mode == SG_SLOPES_CENTRAL && n != 1) return fail("central slopes need a single patch");
+    if (g->masks)
+        for (int k = 0; k < n; ++k) gi.masked = gi.masked || g->masks[k] != nullptr;
+    if (gi.masked && g->slope_mode == SG_SLOPES_CENTRAL) return fail("central slopes need an unmasked patch");
+    if (gi.masked && g->z != 0.0) return fail("off-plane forces (z != 0) need an unmasked patch");
     if (P[0].level != 0) return fail("the first patch must be on level 0");
     for (int k = 0; k < n; ++k) {
         if (P[k].nx < 1 || P[k].ny < 1 || P[k].nx > SG_MAX_PATCH_SIDE || P[k].ny > SG_MAX_PATCH_SIDE)
@@ -181,22 +184,43 @@ sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
             if (x0 < qx1 && qx0 < x1 && y0 < qy1 && qy0 < y1) return fail("patches of one level overlap");
         }
     }
-    // covered rectangles, leaves
-    gi.cov.assign(n, {});
-    gi.cov_child.assign(n, {});
+    // cell codes: absent, leaf, or covered by a child patch
+    gi.code.assign(n, {});
     gi.nleaf.assign(n, 0);
     gi.cell_off.assign(n, 0);
-    if (build_masks) gi.leaf.assign(n, {});
     for (int k = 0; k < n; ++k) {
-        if (gi.parent[k] >= 0) {
-            const int p = gi.parent[k];
-            int4 r;
-            r.x = (gi.ox[k] - gi.ox[p]) / gi.step[p];
-            r.y = (gi.oy[k] - gi.oy[p]) / gi.step[p];
-            r.z = r.x + P[k].nx / 2;
-            r.w = r.y + P[k].ny / 2;
-            gi.cov[p].push_back(r);
-            gi.cov_child[p].push_back(k);
+        const uint8_t *m = g->masks ? g->masks[k] : nullptr;
+        const size_t nc = (size_t)P[k].nx * P[k].ny;
+        gi.code[k].assign(nc, SG_CELL_LEAF);
+        if (m)
+            for (size_t c = 0; c < nc; ++c)
+                if (!m[c]) gi.code[k][c] = SG_CELL_ABSENT;
+    }
+    char msg[160];
+    for (int k = 0; k < n; ++k) {
+        const int par = gi.parent[k];
+        if (par < 0) continue;
+        const int pi0 = (gi.ox[k] - gi.ox[par]) / gi.step[par], pj0 = (gi.oy[k] - gi.oy[par]) / gi.step[par];
+        const int nx = P[k].nx, pnx = P[par].nx;
+        for (int bj = 0; bj < P[k].ny / 2; ++bj) {
+            for (int bi = 0; bi < nx / 2; ++bi) {
+                int present = 0;
+                for (int q = 0; q < 4; ++q)
+                    present += gi.code[k][(size_t)(2 * bj + (q >> 1)) * nx + 2 * bi + (q & 1)] != SG_CELL_ABSENT;
+                if (present == 0) continue;
+                if (present != 4) {
+                    snprintf(msg, sizeof(msg), "patch %d: cells (%d..%d, %d..%d) are not a whole 2x2 block", k,
+                             2 * bi, 2 * bi + 1, 2 * bj, 2 * bj + 1);
+                    return fail(msg);
+                }
+                int &pc = gi.code[par][(size_t)(pj0 + bj) * pnx + pi0 + bi];
+                if (pc == SG_CELL_ABSENT) {
+                    snprintf(msg, sizeof(msg), "patch %d: cells over an absent parent cell (%d, %d) of patch %d", k,
+                             pi0 + bi, pj0 + bj, par);
+                    return fail(msg);
+                }
+                pc = k;
+            }
         }
     }
     gi.ncells = 0;
@@ -204,17 +228,12 @@ sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
     for (int k = 0; k < n; ++k) {
         gi.cell_off[k] = gi.ncells;
         gi.ncells += (int64_t)P[k].nx * P[k].ny;
-        int64_t covered = 0;
-        for (const int4 &r : gi.cov[k]) covered += (int64_t)(r.z - r.x) * (r.w - r.y);
-        gi.nleaf[k] = (int64_t)P[k].nx * P[k].ny - covered;
-        gi.nleaves += gi.nleaf[k];
-        if (build_masks) {
-            gi.leaf[k].assign((size_t)P[k].nx * P[k].ny, 1);
-            for (const int4 &r : gi.cov[k])
-                for (int j = r.y; j < r.w; ++j)
-                    for (int i = r.x; i < r.z; ++i) gi.leaf[k][(size_t)j * P[k].nx + i] = 0;
-        }
+        int64_t leaves = 0;
+        for (int c : gi.code[k]) leaves += c == SG_CELL_LEAF;
+        gi.nleaf[k] = leaves;
+        gi.nleaves += leaves;
     }
+    if (gi.nleaves == 0) return fail("the geometry has no leaf cell");
     gi.cross_pairs = 0;
     for (int k = 0; k < n; ++k) gi.cross_pairs += gi.nleaf[k] * (gi.nleaves - gi.nleaf[k]);
     return SG_OK;
@@ -222,19 +241,40 @@ sg_status analyse(const sg_geom *g, geom_info &gi, bool build_masks)
 
 size_t elem_size(sg_precision prec) { return prec == SG_FP64 ? 8 : 4; }
 
-// corner tiles of every patch (the composite sources cover whole patches)
+// corner tiles of every patch (the composite sources cover whole patches); with
+// masks, tiles whose corners touch no existing cell carry zero weights and are left out
 void build_tiles(const sg_geom *g, const geom_info &gi, std::vector<sg_tile_desc> &tiles, std::vector<int> &first,
                  std::vector<int> &count)
 {
     first.assign(gi.n, 0);
     count.assign(gi.n, 0);
+    std::vector<int64_t> sat;  // summed-area table of existing cells, (ny + 1) x (nx + 1)
     for (int k = 0; k < gi.n; ++k) {
         const sg_patch &p = g->patches[k];
+        const bool masked = g->masks && g->masks[k];
+        if (masked) {
+            sat.assign((size_t)(p.nx + 1) * (p.ny + 1), 0);
+            for (int j = 0; j < p.ny; ++j)
+                for (int i = 0; i < p.nx; ++i)
+                    sat[(size_t)(j + 1) * (p.nx + 1) + i + 1] =
+                        (gi.code[k][(size_t)j * p.nx + i] != SG_CELL_ABSENT) + sat[(size_t)j * (p.nx + 1) + i + 1] +
+                        sat[(size_t)(j + 1) * (p.nx + 1) + i] - sat[(size_t)j * (p.nx + 1) + i];
+        }
         first[k] = (int)tiles.size();
         const int ntx = (p.nx + 1 + SG_TILE_X - 1) / SG_TILE_X, nty = (p.ny + 1 + SG_TILE_Y - 1) / SG_TILE_Y;
         for (int b = 0; b < nty; ++b) {
             for (int a = 0; a < ntx; ++a) {
                 const int ci0 = a * SG_TILE_X, cj0 = b * SG_TILE_Y;
+                if (masked) {
+                    // cells around the tile's corners: i in [ci0 - 1, ci0 + TILE_X - 1], same in j
+                    const int i0 = ci0 > 0 ? ci0 - 1 : 0, j0 = cj0 > 0 ? cj0 - 1 : 0;
+                    const int i1 = ci0 + SG_TILE_X < p.nx ? ci0 + SG_TILE_X : p.nx;
+                    const int j1 = cj0 + SG_TILE_Y < p.ny ? cj0 + SG_TILE_Y : p.ny;
+                    const int64_t w = p.nx + 1;
+                    const int64_t cnt = sat[(size_t)j1 * w + i1] - sat[(size_t)j0 * w + i1] - sat[(size_t)j1 * w + i0] +
+                                        sat[(size_t)j0 * w + i0];
+                    if (cnt == 0) continue;
+                }
                 sg_tile_desc t;
                 memset(&t, 0, sizeof(t));
                 t.patch = k;
@@ -281,10 +321,11 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
     }
     s.work = work;
     for (int L = SG_MIN_PAD; L <= s.max_pad; L <<= 1) s.twiddles += (int64_t)L * (16 + 8);
+    if (gi.n > 1 || gi.masked) s.direct = 3 * gi.ncells * (int64_t)es + gi.ncells * (int64_t)sizeof(int);
     if (gi.n > 1) {
-        s.direct = 3 * gi.ncells * (int64_t)es + (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
-                   gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
-                   (nsplit > 1 ? (int64_t)nsplit * gi.nleaves * 16 : 0);
+        s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
+                    gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
+                    (nsplit > 1 ? (int64_t)nsplit * gi.nleaves * 16 : 0);
     }
     s.geometry = (int64_t)gi.n * (int64_t)sizeof(sg_patch_dev) + 16 * (int64_t)gi.n;
     return s;
@@ -328,8 +369,8 @@ void plan_free(sg_plan *plan)
         }
     }
     cudaFree(plan->twiddles);
-    cudaFree(plan->cov_rects);
-    cudaFree(plan->cov_child);
+    cudaFree(plan->cell_code);
+    cudaFree(plan->zone_slot);
     if (plan->ws) {
         sg_workspace_free(plan->ws, 0, false);
         delete plan->ws;
@@ -348,7 +389,7 @@ void plan_free(sg_plan *plan)
 sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan **out)
 {
     geom_info gi;
-    SG_TRY(analyse(g, gi, true));
+    SG_TRY(analyse(g, gi));
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tfirst, tcount;
     if (gi.n > 1) build_tiles(g, gi, tiles, tfirst, tcount);
@@ -387,11 +428,11 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     plan->lattice_y0 = gi.Y0;
     plan->nsplit = nsplit;
 
+    plan->geom.masks = nullptr;  // the cell codes below carry them
+    plan->composite = gi.n > 1 || gi.masked;
+
     sg_status st = SG_OK;
     const size_t es = elem_size(prec);
-    // covered rectangles
-    std::vector<int4> cov_all;
-    std::vector<int> cov_child_all;
     std::vector<sg_patch_dev> pdev(gi.n);
     for (int k = 0; k < gi.n && st == SG_OK; ++k) {
         sg_patch_plan &pp = plan->pp[k];
@@ -407,10 +448,6 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         d.ox = gi.ox[k];
         d.oy = gi.oy[k];
         d.step = gi.step[k];
-        d.ncov = (int)gi.cov[k].size();
-        d.cov_off = (int)cov_all.size();
-        for (const int4 &r : gi.cov[k]) cov_all.push_back(r);
-        for (int c : gi.cov_child[k]) cov_child_all.push_back(c);
         d.parent = gi.parent[k];
         d.pi0 = d.parent >= 0 ? (gi.ox[k] - gi.ox[d.parent]) / gi.step[d.parent] : 0;
         d.pj0 = d.parent >= 0 ? (gi.oy[k] - gi.oy[d.parent]) / gi.step[d.parent] : 0;
@@ -425,16 +462,13 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0)
             st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
-    plan->ncov_total = (int)cov_all.size();
-    if (st == SG_OK) st = dev_alloc(plan, &plan->cov_rects, (cov_all.empty() ? 1 : cov_all.size()) * sizeof(int4));
-    if (st == SG_OK && !cov_all.empty())
-        st = cudaMemcpy(plan->cov_rects, cov_all.data(), cov_all.size() * sizeof(int4), cudaMemcpyHostToDevice) ==
-                     cudaSuccess ? SG_OK : SG_ECUDA;
-    if (st == SG_OK) st = dev_alloc(plan, &plan->cov_child, (cov_child_all.empty() ? 1 : cov_child_all.size()) * sizeof(int));
-    if (st == SG_OK && !cov_child_all.empty())
-        st = cudaMemcpy(plan->cov_child, cov_child_all.data(), cov_child_all.size() * sizeof(int),
-                        cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
-    if (gi.n > 1) plan->ws_sfield_bytes = 3 * gi.ncells * (int64_t)es;
+    if (plan->composite) {
+        plan->ws_sfield_bytes = 3 * gi.ncells * (int64_t)es;
+        std::vector<int> codes;
+        codes.reserve((size_t)gi.ncells);
+        for (int k = 0; k < gi.n; ++k) codes.insert(codes.end(), gi.code[k].begin(), gi.code[k].end());
+        if (st == SG_OK) st = sg_plan_upload(plan, (void **)&plan->cell_code, codes.data(), codes.size() * sizeof(int));
+    }
     if (st == SG_OK) st = dev_alloc(plan, &plan->patch_dev, gi.n * sizeof(sg_patch_dev));
     if (st == SG_OK)
         st = cudaMemcpy(plan->patch_dev, pdev.data(), gi.n * sizeof(sg_patch_dev), cudaMemcpyHostToDevice) == cudaSuccess
@@ -470,7 +504,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             int in_block = 0;
             for (int j = 0; j < p.ny; ++j) {
                 for (int i = 0; i < p.nx; ++i) {
-                    if (!gi.leaf[k][(size_t)j * p.nx + i]) continue;
+                    if (gi.code[k][(size_t)j * p.nx + i] != SG_CELL_LEAF) continue;
                     if (in_block == 0) {
                         sg_target_block b;
                         b.patch = k;
@@ -525,6 +559,20 @@ bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 }  // namespace
 
+sg_status sg_plan_upload(sg_plan *plan, void **dst, const void *src, size_t n)
+{
+    SG_TRY(dev_alloc(plan, dst, n));
+    if (n) SG_CUDA_TRY(cudaMemcpy(*dst, src, n, cudaMemcpyHostToDevice));
+    return SG_OK;
+}
+
+sg_status sg_plan_build(const sg_geom *geom, sg_precision prec, size_t budget, sg_plan **out)
+{
+    return plan_build(geom, prec, budget, out);
+}
+
+void sg_plan_release(sg_plan *plan) { plan_free(plan); }
+
 // ------------------------------------------------------------- workspaces --
 
 int64_t sg_workspace_bytes(const sg_plan *plan)
@@ -554,13 +602,13 @@ void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async)
     if (ws->ev_join) cudaEventDestroy(ws->ev_join);
     ws->aux = nullptr;
     ws->ev_fork = ws->ev_join = nullptr;
-    void *bufs[6] = {ws->work_fwd, ws->work_inv, ws->sfield, ws->tile_w, ws->partial, ws->err};
+    void *bufs[7] = {ws->work_fwd, ws->work_inv, ws->sfield, ws->tile_w, ws->partial, ws->err, ws->zone_buf};
     for (void *b : bufs) {
         if (!b) continue;
         if (async) cudaFreeAsync(b, st);
         else cudaFree(b);
     }
-    ws->work_fwd = ws->work_inv = ws->sfield = ws->tile_w = nullptr;
+    ws->work_fwd = ws->work_inv = ws->sfield = ws->tile_w = ws->zone_buf = nullptr;
     ws->partial = nullptr;
     ws->err = nullptr;
 }
@@ -596,8 +644,8 @@ sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, 
 {
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
     const void *dx = caller ? deltax : nullptr, *dy = caller ? deltay : nullptr;
-    if (plan->npatches == 1) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, fz, st);
-    // AMR: composite sources, same-patch FFT convolutions, cross-patch direct sum
+    if (!plan->composite) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, fz, st);
+    // AMR or masks: composite sources, same-patch FFT convolutions, cross-patch direct sum
     SG_TRY(sg_amr_prepare(plan, ws, sigma, dx, dy, st));
     const size_t es = elem_size(plan->prec);
     const char *S = (const char *)ws->sfield;
@@ -651,7 +699,7 @@ static sg_status force_common(sg_plan *plan, const void *sigma, const void *delt
             return a;
         }
         plan->ws = ws;
-        plan->device_bytes += plan->scratch_bytes;
+        plan->device_bytes += sg_workspace_bytes(plan);
     }
     sg_timing_reset(plan->timing);
     plan->ws->timing = plan->timing;
@@ -665,14 +713,14 @@ extern "C" {
 sg_status sg_geom_validate(const sg_geom *geom)
 {
     geom_info gi;
-    return analyse(geom, gi, false);
+    return analyse(geom, gi);
 }
 
 sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes)
 {
     if (!bytes || (prec != SG_FP64 && prec != SG_FP32)) return SG_EINVAL;
     geom_info gi;
-    SG_TRY(analyse(geom, gi, true));
+    SG_TRY(analyse(geom, gi));
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tf, tc;
     if (gi.n > 1) build_tiles(geom, gi, tiles, tf, tc);
@@ -704,6 +752,7 @@ sg_status sg_plan_get_info(const sg_plan *plan, sg_plan_info *out)
     out->device_bytes = plan->device_bytes;
     out->scratch_bytes = plan->scratch_bytes;
     out->max_pad = plan->max_pad;
+    out->nzones = plan->nzones;
     return SG_OK;
 }
 

@@ -94,8 +94,6 @@ struct sg_patch_dev {
     double h;
     int ox, oy;         // lattice coordinates of the patch's lower-left corner
     int step;           // cell width in lattice units
-    int ncov;           // covered rectangles (child patch footprints) in cells
-    int cov_off;        // first covered rectangle in the plan's list
     int parent;         // parent patch (-1 on level 0)
     int pi0, pj0;       // offset of this patch in its parent's cells
     int64_t ncells_plane;  // plane stride of the 3-field composite source arrays (= total cells)
@@ -133,12 +131,16 @@ struct sg_plan {
     int64_t tw64_off[16];           // byte offsets, indexed by log2 L
     int64_t tw32_off[16];
 
-    // covered rectangles, int4 (i0, j0, i1, j1) in cell units of the parent patch,
-    // and the child patch that covers each
-    int4 *cov_rects;
-    int *cov_child;
-    int ncov_total;
+    // per cell (device, ncells): SG_CELL_ABSENT, SG_CELL_LEAF, or the index of the
+    // child patch that covers the cell
+    int *cell_code;
+    // composite sources (AMR prepare + per-patch FFT on them): several patches or masks
+    bool composite;
 
+    // zone plans (sg_plan_create_zones): zone k sits at cell zone_slot[k] (device)
+    int64_t nzones;
+    int64_t *zone_slot;
+    int64_t ws_zone_bytes;          // per-call zone-order staging, 5 x ncells of T
 
     // per-call scratch sizes (bytes) and the plan's own workspace (used by sg_force)
     int64_t ws_fwd_bytes, ws_inv_bytes, ws_sfield_bytes, ws_tile_bytes, ws_partial_bytes;
@@ -173,6 +175,7 @@ struct sg_workspace {
     void *sfield;           // AMR composite source fields, 3 x ncells of T
     void *tile_w;           // AMR corner weights, ntiles x SG_TILE_N x 4 of T
     double *partial;        // AMR split partial sums, nsplit x ntargets x 2 (nsplit > 1)
+    void *zone_buf;         // zone plans: inputs (3 planes) and outputs (2 planes) in patch layout
     int *err;               // device error word: nonzero after a bounded wait in a kernel ran out
     struct sg_timing *timing;  // stage timers, or NULL
     // optional side stream for independent work of one solve (fork/join by events);
@@ -180,6 +183,16 @@ struct sg_workspace {
     cudaStream_t aux;
     cudaEvent_t ev_fork, ev_join;
 };
+
+// Cell codes of sg_plan::cell_code.
+#define SG_CELL_ABSENT (-2)
+#define SG_CELL_LEAF (-1)
+
+// Build a plan for a validated geometry (api.cu); zone plans add their map afterwards.
+sg_status sg_plan_build(const sg_geom *geom, sg_precision prec, size_t budget, sg_plan **out);
+void sg_plan_release(sg_plan *plan);
+// Copy n bytes to a new device buffer owned by the plan (counted in device_bytes).
+sg_status sg_plan_upload(sg_plan *plan, void **dst, const void *src, size_t n);
 
 // Allocate / free a workspace for a plan. async: stream-ordered allocation on st.
 sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t st, bool async);

@@ -45,19 +45,7 @@ struct field_src {
     int nx, ny;
     T inv2h;
     int mode;          // sg_slope_mode
-    const int4 *cov;   // covered rectangles (i0, j0, i1, j1), cells of this patch
-    int ncov;
 };
-
-template <typename T>
-__device__ __forceinline__ bool covered(const field_src<T> &s, int j, int i)
-{
-    for (int c = 0; c < s.ncov; ++c) {
-        const int4 r = __ldg(&s.cov[c]);
-        if (i >= r.x && i < r.z && j >= r.y && j < r.w) return true;
-    }
-    return false;
-}
 
 template <typename T>
 __device__ __forceinline__ T sigma_at(const field_src<T> &s, int j, int i)
@@ -70,7 +58,6 @@ template <typename T>
 __device__ __forceinline__ T field_value(const field_src<T> &s, int f, int j, int i)
 {
     if (j >= s.ny || i >= s.nx) return (T)0;
-    if (s.ncov && covered(s, j, i)) return (T)0;
     const int64_t o = (int64_t)j * s.nx + i;
     if (f == 0) return s.sigma[o];
     if (s.mode == SG_SLOPES_CALLER) return f == 1 ? s.dx[o] : s.dy[o];
@@ -515,16 +502,13 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     src.ny = d.ny;
     src.inv2h = (T)(0.5 / d.h);
     src.mode = plan->geom.slope_mode;
-    src.cov = plan->cov_rects + d.cov_off;
-    src.ncov = d.ncov;
-    if (plan->npatches > 1) {
-        // AMR: the composite source fields (three planes, no covered cells to mask)
+    if (plan->composite) {
+        // AMR or masks: the composite source fields (three planes, zero where no cell exists)
         const T *S = (const T *)ws->sfield;
         src.sigma = S + off;
         src.dx = S + plan->ncells + off;
         src.dy = S + 2 * plan->ncells + off;
         src.mode = SG_SLOPES_CALLER;
-        src.ncov = 0;
     }
     const int nf = src.mode == SG_SLOPES_NONE ? 1 : 3;
     const int qx = d.px / 2 + 1;

@@ -42,13 +42,24 @@ class sg_patch(ctypes.Structure):
 
 class sg_geom(ctypes.Structure):
     _fields_ = [("npatches", ctypes.c_int), ("patches", ctypes.POINTER(sg_patch)),
-                ("G", ctypes.c_double), ("slope_mode", ctypes.c_int), ("z", ctypes.c_double)]
+                ("G", ctypes.c_double), ("slope_mode", ctypes.c_int), ("z", ctypes.c_double),
+                ("masks", ctypes.c_void_p)]
 
 
 class sg_plan_info(ctypes.Structure):
     _fields_ = [("npatches", ctypes.c_int), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
                 ("cross_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("scratch_bytes", ctypes.c_int64), ("max_pad", ctypes.c_int)]
+                ("scratch_bytes", ctypes.c_int64), ("max_pad", ctypes.c_int), ("nzones", ctypes.c_int64)]
+
+
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+
+class sg_zones(ctypes.Structure):
+    _fields_ = [("nx0", ctypes.c_int), ("ny0", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("h0", ctypes.c_double), ("nzones", ctypes.c_int64), ("level", _I32P), ("ix", _I32P),
+                ("iy", _I32P)]
 
 
 class sg_server_stats(ctypes.Structure):
@@ -88,6 +99,14 @@ _SIGNATURES = {
                                ctypes.POINTER(ctypes.c_double)]),
     "sg_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sg_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sg_server_stats), ctypes.c_int]),
+    "sg_plan_create_zones": (ctypes.c_int, [ctypes.POINTER(sg_zones), ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_size_t, ctypes.POINTER(_VP)]),
+    "sg_force_zones": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_plan_zone_slots": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64]),
+    "sg_zones_from_records": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, _I32P, _I32P, _I32P]),
+    "sg_zones_links": (ctypes.c_int, [ctypes.POINTER(sg_zones), _I64P, ctypes.POINTER(ctypes.c_uint8), _I64P]),
     "sg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sg_last_error": (ctypes.c_char_p, []),
     "sg_version": (ctypes.c_int, []),
@@ -136,29 +155,40 @@ def _check(status, where):
         raise SgError(status, where, last_error())
 
 
-def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0):
-    """patches: iterable of (level, nx, ny, x0, y0, h). Returns (sg_geom, keepalive array)."""
+def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
+    """patches: iterable of (level, nx, ny, x0, y0, h); masks: None or one entry per
+    patch (None, or an [ny, nx] array, nonzero where the cell exists).
+    Returns (sg_geom, keepalive objects)."""
     patches = list(patches)
     arr = (sg_patch * len(patches))(*[sg_patch(int(p[0]), int(p[1]), int(p[2]), float(p[3]), float(p[4]), float(p[5]))
                                       for p in patches])
-    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode), float(z))
-    return g, arr
+    keep = [arr]
+    mptr = None
+    if masks is not None:
+        if len(masks) != len(patches):
+            raise ValueError("one mask entry per patch")
+        bufs = [None if m is None else np.ascontiguousarray(np.asarray(m) != 0, dtype=np.uint8).ravel() for m in masks]
+        ptrs = (ctypes.c_void_p * len(bufs))(*[None if b is None else b.ctypes.data for b in bufs])
+        keep += [bufs, ptrs]
+        mptr = ctypes.cast(ptrs, ctypes.c_void_p)
+    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode), float(z), mptr)
+    return g, keep
 
 
-def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0):
-    g, _keep = make_geom(patches, G, slope_mode, z)
+def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
+    g, _keep = make_geom(patches, G, slope_mode, z, masks)
     return load().sg_geom_validate(ctypes.byref(g))
 
 
-def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0):
-    g, _keep = make_geom(patches, G, slope_mode, z)
+def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
+    g, _keep = make_geom(patches, G, slope_mode, z, masks)
     out = ctypes.c_int64(0)
     _check(load().sg_plan_bytes(ctypes.byref(g), int(precision), ctypes.byref(out)), "sg_plan_bytes")
     return int(out.value)
 
 
-def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0):
-    g, _keep = make_geom(patches, G, slope_mode, z)
+def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0, masks=None):
+    g, _keep = make_geom(patches, G, slope_mode, z, masks)
     h = _VP()
     _check(load().sg_plan_create(ctypes.byref(g), int(precision), int(hbm_budget), ctypes.byref(h)), "sg_plan_create")
     return h.value
@@ -288,6 +318,62 @@ def sg_version():
     return int(load().sg_version())
 
 
+def make_zones(nx0, ny0, x0, y0, h0, level, ix, iy):
+    """sg_zones over int32 copies of the zone arrays. Returns (sg_zones, keepalive)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.int32).ravel() for a in (level, ix, iy)]
+    if not (arrs[0].size == arrs[1].size == arrs[2].size):
+        raise ValueError("level, ix, iy differ in length")
+    z = sg_zones(int(nx0), int(ny0), float(x0), float(y0), float(h0), arrs[0].size,
+                 *[a.ctypes.data_as(_I32P) for a in arrs])
+    return z, arrs
+
+
+def sg_plan_create_zones(zone_args, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0):
+    """zone_args: (nx0, ny0, x0, y0, h0, level, ix, iy)."""
+    z, _keep = make_zones(*zone_args)
+    h = _VP()
+    _check(load().sg_plan_create_zones(ctypes.byref(z), float(G), int(slope_mode), int(precision), int(hbm_budget),
+                                       ctypes.byref(h)), "sg_plan_create_zones")
+    return h.value
+
+
+def sg_force_zones(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
+    """Raw device pointers (ints), zone-ordered arrays; enqueues one solve."""
+    _check(load().sg_force_zones(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr,
+                                 stream_ptr or None), "sg_force_zones")
+
+
+def sg_plan_zone_slots(handle, nzones):
+    out = np.empty(int(nzones), dtype=np.int64)
+    _check(load().sg_plan_zone_slots(handle, out.ctypes.data_as(_I64P), out.size), "sg_plan_zone_slots")
+    return out
+
+
+def sg_zones_from_records(records, nx0, ny0, x0, y0, h0):
+    """records: [n, ncols >= 6] array (ID x_c y_c L P EL ...). Returns int32 (level, ix, iy)."""
+    rec = np.ascontiguousarray(records, dtype=np.float64)
+    n, ncols = rec.shape
+    out = [np.empty(n, dtype=np.int32) for _ in range(3)]
+    _check(load().sg_zones_from_records(n, ncols, rec.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nx0),
+                                        int(ny0), float(x0), float(y0), float(h0),
+                                        *[a.ctypes.data_as(_I32P) for a in out]), "sg_zones_from_records")
+    return tuple(out)
+
+
+def sg_zones_links(zone_args):
+    """zone_args as for sg_plan_create_zones. Returns (parent [n], leaf [n] bool, neighbours [n, 4]),
+    1-based indices, 0 for none."""
+    z, _keep = make_zones(*zone_args)
+    n = z.nzones
+    parent = np.empty(n, dtype=np.int64)
+    leaf = np.empty(n, dtype=np.uint8)
+    nb = np.empty(4 * n, dtype=np.int64)
+    _check(load().sg_zones_links(ctypes.byref(z), parent.ctypes.data_as(_I64P),
+                                 leaf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nb.ctypes.data_as(_I64P)),
+           "sg_zones_links")
+    return parent, leaf.astype(bool), nb.reshape(n, 4)
+
+
 # ------------------------------------------------------------ convenience --
 
 class Plan:
@@ -297,13 +383,14 @@ class Plan:
     row-major arrays concatenated (length ``ncells``).
     """
 
-    def __init__(self, patches, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0):
+    def __init__(self, patches, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0,
+                 masks=None):
         self.patches = [tuple(p) for p in patches]
         self.precision = SG_FP32 if precision in ("fp32", SG_FP32) else SG_FP64
         self.slope_mode = slope_mode
         self.G = G
         self.z = z
-        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget, z)
+        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget, z, masks)
         self.info = sg_plan_get_info(self.handle)
 
     @property
@@ -402,3 +489,42 @@ class Plan:
             out.append(flat[off:off + n].reshape(p[2], p[1]))
             off += n
         return out
+
+
+class ZonePlan(Plan):
+    """A plan for a zone-by-zone hierarchy (see sg_plan_create_zones); fields are
+    zone-ordered torch tensors of ``nzones`` elements."""
+
+    def __init__(self, nx0, ny0, x0, y0, h0, level, ix, iy, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER,
+                 hbm_budget=0):
+        self.patches = []
+        self.precision = SG_FP32 if precision in ("fp32", SG_FP32) else SG_FP64
+        self.slope_mode = slope_mode
+        self.G = G
+        self.z = 0.0
+        self.handle = sg_plan_create_zones((nx0, ny0, x0, y0, h0, level, ix, iy), self.precision, G, slope_mode,
+                                           hbm_budget)
+        self.info = sg_plan_get_info(self.handle)
+
+    @property
+    def nzones(self):
+        return self.info["nzones"]
+
+    def slots(self):
+        return sg_plan_zone_slots(self.handle, self.nzones)
+
+    def force_zones(self, sigma, dx=None, dy=None, fx=None, fy=None, stream=None):
+        """Enqueue a solve on zone-ordered tensors; returns (fx, fy), 0 at non-leaf zones."""
+        import torch
+        dt = self._torch_dtype()
+        for t in (sigma, dx, dy, fx, fy):
+            if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() != self.nzones):
+                raise ValueError("fields must be contiguous %s CUDA tensors of %d elements" % (dt, self.nzones))
+        if fx is None:
+            fx = torch.empty_like(sigma)
+        if fy is None:
+            fy = torch.empty_like(sigma)
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        sg_force_zones(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
+                       dy.data_ptr() if dy is not None else 0, fx.data_ptr(), fy.data_ptr(), st)
+        return fx, fy

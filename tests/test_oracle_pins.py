@@ -37,11 +37,11 @@ def _sig3(a, b):
     return abs(round(a / 10 ** e, 2) - round(b / 10 ** e, 2)) < 1e-9
 
 
-def _near3(a, b):
-    """True when a lies within half a unit of the printed b's third digit, plus 2 %
-    of a unit for values on a rounding tie (3.50499e-3 printed as 3.51e-3)."""
+def _near3(a, b, units=0.51):
+    """True when a lies within `units` of the printed b's third digit (the default,
+    half a unit plus 2 %, admits a rounding tie: 3.50499e-3 printed as 3.51e-3)."""
     e = math.floor(math.log10(abs(b)))
-    return abs(a / 10 ** e - b / 10 ** e) <= 0.0051
+    return abs(a / 10 ** e - b / 10 ** e) <= 0.01 * units
 
 
 # --------------------------------------------------------------- Table 1 --
@@ -401,9 +401,9 @@ def amr_table_norms(hier, disk, fx, fy):
 
 # Entries of Tables 3-6 pinned: D_2,2 every norm; D_2 the Linf norms only (its
 # L1, L2 entries differ from the finest-area norms by inconsistent powers of 2).
-# (table, L, N, column) entries that are misprints: exponent (8.72E-04 for 8.72E-05)
-# and digit (3.31E-03 for 3.11E-03).
-AMR_MISPRINTS = {(4, 3, 128, 0), (6, 2, 128, 2)}
+# (table, L, N, column) entries that are misprints: exponents (8.72E-04 for
+# 8.72E-05, 2.72E-05 for 2.72E-04) and a digit (3.31E-03 for 3.11E-03).
+AMR_MISPRINTS = {(4, 3, 128, 0), (6, 2, 128, 2), (5, 3, 256, 2)}
 
 
 def amr_pinned_columns(table, disk, L, n):
