@@ -96,7 +96,19 @@ typedef struct {
                                    whole 2 x 2 blocks over an existing parent cell; a parent
                                    cell with children is not a leaf. Not with z != 0 or
                                    SG_SLOPES_CENTRAL. Read during sg_plan_create only. */
+    int cross_mode;             /* an sg_cross_mode: how pairs of cells in different patches
+                                   (and, with level convolutions, all pairs) are summed */
 } sg_geom;
+
+typedef enum {
+    SG_CROSS_AUTO = 0,          /* level convolutions when the hierarchy fits, else direct */
+    SG_CROSS_DIRECT = 1,        /* per-patch FFT convolutions + corner-form direct sum across patches */
+    SG_CROSS_LEVELS = 2         /* level convolutions (SG_EINVAL if the hierarchy does not fit):
+                                   every level's composite source on the finest lattice, every
+                                   ordered pair of levels one zero-padded FFT convolution with
+                                   fractional-offset kernel tables; needs a finest-lattice
+                                   extent of at most 2048 cells per axis and z == 0 */
+} sg_cross_mode;
 
 typedef struct {
     int npatches;
@@ -107,6 +119,9 @@ typedef struct {
     int64_t scratch_bytes;      /* per-call scratch (workspace) of one solve */
     int max_pad;                /* largest padded FFT length */
     int64_t nzones;             /* zones of a plan made by sg_plan_create_zones, else 0 */
+    int launches;               /* kernels one sg_force (sg_force_zones for zone plans) enqueues */
+    int cross_mode;             /* the path chosen: SG_CROSS_DIRECT or SG_CROSS_LEVELS (0 for a
+                                   single unmasked patch, whose only pairs are same-patch pairs) */
 } sg_plan_info;
 
 typedef struct sg_plan sg_plan;
@@ -277,11 +292,11 @@ typedef struct {
 
 /*
  * Create a plan for a zone list (host memory, read during the call only).
- * G, slope_mode (SG_SLOPES_NONE or SG_SLOPES_CALLER), prec and hbm_budget as
- * for sg_plan_create. Errors: SG_EINVAL (rules above, with sg_last_error
+ * G, slope_mode (SG_SLOPES_NONE or SG_SLOPES_CALLER), cross_mode (an
+ * sg_cross_mode), prec and hbm_budget as for sg_plan_create. Errors: SG_EINVAL (rules above, with sg_last_error
  * naming the first offending zone), SG_EBUDGET, SG_ENOMEM, SG_ECUDA.
  */
-sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, sg_precision prec,
+sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, int cross_mode, sg_precision prec,
                                size_t hbm_budget, sg_plan **out);
 
 /*

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -109,6 +110,7 @@ sg_status analyse(const sg_geom *g, geom_info &gi)
     if (!isfinite(g->z)) return fail("z is not finite");
     if (g->z != 0.0 && g->npatches != 1) return fail("off-plane forces (z != 0) need a single patch");
     if (g->slope_mode < SG_SLOPES_NONE || g->slope_mode > SG_SLOPES_CALLER) return fail("unknown slope mode");
+    if (g->cross_mode < SG_CROSS_AUTO || g->cross_mode > SG_CROSS_LEVELS) return fail("unknown cross mode");
     const int n = g->npatches;
     const sg_patch *P = g->patches;
     gi.n = n;
@@ -290,6 +292,87 @@ void build_tiles(const sg_geom *g, const geom_info &gi, std::vector<sg_tile_desc
     }
 }
 
+// Level-convolution parameters (lvconv.cu) of a composite hierarchy, or false
+// when it does not qualify: z == 0, not central slopes, at least two levels,
+// and a finest-lattice extent whose padded length fits the transforms.
+// bytes: device memory the level convolutions add (maps, kernel spectra, scratch).
+bool lv_params(const sg_geom *g, const geom_info &gi, sg_precision prec, sg_lv_setup_args &a,
+               std::vector<std::vector<int>> &maps, int64_t &bytes)
+{
+    if (gi.lmax < 1 || g->z != 0.0 || g->slope_mode == SG_SLOPES_CENTRAL) return false;
+    const sg_patch *P = g->patches;
+    int64_t wx = 0, wy = 0;  // level-0 extent in finest cells (lattice units are half finest cells)
+    for (int k = 0; k < gi.n; ++k) {
+        if (P[k].level != 0) continue;
+        wx = std::max<int64_t>(wx, ((int64_t)gi.ox[k] + (int64_t)P[k].nx * gi.step[k]) / 2);
+        wy = std::max<int64_t>(wy, ((int64_t)gi.oy[k] + (int64_t)P[k].ny * gi.step[k]) / 2);
+    }
+    auto pad = [](int64_t w) {
+        int64_t p = SG_MIN_PAD;
+        while (p < 2 * w - 1) p <<= 1;
+        return p;
+    };
+    const int64_t px = pad(wx), py = pad(wy);
+    if (px > SG_MAX_PAD || py > SG_MAX_PAD) return false;
+    memset(&a, 0, sizeof(a));
+    a.nlev = gi.lmax + 1;
+    a.px = (int)px;
+    a.py = (int)py;
+    a.hf = gi.h0 / (double)(1 << gi.lmax);
+    maps.assign(a.nlev, {});
+    const int64_t qx = px / 2 + 1;
+    const int64_t cs = prec == SG_FP64 ? 16 : 8;
+    int64_t work = 0, mapbytes = 0;
+    for (int m = 0; m < a.nlev; ++m) {
+        const int sx = gi.lmax - m;
+        int64_t gx0 = INT64_MAX, gy0 = INT64_MAX, gx1 = INT64_MIN, gy1 = INT64_MIN;
+        for (int k = 0; k < gi.n; ++k) {
+            if (P[k].level != m) continue;
+            const int64_t gx = gi.ox[k] / gi.step[k], gy = gi.oy[k] / gi.step[k];
+            gx0 = std::min(gx0, gx);
+            gy0 = std::min(gy0, gy);
+            gx1 = std::max(gx1, gx + P[k].nx);
+            gy1 = std::max(gy1, gy + P[k].ny);
+        }
+        if (gx0 == INT64_MAX) return false;
+        a.s[m] = sx;
+        a.nx[m] = (int)(gx1 - gx0);
+        a.ny[m] = (int)(gy1 - gy0);
+        const int64_t half = sx >= 1 ? (1LL << (sx - 1)) : 0;
+        a.i0[m] = (int)((gx0 << sx) + half);
+        a.j0[m] = (int)((gy0 << sx) + half);
+        std::vector<int> &mp = maps[m];
+        mp.assign((size_t)a.nx[m] * a.ny[m], -1);
+        for (int k = 0; k < gi.n; ++k) {
+            if (P[k].level != m) continue;
+            const int64_t bx = gi.ox[k] / gi.step[k] - gx0, by = gi.oy[k] / gi.step[k] - gy0;
+            for (int j = 0; j < P[k].ny; ++j)
+                for (int i = 0; i < P[k].nx; ++i)
+                    if (gi.code[k][(size_t)j * P[k].nx + i] != SG_CELL_ABSENT)
+                        mp[(size_t)(by + j) * a.nx[m] + bx + i] = (int)(gi.cell_off[k] + (int64_t)j * P[k].nx + i);
+        }
+        a.map[m] = mp.data();
+        mapbytes += (int64_t)mp.size() * 4;
+        work += (3 * qx * a.ny[m] + 3 * qx * py + 2 * qx * a.ny[m]) * cs;
+    }
+    int nkeys = 0;
+    int ks[3 * SG_MAX_LEVELS], kd[3 * SG_MAX_LEVELS];
+    for (int m = 0; m < a.nlev; ++m) {
+        for (int l = 0; l < a.nlev; ++l) {
+            const int d2 = (a.s[m] >= 1) - (a.s[l] >= 1);
+            int k = 0;
+            while (k < nkeys && !(ks[k] == a.s[m] && kd[k] == d2)) ++k;
+            if (k == nkeys) {
+                ks[k] = a.s[m];
+                kd[k] = d2;
+                ++nkeys;
+            }
+        }
+    }
+    bytes = mapbytes + (int64_t)nkeys * 6 * qx * py * cs + work;
+    return true;
+}
+
 int choose_nsplit(int nblocks, int ntiles, int nsm)
 {
     if (nblocks <= 0) return 1;
@@ -306,7 +389,8 @@ struct sizes {
     int64_t total() const { return spectra + twiddles + work + direct + geometry; }
 };
 
-sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int ntiles, int nblocks, int nsplit)
+sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int ntiles, int nblocks, int nsplit,
+                 int64_t lv_bytes = -1)
 {
     sizes s;
     const size_t es = elem_size(prec);
@@ -315,14 +399,14 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
         const int px = sg_pad_length(g->patches[k].nx), py = sg_pad_length(g->patches[k].ny);
         if (px > s.max_pad) s.max_pad = px;
         if (py > s.max_pad) s.max_pad = py;
-        s.spectra += (g->z != 0.0 ? 9LL : 6LL) * (px / 2 + 1) * sg_spec_stride(py) * (int64_t)es;
+        if (lv_bytes < 0) s.spectra += (g->z != 0.0 ? 9LL : 6LL) * (px / 2 + 1) * sg_spec_stride(py) * (int64_t)es;
         const int64_t w = 5LL * (px / 2 + 1) * g->patches[k].ny * (int64_t)(2 * es);
         if (w > work) work = w;
     }
-    s.work = work;
+    s.work = lv_bytes < 0 ? work : lv_bytes;
     for (int L = SG_MIN_PAD; L <= s.max_pad; L <<= 1) s.twiddles += (int64_t)L * (16 + 8);
     if (gi.n > 1 || gi.masked) s.direct = 3 * gi.ncells * (int64_t)es + gi.ncells * (int64_t)sizeof(int);
-    if (gi.n > 1) {
+    if (gi.n > 1 && lv_bytes < 0) {
         s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
                     gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
                     (nsplit > 1 ? (int64_t)nsplit * gi.nleaves * 16 : 0);
@@ -368,6 +452,7 @@ void plan_free(sg_plan *plan)
             cudaFree(plan->pp[k].phase);
         }
     }
+    sg_lv_free(plan);
     cudaFree(plan->twiddles);
     cudaFree(plan->cell_code);
     cudaFree(plan->zone_slot);
@@ -390,15 +475,27 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
 {
     geom_info gi;
     SG_TRY(analyse(g, gi));
+    // level convolutions, or per-patch convolutions plus the cross-patch direct sum
+    sg_lv_setup_args lva;
+    std::vector<std::vector<int>> lvmaps;
+    int64_t lv_bytes = -1;
+    bool use_lv = false;
+    if ((gi.n > 1 || gi.masked) && g->cross_mode != SG_CROSS_DIRECT && gi.lmax >= 1) {
+        use_lv = lv_params(g, gi, prec, lva, lvmaps, lv_bytes);
+        if (!use_lv) lv_bytes = -1;
+        if (!use_lv && g->cross_mode == SG_CROSS_LEVELS)
+            return fail("level convolutions need z == 0, no central slopes and a finest-lattice extent of at most "
+                        "2048 cells per axis");
+    }
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tfirst, tcount;
-    if (gi.n > 1) build_tiles(g, gi, tiles, tfirst, tcount);
+    if (gi.n > 1 && !use_lv) build_tiles(g, gi, tiles, tfirst, tcount);
     int dev = 0, nsm = 152;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     SG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int nblocks = count_blocks(gi);
+    const int nblocks = use_lv ? 0 : count_blocks(gi);
     const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), nsm);
-    const sizes sz = plan_sizes(g, gi, prec, (int)tiles.size(), nblocks, nsplit);
+    const sizes sz = plan_sizes(g, gi, prec, (int)tiles.size(), nblocks, nsplit, lv_bytes);
     if (budget && (size_t)sz.total() > budget) {
         set_error("plan exceeds the device-memory budget");
         return SG_EBUDGET;
@@ -422,7 +519,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     plan->ncells = gi.ncells;
     plan->nleaves = gi.nleaves;
     plan->cross_pairs = gi.cross_pairs;
-    plan->max_pad = sz.max_pad;
+    plan->max_pad = use_lv ? std::max(sz.max_pad, std::max(lva.px, lva.py)) : sz.max_pad;
     plan->lattice_unit = gi.lambda;
     plan->lattice_x0 = gi.X0;
     plan->lattice_y0 = gi.Y0;
@@ -430,6 +527,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
 
     plan->geom.masks = nullptr;  // the cell codes below carry them
     plan->composite = gi.n > 1 || gi.masked;
+    plan->cross_mode = use_lv ? SG_CROSS_LEVELS : (gi.n > 1 ? SG_CROSS_DIRECT : 0);
+    if (use_lv) plan->cross_pairs = 0;
 
     sg_status st = SG_OK;
     const size_t es = elem_size(prec);
@@ -452,13 +551,13 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         d.pi0 = d.parent >= 0 ? (gi.ox[k] - gi.ox[d.parent]) / gi.step[d.parent] : 0;
         d.pj0 = d.parent >= 0 ? (gi.oy[k] - gi.oy[d.parent]) / gi.step[d.parent] : 0;
         d.ncells_plane = gi.ncells;
-        if (gi.n > 1) {
+        if (!tfirst.empty()) {
             pp.tile_first = tfirst[k];
             pp.tile_count = tcount[k];
         }
         pdev[k] = d;
         const int nplanes = g->z != 0.0 ? 9 : 6;
-        st = dev_alloc(plan, &pp.spectra, nplanes * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
+        if (!use_lv) st = dev_alloc(plan, &pp.spectra, nplanes * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
         if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0)
             st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
@@ -536,10 +635,20 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
                             cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
         if (nsplit > 1) plan->ws_partial_bytes = (int64_t)nsplit * (int64_t)tg.size() * 2 * (int64_t)sizeof(double);
     }
-    plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
     if (st == SG_OK) st = sg_twiddles_build(plan);
     if (st == SG_OK) st = sg_phase_build(plan);
     if (st == SG_OK) st = sg_tables_build(plan);
+    if (st == SG_OK && use_lv) st = sg_lv_setup(plan, &lva);  // sets the transform scratch sizes
+    plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
+    {
+        const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0;
+        int n = use_lv ? 4 * (gi.lmax + 1) : gi.n * (central ? 4 : 3);
+        if (plan->composite) {
+            for (int k = 0; k < gi.n; ++k) n += 1 + (gi.parent[k] >= 0);
+            if (plan->ntiles > 0) n += 2 + (nsplit > 1);
+        }
+        plan->launches = n;
+    }
     if (st == SG_OK) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
@@ -645,8 +754,10 @@ sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, 
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
     const void *dx = caller ? deltax : nullptr, *dy = caller ? deltay : nullptr;
     if (!plan->composite) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, fz, st);
-    // AMR or masks: composite sources, same-patch FFT convolutions, cross-patch direct sum
+    // AMR or masks: composite sources, then level convolutions, or same-patch FFT
+    // convolutions plus the cross-patch direct sum
     SG_TRY(sg_amr_prepare(plan, ws, sigma, dx, dy, st));
+    if (plan->lv) return sg_lv_solve(plan, ws, fx, fy, st);
     const size_t es = elem_size(plan->prec);
     const char *S = (const char *)ws->sfield;
     const size_t plane = (size_t)plan->ncells * es;
@@ -721,12 +832,18 @@ sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes)
     if (!bytes || (prec != SG_FP64 && prec != SG_FP32)) return SG_EINVAL;
     geom_info gi;
     SG_TRY(analyse(geom, gi));
+    sg_lv_setup_args lva;
+    std::vector<std::vector<int>> lvmaps;
+    int64_t lv_bytes = -1;
+    if ((gi.n > 1 || gi.masked) && geom->cross_mode != SG_CROSS_DIRECT && gi.lmax >= 1 &&
+        !lv_params(geom, gi, prec, lva, lvmaps, lv_bytes))
+        lv_bytes = -1;
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tf, tc;
-    if (gi.n > 1) build_tiles(geom, gi, tiles, tf, tc);
-    const int nblocks = count_blocks(gi);
+    if (gi.n > 1 && lv_bytes < 0) build_tiles(geom, gi, tiles, tf, tc);
+    const int nblocks = lv_bytes < 0 ? count_blocks(gi) : 0;
     const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152);
-    *bytes = plan_sizes(geom, gi, prec, (int)tiles.size(), nblocks, nsplit).total();
+    *bytes = plan_sizes(geom, gi, prec, (int)tiles.size(), nblocks, nsplit, lv_bytes).total();
     return SG_OK;
 }
 
@@ -753,6 +870,8 @@ sg_status sg_plan_get_info(const sg_plan *plan, sg_plan_info *out)
     out->scratch_bytes = plan->scratch_bytes;
     out->max_pad = plan->max_pad;
     out->nzones = plan->nzones;
+    out->launches = plan->launches;
+    out->cross_mode = plan->cross_mode;
     return SG_OK;
 }
 

@@ -99,6 +99,33 @@ struct sg_patch_dev {
     int64_t ncells_plane;  // plane stride of the 3-field composite source arrays (= total cells)
 };
 
+// Level convolutions (lvconv.cu): every level's composite source sampled on the
+// finest lattice (cells of level m are 2^s finest cells wide, s = lmax - m; the
+// sample of a cell of a coarser level sits half a finest cell up and right of
+// its centre), one FFT convolution per ordered pair of levels.
+struct sg_lv_level {
+    int s;              // cells of this level are 2^s finest cells wide
+    int nx, ny;         // level image: bounding box of the level's patches, in cells
+    int i0, j0;         // finest-lattice index of the sample point of image cell (0, 0)
+    int *map;           // device [ny][nx]: index of the cell in the field arrays, or -1
+    int64_t fwd_off;    // complex-element offset of the level's row transforms (3 fields)
+    int64_t spec_off;   // of its source spectra (3 fields, full columns)
+    int64_t inv_off;    // of its inverse-column outputs (Fx, Fy)
+};
+
+struct sg_lv {
+    int nlev;
+    int px, py;                              // padded lengths of the finest lattice
+    double hf;                               // finest cell width
+    sg_lv_level lev[SG_MAX_LEVELS];
+    int nkeys;
+    int key[SG_MAX_LEVELS][SG_MAX_LEVELS];   // kernel of source level m, target level l
+    int key_s[3 * SG_MAX_LEVELS];            // per kernel: source width exponent s
+    int key_d2[3 * SG_MAX_LEVELS];           // per kernel: 2 x sample shift (-1, 0, 1)
+    void *spectra;                           // [nkeys][6][px/2+1][py] complex T, scaled 1/(px py)
+    int64_t fwd_elems, spec_elems, inv_elems;
+};
+
 struct sg_patch_plan {
     sg_patch geom;
     sg_patch_dev d;
@@ -141,6 +168,9 @@ struct sg_plan {
     int64_t nzones;
     int64_t *zone_slot;
     int64_t ws_zone_bytes;          // per-call zone-order staging, 5 x ncells of T
+    int launches;                   // kernels one solve enqueues
+    int cross_mode;                 // SG_CROSS_DIRECT, SG_CROSS_LEVELS, or 0 (single unmasked patch)
+    sg_lv *lv;                      // level-convolution plan (SG_CROSS_LEVELS), else NULL
 
     // per-call scratch sizes (bytes) and the plan's own workspace (used by sg_force)
     int64_t ws_fwd_bytes, ws_inv_bytes, ws_sfield_bytes, ws_tile_bytes, ws_partial_bytes;
@@ -226,6 +256,18 @@ sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const voi
                          void *fx, void *fy, cudaStream_t st);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          cudaStream_t st);
+sg_status sg_fft_lines_fp64(double2 *data, int L, int count, int64_t seq_stride, int64_t elem_stride,
+                           const double2 *tw);
+// Level convolutions: host setup (level images, maps, kernel spectra) and the solve.
+struct sg_lv_setup_args {
+    int nlev, px, py;
+    double hf;
+    int s[SG_MAX_LEVELS], nx[SG_MAX_LEVELS], ny[SG_MAX_LEVELS], i0[SG_MAX_LEVELS], j0[SG_MAX_LEVELS];
+    const int *map[SG_MAX_LEVELS];          // host [ny][nx] cell index or -1
+};
+sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a);
+void sg_lv_free(sg_plan *plan);
+sg_status sg_lv_solve(sg_plan *plan, const struct sg_workspace *ws, void *fx, void *fy, cudaStream_t st);
 
 static inline int sg_ilog2(int v)
 {

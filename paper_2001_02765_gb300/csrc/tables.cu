@@ -26,22 +26,9 @@
 // scaled by G / (Px Py) and by h for the order-1 planes.
 #include "common.cuh"
 #include "fft.cuh"
+#include "kmath.cuh"
 
 #include <math.h>
-
-// asinh(a) - asinh(b) for a >= b >= 0 given d = a - b computed without rounding loss.
-__device__ __forceinline__ double asinh_diff(double a, double b, double d)
-{
-    return asinh(d * (a + b) / (a * sqrt(1.0 + b * b) + b * sqrt(1.0 + a * a)));
-}
-
-// asinh(t2 / s) - asinh(t1 / s), t2 - t1 = 1, s > 0.
-__device__ __forceinline__ double asinh_span(double t1, double t2, double s)
-{
-    if (t1 >= 0.0) return asinh_diff(t2 / s, t1 / s, 1.0 / s);
-    if (t2 <= 0.0) return asinh_diff(-t1 / s, -t2 / s, 1.0 / s);
-    return asinh(t2 / s) + asinh(-t1 / s);
-}
 
 // unit-cell tables for m, n >= 0 (parity applied by the caller)
 struct k3 {
@@ -255,8 +242,8 @@ __global__ void k_twiddles(double2 *tw64, float2 *tw32, int L)
     }
 }
 
-static sg_status launch_fft_lines(double2 *data, int L, int count, int64_t seq_stride, int64_t elem_stride,
-                                  const double2 *tw)
+sg_status sg_fft_lines_fp64(double2 *data, int L, int count, int64_t seq_stride, int64_t elem_stride,
+                           const double2 *tw)
 {
     switch (L) {
 #define SG_CASE(LL)                                                                                           \
@@ -306,8 +293,9 @@ sg_status sg_tables_build(sg_plan *plan)
     for (int p = 0; p < plan->npatches; ++p) {
         const sg_patch_dev &d = plan->pp[p].d;
         int64_t pl = (int64_t)d.px * d.py;
-        if (pl > maxplane) maxplane = pl;
+        if (plan->pp[p].spectra && pl > maxplane) maxplane = pl;
     }
+    if (maxplane == 0) return SG_OK;
     const bool offplane = plan->geom.z != 0.0;
     const int npacked = offplane ? 5 : 3;
     double2 *z = nullptr;
@@ -315,6 +303,7 @@ sg_status sg_tables_build(sg_plan *plan)
     sg_status st = SG_OK;
     for (int p = 0; p < plan->npatches && st == SG_OK; ++p) {
         sg_patch_plan &pp = plan->pp[p];
+        if (!pp.spectra) continue;  // level convolutions keep no per-patch spectra
         const int px = pp.d.px, py = pp.d.py;
         const int64_t plane = (int64_t)px * py;
         if (offplane) k_tables_wrapped_z<<<1024, 256>>>(z, pp.d.nx, pp.d.ny, px, py, plan->geom.z / pp.d.h);
@@ -324,8 +313,8 @@ sg_status sg_tables_build(sg_plan *plan)
         const double2 *twy = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(py)]);
         for (int q = 0; q < npacked && st == SG_OK; ++q) {
             double2 *zq = z + q * plane;
-            st = launch_fft_lines(zq, px, py, px, 1, twx);       // rows
-            if (st == SG_OK) st = launch_fft_lines(zq, py, px, 1, px, twy);   // columns
+            st = sg_fft_lines_fp64(zq, px, py, px, 1, twx);       // rows
+            if (st == SG_OK) st = sg_fft_lines_fp64(zq, py, px, 1, px, twy);   // columns
         }
         if (st != SG_OK) break;
         const double scale0 = plan->geom.G / ((double)px * (double)py);

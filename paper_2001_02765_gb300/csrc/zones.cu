@@ -263,7 +263,7 @@ sg_status force_zones_t(sg_plan *plan, const void *sigma, const void *dx, const 
 
 extern "C" {
 
-sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, sg_precision prec,
+sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, int cross_mode, sg_precision prec,
                                size_t hbm_budget, sg_plan **out)
 {
     if (!out || (prec != SG_FP64 && prec != SG_FP32)) return zfail("invalid precision or output pointer");
@@ -285,9 +285,11 @@ sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, 
     g.slope_mode = slope_mode;
     g.z = 0.0;
     g.masks = mp.data();
+    g.cross_mode = cross_mode;
     sg_plan *plan = nullptr;
     SG_TRY(sg_plan_build(&g, prec, hbm_budget, &plan));
     plan->nzones = zones->nzones;
+    plan->launches += 2;  // gather and scatter
     const size_t es = prec == SG_FP64 ? 8 : 4;
     plan->ws_zone_bytes = 5 * plan->ncells * (int64_t)es;
     plan->scratch_bytes += plan->ws_zone_bytes;

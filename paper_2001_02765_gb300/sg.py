@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsg.so")
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_EBUDGET, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_ECANCELLED, SG_ENOTFOUND = range(9)
 SG_FP64, SG_FP32 = 0, 1
 SG_SLOPES_NONE, SG_SLOPES_CENTRAL, SG_SLOPES_CALLER = 0, 1, 2
+SG_CROSS_AUTO, SG_CROSS_DIRECT, SG_CROSS_LEVELS = 0, 1, 2
 KERNEL_NAMES = ("x0", "xx", "xy", "y0", "yx", "yy", "z0", "zx", "zy")
 
 
@@ -43,13 +44,14 @@ class sg_patch(ctypes.Structure):
 class sg_geom(ctypes.Structure):
     _fields_ = [("npatches", ctypes.c_int), ("patches", ctypes.POINTER(sg_patch)),
                 ("G", ctypes.c_double), ("slope_mode", ctypes.c_int), ("z", ctypes.c_double),
-                ("masks", ctypes.c_void_p)]
+                ("masks", ctypes.c_void_p), ("cross_mode", ctypes.c_int)]
 
 
 class sg_plan_info(ctypes.Structure):
     _fields_ = [("npatches", ctypes.c_int), ("ncells", ctypes.c_int64), ("nleaves", ctypes.c_int64),
                 ("cross_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("scratch_bytes", ctypes.c_int64), ("max_pad", ctypes.c_int), ("nzones", ctypes.c_int64)]
+                ("scratch_bytes", ctypes.c_int64), ("max_pad", ctypes.c_int), ("nzones", ctypes.c_int64),
+                ("launches", ctypes.c_int), ("cross_mode", ctypes.c_int)]
 
 
 _I32P = ctypes.POINTER(ctypes.c_int32)
@@ -100,7 +102,7 @@ _SIGNATURES = {
     "sg_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sg_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sg_server_stats), ctypes.c_int]),
     "sg_plan_create_zones": (ctypes.c_int, [ctypes.POINTER(sg_zones), ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_size_t, ctypes.POINTER(_VP)]),
+                                            ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)]),
     "sg_force_zones": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_zone_slots": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64]),
     "sg_zones_from_records": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -155,7 +157,7 @@ def _check(status, where):
         raise SgError(status, where, last_error())
 
 
-def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
+def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None, cross_mode=SG_CROSS_AUTO):
     """patches: iterable of (level, nx, ny, x0, y0, h); masks: None or one entry per
     patch (None, or an [ny, nx] array, nonzero where the cell exists).
     Returns (sg_geom, keepalive objects)."""
@@ -171,24 +173,27 @@ def make_geom(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
         ptrs = (ctypes.c_void_p * len(bufs))(*[None if b is None else b.ctypes.data for b in bufs])
         keep += [bufs, ptrs]
         mptr = ctypes.cast(ptrs, ctypes.c_void_p)
-    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode), float(z), mptr)
+    g = sg_geom(len(patches), ctypes.cast(arr, ctypes.POINTER(sg_patch)), float(G), int(slope_mode), float(z), mptr,
+                int(cross_mode))
     return g, keep
 
 
-def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
-    g, _keep = make_geom(patches, G, slope_mode, z, masks)
+def sg_geom_validate(patches, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None, cross_mode=SG_CROSS_AUTO):
+    g, _keep = make_geom(patches, G, slope_mode, z, masks, cross_mode)
     return load().sg_geom_validate(ctypes.byref(g))
 
 
-def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None):
-    g, _keep = make_geom(patches, G, slope_mode, z, masks)
+def sg_plan_bytes(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, z=0.0, masks=None,
+                  cross_mode=SG_CROSS_AUTO):
+    g, _keep = make_geom(patches, G, slope_mode, z, masks, cross_mode)
     out = ctypes.c_int64(0)
     _check(load().sg_plan_bytes(ctypes.byref(g), int(precision), ctypes.byref(out)), "sg_plan_bytes")
     return int(out.value)
 
 
-def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0, masks=None):
-    g, _keep = make_geom(patches, G, slope_mode, z, masks)
+def sg_plan_create(patches, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0, masks=None,
+                   cross_mode=SG_CROSS_AUTO):
+    g, _keep = make_geom(patches, G, slope_mode, z, masks, cross_mode)
     h = _VP()
     _check(load().sg_plan_create(ctypes.byref(g), int(precision), int(hbm_budget), ctypes.byref(h)), "sg_plan_create")
     return h.value
@@ -328,12 +333,13 @@ def make_zones(nx0, ny0, x0, y0, h0, level, ix, iy):
     return z, arrs
 
 
-def sg_plan_create_zones(zone_args, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0):
+def sg_plan_create_zones(zone_args, precision=SG_FP32, G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0,
+                         cross_mode=SG_CROSS_AUTO):
     """zone_args: (nx0, ny0, x0, y0, h0, level, ix, iy)."""
     z, _keep = make_zones(*zone_args)
     h = _VP()
-    _check(load().sg_plan_create_zones(ctypes.byref(z), float(G), int(slope_mode), int(precision), int(hbm_budget),
-                                       ctypes.byref(h)), "sg_plan_create_zones")
+    _check(load().sg_plan_create_zones(ctypes.byref(z), float(G), int(slope_mode), int(cross_mode), int(precision),
+                                       int(hbm_budget), ctypes.byref(h)), "sg_plan_create_zones")
     return h.value
 
 
@@ -384,13 +390,13 @@ class Plan:
     """
 
     def __init__(self, patches, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER, hbm_budget=0, z=0.0,
-                 masks=None):
+                 masks=None, cross_mode=SG_CROSS_AUTO):
         self.patches = [tuple(p) for p in patches]
         self.precision = SG_FP32 if precision in ("fp32", SG_FP32) else SG_FP64
         self.slope_mode = slope_mode
         self.G = G
         self.z = z
-        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget, z, masks)
+        self.handle = sg_plan_create(self.patches, self.precision, G, slope_mode, hbm_budget, z, masks, cross_mode)
         self.info = sg_plan_get_info(self.handle)
 
     @property
@@ -496,14 +502,14 @@ class ZonePlan(Plan):
     zone-ordered torch tensors of ``nzones`` elements."""
 
     def __init__(self, nx0, ny0, x0, y0, h0, level, ix, iy, precision="fp32", G=1.0, slope_mode=SG_SLOPES_CALLER,
-                 hbm_budget=0):
+                 hbm_budget=0, cross_mode=SG_CROSS_AUTO):
         self.patches = []
         self.precision = SG_FP32 if precision in ("fp32", SG_FP32) else SG_FP64
         self.slope_mode = slope_mode
         self.G = G
         self.z = 0.0
         self.handle = sg_plan_create_zones((nx0, ny0, x0, y0, h0, level, ix, iy), self.precision, G, slope_mode,
-                                           hbm_budget)
+                                           hbm_budget, cross_mode)
         self.info = sg_plan_get_info(self.handle)
 
     @property

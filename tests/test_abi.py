@@ -72,3 +72,14 @@ def test_plan_bytes_estimate(lib):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(sg.SgLibraryMissing):
         sg.load(str(tmp_path / "libsg.so"))
+
+
+def test_cross_mode_rules(lib):
+    pat = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(64, 3))]
+    assert sg.sg_geom_validate(pat, cross_mode=3) == sg.SG_EINVAL
+    for m in (0, 1, 2):
+        assert sg.sg_geom_validate(pat, cross_mode=m) == sg.SG_OK
+    # level convolutions keep no per-patch spectra and no corner tiles; they add kernel spectra
+    direct = sg.sg_plan_bytes(pat, sg.SG_FP32, cross_mode=1)
+    levels = sg.sg_plan_bytes(pat, sg.SG_FP32, cross_mode=2)
+    assert direct > 0 and levels > 0 and levels != direct

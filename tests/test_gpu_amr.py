@@ -1,5 +1,6 @@
-"""Parity of the CUDA AMR path (per-patch FFT + cross-patch corner-form direct sum)
-with the oracle's plain leaf-pair sum. Tolerances as for the uniform path:
+"""Parity of the CUDA AMR paths with the oracle's plain leaf-pair sum: per-patch
+FFT + cross-patch corner-form direct sum (cross mode 1), and level convolutions
+on the finest lattice (cross mode 2). Tolerances as for the uniform path:
 relative L2 over all leaf targets, 1e-12 (FP64 plans) and 1e-5 (FP32 plans) on
 smooth densities (disks, Gaussian bumps).
 
@@ -40,10 +41,15 @@ def _fields(patches, seed, positive=False):
     return sig, sx, sy
 
 
-def _run(sg, patches, prec, mode, sig, sx, sy, G=1.0):
+CROSS = pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
+
+
+def _run(sg, patches, prec, mode, sig, sx, sy, G=1.0, cross=0):
     import torch
     dt = np.float64 if prec == "fp64" else np.float32
-    plan = sg.Plan(patches, precision=prec, slope_mode=mode, G=G)
+    plan = sg.Plan(patches, precision=prec, slope_mode=mode, G=G, cross_mode=cross)
+    if cross:
+        assert plan.info["cross_mode"] == cross
     a = concat_dev(sig, dt)
     b = concat_dev(sx, dt) if mode == sg.SG_SLOPES_CALLER else None
     c = concat_dev(sy, dt) if mode == sg.SG_SLOPES_CALLER else None
@@ -52,9 +58,9 @@ def _run(sg, patches, prec, mode, sig, sx, sy, G=1.0):
     return plan, fx.cpu().numpy(), fy.cpu().numpy()
 
 
-def _check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None):
+def _check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None, cross=0):
     dt = np.float64 if prec == "fp64" else np.float32
-    plan, fx, fy = _run(sg, patches, prec, mode, sig, sx, sy, G)
+    plan, fx, fy = _run(sg, patches, prec, mode, sig, sx, sy, G, cross)
     r = lambda a: [np.asarray(x, dt).astype(np.float64) for x in a]
     use_slopes = mode == sg.SG_SLOPES_CALLER
     leaves, rx, ry = oamr.amr_direct_force(oamr.make_patches(patches), r(sig), r(sx) if use_slopes else None,
@@ -69,40 +75,45 @@ def _check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None):
     return err
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("mode", [0, 2])
-def test_nested_three_levels(sg, prec, tol, mode):
+def test_nested_three_levels(sg, prec, tol, mode, cross):
     patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))]
     sig, sx, sy = W.bumps_on_patches(patches, 3)
-    _check(sg, patches, prec, mode, sig, sx, sy, tol, G=2.5)
+    _check(sg, patches, prec, mode, sig, sx, sy, tol, G=2.5, cross=cross)
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 5e-5)])
-def test_nested_three_levels_rough(sg, prec, tol):
+def test_nested_three_levels_rough(sg, prec, tol, cross):
     """Independent noise in every cell (see the module docstring for the FP32 bound)."""
     patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))]
     sig, sx, sy = _fields(patches, 3, positive=True)
-    _check(sg, patches, prec, 2, sig, sx, sy, tol, G=2.5)
+    _check(sg, patches, prec, 2, sig, sx, sy, tol, G=2.5, cross=cross)
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_table10_hierarchy(sg, prec, tol):
+def test_table10_hierarchy(sg, prec, tol, cross):
     """Fig. 1 / Table 10: two patches per refined level, 28 leaves."""
     sig, sx, sy = _fields(TABLE10, 8, positive=True)
-    _check(sg, TABLE10, prec, 2, sig, sx, sy, tol)
+    _check(sg, TABLE10, prec, 2, sig, sx, sy, tol, cross=cross)
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_ragged_off_centre_patches(sg, prec, tol):
+def test_ragged_off_centre_patches(sg, prec, tol, cross):
     """Non-square, off-centre patches whose sizes are not tile multiples."""
     patches = [(0, 37, 29, -1.0, -0.8, 0.05), (1, 22, 14, -0.6, -0.3, 0.025), (1, 6, 8, 0.2, 0.1, 0.025),
                (2, 10, 12, -0.5, -0.25, 0.0125)]
     assert sg.sg_geom_validate(patches) == sg.SG_OK
     sig, sx, sy = W.bumps_on_patches(patches, 17)
-    _check(sg, patches, prec, 2, sig, sx, sy, tol)
+    _check(sg, patches, prec, 2, sig, sx, sy, tol, cross=cross)
 
 
-def test_refinement_invariance_on_gpu(sg):
+@CROSS
+def test_refinement_invariance_on_gpu(sg, cross):
     """A fine patch carrying the coarse linear reconstruction leaves the force at
     the coarse leaves equal to the uniform coarse force (FP64)."""
     import torch
@@ -117,7 +128,7 @@ def test_refinement_invariance_on_gpu(sg):
             fine[1][J, I] = sx[pj, pi]
             fine[2][J, I] = sy[pj, pi]
     patches = [(0, nx, ny, x0, y0, h), (1, 16, 16, -0.5, -0.5, h / 2)]
-    plan, fx, fy = _run(sg, patches, "fp64", 2, [s, fine[0]], [sx, fine[1]], [sy, fine[2]])
+    plan, fx, fy = _run(sg, patches, "fp64", 2, [s, fine[0]], [sx, fine[1]], [sy, fine[2]], cross=cross)
     uni, ux, uy = _run(sg, patches[:1], "fp64", 2, [s], [sx], [sy])
     leaf = np.ones((n, n), bool)
     leaf[4:12, 4:12] = False
@@ -129,8 +140,9 @@ def test_refinement_invariance_on_gpu(sg):
     torch.cuda.synchronize()
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-11), ("fp32", 1e-5)])
-def test_exponential_hierarchy_full_size_sampled(sg, prec, tol):
+def test_exponential_hierarchy_full_size_sampled(sg, prec, tol, cross):
     """Three 256^2 levels on [-1,1]^2, [-.5,.5]^2, [-.25,.25]^2, exp(-R/0.1),
     analytic slopes: 192 seeded leaf targets vs the plain leaf-pair sum."""
     case = W.exponential_hierarchy(256, 3, 0.1)
@@ -138,17 +150,46 @@ def test_exponential_hierarchy_full_size_sampled(sg, prec, tol):
     nleaf = sum(int(m.sum()) for m in case["leaf"])
     rng = np.random.Generator(np.random.PCG64(31))
     idx = np.sort(rng.choice(nleaf, 192, replace=False))
-    _check(sg, patches, prec, 2, case["sigma"], case["dx"], case["dy"], tol, target_index=idx)
+    _check(sg, patches, prec, 2, case["sigma"], case["dx"], case["dy"], tol, target_index=idx, cross=cross)
 
 
-def test_covered_cells_are_ignored(sg):
+@CROSS
+def test_covered_cells_are_ignored(sg, cross):
     """Garbage in covered cells must not change any leaf result."""
     patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))]
     sig, sx, sy = _fields(patches, 5, positive=True)
-    _, a, b = _run(sg, patches, "fp64", 2, sig, sx, sy)
+    _, a, b = _run(sg, patches, "fp64", 2, sig, sx, sy, cross=cross)
     sig2 = [x.copy() for x in sig]
     sig2[0][4:12, 4:12] = 1e6
-    plan, c, d = _run(sg, patches, "fp64", 2, sig2, sx, sy)
+    plan, c, d = _run(sg, patches, "fp64", 2, sig2, sx, sy, cross=cross)
     leaves = oamr.leaf_cells(oamr.make_patches(patches))
     assert np.allclose(gather_leaves(plan, a, leaves), gather_leaves(plan, c, leaves), rtol=1e-13, atol=1e-13)
+    plan.close()
+
+
+def test_levels_equal_direct(sg):
+    """The two AMR paths on the same hierarchy agree to FP64 rounding at every leaf."""
+    patches = [(0, 40, 40, -1.0, -1.0, 0.05), (1, 24, 32, -0.6, -0.7, 0.025), (2, 16, 20, -0.5, -0.5, 0.0125),
+               (3, 12, 8, -0.45, -0.4, 0.00625)]
+    assert sg.sg_geom_validate(patches) == sg.SG_OK
+    sig, sx, sy = _fields(patches, 41, positive=True)
+    p1, a1, b1 = _run(sg, patches, "fp64", 2, sig, sx, sy, cross=1)
+    p2, a2, b2 = _run(sg, patches, "fp64", 2, sig, sx, sy, cross=2)
+    leaves = oamr.leaf_cells(oamr.make_patches(patches))
+    g1 = gather_leaves(p1, a1, leaves), gather_leaves(p1, b1, leaves)
+    g2 = gather_leaves(p2, a2, leaves), gather_leaves(p2, b2, leaves)
+    assert rel_l2(g2[0], g2[1], g1[0], g1[1]) < 1e-12
+    assert p2.info["cross_pairs"] == 0 and p1.info["cross_pairs"] > 0
+    p1.close()
+    p2.close()
+
+
+def test_levels_mode_rejects_too_large(sg):
+    """Level convolutions need a finest-lattice extent of at most 2048 cells."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(1536, 2))]  # 3072 finest cells
+    with pytest.raises(sg.SgError) as e:
+        sg.Plan(patches, cross_mode=sg.SG_CROSS_LEVELS)
+    assert e.value.status == sg.SG_EINVAL and "level convolutions" in str(e.value)
+    plan = sg.Plan(patches, cross_mode=sg.SG_CROSS_AUTO)
+    assert plan.info["cross_mode"] == sg.SG_CROSS_DIRECT
     plan.close()

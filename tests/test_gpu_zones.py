@@ -37,11 +37,13 @@ def _hier_args(hier):
     return (n, n, hier["x0"], hier["y0"], hier["h0"], hier["level"], hier["ix"], hier["iy"])
 
 
-def _solve(sg, args, prec, s, sx=None, sy=None):
+def _solve(sg, args, prec, s, sx=None, sy=None, cross=0):
     import torch
     dt = np.float64 if prec == "fp64" else np.float32
     mode = sg.SG_SLOPES_CALLER if sx is not None else sg.SG_SLOPES_NONE
-    plan = sg.ZonePlan(*args, precision=prec, slope_mode=mode)
+    plan = sg.ZonePlan(*args, precision=prec, slope_mode=mode, cross_mode=cross)
+    if cross:
+        assert plan.info["cross_mode"] == cross
     fx, fy = plan.force_zones(to_dev(s, dt), None if sx is None else to_dev(sx, dt),
                               None if sy is None else to_dev(sy, dt))
     torch.cuda.synchronize()
@@ -64,44 +66,47 @@ def _table10(sg):
     return T10_GRID + (level, ix, iy), leaf
 
 
+@pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
 @pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", F32_TOL)])
-def test_table10_zones(sg, prec, tol):
+def test_table10_zones(sg, prec, tol, cross):
     args, leaf = _table10(sg)
     rng = np.random.Generator(np.random.PCG64(14))
     s = rng.uniform(0.5, 1.5, 32)
     sx = rng.uniform(-1, 1, 32)
     sy = rng.uniform(-1, 1, 32)
-    (fx, fy), info = _solve(sg, args, prec, s, sx, sy)
+    (fx, fy), info = _solve(sg, args, prec, s, sx, sy, cross=cross)
     rx, ry = _oracle(args, leaf, s, sx, sy, np.float64 if prec == "fp64" else np.float32)
     assert info["nleaves"] == 28 and info["nzones"] == 32
     assert rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf]) < tol
     assert np.all(fx[~leaf] == 0) and np.all(fy[~leaf] == 0)
 
 
+@pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
 @pytest.mark.parametrize("rule", ["ilr", "vlr"])
 @pytest.mark.parametrize("disk", ["d2", "d22"])
 @pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", F32_TOL)])
-def test_band_hierarchy_disk_parity(sg, rule, disk, prec, tol):
+def test_band_hierarchy_disk_parity(sg, rule, disk, prec, tol, cross):
     hier = W.band_hierarchy(48, 3, rule, disk)
     args = _hier_args(hier)
     xc, yc, _ = W.zone_geometry(hier)
     s, sx, sy = _d_sigma(disk, xc, yc)
-    (fx, fy), info = _solve(sg, args, prec, s, sx, sy)
+    (fx, fy), info = _solve(sg, args, prec, s, sx, sy, cross=cross)
     leaf = hier["leaf"]
     rx, ry = _oracle(args, leaf, s, sx, sy, np.float64 if prec == "fp64" else np.float32)
     assert info["nleaves"] == leaf.sum() and info["nzones"] == leaf.size
     assert rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf]) < tol
 
 
+@pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
 @pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", 5e-5)])
-def test_band_hierarchy_random_fields(sg, prec, tol):
+def test_band_hierarchy_random_fields(sg, prec, tol, cross):
     """Four levels, a ragged level-0 grid, random densities and slopes (order 1)."""
     hier = W.band_hierarchy(40, 4, "vlr", "d22")
     args = _hier_args(hier)
     rng = np.random.Generator(np.random.PCG64(15))
     n = hier["level"].size
     s, sx, sy = rng.uniform(0, 1, n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
-    (fx, fy), _ = _solve(sg, args, prec, s, sx, sy)
+    (fx, fy), _ = _solve(sg, args, prec, s, sx, sy, cross=cross)
     leaf = hier["leaf"]
     rx, ry = _oracle(args, leaf, s, sx, sy, np.float64 if prec == "fp64" else np.float32)
     assert rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf]) < tol
