@@ -698,21 +698,67 @@ def run_gpu(args):
 TRAFFIC = {("spiral1024", "col_conv"): 33.8e6 + 0.03e6}
 
 
+def _pad(n):
+    p = 64
+    while p < 2 * n - 1:
+        p *= 2
+    return p
+
+
+def lv_geometry(wl):
+    """Level-convolution layout of a workload: padded finest-lattice lengths and
+    the (nx, ny) of every level's image (bounding box of its cells)."""
+    if "zones" in wl:
+        nx0, ny0, x0, y0, h0, level, ix, iy = wl["zones"]
+        lmax = int(level.max())
+        imgs = []
+        for m in range(lmax + 1):
+            sel = level == m
+            imgs.append((int(ix[sel].max() - ix[sel].min() + 1), int(iy[sel].max() - iy[sel].min() + 1)))
+        wx, wy = nx0 << lmax, ny0 << lmax
+    else:
+        pats = wl["patches"]
+        lmax = max(p[0] for p in pats)
+        h0 = pats[0][5]
+        X0 = min(p[3] for p in pats if p[0] == 0)
+        Y0 = min(p[4] for p in pats if p[0] == 0)
+        imgs = []
+        for m in range(lmax + 1):
+            ps = [p for p in pats if p[0] == m]
+            h = h0 / 2 ** m
+            gx0 = min(round((p[3] - X0) / h) for p in ps)
+            gy0 = min(round((p[4] - Y0) / h) for p in ps)
+            gx1 = max(round((p[3] - X0) / h) + p[1] for p in ps)
+            gy1 = max(round((p[4] - Y0) / h) + p[2] for p in ps)
+            imgs.append((gx1 - gx0, gy1 - gy0))
+        wx = max(round((p[3] - X0) / h0) + p[1] for p in pats if p[0] == 0) << lmax
+        wy = max(round((p[4] - Y0) / h0) + p[2] for p in pats if p[0] == 0) << lmax
+    return _pad(wx), _pad(wy), imgs
+
+
 def algorithmic_flops(wl, info, stage):
     """Conventional flop counts: 5 L log2 L per complex FFT of length L, plus
     the spectral multiply-adds (8 flops per field per bin; about 60 per bin for
-    the central-slope spectrum); the direct sum counts 28 FP32 operations per
-    target-corner pair (FMA = 2)."""
+    the central-slope spectrum; 10 per field and target for level convolutions);
+    the direct sum counts 28 FP32 operations per target-corner pair (FMA = 2)."""
     import math
     total = 0.0
+    if info.get("cross_mode") == 2:
+        px, py, imgs = lv_geometry(wl)
+        qx = px // 2 + 1
+        fx, fy = 5.0 * px * math.log2(px), 5.0 * py * math.log2(py)
+        L = len(imgs)
+        for nx, ny in imgs:
+            if stage == "row_fwd":
+                total += 3 * (ny / 2) * fx
+            elif stage == "col_conv":
+                total += qx * (3 * fy + 2 * fy + L * 3 * 10 * py)
+            elif stage == "row_inv":
+                total += 2 * (ny / 2) * fx
+        return total
     for p in wl["patches"]:
         nx, ny = p[1], p[2]
-        px = 64
-        while px < 2 * nx - 1:
-            px *= 2
-        py = 64
-        while py < 2 * ny - 1:
-            py *= 2
+        px, py = _pad(nx), _pad(ny)
         qx = px // 2 + 1
         fft_x = 5.0 * px * math.log2(px)
         fft_y = 5.0 * py * math.log2(py)
@@ -731,19 +777,32 @@ def algorithmic_flops(wl, info, stage):
 
 def algorithmic_bytes(wl, info, stage):
     """Bytes a stage must move per solve (see the design notes): FP32 complex
-    intermediates of (P/2+1) x ny bins per field, spectra planes, inputs, outputs."""
+    intermediates of (P/2+1) x ny bins per field, spectra planes, inputs, outputs.
+    Level convolutions: the forward column pass writes full source spectra, the
+    column kernel of every target level reads every source level's spectra and
+    its compressed kernel planes (6 real quarter planes per source level)."""
     es = 4
+    cs = 8
     total = 0
+    if info.get("cross_mode") == 2:
+        px, py, imgs = lv_geometry(wl)
+        qx, qy = px // 2 + 1, py // 2 + 1
+        L = len(imgs)
+        for nx, ny in imgs:
+            if stage == "row_fwd":
+                total += 3 * nx * ny * es + 3 * qx * ny * cs
+            elif stage == "col_conv":
+                total += 3 * qx * ny * cs + 3 * qx * py * cs          # column transforms of this level
+                total += L * (3 * qx * py * cs + 6 * qx * qy * es)    # read by every target level
+                total += 2 * qx * ny * cs                           # this level's inverse columns
+            elif stage == "row_inv":
+                total += 2 * qx * ny * cs + 2 * nx * ny * es
+        return total
     # central slopes are formed from sigma's transforms: one field is transformed
     nf = 3 if wl["slope_mode"] == 2 else 1
     for p in wl["patches"]:
         nx, ny = p[1], p[2]
-        px = 64
-        while px < 2 * nx - 1:
-            px *= 2
-        py = 64
-        while py < 2 * ny - 1:
-            py *= 2
+        px, py = _pad(nx), _pad(ny)
         qx, qy = px // 2 + 1, py // 2 + 1
         inputs = nx * ny * es * (1 if wl["slope_mode"] != 2 else 3)
         if stage == "row_fwd":

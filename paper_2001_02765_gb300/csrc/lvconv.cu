@@ -80,18 +80,22 @@ __device__ bool unit_x_family(double cx, double cy, double &x0, double &xx, doub
 
 // Packed wrapped tables of one kernel key: z0 = Kr^x0 + i Kr^y0, z1 = Kr^xx + i Kr^xy,
 // z2 = Kr^yy + i Kr^yx, each [py][px], for a source cell w = 2^s finest cells wide
-// and sample shift d = d2 / 2: Kr[e] = K(centre offset -e - d).
+// and sample shift d = d2 / 2: Kr[e] = K(centre offset -e - d). The stored period
+// is symmetric about e = -d, so that the compressed spectra below are exact.
 __global__ void k_lv_tables(double2 *z, int px, int py, int s, int d2)
 {
     const int64_t plane = (int64_t)px * py;
     const double w = (double)(1 << s), d = 0.5 * d2;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
         const int a = (int)(e % px), b = (int)(e / px);
-        const int ex = a < px / 2 ? a : a - px;
-        const int ey = b < py / 2 ? b : b - py;
+        // wrap representatives symmetric about -d (offsets |e| = P/2 are never used):
+        // [-P/2, P/2) for d >= 0, (-P/2, P/2] for d < 0, and zero at e = -P/2 for d = 0
+        const int ex = d2 < 0 ? (a <= px / 2 ? a : a - px) : (a < px / 2 ? a : a - px);
+        const int ey = d2 < 0 ? (b <= py / 2 ? b : b - py) : (b < py / 2 ? b : b - py);
         const double cx = (-ex - d) / w, cy = (-ey - d) / w;
         double x0 = 0, xx = 0, xy = 0, y0 = 0, yy = 0, yx = 0;
-        if (!unit_x_family(cx, cy, x0, xx, xy) || !unit_x_family(cy, cx, y0, yy, yx)) {
+        if ((d2 == 0 && (ex == -px / 2 || ey == -py / 2)) || !unit_x_family(cx, cy, x0, xx, xy) ||
+            !unit_x_family(cy, cx, y0, yy, yx)) {
             x0 = xx = xy = y0 = yy = yx = 0.0;
         }
         z[e] = make_double2(x0, y0);
@@ -100,29 +104,59 @@ __global__ void k_lv_tables(double2 *z, int px, int py, int s, int d2)
     }
 }
 
+// Kernel spectra are stored compressed. A table Kr(e) = K(-e - d) of parities
+// (sx, sy) (+1 even, -1 odd in that coordinate of the source offset) is
+// symmetric about e = -d along each axis, so its transform G satisfies
+//   H(k) = G(k) exp(-i pi d2 (kx/Px + ky/Py)),  d2 = 2d in {-1, 0, 1},
+//   H(kx, ky) = sx H(-kx, ky) = sy H(kx, -ky),  H real if sx sy = +1, imaginary if -1,
+// and H is determined by kx, ky in [0, P/2]: G(kx, ky) = ph_x(kx) ph_y(ky) H(kx, ky) for
+// ky <= Py/2 and sy ph_x(kx) ph_y(ky - Py) H(kx, Py - ky) above, ph(k) = exp(i pi d2 k / P).
+// Planes x0 xx xy y0 yx yy have (sx, sy) = (-,+) (+,+) (-,-) (+,-) (-,-) (+,+); the
+// imaginary ones (x0, y0) store Im H, the others Re H, [kx][ky] for kx in [0, px/2],
+// ky in [0, py/2], scaled by 1 / (px py).
+__host__ __device__ constexpr bool lv_plane_imag(int p) { return p == 0 || p == 3; }
+__host__ __device__ constexpr int lv_plane_sy(int p) { return (p == 2 || p == 3 || p == 4) ? -1 : 1; }
+
 // Unpack the transforms of the packed pairs (A + i B: A^(k) = (Z(k) + conj Z(-k)) / 2,
-// B^(k) = (Z(k) - conj Z(-k)) / 2i) into planes x0 xx xy y0 yx yy, [kx][ky] for
-// kx in [0, px/2], scaled by 1 / (px py).
+// B^(k) = (Z(k) - conj Z(-k)) / 2i), remove the half-cell phase and keep the real
+// or imaginary part of every plane.
 template <typename T>
-__global__ void k_lv_extract(const double2 *z, cplx_t<T> *out, int px, int py)
+__global__ void k_lv_extract(const double2 *z, T *out, int px, int py, int d2)
 {
-    using C = cplx_t<T>;
-    const int qx = px / 2 + 1;
-    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * py;
+    const int qx = px / 2 + 1, qy = py / 2 + 1;
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
     const double sc = 1.0 / ((double)px * (double)py);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(e / py), ky = (int)(e % py);
+        const int kx = (int)(e / qy), ky = (int)(e % qy);
         const int64_t ip = (int64_t)ky * px + kx;
         const int64_t im = (int64_t)((py - ky) % py) * px + (px - kx) % px;
+        double sn, cs;  // exp(-i pi d2 (kx/px + ky/py))
+        sincospi(-(double)d2 * ((double)kx / px + (double)ky / py), &sn, &cs);
         // destination planes of the A and B halves of each packed pair
         const int pa[3] = {0, 1, 5}, pb[3] = {3, 2, 4};
         for (int q = 0; q < 3; ++q) {
             const double2 zp = z[q * plane + ip], zm = z[q * plane + im];
             const double ar = 0.5 * (zp.x + zm.x), ai = 0.5 * (zp.y - zm.y);
             const double br = 0.5 * (zp.y + zm.y), bi = -0.5 * (zp.x - zm.x);
-            out[pa[q] * qplane + e] = cmake<C>((T)(sc * ar), (T)(sc * ai));
-            out[pb[q] * qplane + e] = cmake<C>((T)(sc * br), (T)(sc * bi));
+            // H = G (cs + i sn)
+            const double har = ar * cs - ai * sn, hai = ar * sn + ai * cs;
+            const double hbr = br * cs - bi * sn, hbi = br * sn + bi * cs;
+            out[pa[q] * qplane + e] = (T)(sc * (lv_plane_imag(pa[q]) ? hai : har));
+            out[pb[q] * qplane + e] = (T)(sc * (lv_plane_imag(pb[q]) ? hbi : hbr));
         }
+    }
+}
+
+// Phase factors exp(i pi k / P) for k in [-P/2, P/2] (index k + P/2), per axis.
+template <typename T>
+__global__ void k_lv_phase(cplx_t<T> *out, int px, int py)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < px + py + 2; e += gridDim.x * blockDim.x) {
+        const bool xa = e < px + 1;
+        const int P = xa ? px : py, k = (xa ? e : e - (px + 1)) - P / 2;
+        double sn, cs;
+        sincospi((double)k / P, &sn, &cs);
+        out[e] = cmake<cplx_t<T>>((T)cs, (T)sn);
     }
 }
 
@@ -207,17 +241,20 @@ struct lv_mac_args {
     int nsrc;
     int64_t spec_off[SG_MAX_LEVELS];    // complex-element offset of each source level's spectra
     int key[SG_MAX_LEVELS];             // kernel of each source level for this target level
+    int d2[SG_MAX_LEVELS];              // its 2 x sample shift
     int ny, j0, t;                      // target level: sampled rows j0 + j 2^t, j < ny
     int qx;
     double sc0, sc1;                    // G, and G h_f for the order-1 planes
 };
 
 // One column kx per CTA: Fx^, Fy^ = sum over source levels and fields of
-// source spectrum x kernel spectrum; inverse column transforms; the target
-// level's sampled rows to out[(o qx + kx) ny + j].
+// source spectrum x kernel spectrum (decompressed, see k_lv_extract); inverse
+// column transforms; the target level's sampled rows to out[(o qx + kx) ny + j].
 template <typename T, int PY, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
-                                                            const cplx_t<T> *__restrict__ kspec,
+                                                            const T *__restrict__ kspec,
+                                                            const cplx_t<T> *__restrict__ phx,
+                                                            const cplx_t<T> *__restrict__ phy,
                                                             cplx_t<T> *__restrict__ out,
                                                             const cplx_t<T> *__restrict__ tw)
 {
@@ -225,27 +262,51 @@ __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int EPT = PY / THREADS;
+    constexpr int QY = PY / 2 + 1;
     const int kx = blockIdx.x;
-    const int64_t qplane = (int64_t)a.qx * PY;
+    const int64_t sqplane = (int64_t)a.qx * PY, kqplane = (int64_t)a.qx * QY;
     C ax[EPT], ay[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) ax[q] = ay[q] = cmake<C>((T)0, (T)0);
     for (int m = 0; m < a.nsrc; ++m) {
         const C *sm = spec + a.spec_off[m] + (int64_t)kx * PY;
-        const C *km = kspec + (int64_t)a.key[m] * 6 * qplane + (int64_t)kx * PY;
-        for (int f = 0; f < 3; ++f) {
-            const T sc = (T)(f == 0 ? a.sc0 : a.sc1);
-            const C *sf = sm + f * qplane;
-            const C *kfx = km + f * qplane, *kfy = km + (3 + f) * qplane;
+        const T *km = kspec + (int64_t)a.key[m] * 6 * kqplane + (int64_t)kx * QY;
+        const int d2 = a.d2[m];
+        // x half of the phase: exp(i pi d2 kx / Px), from the table at index kx + Px/2
+        C pxk = cmake<C>((T)1, (T)0);
+        if (d2 != 0) {
+            pxk = phx[kx + (a.qx - 1)];
+            if (d2 < 0) pxk.y = -pxk.y;
+        }
 #pragma unroll
-            for (int q = 0; q < EPT; ++q) {
-                const int ky = threadIdx.x + q * THREADS;
-                const C X = sf[ky];
-                const C Kx = kfx[ky], Ky = kfy[ky];
-                const C Xs = cmake<C>(sc * X.x, sc * X.y);
-                ax[q] = cadd(ax[q], cmul(Xs, Kx));
-                ay[q] = cadd(ay[q], cmul(Xs, Ky));
+        for (int q = 0; q < EPT; ++q) {
+            const int ky = threadIdx.x + q * THREADS;
+            const bool lower = ky <= PY / 2;
+            const int kq = lower ? ky : PY - ky;
+            C ph = pxk;
+            if (d2 != 0) {
+                C py_ = phy[(lower ? ky : ky - PY) + PY / 2];
+                if (d2 < 0) py_.y = -py_.y;
+                ph = cmul(pxk, py_);
             }
+            C hx = cmake<C>((T)0, (T)0), hy = cmake<C>((T)0, (T)0);  // sum_f X_f H_f (real part, imaginary part)
+            for (int f = 0; f < 3; ++f) {
+                const T sc = (T)(f == 0 ? a.sc0 : a.sc1);
+                const C X = sm[f * sqplane + ky];
+                const int pxp = f, pyp = 3 + f;
+                T gx = sc * km[pxp * kqplane + kq], gy = sc * km[pyp * kqplane + kq];
+                if (!lower) {
+                    gx *= (T)lv_plane_sy(pxp);
+                    gy *= (T)lv_plane_sy(pyp);
+                }
+                // real planes multiply, imaginary planes multiply by i g
+                if (lv_plane_imag(pxp)) hx = cadd(hx, cmake<C>(-gx * X.y, gx * X.x));
+                else hx = cadd(hx, cmake<C>(gx * X.x, gx * X.y));
+                if (lv_plane_imag(pyp)) hy = cadd(hy, cmake<C>(-gy * X.y, gy * X.x));
+                else hy = cadd(hy, cmake<C>(gy * X.x, gy * X.y));
+            }
+            ax[q] = cadd(ax[q], cmul(hx, ph));
+            ay[q] = cadd(ay[q], cmul(hy, ph));
         }
     }
     for (int o = 0; o < 2; ++o) {
@@ -350,14 +411,14 @@ sg_status launch_col_fwd(const cplx_t<T> *in, cplx_t<T> *spec, int ny, int j0, i
 }
 
 template <typename T, int PY>
-sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const cplx_t<T> *kspec, cplx_t<T> *out,
-                             const cplx_t<T> *tw, cudaStream_t st)
+sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const T *kspec, const cplx_t<T> *phx,
+                             const cplx_t<T> *phy, cplx_t<T> *out, const cplx_t<T> *tw, cudaStream_t st)
 {
     constexpr int TH = lv_col_threads(PY);
     const size_t sm = spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
     auto kern = k_lv_col_mac_inv<T, PY, TH>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<a.qx, TH, sm, st>>>(a, spec, kspec, out, tw);
+    kern<<<a.qx, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -420,6 +481,7 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
         for (int m = 0; m < lv.nlev; ++m) {
             a.spec_off[m] = lv.lev[m].spec_off;
             a.key[m] = lv.key[m][l];
+            a.d2[m] = lv.key_d2[lv.key[m][l]];
         }
         a.ny = L.ny;
         a.j0 = L.j0;
@@ -427,7 +489,9 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
         a.qx = qx;
         a.sc0 = plan->geom.G;
         a.sc1 = plan->geom.G * lv.hf;
-        SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP>(a, spec, (const C *)lv.spectra, wi + L.inv_off, twy, st))));
+        const C *phx = (const C *)lv.phase, *phy = phx + lv.px + 1;
+        SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP>(a, spec, (const T *)lv.spectra, phx, phy, wi + L.inv_off,
+                                                               twy, st))));
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
@@ -447,6 +511,7 @@ void sg_lv_free(sg_plan *plan)
     if (!plan || !plan->lv) return;
     for (int m = 0; m < plan->lv->nlev; ++m) cudaFree(plan->lv->lev[m].map);
     cudaFree(plan->lv->spectra);
+    cudaFree(plan->lv->phase);
     delete plan->lv;
     plan->lv = nullptr;
 }
@@ -497,14 +562,18 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
             lv->key[m][l] = k;
         }
     }
-    const int64_t qplane = (int64_t)qx * a->py;
-    cudaError_t e = cudaMalloc(&lv->spectra, (size_t)lv->nkeys * 6 * qplane * cs);
+    const size_t rs = cs / 2;  // real element
+    const int64_t qplane = (int64_t)qx * (a->py / 2 + 1);
+    cudaError_t e = cudaMalloc(&lv->spectra, (size_t)lv->nkeys * 6 * qplane * rs);
+    if (e == cudaSuccess) e = cudaMalloc(&lv->phase, (size_t)(a->px + a->py + 2) * cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
         sg_set_last_cuda_error(e, "cudaMalloc");
         return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
     }
-    plan->device_bytes += (int64_t)lv->nkeys * 6 * qplane * (int64_t)cs;
+    plan->device_bytes += (int64_t)lv->nkeys * 6 * qplane * (int64_t)rs + (int64_t)(a->px + a->py + 2) * (int64_t)cs;
+    if (plan->prec == SG_FP64) k_lv_phase<double><<<16, 256>>>((double2 *)lv->phase, a->px, a->py);
+    else k_lv_phase<float><<<16, 256>>>((float2 *)lv->phase, a->px, a->py);
     // tables: FP64 wrapped, FP64 2-D transforms, unpacked and cast
     const int64_t plane = (int64_t)a->px * a->py;
     double2 *z = nullptr;
@@ -526,9 +595,9 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
             if (st == SG_OK) st = sg_fft_lines_fp64(zq, a->py, a->px, 1, a->px, twy);
         }
         if (st != SG_OK) break;
-        char *dst = (char *)lv->spectra + (size_t)k * 6 * qplane * cs;
-        if (plan->prec == SG_FP64) k_lv_extract<double><<<2048, 256>>>(z, (double2 *)dst, a->px, a->py);
-        else k_lv_extract<float><<<2048, 256>>>(z, (float2 *)dst, a->px, a->py);
+        char *dst = (char *)lv->spectra + (size_t)k * 6 * qplane * rs;
+        if (plan->prec == SG_FP64) k_lv_extract<double><<<2048, 256>>>(z, (double *)dst, a->px, a->py, lv->key_d2[k]);
+        else k_lv_extract<float><<<2048, 256>>>(z, (float *)dst, a->px, a->py, lv->key_d2[k]);
         if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
     }
     e = cudaDeviceSynchronize();
