@@ -313,7 +313,8 @@ bool lv_params(const sg_geom *g, const geom_info &gi, sg_precision prec, sg_lv_s
         return p;
     };
     const int64_t px = pad(wx), py = pad(wy);
-    if (px > SG_MAX_PAD || py > SG_MAX_PAD) return false;
+    const int64_t maxp = prec == SG_FP64 ? SG_MAX_PAD : SG_LV_MAX_PAD;
+    if (px > maxp || py > maxp) return false;
     memset(&a, 0, sizeof(a));
     a.nlev = gi.lmax + 1;
     a.px = (int)px;
@@ -485,7 +486,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         if (!use_lv) lv_bytes = -1;
         if (!use_lv && g->cross_mode == SG_CROSS_LEVELS)
             return fail("level convolutions need z == 0, no central slopes and a finest-lattice extent of at most "
-                        "2048 cells per axis");
+                        "4096 cells per axis (2048 for FP64 plans)");
     }
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tfirst, tcount;

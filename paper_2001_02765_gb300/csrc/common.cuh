@@ -61,6 +61,8 @@ struct __align__(32) sg_dvec4 {
 
 // Largest padded FFT length handled by the transform kernels.
 #define SG_MAX_PAD 4096
+// Largest padded length of the level convolutions (FP32; FP64 stops at SG_MAX_PAD).
+#define SG_LV_MAX_PAD 8192
 #define SG_MIN_PAD 64
 #define SG_MAX_PATCH_SIDE 2048
 #define SG_MAX_LEVELS 12

@@ -248,8 +248,9 @@ struct lv_mac_args {
 };
 
 // One column kx per CTA: Fx^, Fy^ = sum over source levels and fields of
-// source spectrum x kernel spectrum (decompressed, see k_lv_extract); inverse
-// column transforms; the target level's sampled rows to out[(o qx + kx) ny + j].
+// source spectrum x kernel spectrum (decompressed, see k_lv_extract), formed
+// element by element straight into two shared buffers; inverse column
+// transforms; the target level's sampled rows to out[(o qx + kx) ny + j].
 template <typename T, int PY, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
                                                             const T *__restrict__ kspec,
@@ -260,63 +261,55 @@ __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
-    constexpr int EPT = PY / THREADS;
+    C *bx = reinterpret_cast<C *>(smem_raw);
+    C *by = bx + spad_size<C>(PY);
     constexpr int QY = PY / 2 + 1;
     const int kx = blockIdx.x;
     const int64_t sqplane = (int64_t)a.qx * PY, kqplane = (int64_t)a.qx * QY;
-    C ax[EPT], ay[EPT];
+    for (int ky = threadIdx.x; ky < PY; ky += THREADS) {
+        const bool lower = ky <= PY / 2;
+        const int kq = lower ? ky : PY - ky;
+        const C pyk = phy[(lower ? ky : ky - PY) + PY / 2];
+        C ax = cmake<C>((T)0, (T)0), ay = cmake<C>((T)0, (T)0);
+        for (int m = 0; m < a.nsrc; ++m) {
+            const C *sm = spec + a.spec_off[m] + (int64_t)kx * PY + ky;
+            const T *km = kspec + (int64_t)a.key[m] * 6 * kqplane + (int64_t)kx * QY + kq;
+            C hx = cmake<C>((T)0, (T)0), hy = cmake<C>((T)0, (T)0);
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) ax[q] = ay[q] = cmake<C>((T)0, (T)0);
-    for (int m = 0; m < a.nsrc; ++m) {
-        const C *sm = spec + a.spec_off[m] + (int64_t)kx * PY;
-        const T *km = kspec + (int64_t)a.key[m] * 6 * kqplane + (int64_t)kx * QY;
-        const int d2 = a.d2[m];
-        // x half of the phase: exp(i pi d2 kx / Px), from the table at index kx + Px/2
-        C pxk = cmake<C>((T)1, (T)0);
-        if (d2 != 0) {
-            pxk = phx[kx + (a.qx - 1)];
-            if (d2 < 0) pxk.y = -pxk.y;
-        }
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int ky = threadIdx.x + q * THREADS;
-            const bool lower = ky <= PY / 2;
-            const int kq = lower ? ky : PY - ky;
-            C ph = pxk;
-            if (d2 != 0) {
-                C py_ = phy[(lower ? ky : ky - PY) + PY / 2];
-                if (d2 < 0) py_.y = -py_.y;
-                ph = cmul(pxk, py_);
-            }
-            C hx = cmake<C>((T)0, (T)0), hy = cmake<C>((T)0, (T)0);  // sum_f X_f H_f (real part, imaginary part)
             for (int f = 0; f < 3; ++f) {
                 const T sc = (T)(f == 0 ? a.sc0 : a.sc1);
-                const C X = sm[f * sqplane + ky];
-                const int pxp = f, pyp = 3 + f;
-                T gx = sc * km[pxp * kqplane + kq], gy = sc * km[pyp * kqplane + kq];
+                const C X = sm[f * sqplane];
+                T gx = sc * km[f * kqplane], gy = sc * km[(3 + f) * kqplane];
                 if (!lower) {
-                    gx *= (T)lv_plane_sy(pxp);
-                    gy *= (T)lv_plane_sy(pyp);
+                    gx *= (T)lv_plane_sy(f);
+                    gy *= (T)lv_plane_sy(3 + f);
                 }
-                // real planes multiply, imaginary planes multiply by i g
-                if (lv_plane_imag(pxp)) hx = cadd(hx, cmake<C>(-gx * X.y, gx * X.x));
+                // real planes multiply by g, imaginary planes by i g
+                if (lv_plane_imag(f)) hx = cadd(hx, cmake<C>(-gx * X.y, gx * X.x));
                 else hx = cadd(hx, cmake<C>(gx * X.x, gx * X.y));
-                if (lv_plane_imag(pyp)) hy = cadd(hy, cmake<C>(-gy * X.y, gy * X.x));
+                if (lv_plane_imag(3 + f)) hy = cadd(hy, cmake<C>(-gy * X.y, gy * X.x));
                 else hy = cadd(hy, cmake<C>(gy * X.x, gy * X.y));
             }
-            ax[q] = cadd(ax[q], cmul(hx, ph));
-            ay[q] = cadd(ay[q], cmul(hy, ph));
+            const int d2 = a.d2[m];
+            if (d2 != 0) {
+                // half-cell phase exp(i pi d2 (kx / Px + ky / Py))
+                C ph = cmul(phx[kx + (a.qx - 1)], pyk);
+                if (d2 < 0) ph.y = -ph.y;
+                hx = cmul(hx, ph);
+                hy = cmul(hy, ph);
+            }
+            ax = cadd(ax, hx);
+            ay = cadd(ay, hy);
         }
+        bx[spad<C>(ky)] = ax;
+        by[spad<C>(ky)] = ay;
     }
+    __syncthreads();
     for (int o = 0; o < 2; ++o) {
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? ax[q] : ay[q];
-        __syncthreads();
+        C *buf = o == 0 ? bx : by;
         fft_batch<C, PY, 1, THREADS, true, false, true>(buf, tw);
         C *dst = out + ((int64_t)o * a.qx + kx) * a.ny;
         for (int j = threadIdx.x; j < a.ny; j += THREADS) dst[j] = buf[spad<C>(a.j0 + (j << a.t))];
-        __syncthreads();
     }
 }
 
@@ -415,7 +408,7 @@ sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const 
                              const cplx_t<T> *phy, cplx_t<T> *out, const cplx_t<T> *tw, cudaStream_t st)
 {
     constexpr int TH = lv_col_threads(PY);
-    const size_t sm = spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
+    const size_t sm = 2 * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
     auto kern = k_lv_col_mac_inv<T, PY, TH>;
     SG_TRY(smem_attr(kern, sm));
     kern<<<a.qx, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
@@ -445,6 +438,7 @@ sg_status launch_row_inv(const cplx_t<T> *in, const lv_out_dst &a, T *fx, T *fy,
     case 1024: { constexpr int PP = 1024; CALL; break; } \
     case 2048: { constexpr int PP = 2048; CALL; break; } \
     case 4096: { constexpr int PP = 4096; CALL; break; } \
+    case 8192: { constexpr int PP = 8192; CALL; break; } \
     default: return SG_EINVAL;                 \
     }
 

@@ -253,7 +253,7 @@ sg_status sg_fft_lines_fp64(double2 *data, int L, int count, int64_t seq_stride,
         k_fft_lines<LL><<<count, (LL / 8 >= 64 ? LL / 8 : 64), spad_size<double2>(LL) * sizeof(double2)>>>(   \
             data, seq_stride, elem_stride, tw);                                                               \
         break;
-        SG_CASE(64) SG_CASE(128) SG_CASE(256) SG_CASE(512) SG_CASE(1024) SG_CASE(2048) SG_CASE(4096)
+        SG_CASE(64) SG_CASE(128) SG_CASE(256) SG_CASE(512) SG_CASE(1024) SG_CASE(2048) SG_CASE(4096) SG_CASE(8192)
 #undef SG_CASE
     default:
         return SG_EINVAL;

@@ -184,12 +184,37 @@ def test_levels_equal_direct(sg):
     p2.close()
 
 
-def test_levels_mode_rejects_too_large(sg):
-    """Level convolutions need a finest-lattice extent of at most 2048 cells."""
-    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(1536, 2))]  # 3072 finest cells
+def test_levels_mode_limits(sg):
+    """Level convolutions take finest-lattice extents up to 4096 cells (FP32) or
+    2048 (FP64); beyond, SG_CROSS_LEVELS is refused and SG_CROSS_AUTO falls back
+    to the direct sum."""
+    big = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(1536, 3))]  # 6144 finest cells
     with pytest.raises(sg.SgError) as e:
-        sg.Plan(patches, cross_mode=sg.SG_CROSS_LEVELS)
+        sg.Plan(big, cross_mode=sg.SG_CROSS_LEVELS)
     assert e.value.status == sg.SG_EINVAL and "level convolutions" in str(e.value)
-    plan = sg.Plan(patches, cross_mode=sg.SG_CROSS_AUTO)
+    plan = sg.Plan(big, cross_mode=sg.SG_CROSS_AUTO)
     assert plan.info["cross_mode"] == sg.SG_CROSS_DIRECT
     plan.close()
+    mid = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(768, 3))]  # 3072 finest cells
+    with pytest.raises(sg.SgError):
+        sg.Plan(mid, precision="fp64", cross_mode=sg.SG_CROSS_LEVELS)
+    plan = sg.Plan(mid, precision="fp32", cross_mode=sg.SG_CROSS_AUTO)
+    assert plan.info["cross_mode"] == sg.SG_CROSS_LEVELS and plan.info["max_pad"] == 8192
+    plan.close()
+
+
+def test_levels_8192_four_levels_sampled(sg):
+    """Four nested 512^2 levels (finest extent 4096, 8192-point transforms),
+    exponential disk, FP32: 96 sampled leaves against the plain leaf-pair sum."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(512, 4))]
+    sig, sx, sy = [], [], []
+    for p in patches:
+        X, Y = W.cell_centres(*p[1:])
+        a, b, c = W.exponential_sigma(X, Y, 0.1)
+        sig.append(a)
+        sx.append(b)
+        sy.append(c)
+    nleaf = 3 * (512 * 512 - 256 * 256) + 512 * 512
+    rng = np.random.Generator(np.random.PCG64(44))
+    idx = np.sort(rng.choice(nleaf, 96, replace=False))
+    _check(sg, patches, "fp32", 2, sig, sx, sy, 1e-5, target_index=idx, cross=2)

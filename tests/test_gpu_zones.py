@@ -139,6 +139,22 @@ def test_large_hierarchy_fp32_sampled(sg):
     assert rel_l2(fx[t], fy[t], rx, ry) < F32_TOL
 
 
+def test_ilr_1024_levels_fp32_sampled(sg):
+    """AMR(3, D_2) ILR at N = 1024 (1,419,424 leaves; finest extent 4096, 8192-point
+    level convolutions), FP32, 64 sampled leaves against the plain sum."""
+    hier = W.band_hierarchy(1024, 3, "ilr", "d2")
+    args = _hier_args(hier)
+    xc, yc, _ = W.zone_geometry(hier)
+    s, sx, sy = _d_sigma("d2", xc, yc)
+    (fx, fy), info = _solve(sg, args, "fp32", s, sx, sy)
+    assert info["cross_mode"] == sg.SG_CROSS_LEVELS and info["nleaves"] == 1419424
+    leaf = hier["leaf"]
+    rng = np.random.Generator(np.random.PCG64(17))
+    t = rng.choice(np.nonzero(leaf)[0], 64, replace=False)
+    rx, ry = _oracle(args, leaf, s, sx, sy, np.float32, targets=t)
+    assert rel_l2(fx[t], fy[t], rx, ry) < F32_TOL
+
+
 @pytest.mark.parametrize("n", [128, 256])
 @pytest.mark.parametrize("table, L", [(3, 2), (3, 3), (4, 2), (4, 3), (5, 2), (5, 3), (6, 2), (6, 3)])
 def test_tables3_6_from_cuda_path(sg, table, L, n):
