@@ -266,43 +266,71 @@ __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const
     constexpr int QY = PY / 2 + 1;
     const int kx = blockIdx.x;
     const int64_t sqplane = (int64_t)a.qx * PY, kqplane = (int64_t)a.qx * QY;
-    for (int ky = threadIdx.x; ky < PY; ky += THREADS) {
-        const bool lower = ky <= PY / 2;
-        const int kq = lower ? ky : PY - ky;
-        const C pyk = phy[(lower ? ky : ky - PY) + PY / 2];
-        C ax = cmake<C>((T)0, (T)0), ay = cmake<C>((T)0, (T)0);
+    // U bins per thread at a time, so that their loads are in flight together
+    constexpr int UMAX = sizeof(T) == 8 ? 2 : 4;
+    constexpr int U = PY / THREADS >= UMAX ? UMAX : PY / THREADS;
+    for (int k0 = threadIdx.x; k0 < PY; k0 += U * THREADS) {
+        int kq[U];
+        bool lower[U];
+        C pyk[U], ax[U], ay[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ky = k0 + u * THREADS;
+            lower[u] = ky <= PY / 2;
+            kq[u] = lower[u] ? ky : PY - ky;
+            pyk[u] = phy[(lower[u] ? ky : ky - PY) + PY / 2];
+            ax[u] = ay[u] = cmake<C>((T)0, (T)0);
+        }
         for (int m = 0; m < a.nsrc; ++m) {
-            const C *sm = spec + a.spec_off[m] + (int64_t)kx * PY + ky;
-            const T *km = kspec + (int64_t)a.key[m] * 6 * kqplane + (int64_t)kx * QY + kq;
-            C hx = cmake<C>((T)0, (T)0), hy = cmake<C>((T)0, (T)0);
+            const C *sm = spec + a.spec_off[m] + (int64_t)kx * PY + k0;
+            const T *km = kspec + (int64_t)a.key[m] * 6 * kqplane + (int64_t)kx * QY;
+            C X[3][U];
+            T gx[3][U], gy[3][U];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const T sc = (T)(f == 0 ? a.sc0 : a.sc1);
-                const C X = sm[f * sqplane];
-                T gx = sc * km[f * kqplane], gy = sc * km[(3 + f) * kqplane];
-                if (!lower) {
-                    gx *= (T)lv_plane_sy(f);
-                    gy *= (T)lv_plane_sy(3 + f);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    X[f][u] = sm[f * sqplane + u * THREADS];
+                    gx[f][u] = km[f * kqplane + kq[u]];
+                    gy[f][u] = km[(3 + f) * kqplane + kq[u]];
                 }
-                // real planes multiply by g, imaginary planes by i g
-                if (lv_plane_imag(f)) hx = cadd(hx, cmake<C>(-gx * X.y, gx * X.x));
-                else hx = cadd(hx, cmake<C>(gx * X.x, gx * X.y));
-                if (lv_plane_imag(3 + f)) hy = cadd(hy, cmake<C>(-gy * X.y, gy * X.x));
-                else hy = cadd(hy, cmake<C>(gy * X.x, gy * X.y));
             }
             const int d2 = a.d2[m];
-            if (d2 != 0) {
-                // half-cell phase exp(i pi d2 (kx / Px + ky / Py))
-                C ph = cmul(phx[kx + (a.qx - 1)], pyk);
-                if (d2 < 0) ph.y = -ph.y;
-                hx = cmul(hx, ph);
-                hy = cmul(hy, ph);
+            const C phk = phx[kx + (a.qx - 1)];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                C hx = cmake<C>((T)0, (T)0), hy = cmake<C>((T)0, (T)0);
+#pragma unroll
+                for (int f = 0; f < 3; ++f) {
+                    const T sc = (T)(f == 0 ? a.sc0 : a.sc1);
+                    T g1 = sc * gx[f][u], g2 = sc * gy[f][u];
+                    if (!lower[u]) {
+                        g1 *= (T)lv_plane_sy(f);
+                        g2 *= (T)lv_plane_sy(3 + f);
+                    }
+                    const C Xv = X[f][u];
+                    // real planes multiply by g, imaginary planes by i g
+                    if (lv_plane_imag(f)) hx = cadd(hx, cmake<C>(-g1 * Xv.y, g1 * Xv.x));
+                    else hx = cadd(hx, cmake<C>(g1 * Xv.x, g1 * Xv.y));
+                    if (lv_plane_imag(3 + f)) hy = cadd(hy, cmake<C>(-g2 * Xv.y, g2 * Xv.x));
+                    else hy = cadd(hy, cmake<C>(g2 * Xv.x, g2 * Xv.y));
+                }
+                if (d2 != 0) {
+                    // half-cell phase exp(i pi d2 (kx / Px + ky / Py))
+                    C ph = cmul(phk, pyk[u]);
+                    if (d2 < 0) ph.y = -ph.y;
+                    hx = cmul(hx, ph);
+                    hy = cmul(hy, ph);
+                }
+                ax[u] = cadd(ax[u], hx);
+                ay[u] = cadd(ay[u], hy);
             }
-            ax = cadd(ax, hx);
-            ay = cadd(ay, hy);
         }
-        bx[spad<C>(ky)] = ax;
-        by[spad<C>(ky)] = ay;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            bx[spad<C>(k0 + u * THREADS)] = ax[u];
+            by[spad<C>(k0 + u * THREADS)] = ay[u];
+        }
     }
     __syncthreads();
     for (int o = 0; o < 2; ++o) {
