@@ -184,3 +184,53 @@ int oracle_direct_force3(long ns, const double *xl, const double *xr, const doub
     }
     return 0;
 }
+
+/*
+ * Mid-plane potential (Section 2, the singular kernel integral with K = 1/r):
+ *   Phi(t) = -G sum_i [sigma0_i P0 + deltax_i Px + deltay_i Py],
+ *   P0 = dd[u ln(v + r) + v ln(u + r)],
+ *   Px = dd[(v r + u^2 ln(v + r)) / 2] + (x - xc) P0,   Py = dd[(u r + v^2 ln(u + r)) / 2] + (y - yc) P0,
+ * every logarithm multiplied by a factor that vanishes where it is singular (0 there).
+ */
+static double lvr(double u, double v)   /* ln(v + sqrt(u^2 + v^2)), u != 0 */
+{
+    double r = sqrt(u * u + v * v);
+    if (v >= 0.0) return log(v + r);
+    return 2.0 * log(fabs(u)) - log(r - v);
+}
+
+int oracle_direct_potential(long ns, const double *xl, const double *xr, const double *yd, const double *yu,
+                            const double *s0, const double *sx, const double *sy,
+                            long nt, const double *tx, const double *ty, double G, double *phi, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long t = 0; t < nt; ++t) {
+        double acc = 0.0;
+        for (long i = 0; i < ns; ++i) {
+            double us[2] = { xl[i] - tx[t], xr[i] - tx[t] };
+            double vs[2] = { yd[i] - ty[t], yu[i] - ty[t] };
+            double p0 = 0.0, pu = 0.0, pv = 0.0;
+            for (int a = 0; a < 2; ++a) {
+                for (int b = 0; b < 2; ++b) {
+                    double sgn = (a == b) ? 1.0 : -1.0;
+                    double u = us[a], v = vs[b], r = sqrt(u * u + v * v);
+                    double lv = u != 0.0 ? lvr(u, v) : 0.0;   /* ln(v + r), used with factor u */
+                    double lu = v != 0.0 ? lvr(v, u) : 0.0;   /* ln(u + r), used with factor v */
+                    p0 += sgn * (u * lv + v * lu);
+                    pu += sgn * 0.5 * (v * r + u * u * lv);
+                    pv += sgn * 0.5 * (u * r + v * v * lu);
+                }
+            }
+            double xc = 0.5 * (xl[i] + xr[i]), yc = 0.5 * (yd[i] + yu[i]);
+            double px = pu + (tx[t] - xc) * p0, py = pv + (ty[t] - yc) * p0;
+            acc += s0[i] * p0 + (sx ? sx[i] * px : 0.0) + (sy ? sy[i] * py : 0.0);
+        }
+        phi[t] = -G * acc;
+    }
+    return 0;
+}

@@ -61,3 +61,19 @@ def kuzmin_force_xyz(x, y, z, a, M=1.0, G=1.0):
     b = a + abs(z)
     s = -G * M / (x * x + y * y + b * b) ** 1.5
     return s * x, s * y, s * np.sign(z) * b
+
+
+def d2_potential(R, alpha, sigma0=1.0, G=1.0):
+    """Mid-plane potential of the D_2 disk (Section 3, after Schulz 2009, Eq. 29 there):
+        R <= alpha: -(3 pi^2 sigma0 G / (64 alpha^3)) (8 alpha^4 - 8 alpha^2 R^2 + 3 R^4)
+        R >  alpha: -(3 pi sigma0 G / (32 alpha^3)) [(8 alpha^4 - 8 alpha^2 R^2 + 3 R^4) asin(alpha/R)
+                                                      + 3 alpha (2 alpha^2 - R^2) sqrt(R^2 - alpha^2)]"""
+    R = np.asarray(R, dtype=np.float64)
+    q = 8.0 * alpha ** 4 - 8.0 * alpha ** 2 * R ** 2 + 3.0 * R ** 4
+    inside = R <= alpha
+    out = np.empty_like(R)
+    out[inside] = -(3.0 * np.pi ** 2 * sigma0 * G / (64.0 * alpha ** 3)) * q[inside]
+    Ro = R[~inside]
+    out[~inside] = -(3.0 * np.pi * sigma0 * G / (32.0 * alpha ** 3)) * (
+        q[~inside] * np.arcsin(alpha / Ro) + 3.0 * alpha * (2.0 * alpha ** 2 - Ro ** 2) * np.sqrt(Ro ** 2 - alpha ** 2))
+    return out
