@@ -210,6 +210,25 @@ sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const 
                     void *fz, void *stream);
 
 /*
+ * Mid-plane potential (Section 2: Phi(x, y, 0) = -G times the integral of
+ * K(xbar - x, ybar - y, 0) sigma with K = 1/r, the singular kernel integral
+ * whose gradient gives the force) at every cell centre of a plan of one
+ * unmasked patch in the plane (z == 0), with the plan's slope mode (central
+ * slopes are formed in the row transform here):
+ *   Phi(t) = -G sum_i [sigma0_i P^0_i(t) + deltax_i P^x_i(t) + deltay_i P^y_i(t)],
+ *   P^0, P^x, P^y = integrals over cell i of 1/r, (xbar - xc_i)/r, (ybar - yc_i)/r,
+ * from the antiderivatives u ln(v + r) + v ln(u + r) and (v r + u^2 ln(v + r))/2
+ * (finite everywhere, the own cell included). The first call on a plan builds
+ * its three FP64-built potential spectra synchronously (legacy default
+ * stream); later calls only enqueue on `stream`.
+ *   sigma, deltax, deltay  as for sg_force;  phi  device pointer, ncells elements
+ * Errors: SG_EINVAL (not a single unmasked in-plane patch, null or misaligned
+ * pointer, missing caller slopes), SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
+                       void *stream);
+
+/*
  * The same solve with HOST buffers: copies the inputs to the plan's device
  * staging buffers, runs sg_force on `stream`, copies Fx, Fy back and waits for
  * the stream. Host buffers may be pageable or pinned (pinned is faster).

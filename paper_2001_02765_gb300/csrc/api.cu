@@ -451,7 +451,9 @@ void plan_free(sg_plan *plan)
         for (int k = 0; k < plan->npatches; ++k) {
             cudaFree(plan->pp[k].spectra);
             cudaFree(plan->pp[k].phase);
+            cudaFree(plan->pp[k].pspectra);
         }
+        cudaFree(plan->pot_fwd);
     }
     sg_lv_free(plan);
     cudaFree(plan->twiddles);
@@ -788,6 +790,22 @@ __global__ void k_fz_plane(const T *__restrict__ sigma, T *__restrict__ fz, int6
         fz[i] = (T)(c * (double)sigma[i]);
 }
 
+// The plan's own workspace, allocated at its first solve.
+static sg_status ensure_ws(sg_plan *plan)
+{
+    if (plan->ws) return SG_OK;
+    sg_workspace *ws = new (std::nothrow) sg_workspace();
+    if (!ws) return SG_ENOMEM;
+    sg_status a = sg_workspace_alloc(plan, ws, 0, false);
+    if (a != SG_OK) {
+        delete ws;
+        return a;
+    }
+    plan->ws = ws;
+    plan->device_bytes += sg_workspace_bytes(plan);
+    return SG_OK;
+}
+
 // Validation, the plan's own workspace (allocated at the first call), timers, solve.
 static sg_status force_common(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
                               void *fy, void *fz, void *stream)
@@ -802,17 +820,7 @@ static sg_status force_common(sg_plan *plan, const void *sigma, const void *delt
     int dev = -1;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != plan->device) return fail("the plan's device is not current");
-    if (!plan->ws) {
-        sg_workspace *ws = new (std::nothrow) sg_workspace();
-        if (!ws) return SG_ENOMEM;
-        sg_status a = sg_workspace_alloc(plan, ws, 0, false);
-        if (a != SG_OK) {
-            delete ws;
-            return a;
-        }
-        plan->ws = ws;
-        plan->device_bytes += sg_workspace_bytes(plan);
-    }
+    SG_TRY(ensure_ws(plan));
     sg_timing_reset(plan->timing);
     plan->ws->timing = plan->timing;
     return sg_force_ws(plan, plan->ws, sigma, deltax, deltay, fx, fy, (cudaStream_t)stream, fz);
@@ -903,6 +911,38 @@ sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const 
         k_fz_plane<float><<<grid, 256, 0, (cudaStream_t)stream>>>((const float *)sigma, (float *)fz, n, c);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
+}
+
+sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
+                       void *stream)
+{
+    if (!plan || !sigma || !phi) return fail("null plan or field pointer");
+    if (plan->npatches != 1 || plan->composite || plan->geom.z != 0.0)
+        return fail("sg_potential takes plans of one unmasked patch in the plane");
+    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
+    const size_t es = elem_size(plan->prec);
+    if (!aligned(sigma, es) || !aligned(phi, es) || (caller && (!aligned(deltax, es) || !aligned(deltay, es))))
+        return fail("misaligned field pointer");
+    int dev = -1;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) return fail("the plan's device is not current");
+    SG_TRY(sg_potential_spectra_build(plan));
+    SG_TRY(ensure_ws(plan));
+    const sg_patch_dev &d = plan->pp[0].d;
+    const int64_t need = 3LL * (d.px / 2 + 1) * d.ny * (int64_t)(2 * es);
+    void *wf = plan->ws->work_fwd;
+    if (plan->ws_fwd_bytes < need) {
+        if (!plan->pot_fwd) {
+            SG_TRY(dev_alloc(plan, &plan->pot_fwd, (size_t)need));
+            plan->pot_fwd_bytes = need;
+        }
+        wf = plan->pot_fwd;
+    }
+    sg_timing_reset(plan->timing);
+    plan->ws->timing = plan->timing;
+    return sg_uniform_potential(plan, plan->ws, wf, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr, phi,
+                                (cudaStream_t)stream);
 }
 
 sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,

@@ -135,6 +135,7 @@ struct sg_patch_plan {
     // device buffers owned by the plan
     void *spectra;      // 6 planes [(px/2+1) x sg_spec_stride(py)] of T (quarter spectra, scaled)
     void *phase;        // central-slope spectral factors (see fftconv.cu), NULL unless SG_SLOPES_CENTRAL
+    void *pspectra;     // potential planes p, a, b [(px/2+1) x sg_spec_stride(py)] of T, built at the first sg_potential
     // tile range of this patch in the tile list
     int tile_first, tile_count;
 };
@@ -173,6 +174,8 @@ struct sg_plan {
     int64_t ws_zone_bytes;          // per-call zone-order staging, 5 x ncells of T
     int launches;                   // kernels one solve enqueues
     int cross_mode;                 // SG_CROSS_DIRECT, SG_CROSS_LEVELS, or 0 (single unmasked patch)
+    void *pot_fwd;                  // forward scratch of sg_potential (three fields), when work_fwd is smaller
+    int64_t pot_fwd_bytes;
     sg_lv *lv;                      // level-convolution plan (SG_CROSS_LEVELS), else NULL
 
     // per-call scratch sizes (bytes) and the plan's own workspace (used by sg_force)
@@ -255,6 +258,9 @@ sg_status sg_twiddles_build(sg_plan *plan);
 sg_status sg_phase_build(sg_plan *plan);     // central-slope factors of every patch
 sg_status sg_uniform_solve(sg_plan *plan, const struct sg_workspace *ws, int patch, const void *sigma, const void *dx,
                            const void *dy, void *fx, void *fy, void *fz, cudaStream_t st);
+sg_status sg_uniform_potential(sg_plan *plan, const struct sg_workspace *ws, void *wf, const void *sigma, const void *dx,
+                               const void *dy, void *phi, cudaStream_t st);
+sg_status sg_potential_spectra_build(sg_plan *plan);   // synchronous, patch 0
 sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          void *fx, void *fy, cudaStream_t st);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
     constexpr int EPT = CB * PY / THREADS;
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int kx0 = blockIdx.x * CB;
-    constexpr int NPL = NOUT == 3 ? 9 : 6;
+    constexpr int NPL = NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL>(ssp, spec, kx0, qx, &bar);
@@ -194,6 +194,17 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY>())) k_col_conv
             const T sg = lower ? (T)1 : (T)-1;
             const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
             const C X = buf[spad<C>(e)];
+            if constexpr (NOUT == 1) {
+                // potential planes: p (real, even-even), a (i a: odd in kx), b (i b: odd in ky)
+                if (f == 0) {
+                    const T pp = sp[0];
+                    accx[q] = cmake<C>(pp * X.x, pp * X.y);
+                } else {
+                    const T g = f == 1 ? sp[1 * CB * QS] : sg * sp[2 * CB * QS];
+                    accx[q] = cmake<C>(accx[q].x - g * X.y, accx[q].y + g * X.x);
+                }
+                continue;
+            }
             if (f == 0) {
                 const T a = sp[0 * CB * QS];
                 const T d = sg * sp[3 * CB * QS];
@@ -426,7 +437,7 @@ sg_status launch_rows_inv(const cplx_t<T> *work, T *fx, T *fy, T *fz, int nx, in
     const size_t smem = (size_t)spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
     auto kern = k_row_inv<T, PX, NB, ROW_THREADS>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((ny + 2 * NB - 1) / (2 * NB), fz ? 3 : 2);
+    dim3 grid((ny + 2 * NB - 1) / (2 * NB), fz ? 3 : (fy ? 2 : 1));
     kern<<<grid, ROW_THREADS, smem, st>>>(work, fx, fy, fz, nx, ny, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
@@ -438,7 +449,7 @@ sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny,
 {
     constexpr int CB = col_cb(PY);
     constexpr int THREADS = col_threads(PY);
-    const size_t smem = (size_t)col_smem_bytes<T, PY, CB, NOUT == 3 ? 9 : 6>();
+    const size_t smem = (size_t)col_smem_bytes<T, PY, CB, NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6)>();
     auto kern = k_col_conv<T, PY, CB, THREADS, NOUT>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((qx + CB - 1) / CB);
@@ -486,9 +497,12 @@ sg_status launch_edge_cols(const T *sigma, int nx, int ny, cplx_t<T> *edge, cons
     default: return SG_EINVAL;                 \
     }
 
+// pot_spec != NULL: the potential (one output, three spectrum planes) with the
+// forward scratch wf_pot, slopes formed in the row pass.
 template <typename T>
 sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const void *sigma, const void *dx,
-                          const void *dy, void *fx, void *fy, void *fz, cudaStream_t st)
+                          const void *dy, void *fx, void *fy, void *fz, cudaStream_t st, const T *pot_spec = nullptr,
+                          void *wf_pot = nullptr)
 {
     using C = cplx_t<T>;
     const sg_patch_plan &pp = plan->pp[p];
@@ -512,14 +526,14 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     }
     const int nf = src.mode == SG_SLOPES_NONE ? 1 : 3;
     const int qx = d.px / 2 + 1;
-    C *wf = (C *)ws->work_fwd;
+    C *wf = pot_spec ? (C *)wf_pot : (C *)ws->work_fwd;
     C *wi = (C *)ws->work_inv;
     const int64_t *twoff = sizeof(T) == 8 ? plan->tw64_off : plan->tw32_off;
     const C *twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.px)]);
     const C *twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.py)]);
     T *ox = (T *)fx + off, *oy = (T *)fy + off;
     T *oz = fz ? (T *)fz + off : nullptr;  // off-plane plans only
-    const bool central = src.mode == SG_SLOPES_CENTRAL && pp.phase;
+    const bool central = src.mode == SG_SLOPES_CENTRAL && pp.phase && !pot_spec;
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
     if (central) {
         // the edge-column transform is independent of the row pass: run it beside it
@@ -541,6 +555,8 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
         const C *edge = wf + (int64_t)qx * d.ny;
         SG_PAD_SWITCH(d.py, SG_TRY((launch_cols_central<T, PP>(wf, wi, (const T *)pp.spectra, edge,
                                                                 (const T *)pp.phase, d.ny, qx, twy, ws->err, st))));
+    } else if (pot_spec) {
+        SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP, 1>(wf, wi, pot_spec, d.ny, qx, nf, twy, ws->err, st))));
     } else {
         if (oz) {
             SG_PAD_SWITCH(d.py, SG_TRY((launch_cols<T, PP, 3>(wf, wi, (const T *)pp.spectra, d.ny, qx, nf, twy, ws->err, st))));
@@ -550,7 +566,7 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
-    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, oy, oz, d.nx, d.ny, twx, st))));
+    SG_PAD_SWITCH(d.px, SG_TRY((launch_rows_inv<T, PP>(wi, ox, pot_spec ? nullptr : oy, oz, d.nx, d.ny, twx, st))));
     sg_timing_end(ws, SG_STAGE_ROW_INV, st);
     return SG_OK;
 }
@@ -562,4 +578,15 @@ sg_status sg_uniform_solve(sg_plan *plan, const sg_workspace *ws, int patch, con
 {
     if (plan->prec == SG_FP64) return uniform_solve_t<double>(plan, ws, patch, sigma, dx, dy, fx, fy, fz, st);
     return uniform_solve_t<float>(plan, ws, patch, sigma, dx, dy, fx, fy, fz, st);
+}
+
+sg_status sg_uniform_potential(sg_plan *plan, const sg_workspace *ws, void *wf, const void *sigma, const void *dx,
+                               const void *dy, void *phi, cudaStream_t st)
+{
+    const sg_patch_plan &pp = plan->pp[0];
+    if (plan->prec == SG_FP64)
+        return uniform_solve_t<double>(plan, ws, 0, sigma, dx, dy, phi, nullptr, nullptr, st,
+                                       (const double *)pp.pspectra, wf);
+    return uniform_solve_t<float>(plan, ws, 0, sigma, dx, dy, phi, nullptr, nullptr, st, (const float *)pp.pspectra,
+                                  wf);
 }

@@ -128,6 +128,73 @@ __device__ void unit_kernels_z(int m, int n, double zeta, double *out9)
     out9[8] = sn * b.zx;     // even in m, odd in n
 }
 
+// ---- the mid-plane potential (Section 2, K = 1/r): integrals over the unit cell
+// [m-1/2, m+1/2] x [n-1/2, n+1/2] (target at the origin) of 1/r, (xbar - xc)/r and
+// (ybar - yc)/r. From the antiderivatives u ln(v + r) + v ln(u + r), (v r + u^2 ln(v + r))/2
+// and (u r + v^2 ln(u + r))/2, with the u-only (v-only) logarithm cancelled inside each
+// difference as for the force:
+//   P0 = u2 Dv(u2) - u1 Dv(u1) + v2 Du(v2) - v1 Du(v1)
+//   Px = [v2 Ru(v2) - v1 Ru(v1) + u2^2 Dv(u2) - u1^2 Dv(u1)] / 2 - m P0
+//   Py = [u2 Rv(u2) - u1 Rv(u1) + v2^2 Du(v2) - v1^2 Du(v1)] / 2 - n P0
+// Dv(u) = asinh(v2/|u|) - asinh(v1/|u|), Du(v) likewise, Ru(v) = r(u2, v) - r(u1, v),
+// Rv(u) = r(u, v2) - r(u, v1); terms whose prefactor is 0 are 0 (their limits), so every
+// offset, the own cell included, is finite. P0 scales with h, Px and Py with h^2.
+__device__ void unit_potentials(int m, int n, double *out3)
+{
+    const double u1 = m - 0.5, u2 = m + 0.5, v1 = n - 0.5, v2 = n + 0.5;
+    const double dv1 = u1 != 0.0 ? asinh_span(v1, v2, fabs(u1)) : 0.0;
+    const double dv2 = u2 != 0.0 ? asinh_span(v1, v2, fabs(u2)) : 0.0;
+    const double du1 = v1 != 0.0 ? asinh_span(u1, u2, fabs(v1)) : 0.0;
+    const double du2 = v2 != 0.0 ? asinh_span(u1, u2, fabs(v2)) : 0.0;
+    const double p0 = u2 * dv2 - u1 * dv1 + v2 * du2 - v1 * du1;
+    const double r22 = sqrt(u2 * u2 + v2 * v2), r12 = sqrt(u1 * u1 + v2 * v2);
+    const double r21 = sqrt(u2 * u2 + v1 * v1), r11 = sqrt(u1 * u1 + v1 * v1);
+    const double ru2 = (u2 + u1) / (r22 + r12), ru1 = (u2 + u1) / (r21 + r11);  // r(u2,v) - r(u1,v)
+    const double rv2 = (v2 + v1) / (r22 + r21), rv1 = (v2 + v1) / (r12 + r11);  // r(u,v2) - r(u,v1)
+    out3[0] = p0;
+    out3[1] = 0.5 * (v2 * ru2 - v1 * ru1 + u2 * u2 * dv2 - u1 * u1 * dv1) - (double)m * p0;
+    out3[2] = 0.5 * (u2 * rv2 - u1 * rv1 + v2 * v2 * du2 - v1 * v1 * du1) - (double)n * p0;
+}
+
+// Wrapped correlation tables of the potential packed as z0 = Pr^x + i Pr^y (both
+// transforms imaginary by parity), z1 = Pr^0 (transform real), each [py][px].
+__global__ void k_tables_wrapped_pot(double2 *z, int nx, int ny, int px, int py)
+{
+    const int64_t plane = (int64_t)px * py;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % px), b = (int)(e / px);
+        const int ex = a < px / 2 ? a : a - px;
+        const int ey = b < py / 2 ? b : b - py;
+        const int m = -ex, n = -ey;  // Pr[e] = P[-e]
+        double p3[3] = {0, 0, 0};
+        if (m <= nx - 1 && m >= -(nx - 1) && n <= ny - 1 && n >= -(ny - 1)) unit_potentials(m, n, p3);
+        z[e] = make_double2(p3[1], p3[2]);
+        z[plane + e] = make_double2(p3[0], 0.0);
+    }
+}
+
+// Quarter planes p = Re P^0, a = Im P^x, b = Im P^y (the potential's spectra),
+// [kx][ky] with row stride sg_spec_stride(py), scaled by -G/(px py) times h (p) or h^2.
+template <typename T>
+__global__ void k_extract_pot(const double2 *z, T *planes, int px, int py, double scale0, double scale1)
+{
+    const int qx = px / 2 + 1, qy = py / 2 + 1, qs = sg_spec_stride(py);
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qs;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(e / qs), ky = (int)(e % qs);
+        if (ky >= qy) {
+            for (int c = 0; c < 3; ++c) planes[c * qplane + e] = (T)0;
+            continue;
+        }
+        const int64_t src = (int64_t)ky * px + kx;
+        const double2 z0 = z[src], z1 = z[plane + src];
+        // z0 = i a + i (i b) = -b + i a
+        planes[0 * qplane + e] = (T)(scale0 * z1.x);
+        planes[1 * qplane + e] = (T)(scale1 * z0.y);
+        planes[2 * qplane + e] = (T)(-scale1 * z0.x);
+    }
+}
+
 // Unwrapped table of one kernel, physical units, [(2ny-1)][(2nx-1)].
 __global__ void k_table_unwrapped(double *out, int nx, int ny, double h, double zeta, int which)
 {
@@ -399,5 +466,54 @@ sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host
         sg_set_last_cuda_error(e, "sg_kernel_tables");
         return SG_ECUDA;
     }
+    return SG_OK;
+}
+
+// Potential spectra of patch 0, built once (synchronous).
+sg_status sg_potential_spectra_build(sg_plan *plan)
+{
+    sg_patch_plan &pp = plan->pp[0];
+    if (pp.pspectra) return SG_OK;
+    const int px = pp.d.px, py = pp.d.py;
+    const size_t es = plan->prec == SG_FP64 ? 8 : 4;
+    const size_t bytes = 3 * (size_t)(px / 2 + 1) * sg_spec_stride(py) * es;
+    const int64_t plane = (int64_t)px * py;
+    double2 *z = nullptr;
+    SG_CUDA_TRY(cudaMalloc(&z, (size_t)(2 * plane * sizeof(double2))));
+    void *spec = nullptr;
+    cudaError_t e = cudaMalloc(&spec, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(z);
+        cudaGetLastError();
+        sg_set_last_cuda_error(e, "cudaMalloc");
+        return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
+    }
+    k_tables_wrapped_pot<<<1024, 256>>>(z, pp.d.nx, pp.d.ny, px, py);
+    sg_status st = cudaGetLastError() == cudaSuccess ? SG_OK : SG_ECUDA;
+    const double2 *twx = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(px)]);
+    const double2 *twy = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(py)]);
+    for (int q = 0; q < 2 && st == SG_OK; ++q) {
+        st = sg_fft_lines_fp64(z + q * plane, px, py, px, 1, twx);
+        if (st == SG_OK) st = sg_fft_lines_fp64(z + q * plane, py, px, 1, px, twy);
+    }
+    const double scale0 = -plan->geom.G / ((double)px * (double)py) * pp.d.h;
+    const double scale1 = scale0 * pp.d.h;
+    if (st == SG_OK) {
+        if (plan->prec == SG_FP64) k_extract_pot<double><<<1024, 256>>>(z, (double *)spec, px, py, scale0, scale1);
+        else k_extract_pot<float><<<1024, 256>>>(z, (float *)spec, px, py, scale0, scale1);
+        if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
+    }
+    e = cudaDeviceSynchronize();
+    cudaFree(z);
+    if (st == SG_OK && e != cudaSuccess) {
+        sg_set_last_cuda_error(e, "sg_potential");
+        st = SG_ECUDA;
+    }
+    if (st != SG_OK) {
+        cudaFree(spec);
+        return st;
+    }
+    pp.pspectra = spec;
+    plan->device_bytes += (int64_t)bytes;
     return SG_OK;
 }

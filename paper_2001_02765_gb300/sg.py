@@ -84,6 +84,7 @@ _SIGNATURES = {
     "sg_force": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_force_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_force3": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_potential": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "sg_direct_force_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -228,6 +229,12 @@ def sg_force3(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, fz_ptr, stream_
     """Raw device pointers (ints); enqueues a solve with Fz."""
     _check(load().sg_force3(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr, fz_ptr,
                             stream_ptr or None), "sg_force3")
+
+
+def sg_potential(handle, sigma_ptr, dx_ptr, dy_ptr, phi_ptr, stream_ptr=0):
+    """Raw device pointers (ints); enqueues the potential (builds its spectra at the first call)."""
+    _check(load().sg_potential(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, phi_ptr, stream_ptr or None),
+           "sg_potential")
 
 
 def sg_force_host(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
@@ -459,6 +466,20 @@ class Plan:
         sg_force3(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
                   dy.data_ptr() if dy is not None else 0, fx.data_ptr(), fy.data_ptr(), fz.data_ptr(), st)
         return fx, fy, fz
+
+    def potential(self, sigma, dx=None, dy=None, phi=None, stream=None):
+        """Enqueue the mid-plane potential (see sg_potential); returns phi."""
+        import torch
+        dt = self._torch_dtype()
+        for t in (sigma, dx, dy, phi):
+            if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() != self.ncells):
+                raise ValueError("fields must be contiguous %s CUDA tensors of %d elements" % (dt, self.ncells))
+        if phi is None:
+            phi = torch.empty_like(sigma)
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        sg_potential(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
+                     dy.data_ptr() if dy is not None else 0, phi.data_ptr(), st)
+        return phi
 
     def force_host(self, sigma, dx=None, dy=None, fx=None, fy=None, stream=None):
         """Solve from host arrays (numpy, or pinned torch CPU tensors); returns host (fx, fy)."""
