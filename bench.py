@@ -217,6 +217,13 @@ WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3, "offplane": w
 
 # -------------------------------------------------------------- batch run --
 
+def sg_pad(n):
+    p = 64
+    while p < 2 * n - 1:
+        p *= 2
+    return p
+
+
 def run_batch(args):
     """64 independent spiral disks (N log-uniform 64..512, seed 4), one CUDA
     graph launch per step, versus the same solves launched one by one."""
@@ -226,6 +233,14 @@ def run_batch(args):
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
     ns, a, amp = W.batch_sizes(count=args.batch_size, lo=64, hi=512, seed=4 + rank)
+    # launch shapes picked by the library's autotuner for the padded lengths of the batch
+    pads = sorted({sg_pad(int(n)) for n in ns})
+    tuned, tune_s = None, 0.0
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=5)
+        tune_s = time.perf_counter() - t0
+        tuned = {str(p): res[p][0] for p in pads}
 
     def build(precision):
         dt = torch.float32 if precision == "fp32" else torch.float64
@@ -292,7 +307,9 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch64_graph", "members": len(ns), "sizes": "N = round(exp U(ln 64, ln 512)), seed 4",
                    "disk": "Kuzmin a~U[.05,.3] x (1 + A cos(2 theta - ln R / tan 15deg)), A~U[0,.2]",
-                   "slopes": "central", "precision": "fp32", "l2": "flushed before every batch (512 MB write)"},
+                   "slopes": "central", "precision": "fp32", "l2": "flushed before every batch (512 MB write)",
+                   "launch_shapes": "autotuned" if tuned else "defaults"},
+        "autotune": {"seconds": tune_s, "shapes": tuned} if tuned else None,
         "target_cells_per_s": value / len(ns) * targets,
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
         "one_by_one": {"solves_per_s": len(ns) * args.steps / (sum(per_seq) / 1e3)},
@@ -900,6 +917,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="run the request-server workload instead")
     ap.add_argument("--batch", action="store_true", help="run the graph-captured batch workload instead")
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default launch shapes")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-sweep", action="store_true", help="also run loads 0.3, 0.5, 1.0 on a tenth of the stream")
     ap.add_argument("--serve-inflight", type=int, default=8)

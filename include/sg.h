@@ -362,6 +362,36 @@ sg_status sg_zones_from_records(int64_t n, int ncols, const double *records, int
 sg_status sg_zones_links(const sg_zones *zones, int64_t *parent, uint8_t *leaf, int64_t *neighbours);
 
 /* ------------------------------------------------------------------------
+ * Launch-shape tuning (not in the paper). The uniform-patch passes come in
+ * three compiled launch shapes per padded length: half, the measured default
+ * and twice the default number of row sequences (forward and inverse row
+ * passes) or columns (column passes) per CTA, where shared memory and CTA size
+ * allow. A process-wide table, initially the defaults, selects one per
+ * (precision, padded length); results are bit-identical under every shape
+ * (only the grouping of sequences into CTAs changes). Solves read the table
+ * when they enqueue (a graph captures the shapes in force at capture).
+ *   shape[4]: 0 forward row pass, 1 inverse row pass, 2 column pass,
+ *             3 central-slope column pass; 0 in sg_tune_set = the default.
+ * ------------------------------------------------------------------------ */
+
+/* Shapes in force for `precision` (SG_FP64 / SG_FP32) and padded length `pad`
+ * (64 ... 4096, a power of two). Host only. Errors: SG_EINVAL. */
+sg_status sg_tune_get(int precision, int pad, int *shape);
+
+/* Select shapes (each 0 or one of the compiled candidates; SG_EINVAL names the
+ * first other value). Host only. */
+sg_status sg_tune_set(int precision, int pad, const int *shape);
+
+/* Time every candidate of every pass on a square patch of each padded length
+ * min_pad ... max_pad (powers of two; caller slopes for the row and column
+ * passes, central slopes for the central column pass), median of `reps`
+ * solves after one warm-up, one pass at a time in order, and keep the fastest.
+ * best_ms (NULL or one entry per length) receives the median solve time with
+ * the chosen shapes. Synchronous on the current device; allocates temporary
+ * plans and buffers. Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+sg_status sg_autotune(int precision, int min_pad, int max_pad, int reps, double *best_ms);
+
+/* ------------------------------------------------------------------------
  * Batches (not in the paper): n independent solves bound to their plans and
  * caller-owned device buffers at creation and captured once into a CUDA graph
  * with one branch per member (each with its own workspace), so uneven solves

@@ -43,7 +43,7 @@ def _stale(obj, deps):
 
 def build(verbose=False, extra=()):
     os.makedirs(OBJ, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h", ".inl"))]
     headers.append(os.path.join(INCLUDE, "sg.h"))
     nvcc = _nvcc()
     jobs = []

@@ -52,6 +52,20 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
 
+// Explicitly rounded product and sum: the optimiser may fuse a plain multiply
+// and add into an FMA, and may decide differently in different instantiations
+// of one kernel; these pin the rounding of expressions whose results must not
+// depend on the launch shape.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+// p q with one FMA per component: (fma(p.x, q.x, -(p.y q.y)), fma(p.x, q.y, p.y q.x))
+template <typename C> __device__ __forceinline__ C cmul_rn(C a, C b)
+{
+    return cmake<C>(fma(a.x, b.x, -mul_rn(a.y, b.y)), fma(a.x, b.y, mul_rn(a.y, b.x)));
+}
+
 // 32-byte aligned FP64 4-vector (corner weights of FP64 plans)
 struct __align__(32) sg_dvec4 {
     double x, y, z, w;
@@ -261,6 +275,11 @@ sg_status sg_uniform_solve(sg_plan *plan, const struct sg_workspace *ws, int pat
 sg_status sg_uniform_potential(sg_plan *plan, const struct sg_workspace *ws, void *wf, const void *sigma, const void *dx,
                                const void *dy, void *phi, cudaStream_t st);
 sg_status sg_potential_spectra_build(sg_plan *plan);   // synchronous, patch 0
+// Launch shapes of the uniform-patch passes for a padded length (tune.cu):
+// shape[0] row sequences per CTA (forward), [1] (inverse), [2] columns per CTA
+// of the column pass, [3] of the central-slope column pass.
+#define SG_TUNE_KNOBS 4
+void sg_tune_shape(sg_precision prec, int pad, int *shape);
 sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          void *fx, void *fy, cudaStream_t st);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,

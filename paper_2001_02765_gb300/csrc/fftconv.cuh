@@ -1,0 +1,482 @@
+// Kernels of the uniform-patch force as a zero-padded 2-D FFT convolution (introduction and
+// conclusion of Tseng, Shang & Yen; the uniform-grid route of Yen et al. 2012).
+//
+// For a patch of nx x ny cells padded to Px x Py (powers of two, P >= 2n - 1):
+//   1. k_row_fwd : per row j < ny, the three input fields (sigma0, deltax,
+//                  deltay; the slopes either read or formed by central
+//                  differences on the fly, covered cells masked to zero) are
+//                  real-to-complex transformed along x, two rows per complex
+//                  FFT, and the Px/2+1 bins are written transposed:
+//                  work_fwd[f][kx][j].
+//   2. k_col_conv: per bin column kx, each field's column (ny values, zero
+//                  padded to Py) is transformed along y, multiplied with the
+//                  kernel spectra and accumulated into Fx^, Fy^ in registers:
+//                    Fx^ = sigma^ (i a) + deltax^ b + deltay^ (s c)
+//                    Fy^ = sigma^ (i s d) + deltay^ e + deltax^ (s f)
+//                  (s = -1 for ky > Py/2: those planes are odd in ky); both are
+//                  transformed back along y and the first ny rows written:
+//                  work_inv[o][kx][j].
+//   3. k_row_inv : per row j < ny, the two half spectra are inverse transformed
+//                  along x (two rows per complex FFT) and the first nx values
+//                  written to Fx, Fy. The spectra already carry G / (Px Py).
+// Every transform is the shared-memory Stockham FFT of fft.cuh.
+//
+// Central slopes. When deltax, deltay are central differences of sigma with
+// zero outside the patch, their transforms follow from sigma's exactly: along
+// x the stencil (s[i+1] - s[i-1]) / 2h applied to the zero-padded row has the
+// transform i sin(2 pi k / P) / h times sigma's, except that it also puts
+// s[0] / 2h at i = -1 and -s[nx-1] / 2h at i = nx, outside the patch, whose
+// transforms are removed again:
+//   deltax^(kx, ky) = i csin(kx) S - e^{+2 pi i kx/Px}/2h C0(ky) + e^{-2 pi i nx kx/Px}/2h C1(ky)
+//   deltay^(kx, ky) = i rsin(ky) S - e^{+2 pi i ky/Py}/2h R0(kx) + e^{-2 pi i ny ky/Py}/2h R1(kx)
+// with S = sigma^(kx, ky), C0 / C1 the y-transforms of sigma's first / last
+// column (k_edge_cols), R0 / R1 the x-transforms of its first / last row (the
+// column pass reads them from its own input). So only sigma is transformed:
+// one row field and one forward column transform instead of three.
+#include "common.cuh"
+//
+// The kernels and their launch-shape variants are split over translation
+// units by stage (fftconv_rows.cu, fftconv_cols.cu, fftconv_central.cu); the
+// solve (fftconv.cu) calls them through the dispatchers declared below with
+// the launch shapes of the tuning table (tune.cu).
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "tma.cuh"
+
+namespace sgk {
+
+template <typename T>
+struct field_src {
+    const T *sigma, *dx, *dy;
+    int nx, ny;
+    T inv2h;
+    int mode;          // sg_slope_mode
+};
+
+template <typename T>
+__device__ __forceinline__ T sigma_at(const field_src<T> &s, int j, int i)
+{
+    if (i < 0 || i >= s.nx || j < 0 || j >= s.ny) return (T)0;
+    return s.sigma[(int64_t)j * s.nx + i];
+}
+
+template <typename T>
+__device__ __forceinline__ T field_value(const field_src<T> &s, int f, int j, int i)
+{
+    if (j >= s.ny || i >= s.nx) return (T)0;
+    const int64_t o = (int64_t)j * s.nx + i;
+    if (f == 0) return s.sigma[o];
+    if (s.mode == SG_SLOPES_CALLER) return f == 1 ? s.dx[o] : s.dy[o];
+    // central differences, zero beyond the patch edge
+    if (f == 1) return (sigma_at(s, j, i + 1) - sigma_at(s, j, i - 1)) * s.inv2h;
+    return (sigma_at(s, j + 1, i) - sigma_at(s, j - 1, i)) * s.inv2h;
+}
+
+// ---------------------------------------------------------------- kernels --
+
+template <typename T, int PX, int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T> *__restrict__ work,
+                                                     const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int RB = 2 * NB;
+    constexpr int QX = PX / 2 + 1;
+    const int f = blockIdx.y;
+    const int j0 = blockIdx.x * RB;
+    const int ny = src.ny;
+
+    // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
+    for (int e = threadIdx.x; e < NB * (PX / 2); e += THREADS) {
+        const int s = e / (PX / 2), i = e % (PX / 2);
+        const int ja = j0 + 2 * s;
+        const T a = field_value(src, f, ja, i);
+        const T b = field_value(src, f, ja + 1, i);
+        buf[spad<C>(s * PX + i)] = cmake<C>(a, b);
+    }
+    __syncthreads();
+    fft_batch<C, PX, NB, THREADS, false, true>(buf, tw);
+
+    // unpack: A[k] = (Z[k] + conj Z[-k]) / 2, B[k] = (Z[k] - conj Z[-k]) / 2i
+    const T half = (T)0.5;
+    for (int e = threadIdx.x; e < QX * RB; e += THREADS) {
+        const int kx = e / RB, r = e % RB;
+        const int j = j0 + r;
+        if (j >= ny) continue;
+        const int s = r >> 1;
+        const C z = buf[spad<C>(s * PX + kx)];
+        const C w = buf[spad<C>(s * PX + ((PX - kx) & (PX - 1)))];
+        C out;
+        if ((r & 1) == 0) out = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
+        else out = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
+        work[((int64_t)f * QX + kx) * ny + j] = out;
+    }
+}
+
+// Shared-memory layout of the column kernels: the padded FFT buffer, then the
+// kernel spectra of the CTA's columns, [planes][CB][sg_spec_stride(PY)] of T,
+// which one thread fetches with one 1-D bulk copy (TMA) per plane at kernel
+// start so that they arrive while the forward transform runs.
+template <typename T, int PY, int CB>
+__host__ __device__ constexpr int col_buf_bytes() { return (spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15; }
+template <typename T, int PY, int CB, int NPL = 6>
+__host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * NPL * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
+
+template <typename T, int PY, int CB, int NPL = 6>
+__device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec, int kx0, int qx, uint64_t *bar)
+{
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    const int ncol = qx - kx0 < CB ? qx - kx0 : CB;
+    const int64_t qplane = (int64_t)qx * QS;
+    mbar_arrive_expect_tx(bar, (uint32_t)(ncol * NPL * QS * sizeof(T)));
+    // the CTA's columns are consecutive rows of every plane: one copy per plane
+    for (int p = 0; p < NPL; ++p)
+        bulk_copy_g2s(ssp + p * CB * QS, spec + p * qplane + (int64_t)kx0 * QS, ncol * QS * sizeof(T), bar);
+}
+
+// Bounded wait for the spectra; on timeout records the error, gives the copies
+// one more bounded wait and tells the CTA to return (uniformly).
+__device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err)
+{
+    const bool ok = mbar_wait_bounded(bar, 0, SG_MBAR_MAX_TRIES);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(bar, 0, SG_MBAR_MAX_TRIES);
+        }
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// resident CTAs per SM asked of the register allocator (spill-free choices at
+// the default shapes, scaled by the CTA size for the other candidates)
+template <typename T, int PY>
+constexpr int col_min_blocks_def() { return sizeof(T) == 4 ? (PY == 2048 ? 3 : (PY == 4096 ? 1 : 2)) : 1; }
+template <typename T, int PY, int THREADS>
+constexpr int col_min_blocks()
+{
+    constexpr int def_threads = (PY >= 2048 ? 1 : 2048 / PY) * PY / 8;
+    return col_min_blocks_def<T, PY>() * def_threads / THREADS >= 1 ? col_min_blocks_def<T, PY>() * def_threads / THREADS : 1;
+}
+
+template <typename T, int PY, int CB, int THREADS, int NOUT>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv(const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv,
+                                                      const T *__restrict__ spec, int ny, int qx, int nf,
+                                                      const cplx_t<T> *__restrict__ tw, int *err)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
+    __shared__ uint64_t bar;
+    constexpr int EPT = CB * PY / THREADS;
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    const int kx0 = blockIdx.x * CB;
+    constexpr int NPL = NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL>(ssp, spec, kx0, qx, &bar);
+
+    C accx[EPT], accy[EPT], accz[NOUT == 3 ? EPT : 1];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+#pragma unroll
+    for (int q = 0; q < (NOUT == 3 ? EPT : 1); ++q) accz[q] = cmake<C>((T)0, (T)0);
+
+    for (int f = 0; f < nf; ++f) {
+        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+            const int c = e / PY, j = e % PY;
+            const int kx = kx0 + c;
+            if (j >= PY / 2) continue;  // taken as zero by the first stage
+            buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
+        }
+        __syncthreads();
+        fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
+        if (f == 0 && !spectra_ready(&bar, err)) return;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int e = threadIdx.x + q * THREADS;
+            const int c = e / PY, ky = e % PY;
+            const int kx = kx0 + c;
+            if (kx >= qx) continue;
+            const bool lower = ky <= PY / 2;
+            const int kq = lower ? ky : PY - ky;
+            const T sg = lower ? (T)1 : (T)-1;
+            const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
+            const C X = buf[spad<C>(e)];
+            // explicitly rounded (see mul_rn): the result must not depend on the launch shape
+            if constexpr (NOUT == 1) {
+                // potential planes: p (real, even-even), a (i a: odd in kx), b (i b: odd in ky)
+                if (f == 0) {
+                    const T pp = sp[0];
+                    accx[q] = cmake<C>(mul_rn(pp, X.x), mul_rn(pp, X.y));
+                } else {
+                    const T g = f == 1 ? sp[1 * CB * QS] : sg * sp[2 * CB * QS];
+                    accx[q] = cmake<C>(fma(-g, X.y, accx[q].x), fma(g, X.x, accx[q].y));
+                }
+                continue;
+            }
+            if (f == 0) {
+                const T a = sp[0 * CB * QS];
+                const T d = sg * sp[3 * CB * QS];
+                accx[q] = cmake<C>(-mul_rn(a, X.y), mul_rn(a, X.x));
+                accy[q] = cmake<C>(-mul_rn(d, X.y), mul_rn(d, X.x));
+                if constexpr (NOUT == 3) {
+                    const T g = sp[6 * CB * QS];  // real: sigma^ g
+                    accz[q] = cmake<C>(mul_rn(g, X.x), mul_rn(g, X.y));
+                }
+            } else if (f == 1) {
+                const T b = sp[1 * CB * QS];
+                const T ff = sg * sp[5 * CB * QS];
+                accx[q] = cmake<C>(fma(b, X.x, accx[q].x), fma(b, X.y, accx[q].y));
+                accy[q] = cmake<C>(fma(ff, X.x, accy[q].x), fma(ff, X.y, accy[q].y));
+                if constexpr (NOUT == 3) {
+                    const T hh = sp[7 * CB * QS];  // imaginary: deltax^ (i hh)
+                    accz[q] = cmake<C>(fma(-hh, X.y, accz[q].x), fma(hh, X.x, accz[q].y));
+                }
+            } else {
+                const T cc = sg * sp[2 * CB * QS];
+                const T ee = sp[4 * CB * QS];
+                accx[q] = cmake<C>(fma(cc, X.x, accx[q].x), fma(cc, X.y, accx[q].y));
+                accy[q] = cmake<C>(fma(ee, X.x, accy[q].x), fma(ee, X.y, accy[q].y));
+                if constexpr (NOUT == 3) {
+                    const T kk = sg * sp[8 * CB * QS];  // imaginary, odd in ky: deltay^ (i s kk)
+                    accz[q] = cmake<C>(fma(-kk, X.y, accz[q].x), fma(kk, X.x, accz[q].y));
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    for (int o = 0; o < NOUT; ++o) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            C v = o == 0 ? accx[q] : accy[q];
+            if constexpr (NOUT == 3) {
+                if (o == 2) v = accz[q];
+            }
+            buf[spad<C>(threadIdx.x + q * THREADS)] = v;
+        }
+        __syncthreads();
+        fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
+        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+            const int c = e / PY, j = e % PY;
+            const int kx = kx0 + c;
+            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = buf[spad<C>(e)];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int PX, int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict__ work_inv, T *__restrict__ fx,
+                                                     T *__restrict__ fy, T *__restrict__ fz, int nx, int ny,
+                                                     const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int RB = 2 * NB;
+    constexpr int QX = PX / 2 + 1;
+    const int o = blockIdx.y;
+    const int j0 = blockIdx.x * RB;
+    const C *w = work_inv + (int64_t)o * QX * ny;
+    T *out = o == 0 ? fx : (o == 1 ? fy : fz);
+
+    // Z[k] = A[k] + i B[k] over the full length, from the half spectra of rows 2s, 2s+1
+    for (int e = threadIdx.x; e < NB * QX; e += THREADS) {
+        const int s = e % NB, k = e / NB;
+        const int ja = j0 + 2 * s;
+        C a = ja < ny ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
+        C b = ja + 1 < ny ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
+        if (k == 0 || k == PX / 2) {
+            a.y = (T)0;
+            b.y = (T)0;
+        }
+        buf[spad<C>(s * PX + k)] = cmake<C>(a.x - b.y, a.y + b.x);
+        if (k > 0 && k < PX / 2) buf[spad<C>(s * PX + PX - k)] = cmake<C>(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+    }
+    __syncthreads();
+    fft_batch<C, PX, NB, THREADS, true, false, true>(buf, tw);
+    for (int e = threadIdx.x; e < NB * PX; e += THREADS) {
+        const int s = e / PX, i = e % PX;
+        if (i >= nx) continue;
+        const int ja = j0 + 2 * s;
+        const C z = buf[spad<C>(e)];
+        if (ja < ny) out[(int64_t)ja * nx + i] = z.x;
+        if (ja + 1 < ny) out[(int64_t)(ja + 1) * nx + i] = z.y;
+    }
+}
+
+// y-transforms of sigma's first and last columns, packed as z = c0 + i c1:
+// edge[k] = C0(k), edge[PY + k] = C1(k), k < PY.
+template <typename T, int PY, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_edge_cols(const T *__restrict__ sigma, int nx, int ny, cplx_t<T> *__restrict__ edge,
+                                                       const cplx_t<T> *__restrict__ tw)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    for (int j = threadIdx.x; j < PY / 2; j += THREADS) {  // positions >= PY/2 are zero
+        const T a = j < ny ? sigma[(int64_t)j * nx] : (T)0;
+        const T b = j < ny ? sigma[(int64_t)j * nx + nx - 1] : (T)0;
+        buf[spad<C>(j)] = cmake<C>(a, b);
+    }
+    __syncthreads();
+    fft_batch<C, PY, 1, THREADS, false, true>(buf, tw);
+    const T half = (T)0.5;
+    for (int k = threadIdx.x; k < PY; k += THREADS) {
+        const C z = buf[spad<C>(k)];
+        const C w = buf[spad<C>((PY - k) & (PY - 1))];
+        edge[k] = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
+        edge[PY + k] = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
+    }
+}
+
+// Column pass for central slopes: one forward transform (sigma), the slope
+// spectra formed per bin (see the header comment), two inverse transforms.
+template <typename T, int PY, int CB, int THREADS>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv_central(
+    const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv, const T *__restrict__ spec,
+    const cplx_t<T> *__restrict__ edge, const T *__restrict__ phase, int ny, int qx, const cplx_t<T> *__restrict__ tw,
+    int *err)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
+    __shared__ uint64_t bar;
+    __shared__ C rows[CB][2];  // R0, R1 of each column
+    constexpr int EPT = CB * PY / THREADS;
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    const int kx0 = blockIdx.x * CB;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
+    const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
+    const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
+
+    for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+        const int c = e / PY, j = e % PY;
+        const int kx = kx0 + c;
+        if (j >= PY / 2) continue;  // taken as zero by the first stage
+        buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    if (threadIdx.x < CB) {
+        rows[threadIdx.x][0] = buf[spad<C>(threadIdx.x * PY)];
+        rows[threadIdx.x][1] = buf[spad<C>(threadIdx.x * PY + ny - 1)];
+    }
+    __syncthreads();
+    fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
+    if (!spectra_ready(&bar, err)) return;
+
+    C accx[EPT], accy[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        const int e = threadIdx.x + q * THREADS;
+        const int c = e / PY, ky = e % PY;
+        const int kx = kx0 + c;
+        accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+        if (kx >= qx) continue;
+        const bool lower = ky <= PY / 2;
+        const int kq = lower ? ky : PY - ky;
+        const T sg = lower ? (T)1 : (T)-1;
+        const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
+        const C S = buf[spad<C>(e)];
+        // slope spectra
+        const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
+        const C e1 = cmake<C>(__ldg(&ce1[2 * kx]), __ldg(&ce1[2 * kx + 1]));
+        const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
+        const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
+        const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
+        const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
+        // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
+        const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
+        const C q2 = cmul_rn(f2, rows[c][1]), q1 = cmul_rn(f1, rows[c][0]);
+        const C X = cmake<C>(add_rn(add_rn(-mul_rn(cs, S.y), p2.x), -p1.x), add_rn(add_rn(mul_rn(cs, S.x), p2.y), -p1.y));
+        const C Y = cmake<C>(add_rn(add_rn(-mul_rn(rs, S.y), q2.x), -q1.x), add_rn(add_rn(mul_rn(rs, S.x), q2.y), -q1.y));
+        const T a = sp[0 * CB * QS];
+        const T b = sp[1 * CB * QS];
+        const T cc = sg * sp[2 * CB * QS];
+        const T d = sg * sp[3 * CB * QS];
+        const T ee = sp[4 * CB * QS];
+        const T ff = sg * sp[5 * CB * QS];
+        accx[q] = cmake<C>(fma(cc, Y.x, fma(b, X.x, -mul_rn(a, S.y))), fma(cc, Y.y, fma(b, X.y, mul_rn(a, S.x))));
+        accy[q] = cmake<C>(fma(ff, X.x, fma(ee, Y.x, -mul_rn(d, S.y))), fma(ff, X.y, fma(ee, Y.y, mul_rn(d, S.x))));
+    }
+    __syncthreads();
+
+    for (int o = 0; o < 2; ++o) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
+        __syncthreads();
+        fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
+        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
+            const int c = e / PY, j = e % PY;
+            const int kx = kx0 + c;
+            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = buf[spad<C>(e)];
+        }
+        __syncthreads();
+    }
+}
+
+
+// ------------------------------------------------------------ launch shapes --
+
+// Default shapes (measured): row sequences (two rows each) per CTA of the
+// forward and inverse row passes, columns per CTA of the column passes.
+__host__ __device__ constexpr int row_nb_default(int px) { return px >= 4096 ? 2 : (4096 / px < 2 ? 2 : 4096 / px); }
+__host__ __device__ constexpr int row_nb_inv_default(int px) { return px >= 4096 ? 2 : (px == 2048 ? 4 : 4096 / px); }
+__host__ __device__ constexpr int col_cb_default(int py) { return py >= 2048 ? 1 : 2048 / py; }
+constexpr int ROW_THREADS = 256;
+
+// Candidate shapes: half, the default, and twice the default, where feasible
+// (shared memory within 200 KB, 32..512 threads per CTA: 1024 would cap registers at 64).
+__host__ __device__ constexpr int shape_candidate(int def, int k) { return k == 0 ? def / 2 : (k == 1 ? def : 2 * def); }
+template <typename T>
+__host__ __device__ constexpr bool row_feasible_t(int px, int nb)
+{
+    return nb >= 1 && nb <= 64 && (int64_t)spad_size<cplx_t<T>>(nb * px) * (int64_t)sizeof(cplx_t<T>) <= 200 * 1024;
+}
+template <typename T, int PY, int CB, int NPL>
+__host__ __device__ constexpr bool col_feasible_t()
+{
+    return CB >= 1 && CB * PY / 8 >= 32 && CB * PY / 8 <= 512 && col_smem_bytes<T, PY, CB, NPL>() <= 200 * 1024;
+}
+
+// Dispatchers (explicitly instantiated for float and double in their units).
+template <typename T>
+sg_status rows_fwd(int px, int nb, const field_src<T> &src, cplx_t<T> *work, int nf, const cplx_t<T> *tw,
+                   cudaStream_t st);
+template <typename T>
+sg_status rows_inv(int px, int nb, const cplx_t<T> *work, T *fx, T *fy, T *fz, int nx, int ny, const cplx_t<T> *tw,
+                   cudaStream_t st);
+template <typename T>
+sg_status cols(int py, int cb, int nout, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf,
+               const cplx_t<T> *tw, int *err, cudaStream_t st);
+template <typename T>
+sg_status cols_central(int py, int cb, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge,
+                       const T *phase, int ny, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st);
+template <typename T>
+sg_status edge_cols(int py, const T *sigma, int nx, int ny, cplx_t<T> *edge, const cplx_t<T> *tw, cudaStream_t st);
+
+#define SG_PAD_SWITCH(P, CALL)                 \
+    switch (P) {                               \
+    case 64: { constexpr int PP = 64; CALL; } break;     \
+    case 128: { constexpr int PP = 128; CALL; } break;   \
+    case 256: { constexpr int PP = 256; CALL; } break;   \
+    case 512: { constexpr int PP = 512; CALL; } break;   \
+    case 1024: { constexpr int PP = 1024; CALL; } break; \
+    case 2048: { constexpr int PP = 2048; CALL; } break; \
+    case 4096: { constexpr int PP = 4096; CALL; } break; \
+    default: return SG_EINVAL;                 \
+    }
+
+}  // namespace sgk
+

@@ -1,0 +1,7 @@
+// Column pass, FP32 instantiation (see fftconv_cols.inl).
+#include "fftconv_cols.inl"
+
+namespace sgk {
+template sg_status cols<float>(int, int, int, const float2 *, float2 *, const float *, int, int, int, const float2 *,
+                               int *, cudaStream_t);
+}  // namespace sgk

@@ -1,0 +1,7 @@
+// Column pass, FP64 instantiation (see fftconv_cols.inl).
+#include "fftconv_cols.inl"
+
+namespace sgk {
+template sg_status cols<double>(int, int, int, const double2 *, double2 *, const double *, int, int, int,
+                                const double2 *, int *, cudaStream_t);
+}  // namespace sgk

@@ -110,6 +110,10 @@ _SIGNATURES = {
                                              ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, _I32P, _I32P, _I32P]),
     "sg_zones_links": (ctypes.c_int, [ctypes.POINTER(sg_zones), _I64P, ctypes.POINTER(ctypes.c_uint8), _I64P]),
+    "sg_tune_get": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "sg_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "sg_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double)]),
     "sg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sg_last_error": (ctypes.c_char_p, []),
     "sg_version": (ctypes.c_int, []),
@@ -328,6 +332,34 @@ def sg_server_get_stats(server, reset_latencies=False):
 
 def sg_version():
     return int(load().sg_version())
+
+
+TUNE_KNOBS = ("row_fwd", "row_inv", "col", "col_central")
+
+
+def sg_tune_get(precision, pad):
+    out = (ctypes.c_int * 4)()
+    _check(load().sg_tune_get(int(precision), int(pad), out), "sg_tune_get")
+    return dict(zip(TUNE_KNOBS, list(out)))
+
+
+def sg_tune_set(precision, pad, shape):
+    """shape: dict of TUNE_KNOBS (missing = default) or a 4-sequence (0 = default)."""
+    vals = [int(shape.get(k, 0)) for k in TUNE_KNOBS] if isinstance(shape, dict) else [int(v) for v in shape]
+    arr = (ctypes.c_int * 4)(*vals)
+    _check(load().sg_tune_set(int(precision), int(pad), arr), "sg_tune_set")
+
+
+def sg_autotune(precision, min_pad, max_pad, reps=5):
+    """Tune the launch shapes; returns {pad: (shapes, best solve ms)}."""
+    pads = []
+    p = int(min_pad)
+    while p <= int(max_pad):
+        pads.append(p)
+        p *= 2
+    best = (ctypes.c_double * max(1, len(pads)))()
+    _check(load().sg_autotune(int(precision), int(min_pad), int(max_pad), int(reps), best), "sg_autotune")
+    return {p: (sg_tune_get(precision, p), best[i]) for i, p in enumerate(pads)}
 
 
 def make_zones(nx0, ny0, x0, y0, h0, level, ix, iy):

@@ -83,3 +83,19 @@ def test_cross_mode_rules(lib):
     direct = sg.sg_plan_bytes(pat, sg.SG_FP32, cross_mode=1)
     levels = sg.sg_plan_bytes(pat, sg.SG_FP32, cross_mode=2)
     assert direct > 0 and levels > 0 and levels != direct
+
+
+def test_tune_table_host_rules(lib):
+    """The launch-shape table: defaults, candidates only, reset with zeros (host only)."""
+    d = sg.sg_tune_get(sg.SG_FP32, 2048)
+    assert d == {"row_fwd": 2, "row_inv": 4, "col": 1, "col_central": 1}
+    sg.sg_tune_set(sg.SG_FP32, 2048, {"row_fwd": 1, "col": 2})
+    assert sg.sg_tune_get(sg.SG_FP32, 2048)["row_fwd"] == 1 and sg.sg_tune_get(sg.SG_FP32, 2048)["col"] == 2
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_tune_set(sg.SG_FP32, 2048, {"row_fwd": 3})
+    assert e.value.status == sg.SG_EINVAL and "candidate" in str(e.value)
+    with pytest.raises(sg.SgError):
+        sg.sg_tune_set(sg.SG_FP32, 3000, [0, 0, 0, 0])
+    sg.sg_tune_set(sg.SG_FP32, 2048, [0, 0, 0, 0])
+    assert sg.sg_tune_get(sg.SG_FP32, 2048) == d
+    assert sg.sg_tune_get(sg.SG_FP64, 4096)["col"] == 1
