@@ -580,6 +580,13 @@ def run_gpu(args):
         return sg.Plan(wl["patches"], precision=prec, slope_mode=wl["slope_mode"], z=zt)
 
     plan = make_plan("fp32")
+    # launch shapes of the plan's transform lengths picked by the library's autotuner
+    tuned = None
+    if not args.no_autotune and plan.info["max_pad"] <= 4096 and plan.info["cross_mode"] != 2:
+        t0 = time.perf_counter()
+        pads = sorted({_pad(p[1]) for p in wl["patches"]} | {_pad(p[2]) for p in wl["patches"]})
+        res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=5)
+        tuned = {"seconds": time.perf_counter() - t0, "shapes": {str(p): res[p][0] for p in pads}}
     sg.sg_plan_set_timing(plan.handle, True)
     stream = torch.cuda.Stream()
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
@@ -738,6 +745,7 @@ def run_gpu(args):
         "e2e": ({"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                  "d2h_bytes_per_step": d2h} if e2e_ms else None),
         "gpu_launches": args.steps * info["launches"],
+        "autotune": tuned,
         "clocks": clk.summary(),
         "wall_s": wall,
     }
@@ -917,7 +925,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="run the request-server workload instead")
     ap.add_argument("--batch", action="store_true", help="run the graph-captured batch workload instead")
     ap.add_argument("--batch-size", type=int, default=64)
-    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default launch shapes")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-sweep", action="store_true", help="also run loads 0.3, 0.5, 1.0 on a tenth of the stream")
     ap.add_argument("--serve-inflight", type=int, default=8)
