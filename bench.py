@@ -238,7 +238,7 @@ def run_batch(args):
     tuned, tune_s = None, 0.0
     if not args.no_autotune:
         t0 = time.perf_counter()
-        res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=5)
+        res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=15)
         tune_s = time.perf_counter() - t0
         tuned = {str(p): res[p][0] for p in pads}
 
@@ -582,10 +582,11 @@ def run_gpu(args):
     plan = make_plan("fp32")
     # launch shapes of the plan's transform lengths picked by the library's autotuner
     tuned = None
-    if not args.no_autotune and plan.info["max_pad"] <= 4096 and plan.info["cross_mode"] != 2:
+    if (not args.no_autotune and wl["patches"] and plan.info["max_pad"] <= 4096
+            and plan.info["cross_mode"] != 2):
         t0 = time.perf_counter()
         pads = sorted({_pad(p[1]) for p in wl["patches"]} | {_pad(p[2]) for p in wl["patches"]})
-        res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=5)
+        res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=15)
         tuned = {"seconds": time.perf_counter() - t0, "shapes": {str(p): res[p][0] for p in pads}}
     sg.sg_plan_set_timing(plan.handle, True)
     stream = torch.cuda.Stream()
@@ -771,16 +772,22 @@ def _pad(n):
     return p
 
 
+def _lv_cexp(s, p):
+    """Compression exponent of a level's source transforms (lengths p >> c >= 64)."""
+    return min(s, p.bit_length() - 1 - 6)
+
+
 def lv_geometry(wl):
     """Level-convolution layout of a workload: padded finest-lattice lengths and
-    the (nx, ny) of every level's image (bounding box of its cells)."""
+    the (nx, ny, s) of every level's image (bounding box of its cells; cells
+    2^s finest cells wide)."""
     if "zones" in wl:
         nx0, ny0, x0, y0, h0, level, ix, iy = wl["zones"]
         lmax = int(level.max())
         imgs = []
         for m in range(lmax + 1):
             sel = level == m
-            imgs.append((int(ix[sel].max() - ix[sel].min() + 1), int(iy[sel].max() - iy[sel].min() + 1)))
+            imgs.append((int(ix[sel].max() - ix[sel].min() + 1), int(iy[sel].max() - iy[sel].min() + 1), lmax - m))
         wx, wy = nx0 << lmax, ny0 << lmax
     else:
         pats = wl["patches"]
@@ -796,7 +803,7 @@ def lv_geometry(wl):
             gy0 = min(round((p[4] - Y0) / h) for p in ps)
             gx1 = max(round((p[3] - X0) / h) + p[1] for p in ps)
             gy1 = max(round((p[4] - Y0) / h) + p[2] for p in ps)
-            imgs.append((gx1 - gx0, gy1 - gy0))
+            imgs.append((gx1 - gx0, gy1 - gy0, lmax - m))
         wx = max(round((p[3] - X0) / h0) + p[1] for p in pats if p[0] == 0) << lmax
         wy = max(round((p[4] - Y0) / h0) + p[2] for p in pats if p[0] == 0) << lmax
     return _pad(wx), _pad(wy), imgs
@@ -812,15 +819,16 @@ def algorithmic_flops(wl, info, stage):
     if info.get("cross_mode") == 2:
         px, py, imgs = lv_geometry(wl)
         qx = px // 2 + 1
-        fx, fy = 5.0 * px * math.log2(px), 5.0 * py * math.log2(py)
+        fft = lambda n: 5.0 * n * math.log2(n)
         L = len(imgs)
-        for nx, ny in imgs:
+        for nx, ny, s in imgs:
+            pcx, pcy = px >> _lv_cexp(s, px), py >> _lv_cexp(s, py)
             if stage == "row_fwd":
-                total += 3 * (ny / 2) * fx
+                total += 3 * (ny / 2) * fft(pcx)
             elif stage == "col_conv":
-                total += qx * (3 * fy + 2 * fy + L * 3 * 10 * py)
+                total += (pcx // 2 + 1) * 3 * fft(pcy) + qx * (2 * fft(py) + L * 3 * 10 * py)
             elif stage == "row_inv":
-                total += 2 * (ny / 2) * fx
+                total += 2 * (ny / 2) * fft(px)
         return total
     for p in wl["patches"]:
         nx, ny = p[1], p[2]
@@ -844,9 +852,11 @@ def algorithmic_flops(wl, info, stage):
 def algorithmic_bytes(wl, info, stage):
     """Bytes a stage must move per solve (see the design notes): FP32 complex
     intermediates of (P/2+1) x ny bins per field, spectra planes, inputs, outputs.
-    Level convolutions: the forward column pass writes full source spectra, the
-    column kernel of every target level reads every source level's spectra and
-    its compressed kernel planes (6 real quarter planes per source level)."""
+    Level convolutions: the forward column pass writes compact source spectra
+    (a level of cells 2^s finest cells wide: P/2^s per axis); the column-MAC
+    launch of all target levels reads them once, and once each distinct set of
+    compressed kernel planes (6 real quarter planes per (source width, sample
+    shift))."""
     es = 4
     cs = 8
     total = 0
@@ -854,15 +864,20 @@ def algorithmic_bytes(wl, info, stage):
         px, py, imgs = lv_geometry(wl)
         qx, qy = px // 2 + 1, py // 2 + 1
         L = len(imgs)
-        for nx, ny in imgs:
+        for nx, ny, s in imgs:
+            qxc, pcy = (px >> _lv_cexp(s, px)) // 2 + 1, py >> _lv_cexp(s, py)
             if stage == "row_fwd":
-                total += 3 * nx * ny * es + 3 * qx * ny * cs
+                total += 3 * nx * ny * es + 3 * qxc * ny * cs
             elif stage == "col_conv":
-                total += 3 * qx * ny * cs + 3 * qx * py * cs          # column transforms of this level
-                total += L * (3 * qx * py * cs + 6 * qx * qy * es)    # read by every target level
+                total += 3 * qxc * ny * cs + 3 * qxc * pcy * cs       # compact column transforms of this level
+                total += 3 * qxc * pcy * cs                         # read once by the column-MAC launch
                 total += 2 * qx * ny * cs                           # this level's inverse columns
             elif stage == "row_inv":
                 total += 2 * qx * ny * cs + 2 * nx * ny * es
+        if stage == "col_conv":
+            # kernel planes: one set of 6 real quarter planes per distinct (source width, sample shift)
+            keys = {(sm, (sm >= 1) - (sl >= 1)) for _, _, sm in imgs for _, _, sl in imgs}
+            total += len(keys) * 6 * qx * qy * es
         return total
     # central slopes are formed from sigma's transforms: one field is transformed
     nf = 3 if wl["slope_mode"] == 2 else 1

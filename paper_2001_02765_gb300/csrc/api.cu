@@ -354,7 +354,9 @@ bool lv_params(const sg_geom *g, const geom_info &gi, sg_precision prec, sg_lv_s
         }
         a.map[m] = mp.data();
         mapbytes += (int64_t)mp.size() * 4;
-        work += (3 * qx * a.ny[m] + 3 * qx * py + 2 * qx * a.ny[m]) * cs;
+        // compact row transforms and source spectra, full-width inverse columns
+        const int64_t qxc = (px >> sg_lv_cexp(sx, (int)px)) / 2 + 1, pcy = py >> sg_lv_cexp(sx, (int)py);
+        work += (3 * qxc * a.ny[m] + 3 * qxc * pcy + 2 * qx * a.ny[m]) * cs;
     }
     int nkeys = 0;
     int ks[3 * SG_MAX_LEVELS], kd[3 * SG_MAX_LEVELS];
@@ -645,7 +647,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
     {
         const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0;
-        int n = use_lv ? 4 * (gi.lmax + 1) : gi.n * (central ? 4 : 3);
+        // level convolutions: row, column and inverse-row launches per level, one column-MAC launch
+        int n = use_lv ? 3 * (gi.lmax + 1) + 1 : gi.n * (central ? 4 : 3);
         if (plan->composite) {
             for (int k = 0; k < gi.n; ++k) n += 1 + (gi.parent[k] >= 0);
             if (plan->ntiles > 0) n += 2 + (nsplit > 1);

@@ -123,11 +123,13 @@ struct sg_lv_level {
     int s;              // cells of this level are 2^s finest cells wide
     int nx, ny;         // level image: bounding box of the level's patches, in cells
     int i0, j0;         // finest-lattice index of the sample point of image cell (0, 0)
+    int cx, cy;         // compression exponents: source transforms of length px >> cx, py >> cy
     int *map;           // device [ny][nx]: index of the cell in the field arrays, or -1
     int64_t fwd_off;    // complex-element offset of the level's row transforms (3 fields)
-    int64_t spec_off;   // of its source spectra (3 fields, full columns)
+    int64_t spec_off;   // of its compact source spectra (3 fields)
     int64_t inv_off;    // of its inverse-column outputs (Fx, Fy)
 };
+
 
 struct sg_lv {
     int nlev;
@@ -140,6 +142,7 @@ struct sg_lv {
     int key_d2[3 * SG_MAX_LEVELS];           // per kernel: 2 x sample shift (-1, 0, 1)
     void *spectra;                           // [nkeys][6][px/2+1][py/2+1] T (compressed, see lvconv.cu)
     void *phase;                             // exp(i pi k / P), k in [-P/2, P/2], x then y, complex T
+    void *cphase;                            // exp(-i pi j / P), j in [0, P], x then y, complex T
     int64_t fwd_elems, spec_elems, inv_elems;
 };
 
@@ -302,6 +305,15 @@ static inline int sg_ilog2(int v)
     int l = 0;
     while ((1 << l) < v) ++l;
     return l;
+}
+
+// Compression exponent of a level of width exponent s on an axis of padded
+// length p: its samples lie every 2^s finest cells, so its spectrum repeats
+// with period p / 2^s; transforms stay at 64 points or more.
+static inline int sg_lv_cexp(int s, int p)
+{
+    const int c = sg_ilog2(p) - 6;
+    return s < c ? s : c;
 }
 
 // Row stride of the spectra planes: (Py/2 + 1) rounded up to 4 entries so that

@@ -25,6 +25,22 @@
 // Kernel spectra (six planes per distinct (s, d), FP64-built) depend only on
 // the lattice, not on the density.
 //
+// Compact source spectra: a level of width exponent s has samples only every
+// 2^s finest cells, so the transform of its sampled field repeats with period
+// P / 2^c along an axis for any c <= s. Its row and column transforms run at
+// length Pc = P / 2^c (c = s, or less where Pc would fall below 64 points),
+// on compact positions p = I / 2^c. When c = s >= 1 these are half-integers
+// (I = 2^s i + 2^(s-1)): the samples sit at integer positions q = p - 1/2 and
+// the half shift is the factor psi(k) = exp(-i pi k / Pc). The full spectrum
+// is then
+//   F(kx, ky) = Ghat(kx mod Pcx, ky mod Pcy) psi_x(kx) psi_y(ky),
+//   psi(k + r Pc) = (-1)^r psi(k)  (psi = 1 without the half shift),
+// and the column pass stores Ghat psi over kx in [0, Pcx/2], ky in [0, Pcy).
+// The column kernel reads the other half of the compact kx range from the
+// Hermitian partner, Ghat(kx, ky) = conj Ghat(Pcx - kx, -ky mod Pcy), whose
+// stored phase differs by a sign on every half-shifted axis (but not at
+// ky = 0 on the y axis). This cuts the source spectra of a level by 4^c.
+//
 // Tables: the closed forms of Section 2 at a real-valued centre offset (cx, cy)
 // in units of the cell width,
 //   K^{x,0} = D(u1) - D(u2),  D(u) = asinh(v2/|u|) - asinh(v1/|u|), or on the line
@@ -113,19 +129,18 @@ __global__ void k_lv_tables(double2 *z, int px, int py, int s, int d2)
 // ky <= Py/2 and sy ph_x(kx) ph_y(ky - Py) H(kx, Py - ky) above, ph(k) = exp(i pi d2 k / P).
 // Planes x0 xx xy y0 yx yy have (sx, sy) = (-,+) (+,+) (-,-) (+,-) (-,-) (+,+); the
 // imaginary ones (x0, y0) store Im H, the others Re H, [kx][ky] for kx in [0, px/2],
-// ky in [0, py/2], scaled by 1 / (px py).
+// ky in [0, py/2], scaled by 1 / (px py) and by G (x0, y0) or G h_f (the order-1 planes).
 __host__ __device__ constexpr bool lv_plane_imag(int p) { return p == 0 || p == 3; }
-__host__ __device__ constexpr int lv_plane_sy(int p) { return (p == 2 || p == 3 || p == 4) ? -1 : 1; }
 
 // Unpack the transforms of the packed pairs (A + i B: A^(k) = (Z(k) + conj Z(-k)) / 2,
 // B^(k) = (Z(k) - conj Z(-k)) / 2i), remove the half-cell phase and keep the real
 // or imaginary part of every plane.
 template <typename T>
-__global__ void k_lv_extract(const double2 *z, T *out, int px, int py, int d2)
+__global__ void k_lv_extract(const double2 *z, T *out, int px, int py, int d2, double sc0, double sc1)
 {
     const int qx = px / 2 + 1, qy = py / 2 + 1;
     const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
-    const double sc = 1.0 / ((double)px * (double)py);
+    const double inv = 1.0 / ((double)px * (double)py);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
         const int kx = (int)(e / qy), ky = (int)(e % qy);
         const int64_t ip = (int64_t)ky * px + kx;
@@ -141,13 +156,16 @@ __global__ void k_lv_extract(const double2 *z, T *out, int px, int py, int d2)
             // H = G (cs + i sn)
             const double har = ar * cs - ai * sn, hai = ar * sn + ai * cs;
             const double hbr = br * cs - bi * sn, hbi = br * sn + bi * cs;
-            out[pa[q] * qplane + e] = (T)(sc * (lv_plane_imag(pa[q]) ? hai : har));
-            out[pb[q] * qplane + e] = (T)(sc * (lv_plane_imag(pb[q]) ? hbi : hbr));
+            // order-0 planes (x0, y0) scaled by G, order-1 planes by G h_f
+            const double sa = inv * (lv_plane_imag(pa[q]) ? sc0 : sc1), sb = inv * (lv_plane_imag(pb[q]) ? sc0 : sc1);
+            out[pa[q] * qplane + e] = (T)(sa * (lv_plane_imag(pa[q]) ? hai : har));
+            out[pb[q] * qplane + e] = (T)(sb * (lv_plane_imag(pb[q]) ? hbi : hbr));
         }
     }
 }
 
-// Phase factors exp(i pi k / P) for k in [-P/2, P/2] (index k + P/2), per axis.
+// Phase factors exp(i pi k / P) for k in [-P/2, P/2] (index k + P/2), per axis;
+// and the half-shift factors exp(-i pi j / P) for j in [0, P], per axis.
 template <typename T>
 __global__ void k_lv_phase(cplx_t<T> *out, int px, int py)
 {
@@ -160,6 +178,18 @@ __global__ void k_lv_phase(cplx_t<T> *out, int px, int py)
     }
 }
 
+template <typename T>
+__global__ void k_lv_cphase(cplx_t<T> *out, int px, int py)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < px + py + 2; e += gridDim.x * blockDim.x) {
+        const bool xa = e < px + 1;
+        const int P = xa ? px : py, j = xa ? e : e - (px + 1);
+        double sn, cs;
+        sincospi(-(double)j / P, &sn, &cs);
+        out[e] = cmake<cplx_t<T>>((T)cs, (T)sn);
+    }
+}
+
 // ----------------------------------------------------------- solve kernels --
 
 template <typename T>
@@ -167,23 +197,25 @@ struct lv_rows_src {
     const T *S;         // composite source planes (sigma0, deltax, deltay), plane stride `plane`
     int64_t plane;
     const int *map;
-    int nx, ny, i0, s;
+    int nx, ny;
+    int p0, st;         // image column i sits at compact position p0 + i 2^st
 };
 
 template <typename T>
 __device__ __forceinline__ T lv_sample(const lv_rows_src<T> &a, int f, int j, int I)
 {
     if (j >= a.ny) return (T)0;
-    const int rel = I - a.i0;
-    if (rel < 0 || (rel & ((1 << a.s) - 1))) return (T)0;
-    const int i = rel >> a.s;
+    const int rel = I - a.p0;
+    if (rel < 0 || (rel & ((1 << a.st) - 1))) return (T)0;
+    const int i = rel >> a.st;
     if (i >= a.nx) return (T)0;
     const int c = a.map[(int64_t)j * a.nx + i];
     return c < 0 ? (T)0 : a.S[f * a.plane + c];
 }
 
-// Row transforms of a level's sampled rows (three fields, blockIdx.y), two real
-// rows per complex sequence; out[(f qx + kx) ny + j].
+// Row transforms (length PX = the level's compact Pcx) of its sampled rows
+// (three fields, blockIdx.y), two real rows per complex sequence;
+// out[(f qx + kx) ny + j], qx = PX/2 + 1.
 template <typename T, int PX, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_lv_row_fwd(lv_rows_src<T> a, cplx_t<T> *__restrict__ out,
                                                         const cplx_t<T> *__restrict__ tw)
@@ -217,11 +249,20 @@ __global__ void __launch_bounds__(THREADS) k_lv_row_fwd(lv_rows_src<T> a, cplx_t
     }
 }
 
-// Column transforms to full spectra: the level's ny rows sit at finest rows
-// j0 + j 2^s; spec[(f qx + kx) PY + ky].
+struct lv_col_src {
+    int ny, p0, st;     // image row j sits at compact position p0 + j 2^st
+    int qx;             // compact half-spectrum width Pcx/2 + 1
+    int cx, cy;         // compression exponents (half-shift table index shifts)
+    int hx, hy;         // samples half-shifted on that axis (c = s >= 1)
+};
+
+// Column transforms (length PY = the level's compact Pcy) to compact spectra
+// times the half-shift factors psi_x(kx) psi_y(ky); spec[(f qx + kx) PY + ky].
 template <typename T, int PY, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_lv_col_fwd(const cplx_t<T> *__restrict__ in, cplx_t<T> *__restrict__ spec,
-                                                        int ny, int j0, int s, int qx, const cplx_t<T> *__restrict__ tw)
+                                                        lv_col_src a, const cplx_t<T> *__restrict__ tw,
+                                                        const cplx_t<T> *__restrict__ cphx,
+                                                        const cplx_t<T> *__restrict__ cphy)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -229,28 +270,44 @@ __global__ void __launch_bounds__(THREADS) k_lv_col_fwd(const cplx_t<T> *__restr
     const int kx = blockIdx.x, f = blockIdx.y;
     for (int e = threadIdx.x; e < PY / 2; e += THREADS) buf[spad<C>(e)] = cmake<C>((T)0, (T)0);
     __syncthreads();
-    const C *col = in + ((int64_t)f * qx + kx) * ny;
-    for (int j = threadIdx.x; j < ny; j += THREADS) buf[spad<C>(j0 + (j << s))] = col[j];
+    const C *col = in + ((int64_t)f * a.qx + kx) * a.ny;
+    for (int j = threadIdx.x; j < a.ny; j += THREADS) buf[spad<C>(a.p0 + (j << a.st))] = col[j];
     __syncthreads();
     fft_batch<C, PY, 1, THREADS, false, true>(buf, tw);
-    C *o = spec + ((int64_t)f * qx + kx) * PY;
-    for (int k = threadIdx.x; k < PY; k += THREADS) o[k] = buf[spad<C>(k)];
+    C *o = spec + ((int64_t)f * a.qx + kx) * PY;
+    const C psx = a.hx ? cphx[kx << a.cx] : cmake<C>((T)1, (T)0);
+    for (int k = threadIdx.x; k < PY; k += THREADS) {
+        C v = buf[spad<C>(k)];
+        if (a.hy) v = cmul(v, cphy[k << a.cy]);
+        if (a.hx) v = cmul(v, psx);
+        o[k] = v;
+    }
 }
 
 struct lv_mac_args {
     int nsrc;
-    int64_t spec_off[SG_MAX_LEVELS];    // complex-element offset of each source level's spectra
-    int key[SG_MAX_LEVELS];             // kernel of each source level for this target level
-    int d2[SG_MAX_LEVELS];              // its 2 x sample shift
-    int ny, j0, t;                      // target level: sampled rows j0 + j 2^t, j < ny
+    int64_t spec_off[SG_MAX_LEVELS];    // complex-element offset of each source level's compact spectra
+    int lpx[SG_MAX_LEVELS];             // log2 of its compact lengths Pcx, Pcy
+    int lpy[SG_MAX_LEVELS];
+    int hx[SG_MAX_LEVELS];              // its samples half-shifted along x, y
+    int hy[SG_MAX_LEVELS];
+    int key[SG_MAX_LEVELS][SG_MAX_LEVELS];  // kernel of source level m for target level l, [m][l]
+    int d2[SG_MAX_LEVELS][SG_MAX_LEVELS];   // its 2 x sample shift
+    int ny[SG_MAX_LEVELS];              // target level l: sampled rows j0 + j 2^t, j < ny
+    int j0[SG_MAX_LEVELS];
+    int t[SG_MAX_LEVELS];
+    int64_t inv_off[SG_MAX_LEVELS];     // complex-element offset of its inverse-column outputs
     int qx;
-    double sc0, sc1;                    // G, and G h_f for the order-1 planes
 };
 
-// One column kx per CTA: Fx^, Fy^ = sum over source levels and fields of
-// source spectrum x kernel spectrum (decompressed, see k_lv_extract), formed
-// element by element straight into two shared buffers; inverse column
-// transforms; the target level's sampled rows to out[(o qx + kx) ny + j].
+// One (column kx, target level l) per CTA, kx = blockIdx.x / nsrc and
+// l = blockIdx.x % nsrc, so that the CTAs of all target levels of a column run
+// side by side and read its source spectra (and shared kernel planes) from L2:
+// Fx^, Fy^ = sum over source levels and fields of source spectrum (unfolded
+// from the compact one) x kernel spectrum (decompressed, see k_lv_extract),
+// formed element by element straight into two shared buffers; inverse column
+// transforms; the target level's sampled rows to out[(o qx + kx) ny + j]
+// (out at the level's inverse-column offset).
 template <typename T, int PY, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
                                                             const T *__restrict__ kspec,
@@ -264,80 +321,118 @@ __global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const
     C *bx = reinterpret_cast<C *>(smem_raw);
     C *by = bx + spad_size<C>(PY);
     constexpr int QY = PY / 2 + 1;
-    const int kx = blockIdx.x;
-    const int64_t sqplane = (int64_t)a.qx * PY, kqplane = (int64_t)a.qx * QY;
-    // U bins per thread at a time, so that their loads are in flight together
-    constexpr int UMAX = sizeof(T) == 8 ? 2 : 4;
-    constexpr int U = PY / THREADS >= UMAX ? UMAX : PY / THREADS;
-    for (int k0 = threadIdx.x; k0 < PY; k0 += U * THREADS) {
-        int kq[U];
-        bool lower[U];
-        C pyk[U], ax[U], ay[U];
+    const int kx = blockIdx.x / a.nsrc, l = blockIdx.x % a.nsrc;
+    const int64_t kqplane = (int64_t)a.qx * QY;
+    // Bins in mirror pairs: slot j in [0, PY/2) holds bins j and PY - j, which read
+    // the same kernel values (kq = j); slot 0 holds bins 0 and PY/2 (kq = 0 and PY/2).
+    // V slots per thread at a time, so that their loads are in flight together.
+    constexpr int NSLOT = PY / 2;
+    constexpr int VMAX = sizeof(T) == 8 ? 1 : 2;
+    constexpr int V = NSLOT / THREADS >= VMAX ? VMAX : 1;
+    const C phk = phx[kx + (a.qx - 1)];
+    for (int j0 = threadIdx.x; j0 < NSLOT; j0 += V * THREADS) {
+        int ky[V][2];
+        C ph[V][2], ax[V][2], ay[V][2];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int ky = k0 + u * THREADS;
-            lower[u] = ky <= PY / 2;
-            kq[u] = lower[u] ? ky : PY - ky;
-            pyk[u] = phy[(lower[u] ? ky : ky - PY) + PY / 2];
-            ax[u] = ay[u] = cmake<C>((T)0, (T)0);
+        for (int v = 0; v < V; ++v) {
+            const int j = j0 + v * THREADS;
+            ky[v][0] = j;
+            ky[v][1] = j == 0 ? PY / 2 : PY - j;
+            // half-cell phase exp(i pi (kx / Px + ky / Py)) at the signed frequencies j and -j (PY/2 for slot 0)
+            ph[v][0] = cmul(phk, phy[j + PY / 2]);
+            ph[v][1] = cmul(phk, phy[(j == 0 ? PY / 2 : -j) + PY / 2]);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) ax[v][b] = ay[v][b] = cmake<C>((T)0, (T)0);
         }
         for (int m = 0; m < a.nsrc; ++m) {
-            const C *sm = spec + a.spec_off[m] + (int64_t)kx * PY + k0;
-            const T *km = kspec + (int64_t)a.key[m] * 6 * kqplane + (int64_t)kx * QY;
-            C X[3][U];
-            T gx[3][U], gy[3][U];
+            // compact column of this kx: kx mod Pcx, or its Hermitian partner
+            const int lpx = a.lpx[m], lpy = a.lpy[m], pcx = 1 << lpx, pcy = 1 << lpy;
+            const int kxr = kx & (pcx - 1);
+            const bool fold = kxr > (pcx >> 1);
+            const int64_t splane = (int64_t)((pcx >> 1) + 1) * pcy;
+            const C *sm = spec + a.spec_off[m] + (int64_t)(fold ? pcx - kxr : kxr) * pcy;
+            const bool hy = a.hy[m] != 0;
+            // sign of the x half-shift: (-1)^(kx div Pcx), times -1 on the folded half
+            const bool xneg = a.hx[m] && ((((kx >> lpx) & 1) != 0) != fold);
+            const T *km = kspec + (int64_t)a.key[m][l] * 6 * kqplane + (int64_t)kx * QY;
+            int row[V][2];
+            bool neg[V][2];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int k = ky[v][b], kyr = k & (pcy - 1);
+                    row[v][b] = fold ? ((pcy - kyr) & (pcy - 1)) : kyr;
+                    neg[v][b] = xneg != (hy && ((((k >> lpy) & 1) != 0) != (fold && kyr != 0)));
+                }
+            }
+            C X[3][V][2];
+            T gx[3][V][2], gy[3][V][2];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    X[f][u] = sm[f * sqplane + u * THREADS];
-                    gx[f][u] = km[f * kqplane + kq[u]];
-                    gy[f][u] = km[(3 + f) * kqplane + kq[u]];
+                for (int v = 0; v < V; ++v) {
+                    const int j = j0 + v * THREADS;
+                    X[f][v][0] = sm[f * splane + row[v][0]];
+                    X[f][v][1] = sm[f * splane + row[v][1]];
+                    gx[f][v][0] = gx[f][v][1] = km[f * kqplane + j];
+                    gy[f][v][0] = gy[f][v][1] = km[(3 + f) * kqplane + j];
                 }
             }
-            const int d2 = a.d2[m];
-            const C phk = phx[kx + (a.qx - 1)];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                C hx = cmake<C>((T)0, (T)0), hy = cmake<C>((T)0, (T)0);
+            if (j0 == 0) {  // slot 0: bin PY/2 has kernel values of its own
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
-                    const T sc = (T)(f == 0 ? a.sc0 : a.sc1);
-                    T g1 = sc * gx[f][u], g2 = sc * gy[f][u];
-                    if (!lower[u]) {
-                        g1 *= (T)lv_plane_sy(f);
-                        g2 *= (T)lv_plane_sy(3 + f);
+                    gx[f][0][1] = km[f * kqplane + PY / 2];
+                    gy[f][0][1] = km[(3 + f) * kqplane + PY / 2];
+                }
+            }
+            const int d2 = a.d2[m][l];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    C X0 = X[0][v][b], X1 = X[1][v][b], X2 = X[2][v][b];
+                    if (fold) {
+                        X0.y = -X0.y;
+                        X1.y = -X1.y;
+                        X2.y = -X2.y;
                     }
-                    const C Xv = X[f][u];
-                    // real planes multiply by g, imaginary planes by i g
-                    if (lv_plane_imag(f)) hx = cadd(hx, cmake<C>(-g1 * Xv.y, g1 * Xv.x));
-                    else hx = cadd(hx, cmake<C>(g1 * Xv.x, g1 * Xv.y));
-                    if (lv_plane_imag(3 + f)) hy = cadd(hy, cmake<C>(-g2 * Xv.y, g2 * Xv.x));
-                    else hy = cadd(hy, cmake<C>(g2 * Xv.x, g2 * Xv.y));
+                    // planes (prescaled by G, G h_f): x0 imaginary, xx real, xy real; y0 imaginary,
+                    // yx real, yy real. The parts odd in ky (xy; y0, yx) change sign on the upper half.
+                    const T g0 = gx[0][v][b], g1 = gx[1][v][b], g2 = gx[2][v][b];
+                    const T h0 = gy[0][v][b], h1 = gy[1][v][b], h2 = gy[2][v][b];
+                    const T sg = (b == 0 || ky[v][1] == PY / 2) ? (T)1 : (T)-1;
+                    const T o2 = sg * g2, o0 = sg * h0, o1 = sg * h1;
+                    C hx = cmake<C>(g1 * X1.x - g0 * X0.y + o2 * X2.x, g1 * X1.y + g0 * X0.x + o2 * X2.y);
+                    C hy = cmake<C>(h2 * X2.x - o0 * X0.y + o1 * X1.x, h2 * X2.y + o0 * X0.x + o1 * X1.y);
+                    if (d2 != 0) {
+                        C p = ph[v][b];
+                        if (d2 < 0) p.y = -p.y;
+                        hx = cmul(hx, p);
+                        hy = cmul(hy, p);
+                    }
+                    const T sn = neg[v][b] ? (T)-1 : (T)1;
+                    ax[v][b] = cmake<C>(ax[v][b].x + sn * hx.x, ax[v][b].y + sn * hx.y);
+                    ay[v][b] = cmake<C>(ay[v][b].x + sn * hy.x, ay[v][b].y + sn * hy.y);
                 }
-                if (d2 != 0) {
-                    // half-cell phase exp(i pi d2 (kx / Px + ky / Py))
-                    C ph = cmul(phk, pyk[u]);
-                    if (d2 < 0) ph.y = -ph.y;
-                    hx = cmul(hx, ph);
-                    hy = cmul(hy, ph);
-                }
-                ax[u] = cadd(ax[u], hx);
-                ay[u] = cadd(ay[u], hy);
             }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            bx[spad<C>(k0 + u * THREADS)] = ax[u];
-            by[spad<C>(k0 + u * THREADS)] = ay[u];
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                bx[spad<C>(ky[v][b])] = ax[v][b];
+                by[spad<C>(ky[v][b])] = ay[v][b];
+            }
         }
     }
     __syncthreads();
     for (int o = 0; o < 2; ++o) {
         C *buf = o == 0 ? bx : by;
         fft_batch<C, PY, 1, THREADS, true, false, true>(buf, tw);
-        C *dst = out + ((int64_t)o * a.qx + kx) * a.ny;
-        for (int j = threadIdx.x; j < a.ny; j += THREADS) dst[j] = buf[spad<C>(a.j0 + (j << a.t))];
+        const int ny = a.ny[l], j0 = a.j0[l], t = a.t[l];
+        C *dst = out + a.inv_off[l] + ((int64_t)o * a.qx + kx) * ny;
+        for (int j = threadIdx.x; j < ny; j += THREADS) dst[j] = buf[spad<C>(j0 + (j << t))];
     }
 }
 
@@ -419,14 +514,14 @@ sg_status launch_row_fwd(const lv_rows_src<T> &a, cplx_t<T> *out, const cplx_t<T
 }
 
 template <typename T, int PY>
-sg_status launch_col_fwd(const cplx_t<T> *in, cplx_t<T> *spec, int ny, int j0, int s, int qx, const cplx_t<T> *tw,
-                         cudaStream_t st)
+sg_status launch_col_fwd(const cplx_t<T> *in, cplx_t<T> *spec, const lv_col_src &a, const cplx_t<T> *tw,
+                         const cplx_t<T> *cphx, const cplx_t<T> *cphy, cudaStream_t st)
 {
     constexpr int TH = lv_col_threads(PY);
     const size_t sm = spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
     auto kern = k_lv_col_fwd<T, PY, TH>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<dim3(qx, 3), TH, sm, st>>>(in, spec, ny, j0, s, qx, tw);
+    kern<<<dim3(a.qx, 3), TH, sm, st>>>(in, spec, a, tw, cphx, cphy);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -439,7 +534,7 @@ sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const 
     const size_t sm = 2 * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
     auto kern = k_lv_col_mac_inv<T, PY, TH>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<a.qx, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
+    kern<<<a.qx * a.nsrc, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -477,8 +572,9 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
     const sg_lv &lv = *plan->lv;
     const int qx = lv.px / 2 + 1;
     const int64_t *twoff = sizeof(T) == 8 ? plan->tw64_off : plan->tw32_off;
-    const C *twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(lv.px)]);
-    const C *twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(lv.py)]);
+    auto twid = [&](int L) { return (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(L)]); };
+    const C *twx = twid(lv.px), *twy = twid(lv.py);
+    const C *cphx = (const C *)lv.cphase, *cphy = cphx + lv.px + 1;
     C *wf = (C *)ws->work_fwd;
     C *wi = (C *)ws->work_inv;
     C *spec = wf + lv.fwd_elems;
@@ -486,34 +582,44 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
     for (int m = 0; m < lv.nlev; ++m) {
         const sg_lv_level &L = lv.lev[m];
-        lv_rows_src<T> a = {S, plan->ncells, L.map, L.nx, L.ny, L.i0, L.s};
-        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_fwd<T, PP>(a, wf + L.fwd_off, twx, st))));
+        lv_rows_src<T> a = {S, plan->ncells, L.map, L.nx, L.ny, L.i0 >> L.cx, L.s - L.cx};
+        const int pcx = lv.px >> L.cx;
+        SG_LV_SWITCH(pcx, SG_TRY((launch_row_fwd<T, PP>(a, wf + L.fwd_off, twid(pcx), st))));
     }
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
     for (int m = 0; m < lv.nlev; ++m) {
         const sg_lv_level &L = lv.lev[m];
-        SG_LV_SWITCH(lv.py, SG_TRY((launch_col_fwd<T, PP>(wf + L.fwd_off, spec + L.spec_off, L.ny, L.j0, L.s, qx, twy, st))));
+        const int pcx = lv.px >> L.cx, pcy = lv.py >> L.cy;
+        const lv_col_src a = {L.ny, L.j0 >> L.cy, L.s - L.cy, pcx / 2 + 1, L.cx, L.cy,
+                              L.cx == L.s && L.s >= 1, L.cy == L.s && L.s >= 1};
+        SG_LV_SWITCH(pcy, SG_TRY((launch_col_fwd<T, PP>(wf + L.fwd_off, spec + L.spec_off, a, twid(pcy), cphx, cphy,
+                                                         st))));
     }
-    for (int l = 0; l < lv.nlev; ++l) {
-        const sg_lv_level &L = lv.lev[l];
+    {
+        // one launch for all target levels
         lv_mac_args a;
         memset(&a, 0, sizeof(a));
         a.nsrc = lv.nlev;
         for (int m = 0; m < lv.nlev; ++m) {
-            a.spec_off[m] = lv.lev[m].spec_off;
-            a.key[m] = lv.key[m][l];
-            a.d2[m] = lv.key_d2[lv.key[m][l]];
+            const sg_lv_level &M = lv.lev[m];
+            a.spec_off[m] = M.spec_off;
+            a.lpx[m] = sg_ilog2(lv.px >> M.cx);
+            a.lpy[m] = sg_ilog2(lv.py >> M.cy);
+            a.hx[m] = M.cx == M.s && M.s >= 1;
+            a.hy[m] = M.cy == M.s && M.s >= 1;
+            for (int l = 0; l < lv.nlev; ++l) {
+                a.key[m][l] = lv.key[m][l];
+                a.d2[m][l] = lv.key_d2[lv.key[m][l]];
+            }
+            a.ny[m] = M.ny;
+            a.j0[m] = M.j0;
+            a.t[m] = M.s;
+            a.inv_off[m] = M.inv_off;
         }
-        a.ny = L.ny;
-        a.j0 = L.j0;
-        a.t = L.s;
         a.qx = qx;
-        a.sc0 = plan->geom.G;
-        a.sc1 = plan->geom.G * lv.hf;
         const C *phx = (const C *)lv.phase, *phy = phx + lv.px + 1;
-        SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP>(a, spec, (const T *)lv.spectra, phx, phy, wi + L.inv_off,
-                                                               twy, st))));
+        SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP>(a, spec, (const T *)lv.spectra, phx, phy, wi, twy, st))));
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
@@ -534,6 +640,7 @@ void sg_lv_free(sg_plan *plan)
     for (int m = 0; m < plan->lv->nlev; ++m) cudaFree(plan->lv->lev[m].map);
     cudaFree(plan->lv->spectra);
     cudaFree(plan->lv->phase);
+    cudaFree(plan->lv->cphase);
     delete plan->lv;
     plan->lv = nullptr;
 }
@@ -558,11 +665,21 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
         L.ny = a->ny[m];
         L.i0 = a->i0[m];
         L.j0 = a->j0[m];
+        L.cx = sg_lv_cexp(L.s, a->px);
+        L.cy = sg_lv_cexp(L.s, a->py);
         L.fwd_off = fwd;
         L.spec_off = spec;
         L.inv_off = inv;
-        fwd += 3LL * qx * L.ny;
-        spec += 3LL * qx * a->py;
+        // every compact sample position lies in the first half of its transform
+        // (the level's image is inside the finest extent, at most P/2 wide)
+        if ((L.i0 >> L.cx) + ((int64_t)(L.nx - 1) << (L.s - L.cx)) >= (a->px >> L.cx) / 2 ||
+            (L.j0 >> L.cy) + ((int64_t)(L.ny - 1) << (L.s - L.cy)) >= (a->py >> L.cy) / 2) {
+            sg_set_last_error_message("level convolutions: a level image lies outside the padded lattice");
+            return SG_EINVAL;
+        }
+        const int64_t qxc = (a->px >> L.cx) / 2 + 1;
+        fwd += 3LL * qxc * L.ny;
+        spec += 3LL * qxc * (a->py >> L.cy);
         inv += 2LL * qx * L.ny;
         SG_TRY(sg_plan_upload(plan, (void **)&L.map, a->map[m], (size_t)L.nx * L.ny * sizeof(int)));
     }
@@ -588,14 +705,20 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
     const int64_t qplane = (int64_t)qx * (a->py / 2 + 1);
     cudaError_t e = cudaMalloc(&lv->spectra, (size_t)lv->nkeys * 6 * qplane * rs);
     if (e == cudaSuccess) e = cudaMalloc(&lv->phase, (size_t)(a->px + a->py + 2) * cs);
+    if (e == cudaSuccess) e = cudaMalloc(&lv->cphase, (size_t)(a->px + a->py + 2) * cs);
     if (e != cudaSuccess) {
         cudaGetLastError();
         sg_set_last_cuda_error(e, "cudaMalloc");
         return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
     }
-    plan->device_bytes += (int64_t)lv->nkeys * 6 * qplane * (int64_t)rs + (int64_t)(a->px + a->py + 2) * (int64_t)cs;
-    if (plan->prec == SG_FP64) k_lv_phase<double><<<16, 256>>>((double2 *)lv->phase, a->px, a->py);
-    else k_lv_phase<float><<<16, 256>>>((float2 *)lv->phase, a->px, a->py);
+    plan->device_bytes += (int64_t)lv->nkeys * 6 * qplane * (int64_t)rs + 2 * (int64_t)(a->px + a->py + 2) * (int64_t)cs;
+    if (plan->prec == SG_FP64) {
+        k_lv_phase<double><<<16, 256>>>((double2 *)lv->phase, a->px, a->py);
+        k_lv_cphase<double><<<16, 256>>>((double2 *)lv->cphase, a->px, a->py);
+    } else {
+        k_lv_phase<float><<<16, 256>>>((float2 *)lv->phase, a->px, a->py);
+        k_lv_cphase<float><<<16, 256>>>((float2 *)lv->cphase, a->px, a->py);
+    }
     // tables: FP64 wrapped, FP64 2-D transforms, unpacked and cast
     const int64_t plane = (int64_t)a->px * a->py;
     double2 *z = nullptr;
@@ -618,8 +741,10 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
         }
         if (st != SG_OK) break;
         char *dst = (char *)lv->spectra + (size_t)k * 6 * qplane * rs;
-        if (plan->prec == SG_FP64) k_lv_extract<double><<<2048, 256>>>(z, (double *)dst, a->px, a->py, lv->key_d2[k]);
-        else k_lv_extract<float><<<2048, 256>>>(z, (float *)dst, a->px, a->py, lv->key_d2[k]);
+        const double G = plan->geom.G, Gh = plan->geom.G * a->hf;
+        if (plan->prec == SG_FP64)
+            k_lv_extract<double><<<2048, 256>>>(z, (double *)dst, a->px, a->py, lv->key_d2[k], G, Gh);
+        else k_lv_extract<float><<<2048, 256>>>(z, (float *)dst, a->px, a->py, lv->key_d2[k], G, Gh);
         if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
     }
     e = cudaDeviceSynchronize();
