@@ -647,8 +647,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
     {
         const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0;
-        // level convolutions: row, column and inverse-row launches per level, one column-MAC launch
-        int n = use_lv ? 3 * (gi.lmax + 1) + 1 : gi.n * (central ? 4 : 3);
+        // level convolutions: one launch each for the row, column, column-MAC and inverse-row passes
+        int n = use_lv ? 4 : gi.n * (central ? 4 : 3);
         if (plan->composite) {
             for (int k = 0; k < gi.n; ++k) n += 1 + (gi.parent[k] >= 0);
             if (plan->ntiles > 0) n += 2 + (nsplit > 1);

@@ -213,20 +213,36 @@ __device__ __forceinline__ T lv_sample(const lv_rows_src<T> &a, int f, int j, in
     return c < 0 ? (T)0 : a.S[f * a.plane + c];
 }
 
-// Row transforms (length PX = the level's compact Pcx) of its sampled rows
-// (three fields, blockIdx.y), two real rows per complex sequence;
+// Launch shapes of the transform passes: the row passes run NB = 4096 / PX
+// sequences (two rows each) of length PX per CTA of 512 threads; the forward
+// column pass NB = 4096 / PY columns per CTA of 512 threads (one radix-8
+// butterfly per thread and stage up to 4096 points).
+__host__ __device__ constexpr int lv_nb(int px) { return px >= 4096 ? 1 : 4096 / px; }
+__host__ __device__ constexpr int lv_cnb(int py) { return py >= 4096 ? 1 : 4096 / py; }
+constexpr int LV_ROW_THREADS = 512, LV_CFWD_THREADS = 512;
+
+// All levels in one launch: blockIdx.x runs over the levels' CTA ranges
+// [cta0[m], cta0[m+1]); each level dispatches to the transform of its length.
+__device__ __forceinline__ int lv_level_of(const int *cta0, int nlev)
+{
+    int m = 0;
+    while (m + 1 < nlev && (int)blockIdx.x >= cta0[m + 1]) ++m;
+    return m;
+}
+
+// Row transforms (length PX = the level's compact Pcx) of a level's sampled
+// rows (three fields, blockIdx.y), two real rows per complex sequence;
 // out[(f qx + kx) ny + j], qx = PX/2 + 1.
-template <typename T, int PX, int NB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_lv_row_fwd(lv_rows_src<T> a, cplx_t<T> *__restrict__ out,
-                                                        const cplx_t<T> *__restrict__ tw)
+template <typename T, int PX>
+__device__ __forceinline__ void lv_row_fwd_body(const lv_rows_src<T> &a, cplx_t<T> *__restrict__ out,
+                                                const cplx_t<T> *__restrict__ tw, int blk, cplx_t<T> *buf)
 {
     using C = cplx_t<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int NB = lv_nb(PX), THREADS = LV_ROW_THREADS;
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
     const int f = blockIdx.y;
-    const int j0 = blockIdx.x * RB;
+    const int j0 = blk * RB;
     for (int e = threadIdx.x; e < NB * (PX / 2); e += THREADS) {
         const int q = e / (PX / 2), I = e % (PX / 2);
         const int ja = j0 + 2 * q;
@@ -249,6 +265,40 @@ __global__ void __launch_bounds__(THREADS) k_lv_row_fwd(lv_rows_src<T> a, cplx_t
     }
 }
 
+template <typename T>
+struct lv_row_fwd_args {
+    int nlev;
+    int cta0[SG_MAX_LEVELS + 1];
+    lv_rows_src<T> a[SG_MAX_LEVELS];
+    cplx_t<T> *out[SG_MAX_LEVELS];
+    const cplx_t<T> *tw[SG_MAX_LEVELS];
+    int lp[SG_MAX_LEVELS];  // log2 of the level's compact row length
+};
+
+#define SG_LV_BODY_SWITCH(LP, LMAX, BODY)                                                 \
+    switch (LP) {                                                                      \
+    case 6: { constexpr int PP = 64; BODY; break; }                                    \
+    case 7: { constexpr int PP = 128; BODY; break; }                                   \
+    case 8: { constexpr int PP = 256; BODY; break; }                                   \
+    case 9: { constexpr int PP = 512; BODY; break; }                                   \
+    case 10: { constexpr int PP = 1024; BODY; break; }                                 \
+    case 11: { constexpr int PP = 2048; BODY; break; }                                 \
+    case 12: { constexpr int PP = 4096; BODY; break; }                                 \
+    case 13: if constexpr (LMAX >= 8192) { constexpr int PP = 8192; BODY; } break;     \
+    default: break;                                                                    \
+    }
+
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_fwd(lv_row_fwd_args<T> A)
+{
+    using C = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = reinterpret_cast<C *>(smem_raw);
+    const int m = lv_level_of(A.cta0, A.nlev);
+    const int blk = blockIdx.x - A.cta0[m];
+    SG_LV_BODY_SWITCH(A.lp[m], LMAX, (lv_row_fwd_body<T, PP>(A.a[m], A.out[m], A.tw[m], blk, buf)));
+}
+
 struct lv_col_src {
     int ny, p0, st;     // image row j sits at compact position p0 + j 2^st
     int qx;             // compact half-spectrum width Pcx/2 + 1
@@ -257,31 +307,58 @@ struct lv_col_src {
 };
 
 // Column transforms (length PY = the level's compact Pcy) to compact spectra
-// times the half-shift factors psi_x(kx) psi_y(ky); spec[(f qx + kx) PY + ky].
-template <typename T, int PY, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_lv_col_fwd(const cplx_t<T> *__restrict__ in, cplx_t<T> *__restrict__ spec,
-                                                        lv_col_src a, const cplx_t<T> *__restrict__ tw,
-                                                        const cplx_t<T> *__restrict__ cphx,
-                                                        const cplx_t<T> *__restrict__ cphy)
+// times the half-shift factors psi_x(kx) psi_y(ky), NB = lv_cnb(PY) columns
+// per CTA; spec[(f qx + kx) PY + ky].
+template <typename T, int PY>
+__device__ __forceinline__ void lv_col_fwd_body(const cplx_t<T> *__restrict__ in, cplx_t<T> *__restrict__ spec,
+                                                const lv_col_src &a, const cplx_t<T> *__restrict__ tw,
+                                                const cplx_t<T> *__restrict__ cphx, const cplx_t<T> *__restrict__ cphy,
+                                                int blk, cplx_t<T> *buf)
+{
+    using C = cplx_t<T>;
+    constexpr int NB = lv_cnb(PY), THREADS = LV_CFWD_THREADS;
+    const int f = blockIdx.y, kx0 = blk * NB;
+    for (int e = threadIdx.x; e < NB * (PY / 2); e += THREADS)
+        buf[spad<C>((e / (PY / 2)) * PY + e % (PY / 2))] = cmake<C>((T)0, (T)0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * a.ny; e += THREADS) {
+        const int q = e / a.ny, j = e % a.ny, kx = kx0 + q;
+        if (kx < a.qx) buf[spad<C>(q * PY + a.p0 + (j << a.st))] = in[((int64_t)f * a.qx + kx) * a.ny + j];
+    }
+    __syncthreads();
+    fft_batch<C, PY, NB, THREADS, false, true>(buf, tw);
+    for (int e = threadIdx.x; e < NB * PY; e += THREADS) {
+        const int q = e / PY, k = e % PY, kx = kx0 + q;
+        if (kx >= a.qx) continue;
+        C v = buf[spad<C>(e)];
+        if (a.hy) v = cmul(v, cphy[k << a.cy]);
+        if (a.hx) v = cmul(v, cphx[kx << a.cx]);
+        spec[((int64_t)f * a.qx + kx) * PY + k] = v;
+    }
+}
+
+template <typename T>
+struct lv_col_fwd_args {
+    int nlev;
+    int cta0[SG_MAX_LEVELS + 1];
+    lv_col_src a[SG_MAX_LEVELS];
+    const cplx_t<T> *in[SG_MAX_LEVELS];
+    cplx_t<T> *spec[SG_MAX_LEVELS];
+    const cplx_t<T> *tw[SG_MAX_LEVELS];
+    int lp[SG_MAX_LEVELS];  // log2 of the level's compact column length
+    const cplx_t<T> *cphx, *cphy;
+};
+
+template <typename T, int LMAX>
+__global__ void __launch_bounds__(LV_CFWD_THREADS) k_lv_col_fwd(lv_col_fwd_args<T> A)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
-    const int kx = blockIdx.x, f = blockIdx.y;
-    for (int e = threadIdx.x; e < PY / 2; e += THREADS) buf[spad<C>(e)] = cmake<C>((T)0, (T)0);
-    __syncthreads();
-    const C *col = in + ((int64_t)f * a.qx + kx) * a.ny;
-    for (int j = threadIdx.x; j < a.ny; j += THREADS) buf[spad<C>(a.p0 + (j << a.st))] = col[j];
-    __syncthreads();
-    fft_batch<C, PY, 1, THREADS, false, true>(buf, tw);
-    C *o = spec + ((int64_t)f * a.qx + kx) * PY;
-    const C psx = a.hx ? cphx[kx << a.cx] : cmake<C>((T)1, (T)0);
-    for (int k = threadIdx.x; k < PY; k += THREADS) {
-        C v = buf[spad<C>(k)];
-        if (a.hy) v = cmul(v, cphy[k << a.cy]);
-        if (a.hx) v = cmul(v, psx);
-        o[k] = v;
-    }
+    const int m = lv_level_of(A.cta0, A.nlev);
+    const int blk = blockIdx.x - A.cta0[m];
+    SG_LV_BODY_SWITCH(A.lp[m], LMAX,
+                      (lv_col_fwd_body<T, PP>(A.in[m], A.spec[m], A.a[m], A.tw[m], A.cphx, A.cphy, blk, buf)));
 }
 
 struct lv_mac_args {
@@ -308,8 +385,8 @@ struct lv_mac_args {
 // formed element by element straight into two shared buffers; inverse column
 // transforms; the target level's sampled rows to out[(o qx + kx) ny + j]
 // (out at the level's inverse-column offset).
-template <typename T, int PY, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
+template <typename T, int PY, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
                                                             const T *__restrict__ kspec,
                                                             const cplx_t<T> *__restrict__ phx,
                                                             const cplx_t<T> *__restrict__ phy,
@@ -441,22 +518,33 @@ struct lv_out_dst {
     int nx, ny, i0, t;
 };
 
-// Inverse row transforms of a target level's rows (blockIdx.y = Fx, Fy); the
-// samples at columns i0 + i 2^t go to the level's cells through the map.
-template <typename T, int PX, int NB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_lv_row_inv(const cplx_t<T> *__restrict__ in, lv_out_dst a,
-                                                        T *__restrict__ fx, T *__restrict__ fy,
-                                                        const cplx_t<T> *__restrict__ tw)
+template <typename T>
+struct lv_row_inv_args {
+    int nlev;
+    int cta0[SG_MAX_LEVELS + 1];
+    lv_out_dst a[SG_MAX_LEVELS];
+    const cplx_t<T> *in[SG_MAX_LEVELS];
+};
+
+// Inverse row transforms of every target level's rows (blockIdx.y = Fx, Fy),
+// all levels in one launch; the samples at columns i0 + i 2^t go to the
+// level's cells through the map.
+template <typename T, int PX>
+__global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_inv(lv_row_inv_args<T> A, T *__restrict__ fx,
+                                                              T *__restrict__ fy, const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
+    constexpr int NB = lv_nb(PX), THREADS = LV_ROW_THREADS;
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
+    const int lvl = lv_level_of(A.cta0, A.nlev);
+    const lv_out_dst &a = A.a[lvl];
     const int o = blockIdx.y;
-    const int j0 = blockIdx.x * RB;
+    const int j0 = (blockIdx.x - A.cta0[lvl]) * RB;
     const int ny = a.ny;
-    const C *w = in + (int64_t)o * QX * ny;
+    const C *w = A.in[lvl] + (int64_t)o * QX * ny;
     T *out = o == 0 ? fx : fy;
     for (int e = threadIdx.x; e < NB * QX; e += THREADS) {
         const int q = e % NB, k = e / NB;
@@ -489,9 +577,17 @@ __global__ void __launch_bounds__(THREADS) k_lv_row_inv(const cplx_t<T> *__restr
 
 // ----------------------------------------------------------- launchers --
 
-constexpr int lv_nb(int px) { return px >= 4096 ? 1 : 4096 / px; }
-constexpr int lv_row_threads(int px) { return lv_nb(px) * px / 8 > 512 ? 512 : lv_nb(px) * px / 8; }
 constexpr int lv_col_threads(int py) { return py / 8 < 64 ? 64 : (py / 8 > 512 ? 512 : py / 8); }
+// Column-MAC CTAs: the two shared spectra of a column grow to 2 x 4096 x 8 bytes
+// (FP32) or more, which leaves one or two CTAs per SM; those CTAs get more
+// threads (at most 64 registers each) so that more loads are in flight.
+template <typename T>
+constexpr int lv_mac_threads(int py)
+{
+    return (sizeof(T) == 8 ? py >= 4096 : py >= 8192) ? 1024 : lv_col_threads(py);
+}
+template <typename T>
+constexpr int lv_mac_minb(int py) { return sizeof(T) == 4 && py == 4096 ? 2 : (lv_mac_threads<T>(py) >= 1024 ? 1 : 0); }
 
 template <typename K>
 sg_status smem_attr(K kern, size_t bytes)
@@ -500,28 +596,24 @@ sg_status smem_attr(K kern, size_t bytes)
     return SG_OK;
 }
 
-template <typename T, int PX>
-sg_status launch_row_fwd(const lv_rows_src<T> &a, cplx_t<T> *out, const cplx_t<T> *tw, cudaStream_t st)
+template <typename T>
+sg_status launch_row_fwd(const lv_row_fwd_args<T> &A, int ncta, int lmax, cudaStream_t st)
 {
-    constexpr int NB = lv_nb(PX), TH = lv_row_threads(PX);
-    const size_t sm = spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
-    auto kern = k_lv_row_fwd<T, PX, NB, TH>;
+    const size_t sm = spad_size<cplx_t<T>>(lv_nb(lmax) * lmax) * sizeof(cplx_t<T>);
+    auto kern = lmax > 4096 ? k_lv_row_fwd<T, 8192> : k_lv_row_fwd<T, 4096>;
     SG_TRY(smem_attr(kern, sm));
-    dim3 grid((a.ny + 2 * NB - 1) / (2 * NB), 3);
-    kern<<<grid, TH, sm, st>>>(a, out, tw);
+    kern<<<dim3(ncta, 3), LV_ROW_THREADS, sm, st>>>(A);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
-template <typename T, int PY>
-sg_status launch_col_fwd(const cplx_t<T> *in, cplx_t<T> *spec, const lv_col_src &a, const cplx_t<T> *tw,
-                         const cplx_t<T> *cphx, const cplx_t<T> *cphy, cudaStream_t st)
+template <typename T>
+sg_status launch_col_fwd(const lv_col_fwd_args<T> &A, int ncta, int lmax, cudaStream_t st)
 {
-    constexpr int TH = lv_col_threads(PY);
-    const size_t sm = spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
-    auto kern = k_lv_col_fwd<T, PY, TH>;
+    const size_t sm = spad_size<cplx_t<T>>(lv_cnb(lmax) * lmax) * sizeof(cplx_t<T>);
+    auto kern = lmax > 4096 ? k_lv_col_fwd<T, 8192> : k_lv_col_fwd<T, 4096>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<dim3(a.qx, 3), TH, sm, st>>>(in, spec, a, tw, cphx, cphy);
+    kern<<<dim3(ncta, 3), LV_CFWD_THREADS, sm, st>>>(A);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -530,9 +622,9 @@ template <typename T, int PY>
 sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const T *kspec, const cplx_t<T> *phx,
                              const cplx_t<T> *phy, cplx_t<T> *out, const cplx_t<T> *tw, cudaStream_t st)
 {
-    constexpr int TH = lv_col_threads(PY);
+    constexpr int TH = lv_mac_threads<T>(PY);
     const size_t sm = 2 * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
-    auto kern = k_lv_col_mac_inv<T, PY, TH>;
+    auto kern = k_lv_col_mac_inv<T, PY, TH, lv_mac_minb<T>(PY)>;
     SG_TRY(smem_attr(kern, sm));
     kern<<<a.qx * a.nsrc, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
     SG_CUDA_TRY(cudaGetLastError());
@@ -540,14 +632,12 @@ sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const 
 }
 
 template <typename T, int PX>
-sg_status launch_row_inv(const cplx_t<T> *in, const lv_out_dst &a, T *fx, T *fy, const cplx_t<T> *tw, cudaStream_t st)
+sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, T *fx, T *fy, const cplx_t<T> *tw, cudaStream_t st)
 {
-    constexpr int NB = lv_nb(PX), TH = lv_row_threads(PX);
-    const size_t sm = spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
-    auto kern = k_lv_row_inv<T, PX, NB, TH>;
+    const size_t sm = spad_size<cplx_t<T>>(lv_nb(PX) * PX) * sizeof(cplx_t<T>);
+    auto kern = k_lv_row_inv<T, PX>;
     SG_TRY(smem_attr(kern, sm));
-    dim3 grid((a.ny + 2 * NB - 1) / (2 * NB), 2);
-    kern<<<grid, TH, sm, st>>>(in, a, fx, fy, tw);
+    kern<<<dim3(ncta, 2), LV_ROW_THREADS, sm, st>>>(A, fx, fy, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -578,23 +668,50 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
     C *wf = (C *)ws->work_fwd;
     C *wi = (C *)ws->work_inv;
     C *spec = wf + lv.fwd_elems;
-    const T *S = (const T *)ws->sfield;
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
-    for (int m = 0; m < lv.nlev; ++m) {
-        const sg_lv_level &L = lv.lev[m];
-        lv_rows_src<T> a = {S, plan->ncells, L.map, L.nx, L.ny, L.i0 >> L.cx, L.s - L.cx};
-        const int pcx = lv.px >> L.cx;
-        SG_LV_SWITCH(pcx, SG_TRY((launch_row_fwd<T, PP>(a, wf + L.fwd_off, twid(pcx), st))));
+    {
+        // row transforms of every level's sampled rows, at the level's compact length
+        lv_row_fwd_args<T> A;
+        memset(&A, 0, sizeof(A));
+        A.nlev = lv.nlev;
+        int ncta = 0;
+        for (int m = 0; m < lv.nlev; ++m) {
+            const sg_lv_level &L = lv.lev[m];
+            const int pcx = lv.px >> L.cx;
+            A.cta0[m] = ncta;
+            A.a[m] = {(const T *)ws->sfield, plan->ncells, L.map, L.nx, L.ny, L.i0 >> L.cx, L.s - L.cx};
+            A.out[m] = wf + L.fwd_off;
+            A.tw[m] = twid(pcx);
+            A.lp[m] = sg_ilog2(pcx);
+            ncta += (L.ny + 2 * lv_nb(pcx) - 1) / (2 * lv_nb(pcx));
+        }
+        A.cta0[lv.nlev] = ncta;
+        SG_TRY(launch_row_fwd<T>(A, ncta, lv.px, st));
     }
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
-    for (int m = 0; m < lv.nlev; ++m) {
-        const sg_lv_level &L = lv.lev[m];
-        const int pcx = lv.px >> L.cx, pcy = lv.py >> L.cy;
-        const lv_col_src a = {L.ny, L.j0 >> L.cy, L.s - L.cy, pcx / 2 + 1, L.cx, L.cy,
-                              L.cx == L.s && L.s >= 1, L.cy == L.s && L.s >= 1};
-        SG_LV_SWITCH(pcy, SG_TRY((launch_col_fwd<T, PP>(wf + L.fwd_off, spec + L.spec_off, a, twid(pcy), cphx, cphy,
-                                                         st))));
+    {
+        // column transforms to compact source spectra
+        lv_col_fwd_args<T> A;
+        memset(&A, 0, sizeof(A));
+        A.nlev = lv.nlev;
+        A.cphx = cphx;
+        A.cphy = cphy;
+        int ncta = 0;
+        for (int m = 0; m < lv.nlev; ++m) {
+            const sg_lv_level &L = lv.lev[m];
+            const int pcx = lv.px >> L.cx, pcy = lv.py >> L.cy;
+            A.cta0[m] = ncta;
+            A.a[m] = {L.ny, L.j0 >> L.cy, L.s - L.cy, pcx / 2 + 1, L.cx, L.cy,
+                      L.cx == L.s && L.s >= 1, L.cy == L.s && L.s >= 1};
+            A.in[m] = wf + L.fwd_off;
+            A.spec[m] = spec + L.spec_off;
+            A.tw[m] = twid(pcy);
+            A.lp[m] = sg_ilog2(pcy);
+            ncta += (pcx / 2 + 1 + lv_cnb(pcy) - 1) / lv_cnb(pcy);
+        }
+        A.cta0[lv.nlev] = ncta;
+        SG_TRY(launch_col_fwd<T>(A, ncta, lv.py, st));
     }
     {
         // one launch for all target levels
@@ -623,10 +740,20 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
-    for (int l = 0; l < lv.nlev; ++l) {
-        const sg_lv_level &L = lv.lev[l];
-        lv_out_dst a = {L.map, L.nx, L.ny, L.i0, L.s};
-        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_inv<T, PP>(wi + L.inv_off, a, (T *)fx, (T *)fy, twx, st))));
+    {
+        lv_row_inv_args<T> A;
+        memset(&A, 0, sizeof(A));
+        A.nlev = lv.nlev;
+        int ncta = 0;
+        for (int l = 0; l < lv.nlev; ++l) {
+            const sg_lv_level &L = lv.lev[l];
+            A.cta0[l] = ncta;
+            A.a[l] = {L.map, L.nx, L.ny, L.i0, L.s};
+            A.in[l] = wi + L.inv_off;
+            ncta += (L.ny + 2 * lv_nb(lv.px) - 1) / (2 * lv_nb(lv.px));
+        }
+        A.cta0[lv.nlev] = ncta;
+        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_inv<T, PP>(A, ncta, (T *)fx, (T *)fy, twx, st))));
     }
     sg_timing_end(ws, SG_STAGE_ROW_INV, st);
     return SG_OK;
