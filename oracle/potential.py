@@ -17,7 +17,9 @@ difference over the cell corners. Every term carries a factor that vanishes
 where its logarithm is singular (u ln(v + r) at u = 0, u^2 ln(v + r) at u = 0),
 so the integrals are finite everywhere, the target's own cell included; those
 terms are 0 there (their limits). ln(v + r) for v < 0 uses 2 ln|u| - ln(r - v).
-The force is minus the gradient of this potential.
+The force is minus the gradient of this potential. On an AMR hierarchy the
+sum runs over every leaf cell (Eq. eqnXforce2 with K = 1/r), evaluated at leaf
+centres.
 """
 import numpy as np
 
@@ -134,3 +136,18 @@ def uniform_fft_potential(sigma, dx, dy, h, G=1.0):
     if dy is not None:
         acc = acc + spec(dy) * wrap(tab["py"])
     return -G * np.fft.irfft2(acc, s=(py, px))[:ny, :nx]
+
+
+def amr_direct_potential(patches, sigma, dx=None, dy=None, G=1.0, target_index=None, nthreads=0):
+    """Potential at leaf centres of an AMR hierarchy (oracle.amr patches) from
+    all leaf cells, by the plain C sum. sigma, dx, dy: per-patch [ny, nx] arrays
+    (covered cells ignored). Returns (leaves, phi) as amr.amr_direct_force does."""
+    from .amr import _gather, leaf_cells
+    leaves = leaf_cells(patches)
+    s0 = _gather(sigma, leaves)
+    sx = _gather(dx, leaves)
+    sy = _gather(dy, leaves)
+    tsel = np.arange(leaves["xc"].size) if target_index is None else np.asarray(target_index)
+    phi = direct_potential((leaves["xl"], leaves["xr"], leaves["yd"], leaves["yu"]), s0, sx, sy,
+                           leaves["xc"][tsel], leaves["yc"][tsel], G=G, nthreads=nthreads)
+    return leaves, phi

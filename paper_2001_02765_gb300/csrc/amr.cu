@@ -25,72 +25,207 @@
 // the data's slopes even for rough data, where a least-squares slope grows like
 // (jump in sigma) / H and the large slope terms of consecutive levels, which
 // cancel in the sum, would cost digits in the corner-form sum.
+//
+// Launches: one per refined level below the finest (finest first) for the
+// filled values of its covered cells, then one for every S_l: a refined level's
+// defect needs only its own 2x2 sibling blocks (the parent's filled value is
+// their restriction), so all levels are finalised together.
 #include "common.cuh"
 
 namespace {
 
-// Fill the cells of patch p: leaves copy the input, covered cells restrict
-// their children's filled values (already written: patches run finest first),
-// cells that do not exist get zero.
+// Filled value of a cell that is the child of a covered cell, or of a cell being
+// finalised: its input on a leaf, zero where it does not exist, and the filled
+// value computed by an earlier launch (planes F) where it is covered itself.
+// Arithmetic here runs in the plan precision T (FP64 throughput is a small
+// fraction of FP32 on this GPU, and every value is stored in T anyway).
 template <typename T>
-__global__ void k_fill(sg_patch_dev p, const int *__restrict__ code, const sg_patch_dev *__restrict__ pd,
-                       const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
-                       T *__restrict__ s)
+__device__ __forceinline__ void cell_value(const int *__restrict__ code, const T *__restrict__ sigma,
+                                           const T *__restrict__ dx, const T *__restrict__ dy,
+                                           const T *__restrict__ F, int64_t P, int64_t o, T v[3])
 {
-    const bool slopes = dx != nullptr;
-    const int64_t n = (int64_t)p.nx * p.ny;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % p.nx), j = (int)(e / p.nx);
-        const int64_t o = p.cell_off + e;
-        const int c = code[o];
-        double s0 = 0.0, sx = 0.0, sy = 0.0;
-        if (c == SG_CELL_LEAF) {
-            s0 = (double)sigma[o];
-            sx = dx ? (double)dx[o] : 0.0;
-            sy = dy ? (double)dy[o] : 0.0;
-        } else if (c >= 0) {
-            const sg_patch_dev q = pd[c];
-            const int ci = 2 * (i - q.pi0), cj = 2 * (j - q.pj0);
-            double sum = 0, right = 0, top = 0, gx = 0, gy = 0;
-            for (int b = 0; b < 2; ++b) {
-                for (int a = 0; a < 2; ++a) {
-                    const int64_t oc = q.cell_off + (int64_t)(cj + b) * q.nx + (ci + a);
-                    const double v = (double)s[oc];
-                    sum += v;
-                    right += a ? v : -v;
-                    top += b ? v : -v;
-                    gx += (double)s[oc + q.ncells_plane];
-                    gy += (double)s[oc + 2 * q.ncells_plane];
-                }
-            }
-            s0 = 0.25 * sum;
-            sx = slopes ? 0.25 * gx : 0.75 / p.h * right;
-            sy = slopes ? 0.25 * gy : 0.75 / p.h * top;
-        }
-        s[o] = (T)s0;
-        s[o + p.ncells_plane] = (T)sx;
-        s[o + 2 * p.ncells_plane] = (T)sy;
+    const int c = code[o];
+    if (c == SG_CELL_LEAF) {
+        v[0] = sigma[o];
+        v[1] = dx ? dx[o] : (T)0;
+        v[2] = dy ? dy[o] : (T)0;
+    } else if (c == SG_CELL_ABSENT) {
+        v[0] = v[1] = v[2] = (T)0;
+    } else {
+        v[0] = F[o];
+        v[1] = F[o + P];
+        v[2] = F[o + 2 * P];
     }
 }
 
-// Replace the filled values of patch q (level >= 1) by q - P(parent), in place.
+// Restriction of the four cells (ci..ci+1, cj..cj+1) of patch q to their parent
+// of width hp.
 template <typename T>
-__global__ void k_defect(sg_patch_dev q, sg_patch_dev p, const int *__restrict__ code, T *__restrict__ s)
+__device__ __forceinline__ void restrict4(const int *__restrict__ code, const T *__restrict__ sigma,
+                                          const T *__restrict__ dx, const T *__restrict__ dy,
+                                          const T *__restrict__ F, const sg_patch_dev &q, int ci, int cj, double hp,
+                                          T v[4][3], T out[3])
 {
-    const int64_t n = (int64_t)q.nx * q.ny;
-    const int64_t P = q.ncells_plane;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % q.nx), j = (int)(e / q.nx);
-        const int64_t o = q.cell_off + e;
-        if (code[o] == SG_CELL_ABSENT) continue;
-        const int64_t op = p.cell_off + (int64_t)(q.pj0 + j / 2) * p.nx + (q.pi0 + i / 2);
-        const double ox = ((i & 1) - 0.5) * q.h, oy = ((j & 1) - 0.5) * q.h;
-        const double px = (double)s[op + P], py = (double)s[op + 2 * P];
-        const double pv = (double)s[op] + px * ox + py * oy;
-        s[o] = (T)((double)s[o] - pv);
-        s[o + P] = (T)((double)s[o + P] - px);
-        s[o + 2 * P] = (T)((double)s[o + 2 * P] - py);
+    const bool slopes = dx != nullptr;
+    T sum = 0, right = 0, top = 0, gx = 0, gy = 0;
+    for (int b = 0; b < 2; ++b) {
+        for (int a = 0; a < 2; ++a) {
+            T *w = v[2 * b + a];
+            cell_value(code, sigma, dx, dy, F, q.ncells_plane, q.cell_off + (int64_t)(cj + b) * q.nx + (ci + a), w);
+            sum += w[0];
+            right += a ? w[0] : -w[0];
+            top += b ? w[0] : -w[0];
+            gx += w[1];
+            gy += w[2];
+        }
     }
+    const T c = (T)0.75 / (T)hp;
+    out[0] = (T)0.25 * sum;
+    out[1] = slopes ? (T)0.25 * gx : c * right;
+    out[2] = slopes ? (T)0.25 * gy : c * top;
+}
+
+// The patch table (sorted order, prefix sums, descriptors) of plans with few
+// patches is copied into shared memory at kernel start, so that the lookups of
+// every work item (binary search, patch, child patch) do not wait on global loads.
+constexpr int COMP_SMEM_PATCHES = 128;
+
+struct patch_table {
+    const sg_patch_dev *pd;
+    const int *order;
+    const int64_t *pre;
+};
+
+__device__ __forceinline__ patch_table stage_patch_table(const sg_patch_dev *__restrict__ pd,
+                                                         const int *__restrict__ order,
+                                                         const int64_t *__restrict__ pre, int n)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (n > COMP_SMEM_PATCHES) return {pd, order, pre};
+    sg_patch_dev *spd = reinterpret_cast<sg_patch_dev *>(smem_raw);
+    int64_t *spre = reinterpret_cast<int64_t *>(spd + n);
+    int *sorder = reinterpret_cast<int *>(spre + n + 1);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        spd[k] = pd[k];
+        sorder[k] = order[k];
+    }
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) spre[k] = pre[k];
+    __syncthreads();
+    return {spd, sorder, spre};
+}
+
+inline size_t patch_table_bytes(int n)
+{
+    return n > COMP_SMEM_PATCHES ? 0 : (size_t)n * sizeof(sg_patch_dev) + (size_t)(n + 1) * 8 + (size_t)n * 4;
+}
+
+// Patch k and item r of the patches order[t0 .. t1) with item prefix sums pre[]
+__device__ __forceinline__ int find_item(const int64_t *__restrict__ pre, int t0, int t1, int64_t e)
+{
+    int lo = t0, hi = t1 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Filled values F of the covered cells of one refined level (patches order[t0 .. t1),
+// cells prefix cpre): the restriction of their children (finer levels done earlier).
+template <typename T>
+__global__ void k_fill_covered(const sg_patch_dev *__restrict__ gpd, const int *__restrict__ code,
+                               const int *__restrict__ gorder, const int64_t *__restrict__ gcpre, int npatches, int t0,
+                               int t1, const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
+                               T *__restrict__ F)
+{
+    const patch_table tab = stage_patch_table(gpd, gorder, gcpre, npatches);
+    const sg_patch_dev *pd = tab.pd;
+    const int *order = tab.order;
+    const int64_t *cpre = tab.pre;
+    const int64_t base = cpre[t0], n = cpre[t1] - base;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = find_item(cpre, t0, t1, base + e);
+        const sg_patch_dev p = pd[order[t]];
+        const int64_t r = base + e - cpre[t];
+        const int i = (int)(r % p.nx), j = (int)(r / p.nx);
+        const int64_t o = p.cell_off + r;
+        const int c = code[o];
+        if (c < 0) continue;
+        const sg_patch_dev q = pd[c];
+        T v[4][3], f[3];
+        restrict4(code, sigma, dx, dy, F, q, 2 * (i - q.pi0), 2 * (j - q.pj0), p.h, v, f);
+        const int64_t P = p.ncells_plane;
+        F[o] = f[0];
+        F[o + P] = f[1];
+        F[o + 2 * P] = f[2];
+    }
+}
+
+// The composite sources of every patch (items of the patches order[0 .. n),
+// prefix fpre): a level-0 cell gets its filled value; a 2x2 block of siblings on
+// a refined level gets filled value - P(parent), where the parent's filled value
+// is the restriction of these four cells (the value the parent's own restriction
+// produced).
+template <typename T>
+__global__ void k_composite(const sg_patch_dev *__restrict__ gpd, const int *__restrict__ code,
+                            const int *__restrict__ gorder, const int64_t *__restrict__ gfpre, int n,
+                            const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
+                            const T *__restrict__ F, T *__restrict__ s)
+{
+    const patch_table tab = stage_patch_table(gpd, gorder, gfpre, n);
+    const sg_patch_dev *pd = tab.pd;
+    const int *order = tab.order;
+    const int64_t *fpre = tab.pre;
+    const int64_t nitems = fpre[n];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nitems; e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = find_item(fpre, 0, n, e);
+        const sg_patch_dev p = pd[order[t]];
+        const int64_t P = p.ncells_plane;
+        const int64_t r = e - fpre[t];
+        T v[4][3], f[3];
+        if (p.parent < 0) {
+            const int64_t o = p.cell_off + r;
+            const int c = code[o];
+            if (c >= 0) {
+                const sg_patch_dev q = pd[c];
+                const int i = (int)(r % p.nx), j = (int)(r / p.nx);
+                restrict4(code, sigma, dx, dy, F, q, 2 * (i - q.pi0), 2 * (j - q.pj0), p.h, v, f);
+            } else {
+                cell_value(code, sigma, dx, dy, F, P, o, f);
+            }
+            s[o] = f[0];
+            s[o + P] = f[1];
+            s[o + 2 * P] = f[2];
+            continue;
+        }
+        const int bw = p.nx / 2;
+        const int bi = (int)(r % bw), bj = (int)(r / bw);
+        const int64_t o00 = p.cell_off + (int64_t)(2 * bj) * p.nx + 2 * bi;
+        if (code[o00] == SG_CELL_ABSENT) {  // blocks are wholly absent or present
+            for (int q = 0; q < 4; ++q) {
+                const int64_t o = o00 + (int64_t)(q >> 1) * p.nx + (q & 1);
+                s[o] = s[o + P] = s[o + 2 * P] = (T)0;
+            }
+            continue;
+        }
+        restrict4(code, sigma, dx, dy, F, p, 2 * bi, 2 * bj, pd[p.parent].h, v, f);
+        for (int q = 0; q < 4; ++q) {
+            const int a = q & 1, b = q >> 1;
+            const int64_t o = o00 + (int64_t)b * p.nx + a;
+            const T ox = ((T)a - (T)0.5) * (T)p.h, oy = ((T)b - (T)0.5) * (T)p.h;
+            const T pv = f[0] + f[1] * ox + f[2] * oy;
+            s[o] = v[q][0] - pv;
+            s[o + P] = v[q][1] - f[1];
+            s[o + 2 * P] = v[q][2] - f[2];
+        }
+    }
+}
+
+int grid_for(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
 template <typename T>
@@ -98,25 +233,24 @@ sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, co
                     cudaStream_t st)
 {
     T *s = (T *)ws->sfield;
+    T *F = s + 3 * plan->ncells;  // filled values of covered cells
     const bool slopes = plan->geom.slope_mode == SG_SLOPES_CALLER;
-    for (int k = plan->npatches - 1; k >= 0; --k) {
-        const sg_patch_dev &d = plan->pp[k].d;
-        const int64_t n = (int64_t)d.nx * d.ny;
-        int grid = (int)((n + 255) / 256);
-        if (grid > 4096) grid = 4096;
-        k_fill<T><<<grid, 256, 0, st>>>(d, plan->cell_code, plan->patch_dev, (const T *)sigma,
-                                        slopes ? (const T *)dx : nullptr, slopes ? (const T *)dy : nullptr, s);
+    const T *sx = slopes ? (const T *)dx : nullptr, *sy = slopes ? (const T *)dy : nullptr;
+    const int lmax = plan->comp_depth - 1;
+    // covered cells of the refined levels, finest first (level lmax has none)
+    for (int l = lmax - 1; l >= 1; --l) {
+        const int t0 = plan->comp_lev_first[l], t1 = plan->comp_lev_first[l + 1];
+        const int64_t n = plan->comp_cells_host[t1] - plan->comp_cells_host[t0];
+        if (n <= 0) continue;
+        k_fill_covered<T><<<grid_for(n), 256, patch_table_bytes(plan->npatches), st>>>(
+            plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_cells, plan->npatches, t0, t1,
+            (const T *)sigma, sx, sy, F);
         SG_CUDA_TRY(cudaGetLastError());
     }
-    for (int k = plan->npatches - 1; k >= 0; --k) {
-        const sg_patch_dev &d = plan->pp[k].d;
-        if (d.parent < 0) continue;
-        const int64_t n = (int64_t)d.nx * d.ny;
-        int grid = (int)((n + 255) / 256);
-        if (grid > 4096) grid = 4096;
-        k_defect<T><<<grid, 256, 0, st>>>(d, plan->pp[d.parent].d, plan->cell_code, s);
-        SG_CUDA_TRY(cudaGetLastError());
-    }
+    k_composite<T><<<grid_for(plan->comp_items), 256, patch_table_bytes(plan->npatches), st>>>(
+        plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_item_off, plan->npatches, (const T *)sigma, sx,
+        sy, F, s);
+    SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 

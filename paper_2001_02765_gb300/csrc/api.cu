@@ -460,6 +460,10 @@ void plan_free(sg_plan *plan)
     sg_lv_free(plan);
     cudaFree(plan->twiddles);
     cudaFree(plan->cell_code);
+    cudaFree(plan->comp_item_off);
+    cudaFree(plan->comp_order);
+    cudaFree(plan->comp_cells);
+    delete[] plan->comp_cells_host;
     cudaFree(plan->zone_slot);
     if (plan->ws) {
         sg_workspace_free(plan->ws, 0, false);
@@ -567,11 +571,34 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
     if (plan->composite) {
-        plan->ws_sfield_bytes = 3 * gi.ncells * (int64_t)es;
+        plan->ws_sfield_bytes = 6 * gi.ncells * (int64_t)es;  // composite sources S, filled values F
         std::vector<int> codes;
         codes.reserve((size_t)gi.ncells);
         for (int k = 0; k < gi.n; ++k) codes.insert(codes.end(), gi.code[k].begin(), gi.code[k].end());
         if (st == SG_OK) st = sg_plan_upload(plan, (void **)&plan->cell_code, codes.data(), codes.size() * sizeof(int));
+        // patches sorted by level; prefix sums of their cells and of the final launch's items
+        std::vector<int> order;
+        for (int l = 0; l <= gi.lmax; ++l) {
+            plan->comp_lev_first[l] = (int)order.size();
+            for (int k = 0; k < gi.n; ++k)
+                if (g->patches[k].level == l) order.push_back(k);
+        }
+        plan->comp_lev_first[gi.lmax + 1] = (int)order.size();
+        std::vector<int64_t> cells((size_t)gi.n + 1, 0), items((size_t)gi.n + 1, 0);
+        for (int t = 0; t < gi.n; ++t) {
+            const sg_patch &q = g->patches[order[t]];
+            cells[t + 1] = cells[t] + (int64_t)q.nx * q.ny;
+            items[t + 1] = items[t] + (q.level == 0 ? (int64_t)q.nx * q.ny : (int64_t)(q.nx / 2) * (q.ny / 2));
+        }
+        plan->comp_items = items[gi.n];
+        plan->comp_depth = gi.lmax + 1;
+        plan->comp_cells_host = new (std::nothrow) int64_t[gi.n + 1];
+        if (!plan->comp_cells_host) st = SG_ENOMEM;
+        else std::copy(cells.begin(), cells.end(), plan->comp_cells_host);
+        if (st == SG_OK) st = sg_plan_upload(plan, (void **)&plan->comp_order, order.data(), order.size() * sizeof(int));
+        if (st == SG_OK) st = sg_plan_upload(plan, (void **)&plan->comp_cells, cells.data(), cells.size() * sizeof(int64_t));
+        if (st == SG_OK)
+            st = sg_plan_upload(plan, (void **)&plan->comp_item_off, items.data(), items.size() * sizeof(int64_t));
     }
     if (st == SG_OK) st = dev_alloc(plan, &plan->patch_dev, gi.n * sizeof(sg_patch_dev));
     if (st == SG_OK)
@@ -650,7 +677,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         // level convolutions: one launch each for the row, column, column-MAC and inverse-row passes
         int n = use_lv ? 4 : gi.n * (central ? 4 : 3);
         if (plan->composite) {
-            for (int k = 0; k < gi.n; ++k) n += 1 + (gi.parent[k] >= 0);
+            n += gi.lmax > 0 ? gi.lmax : 1;  // composite sources: covered cells of levels 1 .. lmax-1, then all S_l
             if (plan->ntiles > 0) n += 2 + (nsplit > 1);
         }
         plan->launches = n;

@@ -184,6 +184,17 @@ struct sg_plan {
     int *cell_code;
     // composite sources (AMR prepare + per-patch FFT on them): several patches or masks
     bool composite;
+    // composite-source launches (amr.cu), over the patches sorted by level
+    // (comp_order; level l is comp_lev_first[l] .. comp_lev_first[l+1]): prefix
+    // sums of their cells (comp_cells, device, and a host copy) and of the final
+    // launch's items (comp_item_off: cells on level 0, 2x2 blocks above)
+    int *comp_order;
+    int64_t *comp_cells;
+    int64_t *comp_cells_host;
+    int64_t *comp_item_off;
+    int64_t comp_items;
+    int comp_lev_first[SG_MAX_LEVELS + 1];
+    int comp_depth;                 // levels of the hierarchy (lmax + 1)
 
     // zone plans (sg_plan_create_zones): zone k sits at cell zone_slot[k] (device)
     int64_t nzones;

@@ -39,6 +39,13 @@ __host__ __device__ __forceinline__ constexpr int spad(int i)
     return sizeof(C) == 8 ? i + (i >> 4) : i + (i >> 3);
 }
 
+// elements per padding group: spad(i + g m) = spad(i) + m spad(g) for whole groups
+template <typename C>
+__host__ __device__ __forceinline__ constexpr int spad_group()
+{
+    return sizeof(C) == 8 ? 16 : 8;
+}
+
 template <typename C>
 __host__ __device__ __forceinline__ constexpr int spad_size(int n)
 {
@@ -126,15 +133,21 @@ __device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
     constexpr int NBF = NB * (L / R);            // butterflies in the stage
     constexpr int PER = (NBF + THREADS - 1) / THREADS;
     C v[PER][R];
+    // the R inputs of a butterfly lie L/R apart; when L/R is a whole number of
+    // padding groups their padded positions lie a constant distance apart too
+    constexpr int S = L / R;
+    constexpr bool SPAN_IN = S % spad_group<C>() == 0;
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
         const int b = threadIdx.x + p * THREADS;
         if (NBF % THREADS == 0 || b < NBF) {
-            const int seq = b / (L / R), j = b % (L / R);
+            const int seq = b / S, j = b % S;
+            const C *src = buf + spad<C>(seq * L + j);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (IN_HALF && NS == 1 && r >= R / 2) v[p][r] = cmake<C>(0, 0);
-                else v[p][r] = buf[spad<C>(seq * L + j + r * (L / R))];
+                else if constexpr (SPAN_IN) v[p][r] = src[r * spad<C>(S)];
+                else v[p][r] = buf[spad<C>(seq * L + j + r * S)];
             }
         }
     }
@@ -166,10 +179,13 @@ __device__ __forceinline__ void fft_stage(C *buf, const C *__restrict__ tw)
             else if constexpr (R == 4) dft4<C, INV>(v[p][0], v[p][1], v[p][2], v[p][3]);
             else dft2<C, INV>(v[p][0], v[p][1]);
             const int base = seq * L + (j / NS) * NS * R + k;
+            constexpr bool SPAN_OUT = NS % spad_group<C>() == 0;
+            C *dst = buf + spad<C>(base);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (OUT_HALF && NS * R == L && r >= R / 2) continue;  // position k + r NS >= L/2
-                buf[spad<C>(base + r * NS)] = v[p][r];
+                if constexpr (SPAN_OUT) dst[r * spad<C>(NS)] = v[p][r];
+                else buf[spad<C>(base + r * NS)] = v[p][r];
             }
         }
     }

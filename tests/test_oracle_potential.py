@@ -9,7 +9,8 @@ import pytest
 from oracle.direct import uniform_direct_force
 from oracle.disks import d2_potential
 from oracle.norms import norms
-from oracle.potential import cell_potentials, uniform_direct_potential, uniform_fft_potential
+from oracle import amr as oamr
+from oracle.potential import amr_direct_potential, cell_potentials, uniform_direct_potential, uniform_fft_potential
 from paper_2001_02765_gb300 import workloads as W
 
 
@@ -97,3 +98,33 @@ def test_fft_route_equals_plain_sum(shape):
     a = uniform_direct_potential(s, sx, sy, 0.07, x0=0.3, y0=-0.2)
     b = uniform_fft_potential(s, sx, sy, 0.07)
     assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(a))
+
+
+def test_amr_refinement_invariance():
+    """Refining coarse cells into children that carry the parent's linear
+    reconstruction (sigma0 + delta . offset, same delta) leaves the potential at
+    the coarse leaves equal to the uniform-grid sum: the integrand is identical."""
+    n = 16
+    nx, ny, x0, y0, h = W.unit_grid(n)
+    s, sx, sy = W.random_fields(n, n, seed=23)
+    ref = uniform_direct_potential(s, sx, sy, h, x0=x0, y0=y0)
+    patches = oamr.make_patches([(0, nx, ny, x0, y0, h), (1, 16, 16, -0.5, -0.5, h / 2)])
+    fs, fsx, fsy = (np.zeros((16, 16)) for _ in range(3))
+    for J in range(16):
+        for I in range(16):
+            pj, pi = 4 + J // 2, 4 + I // 2
+            fs[J, I] = s[pj, pi] + sx[pj, pi] * (I % 2 - 0.5) * h / 2 + sy[pj, pi] * (J % 2 - 0.5) * h / 2
+            fsx[J, I], fsy[J, I] = sx[pj, pi], sy[pj, pi]
+    leaves, phi = amr_direct_potential(patches, [s, fs], [sx, fsx], [sy, fsy])
+    coarse = leaves["patch"] == 0
+    got, want = phi[coarse], ref[leaves["j"][coarse], leaves["i"][coarse]]
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+    # the refined region's leaves see the same potential at their own centres as
+    # the plain sum over the unrefined grid's cells
+    fine = ~coarse
+    tx, ty = leaves["xc"][fine], leaves["yc"][fine]
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny))
+    from oracle.potential import direct_potential
+    cells = (x0 + I * h, x0 + (I + 1) * h, y0 + J * h, y0 + (J + 1) * h)
+    want_f = direct_potential(cells, s, sx, sy, tx, ty)
+    assert np.max(np.abs(phi[fine] - want_f)) < 1e-13 * np.max(np.abs(want_f))
