@@ -212,9 +212,11 @@ sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const 
 /*
  * Mid-plane potential (Section 2: Phi(x, y, 0) = -G times the integral of
  * K(xbar - x, ybar - y, 0) sigma with K = 1/r, the singular kernel integral
- * whose gradient gives the force) at every cell centre of a plan of one
- * unmasked patch in the plane (z == 0), with the plan's slope mode (central
- * slopes are formed in the row transform here):
+ * whose gradient gives the force) at every cell centre of a plan in the plane
+ * (z == 0): one unmasked patch, with the plan's slope mode (central slopes are
+ * formed in the row transform here), or a hierarchy (patches, masks) solved by
+ * level convolutions (sg_plan_info.cross_mode == SG_CROSS_LEVELS), summed over
+ * the leaf cells as for sg_force (the output at covered cells is unspecified):
  *   Phi(t) = -G sum_i [sigma0_i P^0_i(t) + deltax_i P^x_i(t) + deltay_i P^y_i(t)],
  *   P^0, P^x, P^y = integrals over cell i of 1/r, (xbar - xc_i)/r, (ybar - yc_i)/r,
  * from the antiderivatives u ln(v + r) + v ln(u + r) and (v r + u^2 ln(v + r))/2
@@ -222,8 +224,8 @@ sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const 
  * its three FP64-built potential spectra synchronously (legacy default
  * stream); later calls only enqueue on `stream`.
  *   sigma, deltax, deltay  as for sg_force;  phi  device pointer, ncells elements
- * Errors: SG_EINVAL (not a single unmasked in-plane patch, null or misaligned
- * pointer, missing caller slopes), SG_ENOMEM, SG_ECUDA.
+ * Errors: SG_EINVAL (off the plane, a hierarchy on the direct-sum path, null or
+ * misaligned pointer, missing caller slopes), SG_ENOMEM, SG_ECUDA.
  */
 sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
                        void *stream);

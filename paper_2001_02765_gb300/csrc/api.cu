@@ -947,8 +947,9 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
                        void *stream)
 {
     if (!plan || !sigma || !phi) return fail("null plan or field pointer");
-    if (plan->npatches != 1 || plan->composite || plan->geom.z != 0.0)
-        return fail("sg_potential takes plans of one unmasked patch in the plane");
+    if (plan->geom.z != 0.0) return fail("sg_potential takes plans in the plane (z = 0)");
+    if (plan->composite && !plan->lv)
+        return fail("sg_potential takes plans of one unmasked patch, or hierarchies solved by level convolutions");
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
     if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
     const size_t es = elem_size(plan->prec);
@@ -957,6 +958,16 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
     int dev = -1;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != plan->device) return fail("the plan's device is not current");
+    if (plan->lv) {
+        // hierarchy: composite sources, then the level convolutions with the potential kernels
+        SG_TRY(sg_lv_potential_spectra_build(plan));
+        SG_TRY(ensure_ws(plan));
+        sg_timing_reset(plan->timing);
+        plan->ws->timing = plan->timing;
+        SG_TRY(sg_amr_prepare(plan, plan->ws, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr,
+                              (cudaStream_t)stream));
+        return sg_lv_potential(plan, plan->ws, phi, (cudaStream_t)stream);
+    }
     SG_TRY(sg_potential_spectra_build(plan));
     SG_TRY(ensure_ws(plan));
     const sg_patch_dev &d = plan->pp[0].d;

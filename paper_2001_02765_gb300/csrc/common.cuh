@@ -143,6 +143,7 @@ struct sg_lv {
     void *spectra;                           // [nkeys][6][px/2+1][py/2+1] T (compressed, see lvconv.cu)
     void *phase;                             // exp(i pi k / P), k in [-P/2, P/2], x then y, complex T
     void *cphase;                            // exp(-i pi j / P), j in [0, P], x then y, complex T
+    void *pspectra;                          // potential: [nkeys][3][px/2+1][py/2+1] T, built at the first call
     int64_t fwd_elems, spec_elems, inv_elems;
 };
 
@@ -310,6 +311,10 @@ struct sg_lv_setup_args {
 sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a);
 void sg_lv_free(sg_plan *plan);
 sg_status sg_lv_solve(sg_plan *plan, const struct sg_workspace *ws, void *fx, void *fy, cudaStream_t st);
+// The mid-plane potential of a level-convolution plan (composite sources already
+// in the workspace); its spectra are built by the first call (synchronously).
+sg_status sg_lv_potential_spectra_build(sg_plan *plan);
+sg_status sg_lv_potential(sg_plan *plan, const struct sg_workspace *ws, void *phi, cudaStream_t st);
 
 static inline int sg_ilog2(int v)
 {

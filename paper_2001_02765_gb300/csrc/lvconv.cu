@@ -164,6 +164,50 @@ __global__ void k_lv_extract(const double2 *z, T *out, int px, int py, int d2, d
     }
 }
 
+// Potential tables of one key (Section 2 with K = 1/r): for a source cell w = 2^s
+// finest cells wide at centre offset c (finest units), P^0 = w p0(c/w) and
+// P^x, P^y = w^2 px(c/w), w^2 py(c/w) with the unit-cell integrals of
+// unit_cell_potentials (finite everywhere). Packed z0 = Kr^px + i Kr^py,
+// z1 = Kr^p0, Kr[e] = P(-e - d), stored period symmetric about -d as for the force.
+__global__ void k_lv_tables_pot(double2 *z, int px, int py, int s, int d2)
+{
+    const int64_t plane = (int64_t)px * py;
+    const double w = (double)(1 << s), d = 0.5 * d2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % px), b = (int)(e / px);
+        const int ex = d2 < 0 ? (a <= px / 2 ? a : a - px) : (a < px / 2 ? a : a - px);
+        const int ey = d2 < 0 ? (b <= py / 2 ? b : b - py) : (b < py / 2 ? b : b - py);
+        double p3[3] = {0.0, 0.0, 0.0};
+        if (!(d2 == 0 && (ex == -px / 2 || ey == -py / 2))) unit_cell_potentials((-ex - d) / w, (-ey - d) / w, p3);
+        z[e] = make_double2(w * w * p3[1], w * w * p3[2]);
+        z[plane + e] = make_double2(w * p3[0], 0.0);
+    }
+}
+
+// Compressed potential spectra: planes p0 (Re H, even-even), px (Im H, odd in x)
+// and py (Im H, odd in y), [kx][ky] for kx in [0, px/2], ky in [0, py/2], scaled by
+// 1 / (px py) and by sc0 (p0) or sc1 (px, py).
+template <typename T>
+__global__ void k_lv_extract_pot(const double2 *z, T *out, int px, int py, int d2, double sc0, double sc1)
+{
+    const int qx = px / 2 + 1, qy = py / 2 + 1;
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
+    const double inv = 1.0 / ((double)px * (double)py);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(e / qy), ky = (int)(e % qy);
+        const int64_t ip = (int64_t)ky * px + kx;
+        const int64_t im = (int64_t)((py - ky) % py) * px + (px - kx) % px;
+        double sn, cs;  // exp(-i pi d2 (kx/px + ky/py))
+        sincospi(-(double)d2 * ((double)kx / px + (double)ky / py), &sn, &cs);
+        const double2 zp = z[ip], zm = z[im], z1 = z[plane + ip];
+        const double ar = 0.5 * (zp.x + zm.x), ai = 0.5 * (zp.y - zm.y);   // transform of Kr^px
+        const double br = 0.5 * (zp.y + zm.y), bi = -0.5 * (zp.x - zm.x);  // of Kr^py
+        out[e] = (T)(inv * sc0 * (z1.x * cs - z1.y * sn));
+        out[qplane + e] = (T)(inv * sc1 * (ar * sn + ai * cs));
+        out[2 * qplane + e] = (T)(inv * sc1 * (br * sn + bi * cs));
+    }
+}
+
 // Phase factors exp(i pi k / P) for k in [-P/2, P/2] (index k + P/2), per axis;
 // and the half-shift factors exp(-i pi j / P) for j in [0, P], per axis.
 template <typename T>
@@ -384,8 +428,9 @@ struct lv_mac_args {
 // from the compact one) x kernel spectrum (decompressed, see k_lv_extract),
 // formed element by element straight into two shared buffers; inverse column
 // transforms; the target level's sampled rows to out[(o qx + kx) ny + j]
-// (out at the level's inverse-column offset).
-template <typename T, int PY, int THREADS, int MINB>
+// (out at the level's inverse-column offset). NOUT = 1: the potential, one
+// output from 3 kernel planes per key (p0 real, px and py imaginary; py odd in ky).
+template <typename T, int PY, int THREADS, int MINB, int NOUT>
 __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
                                                             const T *__restrict__ kspec,
                                                             const cplx_t<T> *__restrict__ phx,
@@ -400,6 +445,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
     constexpr int QY = PY / 2 + 1;
     const int kx = blockIdx.x / a.nsrc, l = blockIdx.x % a.nsrc;
     const int64_t kqplane = (int64_t)a.qx * QY;
+    constexpr int NPL = NOUT == 2 ? 6 : 3;  // kernel planes per key
     // Bins in mirror pairs: slot j in [0, PY/2) holds bins j and PY - j, which read
     // the same kernel values (kq = j); slot 0 holds bins 0 and PY/2 (kq = 0 and PY/2).
     // V slots per thread at a time, so that their loads are in flight together.
@@ -431,7 +477,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
             const bool hy = a.hy[m] != 0;
             // sign of the x half-shift: (-1)^(kx div Pcx), times -1 on the folded half
             const bool xneg = a.hx[m] && ((((kx >> lpx) & 1) != 0) != fold);
-            const T *km = kspec + (int64_t)a.key[m][l] * 6 * kqplane + (int64_t)kx * QY;
+            const T *km = kspec + (int64_t)a.key[m][l] * NPL * kqplane + (int64_t)kx * QY;
             int row[V][2];
             bool neg[V][2];
 #pragma unroll
@@ -453,14 +499,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
                     X[f][v][0] = sm[f * splane + row[v][0]];
                     X[f][v][1] = sm[f * splane + row[v][1]];
                     gx[f][v][0] = gx[f][v][1] = km[f * kqplane + j];
-                    gy[f][v][0] = gy[f][v][1] = km[(3 + f) * kqplane + j];
+                    if constexpr (NOUT == 2) gy[f][v][0] = gy[f][v][1] = km[(3 + f) * kqplane + j];
                 }
             }
             if (j0 == 0) {  // slot 0: bin PY/2 has kernel values of its own
 #pragma unroll
                 for (int f = 0; f < 3; ++f) {
                     gx[f][0][1] = km[f * kqplane + PY / 2];
-                    gy[f][0][1] = km[(3 + f) * kqplane + PY / 2];
+                    if constexpr (NOUT == 2) gy[f][0][1] = km[(3 + f) * kqplane + PY / 2];
                 }
             }
             const int d2 = a.d2[m][l];
@@ -477,20 +523,33 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
                     // planes (prescaled by G, G h_f): x0 imaginary, xx real, xy real; y0 imaginary,
                     // yx real, yy real. The parts odd in ky (xy; y0, yx) change sign on the upper half.
                     const T g0 = gx[0][v][b], g1 = gx[1][v][b], g2 = gx[2][v][b];
-                    const T h0 = gy[0][v][b], h1 = gy[1][v][b], h2 = gy[2][v][b];
                     const T sg = (b == 0 || ky[v][1] == PY / 2) ? (T)1 : (T)-1;
-                    const T o2 = sg * g2, o0 = sg * h0, o1 = sg * h1;
-                    C hx = cmake<C>(g1 * X1.x - g0 * X0.y + o2 * X2.x, g1 * X1.y + g0 * X0.x + o2 * X2.y);
-                    C hy = cmake<C>(h2 * X2.x - o0 * X0.y + o1 * X1.x, h2 * X2.y + o0 * X0.x + o1 * X1.y);
-                    if (d2 != 0) {
-                        C p = ph[v][b];
-                        if (d2 < 0) p.y = -p.y;
-                        hx = cmul(hx, p);
-                        hy = cmul(hy, p);
+                    if constexpr (NOUT == 2) {
+                        const T h0 = gy[0][v][b], h1 = gy[1][v][b], h2 = gy[2][v][b];
+                        const T o2 = sg * g2, o0 = sg * h0, o1 = sg * h1;
+                        C hx = cmake<C>(g1 * X1.x - g0 * X0.y + o2 * X2.x, g1 * X1.y + g0 * X0.x + o2 * X2.y);
+                        C hy = cmake<C>(h2 * X2.x - o0 * X0.y + o1 * X1.x, h2 * X2.y + o0 * X0.x + o1 * X1.y);
+                        if (d2 != 0) {
+                            C p = ph[v][b];
+                            if (d2 < 0) p.y = -p.y;
+                            hx = cmul(hx, p);
+                            hy = cmul(hy, p);
+                        }
+                        const T sn = neg[v][b] ? (T)-1 : (T)1;
+                        ax[v][b] = cmake<C>(ax[v][b].x + sn * hx.x, ax[v][b].y + sn * hx.y);
+                        ay[v][b] = cmake<C>(ay[v][b].x + sn * hy.x, ay[v][b].y + sn * hy.y);
+                    } else {
+                        // potential planes: p0 real, px imaginary, py imaginary and odd in ky
+                        const T o2 = sg * g2;
+                        C hp = cmake<C>(g0 * X0.x - g1 * X1.y - o2 * X2.y, g0 * X0.y + g1 * X1.x + o2 * X2.x);
+                        if (d2 != 0) {
+                            C p = ph[v][b];
+                            if (d2 < 0) p.y = -p.y;
+                            hp = cmul(hp, p);
+                        }
+                        const T sn = neg[v][b] ? (T)-1 : (T)1;
+                        ax[v][b] = cmake<C>(ax[v][b].x + sn * hp.x, ax[v][b].y + sn * hp.y);
                     }
-                    const T sn = neg[v][b] ? (T)-1 : (T)1;
-                    ax[v][b] = cmake<C>(ax[v][b].x + sn * hx.x, ax[v][b].y + sn * hx.y);
-                    ay[v][b] = cmake<C>(ay[v][b].x + sn * hy.x, ay[v][b].y + sn * hy.y);
                 }
             }
         }
@@ -499,12 +558,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 bx[spad<C>(ky[v][b])] = ax[v][b];
-                by[spad<C>(ky[v][b])] = ay[v][b];
+                if constexpr (NOUT == 2) by[spad<C>(ky[v][b])] = ay[v][b];
             }
         }
     }
     __syncthreads();
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < NOUT; ++o) {
         C *buf = o == 0 ? bx : by;
         fft_batch<C, PY, 1, THREADS, true, false, true>(buf, tw);
         const int ny = a.ny[l], j0 = a.j0[l], t = a.t[l];
@@ -618,13 +677,13 @@ sg_status launch_col_fwd(const lv_col_fwd_args<T> &A, int ncta, int lmax, cudaSt
     return SG_OK;
 }
 
-template <typename T, int PY>
+template <typename T, int PY, int NOUT>
 sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const T *kspec, const cplx_t<T> *phx,
                              const cplx_t<T> *phy, cplx_t<T> *out, const cplx_t<T> *tw, cudaStream_t st)
 {
     constexpr int TH = lv_mac_threads<T>(PY);
-    const size_t sm = 2 * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
-    auto kern = k_lv_col_mac_inv<T, PY, TH, lv_mac_minb<T>(PY)>;
+    const size_t sm = NOUT * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
+    auto kern = k_lv_col_mac_inv<T, PY, TH, lv_mac_minb<T>(PY), NOUT>;
     SG_TRY(smem_attr(kern, sm));
     kern<<<a.qx * a.nsrc, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
     SG_CUDA_TRY(cudaGetLastError());
@@ -632,12 +691,13 @@ sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const 
 }
 
 template <typename T, int PX>
-sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, T *fx, T *fy, const cplx_t<T> *tw, cudaStream_t st)
+sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, int nout, T *fx, T *fy, const cplx_t<T> *tw,
+                         cudaStream_t st)
 {
     const size_t sm = spad_size<cplx_t<T>>(lv_nb(PX) * PX) * sizeof(cplx_t<T>);
     auto kern = k_lv_row_inv<T, PX>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<dim3(ncta, 2), LV_ROW_THREADS, sm, st>>>(A, fx, fy, tw);
+    kern<<<dim3(ncta, nout), LV_ROW_THREADS, sm, st>>>(A, fx, fy, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -655,8 +715,10 @@ sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, T *fx, T *fy, co
     default: return SG_EINVAL;                 \
     }
 
+// One solve on the composite sources in ws->sfield: the force (Fx, Fy into
+// out0, out1) or, with pot, the potential (into out0) from the potential spectra.
 template <typename T>
-sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, cudaStream_t st)
+sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *out0, void *out1, bool pot, cudaStream_t st)
 {
     using C = cplx_t<T>;
     const sg_lv &lv = *plan->lv;
@@ -736,7 +798,13 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
         }
         a.qx = qx;
         const C *phx = (const C *)lv.phase, *phy = phx + lv.px + 1;
-        SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP>(a, spec, (const T *)lv.spectra, phx, phy, wi, twy, st))));
+        if (pot) {
+            SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP, 1>(a, spec, (const T *)lv.pspectra, phx, phy, wi, twy,
+                                                                      st))));
+        } else {
+            SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP, 2>(a, spec, (const T *)lv.spectra, phx, phy, wi, twy,
+                                                                      st))));
+        }
     }
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);
@@ -753,7 +821,7 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, 
             ncta += (L.ny + 2 * lv_nb(lv.px) - 1) / (2 * lv_nb(lv.px));
         }
         A.cta0[lv.nlev] = ncta;
-        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_inv<T, PP>(A, ncta, (T *)fx, (T *)fy, twx, st))));
+        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_inv<T, PP>(A, ncta, pot ? 1 : 2, (T *)out0, (T *)out1, twx, st))));
     }
     sg_timing_end(ws, SG_STAGE_ROW_INV, st);
     return SG_OK;
@@ -768,6 +836,7 @@ void sg_lv_free(sg_plan *plan)
     cudaFree(plan->lv->spectra);
     cudaFree(plan->lv->phase);
     cudaFree(plan->lv->cphase);
+    cudaFree(plan->lv->pspectra);
     delete plan->lv;
     plan->lv = nullptr;
 }
@@ -885,8 +954,68 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
     return st;
 }
 
+sg_status sg_lv_potential_spectra_build(sg_plan *plan)
+{
+    sg_lv *lv = plan->lv;
+    if (!lv) return SG_EINVAL;
+    if (lv->pspectra) return SG_OK;
+    const int px = lv->px, py = lv->py;
+    const size_t rs = plan->prec == SG_FP64 ? sizeof(double) : sizeof(float);
+    const int64_t qplane = (int64_t)(px / 2 + 1) * (py / 2 + 1), plane = (int64_t)px * py;
+    void *spec = nullptr;
+    double2 *z = nullptr;
+    cudaError_t e = cudaMalloc(&spec, (size_t)lv->nkeys * 3 * qplane * rs);
+    if (e == cudaSuccess) e = cudaMalloc(&z, (size_t)(2 * plane * sizeof(double2)));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(spec);
+        cudaFree(z);
+        sg_set_last_cuda_error(e, "cudaMalloc");
+        return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
+    }
+    const double2 *twx = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(px)]);
+    const double2 *twy = (const double2 *)((const char *)plan->twiddles + plan->tw64_off[sg_ilog2(py)]);
+    // Phi = -G sum [sigma0 P^0 + deltax P^x + deltay P^y]: P^0 in units of h_f, P^x, P^y of h_f^2
+    const double sc0 = -plan->geom.G * lv->hf, sc1 = -plan->geom.G * lv->hf * lv->hf;
+    sg_status st = SG_OK;
+    for (int k = 0; k < lv->nkeys && st == SG_OK; ++k) {
+        k_lv_tables_pot<<<2048, 256>>>(z, px, py, lv->key_s[k], lv->key_d2[k]);
+        if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
+        for (int q = 0; q < 2 && st == SG_OK; ++q) {
+            double2 *zq = z + q * plane;
+            st = sg_fft_lines_fp64(zq, px, py, px, 1, twx);
+            if (st == SG_OK) st = sg_fft_lines_fp64(zq, py, px, 1, px, twy);
+        }
+        if (st != SG_OK) break;
+        char *dst = (char *)spec + (size_t)k * 3 * qplane * rs;
+        if (plan->prec == SG_FP64)
+            k_lv_extract_pot<double><<<2048, 256>>>(z, (double *)dst, px, py, lv->key_d2[k], sc0, sc1);
+        else k_lv_extract_pot<float><<<2048, 256>>>(z, (float *)dst, px, py, lv->key_d2[k], sc0, sc1);
+        if (cudaGetLastError() != cudaSuccess) st = SG_ECUDA;
+    }
+    e = cudaDeviceSynchronize();
+    cudaFree(z);
+    if (st == SG_OK && e != cudaSuccess) {
+        sg_set_last_cuda_error(e, "level-convolution potential tables");
+        st = SG_ECUDA;
+    }
+    if (st != SG_OK) {
+        cudaFree(spec);
+        return st;
+    }
+    lv->pspectra = spec;
+    plan->device_bytes += (int64_t)lv->nkeys * 3 * qplane * (int64_t)rs;
+    return SG_OK;
+}
+
+sg_status sg_lv_potential(sg_plan *plan, const sg_workspace *ws, void *phi, cudaStream_t st)
+{
+    if (plan->prec == SG_FP64) return lv_solve_t<double>(plan, ws, phi, nullptr, true, st);
+    return lv_solve_t<float>(plan, ws, phi, nullptr, true, st);
+}
+
 sg_status sg_lv_solve(sg_plan *plan, const sg_workspace *ws, void *fx, void *fy, cudaStream_t st)
 {
-    if (plan->prec == SG_FP64) return lv_solve_t<double>(plan, ws, fx, fy, st);
-    return lv_solve_t<float>(plan, ws, fx, fy, st);
+    if (plan->prec == SG_FP64) return lv_solve_t<double>(plan, ws, fx, fy, false, st);
+    return lv_solve_t<float>(plan, ws, fx, fy, false, st);
 }

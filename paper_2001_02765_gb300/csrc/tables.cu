@@ -139,22 +139,8 @@ __device__ void unit_kernels_z(int m, int n, double zeta, double *out9)
 // Dv(u) = asinh(v2/|u|) - asinh(v1/|u|), Du(v) likewise, Ru(v) = r(u2, v) - r(u1, v),
 // Rv(u) = r(u, v2) - r(u, v1); terms whose prefactor is 0 are 0 (their limits), so every
 // offset, the own cell included, is finite. P0 scales with h, Px and Py with h^2.
-__device__ void unit_potentials(int m, int n, double *out3)
-{
-    const double u1 = m - 0.5, u2 = m + 0.5, v1 = n - 0.5, v2 = n + 0.5;
-    const double dv1 = u1 != 0.0 ? asinh_span(v1, v2, fabs(u1)) : 0.0;
-    const double dv2 = u2 != 0.0 ? asinh_span(v1, v2, fabs(u2)) : 0.0;
-    const double du1 = v1 != 0.0 ? asinh_span(u1, u2, fabs(v1)) : 0.0;
-    const double du2 = v2 != 0.0 ? asinh_span(u1, u2, fabs(v2)) : 0.0;
-    const double p0 = u2 * dv2 - u1 * dv1 + v2 * du2 - v1 * du1;
-    const double r22 = sqrt(u2 * u2 + v2 * v2), r12 = sqrt(u1 * u1 + v2 * v2);
-    const double r21 = sqrt(u2 * u2 + v1 * v1), r11 = sqrt(u1 * u1 + v1 * v1);
-    const double ru2 = (u2 + u1) / (r22 + r12), ru1 = (u2 + u1) / (r21 + r11);  // r(u2,v) - r(u1,v)
-    const double rv2 = (v2 + v1) / (r22 + r21), rv1 = (v2 + v1) / (r12 + r11);  // r(u,v2) - r(u,v1)
-    out3[0] = p0;
-    out3[1] = 0.5 * (v2 * ru2 - v1 * ru1 + u2 * u2 * dv2 - u1 * u1 * dv1) - (double)m * p0;
-    out3[2] = 0.5 * (u2 * rv2 - u1 * rv1 + v2 * v2 * du2 - v1 * v1 * du1) - (double)n * p0;
-}
+// (the closed forms themselves: unit_cell_potentials in kmath.cuh, at real offsets)
+__device__ void unit_potentials(int m, int n, double *out3) { unit_cell_potentials((double)m, (double)n, out3); }
 
 // Wrapped correlation tables of the potential packed as z0 = Pr^x + i Pr^y (both
 // transforms imaginary by parity), z1 = Pr^0 (transform real), each [py][px].

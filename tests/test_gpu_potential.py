@@ -8,9 +8,10 @@ import pytest
 from oracle.disks import d2_potential
 from oracle.fftconv import central_slopes
 from oracle.norms import norms, rel_l2
-from oracle.potential import uniform_direct_potential, uniform_fft_potential
+from oracle import amr as oamr
+from oracle.potential import amr_direct_potential, uniform_direct_potential, uniform_fft_potential
 from paper_2001_02765_gb300 import workloads as W
-from tests._lib import ensure_built, to_dev
+from tests._lib import concat_dev, ensure_built, gather_leaves, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -134,9 +135,103 @@ def test_potential_repeatable_and_errors(sg):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     plan.close()
-    amr = sg.Plan([(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))])
+    amr = sg.Plan([(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))], cross_mode=sg.SG_CROSS_DIRECT)
     x = torch.zeros(amr.ncells, device="cuda")
     with pytest.raises(sg.SgError) as e:
         sg.sg_potential(amr.handle, x.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr())
     assert e.value.status == sg.SG_EINVAL and "one unmasked patch" in str(e.value)
     amr.close()
+
+
+# ------------------------------------------- hierarchies (level convolutions) --
+
+TABLE10 = [(0, 4, 4, 0.0, 0.0, 0.25), (1, 2, 2, 0.25, 0.25, 0.125), (1, 2, 2, 0.5, 0.5, 0.125),
+           (2, 2, 2, 0.25, 0.375, 0.0625), (2, 2, 2, 0.375, 0.25, 0.0625)]
+
+
+def _amr_phi(sg, patches, prec, mode, sig, sx, sy, G=1.0):
+    import torch
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan = sg.Plan(patches, precision=prec, slope_mode=mode, G=G, cross_mode=sg.SG_CROSS_LEVELS)
+    a = concat_dev(sig, dt)
+    b = concat_dev(sx, dt) if mode == sg.SG_SLOPES_CALLER else None
+    c = concat_dev(sy, dt) if mode == sg.SG_SLOPES_CALLER else None
+    phi = plan.potential(a, b, c)
+    torch.cuda.synchronize()
+    return plan, phi.cpu().numpy().astype(np.float64)
+
+
+def _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None):
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan, phi = _amr_phi(sg, patches, prec, mode, sig, sx, sy, G)
+    r = lambda a: [np.asarray(x, dt).astype(np.float64) for x in a]
+    slopes = mode == sg.SG_SLOPES_CALLER
+    leaves, ref = amr_direct_potential(oamr.make_patches(patches), r(sig), r(sx) if slopes else None,
+                                       r(sy) if slopes else None, G=G, target_index=target_index)
+    if target_index is not None:
+        leaves = {k: v[target_index] for k, v in leaves.items()}
+    got = gather_leaves(plan, phi, leaves)
+    plan.close()
+    err = _rel(got, ref)
+    assert err < tol, err
+    return err
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("mode", [0, 2])
+def test_amr_potential_nested(sg, prec, tol, mode):
+    """Three centred nested levels of 16^2 cells, smooth bumps: the leaf-sum potential."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))]
+    sig, sx, sy = W.bumps_on_patches(patches, 3)
+    _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=2.5)
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_amr_potential_table10(sg, prec, tol):
+    """Fig. 1 / Table 10: two patches per refined level, 28 leaves, random positive data."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    sig = [rng.uniform(0, 1, (p[2], p[1])) for p in TABLE10]
+    sx = [rng.uniform(-1, 1, (p[2], p[1])) for p in TABLE10]
+    sy = [rng.uniform(-1, 1, (p[2], p[1])) for p in TABLE10]
+    _amr_check(sg, TABLE10, prec, 2, sig, sx, sy, tol)
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_amr_potential_ragged(sg, prec, tol):
+    """Non-square, off-centre patches (two on level 1), sizes not powers of two."""
+    patches = [(0, 37, 29, -1.0, -0.8, 0.05), (1, 22, 14, -0.6, -0.3, 0.025), (1, 6, 8, 0.2, 0.1, 0.025),
+               (2, 10, 12, -0.5, -0.25, 0.0125)]
+    sig, sx, sy = W.bumps_on_patches(patches, 5)
+    _amr_check(sg, patches, prec, 2, sig, sx, sy, tol)
+
+
+def test_amr_potential_config3_sampled(sg):
+    """The 3 x 256^2 exponential-disk hierarchy, FP32: 64 sampled leaves against the plain sum."""
+    case = W.exponential_hierarchy(256, 3, 0.1)
+    patches = [(lev,) + p for lev, p in enumerate(case["patches"])]
+    sig, sx, sy = case["sigma"], case["dx"], case["dy"]
+    n = len(oamr.leaf_cells(oamr.make_patches(patches))["xc"])
+    idx = np.random.Generator(np.random.PCG64(33)).choice(n, 64, replace=False)
+    _amr_check(sg, patches, "fp32", 2, sig, sx, sy, 1e-5, target_index=idx)
+
+
+def test_amr_potential_matches_force(sg):
+    """Central differences of the hierarchy's potential on the finest patch
+    against its force (FP64): agreement to O(h^2) inside the patch."""
+    import torch
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(32, 3))]
+    sig, sx, sy = W.bumps_on_patches(patches, 3)
+    plan = sg.Plan(patches, precision="fp64", slope_mode=sg.SG_SLOPES_CALLER, cross_mode=sg.SG_CROSS_LEVELS)
+    a, b, c = (concat_dev(f, np.float64) for f in (sig, sx, sy))
+    phi = plan.potential(a, b, c)
+    fx, fy = plan.force(a, b, c)
+    torch.cuda.synchronize()
+    P = plan.split(phi.cpu().numpy())[-1]
+    FX = plan.split(fx.cpu().numpy())[-1]
+    FY = plan.split(fy.cpu().numpy())[-1]
+    h = patches[-1][5]
+    plan.close()
+    gx = -(P[1:-1, 2:] - P[1:-1, :-2]) / (2 * h)
+    gy = -(P[2:, 1:-1] - P[:-2, 1:-1]) / (2 * h)
+    err = np.hypot(gx - FX[1:-1, 1:-1], gy - FY[1:-1, 1:-1])
+    assert float(np.sqrt(np.mean(err ** 2))) < 2e-2 * float(np.sqrt(np.mean(FX[1:-1, 1:-1] ** 2 + FY[1:-1, 1:-1] ** 2)))
