@@ -36,6 +36,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "force solves/sec and target-cells/sec (p50/p99 latency) vs FP64 plain, ≤1e-5 rel err"
+METRIC_POTENTIAL = "potential solves/sec and target-cells/sec (p50/p99 latency) vs FP64 plain, ≤1e-5 rel err"
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -500,8 +501,9 @@ class OracleSample:
     """The FP64 plain direct sum (the oracle) on a seeded sample of leaf targets
     of a workload; the leaf list is prepared once."""
 
-    def __init__(self, wl):
+    def __init__(self, wl, potential=False):
         from oracle import amr as oamr
+        self.potential = potential
         from oracle.fftconv import central_slopes
         self.total_targets = wl["targets"]
         self.rng = np.random.Generator(np.random.PCG64(77))
@@ -547,9 +549,11 @@ class OracleSample:
     def run(self, sample_targets, nthreads=0):
         """Returns (solves/s, target-cells/s, seconds, threads, description)."""
         from oracle.direct import direct_force, max_threads
+        from oracle.potential import direct_potential
         tsel = self.rng.choice(self.tx.size, sample_targets, replace=False)
         t0 = time.perf_counter()
-        direct_force(self.cells, self.s0, self.sx, self.sy, self.tx[tsel], self.ty[tsel], nthreads=nthreads)
+        f = direct_potential if self.potential else direct_force
+        f(self.cells, self.s0, self.sx, self.sy, self.tx[tsel], self.ty[tsel], nthreads=nthreads)
         dt = time.perf_counter() - t0
         threads = nthreads or max_threads()
         tps = sample_targets / dt
@@ -573,6 +577,9 @@ def run_gpu(args):
     dt = torch.float32
     zt = wl.get("z", 0.0)
     zones = wl.get("zones")
+    pot = args.quantity == "potential"
+    if pot and (zt or zones is not None):
+        raise SystemExit("--quantity potential takes the in-plane patch workloads")
 
     def make_plan(prec):
         if zones is not None:
@@ -606,7 +613,10 @@ def run_gpu(args):
             elif zones is not None:
                 plan.force_zones(sigma, dxs, dys, fx, fy, stream=stream)
             else:
-                plan.force(sigma, dxs, dys, fx, fy, stream=stream)
+                if pot:
+                    plan.potential(sigma, dxs, dys, phi=fx, stream=stream)
+                else:
+                    plan.force(sigma, dxs, dys, fx, fy, stream=stream)
 
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -649,10 +659,13 @@ def run_gpu(args):
         d64 = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32).astype(np.float64)).cuda()
         s64, dx64, dy64 = d64(wl["sigma"]), d64(wl["dx"]), d64(wl["dy"])
         t0 = time.perf_counter()
-        g64 = plan64.force3(s64, dx64, dy64) if zt else f64(s64, dx64, dy64)
+        if pot:
+            g64 = (plan64.potential(s64, dx64, dy64),)
+        else:
+            g64 = plan64.force3(s64, dx64, dy64) if zt else f64(s64, dx64, dy64)
         torch.cuda.synchronize()
         first = time.perf_counter() - t0
-        ff = [x.double() for x in ((fx, fy, fz) if zt else (fx, fy))]
+        ff = [x.double() for x in ((fx,) if pot else ((fx, fy, fz) if zt else (fx, fy)))]
         num = sum(torch.sum((a - b) ** 2) for a, b in zip(ff, g64))
         den = sum(torch.sum(b ** 2) for b in g64)
         rel_err = float(torch.sqrt(num / den))
@@ -664,7 +677,10 @@ def run_gpu(args):
             if zt:
                 plan64.force3(s64, dx64, dy64)
             else:
-                f64(s64, dx64, dy64, g64[0], g64[1])
+                if pot:
+                    plan64.potential(s64, dx64, dy64, phi=g64[0])
+                else:
+                    f64(s64, dx64, dy64, g64[0], g64[1])
             e64[k][1].record()
         torch.cuda.synchronize()
         fp64_ms = statistics.median([a.elapsed_time(b) for a, b in e64])
@@ -699,6 +715,25 @@ def run_gpu(args):
                 e2e_ms += 1e3 * (time.perf_counter() - t0)
         h2d = 3 * nout * 4
         d2h = 2 * nout * 4
+    elif pot:
+        # pinned host arrays copied in, the potential, phi copied back, all in the timed region
+        e2e_ms = 0.0
+        for k in range(args.steps + 2):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                sigma.copy_(hs, non_blocking=True)
+                if dxs is not None:
+                    dxs.copy_(hdx, non_blocking=True)
+                    dys.copy_(hdy, non_blocking=True)
+                plan.potential(sigma, dxs, dys, phi=fx, stream=stream)
+                hfx.copy_(fx, non_blocking=True)
+            stream.synchronize()
+            if k >= 2:
+                e2e_ms += 1e3 * (time.perf_counter() - t0)
+        h2d = nout * 4 * (3 if dxs is not None else 1)
+        d2h = nout * 4
     elif not zt:  # the host entry point returns Fx, Fy
         for _ in range(2):
             plan.force_host(hs, hdx, hdy, hfx, hfy, stream=stream)
@@ -718,8 +753,8 @@ def run_gpu(args):
     dom = max(stage_mean, key=stage_mean.get)
     hbm_peak, hbm_src, fp32_peak, fp32_src = _peaks()
     info = plan.info
-    alg = algorithmic_bytes(wl, info, dom)
-    flops = algorithmic_flops(wl, info, dom)
+    alg = algorithmic_bytes(wl, info, dom, nout=1 if pot else 2)
+    flops = algorithmic_flops(wl, info, dom, nout=1 if pot else 2)
     secs = stage_mean[dom] * 1e-3
     tflops = flops / secs / 1e12 if secs > 0 else 0.0
     gbs = alg / secs / 1e9 if secs > 0 else 0.0
@@ -728,10 +763,11 @@ def run_gpu(args):
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC_POTENTIAL if pot else METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(wl["config"], parallelism="replicas" if world > 1 else "single"),
+        "config": dict(wl["config"], parallelism="replicas" if world > 1 else "single",
+                       **({"quantity": "potential"} if pot else {})),
         "target_cells_per_s": value * wl["targets"],
         "latency_ms": {"p50": p50, "p99": p99},
         "fp64_plain": {"solves_per_s": 1e3 / fp64_ms * world if fp64_ms else None, "ms_per_solve": fp64_ms,
@@ -751,7 +787,7 @@ def run_gpu(args):
         "wall_s": wall,
     }
     if world == 1 and not args.no_cpu_baseline:
-        sps, tps, secs, thr, what = OracleSample(wl).run(args.cpu_targets)
+        sps, tps, secs, thr, what = OracleSample(wl, potential=pot).run(args.cpu_targets)
         line["cpu_baseline"] = {"value": sps, "unit": "solves/s", "cores": thr, "kind": "oracle", "sample": what,
                                 "target_cells_per_s": tps, "seconds": secs}
     print(json.dumps(line), flush=True)
@@ -809,11 +845,12 @@ def lv_geometry(wl):
     return _pad(wx), _pad(wy), imgs
 
 
-def algorithmic_flops(wl, info, stage):
+def algorithmic_flops(wl, info, stage, nout=2):
     """Conventional flop counts: 5 L log2 L per complex FFT of length L, plus
     the spectral multiply-adds (8 flops per field per bin; about 60 per bin for
     the central-slope spectrum; 10 per field and target for level convolutions);
-    the direct sum counts 28 FP32 operations per target-corner pair (FMA = 2)."""
+    the direct sum counts 28 FP32 operations per target-corner pair (FMA = 2).
+    nout = 1: the potential (one output; slopes formed in the row pass)."""
     import math
     total = 0.0
     if info.get("cross_mode") == 2:
@@ -826,9 +863,9 @@ def algorithmic_flops(wl, info, stage):
             if stage == "row_fwd":
                 total += 3 * (ny / 2) * fft(pcx)
             elif stage == "col_conv":
-                total += (pcx // 2 + 1) * 3 * fft(pcy) + qx * (2 * fft(py) + L * 3 * 10 * py)
+                total += (pcx // 2 + 1) * 3 * fft(pcy) + qx * (nout * fft(py) + L * 3 * 5 * nout * py)
             elif stage == "row_inv":
-                total += 2 * (ny / 2) * fft(px)
+                total += nout * (ny / 2) * fft(px)
         return total
     for p in wl["patches"]:
         nx, ny = p[1], p[2]
@@ -836,27 +873,27 @@ def algorithmic_flops(wl, info, stage):
         qx = px // 2 + 1
         fft_x = 5.0 * px * math.log2(px)
         fft_y = 5.0 * py * math.log2(py)
-        central = wl["slope_mode"] == 1
-        nfwd = 1 if wl["slope_mode"] != 2 else 3
+        central = wl["slope_mode"] == 1 and nout == 2
+        nfwd = 1 if wl["slope_mode"] == 0 or central else 3
         if stage == "row_fwd":
             total += nfwd * (ny / 2) * fft_x + (fft_y if central else 0)
         elif stage == "col_conv":
-            total += qx * ((nfwd + 2) * fft_y + (60 if central else 8 * nfwd) * py)
+            total += qx * ((nfwd + nout) * fft_y + (60 if central else 4 * nout * nfwd) * py)
         elif stage == "row_inv":
-            total += ny * fft_x  # two outputs, two rows per transform
+            total += nout * (ny / 2) * fft_x  # two rows per transform
     if stage == "cross_direct":
         total = 28.0 * info["cross_pairs"]
     return total
 
 
-def algorithmic_bytes(wl, info, stage):
+def algorithmic_bytes(wl, info, stage, nout=2):
     """Bytes a stage must move per solve (see the design notes): FP32 complex
     intermediates of (P/2+1) x ny bins per field, spectra planes, inputs, outputs.
     Level convolutions: the forward column pass writes compact source spectra
     (a level of cells 2^s finest cells wide: P/2^s per axis); the column-MAC
     launch of all target levels reads them once, and once each distinct set of
     compressed kernel planes (6 real quarter planes per (source width, sample
-    shift))."""
+    shift); 3 for the potential, nout = 1, which has one output)."""
     es = 4
     cs = 8
     total = 0
@@ -871,16 +908,17 @@ def algorithmic_bytes(wl, info, stage):
             elif stage == "col_conv":
                 total += 3 * qxc * ny * cs + 3 * qxc * pcy * cs       # compact column transforms of this level
                 total += 3 * qxc * pcy * cs                         # read once by the column-MAC launch
-                total += 2 * qx * ny * cs                           # this level's inverse columns
+                total += nout * qx * ny * cs                        # this level's inverse columns
             elif stage == "row_inv":
-                total += 2 * qx * ny * cs + 2 * nx * ny * es
+                total += nout * qx * ny * cs + nout * nx * ny * es
         if stage == "col_conv":
-            # kernel planes: one set of 6 real quarter planes per distinct (source width, sample shift)
+            # kernel planes: one set of 6 (3) real quarter planes per distinct (source width, sample shift)
             keys = {(sm, (sm >= 1) - (sl >= 1)) for _, _, sm in imgs for _, _, sl in imgs}
-            total += len(keys) * 6 * qx * qy * es
+            total += len(keys) * 3 * nout * qx * qy * es
         return total
     # central slopes are formed from sigma's transforms: one field is transformed
-    nf = 3 if wl["slope_mode"] == 2 else 1
+    # (the potential forms them in the row pass: three fields)
+    nf = 1 if wl["slope_mode"] == 0 or (wl["slope_mode"] == 1 and nout == 2) else 3
     for p in wl["patches"]:
         nx, ny = p[1], p[2]
         px, py = _pad(nx), _pad(ny)
@@ -889,9 +927,9 @@ def algorithmic_bytes(wl, info, stage):
         if stage == "row_fwd":
             total += inputs + nf * qx * ny * 2 * es
         elif stage == "col_conv":
-            total += nf * qx * ny * 2 * es + 6 * qx * qy * es + 2 * qx * ny * 2 * es
+            total += nf * qx * ny * 2 * es + 3 * nout * qx * qy * es + nout * qx * ny * 2 * es
         elif stage == "row_inv":
-            total += 2 * qx * ny * 2 * es + 2 * nx * ny * es
+            total += nout * qx * ny * 2 * es + nout * nx * ny * es
     if stage in ("corner_weights", "cross_direct"):
         total = info["ncells"] * es * 3
     return total
@@ -904,7 +942,8 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]()
-    orc = OracleSample(wl)
+    pot = args.quantity == "potential"
+    orc = OracleSample(wl, potential=pot)
     for _ in range(args.warmup):
         orc.run(8)
     times, tps_all, thr, what = [], [], 0, ""
@@ -915,10 +954,11 @@ def run_reference(args):
     tps = args.steps * args.ref_targets / sum(times)
     value = tps / wl["targets"]
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "impl": "reference", "metric": METRIC_POTENTIAL if pot else METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(wl["config"], precision="fp64", parallelism="host cores"),
+        "config": dict(wl["config"], precision="fp64", parallelism="host cores",
+                       **({"quantity": "potential"} if pot else {})),
         "target_cells_per_s": tps,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": thr, "kind": "oracle",
                          "sample": "each step: " + what},
@@ -941,6 +981,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="run the graph-captured batch workload instead")
     ap.add_argument("--batch-size", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--quantity", default="force", choices=["force", "potential"],
+                    help="what a step computes (the potential: in-plane patch workloads)")
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-sweep", action="store_true", help="also run loads 0.3, 0.5, 1.0 on a tenth of the stream")
     ap.add_argument("--serve-inflight", type=int, default=8)
