@@ -795,10 +795,10 @@ def run_gpu(args):
 
 # DRAM bytes (read + write) per launch of a stage's kernel from the ncu capture
 # of the current kernel build (see profiles/); None when not captured for it.
-# amr3 col_conv: the stage's 3 column-transform and 3 column-MAC launches per
-# solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
-TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.018e6,
-           ("amr3", "col_conv"): 3 * (6.32e6 + 0.51e6) + 3 * (226.94e6 + 5.79e6)}
+# amr3 col_conv: the stage's column-transform and column-MAC launches, one each
+# per solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
+TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.009e6,
+           ("amr3", "col_conv"): (11.14e6 + 7.03e6) + (227.21e6 + 11.05e6)}
 
 
 def _pad(n):
