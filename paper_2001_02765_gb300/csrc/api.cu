@@ -372,7 +372,7 @@ bool lv_params(const sg_geom *g, const geom_info &gi, sg_precision prec, sg_lv_s
             }
         }
     }
-    bytes = mapbytes + (int64_t)nkeys * 6 * qx * (py / 2 + 1) * (cs / 2) + (px + py + 2) * cs + work;
+    bytes = mapbytes + (int64_t)nkeys * 6 * qx * sg_spec_stride((int)py) * (cs / 2) + 2 * (px + py + 2) * cs + work;
     return true;
 }
 

@@ -6,14 +6,24 @@
 // so the graph holds n independent branches that the GPU runs concurrently.
 // sg_batch_launch replays the whole batch with a single graph launch, which
 // removes the per-kernel launch overhead of uneven small solves.
+//
+// Members that are single in-plane patches with the same padded lengths,
+// precision and slope handling form a group: each pass of the group is one
+// launch over all its members (blockIdx.z = member, arguments from a device
+// array), so that small solves fill the GPU together instead of as many
+// concurrent small kernels. Other members keep their own branch.
 #include "common.cuh"
+#include "fftconv.cuh"
 
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 struct sg_batch {
     int n = 0;
     std::vector<sg_workspace> ws;
+    std::vector<void *> dev_args;  // per-group argument arrays
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
@@ -28,7 +38,74 @@ void batch_free(sg_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (sg_workspace &w : b->ws) sg_workspace_free(&w, 0, false);
+    for (void *a : b->dev_args) cudaFree(a);
     delete b;
+}
+
+bool groupable(const sg_plan *p)
+{
+    return p->npatches == 1 && !p->composite && !p->lv && p->geom.z == 0.0;
+}
+
+// A group's passes: the members' arguments in one device array per pass.
+template <typename T>
+struct group_passes {
+    sgk::uniform_passes<T> u;  // lengths, shapes and twiddles are common to the group
+    const sgk::row_fwd_args<T> *rf = nullptr;
+    const sgk::edge_args<T> *ed = nullptr;
+    const sgk::col_args<T> *col = nullptr;
+    const sgk::row_inv_args<T> *ri = nullptr;
+    sgk::batch_shape bs = {0, 0};
+    int *err = nullptr;
+};
+
+// Upload the argument arrays of a group (owned by the batch); before capture.
+template <typename T>
+sg_status group_upload(sg_batch *b, const std::vector<sgk::uniform_passes<T>> &us, int *err, group_passes<T> &g)
+{
+    const int m = (int)us.size();
+    std::vector<sgk::row_fwd_args<T>> rf(m);
+    std::vector<sgk::edge_args<T>> ed(m);
+    std::vector<sgk::col_args<T>> col(m);
+    std::vector<sgk::row_inv_args<T>> ri(m);
+    int maxny = 0;
+    for (int i = 0; i < m; ++i) {
+        rf[i] = us[i].rf;
+        ed[i] = us[i].ed;
+        col[i] = us[i].col;
+        ri[i] = us[i].ri;
+        if (us[i].rf.src.ny > maxny) maxny = us[i].rf.src.ny;
+    }
+    const size_t s0 = m * sizeof(rf[0]), s1 = m * sizeof(ed[0]), s2 = m * sizeof(col[0]), s3 = m * sizeof(ri[0]);
+    auto up = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    char *d = nullptr;
+    SG_CUDA_TRY(cudaMalloc(&d, up(s0) + up(s1) + up(s2) + up(s3)));
+    b->dev_args.push_back(d);
+    SG_CUDA_TRY(cudaMemcpy(d, rf.data(), s0, cudaMemcpyHostToDevice));
+    SG_CUDA_TRY(cudaMemcpy(d + up(s0), ed.data(), s1, cudaMemcpyHostToDevice));
+    SG_CUDA_TRY(cudaMemcpy(d + up(s0) + up(s1), col.data(), s2, cudaMemcpyHostToDevice));
+    SG_CUDA_TRY(cudaMemcpy(d + up(s0) + up(s1) + up(s2), ri.data(), s3, cudaMemcpyHostToDevice));
+    g.u = us[0];
+    g.rf = (const sgk::row_fwd_args<T> *)d;
+    g.ed = (const sgk::edge_args<T> *)(d + up(s0));
+    g.col = (const sgk::col_args<T> *)(d + up(s0) + up(s1));
+    g.ri = (const sgk::row_inv_args<T> *)(d + up(s0) + up(s1) + up(s2));
+    g.bs = {m, maxny};
+    g.err = err;
+    return SG_OK;
+}
+
+// One launch per pass for all the group's members.
+template <typename T>
+sg_status group_enqueue(const group_passes<T> &g, cudaStream_t st)
+{
+    const sgk::uniform_passes<T> &u = g.u;
+    if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st, g.ed, g.bs));
+    SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, g.rf, g.bs));
+    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, g.err, st, g.col, g.bs));
+    else SG_TRY(sgk::cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, g.err, st, g.col, g.bs));
+    SG_TRY(sgk::rows_inv<T>(u.px, u.shx[1], u.ri, u.nout, u.twx, st, g.ri, g.bs));
+    return SG_OK;
 }
 
 }  // namespace
@@ -77,6 +154,43 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&events[i], cudaEventDisableTiming);
     }
     sg_status st = e == cudaSuccess ? SG_OK : SG_ECUDA;
+    // groups of single in-plane patches: (precision, Px, Py, central slopes, fields) -> members
+    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
+    for (int i = 0; i < n; ++i) {
+        const sg_plan *p = plans[i];
+        if (!groupable(p)) continue;
+        const bool caller = p->geom.slope_mode == SG_SLOPES_CALLER;
+        const bool central = p->geom.slope_mode == SG_SLOPES_CENTRAL && p->pp[0].phase;
+        groups[std::make_tuple((int)p->prec, p->pp[0].d.px, p->pp[0].d.py, central ? 1 : 0,
+                               caller ? 3 : (p->geom.slope_mode == SG_SLOPES_NONE ? 1 : 3))]
+            .push_back(i);
+    }
+    std::vector<char> grouped(n, 0);
+    std::vector<group_passes<float>> g32;
+    std::vector<group_passes<double>> g64;
+    auto dxp = [&](int i) { return deltax ? deltax[i] : nullptr; };
+    auto dyp = [&](int i) { return deltay ? deltay[i] : nullptr; };
+    for (auto &g : groups) {
+        const std::vector<int> &mem = g.second;
+        if (mem.size() < 2 || st != SG_OK) continue;
+        const int i0 = mem[0];
+        if (plans[i0]->prec == SG_FP64) {
+            std::vector<sgk::uniform_passes<double>> us;
+            for (int i : mem)
+                us.push_back(sgk::uniform_setup<double>(plans[i], &b->ws[i], 0, sigma[i], dxp(i), dyp(i), fx[i], fy[i],
+                                                        nullptr));
+            g64.emplace_back();
+            st = group_upload<double>(b, us, b->ws[i0].err, g64.back());
+        } else {
+            std::vector<sgk::uniform_passes<float>> us;
+            for (int i : mem)
+                us.push_back(sgk::uniform_setup<float>(plans[i], &b->ws[i], 0, sigma[i], dxp(i), dyp(i), fx[i], fy[i],
+                                                       nullptr));
+            g32.emplace_back();
+            st = group_upload<float>(b, us, b->ws[i0].err, g32.back());
+        }
+        for (int i : mem) grouped[i] = 1;
+    }
     bool capturing = false;
     if (st == SG_OK) {
         e = cudaStreamBeginCapture(streams[n], cudaStreamCaptureModeRelaxed);
@@ -84,16 +198,32 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
         if (e == cudaSuccess) e = cudaEventRecord(events[n], streams[n]);
         if (e != cudaSuccess) st = SG_ECUDA;
     }
+    int branch = 0;  // streams[0 .. n) serve groups and single members alike
+    auto fork = [&](cudaStream_t bs) { return cudaStreamWaitEvent(bs, events[n], 0) == cudaSuccess ? SG_OK : SG_ECUDA; };
+    auto join = [&](cudaStream_t bs) {
+        return cudaEventRecord(events[branch], bs) == cudaSuccess &&
+                       cudaStreamWaitEvent(streams[n], events[branch], 0) == cudaSuccess
+                   ? SG_OK
+                   : SG_ECUDA;
+    };
+    for (size_t k = 0; k < g32.size() && st == SG_OK; ++k, ++branch) {
+        st = fork(streams[branch]);
+        if (st == SG_OK) st = group_enqueue<float>(g32[k], streams[branch]);
+        if (st == SG_OK) st = join(streams[branch]);
+    }
+    for (size_t k = 0; k < g64.size() && st == SG_OK; ++k, ++branch) {
+        st = fork(streams[branch]);
+        if (st == SG_OK) st = group_enqueue<double>(g64[k], streams[branch]);
+        if (st == SG_OK) st = join(streams[branch]);
+    }
     for (int i = 0; i < n && st == SG_OK; ++i) {
-        if (cudaStreamWaitEvent(streams[i], events[n], 0) != cudaSuccess) {
-            st = SG_ECUDA;
-            break;
-        }
-        st = sg_force_ws(plans[i], &b->ws[i], sigma[i], deltax ? deltax[i] : nullptr, deltay ? deltay[i] : nullptr,
-                         fx[i], fy[i], streams[i]);
-        if (st == SG_OK && (cudaEventRecord(events[i], streams[i]) != cudaSuccess ||
-                            cudaStreamWaitEvent(streams[n], events[i], 0) != cudaSuccess))
-            st = SG_ECUDA;
+        if (grouped[i]) continue;
+        cudaStream_t bs = streams[branch];
+        st = fork(bs);
+        if (st == SG_OK)
+            st = sg_force_ws(plans[i], &b->ws[i], sigma[i], dxp(i), dyp(i), fx[i], fy[i], bs);
+        if (st == SG_OK) st = join(bs);
+        ++branch;
     }
     if (capturing) {
         cudaGraph_t g = nullptr;

@@ -140,10 +140,10 @@ struct sg_lv {
     int key[SG_MAX_LEVELS][SG_MAX_LEVELS];   // kernel of source level m, target level l
     int key_s[3 * SG_MAX_LEVELS];            // per kernel: source width exponent s
     int key_d2[3 * SG_MAX_LEVELS];           // per kernel: 2 x sample shift (-1, 0, 1)
-    void *spectra;                           // [nkeys][6][px/2+1][py/2+1] T (compressed, see lvconv.cu)
+    void *spectra;                           // [nkeys][6][px/2+1][sg_spec_stride(py)] T (compressed, see lvconv.cu)
     void *phase;                             // exp(i pi k / P), k in [-P/2, P/2], x then y, complex T
     void *cphase;                            // exp(-i pi j / P), j in [0, P], x then y, complex T
-    void *pspectra;                          // potential: [nkeys][3][px/2+1][py/2+1] T, built at the first call
+    void *pspectra;                          // potential: [nkeys][3][px/2+1][sg_spec_stride(py)] T, built at the first call
     int64_t fwd_elems, spec_elems, inv_elems;
 };
 

@@ -74,10 +74,49 @@ __device__ __forceinline__ T field_value(const field_src<T> &s, int f, int j, in
     return (sigma_at(s, j + 1, i) - sigma_at(s, j - 1, i)) * s.inv2h;
 }
 
+// Per-solve arguments of the passes. A kernel instantiated with BATCH = true
+// runs one member of a batch per blockIdx.z, its arguments read from a device
+// array (members of one padded length share the launch; CTAs beyond a member's
+// own row count return at once); with BATCH = false it runs the solve passed by
+// value.
+template <typename T>
+struct row_fwd_args {
+    field_src<T> src;
+    cplx_t<T> *work;
+};
+template <typename T>
+struct col_args {
+    const cplx_t<T> *wf;
+    cplx_t<T> *wi;
+    const T *spec;
+    const cplx_t<T> *edge;   // central slopes: sigma's edge-column transforms
+    const T *phase;          // central slopes: spectral factors
+    int ny;
+};
+template <typename T>
+struct row_inv_args {
+    const cplx_t<T> *wi;
+    T *fx, *fy, *fz;
+    int nx, ny;
+};
+template <typename T>
+struct edge_args {
+    const T *sigma;
+    int nx, ny;
+    cplx_t<T> *edge;
+};
+
+template <bool BATCH, typename A>
+__device__ __forceinline__ A pass_args(const A &one, const A *__restrict__ many)
+{
+    if constexpr (BATCH) return many[blockIdx.z];
+    return one;
+}
+
 // ---------------------------------------------------------------- kernels --
 
-template <typename T, int PX, int NB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T> *__restrict__ work,
+template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const row_fwd_args<T> *__restrict__ many,
                                                      const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
@@ -85,9 +124,13 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(field_src<T> src, cplx_t<T>
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
+    const row_fwd_args<T> args = pass_args<BATCH>(one, many);
+    const field_src<T> &src = args.src;
+    cplx_t<T> *__restrict__ work = args.work;
     const int f = blockIdx.y;
     const int j0 = blockIdx.x * RB;
     const int ny = src.ny;
+    if (BATCH && j0 >= ny) return;
 
     // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
     for (int e = threadIdx.x; e < NB * (PX / 2); e += THREADS) {
@@ -164,12 +207,16 @@ constexpr int col_min_blocks()
     return col_min_blocks_def<T, PY>() * def_threads / THREADS >= 1 ? col_min_blocks_def<T, PY>() * def_threads / THREADS : 1;
 }
 
-template <typename T, int PY, int CB, int THREADS, int NOUT>
-__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv(const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv,
-                                                      const T *__restrict__ spec, int ny, int qx, int nf,
-                                                      const cplx_t<T> *__restrict__ tw, int *err)
+template <typename T, int PY, int CB, int THREADS, int NOUT, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv(col_args<T> one, const col_args<T> *__restrict__ many,
+                                                      int qx, int nf, const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
+    const col_args<T> args = pass_args<BATCH>(one, many);
+    const cplx_t<T> *__restrict__ work_fwd = args.wf;
+    cplx_t<T> *__restrict__ work_inv = args.wi;
+    const T *__restrict__ spec = args.spec;
+    const int ny = args.ny;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
@@ -273,9 +320,8 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     }
 }
 
-template <typename T, int PX, int NB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict__ work_inv, T *__restrict__ fx,
-                                                     T *__restrict__ fy, T *__restrict__ fz, int nx, int ny,
+template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const row_inv_args<T> *__restrict__ many,
                                                      const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
@@ -283,8 +329,13 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
+    const row_inv_args<T> args = pass_args<BATCH>(one, many);
+    const cplx_t<T> *__restrict__ work_inv = args.wi;
+    T *fx = args.fx, *fy = args.fy, *fz = args.fz;
+    const int nx = args.nx, ny = args.ny;
     const int o = blockIdx.y;
     const int j0 = blockIdx.x * RB;
+    if (BATCH && j0 >= ny) return;
     const C *w = work_inv + (int64_t)o * QX * ny;
     T *out = o == 0 ? fx : (o == 1 ? fy : fz);
 
@@ -315,11 +366,15 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(const cplx_t<T> *__restrict
 
 // y-transforms of sigma's first and last columns, packed as z = c0 + i c1:
 // edge[k] = C0(k), edge[PY + k] = C1(k), k < PY.
-template <typename T, int PY, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_edge_cols(const T *__restrict__ sigma, int nx, int ny, cplx_t<T> *__restrict__ edge,
+template <typename T, int PY, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const edge_args<T> *__restrict__ many,
                                                        const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
+    const edge_args<T> args = pass_args<BATCH>(one, many);
+    const T *__restrict__ sigma = args.sigma;
+    const int nx = args.nx, ny = args.ny;
+    cplx_t<T> *__restrict__ edge = args.edge;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     for (int j = threadIdx.x; j < PY / 2; j += THREADS) {  // positions >= PY/2 are zero
@@ -340,13 +395,18 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(const T *__restrict__ sig
 
 // Column pass for central slopes: one forward transform (sigma), the slope
 // spectra formed per bin (see the header comment), two inverse transforms.
-template <typename T, int PY, int CB, int THREADS>
+template <typename T, int PY, int CB, int THREADS, bool BATCH = false>
 __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv_central(
-    const cplx_t<T> *__restrict__ work_fwd, cplx_t<T> *__restrict__ work_inv, const T *__restrict__ spec,
-    const cplx_t<T> *__restrict__ edge, const T *__restrict__ phase, int ny, int qx, const cplx_t<T> *__restrict__ tw,
-    int *err)
+    col_args<T> one, const col_args<T> *__restrict__ many, int qx, const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
+    const col_args<T> args = pass_args<BATCH>(one, many);
+    const cplx_t<T> *__restrict__ work_fwd = args.wf;
+    cplx_t<T> *__restrict__ work_inv = args.wi;
+    const T *__restrict__ spec = args.spec;
+    const cplx_t<T> *__restrict__ edge = args.edge;
+    const T *__restrict__ phase = args.phase;
+    const int ny = args.ny;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
@@ -451,20 +511,96 @@ __host__ __device__ constexpr bool col_feasible_t()
 }
 
 // Dispatchers (explicitly instantiated for float and double in their units).
+// A batch (one launch for `nmem` members of one padded length): `many` is a
+// device array of the members' arguments and `maxny` their largest row count;
+// the by-value arguments are then unused. nmem == 0: the one solve `one`.
+struct batch_shape {
+    int nmem;   // members (0: a single solve)
+    int maxny;  // largest member row count
+};
 template <typename T>
-sg_status rows_fwd(int px, int nb, const field_src<T> &src, cplx_t<T> *work, int nf, const cplx_t<T> *tw,
-                   cudaStream_t st);
+sg_status rows_fwd(int px, int nb, const row_fwd_args<T> &one, int nf, const cplx_t<T> *tw, cudaStream_t st,
+                   const row_fwd_args<T> *many = nullptr, batch_shape bs = {0, 0});
 template <typename T>
-sg_status rows_inv(int px, int nb, const cplx_t<T> *work, T *fx, T *fy, T *fz, int nx, int ny, const cplx_t<T> *tw,
-                   cudaStream_t st);
+sg_status rows_inv(int px, int nb, const row_inv_args<T> &one, int nout, const cplx_t<T> *tw, cudaStream_t st,
+                   const row_inv_args<T> *many = nullptr, batch_shape bs = {0, 0});
 template <typename T>
-sg_status cols(int py, int cb, int nout, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf,
-               const cplx_t<T> *tw, int *err, cudaStream_t st);
+sg_status cols(int py, int cb, int nout, const col_args<T> &one, int qx, int nf, const cplx_t<T> *tw, int *err,
+               cudaStream_t st, const col_args<T> *many = nullptr, batch_shape bs = {0, 0});
 template <typename T>
-sg_status cols_central(int py, int cb, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge,
-                       const T *phase, int ny, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st);
+sg_status cols_central(int py, int cb, const col_args<T> &one, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st,
+                       const col_args<T> *many = nullptr, batch_shape bs = {0, 0});
 template <typename T>
-sg_status edge_cols(int py, const T *sigma, int nx, int ny, cplx_t<T> *edge, const cplx_t<T> *tw, cudaStream_t st);
+sg_status edge_cols(int py, const edge_args<T> &one, const cplx_t<T> *tw, cudaStream_t st,
+                    const edge_args<T> *many = nullptr, batch_shape bs = {0, 0});
+
+// The arguments of every pass of one patch's solve (fftconv.cu), shared by the
+// single solve and by batches (batch.cu). pot_spec != NULL: the potential (one
+// output, three spectrum planes) with the forward scratch wf_pot, slopes formed
+// in the row pass.
+template <typename T>
+struct uniform_passes {
+    row_fwd_args<T> rf;
+    edge_args<T> ed;
+    col_args<T> col;
+    row_inv_args<T> ri;
+    int nf_rows;    // fields the row pass transforms
+    int nf_cols;    // fields of the generic column pass
+    int nout;       // outputs
+    bool central;   // central slopes formed in the spectrum (edge columns, central column pass)
+    int px, py, qx;
+    const cplx_t<T> *twx, *twy;
+    int shx[SG_TUNE_KNOBS], shy[SG_TUNE_KNOBS];  // launch shapes of the x and y lengths (tuning table)
+};
+
+template <typename T>
+inline uniform_passes<T> uniform_setup(const sg_plan *plan, const sg_workspace *ws, int p, const void *sigma,
+                                       const void *dx, const void *dy, void *fx, void *fy, void *fz,
+                                       const T *pot_spec = nullptr, void *wf_pot = nullptr)
+{
+    using C = cplx_t<T>;
+    uniform_passes<T> u;
+    const sg_patch_plan &pp = plan->pp[p];
+    const sg_patch_dev &d = pp.d;
+    const int64_t off = d.cell_off;
+    field_src<T> &src = u.rf.src;
+    src.sigma = (const T *)sigma + off;
+    src.dx = dx ? (const T *)dx + off : nullptr;
+    src.dy = dy ? (const T *)dy + off : nullptr;
+    src.nx = d.nx;
+    src.ny = d.ny;
+    src.inv2h = (T)(0.5 / d.h);
+    src.mode = plan->geom.slope_mode;
+    if (plan->composite) {
+        // AMR or masks: the composite source fields (three planes, zero where no cell exists)
+        const T *S = (const T *)ws->sfield;
+        src.sigma = S + off;
+        src.dx = S + plan->ncells + off;
+        src.dy = S + 2 * plan->ncells + off;
+        src.mode = SG_SLOPES_CALLER;
+    }
+    const int nf = src.mode == SG_SLOPES_NONE ? 1 : 3;
+    u.px = d.px;
+    u.py = d.py;
+    u.qx = d.px / 2 + 1;
+    C *wf = pot_spec ? (C *)wf_pot : (C *)ws->work_fwd;
+    C *wi = (C *)ws->work_inv;
+    const int64_t *twoff = sizeof(T) == 8 ? plan->tw64_off : plan->tw32_off;
+    u.twx = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.px)]);
+    u.twy = (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(d.py)]);
+    u.central = src.mode == SG_SLOPES_CENTRAL && pp.phase && !pot_spec;
+    u.nf_rows = u.central ? 1 : nf;
+    u.nf_cols = nf;
+    u.nout = pot_spec ? 1 : (fz ? 3 : 2);
+    u.rf.work = wf;
+    C *edge = wf + (int64_t)u.qx * d.ny;  // after sigma's row transforms (central slopes)
+    u.ed = {src.sigma, d.nx, d.ny, edge};
+    u.col = {wf, wi, pot_spec ? pot_spec : (const T *)pp.spectra, edge, (const T *)pp.phase, d.ny};
+    u.ri = {wi, (T *)fx + off, pot_spec ? nullptr : (T *)fy + off, fz ? (T *)fz + off : nullptr, d.nx, d.ny};
+    sg_tune_shape(plan->prec, d.px, u.shx);
+    sg_tune_shape(plan->prec, d.py, u.shy);
+    return u;
+}
 
 #define SG_PAD_SWITCH(P, CALL)                 \
     switch (P) {                               \

@@ -1,49 +1,64 @@
 // Column pass of the central-slope convolution (slope spectra formed from
 // sigma's, see fftconv.cuh) with its launch-shape variants, and the edge-column
-// transforms it needs.
+// transforms it needs, for one solve or a batch of solves of one padded length.
 #include "fftconv.cuh"
 
 namespace sgk {
 namespace {
 
-template <typename T, int PY, int CB>
-sg_status launch_cols_central(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge, const T *phase,
-                              int ny, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st)
+template <typename T, int PY, int CB, bool BATCH>
+sg_status launch_cols_central(const col_args<T> &one, const col_args<T> *many, batch_shape bs, int qx,
+                              const cplx_t<T> *tw, int *err, cudaStream_t st)
 {
     constexpr int THREADS = CB * PY / 8;
     const size_t smem = (size_t)col_smem_bytes<T, PY, CB>();
-    auto kern = k_col_conv_central<T, PY, CB, THREADS>;
+    auto kern = k_col_conv_central<T, PY, CB, THREADS, BATCH>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((qx + CB - 1) / CB);
-    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, edge, phase, ny, qx, tw, err);
+    dim3 grid((qx + CB - 1) / CB, 1, BATCH ? bs.nmem : 1);
+    kern<<<grid, THREADS, smem, st>>>(one, many, qx, tw, err);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
+template <typename T, int PY, int CB>
+sg_status launch_cols_central_any(const col_args<T> &one, const col_args<T> *many, batch_shape bs, int qx,
+                                  const cplx_t<T> *tw, int *err, cudaStream_t st)
+{
+    if (many) return launch_cols_central<T, PY, CB, true>(one, many, bs, qx, tw, err, st);
+    return launch_cols_central<T, PY, CB, false>(one, many, bs, qx, tw, err, st);
+}
+
 template <typename T, int PY>
-sg_status cols_central_py(int cb, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge,
-                          const T *phase, int ny, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st)
+sg_status cols_central_py(int cb, const col_args<T> &one, const col_args<T> *many, batch_shape bs, int qx,
+                          const cplx_t<T> *tw, int *err, cudaStream_t st)
 {
     constexpr int D = col_cb_default(PY);
     constexpr int A = shape_candidate(D, 0), C = shape_candidate(D, 2);
-    if (cb == D) return launch_cols_central<T, PY, D>(wf, wi, spec, edge, phase, ny, qx, tw, err, st);
+    if (cb == D) return launch_cols_central_any<T, PY, D>(one, many, bs, qx, tw, err, st);
     if constexpr (col_feasible_t<T, PY, A, 6>()) {
-        if (cb == A) return launch_cols_central<T, PY, A>(wf, wi, spec, edge, phase, ny, qx, tw, err, st);
+        if (cb == A) return launch_cols_central_any<T, PY, A>(one, many, bs, qx, tw, err, st);
     }
     if constexpr (col_feasible_t<T, PY, C, 6>()) {
-        if (cb == C) return launch_cols_central<T, PY, C>(wf, wi, spec, edge, phase, ny, qx, tw, err, st);
+        if (cb == C) return launch_cols_central_any<T, PY, C>(one, many, bs, qx, tw, err, st);
     }
     return SG_EINVAL;
 }
 
 template <typename T, int PY>
-sg_status launch_edge_cols(const T *sigma, int nx, int ny, cplx_t<T> *edge, const cplx_t<T> *tw, cudaStream_t st)
+sg_status launch_edge_cols(const edge_args<T> &one, const edge_args<T> *many, batch_shape bs, const cplx_t<T> *tw,
+                           cudaStream_t st)
 {
     constexpr int THREADS = PY / 8 >= 64 ? PY / 8 : 64;
     const size_t smem = (size_t)spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
-    auto kern = k_edge_cols<T, PY, THREADS>;
-    SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<1, THREADS, smem, st>>>(sigma, nx, ny, edge, tw);
+    if (many) {
+        auto kern = k_edge_cols<T, PY, THREADS, true>;
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<dim3(1, 1, bs.nmem), THREADS, smem, st>>>(one, many, tw);
+    } else {
+        auto kern = k_edge_cols<T, PY, THREADS, false>;
+        SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<1, THREADS, smem, st>>>(one, many, tw);
+    }
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -51,25 +66,28 @@ sg_status launch_edge_cols(const T *sigma, int nx, int ny, cplx_t<T> *edge, cons
 }  // namespace
 
 template <typename T>
-sg_status cols_central(int py, int cb, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, const cplx_t<T> *edge,
-                       const T *phase, int ny, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st)
+sg_status cols_central(int py, int cb, const col_args<T> &one, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st,
+                       const col_args<T> *many, batch_shape bs)
 {
-    SG_PAD_SWITCH(py, return (cols_central_py<T, PP>(cb, wf, wi, spec, edge, phase, ny, qx, tw, err, st)));
+    SG_PAD_SWITCH(py, return (cols_central_py<T, PP>(cb, one, many, bs, qx, tw, err, st)));
     return SG_EINVAL;
 }
 
 template <typename T>
-sg_status edge_cols(int py, const T *sigma, int nx, int ny, cplx_t<T> *edge, const cplx_t<T> *tw, cudaStream_t st)
+sg_status edge_cols(int py, const edge_args<T> &one, const cplx_t<T> *tw, cudaStream_t st, const edge_args<T> *many,
+                    batch_shape bs)
 {
-    SG_PAD_SWITCH(py, return (launch_edge_cols<T, PP>(sigma, nx, ny, edge, tw, st)));
+    SG_PAD_SWITCH(py, return (launch_edge_cols<T, PP>(one, many, bs, tw, st)));
     return SG_EINVAL;
 }
 
-template sg_status cols_central<float>(int, int, const float2 *, float2 *, const float *, const float2 *, const float *,
-                                       int, int, const float2 *, int *, cudaStream_t);
-template sg_status cols_central<double>(int, int, const double2 *, double2 *, const double *, const double2 *,
-                                        const double *, int, int, const double2 *, int *, cudaStream_t);
-template sg_status edge_cols<float>(int, const float *, int, int, float2 *, const float2 *, cudaStream_t);
-template sg_status edge_cols<double>(int, const double *, int, int, double2 *, const double2 *, cudaStream_t);
+template sg_status cols_central<float>(int, int, const col_args<float> &, int, const float2 *, int *, cudaStream_t,
+                                       const col_args<float> *, batch_shape);
+template sg_status cols_central<double>(int, int, const col_args<double> &, int, const double2 *, int *, cudaStream_t,
+                                        const col_args<double> *, batch_shape);
+template sg_status edge_cols<float>(int, const edge_args<float> &, const float2 *, cudaStream_t,
+                                    const edge_args<float> *, batch_shape);
+template sg_status edge_cols<double>(int, const edge_args<double> &, const double2 *, cudaStream_t,
+                                     const edge_args<double> *, batch_shape);
 
 }  // namespace sgk

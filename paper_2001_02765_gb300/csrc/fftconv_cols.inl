@@ -8,33 +8,45 @@
 namespace sgk {
 namespace {
 
-template <typename T, int PY, int CB, int NOUT>
-sg_status launch_cols(const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf, const cplx_t<T> *tw,
-                      int *err, cudaStream_t st)
+template <typename T, int PY, int CB, int NOUT, bool BATCH>
+sg_status launch_cols(const col_args<T> &one, const col_args<T> *many, batch_shape bs, int qx, int nf,
+                      const cplx_t<T> *tw, int *err, cudaStream_t st)
 {
     constexpr int THREADS = CB * PY / 8;
     const size_t smem = (size_t)col_smem_bytes<T, PY, CB, NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6)>();
-    auto kern = k_col_conv<T, PY, CB, THREADS, NOUT>;
+    auto kern = k_col_conv<T, PY, CB, THREADS, NOUT, BATCH>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((qx + CB - 1) / CB);
-    kern<<<grid, THREADS, smem, st>>>(wf, wi, spec, ny, qx, nf, tw, err);
+    dim3 grid((qx + CB - 1) / CB, 1, BATCH ? bs.nmem : 1);
+    kern<<<grid, THREADS, smem, st>>>(one, many, qx, nf, tw, err);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
+// batches are built for the force (two outputs) only
+template <typename T, int PY, int CB, int NOUT>
+sg_status launch_cols_any(const col_args<T> &one, const col_args<T> *many, batch_shape bs, int qx, int nf,
+                          const cplx_t<T> *tw, int *err, cudaStream_t st)
+{
+    if constexpr (NOUT == 2) {
+        if (many) return launch_cols<T, PY, CB, NOUT, true>(one, many, bs, qx, nf, tw, err, st);
+    }
+    if (many) return SG_EINVAL;
+    return launch_cols<T, PY, CB, NOUT, false>(one, many, bs, qx, nf, tw, err, st);
+}
+
 template <typename T, int PY, int NOUT>
-sg_status cols_py(int cb, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf,
+sg_status cols_py(int cb, const col_args<T> &one, const col_args<T> *many, batch_shape bs, int qx, int nf,
                   const cplx_t<T> *tw, int *err, cudaStream_t st)
 {
     constexpr int NPL = NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6);
     constexpr int D = col_cb_default(PY);
     constexpr int A = shape_candidate(D, 0), C = shape_candidate(D, 2);
-    if (cb == D) return launch_cols<T, PY, D, NOUT>(wf, wi, spec, ny, qx, nf, tw, err, st);
+    if (cb == D) return launch_cols_any<T, PY, D, NOUT>(one, many, bs, qx, nf, tw, err, st);
     if constexpr (col_feasible_t<T, PY, A, NPL>()) {
-        if (cb == A) return launch_cols<T, PY, A, NOUT>(wf, wi, spec, ny, qx, nf, tw, err, st);
+        if (cb == A) return launch_cols_any<T, PY, A, NOUT>(one, many, bs, qx, nf, tw, err, st);
     }
     if constexpr (col_feasible_t<T, PY, C, NPL>()) {
-        if (cb == C) return launch_cols<T, PY, C, NOUT>(wf, wi, spec, ny, qx, nf, tw, err, st);
+        if (cb == C) return launch_cols_any<T, PY, C, NOUT>(one, many, bs, qx, nf, tw, err, st);
     }
     return SG_EINVAL;
 }
@@ -42,18 +54,17 @@ sg_status cols_py(int cb, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int
 }  // namespace
 
 template <typename T>
-sg_status cols(int py, int cb, int nout, const cplx_t<T> *wf, cplx_t<T> *wi, const T *spec, int ny, int qx, int nf,
-               const cplx_t<T> *tw, int *err, cudaStream_t st)
+sg_status cols(int py, int cb, int nout, const col_args<T> &one, int qx, int nf, const cplx_t<T> *tw, int *err,
+               cudaStream_t st, const col_args<T> *many, batch_shape bs)
 {
     if (nout == 1) {
-        SG_PAD_SWITCH(py, return (cols_py<T, PP, 1>(cb, wf, wi, spec, ny, qx, nf, tw, err, st)));
+        SG_PAD_SWITCH(py, return (cols_py<T, PP, 1>(cb, one, many, bs, qx, nf, tw, err, st)));
     } else if (nout == 2) {
-        SG_PAD_SWITCH(py, return (cols_py<T, PP, 2>(cb, wf, wi, spec, ny, qx, nf, tw, err, st)));
+        SG_PAD_SWITCH(py, return (cols_py<T, PP, 2>(cb, one, many, bs, qx, nf, tw, err, st)));
     } else if (nout == 3) {
-        SG_PAD_SWITCH(py, return (cols_py<T, PP, 3>(cb, wf, wi, spec, ny, qx, nf, tw, err, st)));
+        SG_PAD_SWITCH(py, return (cols_py<T, PP, 3>(cb, one, many, bs, qx, nf, tw, err, st)));
     }
     return SG_EINVAL;
 }
-
 
 }  // namespace sgk

@@ -2,6 +2,6 @@
 #include "fftconv_cols.inl"
 
 namespace sgk {
-template sg_status cols<float>(int, int, int, const float2 *, float2 *, const float *, int, int, int, const float2 *,
-                               int *, cudaStream_t);
+template sg_status cols<float>(int, int, int, const col_args<float> &, int, int, const float2 *, int *, cudaStream_t,
+                               const col_args<float> *, batch_shape);
 }  // namespace sgk

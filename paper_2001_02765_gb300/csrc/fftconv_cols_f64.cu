@@ -2,6 +2,6 @@
 #include "fftconv_cols.inl"
 
 namespace sgk {
-template sg_status cols<double>(int, int, int, const double2 *, double2 *, const double *, int, int, int,
-                                const double2 *, int *, cudaStream_t);
+template sg_status cols<double>(int, int, int, const col_args<double> &, int, int, const double2 *, int *,
+                                cudaStream_t, const col_args<double> *, batch_shape);
 }  // namespace sgk

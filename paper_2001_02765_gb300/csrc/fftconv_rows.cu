@@ -1,33 +1,45 @@
 // Forward row pass of the uniform-patch convolution (R2C with the fields
-// formed) and its launch-shape variants.
+// formed) and its launch-shape variants, for one solve or a batch of solves of
+// one padded length.
 #include "fftconv.cuh"
 
 namespace sgk {
 namespace {
 
-template <typename T, int PX, int NB>
-sg_status launch_rows_fwd(const field_src<T> &src, cplx_t<T> *work, int nf, const cplx_t<T> *tw, cudaStream_t st)
+template <typename T, int PX, int NB, bool BATCH>
+sg_status launch_rows_fwd(const row_fwd_args<T> &one, const row_fwd_args<T> *many, batch_shape bs, int nf,
+                          const cplx_t<T> *tw, cudaStream_t st)
 {
     const size_t smem = (size_t)spad_size<cplx_t<T>>(NB * PX) * sizeof(cplx_t<T>);
-    auto kern = k_row_fwd<T, PX, NB, ROW_THREADS>;
+    auto kern = k_row_fwd<T, PX, NB, ROW_THREADS, BATCH>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((src.ny + 2 * NB - 1) / (2 * NB), nf);
-    kern<<<grid, ROW_THREADS, smem, st>>>(src, work, tw);
+    const int ny = BATCH ? bs.maxny : one.src.ny;
+    dim3 grid((ny + 2 * NB - 1) / (2 * NB), nf, BATCH ? bs.nmem : 1);
+    kern<<<grid, ROW_THREADS, smem, st>>>(one, many, tw);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
+template <typename T, int PX, int NB>
+sg_status launch_rows_fwd_any(const row_fwd_args<T> &one, const row_fwd_args<T> *many, batch_shape bs, int nf,
+                              const cplx_t<T> *tw, cudaStream_t st)
+{
+    if (many) return launch_rows_fwd<T, PX, NB, true>(one, many, bs, nf, tw, st);
+    return launch_rows_fwd<T, PX, NB, false>(one, many, bs, nf, tw, st);
+}
+
 template <typename T, int PX>
-sg_status rows_fwd_px(int nb, const field_src<T> &src, cplx_t<T> *work, int nf, const cplx_t<T> *tw, cudaStream_t st)
+sg_status rows_fwd_px(int nb, const row_fwd_args<T> &one, const row_fwd_args<T> *many, batch_shape bs, int nf,
+                      const cplx_t<T> *tw, cudaStream_t st)
 {
     constexpr int D = row_nb_default(PX);
     constexpr int A = shape_candidate(D, 0), C = shape_candidate(D, 2);
-    if (nb == D) return launch_rows_fwd<T, PX, D>(src, work, nf, tw, st);
+    if (nb == D) return launch_rows_fwd_any<T, PX, D>(one, many, bs, nf, tw, st);
     if constexpr (row_feasible_t<T>(PX, A)) {
-        if (nb == A) return launch_rows_fwd<T, PX, A>(src, work, nf, tw, st);
+        if (nb == A) return launch_rows_fwd_any<T, PX, A>(one, many, bs, nf, tw, st);
     }
     if constexpr (row_feasible_t<T>(PX, C)) {
-        if (nb == C) return launch_rows_fwd<T, PX, C>(src, work, nf, tw, st);
+        if (nb == C) return launch_rows_fwd_any<T, PX, C>(one, many, bs, nf, tw, st);
     }
     return SG_EINVAL;
 }
@@ -35,14 +47,16 @@ sg_status rows_fwd_px(int nb, const field_src<T> &src, cplx_t<T> *work, int nf, 
 }  // namespace
 
 template <typename T>
-sg_status rows_fwd(int px, int nb, const field_src<T> &src, cplx_t<T> *work, int nf, const cplx_t<T> *tw,
-                   cudaStream_t st)
+sg_status rows_fwd(int px, int nb, const row_fwd_args<T> &one, int nf, const cplx_t<T> *tw, cudaStream_t st,
+                   const row_fwd_args<T> *many, batch_shape bs)
 {
-    SG_PAD_SWITCH(px, return (rows_fwd_px<T, PP>(nb, src, work, nf, tw, st)));
+    SG_PAD_SWITCH(px, return (rows_fwd_px<T, PP>(nb, one, many, bs, nf, tw, st)));
     return SG_EINVAL;
 }
 
-template sg_status rows_fwd<float>(int, int, const field_src<float> &, float2 *, int, const float2 *, cudaStream_t);
-template sg_status rows_fwd<double>(int, int, const field_src<double> &, double2 *, int, const double2 *, cudaStream_t);
+template sg_status rows_fwd<float>(int, int, const row_fwd_args<float> &, int, const float2 *, cudaStream_t,
+                                   const row_fwd_args<float> *, batch_shape);
+template sg_status rows_fwd<double>(int, int, const row_fwd_args<double> &, int, const double2 *, cudaStream_t,
+                                    const row_fwd_args<double> *, batch_shape);
 
 }  // namespace sgk

@@ -129,7 +129,8 @@ __global__ void k_lv_tables(double2 *z, int px, int py, int s, int d2)
 // ky <= Py/2 and sy ph_x(kx) ph_y(ky - Py) H(kx, Py - ky) above, ph(k) = exp(i pi d2 k / P).
 // Planes x0 xx xy y0 yx yy have (sx, sy) = (-,+) (+,+) (-,-) (+,-) (-,-) (+,+); the
 // imaginary ones (x0, y0) store Im H, the others Re H, [kx][ky] for kx in [0, px/2],
-// ky in [0, py/2], scaled by 1 / (px py) and by G (x0, y0) or G h_f (the order-1 planes).
+// ky in [0, py/2] (rows padded to sg_spec_stride(py) entries, 16-byte aligned for bulk
+// copies), scaled by 1 / (px py) and by G (x0, y0) or G h_f (the order-1 planes).
 __host__ __device__ constexpr bool lv_plane_imag(int p) { return p == 0 || p == 3; }
 
 // Unpack the transforms of the packed pairs (A + i B: A^(k) = (Z(k) + conj Z(-k)) / 2,
@@ -138,11 +139,15 @@ __host__ __device__ constexpr bool lv_plane_imag(int p) { return p == 0 || p == 
 template <typename T>
 __global__ void k_lv_extract(const double2 *z, T *out, int px, int py, int d2, double sc0, double sc1)
 {
-    const int qx = px / 2 + 1, qy = py / 2 + 1;
-    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
+    const int qx = px / 2 + 1, qy = py / 2 + 1, qs = sg_spec_stride(py);
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qs;
     const double inv = 1.0 / ((double)px * (double)py);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(e / qy), ky = (int)(e % qy);
+        const int kx = (int)(e / qs), ky = (int)(e % qs);
+        if (ky >= qy) {  // row padding
+            for (int q = 0; q < 6; ++q) out[q * qplane + e] = (T)0;
+            continue;
+        }
         const int64_t ip = (int64_t)ky * px + kx;
         const int64_t im = (int64_t)((py - ky) % py) * px + (px - kx) % px;
         double sn, cs;  // exp(-i pi d2 (kx/px + ky/py))
@@ -185,16 +190,20 @@ __global__ void k_lv_tables_pot(double2 *z, int px, int py, int s, int d2)
 }
 
 // Compressed potential spectra: planes p0 (Re H, even-even), px (Im H, odd in x)
-// and py (Im H, odd in y), [kx][ky] for kx in [0, px/2], ky in [0, py/2], scaled by
-// 1 / (px py) and by sc0 (p0) or sc1 (px, py).
+// and py (Im H, odd in y), [kx][ky] for kx in [0, px/2], ky in [0, py/2] (rows padded
+// to sg_spec_stride(py)), scaled by 1 / (px py) and by sc0 (p0) or sc1 (px, py).
 template <typename T>
 __global__ void k_lv_extract_pot(const double2 *z, T *out, int px, int py, int d2, double sc0, double sc1)
 {
-    const int qx = px / 2 + 1, qy = py / 2 + 1;
-    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qy;
+    const int qx = px / 2 + 1, qy = py / 2 + 1, qs = sg_spec_stride(py);
+    const int64_t plane = (int64_t)px * py, qplane = (int64_t)qx * qs;
     const double inv = 1.0 / ((double)px * (double)py);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qplane; e += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(e / qy), ky = (int)(e % qy);
+        const int kx = (int)(e / qs), ky = (int)(e % qs);
+        if (ky >= qy) {  // row padding
+            out[e] = out[qplane + e] = out[2 * qplane + e] = (T)0;
+            continue;
+        }
         const int64_t ip = (int64_t)ky * px + kx;
         const int64_t im = (int64_t)((py - ky) % py) * px + (px - kx) % px;
         double sn, cs;  // exp(-i pi d2 (kx/px + ky/py))
@@ -421,6 +430,81 @@ struct lv_mac_args {
     int qx;
 };
 
+// The compact source column of column kx for source level m: kx mod Pcx, or its
+// Hermitian partner (fold), with the sign of the x half-shift.
+struct lv_src_col {
+    int lpy, pcy;
+    bool fold, hy, xneg;
+    int col;        // compact column index
+    int64_t splane; // field plane stride of the source's compact spectra
+};
+
+__device__ __forceinline__ lv_src_col lv_source_column(const lv_mac_args &a, int m, int kx)
+{
+    lv_src_col c;
+    const int lpx = a.lpx[m], pcx = 1 << lpx;
+    c.lpy = a.lpy[m];
+    c.pcy = 1 << c.lpy;
+    const int kxr = kx & (pcx - 1);
+    c.fold = kxr > (pcx >> 1);
+    c.col = c.fold ? pcx - kxr : kxr;
+    c.splane = (int64_t)((pcx >> 1) + 1) * c.pcy;
+    c.hy = a.hy[m] != 0;
+    // sign of the x half-shift: (-1)^(kx div Pcx), times -1 on the folded half
+    c.xneg = a.hx[m] && ((((kx >> lpx) & 1) != 0) != c.fold);
+    return c;
+}
+
+// Row of bin ky in the compact column, and the sign of the half-shifts there.
+__device__ __forceinline__ void lv_source_row(const lv_src_col &c, int ky, int &row, bool &neg)
+{
+    const int kyr = ky & (c.pcy - 1);
+    row = c.fold ? ((c.pcy - kyr) & (c.pcy - 1)) : kyr;
+    neg = c.xneg != (c.hy && ((((ky >> c.lpy) & 1) != 0) != (c.fold && kyr != 0)));
+}
+
+// One bin of one source: the three fields X0..X2 (conjugated on the folded
+// half) times the kernel planes g (x family, or the potential's p0 px py) and h
+// (y family), sg = -1 on the upper half for the planes odd in ky, half-cell
+// phase p when d2 != 0, added into ax (and ay) with the half-shift sign.
+template <typename T, int NOUT>
+__device__ __forceinline__ void lv_mac_bin(cplx_t<T> X0, cplx_t<T> X1, cplx_t<T> X2, bool fold, T g0, T g1, T g2,
+                                           T h0, T h1, T h2, T sg, cplx_t<T> p, int d2, bool neg, cplx_t<T> &ax,
+                                           cplx_t<T> &ay)
+{
+    using C = cplx_t<T>;
+    if (fold) {
+        X0.y = -X0.y;
+        X1.y = -X1.y;
+        X2.y = -X2.y;
+    }
+    if constexpr (NOUT == 2) {
+        // planes (prescaled by G, G h_f): x0 imaginary, xx real, xy real; y0 imaginary,
+        // yx real, yy real. The parts odd in ky (xy; y0, yx) change sign on the upper half.
+        const T o2 = sg * g2, o0 = sg * h0, o1 = sg * h1;
+        C hx = cmake<C>(g1 * X1.x - g0 * X0.y + o2 * X2.x, g1 * X1.y + g0 * X0.x + o2 * X2.y);
+        C hy = cmake<C>(h2 * X2.x - o0 * X0.y + o1 * X1.x, h2 * X2.y + o0 * X0.x + o1 * X1.y);
+        if (d2 != 0) {
+            if (d2 < 0) p.y = -p.y;
+            hx = cmul(hx, p);
+            hy = cmul(hy, p);
+        }
+        const T sn = neg ? (T)-1 : (T)1;
+        ax = cmake<C>(ax.x + sn * hx.x, ax.y + sn * hx.y);
+        ay = cmake<C>(ay.x + sn * hy.x, ay.y + sn * hy.y);
+    } else {
+        // potential planes: p0 real, px imaginary, py imaginary and odd in ky
+        const T o2 = sg * g2;
+        C hp = cmake<C>(g0 * X0.x - g1 * X1.y - o2 * X2.y, g0 * X0.y + g1 * X1.x + o2 * X2.x);
+        if (d2 != 0) {
+            if (d2 < 0) p.y = -p.y;
+            hp = cmul(hp, p);
+        }
+        const T sn = neg ? (T)-1 : (T)1;
+        ax = cmake<C>(ax.x + sn * hp.x, ax.y + sn * hp.y);
+    }
+}
+
 // One (column kx, target level l) per CTA, kx = blockIdx.x / nsrc and
 // l = blockIdx.x % nsrc, so that the CTAs of all target levels of a column run
 // side by side and read its source spectra (and shared kernel planes) from L2:
@@ -442,9 +526,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *bx = reinterpret_cast<C *>(smem_raw);
     C *by = bx + spad_size<C>(PY);
-    constexpr int QY = PY / 2 + 1;
+    constexpr int QS = ((PY / 2 + 1) + 3) & ~3;  // kernel plane row stride (sg_spec_stride)
     const int kx = blockIdx.x / a.nsrc, l = blockIdx.x % a.nsrc;
-    const int64_t kqplane = (int64_t)a.qx * QY;
+    const int64_t kqplane = (int64_t)a.qx * QS;
     constexpr int NPL = NOUT == 2 ? 6 : 3;  // kernel planes per key
     // Bins in mirror pairs: slot j in [0, PY/2) holds bins j and PY - j, which read
     // the same kernel values (kq = j); slot 0 holds bins 0 and PY/2 (kq = 0 and PY/2).
@@ -468,26 +552,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
             for (int b = 0; b < 2; ++b) ax[v][b] = ay[v][b] = cmake<C>((T)0, (T)0);
         }
         for (int m = 0; m < a.nsrc; ++m) {
-            // compact column of this kx: kx mod Pcx, or its Hermitian partner
-            const int lpx = a.lpx[m], lpy = a.lpy[m], pcx = 1 << lpx, pcy = 1 << lpy;
-            const int kxr = kx & (pcx - 1);
-            const bool fold = kxr > (pcx >> 1);
-            const int64_t splane = (int64_t)((pcx >> 1) + 1) * pcy;
-            const C *sm = spec + a.spec_off[m] + (int64_t)(fold ? pcx - kxr : kxr) * pcy;
-            const bool hy = a.hy[m] != 0;
-            // sign of the x half-shift: (-1)^(kx div Pcx), times -1 on the folded half
-            const bool xneg = a.hx[m] && ((((kx >> lpx) & 1) != 0) != fold);
-            const T *km = kspec + (int64_t)a.key[m][l] * NPL * kqplane + (int64_t)kx * QY;
+            const lv_src_col sc = lv_source_column(a, m, kx);
+            const int64_t splane = sc.splane;
+            const C *sm = spec + a.spec_off[m] + (int64_t)sc.col * sc.pcy;
+            const T *km = kspec + (int64_t)a.key[m][l] * NPL * kqplane + (int64_t)kx * QS;
             int row[V][2];
             bool neg[V][2];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int k = ky[v][b], kyr = k & (pcy - 1);
-                    row[v][b] = fold ? ((pcy - kyr) & (pcy - 1)) : kyr;
-                    neg[v][b] = xneg != (hy && ((((k >> lpy) & 1) != 0) != (fold && kyr != 0)));
-                }
+                for (int b = 0; b < 2; ++b) lv_source_row(sc, ky[v][b], row[v][b], neg[v][b]);
             }
             C X[3][V][2];
             T gx[3][V][2], gy[3][V][2];
@@ -514,42 +588,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
             for (int v = 0; v < V; ++v) {
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    C X0 = X[0][v][b], X1 = X[1][v][b], X2 = X[2][v][b];
-                    if (fold) {
-                        X0.y = -X0.y;
-                        X1.y = -X1.y;
-                        X2.y = -X2.y;
-                    }
-                    // planes (prescaled by G, G h_f): x0 imaginary, xx real, xy real; y0 imaginary,
-                    // yx real, yy real. The parts odd in ky (xy; y0, yx) change sign on the upper half.
-                    const T g0 = gx[0][v][b], g1 = gx[1][v][b], g2 = gx[2][v][b];
                     const T sg = (b == 0 || ky[v][1] == PY / 2) ? (T)1 : (T)-1;
-                    if constexpr (NOUT == 2) {
-                        const T h0 = gy[0][v][b], h1 = gy[1][v][b], h2 = gy[2][v][b];
-                        const T o2 = sg * g2, o0 = sg * h0, o1 = sg * h1;
-                        C hx = cmake<C>(g1 * X1.x - g0 * X0.y + o2 * X2.x, g1 * X1.y + g0 * X0.x + o2 * X2.y);
-                        C hy = cmake<C>(h2 * X2.x - o0 * X0.y + o1 * X1.x, h2 * X2.y + o0 * X0.x + o1 * X1.y);
-                        if (d2 != 0) {
-                            C p = ph[v][b];
-                            if (d2 < 0) p.y = -p.y;
-                            hx = cmul(hx, p);
-                            hy = cmul(hy, p);
-                        }
-                        const T sn = neg[v][b] ? (T)-1 : (T)1;
-                        ax[v][b] = cmake<C>(ax[v][b].x + sn * hx.x, ax[v][b].y + sn * hx.y);
-                        ay[v][b] = cmake<C>(ay[v][b].x + sn * hy.x, ay[v][b].y + sn * hy.y);
-                    } else {
-                        // potential planes: p0 real, px imaginary, py imaginary and odd in ky
-                        const T o2 = sg * g2;
-                        C hp = cmake<C>(g0 * X0.x - g1 * X1.y - o2 * X2.y, g0 * X0.y + g1 * X1.x + o2 * X2.x);
-                        if (d2 != 0) {
-                            C p = ph[v][b];
-                            if (d2 < 0) p.y = -p.y;
-                            hp = cmul(hp, p);
-                        }
-                        const T sn = neg[v][b] ? (T)-1 : (T)1;
-                        ax[v][b] = cmake<C>(ax[v][b].x + sn * hp.x, ax[v][b].y + sn * hp.y);
-                    }
+                    if constexpr (NOUT == 2)
+                        lv_mac_bin<T, 2>(X[0][v][b], X[1][v][b], X[2][v][b], sc.fold, gx[0][v][b], gx[1][v][b],
+                                         gx[2][v][b], gy[0][v][b], gy[1][v][b], gy[2][v][b], sg, ph[v][b], d2,
+                                         neg[v][b], ax[v][b], ay[v][b]);
+                    else
+                        lv_mac_bin<T, 1>(X[0][v][b], X[1][v][b], X[2][v][b], sc.fold, gx[0][v][b], gx[1][v][b],
+                                         gx[2][v][b], (T)0, (T)0, (T)0, sg, ph[v][b], d2, neg[v][b], ax[v][b],
+                                         ay[v][b]);
                 }
             }
         }
@@ -898,7 +945,7 @@ sg_status sg_lv_setup(sg_plan *plan, const sg_lv_setup_args *a)
         }
     }
     const size_t rs = cs / 2;  // real element
-    const int64_t qplane = (int64_t)qx * (a->py / 2 + 1);
+    const int64_t qplane = (int64_t)qx * sg_spec_stride(a->py);
     cudaError_t e = cudaMalloc(&lv->spectra, (size_t)lv->nkeys * 6 * qplane * rs);
     if (e == cudaSuccess) e = cudaMalloc(&lv->phase, (size_t)(a->px + a->py + 2) * cs);
     if (e == cudaSuccess) e = cudaMalloc(&lv->cphase, (size_t)(a->px + a->py + 2) * cs);
@@ -961,7 +1008,7 @@ sg_status sg_lv_potential_spectra_build(sg_plan *plan)
     if (lv->pspectra) return SG_OK;
     const int px = lv->px, py = lv->py;
     const size_t rs = plan->prec == SG_FP64 ? sizeof(double) : sizeof(float);
-    const int64_t qplane = (int64_t)(px / 2 + 1) * (py / 2 + 1), plane = (int64_t)px * py;
+    const int64_t qplane = (int64_t)(px / 2 + 1) * sg_spec_stride(py), plane = (int64_t)px * py;
     void *spec = nullptr;
     double2 *z = nullptr;
     cudaError_t e = cudaMalloc(&spec, (size_t)lv->nkeys * 3 * qplane * rs);

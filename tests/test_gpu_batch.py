@@ -62,3 +62,40 @@ def test_batch_argument_errors(sg):
     with pytest.raises(sg.SgError) as e:
         sg.sg_batch_create([0], [0], [0], [0], [0], [0])
     assert e.value.status == sg.SG_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batch_groups_equal_individual_solves(sg, prec, mode):
+    """Members of one padded length share each pass's launch (slope modes none,
+    central, caller; both precisions); results equal sg_force bit for bit,
+    including members whose row counts differ within a group."""
+    import torch
+    dt = np.float64 if prec == "fp64" else np.float32
+    ns = [33, 40, 47, 64, 20, 30, 90, 100, 128, 17]  # padded lengths 128, 128, 128, 128, 64, 64, 256, 256, 256, 64
+    rng = np.random.Generator(np.random.PCG64(40 + mode))
+    plans, ins, outs, refs = [], [], [], []
+    for n in ns:
+        nx, ny = n, max(1, n - int(rng.integers(0, 8)))  # ragged rows
+        plan = sg.Plan([(0, nx, ny, -1.0, -1.0, 2.0 / n)], precision=prec, slope_mode=mode)
+        s, sx, sy = W.random_fields(ny, nx, seed=int(rng.integers(0, 1 << 30)))
+        i = (concat_dev([s], dt), concat_dev([sx], dt) if mode == 2 else None,
+             concat_dev([sy], dt) if mode == 2 else None)
+        rx, ry = plan.force(*i)
+        torch.cuda.synchronize()
+        refs.append((rx.clone(), ry.clone()))
+        plans.append(plan)
+        ins.append(i)
+        outs.append((torch.full_like(i[0], float("nan")), torch.full_like(i[0], float("nan"))))
+    ptr = lambda t: t.data_ptr() if t is not None else 0
+    batch = sg.sg_batch_create([p.handle for p in plans], [ptr(i[0]) for i in ins], [ptr(i[1]) for i in ins],
+                               [ptr(i[2]) for i in ins], [ptr(o[0]) for o in outs], [ptr(o[1]) for o in outs])
+    try:
+        sg.sg_batch_launch(batch, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        for o, r in zip(outs, refs):
+            assert torch.equal(o[0], r[0]) and torch.equal(o[1], r[1])
+    finally:
+        sg.sg_batch_destroy(batch)
+        for p in plans:
+            p.close()
