@@ -258,6 +258,7 @@ def run_batch(args):
     plans, ins, outs = build("fp32")
     batch = sg.sg_batch_create([p.handle for p in plans], [i.data_ptr() for i in ins], [0] * len(ins), [0] * len(ins),
                                [o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs])
+    batch_launches = sg.sg_batch_launches(batch)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -285,6 +286,28 @@ def run_batch(args):
         per = timed(graph, args.steps)
     per_seq = timed(one_by_one, args.steps)
     value, total_ms, solves = job_rate(sum(per), args.steps * len(plans))
+    # end to end: every member's sigma copied in from pinned host memory, the
+    # graph, every Fx, Fy copied back, all in the timed region
+    hin = [i.cpu().pin_memory() for i in ins]
+    hout = [(torch.empty_like(o[0], device="cpu").pin_memory(), torch.empty_like(o[1], device="cpu").pin_memory())
+            for o in outs]
+    e2e_ms = 0.0
+    for k in range(args.steps + 2):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i, h in zip(ins, hin):
+                i.copy_(h, non_blocking=True)
+            graph()
+            for o, h in zip(outs, hout):
+                h[0].copy_(o[0], non_blocking=True)
+                h[1].copy_(o[1], non_blocking=True)
+        stream.synchronize()
+        if k >= 2:
+            e2e_ms += 1e3 * (time.perf_counter() - t0)
+    h2d = sum(i.numel() * 4 for i in ins)
+    d2h = 2 * h2d
     # FP64 plain per-solve path and the FP32 error against it
     plans64, ins64, outs64 = build("fp64")
     for p, i, o in zip(plans64, ins64, outs64):
@@ -316,10 +339,31 @@ def run_batch(args):
         "one_by_one": {"solves_per_s": len(ns) * args.steps / (sum(per_seq) / 1e3)},
         "fp64_plain": {"solves_per_s": len(ns) * n64 / (sum(per64) / 1e3)},
         "rel_err_vs_fp64": float(np.sqrt(num / den)),
-        "gpu_launches": args.steps * 3 * len(ns),
+        "e2e": {"value": args.steps * len(ns) * world / (e2e_ms / 1e3), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": batch_roofline(ns, total_ms / args.steps),
+        "gpu_launches": args.steps * batch_launches,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def batch_roofline(ns, ms_per_batch):
+    """Whole-step roofline of a batch (every pass of every member; the batch has
+    no per-stage timers): conventional FFT flops and algorithmic bytes of the
+    spiral members (central slopes, FP32) against the FP32 and HBM peaks."""
+    hbm_peak, hbm_src, fp32_peak, fp32_src = _peaks()
+    flops = sum(algorithmic_flops({"patches": [(0, int(n), int(n))], "slope_mode": 1}, {}, st)
+                for n in ns for st in ("row_fwd", "col_conv", "row_inv"))
+    alg = sum(algorithmic_bytes({"patches": [(0, int(n), int(n))], "slope_mode": 1}, {}, st)
+              for n in ns for st in ("row_fwd", "col_conv", "row_inv"))
+    secs = ms_per_batch * 1e-3
+    tflops = flops / secs / 1e12
+    return {"kernel": "batch (all passes of all members, one graph)", "bound": "alu", "achieved": tflops,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": None,
+            "algorithmic_flops": flops, "peak_source": fp32_src,
+            "hbm": {"algorithmic_bytes": alg, "achieved_gbs": alg / secs / 1e9, "peak_gbs": hbm_peak,
+                    "frac": alg / secs / 1e9 / hbm_peak, "peak_source": hbm_src}}
 
 
 # ------------------------------------------------------------ serving run --

@@ -416,6 +416,10 @@ sg_status sg_batch_launch(sg_batch *batch, void *stream);
 /* Release the batch's graph and workspaces (synchronises the device). NULL is a no-op. */
 sg_status sg_batch_destroy(sg_batch *batch);
 
+/* Kernel launches one sg_batch_launch replays (members of one padded length
+ * share each pass's launch). Errors: SG_EINVAL (NULL batch or out). */
+sg_status sg_batch_launches(const sg_batch *batch, int *out);
+
 /* ------------------------------------------------------------------------
  * Request server (continuous batching on one GPU; not in the paper).
  *

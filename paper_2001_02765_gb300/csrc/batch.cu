@@ -27,6 +27,7 @@ struct sg_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
+    int launches = 0;  // kernels per replay
 };
 
 namespace {
@@ -210,11 +211,13 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
         st = fork(streams[branch]);
         if (st == SG_OK) st = group_enqueue<float>(g32[k], streams[branch]);
         if (st == SG_OK) st = join(streams[branch]);
+        b->launches += g32[k].u.central ? 4 : 3;
     }
     for (size_t k = 0; k < g64.size() && st == SG_OK; ++k, ++branch) {
         st = fork(streams[branch]);
         if (st == SG_OK) st = group_enqueue<double>(g64[k], streams[branch]);
         if (st == SG_OK) st = join(streams[branch]);
+        b->launches += g64[k].u.central ? 4 : 3;
     }
     for (int i = 0; i < n && st == SG_OK; ++i) {
         if (grouped[i]) continue;
@@ -223,6 +226,7 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
         if (st == SG_OK)
             st = sg_force_ws(plans[i], &b->ws[i], sigma[i], dxp(i), dyp(i), fx[i], fy[i], bs);
         if (st == SG_OK) st = join(bs);
+        b->launches += plans[i]->launches;
         ++branch;
     }
     if (capturing) {
@@ -264,6 +268,13 @@ sg_status sg_batch_launch(sg_batch *b, void *stream)
 sg_status sg_batch_destroy(sg_batch *b)
 {
     batch_free(b);
+    return SG_OK;
+}
+
+sg_status sg_batch_launches(const sg_batch *b, int *out)
+{
+    if (!b || !out) return SG_EINVAL;
+    *out = b->launches;
     return SG_OK;
 }
 

@@ -94,6 +94,7 @@ _SIGNATURES = {
                                        ctypes.POINTER(_VP)]),
     "sg_batch_launch": (ctypes.c_int, [_VP, _VP]),
     "sg_batch_destroy": (ctypes.c_int, [_VP]),
+    "sg_batch_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "sg_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
     "sg_server_destroy": (ctypes.c_int, [_VP]),
     "sg_submit": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
@@ -283,6 +284,13 @@ def sg_batch_launch(batch, stream_ptr=0):
 def sg_batch_destroy(batch):
     if batch:
         _check(load().sg_batch_destroy(batch), "sg_batch_destroy")
+
+
+def sg_batch_launches(batch):
+    """Kernel launches one sg_batch_launch replays."""
+    n = ctypes.c_int(0)
+    _check(load().sg_batch_launches(batch, ctypes.byref(n)), "sg_batch_launches")
+    return n.value
 
 
 def sg_server_create(hbm_budget=0, max_inflight=8):
