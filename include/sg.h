@@ -231,9 +231,12 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
                        void *stream);
 
 /*
- * The same solve with HOST buffers: copies the inputs to the plan's device
- * staging buffers, runs sg_force on `stream`, copies Fx, Fy back and waits for
- * the stream. Host buffers may be pageable or pinned (pinned is faster).
+ * The same solve with HOST buffers, waiting for `stream` before it returns:
+ * the inputs are copied to the plan's device staging buffers and sg_force runs
+ * on `stream`. Fx, Fy are copied back, or, for a single in-plane patch whose
+ * Fx, Fy buffers are page-locked (pinned, so mapped into the device address
+ * space), written in place by the inverse row pass over the CPU-GPU link.
+ * Host buffers may be pageable or pinned.
  * Errors: as sg_force, plus SG_ENOMEM if the staging buffers cannot be allocated.
  */
 sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,

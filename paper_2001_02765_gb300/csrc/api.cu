@@ -986,6 +986,17 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
                                 (cudaStream_t)stream);
 }
 
+// The device address of a page-locked host buffer, or NULL for other memory.
+static const void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
                         void *stream)
 {
@@ -995,6 +1006,16 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
     int dev = -1;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != plan->device) return fail("the plan's device is not current");
+    cudaStream_t st = (cudaStream_t)stream;
+    // Pinned output buffers are mapped into the device address space: for a
+    // single in-plane patch the inverse row pass writes Fx, Fy there in place
+    // (streaming writes over the CPU-GPU link) instead of a copy after the solve.
+    void *hfx = nullptr, *hfy = nullptr;
+    if (!plan->composite && plan->geom.z == 0.0) {
+        hfx = (void *)mapped_host(fx);
+        hfy = (void *)mapped_host(fy);
+        if (!hfx || !hfy) hfx = hfy = nullptr;
+    }
     const size_t bytes = (size_t)plan->ncells * elem_size(plan->prec);
     if (!plan->stage_in) {
         SG_TRY(dev_alloc(plan, &plan->stage_in, 3 * bytes));
@@ -1007,16 +1028,20 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
         }
         plan->stage_bytes = bytes;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     char *in = (char *)plan->stage_in, *out = (char *)plan->stage_out;
     SG_CUDA_TRY(cudaMemcpyAsync(in, sigma, bytes, cudaMemcpyHostToDevice, st));
     if (caller) {
         SG_CUDA_TRY(cudaMemcpyAsync(in + bytes, deltax, bytes, cudaMemcpyHostToDevice, st));
         SG_CUDA_TRY(cudaMemcpyAsync(in + 2 * bytes, deltay, bytes, cudaMemcpyHostToDevice, st));
     }
-    SG_TRY(sg_force(plan, in, caller ? in + bytes : nullptr, caller ? in + 2 * bytes : nullptr, out, out + bytes, stream));
-    SG_CUDA_TRY(cudaMemcpyAsync(fx, out, bytes, cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(cudaMemcpyAsync(fy, out + bytes, bytes, cudaMemcpyDeviceToHost, st));
+    if (hfx) {
+        SG_TRY(sg_force(plan, in, caller ? in + bytes : nullptr, caller ? in + 2 * bytes : nullptr, hfx, hfy, stream));
+    } else {
+        SG_TRY(sg_force(plan, in, caller ? in + bytes : nullptr, caller ? in + 2 * bytes : nullptr, out, out + bytes,
+                        stream));
+        SG_CUDA_TRY(cudaMemcpyAsync(fx, out, bytes, cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaMemcpyAsync(fy, out + bytes, bytes, cudaMemcpyDeviceToHost, st));
+    }
     SG_CUDA_TRY(cudaStreamSynchronize(st));
     return check_device_error(plan);
 }

@@ -181,6 +181,28 @@ def test_host_entry_point_equals_device_entry_point(sg):
     plan.close()
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_host_entry_point_pinned_in_place(sg, mode, prec):
+    """Pinned host output buffers are written in place by the kernels; the
+    result equals the device entry point bit for bit."""
+    import torch
+    ny, nx = 70, 90
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    s, sx, sy = W.random_fields(ny, nx, seed=5 + mode)
+    plan = sg.Plan([(0, nx, ny, 0.0, 0.0, 0.01)], precision=prec, slope_mode=mode)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dt).ravel()).pin_memory()
+    hs, hdx, hdy = pin(s), pin(sx) if mode == 2 else None, pin(sy) if mode == 2 else None
+    hfx = torch.empty(nx * ny, dtype=tdt).pin_memory()
+    hfy = torch.empty(nx * ny, dtype=tdt).pin_memory()
+    plan.force_host(hs, hdx, hdy, hfx, hfy)
+    dfx, dfy = plan.force(to_dev(s, dt), to_dev(sx, dt) if mode == 2 else None, to_dev(sy, dt) if mode == 2 else None)
+    torch.cuda.synchronize()
+    assert torch.equal(hfx, dfx.cpu()) and torch.equal(hfy, dfy.cpu())
+    plan.close()
+
+
 def test_repeatable_bitwise(sg):
     import torch
     ny, nx = 128, 128
