@@ -407,8 +407,10 @@ sg_status sg_autotune(int precision, int min_pad, int max_pad, int reps, double 
 typedef struct sg_batch sg_batch;
 
 /* plans, sigma, fx, fy: arrays of n entries; deltax, deltay: arrays of n
- * entries (entries used for SG_SLOPES_CALLER plans) or NULL. Capture runs on
- * internal streams; nothing executes until sg_batch_launch. Errors: SG_EINVAL,
+ * entries (entries used for SG_SLOPES_CALLER plans) or NULL. The buffers are
+ * device memory, or page-locked host memory (mapped into the device address
+ * space: read and written in place by the kernels). Capture runs on internal
+ * streams; nothing executes until sg_batch_launch. Errors: SG_EINVAL,
  * SG_ENOMEM, SG_ECUDA. */
 sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma, const void *const *deltax,
                           const void *const *deltay, void *const *fx, void *const *fy, sg_batch **out);
