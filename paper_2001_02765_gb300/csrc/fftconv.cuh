@@ -106,6 +106,10 @@ struct edge_args {
     cplx_t<T> *edge;
 };
 
+// Global-to-shared staging loops issue LOAD_UNROLL loads per thread before
+// their shared-memory stores, so that these loads are in flight together.
+constexpr int LOAD_UNROLL = 4;
+
 template <bool BATCH, typename A>
 __device__ __forceinline__ A pass_args(const A &one, const A *__restrict__ many)
 {
@@ -133,12 +137,25 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const 
     if (BATCH && j0 >= ny) return;
 
     // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
-    for (int e = threadIdx.x; e < NB * (PX / 2); e += THREADS) {
-        const int s = e / (PX / 2), i = e % (PX / 2);
-        const int ja = j0 + 2 * s;
-        const T a = field_value(src, f, ja, i);
-        const T b = field_value(src, f, ja + 1, i);
-        buf[spad<C>(s * PX + i)] = cmake<C>(a, b);
+    constexpr int NE = NB * (PX / 2);
+    for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
+        T a[LOAD_UNROLL], b[LOAD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS;
+            a[u] = b[u] = (T)0;
+            if (e < NE) {
+                const int s = e / (PX / 2), i = e % (PX / 2);
+                const int ja = j0 + 2 * s;
+                a[u] = field_value(src, f, ja, i);
+                b[u] = field_value(src, f, ja + 1, i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS;
+            if (e < NE) buf[spad<C>((e / (PX / 2)) * PX + e % (PX / 2))] = cmake<C>(a[u], b[u]);
+        }
     }
     __syncthreads();
     fft_batch<C, PX, NB, THREADS, false, true>(buf, tw);
@@ -236,11 +253,20 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     for (int q = 0; q < (NOUT == 3 ? EPT : 1); ++q) accz[q] = cmake<C>((T)0, (T)0);
 
     for (int f = 0; f < nf; ++f) {
-        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
-            const int c = e / PY, j = e % PY;
-            const int kx = kx0 + c;
-            if (j >= PY / 2) continue;  // taken as zero by the first stage
-            buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
+        // the lower half of each column (the upper half is taken as zero by the first stage)
+        constexpr int NE = CB * (PY / 2);
+        for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
+            C v[LOAD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < LOAD_UNROLL; ++u) {
+                const int e = e0 + u * THREADS, c = e / (PY / 2), j = e % (PY / 2), kx = kx0 + c;
+                v[u] = (e < NE && j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
+            }
+#pragma unroll
+            for (int u = 0; u < LOAD_UNROLL; ++u) {
+                const int e = e0 + u * THREADS;
+                if (e < NE) buf[spad<C>((e / (PY / 2)) * PY + e % (PY / 2))] = v[u];
+            }
         }
         __syncthreads();
         fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
@@ -340,17 +366,27 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const 
     T *out = o == 0 ? fx : (o == 1 ? fy : fz);
 
     // Z[k] = A[k] + i B[k] over the full length, from the half spectra of rows 2s, 2s+1
-    for (int e = threadIdx.x; e < NB * QX; e += THREADS) {
-        const int s = e % NB, k = e / NB;
-        const int ja = j0 + 2 * s;
-        C a = ja < ny ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
-        C b = ja + 1 < ny ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
-        if (k == 0 || k == PX / 2) {
-            a.y = (T)0;
-            b.y = (T)0;
+    constexpr int NE = NB * QX;
+    for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
+        C av[LOAD_UNROLL], bv[LOAD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, s = e % NB, k = e / NB, ja = j0 + 2 * s;
+            av[u] = (e < NE && ja < ny) ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
+            bv[u] = (e < NE && ja + 1 < ny) ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
         }
-        buf[spad<C>(s * PX + k)] = cmake<C>(a.x - b.y, a.y + b.x);
-        if (k > 0 && k < PX / 2) buf[spad<C>(s * PX + PX - k)] = cmake<C>(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+#pragma unroll
+        for (int u = 0; u < LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, s = e % NB, k = e / NB;
+            if (e >= NE) continue;
+            C a = av[u], b = bv[u];
+            if (k == 0 || k == PX / 2) {
+                a.y = (T)0;
+                b.y = (T)0;
+            }
+            buf[spad<C>(s * PX + k)] = cmake<C>(a.x - b.y, a.y + b.x);
+            if (k > 0 && k < PX / 2) buf[spad<C>(s * PX + PX - k)] = cmake<C>(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
+        }
     }
     __syncthreads();
     fft_batch<C, PX, NB, THREADS, true, false, true>(buf, tw);
@@ -421,11 +457,22 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
     const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
 
-    for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
-        const int c = e / PY, j = e % PY;
-        const int kx = kx0 + c;
-        if (j >= PY / 2) continue;  // taken as zero by the first stage
-        buf[spad<C>(e)] = (j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+    {
+        // the lower half of each column (the upper half is taken as zero by the first stage)
+        constexpr int NE = CB * (PY / 2);
+        for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
+            C v[LOAD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < LOAD_UNROLL; ++u) {
+                const int e = e0 + u * THREADS, c = e / (PY / 2), j = e % (PY / 2), kx = kx0 + c;
+                v[u] = (e < NE && j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+            }
+#pragma unroll
+            for (int u = 0; u < LOAD_UNROLL; ++u) {
+                const int e = e0 + u * THREADS;
+                if (e < NE) buf[spad<C>((e / (PY / 2)) * PY + e % (PY / 2))] = v[u];
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x < CB) {
