@@ -273,6 +273,8 @@ __device__ __forceinline__ T lv_sample(const lv_rows_src<T> &a, int f, int j, in
 __host__ __device__ constexpr int lv_nb(int px) { return px >= 4096 ? 1 : 4096 / px; }
 __host__ __device__ constexpr int lv_cnb(int py) { return py >= 4096 ? 1 : 4096 / py; }
 constexpr int LV_ROW_THREADS = 512, LV_CFWD_THREADS = 512;
+// loads per thread issued before their shared-memory stores in the staging loops
+constexpr int LV_LOAD_UNROLL = 4;
 
 // All levels in one launch: blockIdx.x runs over the levels' CTA ranges
 // [cta0[m], cta0[m+1]); each level dispatches to the transform of its length.
@@ -296,10 +298,21 @@ __device__ __forceinline__ void lv_row_fwd_body(const lv_rows_src<T> &a, cplx_t<
     constexpr int QX = PX / 2 + 1;
     const int f = blockIdx.y;
     const int j0 = blk * RB;
-    for (int e = threadIdx.x; e < NB * (PX / 2); e += THREADS) {
-        const int q = e / (PX / 2), I = e % (PX / 2);
-        const int ja = j0 + 2 * q;
-        buf[spad<C>(q * PX + I)] = cmake<C>(lv_sample(a, f, ja, I), lv_sample(a, f, ja + 1, I));
+    // LV_LOAD_UNROLL samples per thread in flight before their stores
+    constexpr int NE = NB * (PX / 2);
+    for (int e0 = threadIdx.x; e0 < NE; e0 += LV_LOAD_UNROLL * THREADS) {
+        T va[LV_LOAD_UNROLL], vb[LV_LOAD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < LV_LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, q = e / (PX / 2), I = e % (PX / 2), ja = j0 + 2 * q;
+            va[u] = e < NE ? lv_sample(a, f, ja, I) : (T)0;
+            vb[u] = e < NE ? lv_sample(a, f, ja + 1, I) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < LV_LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS;
+            if (e < NE) buf[spad<C>((e / (PX / 2)) * PX + e % (PX / 2))] = cmake<C>(va[u], vb[u]);
+        }
     }
     __syncthreads();
     fft_batch<C, PX, NB, THREADS, false, true>(buf, tw);
@@ -374,9 +387,19 @@ __device__ __forceinline__ void lv_col_fwd_body(const cplx_t<T> *__restrict__ in
     for (int e = threadIdx.x; e < NB * (PY / 2); e += THREADS)
         buf[spad<C>((e / (PY / 2)) * PY + e % (PY / 2))] = cmake<C>((T)0, (T)0);
     __syncthreads();
-    for (int e = threadIdx.x; e < NB * a.ny; e += THREADS) {
-        const int q = e / a.ny, j = e % a.ny, kx = kx0 + q;
-        if (kx < a.qx) buf[spad<C>(q * PY + a.p0 + (j << a.st))] = in[((int64_t)f * a.qx + kx) * a.ny + j];
+    const int ne = NB * a.ny;
+    for (int e0 = threadIdx.x; e0 < ne; e0 += LV_LOAD_UNROLL * THREADS) {
+        C v[LV_LOAD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < LV_LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, q = e / a.ny, j = e % a.ny, kx = kx0 + q;
+            v[u] = (e < ne && kx < a.qx) ? in[((int64_t)f * a.qx + kx) * a.ny + j] : cmake<C>((T)0, (T)0);
+        }
+#pragma unroll
+        for (int u = 0; u < LV_LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, q = e / a.ny, j = e % a.ny, kx = kx0 + q;
+            if (e < ne && kx < a.qx) buf[spad<C>(q * PY + a.p0 + (j << a.st))] = v[u];
+        }
     }
     __syncthreads();
     fft_batch<C, PY, NB, THREADS, false, true>(buf, tw);
@@ -652,17 +675,27 @@ __global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_inv(lv_row_inv_args<T
     const int ny = a.ny;
     const C *w = A.in[lvl] + (int64_t)o * QX * ny;
     T *out = o == 0 ? fx : fy;
-    for (int e = threadIdx.x; e < NB * QX; e += THREADS) {
-        const int q = e % NB, k = e / NB;
-        const int ja = j0 + 2 * q;
-        C x = ja < ny ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
-        C y = ja + 1 < ny ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
-        if (k == 0 || k == PX / 2) {
-            x.y = (T)0;
-            y.y = (T)0;
+    constexpr int NE = NB * QX;
+    for (int e0 = threadIdx.x; e0 < NE; e0 += LV_LOAD_UNROLL * THREADS) {
+        C xv[LV_LOAD_UNROLL], yv[LV_LOAD_UNROLL];
+#pragma unroll
+        for (int u = 0; u < LV_LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, q = e % NB, k = e / NB, ja = j0 + 2 * q;
+            xv[u] = (e < NE && ja < ny) ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
+            yv[u] = (e < NE && ja + 1 < ny) ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
         }
-        buf[spad<C>(q * PX + k)] = cmake<C>(x.x - y.y, x.y + y.x);
-        if (k > 0 && k < PX / 2) buf[spad<C>(q * PX + PX - k)] = cmake<C>(x.x + y.y, y.x - x.y);
+#pragma unroll
+        for (int u = 0; u < LV_LOAD_UNROLL; ++u) {
+            const int e = e0 + u * THREADS, q = e % NB, k = e / NB;
+            if (e >= NE) continue;
+            C x = xv[u], y = yv[u];
+            if (k == 0 || k == PX / 2) {
+                x.y = (T)0;
+                y.y = (T)0;
+            }
+            buf[spad<C>(q * PX + k)] = cmake<C>(x.x - y.y, x.y + y.x);
+            if (k > 0 && k < PX / 2) buf[spad<C>(q * PX + PX - k)] = cmake<C>(x.x + y.y, y.x - x.y);
+        }
     }
     __syncthreads();
     fft_batch<C, PX, NB, THREADS, true, false, true>(buf, tw);
