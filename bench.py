@@ -644,7 +644,6 @@ def run_gpu(args):
         pads = sorted({_pad(p[1]) for p in wl["patches"]} | {_pad(p[2]) for p in wl["patches"]})
         res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=15)
         tuned = {"seconds": time.perf_counter() - t0, "shapes": {str(p): res[p][0] for p in pads}}
-    sg.sg_plan_set_timing(plan.handle, True)
     stream = torch.cuda.Stream()
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     sigma, dxs, dys = dev(wl["sigma"]), dev(wl["dx"]), dev(wl["dy"])
@@ -673,10 +672,11 @@ def run_gpu(args):
         solve()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = {k: [] for k in sg.STAGE_NAMES}
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # the timed solves run with the library's stage timers off (their events would
+    # sit between the passes); the stage split comes from a second, shorter pass
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
         for k in range(args.steps):
@@ -686,15 +686,22 @@ def run_gpu(args):
             solve()
             with torch.cuda.stream(stream):
                 ev[k][1].record(stream)
-            t = sg.sg_plan_get_timing(plan.handle)  # waits for this solve's events
-            for name, v in t.items():
-                stage_ms[name].append(v)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     per = [a.elapsed_time(b) for a, b in ev]
     value, total_ms, solves = job_rate(sum(per), args.steps)
     p50 = float(np.percentile(per, 50))
     p99 = float(np.percentile(per, 99))
+    stage_ms = {k: [] for k in sg.STAGE_NAMES}
+    sg.sg_plan_set_timing(plan.handle, True)
+    for k in range(min(args.steps, 20)):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        solve()
+        t = sg.sg_plan_get_timing(plan.handle)  # waits for this solve's events
+        for name, v in t.items():
+            stage_ms[name].append(v)
+    sg.sg_plan_set_timing(plan.handle, False)
 
     # FP64 plain per-solve path on the same GPU, and the FP32 error against it.
     # FP64 level convolutions stop at 4096-point transforms; beyond, the FP64

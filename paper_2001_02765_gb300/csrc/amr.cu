@@ -139,6 +139,8 @@ __global__ void k_fill_covered(const sg_patch_dev *__restrict__ gpd, const int *
                                int t1, const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
                                T *__restrict__ F)
 {
+    sg_dep_trigger();
+    sg_dep_wait();  // the covered cells of the level above
     const patch_table tab = stage_patch_table(gpd, gorder, gcpre, npatches);
     const sg_patch_dev *pd = tab.pd;
     const int *order = tab.order;
@@ -173,6 +175,8 @@ __global__ void k_composite(const sg_patch_dev *__restrict__ gpd, const int *__r
                             const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
                             const T *__restrict__ F, T *__restrict__ s)
 {
+    sg_dep_trigger();
+    sg_dep_wait();  // the filled values of the covered cells
     const patch_table tab = stage_patch_table(gpd, gorder, gfpre, n);
     const sg_patch_dev *pd = tab.pd;
     const int *order = tab.order;
@@ -242,14 +246,27 @@ sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, co
         const int t0 = plan->comp_lev_first[l], t1 = plan->comp_lev_first[l + 1];
         const int64_t n = plan->comp_cells_host[t1] - plan->comp_cells_host[t0];
         if (n <= 0) continue;
-        k_fill_covered<T><<<grid_for(n), 256, patch_table_bytes(plan->npatches), st>>>(
-            plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_cells, plan->npatches, t0, t1,
-            (const T *)sigma, sx, sy, F);
+        // the finest fill reads the caller's fields: an ordinary launch; the next ones depend on it
+        auto kf = k_fill_covered<T>;
+        if (l == lmax - 1)
+            kf<<<grid_for(n), 256, patch_table_bytes(plan->npatches), st>>>(
+                plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_cells, plan->npatches, t0, t1,
+                (const T *)sigma, sx, sy, F);
+        else
+            SG_CUDA_TRY(sg_launch_dep(kf, dim3(grid_for(n)), dim3(256), patch_table_bytes(plan->npatches), st,
+                                      plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_cells,
+                                      plan->npatches, t0, t1, (const T *)sigma, sx, sy, F));
         SG_CUDA_TRY(cudaGetLastError());
     }
-    k_composite<T><<<grid_for(plan->comp_items), 256, patch_table_bytes(plan->npatches), st>>>(
-        plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_item_off, plan->npatches, (const T *)sigma, sx,
-        sy, F, s);
+    auto kc = k_composite<T>;
+    if (lmax >= 2)  // after the fills of the covered cells
+        SG_CUDA_TRY(sg_launch_dep(kc, dim3(grid_for(plan->comp_items)), dim3(256), patch_table_bytes(plan->npatches),
+                                  st, plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_item_off,
+                                  plan->npatches, (const T *)sigma, sx, sy, (const T *)F, s));
+    else
+        kc<<<grid_for(plan->comp_items), 256, patch_table_bytes(plan->npatches), st>>>(
+            plan->patch_dev, plan->cell_code, plan->comp_order, plan->comp_item_off, plan->npatches, (const T *)sigma,
+            sx, sy, F, s);
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }

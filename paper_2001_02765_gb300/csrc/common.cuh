@@ -25,6 +25,31 @@
 void sg_set_last_cuda_error(cudaError_t e, const char *what);
 void sg_set_last_error_message(const char *msg);
 
+// Programmatic dependent launch. A kernel launched by sg_launch_dep may be
+// scheduled before the previous kernel of its stream has finished, once every
+// CTA of that kernel has executed sg_dep_trigger (or exited); it calls
+// sg_dep_wait before it reads anything that kernel wrote. Both are no-ops for
+// kernels launched without the attribute.
+__device__ __forceinline__ void sg_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void sg_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t sg_launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------ complex math --
 
 template <typename T> struct cplx_of;

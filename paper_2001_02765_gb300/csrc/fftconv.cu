@@ -28,7 +28,9 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     if (u.central && ws->aux) SG_CUDA_TRY(cudaStreamWaitEvent(st, ws->ev_join, 0));
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
-    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, ws->err, st));
+    // after the join with the side stream the column pass is an ordinary launch
+    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, ws->err, st, nullptr, {0, 0},
+                                               ws->aux == nullptr));
     else SG_TRY(sgk::cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, ws->err, st));
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);

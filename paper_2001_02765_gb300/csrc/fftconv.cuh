@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const 
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
+    sg_dep_trigger();
     const row_fwd_args<T> args = pass_args<BATCH>(one, many);
     const field_src<T> &src = args.src;
     cplx_t<T> *__restrict__ work = args.work;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const 
     const int j0 = blockIdx.x * RB;
     const int ny = src.ny;
     if (BATCH && j0 >= ny) return;
+    sg_dep_wait();
 
     // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
     constexpr int NE = NB * (PX / 2);
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
                                                       int qx, int nf, const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
+    sg_dep_trigger();
     const col_args<T> args = pass_args<BATCH>(one, many);
     const cplx_t<T> *__restrict__ work_fwd = args.wf;
     cplx_t<T> *__restrict__ work_inv = args.wi;
@@ -245,6 +248,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL>(ssp, spec, kx0, qx, &bar);
+    sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
 
     C accx[EPT], accy[EPT], accz[NOUT == 3 ? EPT : 1];
 #pragma unroll
@@ -355,6 +359,7 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const 
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
+    sg_dep_trigger();
     const row_inv_args<T> args = pass_args<BATCH>(one, many);
     const cplx_t<T> *__restrict__ work_inv = args.wi;
     T *fx = args.fx, *fy = args.fy, *fz = args.fz;
@@ -362,6 +367,7 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const 
     const int o = blockIdx.y;
     const int j0 = blockIdx.x * RB;
     if (BATCH && j0 >= ny) return;
+    sg_dep_wait();
     const C *w = work_inv + (int64_t)o * QX * ny;
     T *out = o == 0 ? fx : (o == 1 ? fy : fz);
 
@@ -407,6 +413,8 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const e
                                                        const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
+    sg_dep_trigger();
+    sg_dep_wait();
     const edge_args<T> args = pass_args<BATCH>(one, many);
     const T *__restrict__ sigma = args.sigma;
     const int nx = args.nx, ny = args.ny;
@@ -436,6 +444,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     col_args<T> one, const col_args<T> *__restrict__ many, int qx, const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
+    sg_dep_trigger();
     const col_args<T> args = pass_args<BATCH>(one, many);
     const cplx_t<T> *__restrict__ work_fwd = args.wf;
     cplx_t<T> *__restrict__ work_inv = args.wi;
@@ -454,6 +463,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
+    sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
     const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
     const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
 
@@ -568,15 +578,18 @@ struct batch_shape {
 template <typename T>
 sg_status rows_fwd(int px, int nb, const row_fwd_args<T> &one, int nf, const cplx_t<T> *tw, cudaStream_t st,
                    const row_fwd_args<T> *many = nullptr, batch_shape bs = {0, 0});
+// The column and inverse-row passes are launched as dependent launches
+// (sg_launch_dep) on the pass before them in the stream; dep = false launches a
+// column pass normally (when its stream waits on an event just before it).
 template <typename T>
 sg_status rows_inv(int px, int nb, const row_inv_args<T> &one, int nout, const cplx_t<T> *tw, cudaStream_t st,
                    const row_inv_args<T> *many = nullptr, batch_shape bs = {0, 0});
 template <typename T>
 sg_status cols(int py, int cb, int nout, const col_args<T> &one, int qx, int nf, const cplx_t<T> *tw, int *err,
-               cudaStream_t st, const col_args<T> *many = nullptr, batch_shape bs = {0, 0});
+               cudaStream_t st, const col_args<T> *many = nullptr, batch_shape bs = {0, 0}, bool dep = true);
 template <typename T>
 sg_status cols_central(int py, int cb, const col_args<T> &one, int qx, const cplx_t<T> *tw, int *err, cudaStream_t st,
-                       const col_args<T> *many = nullptr, batch_shape bs = {0, 0});
+                       const col_args<T> *many = nullptr, batch_shape bs = {0, 0}, bool dep = true);
 template <typename T>
 sg_status edge_cols(int py, const edge_args<T> &one, const cplx_t<T> *tw, cudaStream_t st,
                     const edge_args<T> *many = nullptr, batch_shape bs = {0, 0});

@@ -3,5 +3,5 @@
 
 namespace sgk {
 template sg_status cols<double>(int, int, int, const col_args<double> &, int, int, const double2 *, int *,
-                                cudaStream_t, const col_args<double> *, batch_shape);
+                                cudaStream_t, const col_args<double> *, batch_shape, bool);
 }  // namespace sgk

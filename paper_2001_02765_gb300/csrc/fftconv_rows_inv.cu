@@ -15,7 +15,7 @@ sg_status launch_rows_inv(const row_inv_args<T> &one, const row_inv_args<T> *man
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int ny = BATCH ? bs.maxny : one.ny;
     dim3 grid((ny + 2 * NB - 1) / (2 * NB), nout, BATCH ? bs.nmem : 1);
-    kern<<<grid, ROW_THREADS, smem, st>>>(one, many, tw);
+    SG_CUDA_TRY(sg_launch_dep(kern, grid, dim3(ROW_THREADS), smem, st, one, many, tw));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }

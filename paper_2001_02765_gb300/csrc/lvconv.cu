@@ -357,6 +357,8 @@ struct lv_row_fwd_args {
 template <typename T, int LMAX>
 __global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_fwd(lv_row_fwd_args<T> A)
 {
+    sg_dep_trigger();
+    sg_dep_wait();  // the composite sources
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
@@ -428,6 +430,8 @@ struct lv_col_fwd_args {
 template <typename T, int LMAX>
 __global__ void __launch_bounds__(LV_CFWD_THREADS) k_lv_col_fwd(lv_col_fwd_args<T> A)
 {
+    sg_dep_trigger();
+    sg_dep_wait();  // the row transforms
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
@@ -545,6 +549,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
                                                             cplx_t<T> *__restrict__ out,
                                                             const cplx_t<T> *__restrict__ tw)
 {
+    sg_dep_trigger();
+    sg_dep_wait();  // the source spectra
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *bx = reinterpret_cast<C *>(smem_raw);
@@ -662,6 +668,8 @@ template <typename T, int PX>
 __global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_inv(lv_row_inv_args<T> A, T *__restrict__ fx,
                                                               T *__restrict__ fy, const cplx_t<T> *__restrict__ tw)
 {
+    sg_dep_trigger();
+    sg_dep_wait();  // the target columns
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
@@ -741,7 +749,7 @@ sg_status launch_row_fwd(const lv_row_fwd_args<T> &A, int ncta, int lmax, cudaSt
     const size_t sm = spad_size<cplx_t<T>>(lv_nb(lmax) * lmax) * sizeof(cplx_t<T>);
     auto kern = lmax > 4096 ? k_lv_row_fwd<T, 8192> : k_lv_row_fwd<T, 4096>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<dim3(ncta, 3), LV_ROW_THREADS, sm, st>>>(A);
+    SG_CUDA_TRY(sg_launch_dep(kern, dim3(ncta, 3), dim3(LV_ROW_THREADS), sm, st, A));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -752,7 +760,7 @@ sg_status launch_col_fwd(const lv_col_fwd_args<T> &A, int ncta, int lmax, cudaSt
     const size_t sm = spad_size<cplx_t<T>>(lv_cnb(lmax) * lmax) * sizeof(cplx_t<T>);
     auto kern = lmax > 4096 ? k_lv_col_fwd<T, 8192> : k_lv_col_fwd<T, 4096>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<dim3(ncta, 3), LV_CFWD_THREADS, sm, st>>>(A);
+    SG_CUDA_TRY(sg_launch_dep(kern, dim3(ncta, 3), dim3(LV_CFWD_THREADS), sm, st, A));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -765,7 +773,7 @@ sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const 
     const size_t sm = NOUT * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
     auto kern = k_lv_col_mac_inv<T, PY, TH, lv_mac_minb<T>(PY), NOUT>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<a.qx * a.nsrc, TH, sm, st>>>(a, spec, kspec, phx, phy, out, tw);
+    SG_CUDA_TRY(sg_launch_dep(kern, dim3(a.qx * a.nsrc), dim3(TH), sm, st, a, spec, kspec, phx, phy, out, tw));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -777,7 +785,7 @@ sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, int nout, T *fx,
     const size_t sm = spad_size<cplx_t<T>>(lv_nb(PX) * PX) * sizeof(cplx_t<T>);
     auto kern = k_lv_row_inv<T, PX>;
     SG_TRY(smem_attr(kern, sm));
-    kern<<<dim3(ncta, nout), LV_ROW_THREADS, sm, st>>>(A, fx, fy, tw);
+    SG_CUDA_TRY(sg_launch_dep(kern, dim3(ncta, nout), dim3(LV_ROW_THREADS), sm, st, A, fx, fy, tw));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
