@@ -739,11 +739,6 @@ static sg_status ws_alloc_one(void **p, int64_t bytes, cudaStream_t st, bool asy
 
 void sg_workspace_free(sg_workspace *ws, cudaStream_t st, bool async)
 {
-    if (ws->aux) cudaStreamDestroy(ws->aux);
-    if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
-    if (ws->ev_join) cudaEventDestroy(ws->ev_join);
-    ws->aux = nullptr;
-    ws->ev_fork = ws->ev_join = nullptr;
     void *bufs[7] = {ws->work_fwd, ws->work_inv, ws->sfield, ws->tile_w, ws->partial, ws->err, ws->zone_buf};
     for (void *b : bufs) {
         if (!b) continue;
@@ -767,15 +762,6 @@ sg_status sg_workspace_alloc(const sg_plan *plan, sg_workspace *ws, cudaStream_t
     if (r == SG_OK) {
         cudaError_t e = async ? cudaMemsetAsync(ws->err, 0, 16, st) : cudaMemset(ws->err, 0, 16);
         if (e != cudaSuccess) r = SG_ECUDA;
-    }
-    if (r == SG_OK && !async && plan->geom.slope_mode == SG_SLOPES_CENTRAL) {
-        // side stream for the edge-column transform of the central-slope path
-        if (cudaStreamCreateWithFlags(&ws->aux, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            r = SG_ECUDA;
-        }
     }
     if (r != SG_OK) sg_workspace_free(ws, st, async);
     return r;

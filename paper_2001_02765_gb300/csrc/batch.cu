@@ -101,8 +101,8 @@ template <typename T>
 sg_status group_enqueue(const group_passes<T> &g, cudaStream_t st)
 {
     const sgk::uniform_passes<T> &u = g.u;
-    if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st, g.ed, g.bs));
     SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, g.rf, g.bs));
+    if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st, g.ed, g.bs));
     if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, g.err, st, g.col, g.bs));
     else SG_TRY(sgk::cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, g.err, st, g.col, g.bs));
     SG_TRY(sgk::rows_inv<T>(u.px, u.shx[1], u.ri, u.nout, u.twx, st, g.ri, g.bs));
@@ -135,15 +135,6 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
             b->ws.resize(i);
             batch_free(b);
             return a;
-        }
-        // the members already run side by side: keep each member's work on its own branch
-        sg_workspace &w = b->ws[i];
-        if (w.aux) {
-            cudaStreamDestroy(w.aux);
-            cudaEventDestroy(w.ev_fork);
-            cudaEventDestroy(w.ev_join);
-            w.aux = nullptr;
-            w.ev_fork = w.ev_join = nullptr;
         }
     }
     // capture: root stream -> one branch per member -> join

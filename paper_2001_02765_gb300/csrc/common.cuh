@@ -268,10 +268,6 @@ struct sg_workspace {
     void *zone_buf;         // zone plans: inputs (3 planes) and outputs (2 planes) in patch layout
     int *err;               // device error word: nonzero after a bounded wait in a kernel ran out
     struct sg_timing *timing;  // stage timers, or NULL
-    // optional side stream for independent work of one solve (fork/join by events);
-    // NULL runs that work on the solve's stream
-    cudaStream_t aux;
-    cudaEvent_t ev_fork, ev_join;
 };
 
 // Cell codes of sg_plan::cell_code.

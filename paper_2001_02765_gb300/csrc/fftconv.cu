@@ -13,24 +13,13 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
 {
     const sgk::uniform_passes<T> u = sgk::uniform_setup<T>(plan, ws, p, sigma, dx, dy, fx, fy, fz, pot_spec, wf_pot);
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
-    if (u.central) {
-        // the edge-column transform is independent of the row pass: run it beside it
-        cudaStream_t es = st;
-        if (ws->aux) {
-            SG_CUDA_TRY(cudaEventRecord(ws->ev_fork, st));
-            SG_CUDA_TRY(cudaStreamWaitEvent(ws->aux, ws->ev_fork, 0));
-            es = ws->aux;
-        }
-        SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, es));
-        if (ws->aux) SG_CUDA_TRY(cudaEventRecord(ws->ev_join, ws->aux));
-    }
     SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st));
-    if (u.central && ws->aux) SG_CUDA_TRY(cudaStreamWaitEvent(st, ws->ev_join, 0));
+    // the edge-column transform runs beside the row pass (a dependent launch that
+    // does not wait for it; see k_edge_cols)
+    if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st));
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
-    // after the join with the side stream the column pass is an ordinary launch
-    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, ws->err, st, nullptr, {0, 0},
-                                               ws->aux == nullptr));
+    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, ws->err, st));
     else SG_TRY(sgk::cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, ws->err, st));
     sg_timing_end(ws, SG_STAGE_COL_CONV, st);
     sg_timing_begin(ws, SG_STAGE_ROW_INV, st);

@@ -33,7 +33,6 @@
 // column (k_edge_cols), R0 / R1 the x-transforms of its first / last row (the
 // column pass reads them from its own input). So only sigma is transformed:
 // one row field and one forward column transform instead of three.
-#include "common.cuh"
 //
 // The kernels and their launch-shape variants are split over translation
 // units by stage (fftconv_rows.cu, fftconv_cols.cu, fftconv_central.cu); the
@@ -413,8 +412,10 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const e
                                                        const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
+    // launched after the row pass, beside it: sigma is the caller's (ready
+    // before the row pass started); the wait at the end makes this kernel's
+    // completion imply the row pass's, for the column pass after it
     sg_dep_trigger();
-    sg_dep_wait();
     const edge_args<T> args = pass_args<BATCH>(one, many);
     const T *__restrict__ sigma = args.sigma;
     const int nx = args.nx, ny = args.ny;
@@ -435,6 +436,7 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const e
         edge[k] = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
         edge[PY + k] = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
     }
+    sg_dep_wait();
 }
 
 // Column pass for central slopes: one forward transform (sigma), the slope

@@ -51,14 +51,15 @@ sg_status launch_edge_cols(const edge_args<T> &one, const edge_args<T> *many, ba
 {
     constexpr int THREADS = PY / 8 >= 64 ? PY / 8 : 64;
     const size_t smem = (size_t)spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
+    // a dependent launch after the row pass (see k_edge_cols)
     if (many) {
         auto kern = k_edge_cols<T, PY, THREADS, true>;
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<dim3(1, 1, bs.nmem), THREADS, smem, st>>>(one, many, tw);
+        SG_CUDA_TRY(sg_launch_dep(kern, dim3(1, 1, bs.nmem), dim3(THREADS), smem, st, one, many, tw));
     } else {
         auto kern = k_edge_cols<T, PY, THREADS, false>;
         SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        kern<<<1, THREADS, smem, st>>>(one, many, tw);
+        SG_CUDA_TRY(sg_launch_dep(kern, dim3(1), dim3(THREADS), smem, st, one, many, tw));
     }
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
