@@ -853,8 +853,8 @@ def run_gpu(args):
 # of the current kernel build (see profiles/); None when not captured for it.
 # amr3 col_conv: the stage's column-transform and column-MAC launches, one each
 # per solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
-TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.009e6,
-           ("amr3", "col_conv"): (11.14e6 + 7.03e6) + (227.21e6 + 11.05e6)}
+TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.004e6,
+           ("amr3", "col_conv"): None}
 
 
 def _pad(n):
