@@ -854,7 +854,7 @@ def run_gpu(args):
 # amr3 col_conv: the stage's column-transform and column-MAC launches, one each
 # per solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
 TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.004e6,
-           ("amr3", "col_conv"): None}
+           ("amr3", "col_conv"): (11.152e6 + 7.286e6) + (227.535e6 + 10.888e6)}
 
 
 def _pad(n):
@@ -918,10 +918,14 @@ def algorithmic_flops(wl, info, stage, nout=2):
             pcx, pcy = px >> _lv_cexp(s, px), py >> _lv_cexp(s, py)
             if stage == "row_fwd":
                 total += 3 * (ny / 2) * fft(pcx)
-            elif stage == "col_conv":
-                total += (pcx // 2 + 1) * 3 * fft(pcy) + qx * (nout * fft(py) + L * 3 * 5 * nout * py)
+            # as a target, the level's bins are folded onto its compact lengths
+            # before the inverse transforms from 4096-point transforms up
+            tcx = pcx if px >= 4096 else px
+            tcy = pcy if py >= 4096 else py
+            if stage == "col_conv":
+                total += (pcx // 2 + 1) * 3 * fft(pcy) + qx * (nout * fft(tcy) + L * 3 * 5 * nout * py)
             elif stage == "row_inv":
-                total += nout * (ny / 2) * fft(px)
+                total += nout * (ny / 2) * fft(tcx)
         return total
     for p in wl["patches"]:
         nx, ny = p[1], p[2]

@@ -270,6 +270,12 @@ __device__ __forceinline__ T lv_sample(const lv_rows_src<T> &a, int f, int j, in
 // sequences (two rows each) of length PX per CTA of 512 threads; the forward
 // column pass NB = 4096 / PY columns per CTA of 512 threads (one radix-8
 // butterfly per thread and stage up to 4096 points).
+__host__ __device__ constexpr int lv_log2(int v) { return v <= 1 ? 0 : 1 + lv_log2(v >> 1); }
+// Coarse target levels are folded onto their compact lengths before the inverse
+// transforms only from 4096-point transforms up: below, the transforms are a
+// small part of those passes and the folded ones measured no faster (their
+// stages are latency-bound, and the extra lengths enlarge the kernels).
+__host__ __device__ constexpr bool lv_fold_targets(int p) { return p >= 4096; }
 __host__ __device__ constexpr int lv_nb(int px) { return px >= 4096 ? 1 : 4096 / px; }
 __host__ __device__ constexpr int lv_cnb(int py) { return py >= 4096 ? 1 : 4096 / py; }
 constexpr int LV_ROW_THREADS = 512, LV_CFWD_THREADS = 512;
@@ -450,12 +456,73 @@ struct lv_mac_args {
     int hy[SG_MAX_LEVELS];
     int key[SG_MAX_LEVELS][SG_MAX_LEVELS];  // kernel of source level m for target level l, [m][l]
     int d2[SG_MAX_LEVELS][SG_MAX_LEVELS];   // its 2 x sample shift
-    int ny[SG_MAX_LEVELS];              // target level l: sampled rows j0 + j 2^t, j < ny
-    int j0[SG_MAX_LEVELS];
-    int t[SG_MAX_LEVELS];
+    // target level l: its ny sampled rows sit at compact positions p0 + j 2^st of
+    // its compact column length 2^lm (lm < log2 PY: the bins are folded onto it,
+    // with the half-sample shift when fh), inverse twiddles tw[l]
+    int ny[SG_MAX_LEVELS];
+    int p0[SG_MAX_LEVELS];
+    int st[SG_MAX_LEVELS];
+    int lm[SG_MAX_LEVELS];
+    int fh[SG_MAX_LEVELS];
+    const void *tw[SG_MAX_LEVELS];
     int64_t inv_off[SG_MAX_LEVELS];     // complex-element offset of its inverse-column outputs
     int qx;
 };
+
+// Transform length switch for the compact target lengths 64 .. LMAX (only the
+// lengths up to LMAX are instantiated).
+#define SG_LV_LEN_SWITCH(LP, LMAX, BODY)                                                   \
+    switch (LP) {                                                                        \
+    case 6: if constexpr (64 <= LMAX) { constexpr int PP = 64; BODY; } break;            \
+    case 7: if constexpr (128 <= LMAX) { constexpr int PP = 128; BODY; } break;          \
+    case 8: if constexpr (256 <= LMAX) { constexpr int PP = 256; BODY; } break;          \
+    case 9: if constexpr (512 <= LMAX) { constexpr int PP = 512; BODY; } break;          \
+    case 10: if constexpr (1024 <= LMAX) { constexpr int PP = 1024; BODY; } break;       \
+    case 11: if constexpr (2048 <= LMAX) { constexpr int PP = 2048; BODY; } break;       \
+    case 12: if constexpr (4096 <= LMAX) { constexpr int PP = 4096; BODY; } break;       \
+    case 13: if constexpr (8192 <= LMAX) { constexpr int PP = 8192; BODY; } break;       \
+    default: break;                                                                      \
+    }
+
+// Sampling a length-L inverse transform every 2^c points from position r
+// (c >= 1, L = M 2^c) equals the length-M inverse transform of the folded
+// spectrum Z(k) = sum_q X(k + q M) exp(2 pi i (k + q M) r / L), k < M. Here r is 0,
+// or half a compact sample (r = 2^(c-1), half): Z(k) = conj(psi(k)) sum_q (-1)^q
+// X(k + q M), psi(k) = exp(-i pi k / M) = cph[k 2^c].
+template <typename C, int L>
+__device__ __forceinline__ C lv_fold_bin(const C *buf, int k, int lm, bool half, const C *__restrict__ cph)
+{
+    const int M = 1 << lm, nq = L >> lm;
+    C acc = buf[spad<C>(k)];
+    for (int q = 1; q < nq; ++q) {
+        const C u = buf[spad<C>(k + q * M)];
+        acc = (half && (q & 1)) ? csub(acc, u) : cadd(acc, u);
+    }
+    return half ? cmulc(acc, cph[k << (lv_log2(L) - lm)]) : acc;
+}
+
+// NSEQ sequences of length L back to back in buf become NSEQ folded sequences of
+// length M back to back (staged through registers: the outputs overlap inputs
+// of other threads).
+template <typename C, int L, int NSEQ, int THREADS>
+__device__ __forceinline__ void lv_fold_spectrum(C *buf, int lm, bool half, const C *__restrict__ cph)
+{
+    constexpr int IT = (NSEQ * (L / 2) + THREADS - 1) / THREADS;  // M <= L/2
+    const int M = 1 << lm;
+    C v[IT];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int e = threadIdx.x + i * THREADS;
+        if (e < NSEQ * M) v[i] = lv_fold_bin<C, L>(buf + spad<C>((e >> lm) * L), e & (M - 1), lm, half, cph);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int e = threadIdx.x + i * THREADS;
+        if (e < NSEQ * M) buf[spad<C>(e)] = v[i];
+    }
+    __syncthreads();
+}
 
 // The compact source column of column kx for source level m: kx mod Pcx, or its
 // Hermitian partner (fold), with the sign of the x half-shift.
@@ -532,14 +599,26 @@ __device__ __forceinline__ void lv_mac_bin(cplx_t<T> X0, cplx_t<T> X1, cplx_t<T>
     }
 }
 
+// Inverse transforms (length L) of the NOUT outputs, held PY apart in shared
+// memory. One at a time, and with the length switch outside the loop: a batch of
+// both, or a switch inside the loop, makes the register allocation of the
+// whole kernel (its per-bin loads) grow by a quarter or more.
+template <typename C, int PY, int L, int NOUT, int THREADS>
+__device__ __forceinline__ void lv_inv_columns(C *bx, const C *__restrict__ tw)
+{
+#pragma unroll 1
+    for (int o = 0; o < NOUT; ++o) fft_batch<C, L, 1, THREADS, true, false, true>(bx + spad<C>(o * PY), tw);
+}
+
 // One (column kx, target level l) per CTA, kx = blockIdx.x / nsrc and
 // l = blockIdx.x % nsrc, so that the CTAs of all target levels of a column run
 // side by side and read its source spectra (and shared kernel planes) from L2:
 // Fx^, Fy^ = sum over source levels and fields of source spectrum (unfolded
 // from the compact one) x kernel spectrum (decompressed, see k_lv_extract),
-// formed element by element straight into two shared buffers; inverse column
-// transforms; the target level's sampled rows to out[(o qx + kx) ny + j]
-// (out at the level's inverse-column offset). NOUT = 1: the potential, one
+// formed element by element straight into two shared buffers; for a coarse
+// target level folded onto its compact column length (lv_fold_spectrum); inverse
+// column transforms of that length; the target level's sampled rows to
+// out[(o qx + kx) ny + j] (out at the level's inverse-column offset). NOUT = 1: the potential, one
 // output from 3 kernel planes per key (p0 real, px and py imaginary; py odd in ky).
 template <typename T, int PY, int THREADS, int MINB, int NOUT>
 __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
@@ -547,14 +626,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
                                                             const cplx_t<T> *__restrict__ phx,
                                                             const cplx_t<T> *__restrict__ phy,
                                                             cplx_t<T> *__restrict__ out,
-                                                            const cplx_t<T> *__restrict__ tw)
+                                                            const cplx_t<T> *__restrict__ cph)
 {
     sg_dep_trigger();
     sg_dep_wait();  // the source spectra
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *bx = reinterpret_cast<C *>(smem_raw);
-    C *by = bx + spad_size<C>(PY);
+    C *by = bx + spad<C>(PY);
     constexpr int QS = ((PY / 2 + 1) + 3) & ~3;  // kernel plane row stride (sg_spec_stride)
     const int kx = blockIdx.x / a.nsrc, l = blockIdx.x % a.nsrc;
     const int64_t kqplane = (int64_t)a.qx * QS;
@@ -639,18 +718,35 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
         }
     }
     __syncthreads();
+    const int lm = a.lm[l];
+    if constexpr (lv_fold_targets(PY)) {
+        // a coarse target level is sampled every 2^c rows: fold onto its compact
+        // length, in place (bin k < M of an output is written only by the thread
+        // that reads it)
+        if (lm < lv_log2(PY)) {
+            for (int e = threadIdx.x; e < (NOUT << lm); e += THREADS) {
+                C *seq = bx + spad<C>((e >> lm) * PY);
+                const int k = e & ((1 << lm) - 1);
+                seq[spad<C>(k)] = lv_fold_bin<C, PY>(seq, k, lm, a.fh[l] != 0, cph);
+            }
+            __syncthreads();
+        }
+        SG_LV_LEN_SWITCH(lm, PY, (lv_inv_columns<C, PY, PP, NOUT, THREADS>(bx, (const C *)a.tw[l])));
+    }
+    const int ny = a.ny[l], p0 = a.p0[l], st = a.st[l];
     for (int o = 0; o < NOUT; ++o) {
-        C *buf = o == 0 ? bx : by;
-        fft_batch<C, PY, 1, THREADS, true, false, true>(buf, tw);
-        const int ny = a.ny[l], j0 = a.j0[l], t = a.t[l];
+        C *seq = bx + spad<C>(o * PY);
+        if constexpr (!lv_fold_targets(PY)) fft_batch<C, PY, 1, THREADS, true, false, true>(seq, (const C *)a.tw[l]);
         C *dst = out + a.inv_off[l] + ((int64_t)o * a.qx + kx) * ny;
-        for (int j = threadIdx.x; j < ny; j += THREADS) dst[j] = buf[spad<C>(j0 + (j << t))];
+        for (int j = threadIdx.x; j < ny; j += THREADS) dst[j] = seq[spad<C>(p0 + (j << st))];
     }
 }
 
 struct lv_out_dst {
     const int *map;
-    int nx, ny, i0, t;
+    int nx, ny;
+    int p0, st;  // image column i sits at compact position p0 + i 2^st
+    int lm, fh;  // log2 of the compact row length; samples half-shifted along x
 };
 
 template <typename T>
@@ -659,14 +755,18 @@ struct lv_row_inv_args {
     int cta0[SG_MAX_LEVELS + 1];
     lv_out_dst a[SG_MAX_LEVELS];
     const cplx_t<T> *in[SG_MAX_LEVELS];
+    const cplx_t<T> *tw[SG_MAX_LEVELS];  // inverse twiddles of the compact row length
+    const cplx_t<T> *cph;               // psi_x table (finest length)
 };
 
 // Inverse row transforms of every target level's rows (blockIdx.y = Fx, Fy),
-// all levels in one launch; the samples at columns i0 + i 2^t go to the
-// level's cells through the map.
+// all levels in one launch: the full rows are unpacked from the half spectra,
+// folded onto the level's compact row length (lv_fold_spectrum) when its cells
+// are wider than a finest cell, transformed, and the samples at compact columns
+// p0 + i 2^st go to the level's cells through the map.
 template <typename T, int PX>
 __global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_inv(lv_row_inv_args<T> A, T *__restrict__ fx,
-                                                              T *__restrict__ fy, const cplx_t<T> *__restrict__ tw)
+                                                              T *__restrict__ fy)
 {
     sg_dep_trigger();
     sg_dep_wait();  // the target columns
@@ -706,11 +806,17 @@ __global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_inv(lv_row_inv_args<T
         }
     }
     __syncthreads();
-    fft_batch<C, PX, NB, THREADS, true, false, true>(buf, tw);
+    const int lm = a.lm;
+    if constexpr (lv_fold_targets(PX)) {
+        if (lm < lv_log2(PX)) lv_fold_spectrum<C, PX, NB, THREADS>(buf, lm, a.fh != 0, A.cph);
+        SG_LV_LEN_SWITCH(lm, PX, (fft_batch<C, PP, NB, THREADS, true, false, true>(buf, A.tw[lvl])));
+    } else {
+        fft_batch<C, PX, NB, THREADS, true, false, true>(buf, A.tw[lvl]);
+    }
     for (int e = threadIdx.x; e < NB * a.nx; e += THREADS) {
         const int q = e / a.nx, i = e % a.nx;
         const int ja = j0 + 2 * q;
-        const C zz = buf[spad<C>(q * PX + a.i0 + (i << a.t))];
+        const C zz = buf[spad<C>((q << lm) + a.p0 + (i << a.st))];
         if (ja < ny) {
             const int c = a.map[(int64_t)ja * a.nx + i];
             if (c >= 0) out[c] = zz.x;
@@ -725,16 +831,24 @@ __global__ void __launch_bounds__(LV_ROW_THREADS) k_lv_row_inv(lv_row_inv_args<T
 // ----------------------------------------------------------- launchers --
 
 constexpr int lv_col_threads(int py) { return py / 8 < 64 ? 64 : (py / 8 > 512 ? 512 : py / 8); }
-// Column-MAC CTAs: the two shared spectra of a column grow to 2 x 4096 x 8 bytes
-// (FP32) or more, which leaves one or two CTAs per SM; those CTAs get more
-// threads (at most 64 registers each) so that more loads are in flight.
+// Column-MAC CTAs: the two shared spectra of a column grow to 2 x 8192 x 8 bytes
+// (FP32) or 2 x 4096 x 16 (FP64), which leaves one CTA per SM; the FP32 one gets
+// 1024 threads (at most 64 registers each) so that more loads are in flight, the
+// FP64 one 512 (its allocation spills at 64).
 template <typename T>
 constexpr int lv_mac_threads(int py)
 {
-    return (sizeof(T) == 8 ? py >= 4096 : py >= 8192) ? 1024 : lv_col_threads(py);
+    return sizeof(T) == 8 ? (py >= 4096 ? 512 : lv_col_threads(py)) : (py >= 8192 ? 1024 : lv_col_threads(py));
 }
+// FP32 2048-point columns with two outputs: three CTAs of 256 threads per SM (at
+// most 85 registers)
 template <typename T>
-constexpr int lv_mac_minb(int py) { return sizeof(T) == 4 && py == 4096 ? 2 : (lv_mac_threads<T>(py) >= 1024 ? 1 : 0); }
+constexpr int lv_mac_minb(int py, int nout)
+{
+    return sizeof(T) == 4 && py == 4096               ? 2
+           : sizeof(T) == 4 && py == 2048 && nout == 2 ? 3
+                                                        : (lv_mac_threads<T>(py) >= 1024 ? 1 : 0);
+}
 
 template <typename K>
 sg_status smem_attr(K kern, size_t bytes)
@@ -767,25 +881,24 @@ sg_status launch_col_fwd(const lv_col_fwd_args<T> &A, int ncta, int lmax, cudaSt
 
 template <typename T, int PY, int NOUT>
 sg_status launch_col_mac_inv(const lv_mac_args &a, const cplx_t<T> *spec, const T *kspec, const cplx_t<T> *phx,
-                             const cplx_t<T> *phy, cplx_t<T> *out, const cplx_t<T> *tw, cudaStream_t st)
+                             const cplx_t<T> *phy, cplx_t<T> *out, const cplx_t<T> *cph, cudaStream_t st)
 {
     constexpr int TH = lv_mac_threads<T>(PY);
-    const size_t sm = NOUT * spad_size<cplx_t<T>>(PY) * sizeof(cplx_t<T>);
-    auto kern = k_lv_col_mac_inv<T, PY, TH, lv_mac_minb<T>(PY), NOUT>;
+    const size_t sm = spad_size<cplx_t<T>>(NOUT * PY) * sizeof(cplx_t<T>);
+    auto kern = k_lv_col_mac_inv<T, PY, TH, lv_mac_minb<T>(PY, NOUT), NOUT>;
     SG_TRY(smem_attr(kern, sm));
-    SG_CUDA_TRY(sg_launch_dep(kern, dim3(a.qx * a.nsrc), dim3(TH), sm, st, a, spec, kspec, phx, phy, out, tw));
+    SG_CUDA_TRY(sg_launch_dep(kern, dim3(a.qx * a.nsrc), dim3(TH), sm, st, a, spec, kspec, phx, phy, out, cph));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
 
 template <typename T, int PX>
-sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, int nout, T *fx, T *fy, const cplx_t<T> *tw,
-                         cudaStream_t st)
+sg_status launch_row_inv(const lv_row_inv_args<T> &A, int ncta, int nout, T *fx, T *fy, cudaStream_t st)
 {
     const size_t sm = spad_size<cplx_t<T>>(lv_nb(PX) * PX) * sizeof(cplx_t<T>);
     auto kern = k_lv_row_inv<T, PX>;
     SG_TRY(smem_attr(kern, sm));
-    SG_CUDA_TRY(sg_launch_dep(kern, dim3(ncta, nout), dim3(LV_ROW_THREADS), sm, st, A, fx, fy, tw));
+    SG_CUDA_TRY(sg_launch_dep(kern, dim3(ncta, nout), dim3(LV_ROW_THREADS), sm, st, A, fx, fy));
     SG_CUDA_TRY(cudaGetLastError());
     return SG_OK;
 }
@@ -813,7 +926,6 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *out0, void *ou
     const int qx = lv.px / 2 + 1;
     const int64_t *twoff = sizeof(T) == 8 ? plan->tw64_off : plan->tw32_off;
     auto twid = [&](int L) { return (const C *)((const char *)plan->twiddles + twoff[sg_ilog2(L)]); };
-    const C *twx = twid(lv.px), *twy = twid(lv.py);
     const C *cphx = (const C *)lv.cphase, *cphy = cphx + lv.px + 1;
     C *wf = (C *)ws->work_fwd;
     C *wi = (C *)ws->work_inv;
@@ -879,18 +991,22 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *out0, void *ou
                 a.key[m][l] = lv.key[m][l];
                 a.d2[m][l] = lv.key_d2[lv.key[m][l]];
             }
+            const int fy = lv_fold_targets(lv.py) ? M.cy : 0;  // target fold exponent
             a.ny[m] = M.ny;
-            a.j0[m] = M.j0;
-            a.t[m] = M.s;
+            a.p0[m] = M.j0 >> fy;
+            a.st[m] = M.s - fy;
+            a.lm[m] = sg_ilog2(lv.py >> fy);
+            a.fh[m] = fy == M.s && M.s >= 1;
+            a.tw[m] = twid(lv.py >> fy);
             a.inv_off[m] = M.inv_off;
         }
         a.qx = qx;
         const C *phx = (const C *)lv.phase, *phy = phx + lv.px + 1;
         if (pot) {
-            SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP, 1>(a, spec, (const T *)lv.pspectra, phx, phy, wi, twy,
+            SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP, 1>(a, spec, (const T *)lv.pspectra, phx, phy, wi, cphy,
                                                                       st))));
         } else {
-            SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP, 2>(a, spec, (const T *)lv.spectra, phx, phy, wi, twy,
+            SG_LV_SWITCH(lv.py, SG_TRY((launch_col_mac_inv<T, PP, 2>(a, spec, (const T *)lv.spectra, phx, phy, wi, cphy,
                                                                       st))));
         }
     }
@@ -904,12 +1020,15 @@ sg_status lv_solve_t(sg_plan *plan, const sg_workspace *ws, void *out0, void *ou
         for (int l = 0; l < lv.nlev; ++l) {
             const sg_lv_level &L = lv.lev[l];
             A.cta0[l] = ncta;
-            A.a[l] = {L.map, L.nx, L.ny, L.i0, L.s};
+            const int fx = lv_fold_targets(lv.px) ? L.cx : 0;
+            A.a[l] = {L.map, L.nx, L.ny, L.i0 >> fx, L.s - fx, sg_ilog2(lv.px >> fx), fx == L.s && L.s >= 1};
             A.in[l] = wi + L.inv_off;
+            A.tw[l] = twid(lv.px >> fx);
             ncta += (L.ny + 2 * lv_nb(lv.px) - 1) / (2 * lv_nb(lv.px));
         }
         A.cta0[lv.nlev] = ncta;
-        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_inv<T, PP>(A, ncta, pot ? 1 : 2, (T *)out0, (T *)out1, twx, st))));
+        A.cph = cphx;
+        SG_LV_SWITCH(lv.px, SG_TRY((launch_row_inv<T, PP>(A, ncta, pot ? 1 : 2, (T *)out0, (T *)out1, st))));
     }
     sg_timing_end(ws, SG_STAGE_ROW_INV, st);
     return SG_OK;

@@ -218,3 +218,22 @@ def test_levels_8192_four_levels_sampled(sg):
     rng = np.random.Generator(np.random.PCG64(44))
     idx = np.sort(rng.choice(nleaf, 96, replace=False))
     _check(sg, patches, "fp32", 2, sig, sx, sy, 1e-5, target_index=idx, cross=2)
+
+
+def test_levels_4096_fp64_sampled(sg):
+    """Three nested 512^2 levels (finest extent 2048, 4096-point transforms, the
+    FP64 limit), exponential disk, FP64: 64 sampled leaves on every level against
+    the plain leaf-pair sum (coarse targets take the folded inverse transforms)."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(512, 3))]
+    sig, sx, sy = [], [], []
+    for p in patches:
+        X, Y = W.cell_centres(*p[1:])
+        a, b, c = W.exponential_sigma(X, Y, 0.1)
+        sig.append(a)
+        sx.append(b)
+        sy.append(c)
+    n0 = 512 * 512 - 256 * 256
+    rng = np.random.Generator(np.random.PCG64(45))
+    idx = np.sort(np.concatenate([rng.choice(n0, 64, replace=False), n0 + rng.choice(n0, 64, replace=False),
+                                  2 * n0 + rng.choice(512 * 512, 64, replace=False)]))
+    _check(sg, patches, "fp64", 2, sig, sx, sy, 1e-11, target_index=idx, cross=2)
