@@ -434,7 +434,8 @@ struct lv_col_fwd_args {
 };
 
 template <typename T, int LMAX>
-__global__ void __launch_bounds__(LV_CFWD_THREADS) k_lv_col_fwd(lv_col_fwd_args<T> A)
+__global__ void __launch_bounds__(LV_CFWD_THREADS, sizeof(T) == 4 && LMAX <= 4096 ? 3 : 1)
+    k_lv_col_fwd(lv_col_fwd_args<T> A)
 {
     sg_dep_trigger();
     sg_dep_wait();  // the row transforms
