@@ -559,7 +559,10 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
 __host__ __device__ constexpr int row_nb_default(int px) { return px >= 4096 ? 2 : (4096 / px < 2 ? 2 : 4096 / px); }
 __host__ __device__ constexpr int row_nb_inv_default(int px) { return px >= 4096 ? 2 : (px == 2048 ? 4 : 4096 / px); }
 __host__ __device__ constexpr int col_cb_default(int py) { return py >= 2048 ? 1 : 2048 / py; }
-constexpr int ROW_THREADS = 256;
+// Row-pass CTAs of 512 threads: a 1024² solve has only 256 row CTAs per pass,
+// and 512 threads (instead of 256) double the warps per SM; measured 2-3 %
+// faster per solve (potential, off-plane, central slopes), no spills.
+constexpr int ROW_THREADS = 512;
 
 // Candidate shapes: half, the default, and twice the default, where feasible
 // (shared memory within 200 KB, 32..512 threads per CTA: 1024 would cap registers at 64).
