@@ -433,8 +433,10 @@ struct lv_col_fwd_args {
     const cplx_t<T> *cphx, *cphy;
 };
 
+// (resident CTAs per SM asked of the register allocator: FP32 three at up to
+// 4096 points, two at 8192; FP64 two)
 template <typename T, int LMAX>
-__global__ void __launch_bounds__(LV_CFWD_THREADS, sizeof(T) == 4 && LMAX <= 4096 ? 3 : 1)
+__global__ void __launch_bounds__(LV_CFWD_THREADS, sizeof(T) == 4 ? (LMAX <= 4096 ? 3 : 2) : (LMAX <= 4096 ? 2 : 1))
     k_lv_col_fwd(lv_col_fwd_args<T> A)
 {
     sg_dep_trigger();
