@@ -235,3 +235,34 @@ def test_amr_potential_matches_force(sg):
     gy = -(P[2:, 1:-1] - P[:-2, 1:-1]) / (2 * h)
     err = np.hypot(gx - FX[1:-1, 1:-1], gy - FY[1:-1, 1:-1])
     assert float(np.sqrt(np.mean(err ** 2))) < 2e-2 * float(np.sqrt(np.mean(FX[1:-1, 1:-1] ** 2 + FY[1:-1, 1:-1] ** 2)))
+
+
+def _exp_levels(sg, n, levels):
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(n, levels))]
+    sig, sx, sy = [], [], []
+    for p in patches:
+        X, Y = W.cell_centres(*p[1:])
+        a, b, c = W.exponential_sigma(X, Y, 0.1)
+        sig.append(a)
+        sx.append(b)
+        sy.append(c)
+    return patches, sig, sx, sy
+
+
+def _per_level_sample(counts, k, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    off = np.concatenate([[0], np.cumsum(counts)])
+    return np.sort(np.concatenate([off[i] + rng.choice(c, k, replace=False) for i, c in enumerate(counts)]))
+
+
+@pytest.mark.parametrize("prec, tol, levels", [("fp32", 1e-5, 4), ("fp64", 1e-11, 3)])
+def test_amr_potential_long_transforms_sampled(sg, prec, tol, levels):
+    """Nested 512^2 levels of an exponential disk: four in FP32 (8192-point
+    transforms), three in FP64 (4096, its limit), where the coarse target levels
+    take the folded inverse transforms; 48 sampled leaves per level against the
+    plain leaf sum."""
+    patches, sig, sx, sy = _exp_levels(sg, 512, levels)
+    n0 = 512 * 512 - 256 * 256
+    counts = [n0] * (levels - 1) + [512 * 512]
+    idx = _per_level_sample(counts, 48, 46 + levels)
+    _amr_check(sg, patches, prec, 2, sig, sx, sy, tol, target_index=idx)
