@@ -645,7 +645,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a,
     // the same kernel values (kq = j); slot 0 holds bins 0 and PY/2 (kq = 0 and PY/2).
     // V slots per thread at a time, so that their loads are in flight together.
     constexpr int NSLOT = PY / 2;
-    constexpr int VMAX = sizeof(T) == 8 ? 1 : 2;
+    // (FP32 2048-point force columns: one slot pair, 56 registers, four CTAs per
+    // SM measured 2 % faster than two pairs at three CTAs; two pairs elsewhere,
+    // measured faster than one at 4096 and 8192 points)
+    constexpr int VMAX = sizeof(T) == 8 ? 1 : (NOUT == 2 && PY == 2048 ? 1 : 2);
     constexpr int V = NSLOT / THREADS >= VMAX ? VMAX : 1;
     const C phk = phx[kx + (a.qx - 1)];
     for (int j0 = threadIdx.x; j0 < NSLOT; j0 += V * THREADS) {
@@ -843,13 +846,13 @@ constexpr int lv_mac_threads(int py)
 {
     return sizeof(T) == 8 ? (py >= 4096 ? 512 : lv_col_threads(py)) : (py >= 8192 ? 1024 : lv_col_threads(py));
 }
-// FP32 2048-point columns with two outputs: three CTAs of 256 threads per SM (at
-// most 85 registers)
+// FP32 2048-point columns with two outputs: four CTAs of 256 threads per SM (at
+// most 64 registers; one slot pair per thread)
 template <typename T>
 constexpr int lv_mac_minb(int py, int nout)
 {
     return sizeof(T) == 4 && py == 4096               ? 2
-           : sizeof(T) == 4 && py == 2048 && nout == 2 ? 3
+           : sizeof(T) == 4 && py == 2048 && nout == 2 ? 4
                                                         : (lv_mac_threads<T>(py) >= 1024 ? 1 : 0);
 }
 
