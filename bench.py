@@ -854,7 +854,7 @@ def run_gpu(args):
 # amr3 col_conv: the stage's column-transform and column-MAC launches, one each
 # per solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
 TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.004e6,
-           ("amr3", "col_conv"): (11.152e6 + 7.286e6) + (227.535e6 + 10.888e6)}
+           ("amr3", "col_conv"): (11.152e6 + 7.286e6) + (226.808e6 + 11.011e6)}
 
 
 def _pad(n):
