@@ -843,10 +843,46 @@ def run_gpu(args):
         "wall_s": wall,
     }
     if world == 1 and not args.no_cpu_baseline:
-        sps, tps, secs, thr, what = OracleSample(wl, potential=pot).run(args.cpu_targets)
+        sampler = OracleSample(wl, potential=pot)
+        sps, tps, secs, thr, what = sampler.run(args.cpu_targets)
         line["cpu_baseline"] = {"value": sps, "unit": "solves/s", "cores": thr, "kind": "oracle", "sample": what,
                                 "target_cells_per_s": tps, "seconds": secs}
+        # the same sum on one core (a sixteenth of the sample)
+        sps1, tps1, secs1, _, what1 = sampler.run(max(16, args.cpu_targets // 16), nthreads=1)
+        line["cpu_baseline"]["single_core"] = {"value": sps1, "unit": "solves/s", "cores": 1, "sample": what1,
+                                               "target_cells_per_s": tps1, "seconds": secs1}
+        fft = oracle_fft_route(wl) if not pot and not zt and zones is None else None
+        if fft is not None:
+            line["cpu_baseline"]["fft_route"] = fft
     print(json.dumps(line), flush=True)
+
+
+def oracle_fft_route(wl, reps=3):
+    """The oracle's FP64 FFT route (numpy pocketfft, one thread) on the whole
+    workload when it is one uniform in-plane patch: median of `reps` calls, each
+    building its own kernel tables as the oracle does. None otherwise."""
+    if "zones" in wl or len(wl["patches"]) != 1 or wl.get("z", 0.0) != 0.0 or wl.get("masks") is not None:
+        return None
+    from oracle.fftconv import central_slopes, uniform_fft_force
+    _, nx, ny, _, _, h = wl["patches"][0]
+    s = np.asarray(wl["sigma"], np.float64).reshape(ny, nx)
+    if wl["slope_mode"] == 1:
+        dx, dy = central_slopes(s, h)
+    elif wl["slope_mode"] == 2:
+        dx = np.asarray(wl["dx"], np.float64).reshape(ny, nx)
+        dy = np.asarray(wl["dy"], np.float64).reshape(ny, nx)
+    else:
+        dx = dy = None
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        uniform_fft_force(s, dx, dy, h)
+        times.append(time.perf_counter() - t0)
+    med = float(np.median(times))
+    return {"value": 1.0 / med, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "the whole workload through the oracle's FP64 FFT route (numpy pocketfft, one thread, its "
+                      "kernel tables built in every call); median of %d calls" % reps,
+            "target_cells_per_s": wl["targets"] / med, "seconds": med}
 
 
 # DRAM bytes (read + write) per launch of a stage's kernel from the ncu capture
