@@ -553,6 +553,7 @@ class OracleSample:
     def __init__(self, wl, potential=False):
         from oracle import amr as oamr
         self.potential = potential
+        self.z = wl.get("z", 0.0)  # off the plane: the three-component sum at height z
         from oracle.fftconv import central_slopes
         self.total_targets = wl["targets"]
         self.rng = np.random.Generator(np.random.PCG64(77))
@@ -597,12 +598,16 @@ class OracleSample:
 
     def run(self, sample_targets, nthreads=0):
         """Returns (solves/s, target-cells/s, seconds, threads, description)."""
-        from oracle.direct import direct_force, max_threads
+        from oracle.direct import direct_force, direct_force3, max_threads
         from oracle.potential import direct_potential
         tsel = self.rng.choice(self.tx.size, sample_targets, replace=False)
         t0 = time.perf_counter()
-        f = direct_potential if self.potential else direct_force
-        f(self.cells, self.s0, self.sx, self.sy, self.tx[tsel], self.ty[tsel], nthreads=nthreads)
+        if self.z != 0.0 and not self.potential:
+            direct_force3(self.cells, self.s0, self.sx, self.sy, self.tx[tsel], self.ty[tsel], self.z,
+                          nthreads=nthreads)
+        else:
+            f = direct_potential if self.potential else direct_force
+            f(self.cells, self.s0, self.sx, self.sy, self.tx[tsel], self.ty[tsel], nthreads=nthreads)
         dt = time.perf_counter() - t0
         threads = nthreads or max_threads()
         tps = sample_targets / dt
@@ -851,7 +856,7 @@ def run_gpu(args):
         sps1, tps1, secs1, _, what1 = sampler.run(max(16, args.cpu_targets // 16), nthreads=1)
         line["cpu_baseline"]["single_core"] = {"value": sps1, "unit": "solves/s", "cores": 1, "sample": what1,
                                                "target_cells_per_s": tps1, "seconds": secs1}
-        fft = oracle_fft_route(wl) if not pot and not zt and zones is None else None
+        fft = oracle_fft_route(wl) if not pot and zones is None else None
         if fft is not None:
             line["cpu_baseline"]["fft_route"] = fft
     print(json.dumps(line), flush=True)
@@ -859,11 +864,13 @@ def run_gpu(args):
 
 def oracle_fft_route(wl, reps=3):
     """The oracle's FP64 FFT route (numpy pocketfft, one thread) on the whole
-    workload when it is one uniform in-plane patch: median of `reps` calls, each
-    building its own kernel tables as the oracle does. None otherwise."""
-    if "zones" in wl or len(wl["patches"]) != 1 or wl.get("z", 0.0) != 0.0 or wl.get("masks") is not None:
+    workload when it is one uniform patch (in the plane, or at height z): median
+    of `reps` calls, each building its own kernel tables as the oracle does. None
+    otherwise."""
+    if "zones" in wl or len(wl["patches"]) != 1 or wl.get("masks") is not None:
         return None
-    from oracle.fftconv import central_slopes, uniform_fft_force
+    from oracle.fftconv import central_slopes, uniform_fft_force, uniform_fft_force3
+    z = wl.get("z", 0.0)
     _, nx, ny, _, _, h = wl["patches"][0]
     s = np.asarray(wl["sigma"], np.float64).reshape(ny, nx)
     if wl["slope_mode"] == 1:
@@ -876,7 +883,10 @@ def oracle_fft_route(wl, reps=3):
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        uniform_fft_force(s, dx, dy, h)
+        if z != 0.0:
+            uniform_fft_force3(s, dx, dy, h, z)
+        else:
+            uniform_fft_force(s, dx, dy, h)
         times.append(time.perf_counter() - t0)
     med = float(np.median(times))
     return {"value": 1.0 / med, "unit": "solves/s", "cores": 1, "kind": "oracle",
