@@ -618,11 +618,12 @@ __device__ __forceinline__ void lv_inv_columns(C *bx, const C *__restrict__ tw)
 // side by side and read its source spectra (and shared kernel planes) from L2:
 // Fx^, Fy^ = sum over source levels and fields of source spectrum (unfolded
 // from the compact one) x kernel spectrum (decompressed, see k_lv_extract),
-// formed element by element straight into two shared buffers; for a coarse
-// target level folded onto its compact column length (lv_fold_spectrum); inverse
-// column transforms of that length; the target level's sampled rows to
-// out[(o qx + kx) ny + j] (out at the level's inverse-column offset). NOUT = 1: the potential, one
-// output from 3 kernel planes per key (p0 real, px and py imaginary; py odd in ky).
+// formed element by element straight into two shared buffers; from 4096-point
+// columns up, for a coarse target level, folded in place onto its compact column
+// length (lv_fold_bin); inverse column transforms of that length; the target
+// level's sampled rows to out[(o qx + kx) ny + j] (out at the level's
+// inverse-column offset). NOUT = 1: the potential, one output from 3 kernel
+// planes per key (p0 real, px and py imaginary; py odd in ky).
 template <typename T, int PY, int THREADS, int MINB, int NOUT>
 __global__ void __launch_bounds__(THREADS, MINB) k_lv_col_mac_inv(lv_mac_args a, const cplx_t<T> *__restrict__ spec,
                                                             const T *__restrict__ kspec,
