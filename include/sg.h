@@ -483,6 +483,22 @@ sg_status sg_cancel(sg_server *server, uint64_t ticket);
  * latency samples are cleared afterwards when reset_latencies != 0). */
 sg_status sg_server_get_stats(sg_server *server, sg_server_stats *out, int reset_latencies);
 
+/* ------------------------------------------------------------------------
+ * Pipe calibration (not in the paper): the arithmetic peaks the roofline
+ * fractions of the direct sum and the transforms divide by, measured on the
+ * current device (every SM, 8 CTAs x 256 threads each, independent chains per
+ * thread, best of five timed launches after a warm-up).
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    SG_PEAK_FP64_FMA = 0,   /* FP64 fused multiply-add, flop/s (2 per FMA) */
+    SG_PEAK_FP32_FMA = 1,   /* FP32 fused multiply-add, flop/s (2 per FMA) */
+    SG_PEAK_FP32_LG2 = 2    /* FP32 base-2 logarithm (special-function unit), results/s */
+} sg_peak_kind;
+
+/* Measure one peak (synchronous on the current device; allocates and frees a
+ * small output buffer). Errors: SG_EINVAL (kind, NULL out), SG_ECUDA. */
+sg_status sg_alu_peak(int kind, double *ops_per_s);
+
 /* Static, human-readable name of a status. */
 const char *sg_strerror(sg_status status);
 

@@ -243,14 +243,17 @@ sg_status analyse(const sg_geom *g, geom_info &gi)
 
 size_t elem_size(sg_precision prec) { return prec == SG_FP64 ? 8 : 4; }
 
-// corner tiles of every patch (the composite sources cover whole patches); with
-// masks, tiles whose corners touch no existing cell carry zero weights and are left out
-void build_tiles(const sg_geom *g, const geom_info &gi, std::vector<sg_tile_desc> &tiles, std::vector<int> &first,
-                 std::vector<int> &count)
+// Source tiles of every patch (the composite sources cover whole patches):
+// 16 x 16 corners for the FP64 corner-form sum, 16 x 16 cells for the FP32
+// near/far sum. With masks, tiles that touch no existing cell carry zero
+// weights and are left out.
+void build_tiles(const sg_geom *g, const geom_info &gi, bool cell_tiles, std::vector<sg_tile_desc> &tiles,
+                 std::vector<int> &first, std::vector<int> &count)
 {
     first.assign(gi.n, 0);
     count.assign(gi.n, 0);
     std::vector<int64_t> sat;  // summed-area table of existing cells, (ny + 1) x (nx + 1)
+    const int extra = cell_tiles ? 0 : 1;  // a patch has nx + 1 corners per row, nx cells
     for (int k = 0; k < gi.n; ++k) {
         const sg_patch &p = g->patches[k];
         const bool masked = g->masks && g->masks[k];
@@ -263,13 +266,14 @@ void build_tiles(const sg_geom *g, const geom_info &gi, std::vector<sg_tile_desc
                         sat[(size_t)(j + 1) * (p.nx + 1) + i] - sat[(size_t)j * (p.nx + 1) + i];
         }
         first[k] = (int)tiles.size();
-        const int ntx = (p.nx + 1 + SG_TILE_X - 1) / SG_TILE_X, nty = (p.ny + 1 + SG_TILE_Y - 1) / SG_TILE_Y;
+        const int ntx = (p.nx + extra + SG_TILE_X - 1) / SG_TILE_X, nty = (p.ny + extra + SG_TILE_Y - 1) / SG_TILE_Y;
         for (int b = 0; b < nty; ++b) {
             for (int a = 0; a < ntx; ++a) {
                 const int ci0 = a * SG_TILE_X, cj0 = b * SG_TILE_Y;
                 if (masked) {
-                    // cells around the tile's corners: i in [ci0 - 1, ci0 + TILE_X - 1], same in j
-                    const int i0 = ci0 > 0 ? ci0 - 1 : 0, j0 = cj0 > 0 ? cj0 - 1 : 0;
+                    // cells of the tile (cell tiles: i in [ci0, ci0 + TILE_X - 1]) or around
+                    // its corners (corner tiles: i in [ci0 - 1, ci0 + TILE_X - 1]); same in j
+                    const int i0 = ci0 - extra > 0 ? ci0 - extra : 0, j0 = cj0 - extra > 0 ? cj0 - extra : 0;
                     const int i1 = ci0 + SG_TILE_X < p.nx ? ci0 + SG_TILE_X : p.nx;
                     const int j1 = cj0 + SG_TILE_Y < p.ny ? cj0 + SG_TILE_Y : p.ny;
                     const int64_t w = p.nx + 1;
@@ -289,6 +293,46 @@ void build_tiles(const sg_geom *g, const geom_info &gi, std::vector<sg_tile_desc
             }
         }
         count[k] = (int)tiles.size() - first[k];
+    }
+}
+
+// Leaf targets of the direct sum and their blocks: per patch, the leaves of
+// every 16 x 16-cell square, row-major inside the square (a block is compact,
+// so the distance from a source tile to all of its targets is bounded from below).
+void build_targets(const sg_geom *g, const geom_info &gi, std::vector<int4> &tg, std::vector<sg_target_block> &blocks)
+{
+    tg.clear();
+    blocks.clear();
+    tg.reserve((size_t)gi.nleaves);
+    for (int k = 0; k < gi.n; ++k) {
+        const sg_patch &p = g->patches[k];
+        for (int bj = 0; bj < p.ny; bj += 16) {
+            for (int bi = 0; bi < p.nx; bi += 16) {
+                sg_target_block b;
+                memset(&b, 0, sizeof(b));
+                b.patch = k;
+                b.first = (int)tg.size();
+                b.tx0 = b.ty0 = INT32_MAX;
+                b.tx1 = b.ty1 = INT32_MIN;
+                for (int j = bj; j < std::min(bj + 16, p.ny); ++j) {
+                    for (int i = bi; i < std::min(bi + 16, p.nx); ++i) {
+                        if (gi.code[k][(size_t)j * p.nx + i] != SG_CELL_LEAF) continue;
+                        int4 t;
+                        t.x = gi.ox[k] + (2 * i + 1) * (gi.step[k] / 2);
+                        t.y = gi.oy[k] + (2 * j + 1) * (gi.step[k] / 2);
+                        t.z = (int)(gi.cell_off[k] + (int64_t)j * p.nx + i);
+                        t.w = k;
+                        tg.push_back(t);
+                        b.tx0 = std::min(b.tx0, t.x);
+                        b.tx1 = std::max(b.tx1, t.x);
+                        b.ty0 = std::min(b.ty0, t.y);
+                        b.ty1 = std::max(b.ty1, t.y);
+                        b.count++;
+                    }
+                }
+                if (b.count > 0) blocks.push_back(b);
+            }
+        }
     }
 }
 
@@ -376,10 +420,14 @@ bool lv_params(const sg_geom *g, const geom_info &gi, sg_precision prec, sg_lv_s
     return true;
 }
 
-int choose_nsplit(int nblocks, int ntiles, int nsm)
+// Source-tile ranges per target block. FP64 plans: enough (block, range) CTAs
+// for two per SM. FP32 plans: work items of the persistent far-field launch,
+// about 32 per SM so that dynamic scheduling evens out their unequal costs.
+int choose_nsplit(int nblocks, int ntiles, int nsm, sg_precision prec)
 {
     if (nblocks <= 0) return 1;
-    int s = (2 * nsm + nblocks - 1) / nblocks;
+    const int want = prec == SG_FP64 ? 2 * nsm : 32 * nsm;
+    int s = (want + nblocks - 1) / nblocks;
     const int cap = ntiles / 4 > 1 ? ntiles / 4 : 1;
     if (s > cap) s = cap;
     if (s < 1) s = 1;
@@ -410,19 +458,30 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
     for (int L = SG_MIN_PAD; L <= s.max_pad; L <<= 1) s.twiddles += (int64_t)L * (16 + 8);
     if (gi.n > 1 || gi.masked) s.direct = 3 * gi.ncells * (int64_t)es + gi.ncells * (int64_t)sizeof(int);
     if (gi.n > 1 && lv_bytes < 0) {
+        const int64_t slices = prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1;
         s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
                     gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
-                    (nsplit > 1 ? (int64_t)nsplit * gi.nleaves * 16 : 0);
+                    slices * gi.nleaves * 16;
     }
     s.geometry = (int64_t)gi.n * (int64_t)sizeof(sg_patch_dev) + 16 * (int64_t)gi.n;
     return s;
 }
 
-int count_blocks(const geom_info &gi)
+int count_blocks(const sg_geom *g, const geom_info &gi)
 {
     if (gi.n <= 1) return 0;
     int64_t b = 0;
-    for (int k = 0; k < gi.n; ++k) b += (gi.nleaf[k] + SG_DIRECT_THREADS - 1) / SG_DIRECT_THREADS;
+    for (int k = 0; k < gi.n; ++k) {
+        const sg_patch &p = g->patches[k];
+        for (int bj = 0; bj < p.ny; bj += 16)
+            for (int bi = 0; bi < p.nx; bi += 16) {
+                bool any = false;
+                for (int j = bj; j < std::min(bj + 16, p.ny) && !any; ++j)
+                    for (int i = bi; i < std::min(bi + 16, p.nx) && !any; ++i)
+                        any = gi.code[k][(size_t)j * p.nx + i] == SG_CELL_LEAF;
+                b += any;
+            }
+    }
     return (int)b;
 }
 
@@ -498,12 +557,12 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     }
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tfirst, tcount;
-    if (gi.n > 1 && !use_lv) build_tiles(g, gi, tiles, tfirst, tcount);
+    if (gi.n > 1 && !use_lv) build_tiles(g, gi, prec == SG_FP32, tiles, tfirst, tcount);
     int dev = 0, nsm = 152;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     SG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int nblocks = use_lv ? 0 : count_blocks(gi);
-    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), nsm);
+    const int nblocks = use_lv ? 0 : count_blocks(g, gi);
+    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), nsm, prec);
     const sizes sz = plan_sizes(g, gi, prec, (int)tiles.size(), nblocks, nsplit, lv_bytes);
     if (budget && (size_t)sz.total() > budget) {
         set_error("plan exceeds the device-memory budget");
@@ -561,8 +620,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         d.pj0 = d.parent >= 0 ? (gi.oy[k] - gi.oy[d.parent]) / gi.step[d.parent] : 0;
         d.ncells_plane = gi.ncells;
         if (!tfirst.empty()) {
-            pp.tile_first = tfirst[k];
-            pp.tile_count = tcount[k];
+            pp.tile_first = d.tile_first = tfirst[k];
+            pp.tile_count = d.tile_count = tcount[k];
         }
         pdev[k] = d;
         const int nplanes = g->z != 0.0 ? 9 : 6;
@@ -626,35 +685,10 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
                          cudaSuccess ? SG_OK : SG_ECUDA;
         const size_t nw = (size_t)plan->ntiles * SG_TILE_N;
         plan->ws_tile_bytes = (int64_t)nw * (prec == SG_FP64 ? (int64_t)sizeof(sg_dvec4) : (int64_t)sizeof(float4));
-        // targets: every leaf, row-major per patch, blocks of SG_DIRECT_THREADS
+        // targets: every leaf, in blocks of the leaves of 16 x 16 cells
         std::vector<int4> tg;
         std::vector<sg_target_block> blocks;
-        tg.reserve((size_t)gi.nleaves);
-        for (int k = 0; k < gi.n; ++k) {
-            const sg_patch &p = g->patches[k];
-            int in_block = 0;
-            for (int j = 0; j < p.ny; ++j) {
-                for (int i = 0; i < p.nx; ++i) {
-                    if (gi.code[k][(size_t)j * p.nx + i] != SG_CELL_LEAF) continue;
-                    if (in_block == 0) {
-                        sg_target_block b;
-                        b.patch = k;
-                        b.first = (int)tg.size();
-                        b.count = 0;
-                        b.pad = 0;
-                        blocks.push_back(b);
-                    }
-                    int4 t;
-                    t.x = gi.ox[k] + (2 * i + 1) * (gi.step[k] / 2);
-                    t.y = gi.oy[k] + (2 * j + 1) * (gi.step[k] / 2);
-                    t.z = (int)(gi.cell_off[k] + (int64_t)j * p.nx + i);
-                    t.w = k;
-                    tg.push_back(t);
-                    blocks.back().count++;
-                    if (++in_block == SG_DIRECT_THREADS) in_block = 0;
-                }
-            }
-        }
+        build_targets(g, gi, tg, blocks);
         plan->ntargets = (int)tg.size();
         plan->nblocks = (int)blocks.size();
         if (st == SG_OK) st = dev_alloc(plan, &plan->targets, tg.size() * sizeof(int4));
@@ -665,7 +699,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         if (st == SG_OK)
             st = cudaMemcpy(plan->blocks, blocks.data(), blocks.size() * sizeof(sg_target_block),
                             cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
-        if (nsplit > 1) plan->ws_partial_bytes = (int64_t)nsplit * (int64_t)tg.size() * 2 * (int64_t)sizeof(double);
+        const int64_t slices = prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1;
+        plan->ws_partial_bytes = slices * (int64_t)tg.size() * 2 * (int64_t)sizeof(double);
+        if (st == SG_OK && prec == SG_FP32) st = sg_cross_far_grid(plan, nsm);
     }
     if (st == SG_OK) st = sg_twiddles_build(plan);
     if (st == SG_OK) st = sg_phase_build(plan);
@@ -678,7 +714,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         int n = use_lv ? 4 : gi.n * (central ? 4 : 3);
         if (plan->composite) {
             n += gi.lmax > 0 ? gi.lmax : 1;  // composite sources: covered cells of levels 1 .. lmax-1, then all S_l
-            if (plan->ntiles > 0) n += 2 + (nsplit > 1);
+            // direct sum: corner weights, pair sum (+ split reduction) in FP64; cell coefficients,
+            // far field, near field and the combination in FP32
+            if (plan->ntiles > 0) n += prec == SG_FP64 ? 2 + (nsplit > 1) : 4;
         }
         plan->launches = n;
     }
@@ -865,9 +903,9 @@ sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes)
         lv_bytes = -1;
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tf, tc;
-    if (gi.n > 1 && lv_bytes < 0) build_tiles(geom, gi, tiles, tf, tc);
-    const int nblocks = lv_bytes < 0 ? count_blocks(gi) : 0;
-    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152);
+    if (gi.n > 1 && lv_bytes < 0) build_tiles(geom, gi, prec == SG_FP32, tiles, tf, tc);
+    const int nblocks = lv_bytes < 0 ? count_blocks(geom, gi) : 0;
+    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152, prec);
     *bytes = plan_sizes(geom, gi, prec, (int)tiles.size(), nblocks, nsplit, lv_bytes).total();
     return SG_OK;
 }

@@ -106,18 +106,27 @@ struct __align__(32) sg_dvec4 {
 #define SG_MAX_PATCH_SIDE 2048
 #define SG_MAX_LEVELS 12
 
-// Corner tiles of the cross-patch direct sum: TILE_X x TILE_Y corners.
+// Source tiles of the cross-patch direct sum: TILE_X x TILE_Y corners (FP64
+// plans, corner form) or cells (FP32 plans, near/far split).
 #define SG_TILE_X 16
 #define SG_TILE_Y 16
 #define SG_TILE_N (SG_TILE_X * SG_TILE_Y)
-// Leaf targets per CTA of the direct sum.
+// Leaf targets per CTA of the direct sum (a block covers 16 x 16 cells of one patch).
 #define SG_DIRECT_THREADS 256
+// FP32 direct sum: a source cell whose centre lies less than SG_NEAR_R of its
+// own widths from the target along both axes is summed exactly in FP64 (near
+// field); every other cell by the expansion of its integrals about its centre,
+// through H^6 for tiles closer than SG_FAR_R4 cell widths to a block, through
+// H^4 beyond.
+#define SG_NEAR_R 6
+#define SG_FAR_R4 32
 
 struct sg_tile_desc {
     int patch;          // source patch
-    int ox, oy;         // lattice coordinates of corner (0, 0) of the tile
-    int step;           // corner spacing in lattice units
-    int ci0, cj0;       // first corner index (i, j) of the tile in its patch
+    int ox, oy;         // lattice coordinates of corner (0, 0) of the tile (corner tiles) or of
+                        // the lower-left corner of its cell (0, 0) (cell tiles)
+    int step;           // corner spacing (cell width) in lattice units
+    int ci0, cj0;       // first corner (cell) index (i, j) of the tile in its patch
     int pad0, pad1;
 };
 
@@ -126,6 +135,8 @@ struct sg_target_block {
     int first;          // first index into the target arrays
     int count;          // targets in the block (<= SG_DIRECT_THREADS)
     int pad;
+    int tx0, ty0;       // lattice bounding box of the block's target positions
+    int tx1, ty1;
 };
 
 struct sg_patch_dev {
@@ -138,6 +149,7 @@ struct sg_patch_dev {
     int parent;         // parent patch (-1 on level 0)
     int pi0, pj0;       // offset of this patch in its parent's cells
     int64_t ncells_plane;  // plane stride of the 3-field composite source arrays (= total cells)
+    int tile_first, tile_count;  // the patch's source tiles in the direct-sum tile list
 };
 
 // Level convolutions (lvconv.cu): every level's composite source sampled on the
@@ -239,10 +251,8 @@ struct sg_plan {
     // cross-patch direct sum
     int ntiles;
     sg_tile_desc *tiles;            // device
-    float4 *tile_w32;               // device, ntiles x SG_TILE_N x (B, X, Y, 0) weights (FP32 plans)
-    sg_dvec4 *tile_w64;              // the same in FP64 (FP64 plans)
     int nsplit;                     // source-tile ranges per target block
-    double *partial;                // device, nsplit x ntargets x 2 (nsplit > 1 only)
+    int far_grid;                   // CTAs of the persistent far-field launch (FP32 plans)
     int ntargets;
     int4 *targets;                  // device: (lattice x, lattice y, output index, patch)
     int nblocks;
@@ -263,10 +273,13 @@ struct sg_workspace {
     void *work_fwd;         // uniform-transform scratch: 3 x (px/2+1) x ny complex (largest patch)
     void *work_inv;         // 2 x (px/2+1) x ny complex
     void *sfield;           // AMR composite source fields, 3 x ncells of T
-    void *tile_w;           // AMR corner weights, ntiles x SG_TILE_N x 4 of T
-    double *partial;        // AMR split partial sums, nsplit x ntargets x 2 (nsplit > 1)
+    void *tile_w;           // AMR corner weights (FP64 plans) or cell coefficients (FP32 plans),
+                            // ntiles x SG_TILE_N x 4 of T
+    double *partial;        // AMR direct-sum partial sums: nsplit x ntargets x 2 (FP64 plans, nsplit > 1);
+                            // (nsplit + 1) x ntargets x 2, the last slice the near field (FP32 plans)
     void *zone_buf;         // zone plans: inputs (3 planes) and outputs (2 planes) in patch layout
-    int *err;               // device error word: nonzero after a bounded wait in a kernel ran out
+    int *err;               // device words: err[0] nonzero after a bounded wait in a kernel ran out;
+                            // err[1] the work-item counter of the persistent far-field launch
     struct sg_timing *timing;  // stage timers, or NULL
 };
 
@@ -318,6 +331,8 @@ sg_status sg_potential_spectra_build(sg_plan *plan);   // synchronous, patch 0
 void sg_tune_shape(sg_precision prec, int pad, int *shape);
 sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          void *fx, void *fy, cudaStream_t st);
+// Grid of the persistent far-field launch of an FP32 plan (sets plan->far_grid).
+sg_status sg_cross_far_grid(sg_plan *plan, int nsm);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          cudaStream_t st);
 sg_status sg_fft_lines_fp64(double2 *data, int L, int count, int64_t seq_stride, int64_t elem_stride,

@@ -4,11 +4,13 @@
 // over the cells of every patch other than its own, whose contribution comes
 // from the FFT convolution of its own patch.
 //
-// Corner form. Every cell integral is a double difference over the cell's four
-// corners, dd_i f = sum_c s_ic f(c - t) with s = +1 at the lower-left and
-// upper-right corners and -1 at the other two. Writing the reconstruction of
-// source i evaluated at the target, l_i(t) = sigma0_i + deltax_i (x_t - xc_i)
-// + deltay_i (y_t - yc_i), the closed forms of Section 2 give
+// Two evaluations of the same sum.
+//
+// FP64 plans: corner form. Every cell integral is a double difference over the
+// cell's four corners, dd_i f = sum_c s_ic f(c - t) with s = +1 at the
+// lower-left and upper-right corners and -1 at the other two. Writing the
+// reconstruction of source i evaluated at the target, l_i(t) = sigma0_i +
+// deltax_i (x_t - xc_i) + deltay_i (y_t - yc_i), the closed forms of Section 2 give
 //   Fx(t) = G sum_c [ -A_c(t) g0(c - t) + X_c v g0y(c - t) - Y_c r(c - t) ]
 //   Fy(t) = G sum_c [ -A_c(t) g0y(c - t) + Y_c u g0(c - t) - X_c r(c - t) ]
 // with A_c(t) = sum_i s_ic l_i(t), X_c = sum_i s_ic deltax_i, Y_c = sum_i s_ic deltay_i,
@@ -16,27 +18,57 @@
 // since the terms that depend on u alone (ln|u|) or v alone cancel in each
 // cell's double difference. On u = 0 the coincident-line form of Section 2,
 // sgn(v) ln|v|, is the same as g0 with ln|u| replaced by ln 2 (likewise for
-// g0y on v = 0), which is what the kernel evaluates. A_c(t) is linear in the
-// target position: A_c(t) = B_c + (x_t - x_T) X_c + (y_t - y_T) Y_c with B_c
-// built relative to the tile origin (x_T, y_T) so that its terms stay local.
+// g0y on v = 0). A_c(t) = B_c + (x_t - x_T) X_c + (y_t - y_T) Y_c with B_c
+// built relative to the tile origin (x_T, y_T). Pairs are summed in tiles of
+// 16 x 16 corners staged in shared memory, per tile and across tiles in FP64.
 //
-// All positions are integers on the lattice of half the finest cell width
-// (lambda), so u and v are exact; X and Y are stored premultiplied by lambda.
-// Pairs are summed in tiles of 16 x 16 corners staged in shared memory: FP32
-// per tile, then added to FP64 accumulators across tiles (compensation of the
-// long sum). FP64 plans run the same loop in FP64.
+// FP32 plans: near field in FP64, far field by the expansion of each cell's
+// integrals about its centre. The corner form is unsuited to FP32: a corner's
+// term is O(sigma) times an O(1) logarithm while a distant cell's integral is
+// O(sigma H^2 / rho^2), so rounding of every corner term, not the integrals,
+// sets the error (it grows like the square root of the number of corners).
+//  * Far cells (centre at least SG_NEAR_R cell widths from the target along
+//    some axis). With a, b = (centre - target) / H, rho^2 = a^2 + b^2, and the
+//    complex derivatives d = (d_a - i d_b) / 2, d~ = (d_a + i d_b) / 2, the
+//    integral of sigma0 + deltax xi + deltay eta times (1/rho) over the cell is
+//    an operator series in d, d~ applied to 1/rho (the moments of the square),
+//    and d^k d~^l (1/rho) = (-1)^(k+l) C_k C_l rho^-1 w^k conj(w)^l with
+//    w = 1/(a + i b), C_k = (2k - 1)!! / 2^k. The force is minus the gradient,
+//    Fx - i Fy = -2 d(...), which gives, per unit G, with s = 1/rho^2,
+//    m = sigma0, D = (deltax + i deltay) H:
+//      Q = rho^-1 { m [w (1 + s/8 + 7 s^2/256) - 21 w^5/512 - 7 s conj(w)^3/1536]
+//                 - D w^2/8 - conj(D) s/24
+//                 + 7 conj(D) w^4/384 + D s (conj(w)^2 - 7 w^2)/384 - 7 conj(D) s^2/640 }
+//    (terms through H^6; through H^4: m w (1 + s/8) - D w^2/8 - conj(D) s/24).
+//    Relative to 1/rho^2 the truncation is below 5e-7 from 6 cell widths on
+//    (through H^6) and below 1e-6 for the slope terms, 1e-7 for sigma0, from
+//    32 on (through H^4), both far under the 1e-5 the FP32 path is held to;
+//    every term is a small positive-scale product, so FP32 rounding stays
+//    relative to the cell's own contribution.
+//  * Near cells (both |a|, |b| < SG_NEAR_R): the closed forms in FP64, as the
+//    corner form over the corners of the box of near cells with weights from
+//    the box's cells only.
+// The far field is one persistent launch: each CTA takes (target block,
+// source-tile range) items from a counter, streams the tiles' cell
+// coefficients into a ring of shared-memory buffers by 1-D bulk copies (TMA)
+// completed on mbarriers, and sums per tile in FP32, across tiles in FP64. The
+// near field is one warp per target: lanes take the corners of the box, the
+// warp reduces with shuffles. A last launch adds the far partials, the near
+// field and the patch's own FFT result in a fixed order.
 #include "common.cuh"
+#include "tma.cuh"
 
 #include <math.h>
 
 namespace {
 
+// ================================================================= FP64 ====
+
 // One thread per (tile, corner): signed sums of the (up to) four cells of the
 // patch around the corner, from the composite source fields.
-template <typename T>
 __global__ void k_corner_weights(const sg_tile_desc *__restrict__ tiles, int ntiles, const sg_patch_dev *__restrict__ pd,
-                                 const T *__restrict__ sigma, const T *__restrict__ dx, const T *__restrict__ dy,
-                                 double lambda, T *__restrict__ wout)
+                                 const double *__restrict__ sigma, const double *__restrict__ dx,
+                                 const double *__restrict__ dy, double lambda, double *__restrict__ wout)
 {
     const int64_t total = (int64_t)ntiles * SG_TILE_N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -46,15 +78,14 @@ __global__ void k_corner_weights(const sg_tile_desc *__restrict__ tiles, int nti
         const int ci = td.ci0 + k % SG_TILE_X, cj = td.cj0 + k / SG_TILE_X;
         double B = 0.0, X = 0.0, Y = 0.0;
         if (ci <= p.nx && cj <= p.ny) {
-            // tile origin relative to cell centres, in lattice units
             for (int q = 0; q < 4; ++q) {
                 const int i = ci - 1 + (q & 1), j = cj - 1 + (q >> 1);
                 if (i < 0 || i >= p.nx || j < 0 || j >= p.ny) continue;
                 const double s = (q == 0 || q == 3) ? 1.0 : -1.0;
                 const int64_t o = p.cell_off + (int64_t)j * p.nx + i;
-                const double s0 = (double)sigma[o];
-                const double sx = dx ? (double)dx[o] : 0.0;
-                const double sy = dy ? (double)dy[o] : 0.0;
+                const double s0 = sigma[o];
+                const double sx = dx ? dx[o] : 0.0;
+                const double sy = dy ? dy[o] : 0.0;
                 // cell centre (lattice) = patch origin + (2i + 1) step / 2
                 const double cx = p.ox + (2 * i + 1) * (p.step / 2);
                 const double cy = p.oy + (2 * j + 1) * (p.step / 2);
@@ -63,10 +94,10 @@ __global__ void k_corner_weights(const sg_tile_desc *__restrict__ tiles, int nti
                 Y += s * sy;
             }
         }
-        wout[e * 4 + 0] = (T)B;
-        wout[e * 4 + 1] = (T)(X * lambda);
-        wout[e * 4 + 2] = (T)(Y * lambda);
-        wout[e * 4 + 3] = (T)0;
+        wout[e * 4 + 0] = B;
+        wout[e * 4 + 1] = X * lambda;
+        wout[e * 4 + 2] = Y * lambda;
+        wout[e * 4 + 3] = 0.0;
     }
 }
 
@@ -74,52 +105,7 @@ struct acc4 {
     double xl, xr, yl, yr;
 };
 
-// FP32 pair loop over one tile. g0 and g0y are evaluated as one base-2
-// logarithm of an O(1) ratio, log2((|v| + r) / |u|) and log2((|u| + r) / |v|)
-// (1/|u| and 1/|v| correctly rounded once per column and row; 1/2 on u = 0
-// or v = 0, which gives the coincident-line form), instead of a difference of
-// two logarithms of size ln(distance): the rounding of the result then scales
-// with the ratio, not with the distance. ln 2 is applied at the end.
-__device__ __forceinline__ void tile_pairs_f32(const float4 *__restrict__ w, float du0, float dv0, float st, float dxT,
-                                               float dyT, acc4 &acc)
-{
-    float iu[SG_TILE_X];
-#pragma unroll
-    for (int c = 0; c < SG_TILE_X; ++c) {
-        const float u = fmaf((float)c, st, du0);
-        iu[c] = u == 0.0f ? 0.5f : __frcp_rn(fabsf(u));
-    }
-    float sxl = 0.f, sxr = 0.f, syl = 0.f, syr = 0.f;
-#pragma unroll 1
-    for (int r = 0; r < SG_TILE_Y; ++r) {
-        const float v = fmaf((float)r, st, dv0);
-        // + 1e-30 keeps q > 0 where a zero-weight padding corner sits on a target
-        const float av = fabsf(v), v2 = fmaf(v, v, 1e-30f);
-        const float iv = v == 0.0f ? 0.5f : __frcp_rn(av);
-#pragma unroll
-        for (int c = 0; c < SG_TILE_X; ++c) {
-            const float4 wc = w[r * SG_TILE_X + c];
-            const float u = fmaf((float)c, st, du0);
-            const float q = fmaf(u, u, v2);
-            const float rr = q * rsqrtf(q);
-            const float g0 = copysignf(__log2f((av + rr) * iu[c]), v);
-            const float g0y = copysignf(__log2f((fabsf(u) + rr) * iv), u);
-            const float A = fmaf(dxT, wc.y, fmaf(dyT, wc.z, wc.x));
-            sxl = fmaf(-A, g0, sxl);
-            sxl = fmaf(wc.y, v * g0y, sxl);
-            sxr = fmaf(-wc.z, rr, sxr);
-            syl = fmaf(-A, g0y, syl);
-            syl = fmaf(wc.z, u * g0, syl);
-            syr = fmaf(-wc.y, rr, syr);
-        }
-    }
-    acc.xl += sxl;
-    acc.xr += sxr;
-    acc.yl += syl;
-    acc.yr += syr;
-}
-
-// FP64 pair loop over one tile (natural logarithms).
+// FP64 pair loop over one corner tile (natural logarithms).
 __device__ __forceinline__ void tile_pairs_f64(const sg_dvec4 *__restrict__ w, double du0, double dv0, double st,
                                                double dxT, double dyT, acc4 &acc)
 {
@@ -159,22 +145,13 @@ __device__ __forceinline__ void tile_pairs_f64(const sg_dvec4 *__restrict__ w, d
     acc.yr += syr;
 }
 
-template <typename T>
-struct vec4_of;
-template <>
-struct vec4_of<float> { using type = float4; };
-template <>
-struct vec4_of<double> { using type = sg_dvec4; };
-
 // grid (nblocks, nsplit); block SG_DIRECT_THREADS; one leaf target per thread.
-template <typename T>
 __global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_direct(
     const sg_target_block *__restrict__ blocks, const int4 *__restrict__ targets, const sg_tile_desc *__restrict__ tiles,
-    int ntiles, const T *__restrict__ wts, int nsplit, double G, T *__restrict__ fx, T *__restrict__ fy,
+    int ntiles, const double *__restrict__ wts, int nsplit, double G, double *__restrict__ fx, double *__restrict__ fy,
     double *__restrict__ partial, int ntargets)
 {
-    using V = typename vec4_of<T>::type;
-    __shared__ V sw[SG_TILE_N];
+    __shared__ sg_dvec4 sw[SG_TILE_N];
     const sg_target_block blk = blocks[blockIdx.x];
     const int split = blockIdx.y;
     const int t0 = (int)((int64_t)ntiles * split / nsplit);
@@ -183,30 +160,23 @@ __global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_direct(
     int4 tg = make_int4(0, 0, -1, -1);
     if (active) tg = targets[blk.first + threadIdx.x];
     acc4 acc = {0.0, 0.0, 0.0, 0.0};
-    const V *wv = reinterpret_cast<const V *>(wts);
+    const sg_dvec4 *wv = reinterpret_cast<const sg_dvec4 *>(wts);
     for (int t = t0; t < t1; ++t) {
         const sg_tile_desc td = tiles[t];
         if (td.patch == blk.patch) continue;  // same-patch pairs come from the FFT
         __syncthreads();
         for (int k = threadIdx.x; k < SG_TILE_N; k += SG_DIRECT_THREADS) sw[k] = wv[(int64_t)t * SG_TILE_N + k];
         __syncthreads();
-        const T du0 = (T)(td.ox - tg.x), dv0 = (T)(td.oy - tg.y);
-        const T dxT = (T)(tg.x - td.ox), dyT = (T)(tg.y - td.oy);
-        if (sizeof(T) == 4)
-            tile_pairs_f32(reinterpret_cast<const float4 *>(sw), (float)du0, (float)dv0, (float)td.step, (float)dxT,
-                           (float)dyT, acc);
-        else
-            tile_pairs_f64(reinterpret_cast<const sg_dvec4 *>(sw), (double)du0, (double)dv0, (double)td.step,
-                           (double)dxT, (double)dyT, acc);
+        tile_pairs_f64(sw, (double)(td.ox - tg.x), (double)(td.oy - tg.y), (double)td.step, (double)(tg.x - td.ox),
+                       (double)(tg.y - td.oy), acc);
     }
     if (!active) return;
-    const double lnk = sizeof(T) == 4 ? 0.69314718055994530942 : 1.0;
-    const double Fx = G * (lnk * acc.xl + acc.xr);
-    const double Fy = G * (lnk * acc.yl + acc.yr);
+    const double Fx = G * (acc.xl + acc.xr);
+    const double Fy = G * (acc.yl + acc.yr);
     const int ti = blk.first + threadIdx.x;
     if (nsplit == 1) {
-        fx[tg.z] = (T)((double)fx[tg.z] + Fx);
-        fy[tg.z] = (T)((double)fy[tg.z] + Fy);
+        fx[tg.z] += Fx;
+        fy[tg.z] += Fy;
     } else {
         partial[((int64_t)split * ntargets + ti) * 2 + 0] = Fx;
         partial[((int64_t)split * ntargets + ti) * 2 + 1] = Fy;
@@ -214,9 +184,8 @@ __global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_direct(
 }
 
 // Fixed-order sum of the per-split partials into the outputs.
-template <typename T>
 __global__ void k_cross_reduce(const int4 *__restrict__ targets, int ntargets, int nsplit,
-                               const double *__restrict__ partial, T *__restrict__ fx, T *__restrict__ fy)
+                               const double *__restrict__ partial, double *__restrict__ fx, double *__restrict__ fy)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntargets; t += gridDim.x * blockDim.x) {
         double sx = 0.0, sy = 0.0;
@@ -225,45 +194,431 @@ __global__ void k_cross_reduce(const int4 *__restrict__ targets, int ntargets, i
             sy += partial[((int64_t)s * ntargets + t) * 2 + 1];
         }
         const int o = targets[t].z;
-        fx[o] = (T)((double)fx[o] + sx);
-        fy[o] = (T)((double)fy[o] + sy);
+        fx[o] += sx;
+        fy[o] += sy;
     }
 }
 
-template <typename T>
-sg_status cross_solve_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
-                        void *fx, void *fy, cudaStream_t st)
+sg_status cross_solve_f64(sg_plan *plan, const sg_workspace *ws, const double *sigma, const double *dx,
+                          const double *dy, double *fx, double *fy, cudaStream_t st)
 {
-    if (plan->ntiles == 0 || plan->ntargets == 0) return SG_OK;
-    T *w = (T *)ws->tile_w;
+    double *w = (double *)ws->tile_w;
     const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
     int grid_w = (int)((nw + 255) / 256);
     if (grid_w > 65535) grid_w = 65535;
     sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
-    k_corner_weights<T><<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, (const T *)sigma,
-                                                 (const T *)dx, (const T *)dy, plan->lattice_unit, w);
+    k_corner_weights<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+                                             plan->lattice_unit, w);
     SG_CUDA_TRY(cudaGetLastError());
     sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
     sg_timing_begin(ws, SG_STAGE_DIRECT, st);
     dim3 grid(plan->nblocks, plan->nsplit);
-    k_cross_direct<T><<<grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->targets, plan->tiles, plan->ntiles, w,
-                                                          plan->nsplit, plan->geom.G, (T *)fx, (T *)fy,
-                                                          ws->partial, plan->ntargets);
+    k_cross_direct<<<grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->targets, plan->tiles, plan->ntiles, w,
+                                                       plan->nsplit, plan->geom.G, fx, fy, ws->partial,
+                                                       plan->ntargets);
     SG_CUDA_TRY(cudaGetLastError());
     if (plan->nsplit > 1) {
-        k_cross_reduce<T><<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
-                                                                         ws->partial, (T *)fx, (T *)fy);
+        k_cross_reduce<<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
+                                                                      ws->partial, fx, fy);
         SG_CUDA_TRY(cudaGetLastError());
     }
     sg_timing_end(ws, SG_STAGE_DIRECT, st);
     return SG_OK;
 }
 
+// ================================================================= FP32 ====
+
+constexpr int FAR_STAGES = 4;
+constexpr uint32_t TILE_BYTES = SG_TILE_N * sizeof(float4);
+
+// Cell coefficients of every tile, (sigma0, deltax H / 8, deltay H / 8, 0) of
+// the composite source (zero outside the patch); also resets the far-field
+// launch's work counter.
+__global__ void k_cell_coefs(const sg_tile_desc *__restrict__ tiles, int ntiles, const sg_patch_dev *__restrict__ pd,
+                             const float *__restrict__ sigma, const float *__restrict__ dx,
+                             const float *__restrict__ dy, double lambda, float4 *__restrict__ wout,
+                             int *__restrict__ counter)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+    const int64_t total = (int64_t)ntiles * SG_TILE_N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e / SG_TILE_N), k = (int)(e % SG_TILE_N);
+        const sg_tile_desc td = tiles[t];
+        const sg_patch_dev &p = pd[td.patch];
+        const int nx = p.nx, ny = p.ny;
+        const int i = td.ci0 + k % SG_TILE_X, j = td.cj0 + k / SG_TILE_X;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < nx && j < ny) {
+            const int64_t o = p.cell_off + (int64_t)j * nx + i;
+            const double h8 = p.step * lambda * 0.125;
+            c.x = sigma[o];
+            c.y = (float)((double)dx[o] * h8);
+            c.z = (float)((double)dy[o] * h8);
+        }
+        wout[e] = c;
+    }
+}
+
+// Contribution Q = (Fx - i Fy) / G of one cell (see the file comment),
+// accumulated into (qr, qi). (a, b): centre minus target in cell widths, b2 =
+// b^2, tb = 2 b; c = (m, d_x, d_y) with d = D / 8. Through H^4, in real form
+// with s = 1/rho^2, ir3 = rho^-3, ir5 = rho^-5, c2 = a^2 - b^2, ab2 = 2 a b:
+//   Re Q = m (1 + s/8) ir3 a - d_x (ir5 c2 + ir3/3) - d_y ir5 ab2
+//   Im Q = -m (1 + s/8) ir3 b + d_y (ir3/3 - ir5 c2) + d_x ir5 ab2
+// (m w (1 + s/8) - d w^2 - conj(d) s / 3, times 1/rho); the H^6 terms are added
+// in complex form.
+template <int ORDER>
+__device__ __forceinline__ void cell_far(float a, float b, float b2, float tb, const float4 c, float &qr, float &qi)
+{
+    const float r2 = fmaf(a, a, b2);
+    const float c2 = fmaf(a, a, -b2);
+    const float ab2 = a * tb;
+    const float ir = rsqrtf(r2);
+    const float s = ir * ir;
+    const float ir3 = ir * s, ir5 = ir3 * s;
+    const float poly = ORDER >= 6 ? fmaf(s, fmaf(s, 7.f / 256.f, 0.125f), 1.f) : fmaf(s, 0.125f, 1.f);
+    const float g = c.x * poly * ir3;
+    const float u3 = ir3 * (1.f / 3.f);
+    const float e1 = fmaf(ir5, c2, u3), e2 = fmaf(-ir5, c2, u3), f = ir5 * ab2;
+    qr = fmaf(g, a, qr);
+    qr = fmaf(-c.y, e1, qr);
+    qr = fmaf(-c.z, f, qr);
+    qi = fmaf(-g, b, qi);
+    qi = fmaf(c.z, e2, qi);
+    qi = fmaf(c.y, f, qi);
+    if (ORDER >= 6) {
+        // w = (a - i b) s, w^2 = (c2 - i ab2) s^2
+        const float wr = a * s, wi = -b * s;
+        const float ss = s * s;
+        const float w2r = c2 * ss, w2i = -ab2 * ss;
+        const float w3r = fmaf(w2r, wr, -w2i * wi), w3i = fmaf(w2r, wi, w2i * wr);
+        const float w4r = fmaf(w2r, w2r, -w2i * w2i), w4i = 2.f * w2r * w2i;
+        const float w5r = fmaf(w4r, wr, -w4i * wi), w5i = fmaf(w4r, wi, w4i * wr);
+        // - m (21/512) w^5 - m s (7/1536) conj(w^3)
+        const float m1 = c.x * (21.f / 512.f), m2 = c.x * s * (7.f / 1536.f);
+        float pr = -m1 * w5r, pi = -m1 * w5i;
+        pr = fmaf(-m2, w3r, pr);
+        pi = fmaf(m2, w3i, pi);
+        // + 7 conj(D) w^4 / 384 = (7/48) conj(d) w^4
+        const float e7 = 7.f / 48.f;
+        pr = fmaf(e7, fmaf(c.y, w4r, c.z * w4i), pr);
+        pi = fmaf(e7, fmaf(c.y, w4i, -c.z * w4r), pi);
+        // + D s (conj(w^2) - 7 w^2) / 384 = (s/48) d (-6 w2r - 8 i w2i)
+        const float ur = s * (-6.f / 48.f) * w2r, ui = s * (-8.f / 48.f) * w2i;
+        pr = fmaf(c.y, ur, pr);
+        pr = fmaf(-c.z, ui, pr);
+        pi = fmaf(c.y, ui, pi);
+        pi = fmaf(c.z, ur, pi);
+        // - 7 conj(D) s^2 / 640 = -(7/80) conj(d) s^2
+        const float s2 = ss * (7.f / 80.f);
+        pr = fmaf(-c.y, s2, pr);
+        pi = fmaf(c.z, s2, pi);
+        qr = fmaf(ir, pr, qr);
+        qi = fmaf(ir, pi, qi);
+    }
+}
+
+// All cells of one staged tile against one target: (a0, b0) = offsets of cell
+// (0, 0) in cell widths; MASK drops near cells (summed by the FP64 near field).
+template <int ORDER, bool MASK>
+__device__ __forceinline__ void tile_far(const float4 *__restrict__ w, float a0, float b0, double &ar, double &ai)
+{
+    float qr = 0.f, qi = 0.f;
+#pragma unroll 1
+    for (int r = 0; r < SG_TILE_Y; ++r) {
+        const float b = b0 + (float)r;
+        const float b2 = b * b, tb = 2.f * b;
+        const bool bnear = fabsf(b) < (float)SG_NEAR_R;
+#pragma unroll
+        for (int c = 0; c < SG_TILE_X; ++c) {
+            const float a = a0 + (float)c;
+            if (MASK) {
+                float pr = qr, pi = qi;
+                cell_far<ORDER>(a, b, b2, tb, w[r * SG_TILE_X + c], pr, pi);
+                const bool nearc = bnear && fabsf(a) < (float)SG_NEAR_R;
+                qr = nearc ? qr : pr;
+                qi = nearc ? qi : pi;
+            } else {
+                cell_far<ORDER>(a, b, b2, tb, w[r * SG_TILE_X + c], qr, qi);
+            }
+        }
+    }
+    ar += qr;
+    ai += qi;
+}
+
+// Persistent far-field sum. Work item = (target block, split of the tile list);
+// CTAs take items from words[1] (reset by k_cell_coefs). Thread 0 streams the
+// item's tiles (the split minus the block's own patch) into FAR_STAGES shared
+// buffers by bulk copies; every thread (one target each) waits on the buffer's
+// mbarrier, sums the tile, and after a block barrier thread 0 refills the
+// buffer with the tile FAR_STAGES ahead. Each tile is summed through H^4 when
+// every one of its cell centres is at least SG_FAR_R4 cell widths from the
+// block's targets along some axis, else through H^6, with the near cells
+// dropped when some centre is within SG_NEAR_R (exact integer tests on the
+// lattice). Waits are bounded: if one runs out, the CTA records words[0] = 1,
+// waits (bounded) for its copies in flight and returns.
+__global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_far(
+    const sg_target_block *__restrict__ blocks, int nblocks, const int4 *__restrict__ targets,
+    const sg_tile_desc *__restrict__ tiles, const sg_patch_dev *__restrict__ pd, int ntiles,
+    const float4 *__restrict__ coefs, int nsplit, double G, double *__restrict__ partial, int ntargets,
+    int *__restrict__ words)
+{
+    __shared__ __align__(128) float4 buf[FAR_STAGES][SG_TILE_N];
+    __shared__ uint64_t full[FAR_STAGES];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        for (int s = 0; s < FAR_STAGES; ++s) mbar_init(&full[s], 1);
+    __syncthreads();
+    uint32_t used = 0;    // tiles consumed by this CTA (the same in every thread)
+    uint32_t issued = 0;  // tiles whose copy thread 0 has issued
+    const int nitems = nblocks * nsplit;
+    bool failed = false;
+    while (!failed) {
+        if (tid == 0) s_item = atomicAdd(&words[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int bi = item / nsplit, split = item - bi * nsplit;
+        const sg_target_block blk = blocks[bi];
+        const int t0 = (int)((int64_t)ntiles * split / nsplit), t1 = (int)((int64_t)ntiles * (split + 1) / nsplit);
+        const int own0 = pd[blk.patch].tile_first, own1 = own0 + pd[blk.patch].tile_count;
+        const int n1 = max(0, min(t1, own0) - t0), s2 = max(t0, own1);
+        const int n = n1 + max(0, t1 - s2);
+        const bool active = tid < blk.count;
+        const int4 tg = targets[blk.first + (active ? tid : 0)];
+        if (tid == 0) {
+            for (int k = 0; k < n && k < FAR_STAGES; ++k, ++issued) {
+                const int stg = issued % FAR_STAGES;
+                const int t = k < n1 ? t0 + k : s2 + (k - n1);
+                mbar_arrive_expect_tx(&full[stg], TILE_BYTES);
+                bulk_copy_g2s(buf[stg], coefs + (int64_t)t * SG_TILE_N, TILE_BYTES, &full[stg]);
+            }
+        }
+        double ar = 0.0, ai = 0.0;
+        for (int k = 0; k < n; ++k, ++used) {
+            const int stg = used % FAR_STAGES;
+            const int t = k < n1 ? t0 + k : s2 + (k - n1);
+            const bool ok = mbar_wait_bounded(&full[stg], (used / FAR_STAGES) & 1, SG_MBAR_MAX_TRIES);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const sg_tile_desc td = tiles[t];
+            // Chebyshev gap between the block's targets and the tile's cell centres (lattice units)
+            const int cx0 = td.ox + td.step / 2, cx1 = cx0 + (SG_TILE_X - 1) * td.step;
+            const int cy0 = td.oy + td.step / 2, cy1 = cy0 + (SG_TILE_Y - 1) * td.step;
+            const int gx = max(0, max(cx0 - blk.tx1, blk.tx0 - cx1));
+            const int gy = max(0, max(cy0 - blk.ty1, blk.ty0 - cy1));
+            const int gap = max(gx, gy);
+            const float inv = 1.0f / (float)td.step;  // a power of two: exact
+            const float a0 = (float)(td.ox - tg.x) * inv + 0.5f, b0 = (float)(td.oy - tg.y) * inv + 0.5f;
+            if (gap >= SG_FAR_R4 * td.step)
+                tile_far<4, false>(buf[stg], a0, b0, ar, ai);
+            else if (gap >= SG_NEAR_R * td.step)
+                tile_far<6, false>(buf[stg], a0, b0, ar, ai);
+            else
+                tile_far<6, true>(buf[stg], a0, b0, ar, ai);
+            __syncthreads();  // every thread is done with buf[stg]
+            if (tid == 0 && k + FAR_STAGES < n) {
+                const int kk = k + FAR_STAGES;
+                const int tn = kk < n1 ? t0 + kk : s2 + (kk - n1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_expect_tx(&full[stg], TILE_BYTES);
+                bulk_copy_g2s(buf[stg], coefs + (int64_t)tn * SG_TILE_N, TILE_BYTES, &full[stg]);
+                ++issued;
+            }
+        }
+        if (failed) break;
+        if (active) {
+            const int64_t o = ((int64_t)split * ntargets + blk.first + tid) * 2;
+            partial[o + 0] = G * ar;
+            partial[o + 1] = -G * ai;
+        }
+    }
+    if (failed && tid == 0) {
+        atomicExch(&words[0], 1);
+        for (uint32_t g = used; g < issued; ++g) mbar_wait_bounded(&full[g % FAR_STAGES], (g / FAR_STAGES) & 1, SG_MBAR_MAX_TRIES);
+    }
+}
+
+__device__ __forceinline__ int floor_div(int64_t a, int64_t b)
+{
+    return (int)(a >= 0 ? a / b : -((-a + b - 1) / b));
+}
+
+// Near field in FP64: one warp per target; for every other patch, the box of
+// cells whose centres lie within SG_NEAR_R cell widths of the target along
+// both axes (the cells k_cross_far drops, at most 2 SG_NEAR_R per axis),
+// summed in the corner form over the box's corners with weights from the
+// box's cells only. The warp first stores the box's cell values l_i(t),
+// deltax_i, deltay_i in shared memory with a zero border and the logarithms of
+// |u| and |v| of the corner columns and rows in lanes; then lanes take
+// corners (two logarithms each) and the warp reduces with shuffles.
+constexpr int NEAR_WARPS = 8;
+constexpr int NEAR_SLOTS = (2 * SG_NEAR_R + 2) * (2 * SG_NEAR_R + 2);
+
+__global__ void __launch_bounds__(NEAR_WARPS * 32) k_cross_near(const int4 *__restrict__ targets, int ntargets,
+                                                               const sg_patch_dev *__restrict__ pd, int npatches,
+                                                               const float *__restrict__ sigma,
+                                                               const float *__restrict__ dx,
+                                                               const float *__restrict__ dy, double lambda, double G,
+                                                               double *__restrict__ near_out)
+{
+    __shared__ double cellv[NEAR_WARPS][3][NEAR_SLOTS];
+    const int lane = threadIdx.x & 31;
+    double *cl = cellv[threadIdx.x >> 5][0], *cx = cellv[threadIdx.x >> 5][1], *cy = cellv[threadIdx.x >> 5][2];
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+    const double LN2 = 0.69314718055994530942;
+    for (int t = warp; t < ntargets; t += nwarps) {
+        const int4 tg = targets[t];
+        double fx = 0.0, fy = 0.0;
+        for (int q = 0; q < npatches; ++q) {
+            if (q == tg.w) continue;
+            const sg_patch_dev &p = pd[q];
+            const int64_t L = p.step, RL = (int64_t)SG_NEAR_R * L;
+            // cells i with |ox + i L + L/2 - x_t| < R L, j likewise
+            const int64_t ex = (int64_t)tg.x - p.ox - L / 2, ey = (int64_t)tg.y - p.oy - L / 2;
+            const int i0 = max(0, floor_div(ex - RL, L) + 1), j0 = max(0, floor_div(ey - RL, L) + 1);
+            const int i1 = min(p.nx - 1, -floor_div(-(ex + RL), L) - 1);
+            const int j1 = min(p.ny - 1, -floor_div(-(ey + RL), L) - 1);
+            if (i0 > i1 || j0 > j1) continue;
+            const int nbx = i1 - i0 + 1, nby = j1 - j0 + 1, W = nbx + 2;
+            __syncwarp();  // the previous box's values have been read
+            for (int k = lane; k < W * (nby + 2); k += 32) {
+                const int bi = k % W - 1, bj = k / W - 1;
+                double l = 0.0, X = 0.0, Y = 0.0;
+                if (bi >= 0 && bi < nbx && bj >= 0 && bj < nby) {
+                    const int i = i0 + bi, j = j0 + bj;
+                    const int64_t o = p.cell_off + (int64_t)j * p.nx + i;
+                    X = dx[o];
+                    Y = dy[o];
+                    // target minus cell centre, physical units
+                    const double ux = ((double)tg.x - ((double)p.ox + (i + 0.5) * (double)L)) * lambda;
+                    const double uy = ((double)tg.y - ((double)p.oy + (j + 0.5) * (double)L)) * lambda;
+                    l = fma(X, ux, fma(Y, uy, (double)sigma[o]));
+                }
+                cl[k] = l;
+                cx[k] = X;
+                cy[k] = Y;
+            }
+            // corner column ci (lane ci <= nbx) and row cj: u, v relative to the target
+            const double uc = ((double)p.ox + (double)(i0 + lane) * L - tg.x) * lambda;
+            const double vc = ((double)p.oy + (double)(j0 + lane) * L - tg.y) * lambda;
+            const double lnu = lane <= nbx ? (uc == 0.0 ? LN2 : log(fabs(uc))) : 0.0;
+            const double lnv = lane <= nby ? (vc == 0.0 ? LN2 : log(fabs(vc))) : 0.0;
+            __syncwarp();
+            const int nci = nbx + 1, ncorner = nci * (nby + 1);
+            for (int base = 0; base < ncorner; base += 32) {
+                const int k = base + lane;
+                const bool valid = k < ncorner;
+                const int kk = valid ? k : 0;
+                const int ci = kk % nci, cj = kk / nci;
+                const double Lu = __shfl_sync(0xffffffffu, lnu, ci);
+                const double Lv = __shfl_sync(0xffffffffu, lnv, cj);
+                if (!valid) continue;
+                // cells around corner (ci, cj) of the box: lower-left and upper-right count +1
+                const int s00 = cj * W + ci, s10 = s00 + 1, s01 = s00 + W, s11 = s01 + 1;
+                const double A = (cl[s00] - cl[s10]) - (cl[s01] - cl[s11]);
+                const double X = (cx[s00] - cx[s10]) - (cx[s01] - cx[s11]);
+                const double Y = (cy[s00] - cy[s10]) - (cy[s01] - cy[s11]);
+                const double u = ((double)p.ox + (double)(i0 + ci) * L - tg.x) * lambda;
+                const double v = ((double)p.oy + (double)(j0 + cj) * L - tg.y) * lambda;
+                const double au = fabs(u), av = fabs(v);
+                const double r = sqrt(fma(u, u, v * v));
+                // sgn(v) (ln(|v| + r) - ln|u|), ln|u| -> ln 2 on u = 0 (the coincident-line form
+                // sgn(v) ln|v|, which may be negative: the sign multiplies, it is not copied)
+                const double t0 = log(av + r) - Lu;
+                const double t1 = log(au + r) - Lv;
+                const double g0 = v == 0.0 ? 0.0 : (v > 0.0 ? t0 : -t0);
+                const double g0y = u == 0.0 ? 0.0 : (u > 0.0 ? t1 : -t1);
+                fx += fma(X * v, g0y, fma(-A, g0, -Y * r));
+                fy += fma(Y * u, g0, fma(-A, g0y, -X * r));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, off);
+            fy += __shfl_xor_sync(0xffffffffu, fy, off);
+        }
+        if (lane == 0) {
+            near_out[(int64_t)t * 2 + 0] = G * fx;
+            near_out[(int64_t)t * 2 + 1] = G * fy;
+        }
+    }
+}
+
+// Fixed-order sum: the patch's own FFT result, the far partials of every split,
+// then the near field.
+__global__ void k_cross_combine(const int4 *__restrict__ targets, int ntargets, int nsplit,
+                                const double *__restrict__ partial, float *__restrict__ fx, float *__restrict__ fy)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntargets; t += gridDim.x * blockDim.x) {
+        double sx = 0.0, sy = 0.0;
+        for (int s = 0; s <= nsplit; ++s) {
+            sx += partial[((int64_t)s * ntargets + t) * 2 + 0];
+            sy += partial[((int64_t)s * ntargets + t) * 2 + 1];
+        }
+        const int o = targets[t].z;
+        fx[o] = (float)((double)fx[o] + sx);
+        fy[o] = (float)((double)fy[o] + sy);
+    }
+}
+
+sg_status cross_solve_f32(sg_plan *plan, const sg_workspace *ws, const float *sigma, const float *dx,
+                          const float *dy, float *fx, float *fy, cudaStream_t st)
+{
+    float4 *w = (float4 *)ws->tile_w;
+    const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
+    int grid_w = (int)((nw + 255) / 256);
+    if (grid_w > 65535) grid_w = 65535;
+    sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
+    k_cell_coefs<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+                                         plan->lattice_unit, w, ws->err + 1);
+    SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_DIRECT, st);
+    k_cross_far<<<plan->far_grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->nblocks, plan->targets, plan->tiles,
+                                                              plan->patch_dev, plan->ntiles, w, plan->nsplit,
+                                                              plan->geom.G, ws->partial, plan->ntargets, ws->err);
+    SG_CUDA_TRY(cudaGetLastError());
+    double *near = ws->partial + (int64_t)plan->nsplit * plan->ntargets * 2;
+    const int64_t nblk = ((int64_t)plan->ntargets + NEAR_WARPS - 1) / NEAR_WARPS;
+    const int grid_n = (int)(nblk < (1 << 20) ? nblk : (1 << 20));
+    k_cross_near<<<grid_n, NEAR_WARPS * 32, 0, st>>>(plan->targets, plan->ntargets, plan->patch_dev, plan->npatches, sigma, dx, dy,
+                                         plan->lattice_unit, plan->geom.G, near);
+    SG_CUDA_TRY(cudaGetLastError());
+    k_cross_combine<<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
+                                                                   ws->partial, fx, fy);
+    SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_DIRECT, st);
+    return SG_OK;
+}
+
 }  // namespace
+
+sg_status sg_cross_far_grid(sg_plan *plan, int nsm)
+{
+    int per_sm = 0;
+    SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cross_far, SG_DIRECT_THREADS, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t items = (int64_t)plan->nblocks * plan->nsplit;
+    int64_t g = (int64_t)nsm * per_sm;
+    if (g > items) g = items;
+    plan->far_grid = (int)(g < 1 ? 1 : g);
+    return SG_OK;
+}
 
 sg_status sg_cross_solve(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          void *fx, void *fy, cudaStream_t st)
 {
-    if (plan->prec == SG_FP64) return cross_solve_t<double>(plan, ws, sigma, dx, dy, fx, fy, st);
-    return cross_solve_t<float>(plan, ws, sigma, dx, dy, fx, fy, st);
+    if (plan->ntiles == 0 || plan->ntargets == 0) return SG_OK;
+    if (plan->prec == SG_FP64)
+        return cross_solve_f64(plan, ws, (const double *)sigma, (const double *)dx, (const double *)dy, (double *)fx,
+                               (double *)fy, st);
+    return cross_solve_f32(plan, ws, (const float *)sigma, (const float *)dx, (const float *)dy, (float *)fx,
+                           (float *)fy, st);
 }

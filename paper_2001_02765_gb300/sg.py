@@ -115,6 +115,7 @@ _SIGNATURES = {
     "sg_tune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "sg_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_double)]),
+    "sg_alu_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sg_last_error": (ctypes.c_char_p, []),
     "sg_version": (ctypes.c_int, []),
@@ -336,6 +337,17 @@ def sg_server_get_stats(server, reset_latencies=False):
     out = sg_server_stats()
     _check(load().sg_server_get_stats(server, ctypes.byref(out), int(bool(reset_latencies))), "sg_server_get_stats")
     return {k: getattr(out, k) for k, _ in sg_server_stats._fields_}
+
+
+SG_PEAK_FP64_FMA, SG_PEAK_FP32_FMA, SG_PEAK_FP32_LG2 = 0, 1, 2
+
+
+def sg_alu_peak(kind):
+    """Measured pipe throughput of the current device (flop/s for the FMA kinds,
+    results/s for the base-2 logarithm)."""
+    out = ctypes.c_double(0.0)
+    _check(load().sg_alu_peak(int(kind), ctypes.byref(out)), "sg_alu_peak")
+    return float(out.value)
 
 
 def sg_version():

@@ -3,8 +3,7 @@ ILR/VLR hierarchies of Section 4) and on masked patches, against the oracle's
 plain leaf sum; and the printed errors of Tables 3-6 from the CUDA path.
 
 Tolerances (relative L2 over both components and all leaves): FP64 1e-12;
-FP32 1e-5 for smooth densities (the composite sources keep the cross-patch
-corner weights small), 5e-5 for uniform random fields.
+FP32 1e-5, for smooth densities and for uniform random fields alike.
 """
 import numpy as np
 import pytest
@@ -98,7 +97,7 @@ def test_band_hierarchy_disk_parity(sg, rule, disk, prec, tol, cross):
 
 
 @pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
-@pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", 5e-5)])
+@pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", F32_TOL)])
 def test_band_hierarchy_random_fields(sg, prec, tol, cross):
     """Four levels, a ragged level-0 grid, random densities and slopes (order 1)."""
     hier = W.band_hierarchy(40, 4, "vlr", "d22")
@@ -109,7 +108,9 @@ def test_band_hierarchy_random_fields(sg, prec, tol, cross):
     (fx, fy), _ = _solve(sg, args, prec, s, sx, sy, cross=cross)
     leaf = hier["leaf"]
     rx, ry = _oracle(args, leaf, s, sx, sy, np.float64 if prec == "fp64" else np.float32)
-    assert rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf]) < tol
+    err = rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf])
+    print("rel L2 %s cross=%d: %.3e (tolerance %.0e)" % (prec, cross, err, tol))
+    assert err < tol
 
 
 def test_band_hierarchy_order0(sg):
