@@ -213,3 +213,105 @@ __device__ __forceinline__ void fft_batch(C *buf, const C *__restrict__ tw)
 {
     fft_stages<C, L, NB, THREADS, 1, INV, IN_HALF, OUT_HALF>(buf, tw);
 }
+
+// ------------------------------------------------- register-resident form --
+//
+// The same stages with the data kept in registers between them, for CTAs of
+// NSEQ * L / 8 threads (eight elements per thread). Thread t works on sequence
+// seq = t / (L/8) and holds, at the start and at the end of a transform, the
+// elements of the "pattern P0": v[m] = element jt + m L/8 of its sequence,
+// jt = t mod (L/8), m = 0..7. That is the input pattern of a radix-8 first
+// stage (butterfly j = jt reads j + r L/8) and the output pattern of the last
+// stage (butterfly j writes j + r NS with NS = L/R; a last stage of radix R < 8
+// gives thread t the butterflies jt + p L/8, p < 8/R, so that its outputs are
+// again P0). Consequences: a transform needs no shared memory before its first
+// stage or after its last (loads and stores to global memory go straight to
+// and from registers), a forward transform's outputs are the inputs of an
+// inverse transform of the same thread with no exchange in between, and
+// between two stages one exchange through shared memory (outputs written to
+// their auto-sorted positions, a barrier, next inputs read). With NBUF = 2 the
+// exchanges alternate between two buffers (one barrier each; `par` carries the
+// buffer parity from one transform to the next); with NBUF = 1 a second
+// barrier separates each exchange's reads from the next one's writes. Every
+// butterfly does the arithmetic of fft_stage (same twiddles, same radix-R
+// DFT), so the results are those of fft_batch.
+template <typename C, int L, int NSEQ, int THREADS, int NS, int NBUF, bool INV>
+__device__ __forceinline__ void rfft_stages(C (&v)[8], C *bufs, int &par, const C *__restrict__ tw)
+{
+    static_assert(THREADS == NSEQ * L / 8, "eight elements per thread");
+    if constexpr (NS < L) {
+        constexpr int REM = L / NS;
+        constexpr int R = REM >= 8 ? 8 : REM;
+        constexpr int PER = 8 / R;
+        constexpr int S = L / R;
+        constexpr int BUF = spad_size<C>(NSEQ * L);
+        const int seq = threadIdx.x / (L / 8), jt = threadIdx.x % (L / 8);
+        if constexpr (NS > 1) {
+            // gather this stage's inputs from the previous stage's outputs
+            const C *in = bufs + (NBUF == 2 ? (par ^ 1) * BUF : 0);
+#pragma unroll
+            for (int p = 0; p < PER; ++p)
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[p * R + r] = in[spad<C>(seq * L + jt + p * (L / 8) + r * S)];
+            if constexpr (NBUF == 1) __syncthreads();
+        }
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            C *u = v + p * R;
+            const int j = jt + p * (L / 8);
+            const int k = j % NS;
+            if constexpr (NS > 1) {
+                const C w1 = twiddle<C, INV>(tw, stage_table_offset(NS) + k);
+                u[1] = cmul(u[1], w1);
+                if constexpr (R >= 4) {
+                    const C w2 = cmul(w1, w1);
+                    const C w3 = cmul(w2, w1);
+                    u[2] = cmul(u[2], w2);
+                    u[3] = cmul(u[3], w3);
+                    if constexpr (R == 8) {
+                        const C w4 = cmul(w2, w2);
+                        u[4] = cmul(u[4], w4);
+                        u[5] = cmul(u[5], cmul(w4, w1));
+                        u[6] = cmul(u[6], cmul(w3, w3));
+                        u[7] = cmul(u[7], cmul(w4, w3));
+                    }
+                }
+            }
+            if constexpr (R == 8) dft8<C, INV>(u);
+            else if constexpr (R == 4) dft4<C, INV>(u[0], u[1], u[2], u[3]);
+            else dft2<C, INV>(u[0], u[1]);
+        }
+        if constexpr (NS * R == L) {
+            // last stage: butterfly jt + p L/8, output r at jt + (p + r PER) L/8
+            C o[8];
+#pragma unroll
+            for (int p = 0; p < PER; ++p)
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[p + r * PER] = v[p * R + r];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = o[m];
+        } else {
+            C *out = bufs + (NBUF == 2 ? par * BUF : 0);
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                const int j = jt + p * (L / 8);
+                const int base = seq * L + (j / NS) * NS * R + j % NS;
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[spad<C>(base + r * NS)] = v[p * R + r];
+            }
+            __syncthreads();
+            if constexpr (NBUF == 2) par ^= 1;
+            rfft_stages<C, L, NSEQ, THREADS, NS * R, NBUF, INV>(v, bufs, par, tw);
+        }
+    }
+}
+
+// Transform of the P0-held data of every thread's sequence (see above). Every
+// thread of the CTA calls it. bufs: NBUF buffers of spad_size(NSEQ L) elements.
+// With NBUF = 1 the caller must make sure that no thread still reads the
+// buffer from an earlier use when this call starts writing it.
+template <typename C, int L, int NSEQ, int THREADS, int NBUF, bool INV>
+__device__ __forceinline__ void fft_regs(C (&v)[8], C *bufs, int &par, const C *__restrict__ tw)
+{
+    rfft_stages<C, L, NSEQ, THREADS, 1, NBUF, INV>(v, bufs, par, tw);
+}

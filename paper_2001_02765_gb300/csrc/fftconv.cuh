@@ -181,8 +181,11 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const 
 // kernel spectra of the CTA's columns, [planes][CB][sg_spec_stride(PY)] of T,
 // which one thread fetches with one 1-D bulk copy (TMA) per plane at kernel
 // start so that they arrive while the forward transform runs.
+// Column kernels keep each column in registers between transform stages and
+// exchange through COL_NBUF shared buffers (fft_regs in fft.cuh).
+constexpr int COL_NBUF = 2;
 template <typename T, int PY, int CB>
-__host__ __device__ constexpr int col_buf_bytes() { return (spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15; }
+__host__ __device__ constexpr int col_buf_bytes() { return COL_NBUF * ((spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15); }
 template <typename T, int PY, int CB, int NPL = 6>
 __host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * NPL * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
 
@@ -215,13 +218,13 @@ __device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err)
 }
 
 // resident CTAs per SM asked of the register allocator (spill-free choices at
-// the default shapes, scaled by the CTA size for the other candidates)
-// (FP32 2048-point columns: four CTAs of 64 registers, measured 2-3 % faster
-// than three of 80 for one or two outputs; the three-output pass spills at 64)
+// the default shapes, scaled by the CTA size for the other candidates). FP32
+// 2048-point columns: the two exchange buffers and six spectrum planes take
+// 59.5 KB of shared memory, so three CTAs fit per SM: 80 registers each.
 template <typename T, int PY, int NOUT>
 constexpr int col_min_blocks_def()
 {
-    return sizeof(T) == 4 ? (PY == 2048 ? (NOUT == 3 ? 3 : 4) : (PY == 4096 ? 1 : 2)) : 1;
+    return sizeof(T) == 4 ? (PY == 2048 ? (NOUT == 3 ? 2 : 3) : (PY == 4096 ? 1 : 2)) : 1;
 }
 template <typename T, int PY, int THREADS, int NOUT = 2>
 constexpr int col_min_blocks()
@@ -243,54 +246,49 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
     const T *__restrict__ spec = args.spec;
     const int ny = args.ny;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
+    C *bufs = reinterpret_cast<C *>(smem_raw);
     T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
     __shared__ uint64_t bar;
-    constexpr int EPT = CB * PY / THREADS;
+    static_assert(CB * PY / THREADS == 8, "eight elements per thread");
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    constexpr int STEP = PY / 8;
     const int kx0 = blockIdx.x * CB;
+    // this thread's column and the rows it holds: jt + m PY/8, m = 0..7
+    const int c = threadIdx.x / STEP, jt = threadIdx.x % STEP;
+    const int kx = kx0 + c;
     constexpr int NPL = NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
 
-    C accx[EPT], accy[EPT], accz[NOUT == 3 ? EPT : 1];
+    C accx[8], accy[8], accz[NOUT == 3 ? 8 : 1];
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+    for (int q = 0; q < 8; ++q) accx[q] = accy[q] = cmake<C>((T)0, (T)0);
 #pragma unroll
-    for (int q = 0; q < (NOUT == 3 ? EPT : 1); ++q) accz[q] = cmake<C>((T)0, (T)0);
+    for (int q = 0; q < (NOUT == 3 ? 8 : 1); ++q) accz[q] = cmake<C>((T)0, (T)0);
 
+    int par = 0;
     for (int f = 0; f < nf; ++f) {
-        // the lower half of each column (the upper half is taken as zero by the first stage)
-        constexpr int NE = CB * (PY / 2);
-        for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
-            C v[LOAD_UNROLL];
+        // the lower half of the column straight into registers (the upper half is zero)
+        C v[8];
 #pragma unroll
-            for (int u = 0; u < LOAD_UNROLL; ++u) {
-                const int e = e0 + u * THREADS, c = e / (PY / 2), j = e % (PY / 2), kx = kx0 + c;
-                v[u] = (e < NE && j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
-            }
-#pragma unroll
-            for (int u = 0; u < LOAD_UNROLL; ++u) {
-                const int e = e0 + u * THREADS;
-                if (e < NE) buf[spad<C>((e / (PY / 2)) * PY + e % (PY / 2))] = v[u];
-            }
+        for (int m = 0; m < 8; ++m) {
+            const int j = jt + m * STEP;
+            v[m] = (m < 4 && j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
         }
-        __syncthreads();
-        fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
+        if (COL_NBUF == 1 && f > 0) __syncthreads();
+        fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
         if (f == 0 && !spectra_ready(&bar, err)) return;
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const int e = threadIdx.x + q * THREADS;
-            const int c = e / PY, ky = e % PY;
-            const int kx = kx0 + c;
+        for (int q = 0; q < 8; ++q) {
+            const int ky = jt + q * STEP;
             if (kx >= qx) continue;
             const bool lower = ky <= PY / 2;
             const int kq = lower ? ky : PY - ky;
             const T sg = lower ? (T)1 : (T)-1;
             const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
-            const C X = buf[spad<C>(e)];
+            const C X = v[q];
             // explicitly rounded (see mul_rn): the result must not depend on the launch shape
             if constexpr (NOUT == 1) {
                 // potential planes: p (real, even-even), a (i a: odd in kx), b (i b: odd in ky)
@@ -332,26 +330,26 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
                 }
             }
         }
-        __syncthreads();
     }
 
+    // inverse transforms: the accumulators are already in the transform's input pattern
+#pragma unroll 1
     for (int o = 0; o < NOUT; ++o) {
+        C v[8];
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            C v = o == 0 ? accx[q] : accy[q];
+        for (int q = 0; q < 8; ++q) {
+            v[q] = o == 0 ? accx[q] : accy[q];
             if constexpr (NOUT == 3) {
-                if (o == 2) v = accz[q];
+                if (o == 2) v[q] = accz[q];
             }
-            buf[spad<C>(threadIdx.x + q * THREADS)] = v;
         }
-        __syncthreads();
-        fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
-        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
-            const int c = e / PY, j = e % PY;
-            const int kx = kx0 + c;
-            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = buf[spad<C>(e)];
+        if (COL_NBUF == 1) __syncthreads();
+        fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(v, bufs, par, tw);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = jt + m * STEP;
+            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = v[m];
         }
-        __syncthreads();
     }
 }
 
@@ -461,13 +459,16 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     const T *__restrict__ phase = args.phase;
     const int ny = args.ny;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *buf = reinterpret_cast<C *>(smem_raw);
+    C *bufs = reinterpret_cast<C *>(smem_raw);
     T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
     __shared__ uint64_t bar;
     __shared__ C rows[CB][2];  // R0, R1 of each column
-    constexpr int EPT = CB * PY / THREADS;
+    static_assert(CB * PY / THREADS == 8, "eight elements per thread");
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    constexpr int STEP = PY / 8;
     const int kx0 = blockIdx.x * CB;
+    const int c = threadIdx.x / STEP, jt = threadIdx.x % STEP;
+    const int kx = kx0 + c;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
@@ -475,45 +476,33 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
     const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
 
-    {
-        // the lower half of each column (the upper half is taken as zero by the first stage)
-        constexpr int NE = CB * (PY / 2);
-        for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
-            C v[LOAD_UNROLL];
+    // the lower half of the column straight into registers (the upper half is zero)
+    C v[8];
 #pragma unroll
-            for (int u = 0; u < LOAD_UNROLL; ++u) {
-                const int e = e0 + u * THREADS, c = e / (PY / 2), j = e % (PY / 2), kx = kx0 + c;
-                v[u] = (e < NE && j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
-            }
+    for (int m = 0; m < 8; ++m) {
+        const int j = jt + m * STEP;
+        v[m] = (m < 4 && j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+    }
+    // the column's first and last rows (read after the transform's barriers)
+    if (jt == 0) rows[c][0] = v[0];
 #pragma unroll
-            for (int u = 0; u < LOAD_UNROLL; ++u) {
-                const int e = e0 + u * THREADS;
-                if (e < NE) buf[spad<C>((e / (PY / 2)) * PY + e % (PY / 2))] = v[u];
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < CB) {
-        rows[threadIdx.x][0] = buf[spad<C>(threadIdx.x * PY)];
-        rows[threadIdx.x][1] = buf[spad<C>(threadIdx.x * PY + ny - 1)];
-    }
-    __syncthreads();
-    fft_batch<C, PY, CB, THREADS, false, true>(buf, tw);
+    for (int m = 0; m < 4; ++m)
+        if (jt + m * STEP == ny - 1) rows[c][1] = v[m];
+    int par = 0;
+    fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
     if (!spectra_ready(&bar, err)) return;
 
-    C accx[EPT], accy[EPT];
+    C accx[8], accy[8];
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-        const int e = threadIdx.x + q * THREADS;
-        const int c = e / PY, ky = e % PY;
-        const int kx = kx0 + c;
+    for (int q = 0; q < 8; ++q) {
+        const int ky = jt + q * STEP;
         accx[q] = accy[q] = cmake<C>((T)0, (T)0);
         if (kx >= qx) continue;
         const bool lower = ky <= PY / 2;
         const int kq = lower ? ky : PY - ky;
         const T sg = lower ? (T)1 : (T)-1;
         const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
-        const C S = buf[spad<C>(e)];
+        const C S = v[q];
         // slope spectra
         const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
         const C e1 = cmake<C>(__ldg(&ce1[2 * kx]), __ldg(&ce1[2 * kx + 1]));
@@ -535,19 +524,21 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
         accx[q] = cmake<C>(fma(cc, Y.x, fma(b, X.x, -mul_rn(a, S.y))), fma(cc, Y.y, fma(b, X.y, mul_rn(a, S.x))));
         accy[q] = cmake<C>(fma(ff, X.x, fma(ee, Y.x, -mul_rn(d, S.y))), fma(ff, X.y, fma(ee, Y.y, mul_rn(d, S.x))));
     }
-    __syncthreads();
 
-    for (int o = 0; o < 2; ++o) {
+    // inverse transforms: the products are already in the transform's input pattern
+    if (COL_NBUF == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accx, bufs, par, tw);
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) buf[spad<C>(threadIdx.x + q * THREADS)] = o == 0 ? accx[q] : accy[q];
-        __syncthreads();
-        fft_batch<C, PY, CB, THREADS, true, false, true>(buf, tw);
-        for (int e = threadIdx.x; e < CB * PY; e += THREADS) {
-            const int c = e / PY, j = e % PY;
-            const int kx = kx0 + c;
-            if (j < ny && kx < qx) work_inv[((int64_t)o * qx + kx) * ny + j] = buf[spad<C>(e)];
-        }
-        __syncthreads();
+    for (int m = 0; m < 4; ++m) {
+        const int j = jt + m * STEP;
+        if (j < ny && kx < qx) work_inv[(int64_t)kx * ny + j] = accx[m];
+    }
+    if (COL_NBUF == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accy, bufs, par, tw);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = jt + m * STEP;
+        if (j < ny && kx < qx) work_inv[((int64_t)qx + kx) * ny + j] = accy[m];
     }
 }
 

@@ -7,11 +7,14 @@ corner weights in a fixed array inside the library. This test calls it through
 the C ABI twice in a row (the second call reuses the array the first one left
 behind) and compares both results with the plan-based entry point sg_force on
 the same grid, within the FP32 tolerance of the other parity tests (relative L2
-1e-5). It sits in a file of its own, collected last.
+1e-5), and, on small grids with random densities and slopes, with the FP64
+oracle's plain sum over every cell pair. It sits in a file of its own,
+collected last.
 """
 import numpy as np
 import pytest
 
+from oracle.direct import uniform_direct_force
 from oracle.norms import rel_l2
 from paper_2001_02765_gb300 import workloads as W
 from tests._lib import ensure_built, to_dev
@@ -52,6 +55,30 @@ def test_static_entry_point_matches_sg_force(sg, nx, ny, slopes):
         gx, gy = fx.cpu().numpy().astype(np.float64), fy.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gy)), call
         assert rel_l2(gx, gy, rx, ry) < 1e-5, (call, rel_l2(gx, gy, rx, ry))
+
+
+@pytest.mark.parametrize("nx, ny, slopes", [(16, 16, True), (31, 9, True), (24, 40, False)])
+def test_static_entry_point_matches_oracle(sg, nx, ny, slopes):
+    """Random density and slopes on a small grid: both of two consecutive calls
+    against the oracle's FP64 plain sum (Section 2 closed forms), 1e-5."""
+    import torch
+    h = 0.0625
+    x0, y0 = -0.5, -0.75
+    sig, sx, sy = W.random_fields(ny, nx, seed=nx * ny)
+    s32 = [np.asarray(a, np.float32) for a in (sig, sx, sy)]
+    ox, oy = uniform_direct_force(s32[0].astype(np.float64), s32[1].astype(np.float64) if slopes else None,
+                                  s32[2].astype(np.float64) if slopes else None, h, x0=x0, y0=y0, G=0.8)
+    s, dx, dy = (to_dev(a, np.float32) for a in s32)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        fx = torch.full((nx * ny,), float("nan"), device="cuda")
+        fy = torch.full((nx * ny,), float("nan"), device="cuda")
+        sg.sg_direct_force_static(nx, ny, h, 0.8, s.data_ptr(), dx.data_ptr() if slopes else 0,
+                                  dy.data_ptr() if slopes else 0, fx.data_ptr(), fy.data_ptr(), stream)
+        torch.cuda.synchronize()
+        err = rel_l2(fx.cpu().numpy().astype(np.float64), fy.cpu().numpy().astype(np.float64), ox.ravel(), oy.ravel())
+        print("rel L2 vs oracle, call %d: %.3e" % (call, err))
+        assert err < 1e-5, (call, err)
 
 
 def test_static_entry_point_rejects_oversize(sg):
