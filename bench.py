@@ -40,18 +40,34 @@ METRIC_POTENTIAL = "potential solves/sec and target-cells/sec (p50/p99 latency) 
 L2_FLUSH_BYTES = 512 << 20
 
 
+_ALU = {}
+
+
+def _alu_peaks():
+    """Pipe throughput of this GPU measured by the library (sg_alu_peak: every
+    SM, 8 CTAs x 256 threads each, independent chains, best of five launches):
+    FP32 and FP64 FMA in TFLOP/s, FP32 base-2 logarithm in 1e12 results/s.
+    Measured once per process."""
+    if not _ALU:
+        from paper_2001_02765_gb300 import sg
+        _ALU["fp32_tflops"] = sg.sg_alu_peak(sg.SG_PEAK_FP32_FMA) / 1e12
+        _ALU["fp64_tflops"] = sg.sg_alu_peak(sg.SG_PEAK_FP64_FMA) / 1e12
+        _ALU["lg2_tops"] = sg.sg_alu_peak(sg.SG_PEAK_FP32_LG2) / 1e12
+    return dict(_ALU)
+
+
 def _peaks():
-    """(HBM GB/s, its source, FP32 non-tensor TFLOP/s, its source). The FP32
-    peak is derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x the maximum SM
-    clock recorded in MEASURED_PEAKS.json (2070 MHz on this pool)."""
+    """(HBM GB/s, its source, FP32 non-tensor TFLOP/s, its source). HBM: the
+    driver's measured copy bandwidth (MEASURED_PEAKS.json); FP32: measured on
+    this GPU by sg_alu_peak."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
         hbm, src = float(p["hbm_gbs"]), "measured"
-        mhz = float(p.get("sm_max_mhz", 2070.0))
     except Exception:
-        hbm, src, mhz = 6800.0, "fallback", 2070.0
-    return hbm, src, 152 * 128 * 2 * mhz * 1e6 / 1e12, "derived: 152 SM x 128 lanes x 2 x %.0f MHz" % mhz
+        hbm, src = 6800.0, "fallback"
+    alu = _alu_peaks()
+    return hbm, src, alu["fp32_tflops"], "measured (sg_alu_peak: FP32 FMA on every SM, best of 5)"
 
 
 class ClockSampler:
@@ -366,7 +382,7 @@ def batch_roofline(ns, ms_per_batch):
     tflops = flops / secs / 1e12
     return {"kernel": "batch (all passes of all members, one graph)", "bound": "alu", "achieved": tflops,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": None,
-            "algorithmic_flops": flops, "peak_source": fp32_src,
+            "algorithmic_flops": flops, "peak_source": fp32_src, "alu_peaks": _alu_peaks(),
             "hbm": {"algorithmic_bytes": alg, "achieved_gbs": alg / secs / 1e9, "peak_gbs": hbm_peak,
                     "frac": alg / secs / 1e9 / hbm_peak, "peak_source": hbm_src}}
 
@@ -415,6 +431,24 @@ def _serve_inputs(patches, density):
         gx.append(b.ravel())
         gy.append(c.ravel())
     return np.concatenate(sig), np.concatenate(gx), np.concatenate(gy)
+
+
+def _leaf_mask(patches):
+    """Leaf cells of a patch hierarchy in field-array order: a cell is covered
+    when its centre lies inside a patch of the next level."""
+    out = []
+    for lev, nx, ny, x0, y0, h in patches:
+        xc = x0 + (np.arange(nx) + 0.5) * h
+        yc = y0 + (np.arange(ny) + 0.5) * h
+        leaf = np.ones((ny, nx), bool)
+        for lq, qnx, qny, qx0, qy0, qh in patches:
+            if lq != lev + 1:
+                continue
+            ix = (xc > qx0) & (xc < qx0 + qnx * qh)
+            iy = (yc > qy0) & (yc < qy0 + qny * qh)
+            leaf &= ~(iy[:, None] & ix[None, :])
+        out.append(leaf.ravel())
+    return np.concatenate(out)
 
 
 def run_serve(args):
@@ -490,25 +524,77 @@ def run_serve(args):
     rate = args.serve_load * capacity
     with ClockSampler(local) as clk:
         wall, tickets, stats = open_loop(reqs, args.serve_load)
+
+    # end to end, closed loop on a prefix: each request's inputs copied from
+    # pinned host memory before it is submitted, its Fx, Fy copied back to pinned
+    # host memory once it has finished (at most max_inflight requests in flight)
+    part = reqs[: min(len(reqs), args.serve_e2e_requests)]
+    host = {}
+    for key, patches, mode, dens in part:
+        if key not in host:
+            n = plans[(key[0], key[1], "fp32")].ncells
+            ins = inputs[(key, "fp32")]
+            host[key] = ([t.cpu().pin_memory() if t is not None else None for t in ins],
+                         torch.empty(n, dtype=torch.float32).pin_memory(),
+                         torch.empty(n, dtype=torch.float32).pin_memory())
+    copy = torch.cuda.Stream()
+    h2d = d2h = 0
+    pending = []
+    t0 = time.perf_counter()
+
+    def retire(item):
+        nonlocal d2h
+        t_, g_, hx, hy, outs_ = item
+        sg.sg_wait(server, t_, 600000.0)
+        with torch.cuda.stream(copy):
+            hx.copy_(outs_[0], non_blocking=True)
+            hy.copy_(outs_[1], non_blocking=True)
+        copy.synchronize()
+        d2h += 2 * hx.numel() * 4
+
+    for key, patches, mode, dens in part:
+        g = (key[0], key[1], "fp32")
+        hin, hx, hy = host[key]
+        din = inputs[(key, "fp32")]
+        with torch.cuda.stream(copy):
+            for dst, src in zip(din, hin):
+                if dst is not None:
+                    dst.copy_(src, non_blocking=True)
+                    h2d += src.numel() * 4
+        copy.synchronize()
+        outs_ = outputs[g][outputs[g + ("n",)] % len(outputs[g])]
+        pending.append((submit(server, key, "fp32"), g, hx, hy, outs_))
+        if len(pending) >= args.serve_inflight:
+            retire(pending.pop(0))
+    while pending:
+        retire(pending.pop(0))
+    e2e_s = time.perf_counter() - t0
     sg.sg_server_destroy(server)
     value = len(tickets) / wall  # the open-loop requests, all completed
     targets = sum(plans[(key[0], key[1], "fp32")].info["nleaves"] for key, *_ in reqs)
 
-    # the plain FP64 per-solve path on a time-bounded prefix of the same stream
+    # the plain FP64 per-solve path on a time-bounded prefix of the same stream,
+    # and every served result of that prefix against it: the FP32 plan's sg_force
+    # on the same inputs (a request's result is the same bit for bit alone and in
+    # any mix), relative L2 over the request's leaf cells
     t_budget = args.serve_fp64_seconds
     done64 = 0
     t64 = 0.0
     skipped64 = set()
+    left_out = 0
+    errs = []
     for key, patches, mode, dens in reqs:
         if t64 > t_budget:
             break
         if (key[0], mode) in skipped64:
+            left_out += 1
             continue
         prepare("fp64", [(key, patches, mode, dens)])
         g = (key[0], mode, "fp64")
         info64 = plans[g].info
         if info64["cross_mode"] == 1 and info64["cross_pairs"] > 5e10:
             skipped64.add((key[0], mode))  # FP64 direct sum of minutes: left out of the comparison
+            left_out += 1
             continue
         ins = inputs[(key, "fp64")]
         fx, fy = outputs[g][0]
@@ -518,6 +604,13 @@ def run_serve(args):
         torch.cuda.synchronize()
         t64 += time.perf_counter() - a
         done64 += 1
+        g32 = (key[0], mode, "fp32")
+        i32 = inputs[(key, "fp32")]
+        sx, sy = plans[g32].force(i32[0], i32[1], i32[2])
+        leaf = torch.from_numpy(_leaf_mask(patches)).cuda()
+        num = ((sx.double() - fx)[leaf] ** 2).sum() + ((sy.double() - fy)[leaf] ** 2).sum()
+        den = (fx[leaf] ** 2).sum() + (fy[leaf] ** 2).sum()
+        errs.append(float(torch.sqrt(num / den)))
     for p_ in plans.values():
         p_.close()
     if rank != 0:
@@ -537,8 +630,19 @@ def run_serve(args):
         "capacity_solves_per_s": capacity, "offered_rate": rate, "load_sweep": sweep,
         "peak_bytes": stats["peak_bytes"],
         "fp64_plain": {"solves_per_s": done64 / t64 if t64 else None, "requests": done64,
-                       "note": "one solve at a time, same stream prefix; geometries whose FP64 plan would take "
-                               "the direct sum over > 5e10 pairs left out (%d)" % len(skipped64)},
+                       "left_out": left_out,
+                       "note": "one solve at a time on a %.0f s prefix of the same stream; requests whose FP64 plan "
+                               "would take the direct sum over > 5e10 pairs (hierarchies too wide for FP64 level "
+                               "convolutions: %d geometries) are left out of the comparison" % (
+                                   t_budget, len(skipped64))},
+        "rel_err_vs_fp64": {"max": max(errs) if errs else None,
+                            "median": float(np.median(errs)) if errs else None, "results": len(errs),
+                            "note": "every FP32 result of the FP64 prefix against the FP64 plain path, relative L2 "
+                                    "over the request's leaf cells"},
+        "e2e": {"value": len(part) / e2e_s * world, "unit": "solves/s", "requests": len(part),
+                "h2d_bytes_per_step": h2d / len(part), "d2h_bytes_per_step": d2h / len(part),
+                "note": "closed loop, inputs copied from pinned host memory before each submit, Fx and Fy copied "
+                        "back to pinned host memory when the request finishes, %d in flight" % args.serve_inflight},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -837,7 +941,7 @@ def run_gpu(args):
         "stage_ms": stage_mean,
         "roofline": {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": tflops / fp32_peak, "traffic": TRAFFIC.get((args.workload, dom)),
-                     "algorithmic_flops": flops, "peak_source": fp32_src,
+                     "algorithmic_flops": flops, "peak_source": fp32_src, "alu_peaks": _alu_peaks(),
                      "hbm": {"algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
                              "frac": gbs / hbm_peak, "peak_source": hbm_src}},
         "e2e": ({"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -899,8 +1003,7 @@ def oracle_fft_route(wl, reps=3):
 # of the current kernel build (see profiles/); None when not captured for it.
 # amr3 col_conv: the stage's column-transform and column-MAC launches, one each
 # per solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
-TRAFFIC = {("spiral1024", "col_conv"): 33.82e6 + 0.004e6,
-           ("amr3", "col_conv"): (11.152e6 + 7.286e6) + (226.808e6 + 11.011e6)}
+TRAFFIC = {("amr3", "col_conv"): (11.152e6 + 7.286e6) + (226.808e6 + 11.011e6)}
 
 
 def _pad(n):
@@ -988,7 +1091,9 @@ def algorithmic_flops(wl, info, stage, nout=2):
         elif stage == "row_inv":
             total += nout * (ny / 2) * fft_x  # two rows per transform
     if stage == "cross_direct":
-        total = 28.0 * info["cross_pairs"]
+        # FP32 plans: 30 flops per target-cell pair (the far-field expansion
+        # through H^4, FMA = 2); FP64 plans: 28 per target-corner pair
+        total = (30.0 if wl.get("precision", "fp32") == "fp32" else 28.0) * info["cross_pairs"]
     return total
 
 
@@ -1095,6 +1200,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-fp64-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-e2e-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -235,12 +235,34 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
  * the inputs are copied to the plan's device staging buffers and sg_force runs
  * on `stream`. Fx, Fy are copied back, or, for a single in-plane patch whose
  * Fx, Fy buffers are page-locked (pinned, so mapped into the device address
- * space), written in place by the inverse row pass over the CPU-GPU link.
- * Host buffers may be pageable or pinned.
+ * space), written in place by the inverse row pass over the CPU-GPU link; when
+ * its input buffers are pinned too, the forward row pass reads them in place
+ * (no staging copy). Host buffers may be pageable or pinned.
  * Errors: as sg_force, plus SG_ENOMEM if the staging buffers cannot be allocated.
  */
 sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
                         void *fx, void *fy, void *stream);
+
+/*
+ * Bounded waits (not in the paper). Kernels that wait for bulk copies into
+ * shared memory (the column passes' kernel spectra, the FP32 direct sum's
+ * source tiles) give up after a number of attempts, record the failure in the
+ * workspace's device error word, wait for their copies in flight (with the
+ * default limit) and return early; the solve's outputs are then invalid.
+ *
+ * sg_plan_set_wait_limit sets the attempts of the solves of `plan` enqueued
+ * from then on (a batch keeps the limit in force when it was created): tries
+ * >= 0 attempts (0 gives up at once: a test of the error path), -1 the
+ * default (far above any real copy time). Host only. Errors: SG_EINVAL.
+ *
+ * sg_plan_check_error waits for all work on the device, then reads and clears
+ * the error word of the plan's own workspace (the one sg_force uses):
+ * SG_ETIMEOUT if a wait ran out since the last check, else SG_OK. The host
+ * entry points (sg_force_host) check it themselves; requests of a server
+ * report it as their result (sg_poll / sg_wait: SG_ETIMEOUT).
+ */
+sg_status sg_plan_set_wait_limit(sg_plan *plan, int tries);
+sg_status sg_plan_check_error(sg_plan *plan);
 
 /*
  * Per-stage device timers (tracing). With timing enabled, every sg_force on the
@@ -420,6 +442,11 @@ sg_status sg_batch_launch(sg_batch *batch, void *stream);
 
 /* Release the batch's graph and workspaces (synchronises the device). NULL is a no-op. */
 sg_status sg_batch_destroy(sg_batch *batch);
+
+/* Wait for all work on the device, then read and clear the device error words
+ * of the batch's workspaces: SG_ETIMEOUT if a bounded wait ran out in one of
+ * its kernels since the last check (see sg_plan_set_wait_limit), else SG_OK. */
+sg_status sg_batch_check_error(sg_batch *batch);
 
 /* Kernel launches one sg_batch_launch replays (members of one padded length
  * share each pass's launch). Errors: SG_EINVAL (NULL batch or out). */

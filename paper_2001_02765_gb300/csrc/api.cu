@@ -592,6 +592,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     plan->lattice_x0 = gi.X0;
     plan->lattice_y0 = gi.Y0;
     plan->nsplit = nsplit;
+    plan->wait_tries = SG_MBAR_MAX_TRIES;
 
     plan->geom.masks = nullptr;  // the cell codes below carry them
     plan->composite = gi.n > 1 || gi.masked;
@@ -1053,12 +1054,23 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
         plan->stage_bytes = bytes;
     }
     char *in = (char *)plan->stage_in, *out = (char *)plan->stage_out;
-    SG_CUDA_TRY(cudaMemcpyAsync(in, sigma, bytes, cudaMemcpyHostToDevice, st));
-    if (caller) {
-        SG_CUDA_TRY(cudaMemcpyAsync(in + bytes, deltax, bytes, cudaMemcpyHostToDevice, st));
-        SG_CUDA_TRY(cudaMemcpyAsync(in + 2 * bytes, deltay, bytes, cudaMemcpyHostToDevice, st));
+    // Likewise pinned inputs of a single in-plane patch are read in place by the
+    // forward row pass (and the edge-column transform), so the transfer overlaps
+    // the transform instead of preceding it.
+    const void *ms = hfx ? mapped_host(sigma) : nullptr;
+    const void *mdx = ms && caller ? mapped_host(deltax) : nullptr;
+    const void *mdy = ms && caller ? mapped_host(deltay) : nullptr;
+    const bool in_place = ms && (!caller || (mdx && mdy));
+    if (!in_place) {
+        SG_CUDA_TRY(cudaMemcpyAsync(in, sigma, bytes, cudaMemcpyHostToDevice, st));
+        if (caller) {
+            SG_CUDA_TRY(cudaMemcpyAsync(in + bytes, deltax, bytes, cudaMemcpyHostToDevice, st));
+            SG_CUDA_TRY(cudaMemcpyAsync(in + 2 * bytes, deltay, bytes, cudaMemcpyHostToDevice, st));
+        }
     }
-    if (hfx) {
+    if (in_place) {
+        SG_TRY(sg_force(plan, ms, mdx, mdy, hfx, hfy, stream));
+    } else if (hfx) {
         SG_TRY(sg_force(plan, in, caller ? in + bytes : nullptr, caller ? in + 2 * bytes : nullptr, hfx, hfy, stream));
     } else {
         SG_TRY(sg_force(plan, in, caller ? in + bytes : nullptr, caller ? in + 2 * bytes : nullptr, out, out + bytes,
@@ -1067,6 +1079,20 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
         SG_CUDA_TRY(cudaMemcpyAsync(fy, out + bytes, bytes, cudaMemcpyDeviceToHost, st));
     }
     SG_CUDA_TRY(cudaStreamSynchronize(st));
+    return check_device_error(plan);
+}
+
+sg_status sg_plan_set_wait_limit(sg_plan *plan, int tries)
+{
+    if (!plan || tries < -1) return fail("null plan or wait limit below -1");
+    plan->wait_tries = tries == -1 ? SG_MBAR_MAX_TRIES : tries;
+    return SG_OK;
+}
+
+sg_status sg_plan_check_error(sg_plan *plan)
+{
+    if (!plan) return fail("null plan");
+    SG_CUDA_TRY(cudaDeviceSynchronize());
     return check_device_error(plan);
 }
 

@@ -262,6 +262,24 @@ sg_status sg_batch_destroy(sg_batch *b)
     return SG_OK;
 }
 
+sg_status sg_batch_check_error(sg_batch *b)
+{
+    if (!b) return SG_EINVAL;
+    SG_CUDA_TRY(cudaDeviceSynchronize());
+    sg_status r = SG_OK;
+    for (sg_workspace &w : b->ws) {
+        int e = 0;
+        if (!w.err) continue;
+        SG_CUDA_TRY(cudaMemcpy(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            SG_CUDA_TRY(cudaMemset(w.err, 0, sizeof(int)));
+            sg_set_last_error_message("a bounded wait for a bulk copy ran out in a kernel of the batch");
+            r = SG_ETIMEOUT;
+        }
+    }
+    return r;
+}
+
 sg_status sg_batch_launches(const sg_batch *b, int *out)
 {
     if (!b || !out) return SG_EINVAL;

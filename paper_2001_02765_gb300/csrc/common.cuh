@@ -6,6 +6,7 @@
 #include <stddef.h>
 
 #include "sg.h"
+#include "tma.cuh"
 
 #define SG_CUDA_TRY(expr)                                  \
     do {                                                   \
@@ -253,6 +254,7 @@ struct sg_plan {
     sg_tile_desc *tiles;            // device
     int nsplit;                     // source-tile ranges per target block
     int far_grid;                   // CTAs of the persistent far-field launch (FP32 plans)
+    int wait_tries;                 // attempts of the kernels' bounded waits (SG_MBAR_MAX_TRIES by default)
     int ntargets;
     int4 *targets;                  // device: (lattice x, lattice y, output index, patch)
     int nblocks;

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_far(
     const sg_target_block *__restrict__ blocks, int nblocks, const int4 *__restrict__ targets,
     const sg_tile_desc *__restrict__ tiles, const sg_patch_dev *__restrict__ pd, int ntiles,
     const float4 *__restrict__ coefs, int nsplit, double G, double *__restrict__ partial, int ntargets,
-    int *__restrict__ words)
+    int *__restrict__ words, int tries)
 {
     __shared__ __align__(128) float4 buf[FAR_STAGES][SG_TILE_N];
     __shared__ uint64_t full[FAR_STAGES];
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_far(
         for (int k = 0; k < n; ++k, ++used) {
             const int stg = used % FAR_STAGES;
             const int t = k < n1 ? t0 + k : s2 + (k - n1);
-            const bool ok = mbar_wait_bounded(&full[stg], (used / FAR_STAGES) & 1, SG_MBAR_MAX_TRIES);
+            const bool ok = mbar_wait_bounded(&full[stg], (used / FAR_STAGES) & 1, tries);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -583,7 +583,8 @@ sg_status cross_solve_f32(sg_plan *plan, const sg_workspace *ws, const float *si
     sg_timing_begin(ws, SG_STAGE_DIRECT, st);
     k_cross_far<<<plan->far_grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->nblocks, plan->targets, plan->tiles,
                                                               plan->patch_dev, plan->ntiles, w, plan->nsplit,
-                                                              plan->geom.G, ws->partial, plan->ntargets, ws->err);
+                                                              plan->geom.G, ws->partial, plan->ntargets, ws->err,
+                                                              plan->wait_tries);
     SG_CUDA_TRY(cudaGetLastError());
     double *near = ws->partial + (int64_t)plan->nsplit * plan->ntargets * 2;
     const int64_t nblk = ((int64_t)plan->ntargets + NEAR_WARPS - 1) / NEAR_WARPS;

@@ -91,6 +91,7 @@ struct col_args {
     const cplx_t<T> *edge;   // central slopes: sigma's edge-column transforms
     const T *phase;          // central slopes: spectral factors
     int ny;
+    int tries;               // attempts of the bounded wait for the spectra (the plan's wait limit)
 };
 template <typename T>
 struct row_inv_args {
@@ -201,11 +202,12 @@ __device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec
         bulk_copy_g2s(ssp + p * CB * QS, spec + p * qplane + (int64_t)kx0 * QS, ncol * QS * sizeof(T), bar);
 }
 
-// Bounded wait for the spectra; on timeout records the error, gives the copies
-// one more bounded wait and tells the CTA to return (uniformly).
-__device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err)
+// Bounded wait for the spectra (`tries` attempts); on timeout records the
+// error, waits for the copies in flight (bounded, full limit) and tells the CTA
+// to return (uniformly).
+__device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err, int tries)
 {
-    const bool ok = mbar_wait_bounded(bar, 0, SG_MBAR_MAX_TRIES);
+    const bool ok = mbar_wait_bounded(bar, 0, tries);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
             atomicExch(err, 1);
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
         }
         if (COL_NBUF == 1 && f > 0) __syncthreads();
         fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
-        if (f == 0 && !spectra_ready(&bar, err)) return;
+        if (f == 0 && !spectra_ready(&bar, err, args.tries)) return;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int ky = jt + q * STEP;
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
         if (jt + m * STEP == ny - 1) rows[c][1] = v[m];
     int par = 0;
     fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
-    if (!spectra_ready(&bar, err)) return;
+    if (!spectra_ready(&bar, err, args.tries)) return;
 
     C accx[8], accy[8];
 #pragma unroll
@@ -657,7 +659,7 @@ inline uniform_passes<T> uniform_setup(const sg_plan *plan, const sg_workspace *
     u.rf.work = wf;
     C *edge = wf + (int64_t)u.qx * d.ny;  // after sigma's row transforms (central slopes)
     u.ed = {src.sigma, d.nx, d.ny, edge};
-    u.col = {wf, wi, pot_spec ? pot_spec : (const T *)pp.spectra, edge, (const T *)pp.phase, d.ny};
+    u.col = {wf, wi, pot_spec ? pot_spec : (const T *)pp.spectra, edge, (const T *)pp.phase, d.ny, plan->wait_tries};
     u.ri = {wi, (T *)fx + off, pot_spec ? nullptr : (T *)fy + off, fz ? (T *)fz + off : nullptr, d.nx, d.ny};
     sg_tune_shape(plan->prec, d.px, u.shx);
     sg_tune_shape(plan->prec, d.py, u.shy);

@@ -15,6 +15,8 @@
 // Nothing on the device waits for anything: completion is observed on the host.
 #include "common.cuh"
 
+#include <string.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -58,6 +60,7 @@ struct sg_server {
     int max_inflight = 0;
     cudaMemPool_t pool = nullptr;
     std::vector<cudaStream_t> streams;
+    int *err_host = nullptr;            // per slot: the request's device error word, copied after its solve (pinned)
     std::vector<int> free_slots;
     std::deque<sg_request *> queue;
     std::vector<sg_request *> running;
@@ -87,8 +90,10 @@ void CUDART_CB on_done(void *p)
 void finalize(sg_server *s, sg_request *r)
 {
     sg_workspace_free(&r->ws, s->streams[r->slot], true);
-    s->free_slots.push_back(r->slot);
     s->bytes_in_use -= r->bytes;
+    // a bounded wait that ran out in one of the request's kernels (device error word)
+    if (r->result == SG_OK && s->err_host[r->slot] != 0) r->result = SG_ETIMEOUT;
+    s->free_slots.push_back(r->slot);
     r->slot = -1;
     if (r->result == SG_OK) {
         s->completed++;
@@ -134,7 +139,11 @@ bool start(sg_server *s, sg_request *r)
     s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
     r->t_start = now_s();
     r->state.store(RQ_RUNNING);
+    s->err_host[slot] = 0;
     r->result = sg_force_ws(r->plan, &r->ws, r->sigma, r->dx, r->dy, r->fx, r->fy, st);
+    if (r->result == SG_OK &&
+        cudaMemcpyAsync(&s->err_host[slot], r->ws.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        r->result = SG_ECUDA;
     if (r->result != SG_OK || cudaLaunchHostFunc(st, on_done, r) != cudaSuccess) {
         if (r->result == SG_OK) r->result = SG_ECUDA;
         cudaGetLastError();
@@ -208,6 +217,8 @@ sg_status sg_server_create(size_t hbm_budget, int max_inflight, sg_server **out)
         uint64_t keep = UINT64_MAX;  // keep freed blocks in the pool for the next request
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->err_host, sizeof(int) * max_inflight, cudaHostAllocDefault);
+    if (e == cudaSuccess) memset(s->err_host, 0, sizeof(int) * max_inflight);
     for (int k = 0; k < max_inflight && e == cudaSuccess; ++k) {
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -220,6 +231,7 @@ sg_status sg_server_create(size_t hbm_budget, int max_inflight, sg_server **out)
         sg_set_last_cuda_error(e, "sg_server_create");
         for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
         if (s->pool) cudaMemPoolDestroy(s->pool);
+        if (s->err_host) cudaFreeHost(s->err_host);
         delete s;
         return SG_ECUDA;
     }
@@ -250,6 +262,7 @@ sg_status sg_server_destroy(sg_server *s)
         cudaStreamDestroy(st);
     }
     cudaMemPoolDestroy(s->pool);
+    cudaFreeHost(s->err_host);
     delete s;
     return SG_OK;
 }

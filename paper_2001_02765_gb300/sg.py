@@ -86,6 +86,9 @@ _SIGNATURES = {
     "sg_force3": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_potential": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sg_plan_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sg_plan_check_error": (ctypes.c_int, [_VP]),
+    "sg_batch_check_error": (ctypes.c_int, [_VP]),
     "sg_plan_get_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "sg_direct_force_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -250,6 +253,19 @@ def sg_force_host(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=
 
 
 STAGE_NAMES = ("row_fwd", "col_conv", "row_inv", "corner_weights", "cross_direct", "composite")
+
+
+def sg_plan_set_wait_limit(handle, tries):
+    _check(load().sg_plan_set_wait_limit(handle, int(tries)), "sg_plan_set_wait_limit")
+
+
+def sg_plan_check_error(handle):
+    """Status of the plan's device error word (waits for the device): SG_OK or SG_ETIMEOUT."""
+    return load().sg_plan_check_error(handle)
+
+
+def sg_batch_check_error(batch):
+    return load().sg_batch_check_error(batch)
 
 
 def sg_plan_set_timing(handle, enable):
