@@ -232,13 +232,70 @@ int grid_for(int64_t n)
     return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
 }
 
+// Neighbour-leaf slopes of the leaves among the cells c0 .. c1 (one level; the
+// coarser levels' slopes are in D already). Per axis, deltax = (v_R - v_L) /
+// (x_R - x_L) from what lies across the two sides (links nb, see sg_plan):
+// a leaf of the level (its sigma0 at its centre), a refined cell (the mean of
+// the two children touching the side: their sigma0, or their filled value F
+// when refined themselves, at their centres), a coarser leaf (its linear
+// reconstruction sigma0 + delta_perp (t_perp - c_perp) at its centre line), or
+// nothing (0 at one cell width). Exact for a linear density. FP64 arithmetic.
+template <typename T>
+__global__ void k_amr_slopes(const int2 *__restrict__ nb, const int2 *__restrict__ pos, const int *__restrict__ code,
+                             const T *__restrict__ sigma, const T *__restrict__ F, T *__restrict__ D, int64_t P,
+                             int64_t c0, int64_t c1, int step, double lambda)
+{
+    for (int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < c1; c += (int64_t)gridDim.x * blockDim.x) {
+        if (code[c] != SG_CELL_LEAF) {
+            D[c] = D[c + P] = (T)0;
+            continue;
+        }
+        const int2 tp = pos[c];
+        double out[2];
+#pragma unroll
+        for (int axis = 0; axis < 2; ++axis) {
+            double v[2], x[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int side = axis == 0 ? 2 * k : 2 * k + 1;  // left, down, right, up
+                const int2 d = nb[c * 4 + side];
+                const double t_ax = axis == 0 ? tp.x : tp.y;
+                if (d.y >= 0) {
+                    const double va = code[d.x] == SG_CELL_LEAF ? (double)sigma[d.x] : (double)F[d.x];
+                    const double vb = code[d.y] == SG_CELL_LEAF ? (double)sigma[d.y] : (double)F[d.y];
+                    const int2 pa = pos[d.x], pb = pos[d.y];
+                    v[k] = 0.5 * (va + vb);
+                    x[k] = axis == 0 ? 0.5 * ((double)pa.x + pb.x) : 0.5 * ((double)pa.y + pb.y);
+                } else if (d.y == -1) {
+                    const int2 pa = pos[d.x];
+                    v[k] = sigma[d.x];
+                    x[k] = axis == 0 ? pa.x : pa.y;
+                } else if (d.y == -2) {
+                    const int2 pa = pos[d.x];
+                    // the coarser leaf's slope across the axis: deltay for the x axis, deltax for y
+                    const double perp = axis == 0 ? (double)D[d.x + P] * ((double)tp.y - pa.y)
+                                                  : (double)D[d.x] * ((double)tp.x - pa.x);
+                    v[k] = (double)sigma[d.x] + perp * lambda;
+                    x[k] = axis == 0 ? pa.x : pa.y;
+                } else {
+                    v[k] = 0.0;
+                    x[k] = t_ax + (k ? step : -step);
+                }
+            }
+            out[axis] = (v[1] - v[0]) / ((x[1] - x[0]) * lambda);
+        }
+        D[c] = (T)out[0];
+        D[c + P] = (T)out[1];
+    }
+}
+
 template <typename T>
 sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
-                    cudaStream_t st)
+                    cudaStream_t st, bool fill_only = false)
 {
     T *s = (T *)ws->sfield;
     T *F = s + 3 * plan->ncells;  // filled values of covered cells
-    const bool slopes = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    const bool slopes = dx != nullptr && dy != nullptr;
     const T *sx = slopes ? (const T *)dx : nullptr, *sy = slopes ? (const T *)dy : nullptr;
     const int lmax = plan->comp_depth - 1;
     // covered cells of the refined levels, finest first (level lmax has none)
@@ -258,6 +315,7 @@ sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, co
                                       plan->npatches, t0, t1, (const T *)sigma, sx, sy, F));
         SG_CUDA_TRY(cudaGetLastError());
     }
+    if (fill_only) return SG_OK;
     auto kc = k_composite<T>;
     if (lmax >= 2)  // after the fills of the covered cells
         SG_CUDA_TRY(sg_launch_dep(kc, dim3(grid_for(plan->comp_items)), dim3(256), patch_table_bytes(plan->npatches),
@@ -272,6 +330,45 @@ sg_status prepare_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, co
 }
 
 }  // namespace
+
+// Slopes of a hierarchy with SG_SLOPES_CENTRAL into the workspace planes D
+// (after the composite's filled values F of the covered cells), one launch per
+// level from the coarsest (a leaf's slope reads only coarser leaves' slopes).
+template <typename T>
+sg_status slopes_t(sg_plan *plan, const sg_workspace *ws, const void *sigma, cudaStream_t st)
+{
+    T *s = (T *)ws->sfield;
+    const int64_t P = plan->ncells;
+    const T *F = s + 3 * P;
+    T *D = s + 6 * P;
+    for (int l = 0; l < plan->comp_depth; ++l) {
+        const int64_t c0 = plan->lev_cells[l], c1 = plan->lev_cells[l + 1];
+        if (c1 <= c0) continue;
+        k_amr_slopes<T><<<grid_for(c1 - c0), 256, 0, st>>>(plan->slope_nb, plan->cell_pos, plan->cell_code,
+                                                          (const T *)sigma, F, D, P, c0, c1, plan->lev_step[l],
+                                                          plan->lattice_unit);
+        SG_CUDA_TRY(cudaGetLastError());
+    }
+    return SG_OK;
+}
+
+sg_status sg_composite_prepare(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx,
+                               const void *dy, cudaStream_t st)
+{
+    if (!plan->amr_central) return sg_amr_prepare(plan, ws, sigma, dx, dy, st);
+    sg_timing_begin(ws, SG_STAGE_COMPOSITE, st);
+    const size_t es = plan->prec == SG_FP64 ? 8 : 4;
+    const char *D = (const char *)ws->sfield + 6 * (size_t)plan->ncells * es;
+    sg_status r = plan->prec == SG_FP64 ? prepare_t<double>(plan, ws, sigma, nullptr, nullptr, st, true)
+                                        : prepare_t<float>(plan, ws, sigma, nullptr, nullptr, st, true);
+    if (r == SG_OK)
+        r = plan->prec == SG_FP64 ? slopes_t<double>(plan, ws, sigma, st) : slopes_t<float>(plan, ws, sigma, st);
+    if (r == SG_OK)
+        r = plan->prec == SG_FP64 ? prepare_t<double>(plan, ws, sigma, D, D + (size_t)plan->ncells * es, st)
+                                  : prepare_t<float>(plan, ws, sigma, D, D + (size_t)plan->ncells * es, st);
+    sg_timing_end(ws, SG_STAGE_COMPOSITE, st);
+    return r;
+}
 
 sg_status sg_amr_prepare(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          cudaStream_t st)

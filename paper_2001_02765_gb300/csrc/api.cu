@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 // ------------------------------------------------------------------ errors --
@@ -114,10 +115,8 @@ sg_status analyse(const sg_geom *g, geom_info &gi)
     const int n = g->npatches;
     const sg_patch *P = g->patches;
     gi.n = n;
-    if (g->slope_mode == SG_SLOPES_CENTRAL && n != 1) return fail("central slopes need a single patch");
     if (g->masks)
         for (int k = 0; k < n; ++k) gi.masked = gi.masked || g->masks[k] != nullptr;
-    if (gi.masked && g->slope_mode == SG_SLOPES_CENTRAL) return fail("central slopes need an unmasked patch");
     if (gi.masked && g->z != 0.0) return fail("off-plane forces (z != 0) need an unmasked patch");
     if (P[0].level != 0) return fail("the first patch must be on level 0");
     for (int k = 0; k < n; ++k) {
@@ -336,6 +335,88 @@ void build_targets(const sg_geom *g, const geom_info &gi, std::vector<int4> &tg,
     }
 }
 
+// Links of the neighbour-leaf slope rule (amr.cu): per cell and side (left,
+// down, right, up) what lies across the side's midpoint (see sg_plan), found
+// through per-level maps of the cells' level-grid coordinates; and the lattice
+// coordinates of every cell centre.
+int64_t floor_div64(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+void build_slope_links(const sg_geom *g, const geom_info &gi, std::vector<int2> &nb, std::vector<int2> &pos)
+{
+    const int nlev = gi.lmax + 1;
+    std::vector<std::unordered_map<uint64_t, int64_t>> map(nlev);
+    auto key = [](int64_t x, int64_t y) { return ((uint64_t)(uint32_t)x << 32) | (uint32_t)y; };
+    for (int k = 0; k < gi.n; ++k) {
+        const sg_patch &p = g->patches[k];
+        const int64_t gx0 = gi.ox[k] / gi.step[k], gy0 = gi.oy[k] / gi.step[k];
+        auto &m = map[p.level];
+        m.reserve(m.size() + (size_t)p.nx * p.ny);
+        for (int j = 0; j < p.ny; ++j)
+            for (int i = 0; i < p.nx; ++i)
+                if (gi.code[k][(size_t)j * p.nx + i] != SG_CELL_ABSENT)
+                    m[key(gx0 + i, gy0 + j)] = gi.cell_off[k] + (int64_t)j * p.nx + i;
+    }
+    auto find = [&](int l, int64_t x, int64_t y) -> int64_t {
+        if (x < 0 || y < 0) return -1;
+        auto it = map[l].find(key(x, y));
+        return it == map[l].end() ? -1 : it->second;
+    };
+    std::vector<int> code_of((size_t)gi.ncells);
+    for (int k = 0; k < gi.n; ++k)
+        std::copy(gi.code[k].begin(), gi.code[k].end(), code_of.begin() + gi.cell_off[k]);
+    nb.assign((size_t)gi.ncells * 4, make_int2(-1, -3));
+    pos.assign((size_t)gi.ncells, make_int2(0, 0));
+    const int sdx[4] = {-1, 0, 1, 0}, sdy[4] = {0, -1, 0, 1};
+    for (int k = 0; k < gi.n; ++k) {
+        const sg_patch &p = g->patches[k];
+        const int l = p.level;
+        const int64_t gx0 = gi.ox[k] / gi.step[k], gy0 = gi.oy[k] / gi.step[k];
+        for (int j = 0; j < p.ny; ++j) {
+            for (int i = 0; i < p.nx; ++i) {
+                const int64_t c = gi.cell_off[k] + (int64_t)j * p.nx + i;
+                pos[c] = make_int2(gi.ox[k] + (2 * i + 1) * (gi.step[k] / 2), gi.oy[k] + (2 * j + 1) * (gi.step[k] / 2));
+                if (code_of[c] != SG_CELL_LEAF) continue;
+                const int64_t gx = gx0 + i, gy = gy0 + j;
+                for (int s = 0; s < 4; ++s) {
+                    const int dx = sdx[s], dy = sdy[s];
+                    int2 d = make_int2(-1, -3);
+                    const int64_t n = find(l, gx + dx, gy + dy);
+                    if (n >= 0 && code_of[n] == SG_CELL_LEAF) {
+                        d = make_int2((int)n, -1);
+                    } else if (n >= 0 && code_of[n] >= 0 && l + 1 < nlev) {
+                        // the two children of the refined neighbour that touch the side
+                        const int64_t nx2 = 2 * (gx + dx), ny2 = 2 * (gy + dy);
+                        int64_t a, b;
+                        if (dx != 0) {
+                            const int64_t cx = nx2 + (dx > 0 ? 0 : 1);
+                            a = find(l + 1, cx, ny2);
+                            b = find(l + 1, cx, ny2 + 1);
+                        } else {
+                            const int64_t cy = ny2 + (dy > 0 ? 0 : 1);
+                            a = find(l + 1, nx2, cy);
+                            b = find(l + 1, nx2 + 1, cy);
+                        }
+                        if (a >= 0 && b >= 0) d = make_int2((int)a, (int)b);
+                    } else {
+                        // the coarser leaf containing the point just across the side's midpoint
+                        // (quarters of a level-l cell: 4 g + 2 + 3 d)
+                        const int64_t qx = 4 * gx + 2 + 3 * dx, qy = 4 * gy + 2 + 3 * dy;
+                        for (int m = l - 1; m >= 0; --m) {
+                            const int64_t w = 4LL << (l - m);
+                            const int64_t c2 = find(m, floor_div64(qx, w), floor_div64(qy, w));
+                            if (c2 >= 0 && code_of[c2] == SG_CELL_LEAF) {
+                                d = make_int2((int)c2, -2);
+                                break;
+                            }
+                        }
+                    }
+                    nb[(size_t)c * 4 + s] = d;
+                }
+            }
+        }
+    }
+}
+
 // Level-convolution parameters (lvconv.cu) of a composite hierarchy, or false
 // when it does not qualify: z == 0, not central slopes, at least two levels,
 // and a finest-lattice extent whose padded length fits the transforms.
@@ -343,7 +424,7 @@ void build_targets(const sg_geom *g, const geom_info &gi, std::vector<int4> &tg,
 bool lv_params(const sg_geom *g, const geom_info &gi, sg_precision prec, sg_lv_setup_args &a,
                std::vector<std::vector<int>> &maps, int64_t &bytes)
 {
-    if (gi.lmax < 1 || g->z != 0.0 || g->slope_mode == SG_SLOPES_CENTRAL) return false;
+    if (gi.lmax < 1 || g->z != 0.0) return false;
     const sg_patch *P = g->patches;
     int64_t wx = 0, wy = 0;  // level-0 extent in finest cells (lattice units are half finest cells)
     for (int k = 0; k < gi.n; ++k) {
@@ -457,6 +538,7 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
     s.work = lv_bytes < 0 ? work : lv_bytes;
     for (int L = SG_MIN_PAD; L <= s.max_pad; L <<= 1) s.twiddles += (int64_t)L * (16 + 8);
     if (gi.n > 1 || gi.masked) s.direct = 3 * gi.ncells * (int64_t)es + gi.ncells * (int64_t)sizeof(int);
+    if ((gi.n > 1 || gi.masked) && g->slope_mode == SG_SLOPES_CENTRAL) s.direct += 40 * gi.ncells;  // links, centres
     if (gi.n > 1 && lv_bytes < 0) {
         const int64_t slices = prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1;
         s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
@@ -524,6 +606,8 @@ void plan_free(sg_plan *plan)
     cudaFree(plan->comp_cells);
     delete[] plan->comp_cells_host;
     cudaFree(plan->zone_slot);
+    cudaFree(plan->slope_nb);
+    cudaFree(plan->cell_pos);
     if (plan->ws) {
         sg_workspace_free(plan->ws, 0, false);
         delete plan->ws;
@@ -627,7 +711,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         pdev[k] = d;
         const int nplanes = g->z != 0.0 ? 9 : 6;
         if (!use_lv) st = dev_alloc(plan, &pp.spectra, nplanes * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
-        if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0)
+        if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0 && !(gi.n > 1 || gi.masked))
             st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
     }
     if (plan->composite) {
@@ -659,6 +743,23 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         if (st == SG_OK) st = sg_plan_upload(plan, (void **)&plan->comp_cells, cells.data(), cells.size() * sizeof(int64_t));
         if (st == SG_OK)
             st = sg_plan_upload(plan, (void **)&plan->comp_item_off, items.data(), items.size() * sizeof(int64_t));
+        if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL) {
+            // neighbour-leaf slopes: links across every side, cell centres, level ranges,
+            // and two more workspace planes for the slopes
+            std::vector<int2> nb, pos;
+            build_slope_links(g, gi, nb, pos);
+            plan->amr_central = true;
+            plan->ws_sfield_bytes = 8 * gi.ncells * (int64_t)es;
+            st = sg_plan_upload(plan, (void **)&plan->slope_nb, nb.data(), nb.size() * sizeof(int2));
+            if (st == SG_OK) st = sg_plan_upload(plan, (void **)&plan->cell_pos, pos.data(), pos.size() * sizeof(int2));
+            for (int l = 0; l <= SG_MAX_LEVELS; ++l) plan->lev_cells[l] = gi.ncells;
+            for (int k = gi.n - 1; k >= 0; --k) {
+                plan->lev_cells[g->patches[k].level] = gi.cell_off[k];
+                plan->lev_step[g->patches[k].level] = gi.step[k];
+            }
+            for (int l = SG_MAX_LEVELS - 1; l >= 0; --l)
+                if (plan->lev_cells[l] > plan->lev_cells[l + 1]) plan->lev_cells[l] = plan->lev_cells[l + 1];
+        }
     }
     if (st == SG_OK) st = dev_alloc(plan, &plan->patch_dev, gi.n * sizeof(sg_patch_dev));
     if (st == SG_OK)
@@ -668,8 +769,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     int64_t wf = 0, wi = 0;
     for (int k = 0; k < gi.n; ++k) {
         const int64_t q = (int64_t)(pdev[k].px / 2 + 1) * pdev[k].ny * (int64_t)(2 * es);
-        // central slopes (in the plane) transform sigma only, plus the two edge columns (2 x py complex)
-        const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0;
+        // central slopes of a single unmasked patch (in the plane) transform sigma only, plus the
+        // two edge columns (2 x py complex); hierarchies transform three composite fields
+        const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0 && !(gi.n > 1 || gi.masked);
         const int64_t f = central ? q + 2LL * pdev[k].py * (int64_t)(2 * es) : 3 * q;
         const int nout = g->z != 0.0 ? 3 : 2;
         if (f > wf) wf = f;
@@ -710,11 +812,12 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     if (st == SG_OK && use_lv) st = sg_lv_setup(plan, &lva);  // sets the transform scratch sizes
     plan->scratch_bytes = sg_workspace_bytes(plan);  // the plan's own workspace is allocated at its first sg_force
     {
-        const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0;
+        const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0 && !(gi.n > 1 || gi.masked);
         // level convolutions: one launch each for the row, column, column-MAC and inverse-row passes
         int n = use_lv ? 4 : gi.n * (central ? 4 : 3);
         if (plan->composite) {
             n += gi.lmax > 0 ? gi.lmax : 1;  // composite sources: covered cells of levels 1 .. lmax-1, then all S_l
+            if (plan->amr_central) n += (gi.lmax > 1 ? gi.lmax - 1 : 0) + gi.lmax + 1;  // fills, then slopes per level
             // direct sum: corner weights, pair sum (+ split reduction) in FP64; cell coefficients,
             // far field, near field and the combination in FP32
             if (plan->ntiles > 0) n += prec == SG_FP64 ? 2 + (nsplit > 1) : 4;
@@ -814,7 +917,7 @@ sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, 
     if (!plan->composite) return sg_uniform_solve(plan, ws, 0, sigma, dx, dy, fx, fy, fz, st);
     // AMR or masks: composite sources, then level convolutions, or same-patch FFT
     // convolutions plus the cross-patch direct sum
-    SG_TRY(sg_amr_prepare(plan, ws, sigma, dx, dy, st));
+    SG_TRY(sg_composite_prepare(plan, ws, sigma, dx, dy, st));
     if (plan->lv) return sg_lv_solve(plan, ws, fx, fy, st);
     const size_t es = elem_size(plan->prec);
     const char *S = (const char *)ws->sfield;
@@ -989,8 +1092,8 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
         SG_TRY(ensure_ws(plan));
         sg_timing_reset(plan->timing);
         plan->ws->timing = plan->timing;
-        SG_TRY(sg_amr_prepare(plan, plan->ws, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr,
-                              (cudaStream_t)stream));
+        SG_TRY(sg_composite_prepare(plan, plan->ws, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr,
+                                    (cudaStream_t)stream));
         return sg_lv_potential(plan, plan->ws, phi, (cudaStream_t)stream);
     }
     SG_TRY(sg_potential_spectra_build(plan));

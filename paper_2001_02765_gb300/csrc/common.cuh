@@ -235,6 +235,16 @@ struct sg_plan {
     int comp_lev_first[SG_MAX_LEVELS + 1];
     int comp_depth;                 // levels of the hierarchy (lmax + 1)
 
+    // slopes of hierarchies with SG_SLOPES_CENTRAL (the neighbour-leaf rule, amr.cu):
+    // per cell and side (left, down, right, up) what lies across it, {a, b}: b >= 0 the
+    // two children a, b of a refined cell of the same level that touch the side; b = -1
+    // the leaf a of the same level; b = -2 the coarser leaf a; b = -3 nothing (outside)
+    bool amr_central;
+    int2 *slope_nb;                 // device, 4 x ncells
+    int2 *cell_pos;                 // device, ncells: lattice coordinates of the cell centres
+    int64_t lev_cells[SG_MAX_LEVELS + 1];  // cells of level l: [lev_cells[l], lev_cells[l+1]) (patches sorted by level)
+    int lev_step[SG_MAX_LEVELS];    // cell width of level l in lattice units
+
     // zone plans (sg_plan_create_zones): zone k sits at cell zone_slot[k] (device)
     int64_t nzones;
     int64_t *zone_slot;
@@ -337,6 +347,10 @@ sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const voi
 sg_status sg_cross_far_grid(sg_plan *plan, int nsm);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          cudaStream_t st);
+// Composite sources of a solve (amr.cu): with caller slopes or none as given; for
+// SG_SLOPES_CENTRAL hierarchies the neighbour-leaf slopes first (workspace planes).
+sg_status sg_composite_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx,
+                               const void *dy, cudaStream_t st);
 sg_status sg_fft_lines_fp64(double2 *data, int L, int count, int64_t seq_stride, int64_t elem_stride,
                            const double2 *tw);
 // Level convolutions: host setup (level images, maps, kernel spectra) and the solve.

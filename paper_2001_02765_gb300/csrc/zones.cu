@@ -267,8 +267,7 @@ sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, 
                                size_t hbm_budget, sg_plan **out)
 {
     if (!out || (prec != SG_FP64 && prec != SG_FP32)) return zfail("invalid precision or output pointer");
-    if (slope_mode != SG_SLOPES_NONE && slope_mode != SG_SLOPES_CALLER)
-        return zfail("zone plans take SG_SLOPES_NONE or SG_SLOPES_CALLER");
+    if (slope_mode < SG_SLOPES_NONE || slope_mode > SG_SLOPES_CALLER) return zfail("unknown slope mode");
     std::unordered_map<uint64_t, int64_t> idx;
     int lmax = 0;
     SG_TRY(zones_index(zones, idx, lmax));

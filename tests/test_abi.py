@@ -53,10 +53,13 @@ def test_validate_rejects(lib, bad, why):
     assert sg.sg_geom_validate(bad) == sg.SG_EINVAL, why
 
 
-def test_validate_rejects_central_slopes_on_amr(lib):
+def test_validate_central_slopes_on_amr(lib):
+    """Central slopes are the neighbour-leaf rule on hierarchies (in the plane);
+    off the plane they still need a single unmasked patch."""
     pat = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))]
-    assert sg.sg_geom_validate(pat, slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_EINVAL
+    assert sg.sg_geom_validate(pat, slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_OK
     assert sg.sg_geom_validate(pat[:1], slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_OK
+    assert sg.sg_geom_validate(pat, slope_mode=sg.SG_SLOPES_CENTRAL, z=0.1) == sg.SG_EINVAL
 
 
 def test_plan_bytes_estimate(lib):

@@ -289,3 +289,56 @@ def test_levels_4096_fp64_sampled(sg):
     idx = np.sort(np.concatenate([rng.choice(n0, 64, replace=False), n0 + rng.choice(n0, 64, replace=False),
                                   2 * n0 + rng.choice(512 * 512, 64, replace=False)]))
     _check(sg, patches, "fp64", 2, sig, sx, sy, 1e-11, target_index=idx, cross=2)
+
+
+CENTRAL_CASES = {
+    "nested": [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))],
+    "ragged": [(0, 37, 29, -1.0, -0.8, 0.05), (1, 22, 14, -0.6, -0.3, 0.025), (1, 6, 8, 0.2, 0.1, 0.025),
+               (2, 10, 12, -0.5, -0.25, 0.0125)],
+    "table10": TABLE10,
+}
+
+
+@CROSS
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("case", sorted(CENTRAL_CASES))
+def test_central_slopes_on_hierarchies(sg, case, prec, tol, cross):
+    """SG_SLOPES_CENTRAL on a hierarchy: the neighbour-leaf slope rule computed
+    on the GPU, against the oracle's rule (oracle.slopes) fed to the plain
+    leaf-pair sum."""
+    from oracle import slopes as S
+    patches = CENTRAL_CASES[case]
+    sig, _, _ = W.bumps_on_patches(patches, 23)
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan, fx, fy = _run(sg, patches, prec, sg.SG_SLOPES_CENTRAL, sig, None, None, cross=cross)
+    P = oamr.make_patches(patches)
+    s64 = [np.asarray(a, dt).astype(np.float64) for a in sig]
+    ox, oy = S.patch_neighbour_slopes(P, s64)
+    leaves, rx, ry = oamr.amr_direct_force(P, s64, ox, oy)
+    err = rel_l2(gather_leaves(plan, fx, leaves), gather_leaves(plan, fy, leaves), rx, ry)
+    plan.close()
+    print("rel L2 %s cross=%d central: %.3e (tolerance %.0e)" % (prec, cross, err, tol))
+    assert err < tol
+
+
+def test_central_slopes_fp32_config3_sampled(sg):
+    """The config-3 hierarchy (three 256^2 levels, exp(-R/0.1)) with slopes from
+    the neighbour-leaf rule, FP32 level convolutions: 128 leaves next to the
+    coarse/fine boundaries and 64 elsewhere against the oracle."""
+    from oracle import slopes as S
+    case = W.exponential_hierarchy(256, 3, 0.1)
+    patches = [(lev,) + p for lev, p in enumerate(case["patches"])]
+    plan, fx, fy = _run(sg, patches, "fp32", sg.SG_SLOPES_CENTRAL, case["sigma"], None, None)
+    P = oamr.make_patches(patches)
+    s64 = [np.asarray(a, np.float32).astype(np.float64) for a in case["sigma"]]
+    ox, oy = S.patch_neighbour_slopes(P, s64)
+    cand = _boundary_leaf_index(patches)
+    nleaf = sum(int(m.sum()) for m in case["leaf"])
+    rng = np.random.Generator(np.random.PCG64(33))
+    idx = np.unique(np.concatenate([rng.choice(cand, 128, replace=False), rng.choice(nleaf, 64, replace=False)]))
+    leaves, rx, ry = oamr.amr_direct_force(P, s64, ox, oy, target_index=idx)
+    leaves = {k: v[idx] for k, v in leaves.items()}
+    err = rel_l2(gather_leaves(plan, fx, leaves), gather_leaves(plan, fy, leaves), rx, ry)
+    plan.close()
+    print("rel L2 fp32 central config 3: %.3e" % err)
+    assert err < 1e-5

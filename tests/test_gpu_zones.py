@@ -250,3 +250,31 @@ def test_force_zones_errors(sg):
         sg.sg_force_zones(zp.handle, b.data_ptr(), 0, 0, b.data_ptr(), b.data_ptr())  # slopes missing
     assert e.value.status == sg.SG_EINVAL
     zp.close()
+
+
+@pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
+@pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", F32_TOL)])
+def test_band_hierarchy_central_slopes(sg, prec, tol, cross):
+    """Zone plans with SG_SLOPES_CENTRAL (the neighbour-leaf rule across zones of
+    every level): against the oracle's rule and the plain leaf sum."""
+    from oracle import slopes as S
+    hier = W.band_hierarchy(40, 3, "ilr", "d22")
+    args = _hier_args(hier)
+    xc, yc, _ = W.zone_geometry(hier)
+    s, _, _ = _d_sigma("d22", xc, yc)
+    dt = np.float64 if prec == "fp64" else np.float32
+    import torch
+    plan = sg.ZonePlan(*args, precision=prec, slope_mode=sg.SG_SLOPES_CENTRAL, cross_mode=cross)
+    assert plan.info["cross_mode"] == cross
+    fx, fy = plan.force_zones(to_dev(s, dt))
+    torch.cuda.synchronize()
+    fx, fy = fx.cpu().numpy().astype(np.float64), fy.cpu().numpy().astype(np.float64)
+    plan.close()
+    leaf = hier["leaf"]
+    s64 = np.asarray(s, dt).astype(np.float64)
+    ox, oy = S.zone_neighbour_slopes(hier["x0"], hier["y0"], hier["h0"], hier["level"], hier["ix"], hier["iy"], leaf,
+                                     s64)
+    rx, ry = _oracle(args, leaf, s64, ox, oy, np.float64)
+    err = rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf])
+    print("rel L2 %s cross=%d central: %.3e (tolerance %.0e)" % (prec, cross, err, tol))
+    assert err < tol

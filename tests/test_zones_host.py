@@ -121,6 +121,7 @@ def test_masked_patch_rules(lib):
     hole[2, 2] = 0  # the parent of the fine block at (0..1, 0..1) of the child is coarse cell (2, 2)
     assert sg.sg_geom_validate([base, fine], masks=[hole, None]) == sg.SG_EINVAL
     assert "absent parent" in sg.last_error()
-    assert sg.sg_geom_validate([base], masks=[hole], slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_EINVAL
+    # central slopes on a masked patch: the neighbour-leaf rule (absent cells count as outside)
+    assert sg.sg_geom_validate([base], masks=[hole], slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_OK
     assert sg.sg_geom_validate([base], masks=[hole], z=0.1) == sg.SG_EINVAL
     assert sg.sg_geom_validate([base], masks=[np.zeros((8, 8))]) == sg.SG_EINVAL  # no leaf at all
