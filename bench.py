@@ -739,10 +739,14 @@ def run_gpu(args):
     if pot and (zt or zones is not None):
         raise SystemExit("--quantity potential takes the in-plane patch workloads")
 
+    cross = {"auto": sg.SG_CROSS_AUTO, "direct": sg.SG_CROSS_DIRECT, "levels": sg.SG_CROSS_LEVELS}[args.cross]
+
     def make_plan(prec):
+        # the FP32 plan takes --cross; the FP64 plain comparator the library's own choice
+        c = cross if prec == "fp32" else sg.SG_CROSS_AUTO
         if zones is not None:
-            return sg.ZonePlan(*zones, precision=prec, slope_mode=wl["slope_mode"])
-        return sg.Plan(wl["patches"], precision=prec, slope_mode=wl["slope_mode"], z=zt)
+            return sg.ZonePlan(*zones, precision=prec, slope_mode=wl["slope_mode"], cross_mode=c)
+        return sg.Plan(wl["patches"], precision=prec, slope_mode=wl["slope_mode"], z=zt, cross_mode=c)
 
     plan = make_plan("fp32")
     # launch shapes of the plan's transform lengths picked by the library's autotuner
@@ -932,6 +936,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(wl["config"], parallelism="replicas" if world > 1 else "single",
+                       **({"cross": args.cross} if args.cross != "auto" else {}),
                        **({"quantity": "potential"} if pot else {})),
         "target_cells_per_s": value * wl["targets"],
         "latency_ms": {"p50": p50, "p99": p99},
@@ -1003,7 +1008,9 @@ def oracle_fft_route(wl, reps=3):
 # of the current kernel build (see profiles/); None when not captured for it.
 # amr3 col_conv: the stage's column-transform and column-MAC launches, one each
 # per solve (profiles/k_lv_col_fwd_amr3.md, k_lv_col_mac_inv_amr3.md).
-TRAFFIC = {("amr3", "col_conv"): (11.152e6 + 7.286e6) + (226.808e6 + 11.011e6)}
+TRAFFIC = {("spiral1024", "col_conv"): 33.822e6 + 0.018e6,
+           ("amr3", "col_conv"): (11.152e6 + 7.286e6) + (226.808e6 + 11.011e6),
+           ("amr3", "cross_direct"): 5.882e6 + 3.741e6}
 
 
 def _pad(n):
@@ -1192,6 +1199,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="run the graph-captured batch workload instead")
     ap.add_argument("--batch-size", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--cross", default="auto", choices=["auto", "direct", "levels"],
+                    help="how the FP32 plan sums pairs of cells in different patches (hierarchies)")
     ap.add_argument("--quantity", default="force", choices=["force", "potential"],
                     help="what a step computes (the potential: in-plane patch workloads)")
     ap.add_argument("--serve-requests", type=int, default=10000)
