@@ -229,6 +229,7 @@ def workload_ilr(n=512, levels=3, rule="ilr", disk="d2"):
 
 WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3, "offplane": workload_offplane,
              "ilr512": lambda: workload_ilr(512, 3, "ilr", "d2"), "ilr1024": lambda: workload_ilr(1024, 3, "ilr", "d2"),
+             "ilr2048": lambda: workload_ilr(2048, 3, "ilr", "d2"),
              "amr4_512": lambda: workload_nested(512, 4)}
 
 

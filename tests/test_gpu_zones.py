@@ -278,3 +278,30 @@ def test_band_hierarchy_central_slopes(sg, prec, tol, cross):
     err = rel_l2(fx[leaf], fy[leaf], rx[leaf], ry[leaf])
     print("rel L2 %s cross=%d central: %.3e (tolerance %.0e)" % (prec, cross, err, tol))
     assert err < tol
+
+
+def test_ilr2048_fp32_sampled(sg):
+    """AMR(3, D_2) ILR at N = 2048 (Table 8's largest hierarchy: 5,677,336
+    leaves, finest extent 8192 cells, beyond the level convolutions: the direct
+    path), FP32: 96 sampled leaves (32 per level) against the plain sum over
+    every leaf."""
+    import torch
+    hier = W.band_hierarchy(2048, 3, "ilr", "d2")
+    args = _hier_args(hier)
+    xc, yc, _ = W.zone_geometry(hier)
+    s, sx, sy = _d_sigma("d2", xc, yc)
+    leaf = hier["leaf"]
+    assert int(leaf.sum()) == 5677336
+    plan = sg.ZonePlan(*args, precision="fp32", slope_mode=sg.SG_SLOPES_CALLER)
+    assert plan.info["cross_mode"] == sg.SG_CROSS_DIRECT
+    fx, fy = plan.force_zones(to_dev(s, np.float32), to_dev(sx, np.float32), to_dev(sy, np.float32))
+    torch.cuda.synchronize()
+    fx, fy = fx.cpu().numpy().astype(np.float64), fy.cpu().numpy().astype(np.float64)
+    assert sg.sg_plan_check_error(plan.handle) == sg.SG_OK
+    plan.close()
+    rng = np.random.Generator(np.random.PCG64(2048))
+    t = np.concatenate([rng.choice(np.nonzero(leaf & (hier["level"] == l))[0], 32, replace=False) for l in range(3)])
+    rx, ry = _oracle(args, leaf, s, sx, sy, np.float32, targets=t)
+    err = rel_l2(fx[t], fy[t], rx, ry)
+    print("rel L2 fp32 ILR N=2048: %.3e" % err)
+    assert err < F32_TOL
