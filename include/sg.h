@@ -420,11 +420,16 @@ sg_status sg_autotune(int precision, int min_pad, int max_pad, int reps, double 
 
 /* ------------------------------------------------------------------------
  * Batches (not in the paper): n independent solves bound to their plans and
- * caller-owned device buffers at creation and captured once into a CUDA graph
- * with one branch per member (each with its own workspace), so uneven solves
- * overlap on the device and the whole batch costs one graph launch. The
- * buffers stay bound: refill them and launch again. Results are bit-for-bit
- * those of sg_force on the same inputs.
+ * caller-owned device buffers at creation and captured once into a CUDA graph,
+ * so the whole batch costs one graph launch. Members that are single in-plane
+ * patches with padded lengths up to 2048 (any mix of lengths and slope modes)
+ * run in ONE persistent kernel per precision: every pass of every such member
+ * is a work item taken from a counter, column items waiting (bounded) for
+ * their member's row items and inverse row items for its column items. Other
+ * members (hierarchies, off-plane plans, 4096-point transforms) run as graph
+ * branches beside it, each on its own workspace. The buffers stay bound:
+ * refill them and launch again. Results are bit-for-bit those of sg_force on
+ * the same inputs.
  * ------------------------------------------------------------------------ */
 typedef struct sg_batch sg_batch;
 
@@ -448,8 +453,8 @@ sg_status sg_batch_destroy(sg_batch *batch);
  * its kernels since the last check (see sg_plan_set_wait_limit), else SG_OK. */
 sg_status sg_batch_check_error(sg_batch *batch);
 
-/* Kernel launches one sg_batch_launch replays (members of one padded length
- * share each pass's launch). Errors: SG_EINVAL (NULL batch or out). */
+/* Kernel launches one sg_batch_launch replays (1 for a batch of single
+ * patches of one precision). Errors: SG_EINVAL (NULL batch or out). */
 sg_status sg_batch_launches(const sg_batch *batch, int *out);
 
 /* ------------------------------------------------------------------------

@@ -1,29 +1,26 @@
 // Batches of independent solves replayed as one CUDA graph.
 //
 // sg_batch_create binds n solves (plan + caller buffers each) and captures them
-// once: the capture forks one stream per member from a root stream, enqueues
-// the member's solve on its own workspace there, and joins all members back,
-// so the graph holds n independent branches that the GPU runs concurrently.
-// sg_batch_launch replays the whole batch with a single graph launch, which
-// removes the per-kernel launch overhead of uneven small solves.
-//
-// Members that are single in-plane patches with the same padded lengths,
-// precision and slope handling form a group: each pass of the group is one
-// launch over all its members (blockIdx.z = member, arguments from a device
-// array), so that small solves fill the GPU together instead of as many
-// concurrent small kernels. Other members keep their own branch.
+// once into a CUDA graph, so that sg_batch_launch replays the whole batch with
+// a single graph launch. Members that are single in-plane patches with padded
+// lengths up to 2048 run together in ONE persistent kernel per precision
+// (batch_run.cuh): every pass of every such member is a work item of that
+// launch, whatever their lengths and slope handling, ordered per member by
+// completion counters, so uneven small solves fill the GPU together and the
+// batch pays one kernel launch. Other members (hierarchies, off-plane plans,
+// 4096-point transforms) keep a graph branch of their own, running beside it.
+// Results are the members' sg_force results bit for bit.
 #include "common.cuh"
-#include "fftconv.cuh"
+#include "batch_run.cuh"
 
-#include <map>
+#include <algorithm>
 #include <new>
-#include <tuple>
 #include <vector>
 
 struct sg_batch {
     int n = 0;
     std::vector<sg_workspace> ws;
-    std::vector<void *> dev_args;  // per-group argument arrays
+    std::vector<void *> dev_args;  // item lists, member arguments and counters of the persistent launches
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
@@ -43,69 +40,86 @@ void batch_free(sg_batch *b)
     delete b;
 }
 
-bool groupable(const sg_plan *p)
+// a member of the persistent launch: one unmasked in-plane patch, lengths <= 2048
+bool persistent_member(const sg_plan *p)
 {
-    return p->npatches == 1 && !p->composite && !p->lv && p->geom.z == 0.0;
+    return p->npatches == 1 && !p->composite && !p->lv && p->geom.z == 0.0 &&
+           sgk::batch_run_smem(p->prec == SG_FP64, p->pp[0].d.px, p->pp[0].d.py) > 0;
 }
 
-// A group's passes: the members' arguments in one device array per pass.
+// The persistent launch of the members `mem` (one precision): item list,
+// member arguments and counters uploaded (owned by the batch), before capture.
 template <typename T>
-struct group_passes {
-    sgk::uniform_passes<T> u;  // lengths, shapes and twiddles are common to the group
-    const sgk::row_fwd_args<T> *rf = nullptr;
-    const sgk::edge_args<T> *ed = nullptr;
-    const sgk::col_args<T> *col = nullptr;
-    const sgk::row_inv_args<T> *ri = nullptr;
-    sgk::batch_shape bs = {0, 0};
+struct persistent_run {
+    const sgk::batch_item *items = nullptr;
+    const sgk::batch_member<T> *members = nullptr;
+    int *ctl = nullptr;
+    int nitems = 0, nmem = 0, smem = 0, tries = 0;
     int *err = nullptr;
 };
 
-// Upload the argument arrays of a group (owned by the batch); before capture.
 template <typename T>
-sg_status group_upload(sg_batch *b, const std::vector<sgk::uniform_passes<T>> &us, int *err, group_passes<T> &g)
+sg_status persistent_upload(sg_batch *b, const std::vector<int> &mem, sg_plan *const *plans,
+                            const void *const *sigma, const void *const *deltax, const void *const *deltay,
+                            void *const *fx, void *const *fy, persistent_run<T> &run)
 {
-    const int m = (int)us.size();
-    std::vector<sgk::row_fwd_args<T>> rf(m);
-    std::vector<sgk::edge_args<T>> ed(m);
-    std::vector<sgk::col_args<T>> col(m);
-    std::vector<sgk::row_inv_args<T>> ri(m);
-    int maxny = 0;
-    for (int i = 0; i < m; ++i) {
-        rf[i] = us[i].rf;
-        ed[i] = us[i].ed;
-        col[i] = us[i].col;
-        ri[i] = us[i].ri;
-        if (us[i].rf.src.ny > maxny) maxny = us[i].rf.src.ny;
+    using namespace sgk;
+    const int m = (int)mem.size();
+    std::vector<batch_member<T>> ms(m);
+    std::vector<batch_item> fwd, col, inv;
+    run.smem = 0;
+    run.tries = SG_MBAR_MAX_TRIES;
+    for (int k = 0; k < m; ++k) {
+        const int i = mem[k];
+        sg_plan *p = plans[i];
+        const bool caller = p->geom.slope_mode == SG_SLOPES_CALLER;
+        const uniform_passes<T> u = uniform_setup<T>(p, &b->ws[i], 0, sigma[i], caller ? deltax[i] : nullptr,
+                                                      caller ? deltay[i] : nullptr, fx[i], fy[i], nullptr);
+        batch_member<T> &bm = ms[k];
+        bm.rf = u.rf;
+        bm.ed = u.ed;
+        bm.col = u.col;
+        bm.ri = u.ri;
+        bm.twx = u.twx;
+        bm.twy = u.twy;
+        bm.px = u.px;
+        bm.py = u.py;
+        bm.qx = u.qx;
+        bm.nf_cols = u.nf_cols;
+        bm.central = u.central ? 1 : 0;
+        const int ny = p->pp[0].d.ny;
+        const int groups = (ny + 2 * batch_nb(u.px) - 1) / (2 * batch_nb(u.px));
+        for (int f = 0; f < u.nf_rows; ++f)
+            for (int bx = 0; bx < groups; ++bx) fwd.push_back({BI_ROWF, k, bx, f});
+        if (u.central) fwd.push_back({BI_EDGE, k, 0, 0});
+        bm.need_fwd = u.nf_rows * groups + (u.central ? 1 : 0);
+        const int cgroups = (u.qx + batch_cb(u.py) - 1) / batch_cb(u.py);
+        for (int bx = 0; bx < cgroups; ++bx) col.push_back({BI_COL, k, bx, 0});
+        bm.need_col = cgroups;
+        for (int o = 0; o < 2; ++o)
+            for (int bx = 0; bx < groups; ++bx) inv.push_back({BI_ROWI, k, bx, o});
+        run.smem = std::max(run.smem, batch_run_smem(p->prec == SG_FP64, u.px, u.py));
+        run.tries = std::min(run.tries, p->wait_tries);
     }
-    const size_t s0 = m * sizeof(rf[0]), s1 = m * sizeof(ed[0]), s2 = m * sizeof(col[0]), s3 = m * sizeof(ri[0]);
-    auto up = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    std::vector<batch_item> items;
+    items.reserve(fwd.size() + col.size() + inv.size());
+    items.insert(items.end(), fwd.begin(), fwd.end());
+    items.insert(items.end(), col.begin(), col.end());
+    items.insert(items.end(), inv.begin(), inv.end());
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t si = items.size() * sizeof(batch_item), sm = ms.size() * sizeof(batch_member<T>);
+    const size_t sc = (1 + 2 * (size_t)m) * sizeof(int);
     char *d = nullptr;
-    SG_CUDA_TRY(cudaMalloc(&d, up(s0) + up(s1) + up(s2) + up(s3)));
+    SG_CUDA_TRY(cudaMalloc(&d, up(si) + up(sm) + up(sc)));
     b->dev_args.push_back(d);
-    SG_CUDA_TRY(cudaMemcpy(d, rf.data(), s0, cudaMemcpyHostToDevice));
-    SG_CUDA_TRY(cudaMemcpy(d + up(s0), ed.data(), s1, cudaMemcpyHostToDevice));
-    SG_CUDA_TRY(cudaMemcpy(d + up(s0) + up(s1), col.data(), s2, cudaMemcpyHostToDevice));
-    SG_CUDA_TRY(cudaMemcpy(d + up(s0) + up(s1) + up(s2), ri.data(), s3, cudaMemcpyHostToDevice));
-    g.u = us[0];
-    g.rf = (const sgk::row_fwd_args<T> *)d;
-    g.ed = (const sgk::edge_args<T> *)(d + up(s0));
-    g.col = (const sgk::col_args<T> *)(d + up(s0) + up(s1));
-    g.ri = (const sgk::row_inv_args<T> *)(d + up(s0) + up(s1) + up(s2));
-    g.bs = {m, maxny};
-    g.err = err;
-    return SG_OK;
-}
-
-// One launch per pass for all the group's members.
-template <typename T>
-sg_status group_enqueue(const group_passes<T> &g, cudaStream_t st)
-{
-    const sgk::uniform_passes<T> &u = g.u;
-    SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, g.rf, g.bs));
-    if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st, g.ed, g.bs));
-    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, g.err, st, g.col, g.bs));
-    else SG_TRY(sgk::cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, g.err, st, g.col, g.bs));
-    SG_TRY(sgk::rows_inv<T>(u.px, u.shx[1], u.ri, u.nout, u.twx, st, g.ri, g.bs));
+    SG_CUDA_TRY(cudaMemcpy(d, items.data(), si, cudaMemcpyHostToDevice));
+    SG_CUDA_TRY(cudaMemcpy(d + up(si), ms.data(), sm, cudaMemcpyHostToDevice));
+    run.items = (const batch_item *)d;
+    run.members = (const batch_member<T> *)(d + up(si));
+    run.ctl = (int *)(d + up(si) + up(sm));
+    run.nitems = (int)items.size();
+    run.nmem = m;
+    run.err = b->ws[mem[0]].err;
     return SG_OK;
 }
 
@@ -117,8 +131,9 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
                           const void *const *deltay, void *const *fx, void *const *fy, sg_batch **out)
 {
     if (n < 1 || !plans || !sigma || !fx || !fy || !out) return SG_EINVAL;
-    int dev = 0;
+    int dev = 0, nsm = 0;
     SG_CUDA_TRY(cudaGetDevice(&dev));
+    SG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     for (int i = 0; i < n; ++i) {
         if (!plans[i] || !sigma[i] || !fx[i] || !fy[i] || plans[i]->device != dev) return SG_EINVAL;
         if (plans[i]->geom.slope_mode == SG_SLOPES_CALLER && (!deltax || !deltay || !deltax[i] || !deltay[i]))
@@ -137,92 +152,78 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
             return a;
         }
     }
-    // capture: root stream -> one branch per member -> join
-    std::vector<cudaStream_t> streams(n + 1, nullptr);
-    std::vector<cudaEvent_t> events(n + 1, nullptr);
+    // members of the persistent launches (per precision) and the rest
+    std::vector<int> mem32, mem64, rest;
+    for (int i = 0; i < n; ++i) {
+        if (!persistent_member(plans[i])) rest.push_back(i);
+        else if (plans[i]->prec == SG_FP64) mem64.push_back(i);
+        else mem32.push_back(i);
+    }
+    sg_status st = SG_OK;
+    persistent_run<float> r32;
+    persistent_run<double> r64;
+    if (!mem32.empty()) st = persistent_upload<float>(b, mem32, plans, sigma, deltax, deltay, fx, fy, r32);
+    if (st == SG_OK && !mem64.empty()) st = persistent_upload<double>(b, mem64, plans, sigma, deltax, deltay, fx, fy, r64);
+    // capture: root stream -> one branch per persistent launch and per other member -> join
+    const int nb = (int)rest.size() + 2;
+    std::vector<cudaStream_t> streams(nb + 1, nullptr);
+    std::vector<cudaEvent_t> events(nb + 1, nullptr);
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i <= n && e == cudaSuccess; ++i) {
+    for (int i = 0; i <= nb && e == cudaSuccess && st == SG_OK; ++i) {
         e = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&events[i], cudaEventDisableTiming);
     }
-    sg_status st = e == cudaSuccess ? SG_OK : SG_ECUDA;
-    // groups of single in-plane patches: (precision, Px, Py, central slopes, fields) -> members
-    std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
-    for (int i = 0; i < n; ++i) {
-        const sg_plan *p = plans[i];
-        if (!groupable(p)) continue;
-        const bool caller = p->geom.slope_mode == SG_SLOPES_CALLER;
-        const bool central = p->geom.slope_mode == SG_SLOPES_CENTRAL && p->pp[0].phase;
-        groups[std::make_tuple((int)p->prec, p->pp[0].d.px, p->pp[0].d.py, central ? 1 : 0,
-                               caller ? 3 : (p->geom.slope_mode == SG_SLOPES_NONE ? 1 : 3))]
-            .push_back(i);
-    }
-    std::vector<char> grouped(n, 0);
-    std::vector<group_passes<float>> g32;
-    std::vector<group_passes<double>> g64;
-    auto dxp = [&](int i) { return deltax ? deltax[i] : nullptr; };
-    auto dyp = [&](int i) { return deltay ? deltay[i] : nullptr; };
-    for (auto &g : groups) {
-        const std::vector<int> &mem = g.second;
-        if (mem.size() < 2 || st != SG_OK) continue;
-        const int i0 = mem[0];
-        if (plans[i0]->prec == SG_FP64) {
-            std::vector<sgk::uniform_passes<double>> us;
-            for (int i : mem)
-                us.push_back(sgk::uniform_setup<double>(plans[i], &b->ws[i], 0, sigma[i], dxp(i), dyp(i), fx[i], fy[i],
-                                                        nullptr));
-            g64.emplace_back();
-            st = group_upload<double>(b, us, b->ws[i0].err, g64.back());
-        } else {
-            std::vector<sgk::uniform_passes<float>> us;
-            for (int i : mem)
-                us.push_back(sgk::uniform_setup<float>(plans[i], &b->ws[i], 0, sigma[i], dxp(i), dyp(i), fx[i], fy[i],
-                                                       nullptr));
-            g32.emplace_back();
-            st = group_upload<float>(b, us, b->ws[i0].err, g32.back());
-        }
-        for (int i : mem) grouped[i] = 1;
-    }
+    if (e != cudaSuccess) st = SG_ECUDA;
     bool capturing = false;
     if (st == SG_OK) {
-        e = cudaStreamBeginCapture(streams[n], cudaStreamCaptureModeRelaxed);
+        e = cudaStreamBeginCapture(streams[nb], cudaStreamCaptureModeRelaxed);
         capturing = e == cudaSuccess;
-        if (e == cudaSuccess) e = cudaEventRecord(events[n], streams[n]);
+        if (e == cudaSuccess) e = cudaEventRecord(events[nb], streams[nb]);
         if (e != cudaSuccess) st = SG_ECUDA;
     }
-    int branch = 0;  // streams[0 .. n) serve groups and single members alike
-    auto fork = [&](cudaStream_t bs) { return cudaStreamWaitEvent(bs, events[n], 0) == cudaSuccess ? SG_OK : SG_ECUDA; };
+    int branch = 0;
+    auto fork = [&](cudaStream_t bs) { return cudaStreamWaitEvent(bs, events[nb], 0) == cudaSuccess ? SG_OK : SG_ECUDA; };
     auto join = [&](cudaStream_t bs) {
         return cudaEventRecord(events[branch], bs) == cudaSuccess &&
-                       cudaStreamWaitEvent(streams[n], events[branch], 0) == cudaSuccess
+                       cudaStreamWaitEvent(streams[nb], events[branch], 0) == cudaSuccess
                    ? SG_OK
                    : SG_ECUDA;
     };
-    for (size_t k = 0; k < g32.size() && st == SG_OK; ++k, ++branch) {
-        st = fork(streams[branch]);
-        if (st == SG_OK) st = group_enqueue<float>(g32[k], streams[branch]);
-        if (st == SG_OK) st = join(streams[branch]);
-        b->launches += g32[k].u.central ? 4 : 3;
-    }
-    for (size_t k = 0; k < g64.size() && st == SG_OK; ++k, ++branch) {
-        st = fork(streams[branch]);
-        if (st == SG_OK) st = group_enqueue<double>(g64[k], streams[branch]);
-        if (st == SG_OK) st = join(streams[branch]);
-        b->launches += g64[k].u.central ? 4 : 3;
-    }
-    for (int i = 0; i < n && st == SG_OK; ++i) {
-        if (grouped[i]) continue;
+    if (st == SG_OK && !mem32.empty()) {
         cudaStream_t bs = streams[branch];
         st = fork(bs);
         if (st == SG_OK)
-            st = sg_force_ws(plans[i], &b->ws[i], sigma[i], dxp(i), dyp(i), fx[i], fy[i], bs);
+            st = sgk::batch_run_launch<float>(r32.items, r32.nitems, r32.members, r32.nmem, r32.ctl, r32.err,
+                                              r32.tries, r32.smem, nsm, bs);
+        if (st == SG_OK) st = join(bs);
+        b->launches += 1;
+        ++branch;
+    }
+    if (st == SG_OK && !mem64.empty()) {
+        cudaStream_t bs = streams[branch];
+        st = fork(bs);
+        if (st == SG_OK)
+            st = sgk::batch_run_launch<double>(r64.items, r64.nitems, r64.members, r64.nmem, r64.ctl, r64.err,
+                                               r64.tries, r64.smem, nsm, bs);
+        if (st == SG_OK) st = join(bs);
+        b->launches += 1;
+        ++branch;
+    }
+    for (size_t k = 0; k < rest.size() && st == SG_OK; ++k) {
+        const int i = rest[k];
+        cudaStream_t bs = streams[branch];
+        st = fork(bs);
+        const bool caller = plans[i]->geom.slope_mode == SG_SLOPES_CALLER;
+        if (st == SG_OK)
+            st = sg_force_ws(plans[i], &b->ws[i], sigma[i], caller ? deltax[i] : nullptr,
+                             caller ? deltay[i] : nullptr, fx[i], fy[i], bs);
         if (st == SG_OK) st = join(bs);
         b->launches += plans[i]->launches;
         ++branch;
     }
     if (capturing) {
         cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(streams[n], &g);
+        e = cudaStreamEndCapture(streams[nb], &g);
         if (st == SG_OK && e == cudaSuccess) {
             b->graph = g;
             e = cudaGraphInstantiate(&b->exec, g, 0);
@@ -234,7 +235,7 @@ sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma
     }
     if (st != SG_OK && e != cudaSuccess) sg_set_last_cuda_error(e, "sg_batch_create");
     cudaGetLastError();
-    for (int i = 0; i <= n; ++i) {
+    for (int i = 0; i <= nb; ++i) {
         if (streams[i]) cudaStreamDestroy(streams[i]);
         if (events[i]) cudaEventDestroy(events[i]);
     }

@@ -119,23 +119,26 @@ __device__ __forceinline__ A pass_args(const A &one, const A *__restrict__ many)
 
 // ---------------------------------------------------------------- kernels --
 
-template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
-__global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const row_fwd_args<T> *__restrict__ many,
-                                                     const cplx_t<T> *__restrict__ tw)
+// Every pass is a device body run by one CTA on one tile of its work (row
+// group bx, field or output f, column group bx), called by the pass's kernel
+// with blockIdx and by the persistent batch kernel (batch_run.inl) with the
+// coordinates of a work item; both run the same arithmetic. Buffers that an
+// earlier pass wrote are read with __ldcg (through L2, not the non-coherent
+// path), so the body is also correct when that pass ran in the same launch.
+template <typename T, int PX, int NB, int THREADS>
+__device__ __forceinline__ void row_fwd_body(const row_fwd_args<T> &args, int bx, int f,
+                                             const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
-    sg_dep_trigger();
-    const row_fwd_args<T> args = pass_args<BATCH>(one, many);
     const field_src<T> &src = args.src;
     cplx_t<T> *__restrict__ work = args.work;
-    const int f = blockIdx.y;
-    const int j0 = blockIdx.x * RB;
+    const int j0 = bx * RB;
     const int ny = src.ny;
-    if (BATCH && j0 >= ny) return;
+    if (j0 >= ny) return;
     sg_dep_wait();
 
     // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
@@ -178,6 +181,15 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const 
     }
 }
 
+template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const row_fwd_args<T> *__restrict__ many,
+                                                     const cplx_t<T> *__restrict__ tw)
+{
+    sg_dep_trigger();
+    const row_fwd_args<T> args = pass_args<BATCH>(one, many);
+    row_fwd_body<T, PX, NB, THREADS>(args, blockIdx.x, blockIdx.y, tw);
+}
+
 // Shared-memory layout of the column kernels: the padded FFT buffer, then the
 // kernel spectra of the CTA's columns, [planes][CB][sg_spec_stride(PY)] of T,
 // which one thread fetches with one 1-D bulk copy (TMA) per plane at kernel
@@ -196,6 +208,7 @@ __device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int ncol = qx - kx0 < CB ? qx - kx0 : CB;
     const int64_t qplane = (int64_t)qx * QS;
+    fence_proxy_async_smem();  // shared memory an earlier body in the same CTA used
     mbar_arrive_expect_tx(bar, (uint32_t)(ncol * NPL * QS * sizeof(T)));
     // the CTA's columns are consecutive rows of every plane: one copy per plane
     for (int p = 0; p < NPL; ++p)
@@ -236,13 +249,11 @@ constexpr int col_min_blocks()
     return d * def_threads / THREADS >= 1 ? d * def_threads / THREADS : 1;
 }
 
-template <typename T, int PY, int CB, int THREADS, int NOUT, bool BATCH = false>
-__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>())) k_col_conv(col_args<T> one, const col_args<T> *__restrict__ many,
-                                                      int qx, int nf, const cplx_t<T> *__restrict__ tw, int *err)
+template <typename T, int PY, int CB, int THREADS, int NOUT>
+__device__ __forceinline__ void col_body(const col_args<T> &args, int bx, int qx, int nf,
+                                         const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
-    sg_dep_trigger();
-    const col_args<T> args = pass_args<BATCH>(one, many);
     const cplx_t<T> *__restrict__ work_fwd = args.wf;
     cplx_t<T> *__restrict__ work_inv = args.wi;
     const T *__restrict__ spec = args.spec;
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
     static_assert(CB * PY / THREADS == 8, "eight elements per thread");
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     constexpr int STEP = PY / 8;
-    const int kx0 = blockIdx.x * CB;
+    const int kx0 = bx * CB;
     // this thread's column and the rows it holds: jt + m PY/8, m = 0..7
     const int c = threadIdx.x / STEP, jt = threadIdx.x % STEP;
     const int kx = kx0 + c;
@@ -277,11 +288,15 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int j = jt + m * STEP;
-            v[m] = (m < 4 && j < ny && kx < qx) ? work_fwd[((int64_t)f * qx + kx) * ny + j] : cmake<C>((T)0, (T)0);
+            v[m] = (m < 4 && j < ny && kx < qx) ? __ldcg(&work_fwd[((int64_t)f * qx + kx) * ny + j])
+                                                : cmake<C>((T)0, (T)0);
         }
         if (COL_NBUF == 1 && f > 0) __syncthreads();
         fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
-        if (f == 0 && !spectra_ready(&bar, err, args.tries)) return;
+        if (f == 0) {
+            if (!spectra_ready(&bar, err, args.tries)) return;
+            if (threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int ky = jt + q * STEP;
@@ -355,23 +370,29 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
     }
 }
 
-template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
-__global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const row_inv_args<T> *__restrict__ many,
-                                                     const cplx_t<T> *__restrict__ tw)
+template <typename T, int PY, int CB, int THREADS, int NOUT, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>())) k_col_conv(col_args<T> one, const col_args<T> *__restrict__ many,
+                                                      int qx, int nf, const cplx_t<T> *__restrict__ tw, int *err)
+{
+    sg_dep_trigger();
+    const col_args<T> args = pass_args<BATCH>(one, many);
+    col_body<T, PY, CB, THREADS, NOUT>(args, blockIdx.x, qx, nf, tw, err);
+}
+
+template <typename T, int PX, int NB, int THREADS>
+__device__ __forceinline__ void row_inv_body(const row_inv_args<T> &args, int bx, int o,
+                                             const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf = reinterpret_cast<C *>(smem_raw);
     constexpr int RB = 2 * NB;
     constexpr int QX = PX / 2 + 1;
-    sg_dep_trigger();
-    const row_inv_args<T> args = pass_args<BATCH>(one, many);
     const cplx_t<T> *__restrict__ work_inv = args.wi;
     T *fx = args.fx, *fy = args.fy, *fz = args.fz;
     const int nx = args.nx, ny = args.ny;
-    const int o = blockIdx.y;
-    const int j0 = blockIdx.x * RB;
-    if (BATCH && j0 >= ny) return;
+    const int j0 = bx * RB;
+    if (j0 >= ny) return;
     sg_dep_wait();
     const C *w = work_inv + (int64_t)o * QX * ny;
     T *out = o == 0 ? fx : (o == 1 ? fy : fz);
@@ -383,8 +404,8 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const 
 #pragma unroll
         for (int u = 0; u < LOAD_UNROLL; ++u) {
             const int e = e0 + u * THREADS, s = e % NB, k = e / NB, ja = j0 + 2 * s;
-            av[u] = (e < NE && ja < ny) ? w[(int64_t)k * ny + ja] : cmake<C>((T)0, (T)0);
-            bv[u] = (e < NE && ja + 1 < ny) ? w[(int64_t)k * ny + ja + 1] : cmake<C>((T)0, (T)0);
+            av[u] = (e < NE && ja < ny) ? __ldcg(&w[(int64_t)k * ny + ja]) : cmake<C>((T)0, (T)0);
+            bv[u] = (e < NE && ja + 1 < ny) ? __ldcg(&w[(int64_t)k * ny + ja + 1]) : cmake<C>((T)0, (T)0);
         }
 #pragma unroll
         for (int u = 0; u < LOAD_UNROLL; ++u) {
@@ -411,18 +432,21 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const 
     }
 }
 
+template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const row_inv_args<T> *__restrict__ many,
+                                                     const cplx_t<T> *__restrict__ tw)
+{
+    sg_dep_trigger();
+    const row_inv_args<T> args = pass_args<BATCH>(one, many);
+    row_inv_body<T, PX, NB, THREADS>(args, blockIdx.x, blockIdx.y, tw);
+}
+
 // y-transforms of sigma's first and last columns, packed as z = c0 + i c1:
 // edge[k] = C0(k), edge[PY + k] = C1(k), k < PY.
-template <typename T, int PY, int THREADS, bool BATCH = false>
-__global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const edge_args<T> *__restrict__ many,
-                                                       const cplx_t<T> *__restrict__ tw)
+template <typename T, int PY, int THREADS>
+__device__ __forceinline__ void edge_body(const edge_args<T> &args, const cplx_t<T> *__restrict__ tw)
 {
     using C = cplx_t<T>;
-    // launched after the row pass, beside it: sigma is the caller's (ready
-    // before the row pass started); the wait at the end makes this kernel's
-    // completion imply the row pass's, for the column pass after it
-    sg_dep_trigger();
-    const edge_args<T> args = pass_args<BATCH>(one, many);
     const T *__restrict__ sigma = args.sigma;
     const int nx = args.nx, ny = args.ny;
     cplx_t<T> *__restrict__ edge = args.edge;
@@ -445,15 +469,25 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const e
     sg_dep_wait();
 }
 
+template <typename T, int PY, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const edge_args<T> *__restrict__ many,
+                                                       const cplx_t<T> *__restrict__ tw)
+{
+    // launched after the row pass, beside it: sigma is the caller's (ready
+    // before the row pass started); the wait at the end of the body makes this
+    // kernel's completion imply the row pass's, for the column pass after it
+    sg_dep_trigger();
+    const edge_args<T> args = pass_args<BATCH>(one, many);
+    edge_body<T, PY, THREADS>(args, tw);
+}
+
 // Column pass for central slopes: one forward transform (sigma), the slope
 // spectra formed per bin (see the header comment), two inverse transforms.
-template <typename T, int PY, int CB, int THREADS, bool BATCH = false>
-__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv_central(
-    col_args<T> one, const col_args<T> *__restrict__ many, int qx, const cplx_t<T> *__restrict__ tw, int *err)
+template <typename T, int PY, int CB, int THREADS>
+__device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx, int qx,
+                                                 const cplx_t<T> *__restrict__ tw, int *err)
 {
     using C = cplx_t<T>;
-    sg_dep_trigger();
-    const col_args<T> args = pass_args<BATCH>(one, many);
     const cplx_t<T> *__restrict__ work_fwd = args.wf;
     cplx_t<T> *__restrict__ work_inv = args.wi;
     const T *__restrict__ spec = args.spec;
@@ -468,7 +502,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     static_assert(CB * PY / THREADS == 8, "eight elements per thread");
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     constexpr int STEP = PY / 8;
-    const int kx0 = blockIdx.x * CB;
+    const int kx0 = bx * CB;
     const int c = threadIdx.x / STEP, jt = threadIdx.x % STEP;
     const int kx = kx0 + c;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -483,7 +517,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int j = jt + m * STEP;
-        v[m] = (m < 4 && j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+        v[m] = (m < 4 && j < ny && kx < qx) ? __ldcg(&work_fwd[(int64_t)kx * ny + j]) : cmake<C>((T)0, (T)0);
     }
     // the column's first and last rows (read after the transform's barriers)
     if (jt == 0) rows[c][0] = v[0];
@@ -493,6 +527,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     int par = 0;
     fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
     if (!spectra_ready(&bar, err, args.tries)) return;
+    if (threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait
 
     C accx[8], accy[8];
 #pragma unroll
@@ -511,7 +546,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
         const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
         const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
         const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
-        const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
+        const C c0 = __ldcg(&edge[ky]), c1 = __ldcg(&edge[PY + ky]);
         // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
         const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
         const C q2 = cmul_rn(f2, rows[c][1]), q1 = cmul_rn(f1, rows[c][0]);
@@ -544,6 +579,15 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     }
 }
 
+
+template <typename T, int PY, int CB, int THREADS, bool BATCH = false>
+__global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv_central(
+    col_args<T> one, const col_args<T> *__restrict__ many, int qx, const cplx_t<T> *__restrict__ tw, int *err)
+{
+    sg_dep_trigger();
+    const col_args<T> args = pass_args<BATCH>(one, many);
+    col_central_body<T, PY, CB, THREADS>(args, blockIdx.x, qx, tw, err);
+}
 
 // ------------------------------------------------------------ launch shapes --
 
