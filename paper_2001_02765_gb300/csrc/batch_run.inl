@@ -54,17 +54,17 @@ __device__ __noinline__ void batch_edge(const edge_args<T> &a, const cplx_t<T> *
 template <typename T, int P>
 __device__ __noinline__ void batch_colc(const col_args<T> &a, int bx, int qx, const cplx_t<T> *tw, int *err)
 {
-    col_central_body<T, P, batch_cb(P), BATCH_THREADS>(a, bx, qx, tw, err);
+    col_central_body<T, P, batch_cb(P), BATCH_THREADS, true>(a, bx, qx, tw, err);
 }
 template <typename T, int P>
 __device__ __noinline__ void batch_col(const col_args<T> &a, int bx, int qx, int nf, const cplx_t<T> *tw, int *err)
 {
-    col_body<T, P, batch_cb(P), BATCH_THREADS, 2>(a, bx, qx, nf, tw, err);
+    col_body<T, P, batch_cb(P), BATCH_THREADS, 2, true>(a, bx, qx, nf, tw, err);
 }
 template <typename T, int P>
 __device__ __noinline__ void batch_rowi(const row_inv_args<T> &a, int bx, int o, const cplx_t<T> *tw)
 {
-    row_inv_body<T, P, batch_nb(P), BATCH_THREADS>(a, bx, o, tw);
+    row_inv_body<T, P, batch_nb(P), BATCH_THREADS, true>(a, bx, o, tw);
 }
 
 template <typename T, int P>

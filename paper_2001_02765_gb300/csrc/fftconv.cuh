@@ -122,9 +122,27 @@ __device__ __forceinline__ A pass_args(const A &one, const A *__restrict__ many)
 // Every pass is a device body run by one CTA on one tile of its work (row
 // group bx, field or output f, column group bx), called by the pass's kernel
 // with blockIdx and by the persistent batch kernel (batch_run.inl) with the
-// coordinates of a work item; both run the same arithmetic. Buffers that an
-// earlier pass wrote are read with __ldcg (through L2, not the non-coherent
-// path), so the body is also correct when that pass ran in the same launch.
+// coordinates of a work item; both run the same arithmetic (the central column
+// pass's kernel holds its own copy of that arithmetic; see there). With CO (the
+// persistent kernel) buffers that an earlier pass wrote are read with coherent
+// loads (__ldcg for data read once, __ldca for tables every CTA reads) rather
+// than through the non-coherent read-only path, since that pass ran in the same
+// launch (they are read only after its items completed, by SMs that had not
+// read them); the pass kernels keep plain loads of the spectra and the
+// read-only path for tables (CO = false; an __ldg of the spectra measured
+// slower in the column pass).
+template <bool CO, typename X>
+__device__ __forceinline__ X ld_plain(const X *p)
+{
+    if constexpr (CO) return __ldcg(p);
+    return *p;
+}
+template <bool CO, typename X>
+__device__ __forceinline__ X ld_table(const X *p)
+{
+    if constexpr (CO) return __ldca(p);
+    return __ldg(p);
+}
 template <typename T, int PX, int NB, int THREADS>
 __device__ __forceinline__ void row_fwd_body(const row_fwd_args<T> &args, int bx, int f,
                                              const cplx_t<T> *__restrict__ tw)
@@ -202,13 +220,13 @@ __host__ __device__ constexpr int col_buf_bytes() { return COL_NBUF * ((spad_siz
 template <typename T, int PY, int CB, int NPL = 6>
 __host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * NPL * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
 
-template <typename T, int PY, int CB, int NPL = 6>
+template <typename T, int PY, int CB, int NPL = 6, bool CO = false>
 __device__ __forceinline__ void fetch_spectra(T *ssp, const T *__restrict__ spec, int kx0, int qx, uint64_t *bar)
 {
     constexpr int QS = (PY / 2 + 1 + 3) & ~3;
     const int ncol = qx - kx0 < CB ? qx - kx0 : CB;
     const int64_t qplane = (int64_t)qx * QS;
-    fence_proxy_async_smem();  // shared memory an earlier body in the same CTA used
+    if constexpr (CO) fence_proxy_async_smem();  // shared memory an earlier body in the same CTA used
     mbar_arrive_expect_tx(bar, (uint32_t)(ncol * NPL * QS * sizeof(T)));
     // the CTA's columns are consecutive rows of every plane: one copy per plane
     for (int p = 0; p < NPL; ++p)
@@ -249,7 +267,7 @@ constexpr int col_min_blocks()
     return d * def_threads / THREADS >= 1 ? d * def_threads / THREADS : 1;
 }
 
-template <typename T, int PY, int CB, int THREADS, int NOUT>
+template <typename T, int PY, int CB, int THREADS, int NOUT, bool CO = false>
 __device__ __forceinline__ void col_body(const col_args<T> &args, int bx, int qx, int nf,
                                          const cplx_t<T> *__restrict__ tw, int *err)
 {
@@ -272,7 +290,7 @@ __device__ __forceinline__ void col_body(const col_args<T> &args, int bx, int qx
     constexpr int NPL = NOUT == 3 ? 9 : (NOUT == 1 ? 3 : 6);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL>(ssp, spec, kx0, qx, &bar);
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB, NPL, CO>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
 
     C accx[8], accy[8], accz[NOUT == 3 ? 8 : 1];
@@ -288,14 +306,14 @@ __device__ __forceinline__ void col_body(const col_args<T> &args, int bx, int qx
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int j = jt + m * STEP;
-            v[m] = (m < 4 && j < ny && kx < qx) ? __ldcg(&work_fwd[((int64_t)f * qx + kx) * ny + j])
+            v[m] = (m < 4 && j < ny && kx < qx) ? ld_plain<CO>(&work_fwd[((int64_t)f * qx + kx) * ny + j])
                                                 : cmake<C>((T)0, (T)0);
         }
         if (COL_NBUF == 1 && f > 0) __syncthreads();
         fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
         if (f == 0) {
             if (!spectra_ready(&bar, err, args.tries)) return;
-            if (threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait
+            if (CO && threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait; the body runs again
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -379,7 +397,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS, NOUT>
     col_body<T, PY, CB, THREADS, NOUT>(args, blockIdx.x, qx, nf, tw, err);
 }
 
-template <typename T, int PX, int NB, int THREADS>
+template <typename T, int PX, int NB, int THREADS, bool CO = false>
 __device__ __forceinline__ void row_inv_body(const row_inv_args<T> &args, int bx, int o,
                                              const cplx_t<T> *__restrict__ tw)
 {
@@ -404,8 +422,8 @@ __device__ __forceinline__ void row_inv_body(const row_inv_args<T> &args, int bx
 #pragma unroll
         for (int u = 0; u < LOAD_UNROLL; ++u) {
             const int e = e0 + u * THREADS, s = e % NB, k = e / NB, ja = j0 + 2 * s;
-            av[u] = (e < NE && ja < ny) ? __ldcg(&w[(int64_t)k * ny + ja]) : cmake<C>((T)0, (T)0);
-            bv[u] = (e < NE && ja + 1 < ny) ? __ldcg(&w[(int64_t)k * ny + ja + 1]) : cmake<C>((T)0, (T)0);
+            av[u] = (e < NE && ja < ny) ? ld_plain<CO>(&w[(int64_t)k * ny + ja]) : cmake<C>((T)0, (T)0);
+            bv[u] = (e < NE && ja + 1 < ny) ? ld_plain<CO>(&w[(int64_t)k * ny + ja + 1]) : cmake<C>((T)0, (T)0);
         }
 #pragma unroll
         for (int u = 0; u < LOAD_UNROLL; ++u) {
@@ -483,7 +501,7 @@ __global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const e
 
 // Column pass for central slopes: one forward transform (sigma), the slope
 // spectra formed per bin (see the header comment), two inverse transforms.
-template <typename T, int PY, int CB, int THREADS>
+template <typename T, int PY, int CB, int THREADS, bool CO = false>
 __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx, int qx,
                                                  const cplx_t<T> *__restrict__ tw, int *err)
 {
@@ -507,7 +525,7 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
     const int kx = kx0 + c;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB, 6, CO>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
     const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
     const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
@@ -517,7 +535,7 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int j = jt + m * STEP;
-        v[m] = (m < 4 && j < ny && kx < qx) ? __ldcg(&work_fwd[(int64_t)kx * ny + j]) : cmake<C>((T)0, (T)0);
+        v[m] = (m < 4 && j < ny && kx < qx) ? ld_plain<CO>(&work_fwd[(int64_t)kx * ny + j]) : cmake<C>((T)0, (T)0);
     }
     // the column's first and last rows (read after the transform's barriers)
     if (jt == 0) rows[c][0] = v[0];
@@ -527,7 +545,7 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
     int par = 0;
     fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
     if (!spectra_ready(&bar, err, args.tries)) return;
-    if (threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait
+    if (CO && threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait; the body runs again
 
     C accx[8], accy[8];
 #pragma unroll
@@ -546,7 +564,7 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
         const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
         const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
         const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
-        const C c0 = __ldcg(&edge[ky]), c1 = __ldcg(&edge[PY + ky]);
+        const C c0 = ld_table<CO>(&edge[ky]), c1 = ld_table<CO>(&edge[PY + ky]);
         // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
         const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
         const C q2 = cmul_rn(f2, rows[c][1]), q1 = cmul_rn(f1, rows[c][0]);
@@ -580,13 +598,106 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
 }
 
 
+// The pass kernel for one solve or a batch of launches keeps its own copy of
+// col_central_body's arithmetic, operation for operation: compiled through the
+// inlined body it ran 19% slower (32.8 against 27.6 us at 2048 x 2048, FP32;
+// same registers, more time waiting on global loads). The batch tests check that
+// the persistent kernel (which runs the body) and this kernel agree bit for bit.
 template <typename T, int PY, int CB, int THREADS, bool BATCH = false>
 __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k_col_conv_central(
     col_args<T> one, const col_args<T> *__restrict__ many, int qx, const cplx_t<T> *__restrict__ tw, int *err)
 {
+    using C = cplx_t<T>;
     sg_dep_trigger();
     const col_args<T> args = pass_args<BATCH>(one, many);
-    col_central_body<T, PY, CB, THREADS>(args, blockIdx.x, qx, tw, err);
+    const cplx_t<T> *__restrict__ work_fwd = args.wf;
+    cplx_t<T> *__restrict__ work_inv = args.wi;
+    const T *__restrict__ spec = args.spec;
+    const cplx_t<T> *__restrict__ edge = args.edge;
+    const T *__restrict__ phase = args.phase;
+    const int ny = args.ny;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *bufs = reinterpret_cast<C *>(smem_raw);
+    T *ssp = reinterpret_cast<T *>(smem_raw + col_buf_bytes<T, PY, CB>());
+    __shared__ uint64_t bar;
+    __shared__ C rows[CB][2];  // R0, R1 of each column
+    static_assert(CB * PY / THREADS == 8, "eight elements per thread");
+    constexpr int QS = (PY / 2 + 1 + 3) & ~3;
+    constexpr int STEP = PY / 8;
+    const int kx0 = blockIdx.x * CB;
+    const int c = threadIdx.x / STEP, jt = threadIdx.x % STEP;
+    const int kx = kx0 + c;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
+    sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
+    const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
+    const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
+
+    // the lower half of the column straight into registers (the upper half is zero)
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int j = jt + m * STEP;
+        v[m] = (m < 4 && j < ny && kx < qx) ? work_fwd[(int64_t)kx * ny + j] : cmake<C>((T)0, (T)0);
+    }
+    // the column's first and last rows (read after the transform's barriers)
+    if (jt == 0) rows[c][0] = v[0];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (jt + m * STEP == ny - 1) rows[c][1] = v[m];
+    int par = 0;
+    fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
+    if (!spectra_ready(&bar, err, args.tries)) return;
+
+    C accx[8], accy[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int ky = jt + q * STEP;
+        accx[q] = accy[q] = cmake<C>((T)0, (T)0);
+        if (kx >= qx) continue;
+        const bool lower = ky <= PY / 2;
+        const int kq = lower ? ky : PY - ky;
+        const T sg = lower ? (T)1 : (T)-1;
+        const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
+        const C S = v[q];
+        // slope spectra
+        const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
+        const C e1 = cmake<C>(__ldg(&ce1[2 * kx]), __ldg(&ce1[2 * kx + 1]));
+        const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
+        const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
+        const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
+        const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
+        // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
+        const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
+        const C q2 = cmul_rn(f2, rows[c][1]), q1 = cmul_rn(f1, rows[c][0]);
+        const C X = cmake<C>(add_rn(add_rn(-mul_rn(cs, S.y), p2.x), -p1.x), add_rn(add_rn(mul_rn(cs, S.x), p2.y), -p1.y));
+        const C Y = cmake<C>(add_rn(add_rn(-mul_rn(rs, S.y), q2.x), -q1.x), add_rn(add_rn(mul_rn(rs, S.x), q2.y), -q1.y));
+        const T a = sp[0 * CB * QS];
+        const T b = sp[1 * CB * QS];
+        const T cc = sg * sp[2 * CB * QS];
+        const T d = sg * sp[3 * CB * QS];
+        const T ee = sp[4 * CB * QS];
+        const T ff = sg * sp[5 * CB * QS];
+        accx[q] = cmake<C>(fma(cc, Y.x, fma(b, X.x, -mul_rn(a, S.y))), fma(cc, Y.y, fma(b, X.y, mul_rn(a, S.x))));
+        accy[q] = cmake<C>(fma(ff, X.x, fma(ee, Y.x, -mul_rn(d, S.y))), fma(ff, X.y, fma(ee, Y.y, mul_rn(d, S.x))));
+    }
+
+    // inverse transforms: the products are already in the transform's input pattern
+    if (COL_NBUF == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accx, bufs, par, tw);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = jt + m * STEP;
+        if (j < ny && kx < qx) work_inv[(int64_t)kx * ny + j] = accx[m];
+    }
+    if (COL_NBUF == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accy, bufs, par, tw);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = jt + m * STEP;
+        if (j < ny && kx < qx) work_inv[((int64_t)qx + kx) * ny + j] = accy[m];
+    }
 }
 
 // ------------------------------------------------------------ launch shapes --
