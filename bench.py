@@ -866,6 +866,7 @@ def run_gpu(args):
     hfy = torch.empty(nout, dtype=dt).pin_memory()
     sg.sg_plan_set_timing(plan.handle, False)
     e2e_ms, h2d, d2h = None, 0, 0
+    e2e_sync_ms, e2e_mode = None, "one synchronous call per step"
     if zones is not None:
         # zone plans: pinned host arrays copied in, the zone solve, forces copied back, all in the timed region
         e2e_ms = 0.0
@@ -917,6 +918,41 @@ def run_gpu(args):
         nbytes = nout * 4
         h2d = nbytes * (3 if wl["dx"] is not None else 1)
         d2h = 2 * nbytes
+        e2e_sync_ms = e2e_ms
+        # pipelined: two plans on two streams, each solve enqueued by
+        # sg_force_host_async and waited for one step later, so one solve's
+        # results stream back over the CPU-GPU link while the next one's inputs
+        # come in and transform; host buffers rotate over enough sets to exceed L2
+        if e2e_ms:
+            sets = max(4, -(-2 * (129 << 20) // (h2d + d2h)))
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32).ravel()).pin_memory()
+            rot = [(pin(wl["sigma"]), pin(wl["dx"]) if wl["dx"] is not None else None,
+                    pin(wl["dy"]) if wl["dy"] is not None else None,
+                    torch.empty(nout, dtype=dt).pin_memory(), torch.empty(nout, dtype=dt).pin_memory())
+                   for _ in range(sets)]
+            plan2 = make_plan("fp32")
+            sg.sg_plan_set_timing(plan2.handle, False)
+            pair = [(plan, stream), (plan2, torch.cuda.Stream())]
+
+            def pipelined(k_steps):
+                for k in range(k_steps):
+                    pl, st = pair[k % 2]
+                    if k >= 2:
+                        pl.wait(st)
+                    pl.force_host_async(*rot[k % sets], stream=st)
+                for pl, st in pair:
+                    pl.wait(st)
+
+            pipelined(4)
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pipelined(args.steps)
+            e2e_ms = 1e3 * (time.perf_counter() - t0)
+            e2e_mode = ("pipelined: sg_force_host_async on two plans and two streams, each solve waited for one "
+                        "step later; %d rotating pinned host buffer sets (%.0f MB, more than L2)"
+                        % (sets, sets * (h2d + d2h) / 2**20))
+            plan2.close()
 
     # roofline of the dominant kernel
     stage_mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
@@ -951,7 +987,9 @@ def run_gpu(args):
                      "hbm": {"algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
                              "frac": gbs / hbm_peak, "peak_source": hbm_src}},
         "e2e": ({"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                 "d2h_bytes_per_step": d2h} if e2e_ms else None),
+                 "d2h_bytes_per_step": d2h, "mode": e2e_mode,
+                 **({"sync_value": args.steps * world / (e2e_sync_ms / 1e3)}
+                    if e2e_sync_ms and e2e_sync_ms != e2e_ms else {})} if e2e_ms else None),
         "gpu_launches": args.steps * info["launches"],
         "autotune": tuned,
         "clocks": clk.summary(),

@@ -244,6 +244,28 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
                         void *fx, void *fy, void *stream);
 
 /*
+ * A host-buffer solve in two halves (not in the paper: a host-side interface).
+ * sg_force_host_async enqueues on `stream` the copies of the inputs into the
+ * plan's device staging buffers, the solve, the copies of Fx, Fy back (all
+ * transfers on the copy engines, even for pinned buffers, so that the SMs stay
+ * free for other solves) and a copy of the workspace's error word into a
+ * pinned word of the plan, and returns without waiting; the host buffers must
+ * stay valid and untouched until sg_plan_wait(plan, stream) returns, which
+ * waits for `stream` and then reports that error word (SG_ETIMEOUT if a
+ * kernel's bounded wait ran out, clearing it; else SG_OK). Solves on two plans
+ * (each with its own workspace and staging) and two streams overlap one
+ * solve's transfers over the CPU-GPU link with the other's transforms. For
+ * pinned buffers the copies are asynchronous; pageable ones are copied
+ * synchronously. sg_force_host (in-place transfers for a single in-plane patch,
+ * the lower latency of one solve) also reads the error word this way.
+ * Errors: as sg_force_host (sg_force_host_async); SG_EINVAL for a null plan,
+ * SG_ECUDA, SG_ETIMEOUT (sg_plan_wait).
+ */
+sg_status sg_force_host_async(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
+                              void *fx, void *fy, void *stream);
+sg_status sg_plan_wait(sg_plan *plan, void *stream);
+
+/*
  * Bounded waits (not in the paper). Kernels that wait for bulk copies into
  * shared memory (the column passes' kernel spectra, the FP32 direct sum's
  * source tiles) give up after a number of attempts, record the failure in the

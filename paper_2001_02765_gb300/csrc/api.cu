@@ -618,6 +618,7 @@ void plan_free(sg_plan *plan)
     cudaFree(plan->patch_dev);
     cudaFree(plan->stage_in);
     cudaFree(plan->stage_out);
+    cudaFreeHost(plan->err_host);
     delete[] plan->pp;
     delete[] plan->patches_host;
     delete plan;
@@ -1125,8 +1126,14 @@ static const void *mapped_host(const void *p)
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
-                        void *stream)
+// The host-buffer solve enqueued on `stream`. mapped_io: pinned buffers of a
+// single in-plane patch are read and written in place by the transform passes
+// (the transfers overlap the solve's own passes: the lower latency of one
+// solve); otherwise every transfer is a copy-engine copy into or out of the
+// plan's staging buffers, leaving the SMs to the other solves in flight (the
+// higher throughput when solves on several streams overlap).
+static sg_status host_enqueue(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
+                              void *fy, void *stream, bool mapped_io)
 {
     if (!plan || !sigma || !fx || !fy) return fail("null plan or field pointer");
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
@@ -1139,7 +1146,7 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
     // single in-plane patch the inverse row pass writes Fx, Fy there in place
     // (streaming writes over the CPU-GPU link) instead of a copy after the solve.
     void *hfx = nullptr, *hfy = nullptr;
-    if (!plan->composite && plan->geom.z == 0.0) {
+    if (mapped_io && !plan->composite && plan->geom.z == 0.0) {
         hfx = (void *)mapped_host(fx);
         hfy = (void *)mapped_host(fy);
         if (!hfx || !hfy) hfx = hfy = nullptr;
@@ -1181,8 +1188,38 @@ sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, co
         SG_CUDA_TRY(cudaMemcpyAsync(fx, out, bytes, cudaMemcpyDeviceToHost, st));
         SG_CUDA_TRY(cudaMemcpyAsync(fy, out + bytes, bytes, cudaMemcpyDeviceToHost, st));
     }
-    SG_CUDA_TRY(cudaStreamSynchronize(st));
-    return check_device_error(plan);
+    // the error word follows the solve on the stream, so that the wait reads it
+    // without another round trip to the device
+    if (!plan->ws || !plan->ws->err) return SG_OK;
+    if (!plan->err_host) SG_CUDA_TRY(cudaHostAlloc((void **)&plan->err_host, sizeof(int), cudaHostAllocDefault));
+    SG_CUDA_TRY(cudaMemcpyAsync(plan->err_host, plan->ws->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return SG_OK;
+}
+
+sg_status sg_force_host_async(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
+                              void *fy, void *stream)
+{
+    return host_enqueue(plan, sigma, deltax, deltay, fx, fy, stream, false);
+}
+
+sg_status sg_plan_wait(sg_plan *plan, void *stream)
+{
+    if (!plan) return fail("null plan");
+    SG_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (plan->err_host && *(volatile int *)plan->err_host) {
+        *(volatile int *)plan->err_host = 0;
+        SG_CUDA_TRY(cudaMemset(plan->ws->err, 0, sizeof(int)));
+        sg_set_last_error_message("a bounded wait for a bulk copy ran out in a kernel");
+        return SG_ETIMEOUT;
+    }
+    return SG_OK;
+}
+
+sg_status sg_force_host(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx, void *fy,
+                        void *stream)
+{
+    SG_TRY(host_enqueue(plan, sigma, deltax, deltay, fx, fy, stream, true));
+    return sg_plan_wait(plan, stream);
 }
 
 sg_status sg_plan_set_wait_limit(sg_plan *plan, int tries)

@@ -274,6 +274,7 @@ struct sg_plan {
     // host staging for sg_force_host
     void *stage_in, *stage_out;
     size_t stage_bytes;
+    int *err_host;                  // pinned: the workspace's error word, copied after each host-buffer solve
 
     // per-stage device timers of the last sg_force (NULL when timing is off)
     struct sg_timing *timing;

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "sg_kernel_tables": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "sg_force": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_force_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_force_host_async": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_plan_wait": (ctypes.c_int, [_VP, _VP]),
     "sg_force3": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_potential": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -250,6 +252,17 @@ def sg_force_host(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=
     """Raw host pointers (ints); synchronous."""
     _check(load().sg_force_host(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr,
                                 stream_ptr or None), "sg_force_host")
+
+
+def sg_force_host_async(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr=0):
+    """Raw host pointers (ints); enqueues only: the buffers stay in use until sg_plan_wait."""
+    _check(load().sg_force_host_async(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, fx_ptr, fy_ptr,
+                                      stream_ptr or None), "sg_force_host_async")
+
+
+def sg_plan_wait(handle, stream_ptr=0):
+    """Wait for the stream, then report the plan's device error word (SG_ETIMEOUT raises)."""
+    _check(load().sg_plan_wait(handle, stream_ptr or None), "sg_plan_wait")
 
 
 STAGE_NAMES = ("row_fwd", "col_conv", "row_inv", "corner_weights", "cross_direct", "composite")
@@ -575,6 +588,17 @@ class Plan:
             st = stream.cuda_stream
         sg_force_host(self.handle, ps, pdx, pdy, pfx, pfy, st)
         return fx, fy
+
+    def force_host_async(self, sigma, dx, dy, fx, fy, stream=None):
+        """Enqueue a solve from pinned torch CPU tensors (sigma, dx, dy; None
+        where unused) into pinned fx, fy; the tensors stay in use until wait()."""
+        p = lambda a: 0 if a is None else a.data_ptr()
+        sg_force_host_async(self.handle, p(sigma), p(dx), p(dy), p(fx), p(fy),
+                            0 if stream is None else stream.cuda_stream)
+
+    def wait(self, stream=None):
+        """Wait for a solve enqueued by force_host_async on `stream`."""
+        sg_plan_wait(self.handle, 0 if stream is None else stream.cuda_stream)
 
     def split(self, flat):
         """Split a flat field array into per-patch [ny, nx] views."""

@@ -203,6 +203,38 @@ def test_host_entry_point_pinned_in_place(sg, mode, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_host_async_two_plans_pipelined(sg, prec):
+    """Solves enqueued by sg_force_host_async alternately on two plans and two
+    streams, each waited for one step later (the pipelined host loop), give
+    every input set's device-entry result bit for bit."""
+    import torch
+    ny, nx = 100, 84
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    plans = [sg.Plan([(0, nx, ny, 0.0, 0.0, 0.01)], precision=prec, slope_mode=sg.SG_SLOPES_CENTRAL)
+             for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    sets = 5
+    hs = [torch.from_numpy(np.ascontiguousarray(W.random_fields(ny, nx, seed=20 + k)[0], dt).ravel()).pin_memory()
+          for k in range(sets)]
+    outs = [(torch.empty(nx * ny, dtype=tdt).pin_memory(), torch.empty(nx * ny, dtype=tdt).pin_memory())
+            for _ in range(sets)]
+    for k in range(sets):
+        j = k % 2
+        if k >= 2:
+            plans[j].wait(streams[j])
+        plans[j].force_host_async(hs[k], None, None, outs[k][0], outs[k][1], stream=streams[j])
+    for j in range(2):
+        plans[j].wait(streams[j])
+    for k in range(sets):
+        dfx, dfy = plans[0].force(hs[k].cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(outs[k][0], dfx.cpu()) and torch.equal(outs[k][1], dfy.cpu())
+    for p in plans:
+        p.close()
+
+
 def test_repeatable_bitwise(sg):
     import torch
     ny, nx = 128, 128

@@ -52,6 +52,35 @@ def test_plan_wait_runs_out_and_recovers(sg):
     plan.close()
 
 
+def test_host_entry_reports_wait_run_out(sg):
+    """The host entry points read the error word copied after the solve: a
+    wait that ran out raises SG_ETIMEOUT from sg_force_host and from
+    sg_plan_wait, once, and the next solve is correct."""
+    import torch
+    n = 64
+    patches = [(0,) + W.unit_grid(n)]
+    sig, _, _ = W.bumps_on_patches(patches, seed=6)
+    plan = sg.Plan(patches, precision="fp32", slope_mode=sg.SG_SLOPES_CENTRAL)
+    hs = torch.from_numpy(np.ascontiguousarray(sig[0], np.float32).ravel()).pin_memory()
+    hfx = torch.empty(n * n, dtype=torch.float32).pin_memory()
+    hfy = torch.empty(n * n, dtype=torch.float32).pin_memory()
+    plan.force_host(hs, None, None, hfx, hfy)
+    ref = (hfx.clone(), hfy.clone())
+    sg.sg_plan_set_wait_limit(plan.handle, 0)
+    with pytest.raises(sg.SgError) as e:
+        plan.force_host(hs, None, None, hfx, hfy)
+    assert e.value.status == sg.SG_ETIMEOUT
+    plan.force_host_async(hs, None, None, hfx, hfy)
+    with pytest.raises(sg.SgError) as e:
+        plan.wait()
+    assert e.value.status == sg.SG_ETIMEOUT
+    sg.sg_plan_set_wait_limit(plan.handle, -1)
+    plan.force_host_async(hs, None, None, hfx, hfy)
+    plan.wait()
+    assert torch.equal(hfx, ref[0]) and torch.equal(hfy, ref[1])
+    plan.close()
+
+
 def test_direct_sum_wait_runs_out_and_recovers(sg):
     """The persistent far-field launch of an FP32 hierarchy on the direct path."""
     import torch
