@@ -285,6 +285,10 @@ def run_batch(args):
     batch = sg.sg_batch_create([p.handle for p in plans], [i.data_ptr() for i in ins], [0] * len(ins), [0] * len(ins),
                                [o[0].data_ptr() for o in outs], [o[1].data_ptr() for o in outs])
     batch_launches = sg.sg_batch_launches(batch)
+    mode, ms_p, ms_g = sg.sg_batch_layout(batch)
+    layout = {"chosen": "persistent" if mode == sg.SG_BATCH_PERSISTENT else "grouped",
+              "replay_ms_persistent": ms_p, "replay_ms_grouped": ms_g,
+              "note": "both layouts captured and replayed three times at creation; the faster is kept"}
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -365,6 +369,7 @@ def run_batch(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": batch_roofline(ns, total_ms / args.steps),
         "gpu_launches": args.steps * batch_launches,
+        "batch_layout": layout,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -444,25 +444,40 @@ sg_status sg_autotune(int precision, int min_pad, int max_pad, int reps, double 
  * Batches (not in the paper): n independent solves bound to their plans and
  * caller-owned device buffers at creation and captured once into a CUDA graph,
  * so the whole batch costs one graph launch. Members that are single in-plane
- * patches with padded lengths up to 2048 (any mix of lengths and slope modes)
- * run in ONE persistent kernel per precision: every pass of every such member
- * is a work item taken from a counter, column items waiting (bounded) for
- * their member's row items and inverse row items for its column items. Other
- * members (hierarchies, off-plane plans, 4096-point transforms) run as graph
- * branches beside it, each on its own workspace. The buffers stay bound:
+ * patches run in one of two layouts:
+ *   SG_BATCH_PERSISTENT  those with padded lengths up to 2048 (any mix of
+ *     lengths and slope modes) in ONE persistent kernel per precision: every
+ *     pass of every such member is a work item taken from a counter, column
+ *     items waiting (bounded) for their member's row items and inverse row
+ *     items for its column items;
+ *   SG_BATCH_GROUPED  members of one precision, padded lengths and slope
+ *     handling form a group; each pass of a group is one launch of that pass's
+ *     kernel over all its members; groups run as concurrent graph branches.
+ * SG_BATCH_AUTO (sg_batch_create) captures both and keeps the one that replays
+ * faster (a median of three replays each, run on the bound buffers during
+ * creation: their outputs are written then). Other members (hierarchies,
+ * off-plane plans, 4096-point transforms, a group of one) run as graph
+ * branches beside them, each on its own workspace. The buffers stay bound:
  * refill them and launch again. Results are bit-for-bit those of sg_force on
- * the same inputs.
+ * the same inputs, in either layout.
  * ------------------------------------------------------------------------ */
 typedef struct sg_batch sg_batch;
+
+typedef enum { SG_BATCH_AUTO = 0, SG_BATCH_PERSISTENT = 1, SG_BATCH_GROUPED = 2 } sg_batch_mode;
 
 /* plans, sigma, fx, fy: arrays of n entries; deltax, deltay: arrays of n
  * entries (entries used for SG_SLOPES_CALLER plans) or NULL. The buffers are
  * device memory, or page-locked host memory (mapped into the device address
  * space: read and written in place by the kernels). Capture runs on internal
- * streams; nothing executes until sg_batch_launch. Errors: SG_EINVAL,
- * SG_ENOMEM, SG_ECUDA. */
+ * streams; with SG_BATCH_AUTO the candidate layouts are replayed during
+ * creation (synchronously), otherwise nothing executes until sg_batch_launch.
+ * sg_batch_create is sg_batch_create_mode with SG_BATCH_AUTO. Errors:
+ * SG_EINVAL (also an unknown mode), SG_ENOMEM, SG_ECUDA. */
 sg_status sg_batch_create(int n, sg_plan *const *plans, const void *const *sigma, const void *const *deltax,
                           const void *const *deltay, void *const *fx, void *const *fy, sg_batch **out);
+sg_status sg_batch_create_mode(int n, sg_plan *const *plans, const void *const *sigma, const void *const *deltax,
+                               const void *const *deltay, void *const *fx, void *const *fy, int mode,
+                               sg_batch **out);
 
 /* Enqueue the whole batch on `stream` (one graph launch). */
 sg_status sg_batch_launch(sg_batch *batch, void *stream);
@@ -475,9 +490,14 @@ sg_status sg_batch_destroy(sg_batch *batch);
  * its kernels since the last check (see sg_plan_set_wait_limit), else SG_OK. */
 sg_status sg_batch_check_error(sg_batch *batch);
 
-/* Kernel launches one sg_batch_launch replays (1 for a batch of single
- * patches of one precision). Errors: SG_EINVAL (NULL batch or out). */
+/* Kernel launches one sg_batch_launch replays (1 for a persistent batch of
+ * single patches of one precision). Errors: SG_EINVAL (NULL batch or out). */
 sg_status sg_batch_launches(const sg_batch *batch, int *out);
+
+/* The layout the batch runs (SG_BATCH_PERSISTENT or SG_BATCH_GROUPED) and, for
+ * SG_BATCH_AUTO, the median replay times of both candidates in milliseconds
+ * (0 otherwise); ms_persistent, ms_grouped may be NULL. Errors: SG_EINVAL. */
+sg_status sg_batch_layout(const sg_batch *batch, int *mode, double *ms_persistent, double *ms_grouped);
 
 /* ------------------------------------------------------------------------
  * Request server (continuous batching on one GPU; not in the paper).

@@ -25,9 +25,10 @@ namespace sgk {
 enum { BI_ROWF = 0, BI_EDGE = 1, BI_COL = 2, BI_ROWI = 3 };
 
 struct batch_item {
-    int kind;    // BI_*
+    short kind;  // BI_*
+    short nt;    // tiles: row or column groups bx .. bx + nt - 1, one after another
     int member;
-    int bx;      // row group or column group
+    int bx;      // first row group or column group
     int f;       // field (forward rows) or output (inverse rows)
 };
 
@@ -46,6 +47,11 @@ struct batch_member {
 };
 
 constexpr int BATCH_THREADS = 256;
+// CTAs per SM the FP32 kernel is compiled for (registers: 65536 / (256 x this))
+constexpr int BATCH_MIN_BLOCKS_F32 = 3;
+// tiles (row or column groups) per work item: fewer items, so less of the
+// per-item cost (taking an item, checking and signalling completion)
+constexpr int BATCH_TILES = 4;
 constexpr int BATCH_MAX_PAD = 2048;
 __host__ __device__ constexpr int batch_nb(int px) { return BATCH_MAX_PAD / px; }
 __host__ __device__ constexpr int batch_cb(int py) { return BATCH_MAX_PAD / py; }

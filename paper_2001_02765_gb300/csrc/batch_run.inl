@@ -70,14 +70,18 @@ __device__ __noinline__ void batch_rowi(const row_inv_args<T> &a, int bx, int o,
 template <typename T, int P>
 __device__ __forceinline__ void batch_item_len(const batch_item &it, const batch_member<T> &m, int *err)
 {
-    switch (it.kind) {
-    case BI_ROWF: batch_rowf<T, P>(m.rf, it.bx, it.f, m.twx); break;
-    case BI_EDGE: batch_edge<T, P>(m.ed, m.twy); break;
-    case BI_COL:
-        if (m.central) batch_colc<T, P>(m.col, it.bx, m.qx, m.twy, err);
-        else batch_col<T, P>(m.col, it.bx, m.qx, m.nf_cols, m.twy, err);
-        break;
-    default: batch_rowi<T, P>(m.ri, it.bx, it.f, m.twx); break;
+    for (int t = 0; t < it.nt; ++t) {
+        if (t > 0) __syncthreads();  // the previous tile's use of shared memory is over
+        const int bx = it.bx + t;
+        switch (it.kind) {
+        case BI_ROWF: batch_rowf<T, P>(m.rf, bx, it.f, m.twx); break;
+        case BI_EDGE: batch_edge<T, P>(m.ed, m.twy); break;
+        case BI_COL:
+            if (m.central) batch_colc<T, P>(m.col, bx, m.qx, m.twy, err);
+            else batch_col<T, P>(m.col, bx, m.qx, m.nf_cols, m.twy, err);
+            break;
+        default: batch_rowi<T, P>(m.ri, bx, it.f, m.twx); break;
+        }
     }
 }
 
@@ -98,18 +102,25 @@ __device__ __forceinline__ void batch_run_item(const batch_item &it, const batch
 
 // ctl: [0] the item counter, [1 .. nmem] forward items done per member,
 // [1 + nmem .. 2 nmem] column items done per member (all zero at launch).
+// Thread 0 takes the CTA's next item while the current one runs (its atomic's
+// round trip then overlaps the work); a CTA holding an item it has not started
+// never blocks another, since that item's index exceeds the one it works on,
+// so the lowest unfinished item always runs.
 template <typename T>
-__global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 4 ? 3 : 1) k_batch_run(
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(T) == 4 ? BATCH_MIN_BLOCKS_F32 : 1) k_batch_run(
     const batch_item *__restrict__ items, int nitems, const batch_member<T> *__restrict__ members, int nmem,
     int *__restrict__ ctl, int *err, int tries)
 {
     __shared__ int s_item;
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(&ctl[0], 1);
     for (;;) {
         __syncthreads();  // the previous item's use of shared memory is over
-        if (threadIdx.x == 0) s_item = atomicAdd(&ctl[0], 1);
+        if (threadIdx.x == 0) s_item = next;
         __syncthreads();
         const int i = s_item;
         if (i >= nitems) break;
+        if (threadIdx.x == 0) next = atomicAdd(&ctl[0], 1);
         const batch_item it = items[i];
         const batch_member<T> &m = members[it.member];
         bool ok = true;

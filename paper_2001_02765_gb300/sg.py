@@ -100,6 +100,10 @@ _SIGNATURES = {
     "sg_batch_launch": (ctypes.c_int, [_VP, _VP]),
     "sg_batch_destroy": (ctypes.c_int, [_VP]),
     "sg_batch_launches": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "sg_batch_create_mode": (ctypes.c_int, [ctypes.c_int] + [ctypes.POINTER(_VP)] * 6 + [ctypes.c_int,
+                                                                                         ctypes.POINTER(_VP)]),
+    "sg_batch_layout": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "sg_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_VP)]),
     "sg_server_destroy": (ctypes.c_int, [_VP]),
     "sg_submit": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
@@ -297,14 +301,30 @@ def sg_direct_force_static(nx, ny, h, G, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_p
                                          dy_ptr or None, fx_ptr, fy_ptr, stream_ptr or None), "sg_direct_force_static")
 
 
-def sg_batch_create(plan_handles, sigma_ptrs, dx_ptrs, dy_ptrs, fx_ptrs, fy_ptrs):
-    """Bind n solves (raw device pointers; dx/dy entries 0 where unused) into one graph."""
+SG_BATCH_AUTO, SG_BATCH_PERSISTENT, SG_BATCH_GROUPED = 0, 1, 2
+
+
+def sg_batch_create(plan_handles, sigma_ptrs, dx_ptrs, dy_ptrs, fx_ptrs, fy_ptrs, mode=None):
+    """Bind n solves (raw device pointers; dx/dy entries 0 where unused) into one
+    graph; mode None is sg_batch_create (SG_BATCH_AUTO), else sg_batch_create_mode."""
     n = len(plan_handles)
     arr = lambda v: (_VP * n)(*[x or None for x in v])
     h = _VP()
-    _check(load().sg_batch_create(n, arr(plan_handles), arr(sigma_ptrs), arr(dx_ptrs), arr(dy_ptrs), arr(fx_ptrs),
-                                  arr(fy_ptrs), ctypes.byref(h)), "sg_batch_create")
+    if mode is None:
+        _check(load().sg_batch_create(n, arr(plan_handles), arr(sigma_ptrs), arr(dx_ptrs), arr(dy_ptrs),
+                                      arr(fx_ptrs), arr(fy_ptrs), ctypes.byref(h)), "sg_batch_create")
+    else:
+        _check(load().sg_batch_create_mode(n, arr(plan_handles), arr(sigma_ptrs), arr(dx_ptrs), arr(dy_ptrs),
+                                           arr(fx_ptrs), arr(fy_ptrs), int(mode), ctypes.byref(h)),
+               "sg_batch_create_mode")
     return h.value
+
+
+def sg_batch_layout(batch):
+    """(mode, ms_persistent, ms_grouped) of a batch."""
+    m, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(load().sg_batch_layout(batch, ctypes.byref(m), ctypes.byref(a), ctypes.byref(b)), "sg_batch_layout")
+    return m.value, a.value, b.value
 
 
 def sg_batch_launch(batch, stream_ptr=0):

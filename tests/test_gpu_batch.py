@@ -64,13 +64,15 @@ def test_batch_argument_errors(sg):
     assert e.value.status == sg.SG_EINVAL
 
 
+@pytest.mark.parametrize("layout", ["persistent", "grouped", "auto"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("mode", [0, 1, 2])
-def test_batch_groups_equal_individual_solves(sg, prec, mode):
+def test_batch_groups_equal_individual_solves(sg, prec, mode, layout):
     """Single-patch members of any padded length up to 2048 run in one
-    persistent kernel launch (slope modes none, central, caller; both
-    precisions); results equal sg_force bit for bit, including members whose
-    row counts differ, on two replays in a row."""
+    persistent kernel launch, or as one launch per pass per group of equal
+    lengths, or whichever of the two replays faster (slope modes none,
+    central, caller; both precisions); results equal sg_force bit for bit,
+    including members whose row counts differ, on two replays in a row."""
     import torch
     dt = np.float64 if prec == "fp64" else np.float32
     ns = [33, 40, 47, 64, 20, 30, 90, 100, 128, 17]  # padded lengths 128, 128, 128, 128, 64, 64, 256, 256, 256, 64
@@ -89,10 +91,24 @@ def test_batch_groups_equal_individual_solves(sg, prec, mode):
         ins.append(i)
         outs.append((torch.full_like(i[0], float("nan")), torch.full_like(i[0], float("nan"))))
     ptr = lambda t: t.data_ptr() if t is not None else 0
+    want = {"persistent": sg.SG_BATCH_PERSISTENT, "grouped": sg.SG_BATCH_GROUPED, "auto": sg.SG_BATCH_AUTO}[layout]
     batch = sg.sg_batch_create([p.handle for p in plans], [ptr(i[0]) for i in ins], [ptr(i[1]) for i in ins],
-                               [ptr(i[2]) for i in ins], [ptr(o[0]) for o in outs], [ptr(o[1]) for o in outs])
+                               [ptr(i[2]) for i in ins], [ptr(o[0]) for o in outs], [ptr(o[1]) for o in outs],
+                               mode=want)
     try:
-        assert sg.sg_batch_launches(batch) == 1
+        got, ms_p, ms_g = sg.sg_batch_layout(batch)
+        if layout == "auto":
+            assert got in (sg.SG_BATCH_PERSISTENT, sg.SG_BATCH_GROUPED) and ms_p > 0 and ms_g > 0
+            assert (got == sg.SG_BATCH_PERSISTENT) == (ms_p <= ms_g)
+            for o in outs:  # the timing replays ran on the bound buffers
+                o[0].fill_(float("nan"))
+                o[1].fill_(float("nan"))
+        else:
+            assert got == want and ms_p == 0 and ms_g == 0
+        # persistent: one kernel; grouped: one launch per pass of each group of
+        # equal padded lengths (and a solve's launches for a member alone)
+        nl = sg.sg_batch_launches(batch)
+        assert nl == 1 if got == sg.SG_BATCH_PERSISTENT else nl >= (4 if mode == 1 else 3)
         for _ in range(2):
             sg.sg_batch_launch(batch, torch.cuda.current_stream().cuda_stream)
             torch.cuda.synchronize()
