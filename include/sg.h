@@ -379,6 +379,19 @@ sg_status sg_force_zones(sg_plan *plan, const void *sigma, const void *deltax, c
                          void *fy, void *stream);
 
 /*
+ * The mid-plane potential of a zone plan (sg_potential's sum, Section 2's
+ * K = 1/r integral over the leaf cells) on zone-ordered arrays: sigma, deltax,
+ * deltay as for sg_force_zones; phi (nzones elements) receives the potential
+ * at every leaf zone and 0 at non-leaf zones. The plan must be solved by level
+ * convolutions (sg_plan_info.cross_mode == SG_CROSS_LEVELS), as sg_potential
+ * requires of hierarchies. The first call builds the potential spectra
+ * synchronously. Errors: SG_EINVAL (not a zone plan, a plan on the direct-sum
+ * path, null or misaligned pointer, missing caller slopes), SG_ENOMEM, SG_ECUDA.
+ */
+sg_status sg_potential_zones(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
+                             void *stream);
+
+/*
  * Index of every zone in the plan's patch layout (the field arrays of
  * sg_force): host_out[k] for zone k, n >= nzones. Synchronous.
  */

@@ -241,6 +241,36 @@ __global__ void k_zone_scatter(const int64_t *__restrict__ slot, const int *__re
 }
 
 template <typename T>
+__global__ void k_zone_scatter1(const int64_t *__restrict__ slot, const int *__restrict__ code, int64_t n,
+                                const T *__restrict__ vp, T *__restrict__ v)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = slot[k];
+        v[k] = code[o] == SG_CELL_LEAF ? vp[o] : (T)0;
+    }
+}
+
+// The potential of a zone plan: zone-ordered inputs gathered into the patch
+// layout, sg_potential, the leaf values scattered back (zeros at non-leaves).
+template <typename T>
+sg_status potential_zones_t(sg_plan *plan, const void *sigma, const void *dx, const void *dy, void *phi,
+                            cudaStream_t st)
+{
+    const int64_t nc = plan->ncells;
+    T *buf = (T *)plan->ws->zone_buf;
+    const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
+    int grid = (int)((plan->nzones + 255) / 256);
+    if (grid > 8192) grid = 8192;
+    k_zone_gather<T><<<grid, 256, 0, st>>>(plan->zone_slot, plan->nzones, (const T *)sigma,
+                                           caller ? (const T *)dx : nullptr, caller ? (const T *)dy : nullptr, buf, nc);
+    SG_CUDA_TRY(cudaGetLastError());
+    SG_TRY(sg_potential(plan, buf, caller ? buf + nc : nullptr, caller ? buf + 2 * nc : nullptr, buf + 3 * nc, st));
+    k_zone_scatter1<T><<<grid, 256, 0, st>>>(plan->zone_slot, plan->cell_code, plan->nzones, buf + 3 * nc, (T *)phi);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
+template <typename T>
 sg_status force_zones_t(sg_plan *plan, const void *sigma, const void *dx, const void *dy, void *fx, void *fy,
                         cudaStream_t st)
 {
@@ -305,15 +335,17 @@ sg_status sg_plan_create_zones(const sg_zones *zones, double G, int slope_mode, 
     return SG_OK;
 }
 
-sg_status sg_force_zones(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
-                         void *fy, void *stream)
+// Checks shared by the zone entry points, and the plan's workspace with its
+// zone buffer (allocated at the first call).
+static sg_status zones_call_setup(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay,
+                                  const void *out0, const void *out1)
 {
     if (!plan || plan->nzones <= 0) return zfail("not a zone plan");
-    if (!sigma || !fx || !fy) return zfail("null field pointer");
+    if (!sigma || !out0) return zfail("null field pointer");
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
     if (caller && (!deltax || !deltay)) return zfail("caller slopes requested but deltax/deltay is NULL");
     const size_t es = plan->prec == SG_FP64 ? 8 : 4;
-    const void *ptrs[5] = {sigma, fx, fy, caller ? deltax : nullptr, caller ? deltay : nullptr};
+    const void *ptrs[5] = {sigma, out0, out1, caller ? deltax : nullptr, caller ? deltay : nullptr};
     for (const void *p : ptrs)
         if (p && (uintptr_t)p % es) return zfail("misaligned field pointer");
     int dev = -1;
@@ -340,11 +372,29 @@ sg_status sg_force_zones(sg_plan *plan, const void *sigma, const void *deltax, c
         }
         plan->device_bytes += plan->ws_zone_bytes;
     }
+    return SG_OK;
+}
+
+sg_status sg_force_zones(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *fx,
+                         void *fy, void *stream)
+{
+    if (!fx || !fy) return zfail("null field pointer");
+    SG_TRY(zones_call_setup(plan, sigma, deltax, deltay, fx, fy));
     sg_timing_reset(plan->timing);
     plan->ws->timing = plan->timing;
     cudaStream_t st = (cudaStream_t)stream;
     if (plan->prec == SG_FP64) return force_zones_t<double>(plan, sigma, deltax, deltay, fx, fy, st);
     return force_zones_t<float>(plan, sigma, deltax, deltay, fx, fy, st);
+}
+
+sg_status sg_potential_zones(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
+                             void *stream)
+{
+    if (!phi) return zfail("null field pointer");
+    SG_TRY(zones_call_setup(plan, sigma, deltax, deltay, phi, nullptr));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (plan->prec == SG_FP64) return potential_zones_t<double>(plan, sigma, deltax, deltay, phi, st);
+    return potential_zones_t<float>(plan, sigma, deltax, deltay, phi, st);
 }
 
 sg_status sg_plan_zone_slots(const sg_plan *plan, int64_t *host_out, int64_t n)

@@ -115,6 +115,7 @@ _SIGNATURES = {
     "sg_plan_create_zones": (ctypes.c_int, [ctypes.POINTER(sg_zones), ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)]),
     "sg_force_zones": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sg_potential_zones": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "sg_plan_zone_slots": (ctypes.c_int, [_VP, _I64P, ctypes.c_int64]),
     "sg_zones_from_records": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -457,6 +458,12 @@ def sg_force_zones(handle, sigma_ptr, dx_ptr, dy_ptr, fx_ptr, fy_ptr, stream_ptr
                                  stream_ptr or None), "sg_force_zones")
 
 
+def sg_potential_zones(handle, sigma_ptr, dx_ptr, dy_ptr, phi_ptr, stream_ptr=0):
+    """Raw device pointers (ints), zone-ordered arrays; enqueues the potential."""
+    _check(load().sg_potential_zones(handle, sigma_ptr, dx_ptr or None, dy_ptr or None, phi_ptr,
+                                     stream_ptr or None), "sg_potential_zones")
+
+
 def sg_plan_zone_slots(handle, nzones):
     out = np.empty(int(nzones), dtype=np.int64)
     _check(load().sg_plan_zone_slots(handle, out.ctypes.data_as(_I64P), out.size), "sg_plan_zone_slots")
@@ -667,3 +674,17 @@ class ZonePlan(Plan):
         sg_force_zones(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
                        dy.data_ptr() if dy is not None else 0, fx.data_ptr(), fy.data_ptr(), st)
         return fx, fy
+
+    def potential_zones(self, sigma, dx=None, dy=None, phi=None, stream=None):
+        """Enqueue the potential on zone-ordered tensors; returns phi, 0 at non-leaf zones."""
+        import torch
+        dt = self._torch_dtype()
+        for t in (sigma, dx, dy, phi):
+            if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() != self.nzones):
+                raise ValueError("fields must be contiguous %s CUDA tensors of %d elements" % (dt, self.nzones))
+        if phi is None:
+            phi = torch.empty_like(sigma)
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        sg_potential_zones(self.handle, sigma.data_ptr(), dx.data_ptr() if dx is not None else 0,
+                           dy.data_ptr() if dy is not None else 0, phi.data_ptr(), st)
+        return phi

@@ -305,3 +305,39 @@ def test_ilr2048_fp32_sampled(sg):
     err = rel_l2(fx[t], fy[t], rx, ry)
     print("rel L2 fp32 ILR N=2048: %.3e" % err)
     assert err < F32_TOL
+
+
+@pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", F32_TOL)])
+def test_band_hierarchy_potential_zones(sg, prec, tol):
+    """sg_potential_zones on a four-level VLR hierarchy (level convolutions),
+    random densities and slopes: the leaf potentials equal the oracle's plain
+    sum of Section 2's 1/r cell integrals over the leaf cells; non-leaf zones
+    get 0; a plan on the direct path is refused."""
+    import torch
+    from oracle.potential import direct_potential
+    hier = W.band_hierarchy(32, 4, "vlr", "d22")
+    args = _hier_args(hier)
+    nx0, ny0, x0, y0, h0, level, ix, iy = args
+    leaf = hier["leaf"]
+    rng = np.random.Generator(np.random.PCG64(16))
+    n = level.size
+    s, sx, sy = rng.uniform(0, 1, n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan = sg.ZonePlan(*args, precision=prec, slope_mode=sg.SG_SLOPES_CALLER, cross_mode=2)
+    assert plan.info["cross_mode"] == 2
+    phi = plan.potential_zones(to_dev(s, dt), to_dev(sx, dt), to_dev(sy, dt))
+    torch.cuda.synchronize()
+    phi = phi.cpu().numpy().astype(np.float64)
+    plan.close()
+    xl, xr, yd, yu, xc, yc = oamr.zone_bounds(x0, y0, h0, level, ix, iy)
+    c = lambda a: np.asarray(a, dt).astype(np.float64)[leaf]
+    ref = direct_potential((xl[leaf], xr[leaf], yd[leaf], yu[leaf]), c(s), c(sx), c(sy), xc[leaf], yc[leaf])
+    err = np.linalg.norm(phi[leaf] - ref) / np.linalg.norm(ref)
+    print("rel L2 potential %s: %.3e (tolerance %.0e)" % (prec, err, tol))
+    assert err < tol
+    assert np.all(phi[~leaf] == 0.0)
+    direct = sg.ZonePlan(*args, precision=prec, slope_mode=sg.SG_SLOPES_CALLER, cross_mode=1)
+    with pytest.raises(sg.SgError) as e:
+        direct.potential_zones(to_dev(s, dt), to_dev(sx, dt), to_dev(sy, dt))
+    assert e.value.status == sg.SG_EINVAL
+    direct.close()
