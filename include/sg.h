@@ -214,9 +214,11 @@ sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const 
  * K(xbar - x, ybar - y, 0) sigma with K = 1/r, the singular kernel integral
  * whose gradient gives the force) at every cell centre of a plan in the plane
  * (z == 0): one unmasked patch, with the plan's slope mode (central slopes are
- * formed in the row transform here), or a hierarchy (patches, masks) solved by
- * level convolutions (sg_plan_info.cross_mode == SG_CROSS_LEVELS), summed over
- * the leaf cells as for sg_force (the output at covered cells is unspecified):
+ * formed in the row transform here), or a hierarchy (patches, masks) on either
+ * path of its plan (level convolutions, or each patch's own convolution plus
+ * the cross-patch direct sum: the corner form in FP64 plans, FP64 near cells
+ * and a moment expansion of far cells in FP32 plans), summed over the leaf
+ * cells as for sg_force (the output at covered cells is unspecified):
  *   Phi(t) = -G sum_i [sigma0_i P^0_i(t) + deltax_i P^x_i(t) + deltay_i P^y_i(t)],
  *   P^0, P^x, P^y = integrals over cell i of 1/r, (xbar - xc_i)/r, (ybar - yc_i)/r,
  * from the antiderivatives u ln(v + r) + v ln(u + r) and (v r + u^2 ln(v + r))/2
@@ -224,8 +226,8 @@ sg_status sg_force3(sg_plan *plan, const void *sigma, const void *deltax, const 
  * its three FP64-built potential spectra synchronously (legacy default
  * stream); later calls only enqueue on `stream`.
  *   sigma, deltax, deltay  as for sg_force;  phi  device pointer, ncells elements
- * Errors: SG_EINVAL (off the plane, a hierarchy on the direct-sum path, null or
- * misaligned pointer, missing caller slopes), SG_ENOMEM, SG_ECUDA.
+ * Errors: SG_EINVAL (off the plane, null or misaligned pointer, missing caller
+ * slopes), SG_ENOMEM, SG_ECUDA.
  */
 sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
                        void *stream);
@@ -382,11 +384,10 @@ sg_status sg_force_zones(sg_plan *plan, const void *sigma, const void *deltax, c
  * The mid-plane potential of a zone plan (sg_potential's sum, Section 2's
  * K = 1/r integral over the leaf cells) on zone-ordered arrays: sigma, deltax,
  * deltay as for sg_force_zones; phi (nzones elements) receives the potential
- * at every leaf zone and 0 at non-leaf zones. The plan must be solved by level
- * convolutions (sg_plan_info.cross_mode == SG_CROSS_LEVELS), as sg_potential
- * requires of hierarchies. The first call builds the potential spectra
- * synchronously. Errors: SG_EINVAL (not a zone plan, a plan on the direct-sum
- * path, null or misaligned pointer, missing caller slopes), SG_ENOMEM, SG_ECUDA.
+ * at every leaf zone and 0 at non-leaf zones, on either path of the plan. The
+ * first call builds the potential spectra synchronously. Errors: SG_EINVAL (not
+ * a zone plan, null or misaligned pointer, missing caller slopes), SG_ENOMEM,
+ * SG_ECUDA.
  */
 sg_status sg_potential_zones(sg_plan *plan, const void *sigma, const void *deltax, const void *deltay, void *phi,
                              void *stream);

@@ -1077,8 +1077,6 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
 {
     if (!plan || !sigma || !phi) return fail("null plan or field pointer");
     if (plan->geom.z != 0.0) return fail("sg_potential takes plans in the plane (z = 0)");
-    if (plan->composite && !plan->lv)
-        return fail("sg_potential takes plans of one unmasked patch, or hierarchies solved by level convolutions");
     const bool caller = plan->geom.slope_mode == SG_SLOPES_CALLER;
     if (caller && (!deltax || !deltay)) return fail("caller slopes requested but deltax/deltay is NULL");
     const size_t es = elem_size(plan->prec);
@@ -1097,6 +1095,21 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
                                     (cudaStream_t)stream));
         return sg_lv_potential(plan, plan->ws, phi, (cudaStream_t)stream);
     }
+    if (plan->composite) {
+        // hierarchy on the direct path: composite sources, each patch's own
+        // convolution with its potential spectra, then the cross-patch sum
+        SG_TRY(sg_potential_spectra_build(plan));
+        SG_TRY(ensure_ws(plan));
+        sg_timing_reset(plan->timing);
+        plan->ws->timing = plan->timing;
+        cudaStream_t st = (cudaStream_t)stream;
+        SG_TRY(sg_composite_prepare(plan, plan->ws, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr, st));
+        const char *S = (const char *)plan->ws->sfield;
+        const size_t plane = (size_t)plan->ncells * es;
+        for (int k = 0; k < plan->npatches; ++k)
+            SG_TRY(sg_uniform_potential(plan, plan->ws, k, plan->ws->work_fwd, S, S + plane, S + 2 * plane, phi, st));
+        return sg_cross_potential(plan, plan->ws, S, S + plane, S + 2 * plane, phi, st);
+    }
     SG_TRY(sg_potential_spectra_build(plan));
     SG_TRY(ensure_ws(plan));
     const sg_patch_dev &d = plan->pp[0].d;
@@ -1111,7 +1124,7 @@ sg_status sg_potential(sg_plan *plan, const void *sigma, const void *deltax, con
     }
     sg_timing_reset(plan->timing);
     plan->ws->timing = plan->timing;
-    return sg_uniform_potential(plan, plan->ws, wf, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr, phi,
+    return sg_uniform_potential(plan, plan->ws, 0, wf, sigma, caller ? deltax : nullptr, caller ? deltay : nullptr, phi,
                                 (cudaStream_t)stream);
 }
 

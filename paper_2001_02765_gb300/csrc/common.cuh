@@ -334,9 +334,9 @@ sg_status sg_twiddles_build(sg_plan *plan);
 sg_status sg_phase_build(sg_plan *plan);     // central-slope factors of every patch
 sg_status sg_uniform_solve(sg_plan *plan, const struct sg_workspace *ws, int patch, const void *sigma, const void *dx,
                            const void *dy, void *fx, void *fy, void *fz, cudaStream_t st);
-sg_status sg_uniform_potential(sg_plan *plan, const struct sg_workspace *ws, void *wf, const void *sigma, const void *dx,
-                               const void *dy, void *phi, cudaStream_t st);
-sg_status sg_potential_spectra_build(sg_plan *plan);   // synchronous, patch 0
+sg_status sg_uniform_potential(sg_plan *plan, const struct sg_workspace *ws, int patch, void *wf, const void *sigma,
+                               const void *dx, const void *dy, void *phi, cudaStream_t st);
+sg_status sg_potential_spectra_build(sg_plan *plan);   // synchronous, every patch
 // Launch shapes of the uniform-patch passes for a padded length (tune.cu):
 // shape[0] row sequences per CTA (forward), [1] (inverse), [2] columns per CTA
 // of the column pass, [3] of the central-slope column pass.
@@ -346,6 +346,9 @@ sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const voi
                          void *fx, void *fy, cudaStream_t st);
 // Grid of the persistent far-field launch of an FP32 plan (sets plan->far_grid).
 sg_status sg_cross_far_grid(sg_plan *plan, int nsm);
+// the potential's cross-patch sum, added into phi (the patches' own convolutions already there)
+sg_status sg_cross_potential(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx,
+                             const void *dy, void *phi, cudaStream_t st);
 sg_status sg_amr_prepare(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
                          cudaStream_t st);
 // Composite sources of a solve (amr.cu): with caller slopes or none as given; for

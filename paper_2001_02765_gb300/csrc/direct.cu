@@ -55,6 +55,10 @@
 // near field is one warp per target: lanes take the corners of the box, the
 // warp reduces with shuffles. A last launch adds the far partials, the near
 // field and the patch's own FFT result in a fixed order.
+//
+// The mid-plane potential (sg_potential on hierarchies of this path) is the
+// same sum with the kernel 1/r: its corner form, far-field moments and
+// kernels follow the force's (see the potential section below).
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -599,6 +603,372 @@ sg_status cross_solve_f32(sg_plan *plan, const sg_workspace *ws, const float *si
     return SG_OK;
 }
 
+// ============================================================ potential ====
+//
+// The same cross-patch sum for the mid-plane potential Phi = -G sum_i of the
+// cell integrals of (sigma0_i + deltax_i (xbar - xc_i) + deltay_i (ybar - yc_i)) / r.
+// With l_i(t) as above, xbar - xc_i = u + (x_t - xc_i), so the cell integral is
+// l_i(t) P0 + deltax_i U + deltay_i V with P0, U, V the integrals of 1/r, u/r,
+// v/r, and Section 2's antiderivatives give the corner form
+//   Phi(t) = -G sum_c [ A_c(t) F0(c - t) + X_c Fu(c - t) + Y_c Fv(c - t) ],
+//   F0 = u g0 + v g0y,  Fu = (v r + u^2 g0) / 2,  Fv = (u r + v^2 g0y) / 2
+// (u ln(v + r) + v ln(u + r) and (v r + u^2 ln(v + r)) / 2 with the terms of one
+// variable alone dropped, which cancel in each cell's double difference; every
+// term vanishes where its factor u or v does, so the potential needs no
+// coincident-line form). Far cells in FP32 plans: the cell average of 1/rho
+// over the unit square by its moments (f = 1/rho, p = 1/rho, centre minus
+// target (a, b) in cell widths, Laplacian of p = p^3, bilaplacian = 9 p^5):
+//   I0 = p + p^3/24 + p^5 (-7/1920 + (7/96) a^2 b^2 p^4)
+//   Ix = -a p^3/12 + (7/240) a p^5 - a p^7 (a^2/32 + 5 b^2/96)   (Iy: a <-> b)
+// and Phi_cell = -G H (m I0 + deltax H Ix + deltay H Iy). Truncation relative
+// to the cell's p is below 1e-7 from SG_NEAR_R cell widths on; from SG_FAR_R4
+// on the p^5 and p^7 terms (below 2e-7 relative) are dropped.
+
+// One cell's far potential per unit (-G H): c = (m, deltax H / 8, deltay H / 8).
+template <int ORDER>
+__device__ __forceinline__ float cell_far_pot(float a, float b, float b2, const float4 c)
+{
+    const float r2 = fmaf(a, a, b2);
+    const float p = rsqrtf(r2);
+    const float s = p * p;
+    const float p3 = p * s;
+    // m-moments and slope moments (8 d = deltax H)
+    float i0 = fmaf(p3, 1.f / 24.f, p);
+    float kx = p3 * (-8.f / 12.f), ky = kx;
+    if (ORDER >= 6) {
+        const float p5 = p3 * s, p7 = p5 * s;
+        const float ab = a * b;
+        i0 = fmaf(p5, fmaf(ab * ab * s * s, 7.f / 96.f, -7.f / 1920.f), i0);
+        kx = fmaf(p5, 8.f * 7.f / 240.f, kx);
+        ky = kx;
+        kx = fmaf(-8.f * p7, fmaf(a, a * (1.f / 32.f), b2 * (5.f / 96.f)), kx);
+        ky = fmaf(-8.f * p7, fmaf(b2, 1.f / 32.f, a * a * (5.f / 96.f)), ky);
+    }
+    return fmaf(c.x, i0, fmaf(c.y * a, kx, c.z * b * ky));
+}
+
+template <int ORDER, bool MASK>
+__device__ __forceinline__ float tile_far_pot(const float4 *__restrict__ w, float a0, float b0)
+{
+    float q = 0.f;
+#pragma unroll 1
+    for (int r = 0; r < SG_TILE_Y; ++r) {
+        const float b = b0 + (float)r;
+        const float b2 = b * b;
+        const bool bnear = fabsf(b) < (float)SG_NEAR_R;
+#pragma unroll
+        for (int c = 0; c < SG_TILE_X; ++c) {
+            const float a = a0 + (float)c;
+            const float v = cell_far_pot<ORDER>(a, b, b2, w[r * SG_TILE_X + c]);
+            if (MASK) q += (bnear && fabsf(a) < (float)SG_NEAR_R) ? 0.f : v;
+            else q += v;
+        }
+    }
+    return q;
+}
+
+// The potential's persistent far-field launch: k_cross_far's work items,
+// staging and bounded waits; one output per target (partial[.. * 2]).
+__global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_far_pot(
+    const sg_target_block *__restrict__ blocks, int nblocks, const int4 *__restrict__ targets,
+    const sg_tile_desc *__restrict__ tiles, const sg_patch_dev *__restrict__ pd, int ntiles,
+    const float4 *__restrict__ coefs, int nsplit, double G, double lambda, double *__restrict__ partial,
+    int ntargets, int *__restrict__ words, int tries)
+{
+    __shared__ __align__(128) float4 buf[FAR_STAGES][SG_TILE_N];
+    __shared__ uint64_t full[FAR_STAGES];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        for (int s = 0; s < FAR_STAGES; ++s) mbar_init(&full[s], 1);
+    __syncthreads();
+    uint32_t used = 0, issued = 0;
+    const int nitems = nblocks * nsplit;
+    bool failed = false;
+    while (!failed) {
+        if (tid == 0) s_item = atomicAdd(&words[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int bi = item / nsplit, split = item - bi * nsplit;
+        const sg_target_block blk = blocks[bi];
+        const int t0 = (int)((int64_t)ntiles * split / nsplit), t1 = (int)((int64_t)ntiles * (split + 1) / nsplit);
+        const int own0 = pd[blk.patch].tile_first, own1 = own0 + pd[blk.patch].tile_count;
+        const int n1 = max(0, min(t1, own0) - t0), s2 = max(t0, own1);
+        const int n = n1 + max(0, t1 - s2);
+        const bool active = tid < blk.count;
+        const int4 tg = targets[blk.first + (active ? tid : 0)];
+        if (tid == 0) {
+            for (int k = 0; k < n && k < FAR_STAGES; ++k, ++issued) {
+                const int stg = issued % FAR_STAGES;
+                const int t = k < n1 ? t0 + k : s2 + (k - n1);
+                mbar_arrive_expect_tx(&full[stg], TILE_BYTES);
+                bulk_copy_g2s(buf[stg], coefs + (int64_t)t * SG_TILE_N, TILE_BYTES, &full[stg]);
+            }
+        }
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k, ++used) {
+            const int stg = used % FAR_STAGES;
+            const int t = k < n1 ? t0 + k : s2 + (k - n1);
+            const bool ok = mbar_wait_bounded(&full[stg], (used / FAR_STAGES) & 1, tries);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const sg_tile_desc td = tiles[t];
+            const int cx0 = td.ox + td.step / 2, cx1 = cx0 + (SG_TILE_X - 1) * td.step;
+            const int cy0 = td.oy + td.step / 2, cy1 = cy0 + (SG_TILE_Y - 1) * td.step;
+            const int gx = max(0, max(cx0 - blk.tx1, blk.tx0 - cx1));
+            const int gy = max(0, max(cy0 - blk.ty1, blk.ty0 - cy1));
+            const int gap = max(gx, gy);
+            const float inv = 1.0f / (float)td.step;
+            const float a0 = (float)(td.ox - tg.x) * inv + 0.5f, b0 = (float)(td.oy - tg.y) * inv + 0.5f;
+            float q;
+            if (gap >= SG_FAR_R4 * td.step) q = tile_far_pot<4, false>(buf[stg], a0, b0);
+            else if (gap >= SG_NEAR_R * td.step) q = tile_far_pot<6, false>(buf[stg], a0, b0);
+            else q = tile_far_pot<6, true>(buf[stg], a0, b0);
+            acc = fma((double)td.step * lambda, (double)q, acc);  // times the tile's cell width H
+            __syncthreads();
+            if (tid == 0 && k + FAR_STAGES < n) {
+                const int kk = k + FAR_STAGES;
+                const int tn = kk < n1 ? t0 + kk : s2 + (kk - n1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_expect_tx(&full[stg], TILE_BYTES);
+                bulk_copy_g2s(buf[stg], coefs + (int64_t)tn * SG_TILE_N, TILE_BYTES, &full[stg]);
+                ++issued;
+            }
+        }
+        if (failed) break;
+        if (active) partial[((int64_t)split * ntargets + blk.first + tid) * 2] = -G * acc;
+    }
+    if (failed && tid == 0) {
+        atomicExch(&words[0], 1);
+        for (uint32_t g = used; g < issued; ++g) mbar_wait_bounded(&full[g % FAR_STAGES], (g / FAR_STAGES) & 1, SG_MBAR_MAX_TRIES);
+    }
+}
+
+// The corner functions of the potential at (u, v) = corner - target, r = |(u, v)|,
+// from the logarithms ln(|v| + r) - ln|u| and ln(|u| + r) - ln|v| (t0, t1);
+// accumulates A F0 + X Fu + Y Fv.
+__device__ __forceinline__ double corner_pot(double u, double v, double r, double t0, double t1, double A, double X,
+                                             double Y)
+{
+    const double g0 = (v == 0.0 || u == 0.0) ? 0.0 : (v > 0.0 ? t0 : -t0);   // multiplied by u, u^2
+    const double g0y = (u == 0.0 || v == 0.0) ? 0.0 : (u > 0.0 ? t1 : -t1);  // multiplied by v, v^2
+    const double ug = u * g0, vg = v * g0y;
+    const double F0 = ug + vg;
+    const double Fu = 0.5 * fma(v, r, u * ug);
+    const double Fv = 0.5 * fma(u, r, v * vg);
+    return fma(A, F0, fma(X, Fu, Y * Fv));
+}
+
+// FP64 corner form of the potential (k_cross_direct's layout; one output).
+__global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_direct_pot(
+    const sg_target_block *__restrict__ blocks, const int4 *__restrict__ targets, const sg_tile_desc *__restrict__ tiles,
+    int ntiles, const double *__restrict__ wts, int nsplit, double G, double lambda, double *__restrict__ phi,
+    double *__restrict__ partial, int ntargets)
+{
+    __shared__ sg_dvec4 sw[SG_TILE_N];
+    const sg_target_block blk = blocks[blockIdx.x];
+    const int split = blockIdx.y;
+    const int t0 = (int)((int64_t)ntiles * split / nsplit);
+    const int t1 = (int)((int64_t)ntiles * (split + 1) / nsplit);
+    const bool active = threadIdx.x < blk.count;
+    int4 tg = make_int4(0, 0, -1, -1);
+    if (active) tg = targets[blk.first + threadIdx.x];
+    double acc = 0.0;
+    const sg_dvec4 *wv = reinterpret_cast<const sg_dvec4 *>(wts);
+    for (int t = t0; t < t1; ++t) {
+        const sg_tile_desc td = tiles[t];
+        if (td.patch == blk.patch) continue;  // same-patch pairs come from the FFT
+        __syncthreads();
+        for (int k = threadIdx.x; k < SG_TILE_N; k += SG_DIRECT_THREADS) sw[k] = wv[(int64_t)t * SG_TILE_N + k];
+        __syncthreads();
+        const double du0 = (double)(td.ox - tg.x), dv0 = (double)(td.oy - tg.y), st = (double)td.step;
+        const double dxT = (double)(tg.x - td.ox), dyT = (double)(tg.y - td.oy);
+        double Lu[SG_TILE_X];
+#pragma unroll
+        for (int c = 0; c < SG_TILE_X; ++c) {
+            const double u = fma((double)c, st, du0);
+            Lu[c] = u == 0.0 ? 0.0 : log(fabs(u));
+        }
+        double sum = 0.0;
+#pragma unroll 1
+        for (int r = 0; r < SG_TILE_Y; ++r) {
+            const double v = fma((double)r, st, dv0);
+            const double av = fabs(v), v2 = v * v;
+            const double Lv = v == 0.0 ? 0.0 : log(av);
+#pragma unroll 4
+            for (int c = 0; c < SG_TILE_X; ++c) {
+                const sg_dvec4 wc = sw[r * SG_TILE_X + c];
+                const double u = fma((double)c, st, du0);
+                const double rr = sqrt(fma(u, u, v2));
+                const double A = fma(dxT, wc.y, fma(dyT, wc.z, wc.x));
+                sum += corner_pot(u, v, rr, log(av + rr) - Lu[c], log(fabs(u) + rr) - Lv, A, wc.y, wc.z);
+            }
+        }
+        acc += sum;
+    }
+    if (!active) return;
+    // corner offsets are in lattice units: F0 is a length and Fu, Fv are lengths
+    // squared, against weights X, Y that carry one lattice unit already, so one
+    // factor lambda makes every term physical
+    const double P = -G * lambda * acc;
+    const int ti = blk.first + threadIdx.x;
+    if (nsplit == 1) phi[tg.z] += P;
+    else partial[(int64_t)split * ntargets + ti] = P;
+}
+
+__global__ void k_cross_reduce_pot(const int4 *__restrict__ targets, int ntargets, int nsplit,
+                                   const double *__restrict__ partial, double *__restrict__ phi)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntargets; t += gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int s = 0; s < nsplit; ++s) sum += partial[(int64_t)s * ntargets + t];
+        phi[targets[t].z] += sum;
+    }
+}
+
+// Near field of the potential in FP64 (k_cross_near's boxes, staging and warp
+// reduction; one output).
+__global__ void __launch_bounds__(NEAR_WARPS * 32) k_cross_near_pot(const int4 *__restrict__ targets, int ntargets,
+                                                                   const sg_patch_dev *__restrict__ pd, int npatches,
+                                                                   const float *__restrict__ sigma,
+                                                                   const float *__restrict__ dx,
+                                                                   const float *__restrict__ dy, double lambda,
+                                                                   double G, double *__restrict__ near_out)
+{
+    __shared__ double cellv[NEAR_WARPS][3][NEAR_SLOTS];
+    const int lane = threadIdx.x & 31;
+    double *cl = cellv[threadIdx.x >> 5][0], *cx = cellv[threadIdx.x >> 5][1], *cy = cellv[threadIdx.x >> 5][2];
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+    for (int t = warp; t < ntargets; t += nwarps) {
+        const int4 tg = targets[t];
+        double ph = 0.0;
+        for (int q = 0; q < npatches; ++q) {
+            if (q == tg.w) continue;
+            const sg_patch_dev &p = pd[q];
+            const int64_t L = p.step, RL = (int64_t)SG_NEAR_R * L;
+            const int64_t ex = (int64_t)tg.x - p.ox - L / 2, ey = (int64_t)tg.y - p.oy - L / 2;
+            const int i0 = max(0, floor_div(ex - RL, L) + 1), j0 = max(0, floor_div(ey - RL, L) + 1);
+            const int i1 = min(p.nx - 1, -floor_div(-(ex + RL), L) - 1);
+            const int j1 = min(p.ny - 1, -floor_div(-(ey + RL), L) - 1);
+            if (i0 > i1 || j0 > j1) continue;
+            const int nbx = i1 - i0 + 1, nby = j1 - j0 + 1, W = nbx + 2;
+            __syncwarp();  // the previous box's values have been read
+            for (int k = lane; k < W * (nby + 2); k += 32) {
+                const int bi = k % W - 1, bj = k / W - 1;
+                double l = 0.0, X = 0.0, Y = 0.0;
+                if (bi >= 0 && bi < nbx && bj >= 0 && bj < nby) {
+                    const int i = i0 + bi, j = j0 + bj;
+                    const int64_t o = p.cell_off + (int64_t)j * p.nx + i;
+                    X = dx[o];
+                    Y = dy[o];
+                    const double ux = ((double)tg.x - ((double)p.ox + (i + 0.5) * (double)L)) * lambda;
+                    const double uy = ((double)tg.y - ((double)p.oy + (j + 0.5) * (double)L)) * lambda;
+                    l = fma(X, ux, fma(Y, uy, (double)sigma[o]));
+                }
+                cl[k] = l;
+                cx[k] = X;
+                cy[k] = Y;
+            }
+            const double uc = ((double)p.ox + (double)(i0 + lane) * L - tg.x) * lambda;
+            const double vc = ((double)p.oy + (double)(j0 + lane) * L - tg.y) * lambda;
+            const double lnu = lane <= nbx ? (uc == 0.0 ? 0.0 : log(fabs(uc))) : 0.0;
+            const double lnv = lane <= nby ? (vc == 0.0 ? 0.0 : log(fabs(vc))) : 0.0;
+            __syncwarp();
+            const int nci = nbx + 1, ncorner = nci * (nby + 1);
+            for (int base = 0; base < ncorner; base += 32) {
+                const int k = base + lane;
+                const bool valid = k < ncorner;
+                const int kk = valid ? k : 0;
+                const int ci = kk % nci, cj = kk / nci;
+                const double Lu = __shfl_sync(0xffffffffu, lnu, ci);
+                const double Lv = __shfl_sync(0xffffffffu, lnv, cj);
+                if (!valid) continue;
+                const int s00 = cj * W + ci, s10 = s00 + 1, s01 = s00 + W, s11 = s01 + 1;
+                const double A = (cl[s00] - cl[s10]) - (cl[s01] - cl[s11]);
+                const double X = (cx[s00] - cx[s10]) - (cx[s01] - cx[s11]);
+                const double Y = (cy[s00] - cy[s10]) - (cy[s01] - cy[s11]);
+                const double u = ((double)p.ox + (double)(i0 + ci) * L - tg.x) * lambda;
+                const double v = ((double)p.oy + (double)(j0 + cj) * L - tg.y) * lambda;
+                const double r = sqrt(fma(u, u, v * v));
+                ph += corner_pot(u, v, r, log(fabs(v) + r) - Lu, log(fabs(u) + r) - Lv, A, X, Y);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ph += __shfl_xor_sync(0xffffffffu, ph, off);
+        if (lane == 0) near_out[(int64_t)t * 2] = -G * ph;
+    }
+}
+
+// Fixed-order sum into the potential: the patch's own FFT result, the far
+// partials of every split, then the near field.
+__global__ void k_cross_combine_pot(const int4 *__restrict__ targets, int ntargets, int nsplit,
+                                    const double *__restrict__ partial, float *__restrict__ phi)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntargets; t += gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int s = 0; s <= nsplit; ++s) sum += partial[((int64_t)s * ntargets + t) * 2];
+        const int o = targets[t].z;
+        phi[o] = (float)((double)phi[o] + sum);
+    }
+}
+
+sg_status cross_potential_f64(sg_plan *plan, const sg_workspace *ws, const double *sigma, const double *dx,
+                              const double *dy, double *phi, cudaStream_t st)
+{
+    double *w = (double *)ws->tile_w;
+    const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
+    int grid_w = (int)((nw + 255) / 256);
+    if (grid_w > 65535) grid_w = 65535;
+    k_corner_weights<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+                                             plan->lattice_unit, w);
+    SG_CUDA_TRY(cudaGetLastError());
+    dim3 grid(plan->nblocks, plan->nsplit);
+    k_cross_direct_pot<<<grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->targets, plan->tiles, plan->ntiles, w,
+                                                           plan->nsplit, plan->geom.G, plan->lattice_unit, phi,
+                                                           ws->partial, plan->ntargets);
+    SG_CUDA_TRY(cudaGetLastError());
+    if (plan->nsplit > 1) {
+        k_cross_reduce_pot<<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets,
+                                                                          plan->nsplit, ws->partial, phi);
+        SG_CUDA_TRY(cudaGetLastError());
+    }
+    return SG_OK;
+}
+
+sg_status cross_potential_f32(sg_plan *plan, const sg_workspace *ws, const float *sigma, const float *dx,
+                              const float *dy, float *phi, cudaStream_t st)
+{
+    float4 *w = (float4 *)ws->tile_w;
+    const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
+    int grid_w = (int)((nw + 255) / 256);
+    if (grid_w > 65535) grid_w = 65535;
+    k_cell_coefs<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+                                         plan->lattice_unit, w, ws->err + 1);
+    SG_CUDA_TRY(cudaGetLastError());
+    k_cross_far_pot<<<plan->far_grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->nblocks, plan->targets,
+                                                                  plan->tiles, plan->patch_dev, plan->ntiles, w,
+                                                                  plan->nsplit, plan->geom.G, plan->lattice_unit,
+                                                                  ws->partial, plan->ntargets, ws->err,
+                                                                  plan->wait_tries);
+    SG_CUDA_TRY(cudaGetLastError());
+    double *near = ws->partial + (int64_t)plan->nsplit * plan->ntargets * 2;
+    const int64_t nblk = ((int64_t)plan->ntargets + NEAR_WARPS - 1) / NEAR_WARPS;
+    const int grid_n = (int)(nblk < (1 << 20) ? nblk : (1 << 20));
+    k_cross_near_pot<<<grid_n, NEAR_WARPS * 32, 0, st>>>(plan->targets, plan->ntargets, plan->patch_dev,
+                                                         plan->npatches, sigma, dx, dy, plan->lattice_unit,
+                                                         plan->geom.G, near);
+    SG_CUDA_TRY(cudaGetLastError());
+    k_cross_combine_pot<<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
+                                                                       ws->partial, phi);
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+}
+
 }  // namespace
 
 sg_status sg_cross_far_grid(sg_plan *plan, int nsm)
@@ -622,4 +992,15 @@ sg_status sg_cross_solve(sg_plan *plan, const sg_workspace *ws, const void *sigm
                                (double *)fy, st);
     return cross_solve_f32(plan, ws, (const float *)sigma, (const float *)dx, (const float *)dy, (float *)fx,
                            (float *)fy, st);
+}
+
+sg_status sg_cross_potential(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
+                             void *phi, cudaStream_t st)
+{
+    if (plan->ntiles == 0 || plan->ntargets == 0) return SG_OK;
+    if (plan->prec == SG_FP64)
+        return cross_potential_f64(plan, ws, (const double *)sigma, (const double *)dx, (const double *)dy,
+                                   (double *)phi, st);
+    return cross_potential_f32(plan, ws, (const float *)sigma, (const float *)dx, (const float *)dy, (float *)phi,
+                               st);
 }

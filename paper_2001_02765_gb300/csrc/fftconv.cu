@@ -45,13 +45,13 @@ sg_status sg_uniform_solve(sg_plan *plan, const sg_workspace *ws, int patch, con
     return uniform_solve_t<float>(plan, ws, patch, sigma, dx, dy, fx, fy, fz, st);
 }
 
-sg_status sg_uniform_potential(sg_plan *plan, const sg_workspace *ws, void *wf, const void *sigma, const void *dx,
-                               const void *dy, void *phi, cudaStream_t st)
+sg_status sg_uniform_potential(sg_plan *plan, const sg_workspace *ws, int patch, void *wf, const void *sigma,
+                               const void *dx, const void *dy, void *phi, cudaStream_t st)
 {
-    const sg_patch_plan &pp = plan->pp[0];
+    const sg_patch_plan &pp = plan->pp[patch];
     if (plan->prec == SG_FP64)
-        return uniform_solve_t<double>(plan, ws, 0, sigma, dx, dy, phi, nullptr, nullptr, st,
+        return uniform_solve_t<double>(plan, ws, patch, sigma, dx, dy, phi, nullptr, nullptr, st,
                                        (const double *)pp.pspectra, wf);
-    return uniform_solve_t<float>(plan, ws, 0, sigma, dx, dy, phi, nullptr, nullptr, st, (const float *)pp.pspectra,
-                                  wf);
+    return uniform_solve_t<float>(plan, ws, patch, sigma, dx, dy, phi, nullptr, nullptr, st,
+                                  (const float *)pp.pspectra, wf);
 }

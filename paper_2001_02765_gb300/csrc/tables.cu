@@ -455,10 +455,10 @@ sg_status sg_tables_copy(const sg_plan *plan, int patch, int which, double *host
     return SG_OK;
 }
 
-// Potential spectra of patch 0, built once (synchronous).
-sg_status sg_potential_spectra_build(sg_plan *plan)
+// Potential spectra of patch p, built once (synchronous).
+static sg_status potential_spectra_patch(sg_plan *plan, int p)
 {
-    sg_patch_plan &pp = plan->pp[0];
+    sg_patch_plan &pp = plan->pp[p];
     if (pp.pspectra) return SG_OK;
     const int px = pp.d.px, py = pp.d.py;
     const size_t es = plan->prec == SG_FP64 ? 8 : 4;
@@ -501,5 +501,12 @@ sg_status sg_potential_spectra_build(sg_plan *plan)
     }
     pp.pspectra = spec;
     plan->device_bytes += (int64_t)bytes;
+    return SG_OK;
+}
+
+// Potential spectra of every patch (each patch's own convolution).
+sg_status sg_potential_spectra_build(sg_plan *plan)
+{
+    for (int p = 0; p < plan->npatches; ++p) SG_TRY(potential_spectra_patch(plan, p));
     return SG_OK;
 }

@@ -135,24 +135,26 @@ def test_potential_repeatable_and_errors(sg):
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     plan.close()
-    amr = sg.Plan([(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 2))], cross_mode=sg.SG_CROSS_DIRECT)
-    x = torch.zeros(amr.ncells, device="cuda")
+    off = sg.Plan([(0, 16, 16, 0.0, 0.0, 0.1)], z=0.05)
+    x = torch.zeros(off.ncells, device="cuda")
     with pytest.raises(sg.SgError) as e:
-        sg.sg_potential(amr.handle, x.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr())
-    assert e.value.status == sg.SG_EINVAL and "one unmasked patch" in str(e.value)
-    amr.close()
+        sg.sg_potential(off.handle, x.data_ptr(), x.data_ptr(), x.data_ptr(), x.data_ptr())
+    assert e.value.status == sg.SG_EINVAL and "in the plane" in str(e.value)
+    off.close()
 
 
-# ------------------------------------------- hierarchies (level convolutions) --
+# ----------------- hierarchies (level convolutions, and the direct-sum path) --
 
 TABLE10 = [(0, 4, 4, 0.0, 0.0, 0.25), (1, 2, 2, 0.25, 0.25, 0.125), (1, 2, 2, 0.5, 0.5, 0.125),
            (2, 2, 2, 0.25, 0.375, 0.0625), (2, 2, 2, 0.375, 0.25, 0.0625)]
 
 
-def _amr_phi(sg, patches, prec, mode, sig, sx, sy, G=1.0):
+def _amr_phi(sg, patches, prec, mode, sig, sx, sy, G=1.0, cross="levels"):
     import torch
     dt = np.float64 if prec == "fp64" else np.float32
-    plan = sg.Plan(patches, precision=prec, slope_mode=mode, G=G, cross_mode=sg.SG_CROSS_LEVELS)
+    cm = sg.SG_CROSS_LEVELS if cross == "levels" else sg.SG_CROSS_DIRECT
+    plan = sg.Plan(patches, precision=prec, slope_mode=mode, G=G, cross_mode=cm)
+    assert plan.info["cross_mode"] == cm
     a = concat_dev(sig, dt)
     b = concat_dev(sx, dt) if mode == sg.SG_SLOPES_CALLER else None
     c = concat_dev(sy, dt) if mode == sg.SG_SLOPES_CALLER else None
@@ -161,9 +163,9 @@ def _amr_phi(sg, patches, prec, mode, sig, sx, sy, G=1.0):
     return plan, phi.cpu().numpy().astype(np.float64)
 
 
-def _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None):
+def _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=None, cross="levels"):
     dt = np.float64 if prec == "fp64" else np.float32
-    plan, phi = _amr_phi(sg, patches, prec, mode, sig, sx, sy, G)
+    plan, phi = _amr_phi(sg, patches, prec, mode, sig, sx, sy, G, cross)
     r = lambda a: [np.asarray(x, dt).astype(np.float64) for x in a]
     slopes = mode == sg.SG_SLOPES_CALLER
     leaves, ref = amr_direct_potential(oamr.make_patches(patches), r(sig), r(sx) if slopes else None,
@@ -173,46 +175,67 @@ def _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=1.0, target_index=No
     got = gather_leaves(plan, phi, leaves)
     plan.close()
     err = _rel(got, ref)
+    print("rel L2 potential %s %s: %.3e (tolerance %.0e)" % (prec, cross, err, tol))
     assert err < tol, err
     return err
 
 
+CROSS = pytest.mark.parametrize("cross", ["levels", "direct"])
+
+
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("mode", [0, 2])
-def test_amr_potential_nested(sg, prec, tol, mode):
+def test_amr_potential_nested(sg, prec, tol, mode, cross):
     """Three centred nested levels of 16^2 cells, smooth bumps: the leaf-sum potential."""
     patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(16, 3))]
     sig, sx, sy = W.bumps_on_patches(patches, 3)
-    _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=2.5)
+    _amr_check(sg, patches, prec, mode, sig, sx, sy, tol, G=2.5, cross=cross)
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_amr_potential_table10(sg, prec, tol):
+def test_amr_potential_table10(sg, prec, tol, cross):
     """Fig. 1 / Table 10: two patches per refined level, 28 leaves, random positive data."""
     rng = np.random.Generator(np.random.PCG64(8))
     sig = [rng.uniform(0, 1, (p[2], p[1])) for p in TABLE10]
     sx = [rng.uniform(-1, 1, (p[2], p[1])) for p in TABLE10]
     sy = [rng.uniform(-1, 1, (p[2], p[1])) for p in TABLE10]
-    _amr_check(sg, TABLE10, prec, 2, sig, sx, sy, tol)
+    _amr_check(sg, TABLE10, prec, 2, sig, sx, sy, tol, cross=cross)
 
 
+@CROSS
 @pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_amr_potential_ragged(sg, prec, tol):
+def test_amr_potential_ragged(sg, prec, tol, cross):
     """Non-square, off-centre patches (two on level 1), sizes not powers of two."""
     patches = [(0, 37, 29, -1.0, -0.8, 0.05), (1, 22, 14, -0.6, -0.3, 0.025), (1, 6, 8, 0.2, 0.1, 0.025),
                (2, 10, 12, -0.5, -0.25, 0.0125)]
     sig, sx, sy = W.bumps_on_patches(patches, 5)
-    _amr_check(sg, patches, prec, 2, sig, sx, sy, tol)
+    _amr_check(sg, patches, prec, 2, sig, sx, sy, tol, cross=cross)
 
 
-def test_amr_potential_config3_sampled(sg):
+@CROSS
+@pytest.mark.parametrize("prec, tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_amr_potential_rough(sg, prec, tol, cross):
+    """Three nested levels of 24^2 cells with independent uniform noise in
+    sigma0 and both slopes (signed): every far-field and near-field term."""
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(24, 3))]
+    rng = np.random.Generator(np.random.PCG64(17))
+    sig = [rng.uniform(-1, 1, (p[2], p[1])) for p in patches]
+    sx = [rng.uniform(-1, 1, (p[2], p[1])) for p in patches]
+    sy = [rng.uniform(-1, 1, (p[2], p[1])) for p in patches]
+    _amr_check(sg, patches, prec, 2, sig, sx, sy, tol, cross=cross)
+
+
+@CROSS
+def test_amr_potential_config3_sampled(sg, cross):
     """The 3 x 256^2 exponential-disk hierarchy, FP32: 64 sampled leaves against the plain sum."""
     case = W.exponential_hierarchy(256, 3, 0.1)
     patches = [(lev,) + p for lev, p in enumerate(case["patches"])]
     sig, sx, sy = case["sigma"], case["dx"], case["dy"]
     n = len(oamr.leaf_cells(oamr.make_patches(patches))["xc"])
     idx = np.random.Generator(np.random.PCG64(33)).choice(n, 64, replace=False)
-    _amr_check(sg, patches, "fp32", 2, sig, sx, sy, 1e-5, target_index=idx)
+    _amr_check(sg, patches, "fp32", 2, sig, sx, sy, 1e-5, target_index=idx, cross=cross)
 
 
 def test_amr_potential_matches_force(sg):

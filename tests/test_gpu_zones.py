@@ -307,12 +307,13 @@ def test_ilr2048_fp32_sampled(sg):
     assert err < F32_TOL
 
 
+@pytest.mark.parametrize("cross", [1, 2], ids=["direct", "levels"])
 @pytest.mark.parametrize("prec, tol", [("fp64", F64_TOL), ("fp32", F32_TOL)])
-def test_band_hierarchy_potential_zones(sg, prec, tol):
-    """sg_potential_zones on a four-level VLR hierarchy (level convolutions),
-    random densities and slopes: the leaf potentials equal the oracle's plain
-    sum of Section 2's 1/r cell integrals over the leaf cells; non-leaf zones
-    get 0; a plan on the direct path is refused."""
+def test_band_hierarchy_potential_zones(sg, prec, tol, cross):
+    """sg_potential_zones on a four-level VLR hierarchy (level convolutions or
+    the direct-sum path), random densities and slopes: the leaf potentials
+    equal the oracle's plain sum of Section 2's 1/r cell integrals over the
+    leaf cells; non-leaf zones get 0."""
     import torch
     from oracle.potential import direct_potential
     hier = W.band_hierarchy(32, 4, "vlr", "d22")
@@ -323,8 +324,8 @@ def test_band_hierarchy_potential_zones(sg, prec, tol):
     n = level.size
     s, sx, sy = rng.uniform(0, 1, n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)
     dt = np.float64 if prec == "fp64" else np.float32
-    plan = sg.ZonePlan(*args, precision=prec, slope_mode=sg.SG_SLOPES_CALLER, cross_mode=2)
-    assert plan.info["cross_mode"] == 2
+    plan = sg.ZonePlan(*args, precision=prec, slope_mode=sg.SG_SLOPES_CALLER, cross_mode=cross)
+    assert plan.info["cross_mode"] == cross
     phi = plan.potential_zones(to_dev(s, dt), to_dev(sx, dt), to_dev(sy, dt))
     torch.cuda.synchronize()
     phi = phi.cpu().numpy().astype(np.float64)
@@ -333,11 +334,6 @@ def test_band_hierarchy_potential_zones(sg, prec, tol):
     c = lambda a: np.asarray(a, dt).astype(np.float64)[leaf]
     ref = direct_potential((xl[leaf], xr[leaf], yd[leaf], yu[leaf]), c(s), c(sx), c(sy), xc[leaf], yc[leaf])
     err = np.linalg.norm(phi[leaf] - ref) / np.linalg.norm(ref)
-    print("rel L2 potential %s: %.3e (tolerance %.0e)" % (prec, err, tol))
+    print("rel L2 potential %s cross=%d: %.3e (tolerance %.0e)" % (prec, cross, err, tol))
     assert err < tol
     assert np.all(phi[~leaf] == 0.0)
-    direct = sg.ZonePlan(*args, precision=prec, slope_mode=sg.SG_SLOPES_CALLER, cross_mode=1)
-    with pytest.raises(sg.SgError) as e:
-        direct.potential_zones(to_dev(s, dt), to_dev(sx, dt), to_dev(sy, dt))
-    assert e.value.status == sg.SG_EINVAL
-    direct.close()
