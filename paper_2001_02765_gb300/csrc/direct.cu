@@ -924,9 +924,12 @@ sg_status cross_potential_f64(sg_plan *plan, const sg_workspace *ws, const doubl
     const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
     int grid_w = (int)((nw + 255) / 256);
     if (grid_w > 65535) grid_w = 65535;
+    sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
     k_corner_weights<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
                                              plan->lattice_unit, w);
     SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_DIRECT, st);
     dim3 grid(plan->nblocks, plan->nsplit);
     k_cross_direct_pot<<<grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->targets, plan->tiles, plan->ntiles, w,
                                                            plan->nsplit, plan->geom.G, plan->lattice_unit, phi,
@@ -937,6 +940,7 @@ sg_status cross_potential_f64(sg_plan *plan, const sg_workspace *ws, const doubl
                                                                           plan->nsplit, ws->partial, phi);
         SG_CUDA_TRY(cudaGetLastError());
     }
+    sg_timing_end(ws, SG_STAGE_DIRECT, st);
     return SG_OK;
 }
 
@@ -947,9 +951,12 @@ sg_status cross_potential_f32(sg_plan *plan, const sg_workspace *ws, const float
     const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
     int grid_w = (int)((nw + 255) / 256);
     if (grid_w > 65535) grid_w = 65535;
+    sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
     k_cell_coefs<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
                                          plan->lattice_unit, w, ws->err + 1);
     SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_DIRECT, st);
     k_cross_far_pot<<<plan->far_grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->nblocks, plan->targets,
                                                                   plan->tiles, plan->patch_dev, plan->ntiles, w,
                                                                   plan->nsplit, plan->geom.G, plan->lattice_unit,
@@ -966,6 +973,7 @@ sg_status cross_potential_f32(sg_plan *plan, const sg_workspace *ws, const float
     k_cross_combine_pot<<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
                                                                        ws->partial, phi);
     SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_DIRECT, st);
     return SG_OK;
 }
 
