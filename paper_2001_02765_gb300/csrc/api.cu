@@ -109,7 +109,6 @@ sg_status analyse(const sg_geom *g, geom_info &gi)
     if (g->npatches < 1 || !g->patches) return fail("geometry has no patches");
     if (!isfinite(g->G)) return fail("G is not finite");
     if (!isfinite(g->z)) return fail("z is not finite");
-    if (g->z != 0.0 && g->npatches != 1) return fail("off-plane forces (z != 0) need a single patch");
     if (g->slope_mode < SG_SLOPES_NONE || g->slope_mode > SG_SLOPES_CALLER) return fail("unknown slope mode");
     if (g->cross_mode < SG_CROSS_AUTO || g->cross_mode > SG_CROSS_LEVELS) return fail("unknown cross mode");
     const int n = g->npatches;
@@ -117,7 +116,6 @@ sg_status analyse(const sg_geom *g, geom_info &gi)
     gi.n = n;
     if (g->masks)
         for (int k = 0; k < n; ++k) gi.masked = gi.masked || g->masks[k] != nullptr;
-    if (gi.masked && g->z != 0.0) return fail("off-plane forces (z != 0) need an unmasked patch");
     if (P[0].level != 0) return fail("the first patch must be on level 0");
     for (int k = 0; k < n; ++k) {
         if (P[k].nx < 1 || P[k].ny < 1 || P[k].nx > SG_MAX_PATCH_SIDE || P[k].ny > SG_MAX_PATCH_SIDE)
@@ -540,8 +538,10 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
     if (gi.n > 1 || gi.masked) s.direct = 3 * gi.ncells * (int64_t)es + gi.ncells * (int64_t)sizeof(int);
     if ((gi.n > 1 || gi.masked) && g->slope_mode == SG_SLOPES_CENTRAL) s.direct += 40 * gi.ncells;  // links, centres
     if (gi.n > 1 && lv_bytes < 0) {
-        const int64_t slices = prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1;
-        s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
+        // off the plane: FP64 corner weights and three partial components per split
+        const bool off = g->z != 0.0;
+        const int64_t slices = off ? (int64_t)nsplit * 3 / 2 + 1 : (prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1);
+        s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)(off ? 8 : es)) +
                     gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
                     slices * gi.nleaves * 16;
     }
@@ -642,12 +642,14 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     }
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tfirst, tcount;
-    if (gi.n > 1 && !use_lv) build_tiles(g, gi, prec == SG_FP32, tiles, tfirst, tcount);
+    // corner tiles for the corner form (FP64 plans, and every plan off the plane), cell tiles otherwise
+    const bool corner_form = prec == SG_FP64 || g->z != 0.0;
+    if (gi.n > 1 && !use_lv) build_tiles(g, gi, !corner_form, tiles, tfirst, tcount);
     int dev = 0, nsm = 152;
     SG_CUDA_TRY(cudaGetDevice(&dev));
     SG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int nblocks = use_lv ? 0 : count_blocks(g, gi);
-    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), nsm, prec);
+    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), nsm, corner_form ? SG_FP64 : prec);
     const sizes sz = plan_sizes(g, gi, prec, (int)tiles.size(), nblocks, nsplit, lv_bytes);
     if (budget && (size_t)sz.total() > budget) {
         set_error("plan exceeds the device-memory budget");
@@ -788,7 +790,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             st = cudaMemcpy(plan->tiles, tiles.data(), tiles.size() * sizeof(sg_tile_desc), cudaMemcpyHostToDevice) ==
                          cudaSuccess ? SG_OK : SG_ECUDA;
         const size_t nw = (size_t)plan->ntiles * SG_TILE_N;
-        plan->ws_tile_bytes = (int64_t)nw * (prec == SG_FP64 ? (int64_t)sizeof(sg_dvec4) : (int64_t)sizeof(float4));
+        // FP64 corner weights (FP64 plans, and every plan off the plane), FP32 cell coefficients otherwise
+        const bool wide = prec == SG_FP64 || g->z != 0.0;
+        plan->ws_tile_bytes = (int64_t)nw * (wide ? (int64_t)sizeof(sg_dvec4) : (int64_t)sizeof(float4));
         // targets: every leaf, in blocks of the leaves of 16 x 16 cells
         std::vector<int4> tg;
         std::vector<sg_target_block> blocks;
@@ -805,7 +809,9 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
                             cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
         const int64_t slices = prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1;
         plan->ws_partial_bytes = slices * (int64_t)tg.size() * 2 * (int64_t)sizeof(double);
-        if (st == SG_OK && prec == SG_FP32) st = sg_cross_far_grid(plan, nsm);
+        if (g->z != 0.0)  // off the plane: three components per split, both precisions
+            plan->ws_partial_bytes = (int64_t)nsplit * (int64_t)tg.size() * 3 * (int64_t)sizeof(double);
+        if (st == SG_OK && prec == SG_FP32 && g->z == 0.0) st = sg_cross_far_grid(plan, nsm);
     }
     if (st == SG_OK) st = sg_twiddles_build(plan);
     if (st == SG_OK) st = sg_phase_build(plan);
@@ -924,8 +930,8 @@ sg_status sg_force_ws(sg_plan *plan, const sg_workspace *ws, const void *sigma, 
     const char *S = (const char *)ws->sfield;
     const size_t plane = (size_t)plan->ncells * es;
     for (int k = 0; k < plan->npatches; ++k)
-        SG_TRY(sg_uniform_solve(plan, ws, k, S, S + plane, S + 2 * plane, fx, fy, nullptr, st));
-    return sg_cross_solve(plan, ws, S, S + plane, S + 2 * plane, fx, fy, st);
+        SG_TRY(sg_uniform_solve(plan, ws, k, S, S + plane, S + 2 * plane, fx, fy, fz, st));
+    return sg_cross_solve(plan, ws, S, S + plane, S + 2 * plane, fx, fy, fz, st);
 }
 
 // Reads and clears the device error word of the plan's workspace (synchronises).
@@ -1008,9 +1014,10 @@ sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes)
         lv_bytes = -1;
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tf, tc;
-    if (gi.n > 1 && lv_bytes < 0) build_tiles(geom, gi, prec == SG_FP32, tiles, tf, tc);
+    const bool corner_form = prec == SG_FP64 || geom->z != 0.0;
+    if (gi.n > 1 && lv_bytes < 0) build_tiles(geom, gi, !corner_form, tiles, tf, tc);
     const int nblocks = lv_bytes < 0 ? count_blocks(geom, gi) : 0;
-    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152, prec);
+    const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152, corner_form ? SG_FP64 : prec);
     *bytes = plan_sizes(geom, gi, prec, (int)tiles.size(), nblocks, nsplit, lv_bytes).total();
     return SG_OK;
 }

@@ -343,7 +343,7 @@ sg_status sg_potential_spectra_build(sg_plan *plan);   // synchronous, every pat
 #define SG_TUNE_KNOBS 4
 void sg_tune_shape(sg_precision prec, int pad, int *shape);
 sg_status sg_cross_solve(sg_plan *plan, const struct sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
-                         void *fx, void *fy, cudaStream_t st);
+                         void *fx, void *fy, void *fz, cudaStream_t st);  // fz: z != 0 plans only
 // Grid of the persistent far-field launch of an FP32 plan (sets plan->far_grid).
 sg_status sg_cross_far_grid(sg_plan *plan, int nsm);
 // the potential's cross-patch sum, added into phi (the patches' own convolutions already there)

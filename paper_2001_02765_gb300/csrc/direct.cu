@@ -70,9 +70,10 @@ namespace {
 
 // One thread per (tile, corner): signed sums of the (up to) four cells of the
 // patch around the corner, from the composite source fields.
+template <typename T>
 __global__ void k_corner_weights(const sg_tile_desc *__restrict__ tiles, int ntiles, const sg_patch_dev *__restrict__ pd,
-                                 const double *__restrict__ sigma, const double *__restrict__ dx,
-                                 const double *__restrict__ dy, double lambda, double *__restrict__ wout)
+                                 const T *__restrict__ sigma, const T *__restrict__ dx,
+                                 const T *__restrict__ dy, double lambda, double *__restrict__ wout)
 {
     const int64_t total = (int64_t)ntiles * SG_TILE_N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -87,9 +88,9 @@ __global__ void k_corner_weights(const sg_tile_desc *__restrict__ tiles, int nti
                 if (i < 0 || i >= p.nx || j < 0 || j >= p.ny) continue;
                 const double s = (q == 0 || q == 3) ? 1.0 : -1.0;
                 const int64_t o = p.cell_off + (int64_t)j * p.nx + i;
-                const double s0 = sigma[o];
-                const double sx = dx ? dx[o] : 0.0;
-                const double sy = dy ? dy[o] : 0.0;
+                const double s0 = (double)sigma[o];
+                const double sx = dx ? (double)dx[o] : 0.0;
+                const double sy = dy ? (double)dy[o] : 0.0;
                 // cell centre (lattice) = patch origin + (2i + 1) step / 2
                 const double cx = p.ox + (2 * i + 1) * (p.step / 2);
                 const double cy = p.oy + (2 * j + 1) * (p.step / 2);
@@ -211,7 +212,7 @@ sg_status cross_solve_f64(sg_plan *plan, const sg_workspace *ws, const double *s
     int grid_w = (int)((nw + 255) / 256);
     if (grid_w > 65535) grid_w = 65535;
     sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
-    k_corner_weights<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+    k_corner_weights<double><<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
                                              plan->lattice_unit, w);
     SG_CUDA_TRY(cudaGetLastError());
     sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
@@ -925,7 +926,7 @@ sg_status cross_potential_f64(sg_plan *plan, const sg_workspace *ws, const doubl
     int grid_w = (int)((nw + 255) / 256);
     if (grid_w > 65535) grid_w = 65535;
     sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
-    k_corner_weights<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+    k_corner_weights<double><<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
                                              plan->lattice_unit, w);
     SG_CUDA_TRY(cudaGetLastError());
     sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
@@ -977,6 +978,134 @@ sg_status cross_potential_f32(sg_plan *plan, const sg_workspace *ws, const float
     return SG_OK;
 }
 
+// ============================================================ off plane ====
+//
+// Targets at height z != 0 above the plane of the sources (Section 2's kernels
+// with R = sqrt(u^2 + v^2 + z^2)): the corner form with the off-plane
+// antiderivatives, in FP64 for plans of either precision. With the corner
+// weights A_c(t), X_c, Y_c as in the plane,
+//   Fx(t) = G sum_c [ -A_c G0 + X_c (v G0y - |z| T) - Y_c R ]
+//   Fy(t) = G sum_c [ -A_c G0y + Y_c (u G0 - |z| T) - X_c R ]
+//   Fz(t) = G sum_c [ -sgn(z) A_c T + z (X_c G0 + Y_c G0y) ]
+// G0 = asinh(v / rho_u), rho_u = sqrt(u^2 + z^2), G0y = asinh(u / rho_v),
+// T = atan(u v / (|z| R)): the x-family kernels K^{x,0} = -dd G0,
+// K^{x,x} = -m K^{x,0} + dd[v G0y] - |z| dd T, K^{x,y} = -n K^{x,0} - dd R, and
+// K^{z,0} = -sgn(z) dd T, K^{z,x} = -m K^{z,0} - z K^{x,0} (y-family by
+// symmetry), the -m, -n terms folded into A_c(t). R >= |z| > 0: no coincident
+// lines. asinh(v / rho) = sgn(v) (ln(|v| + R) - ln rho), rho per corner column
+// (row) of the tile.
+
+// grid (nblocks, nsplit); one leaf target per thread; partial[(split, target)][3].
+__global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_direct_z(
+    const sg_target_block *__restrict__ blocks, const int4 *__restrict__ targets, const sg_tile_desc *__restrict__ tiles,
+    int ntiles, const double *__restrict__ wts, int nsplit, double G, double zl, double *__restrict__ partial,
+    int ntargets)
+{
+    __shared__ sg_dvec4 sw[SG_TILE_N];
+    const sg_target_block blk = blocks[blockIdx.x];
+    const int split = blockIdx.y;
+    const int t0 = (int)((int64_t)ntiles * split / nsplit);
+    const int t1 = (int)((int64_t)ntiles * (split + 1) / nsplit);
+    const bool active = threadIdx.x < blk.count;
+    int4 tg = make_int4(0, 0, -1, -1);
+    if (active) tg = targets[blk.first + threadIdx.x];
+    const double az = fabs(zl), z2 = zl * zl, sz = zl > 0.0 ? 1.0 : -1.0;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    const sg_dvec4 *wv = reinterpret_cast<const sg_dvec4 *>(wts);
+    for (int t = t0; t < t1; ++t) {
+        const sg_tile_desc td = tiles[t];
+        if (td.patch == blk.patch) continue;  // same-patch pairs come from the FFT
+        __syncthreads();
+        for (int k = threadIdx.x; k < SG_TILE_N; k += SG_DIRECT_THREADS) sw[k] = wv[(int64_t)t * SG_TILE_N + k];
+        __syncthreads();
+        const double du0 = (double)(td.ox - tg.x), dv0 = (double)(td.oy - tg.y), st = (double)td.step;
+        const double dxT = (double)(tg.x - td.ox), dyT = (double)(tg.y - td.oy);
+        double Lu[SG_TILE_X];
+#pragma unroll
+        for (int c = 0; c < SG_TILE_X; ++c) {
+            const double u = fma((double)c, st, du0);
+            Lu[c] = 0.5 * log(fma(u, u, z2));  // ln rho_u
+        }
+        double sx = 0.0, sy = 0.0, sz3 = 0.0;
+#pragma unroll 1
+        for (int r = 0; r < SG_TILE_Y; ++r) {
+            const double v = fma((double)r, st, dv0);
+            const double av = fabs(v), v2z = fma(v, v, z2);
+            const double Lv = 0.5 * log(v2z);  // ln rho_v
+#pragma unroll 2
+            for (int c = 0; c < SG_TILE_X; ++c) {
+                const sg_dvec4 wc = sw[r * SG_TILE_X + c];
+                const double u = fma((double)c, st, du0);
+                const double R = sqrt(fma(u, u, v2z));
+                const double ta = log(av + R) - Lu[c];
+                const double tb = log(fabs(u) + R) - Lv;
+                const double g0 = v > 0.0 ? ta : (v < 0.0 ? -ta : 0.0);
+                const double g0y = u > 0.0 ? tb : (u < 0.0 ? -tb : 0.0);
+                const double T = atan(u * v / (az * R));
+                const double A = fma(dxT, wc.y, fma(dyT, wc.z, wc.x));
+                sx += fma(-A, g0, fma(wc.y, fma(v, g0y, -az * T), -wc.z * R));
+                sy += fma(-A, g0y, fma(wc.z, fma(u, g0, -az * T), -wc.y * R));
+                sz3 += fma(-sz * A, T, zl * fma(wc.y, g0, wc.z * g0y));
+            }
+        }
+        fx += sx;
+        fy += sy;
+        fz += sz3;
+    }
+    if (!active) return;
+    double *o = partial + ((int64_t)split * ntargets + blk.first + threadIdx.x) * 3;
+    o[0] = G * fx;
+    o[1] = G * fy;
+    o[2] = G * fz;
+}
+
+// Fixed-order sum of the splits, added into the outputs.
+template <typename T>
+__global__ void k_cross_reduce_z(const int4 *__restrict__ targets, int ntargets, int nsplit,
+                                 const double *__restrict__ partial, T *__restrict__ fx, T *__restrict__ fy,
+                                 T *__restrict__ fz)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntargets; t += gridDim.x * blockDim.x) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int s = 0; s < nsplit; ++s) {
+            const double *q = partial + ((int64_t)s * ntargets + t) * 3;
+            a += q[0];
+            b += q[1];
+            c += q[2];
+        }
+        const int o = targets[t].z;
+        fx[o] = (T)((double)fx[o] + a);
+        fy[o] = (T)((double)fy[o] + b);
+        if (fz) fz[o] = (T)((double)fz[o] + c);  // sg_force on such a plan returns Fx, Fy only
+    }
+}
+
+template <typename T>
+sg_status cross_solve_z(sg_plan *plan, const sg_workspace *ws, const T *sigma, const T *dx, const T *dy, T *fx,
+                        T *fy, T *fz, cudaStream_t st)
+{
+    double *w = (double *)ws->tile_w;
+    const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
+    int grid_w = (int)((nw + 255) / 256);
+    if (grid_w > 65535) grid_w = 65535;
+    sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
+    k_corner_weights<T><<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+                                                plan->lattice_unit, w);
+    SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_DIRECT, st);
+    dim3 grid(plan->nblocks, plan->nsplit);
+    k_cross_direct_z<<<grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->targets, plan->tiles, plan->ntiles, w,
+                                                         plan->nsplit, plan->geom.G, plan->geom.z / plan->lattice_unit,
+                                                         ws->partial, plan->ntargets);
+    SG_CUDA_TRY(cudaGetLastError());
+    k_cross_reduce_z<T><<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets, plan->nsplit,
+                                                                       ws->partial, fx, fy, fz);
+    SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_DIRECT, st);
+    return SG_OK;
+}
+
 }  // namespace
 
 sg_status sg_cross_far_grid(sg_plan *plan, int nsm)
@@ -992,9 +1121,16 @@ sg_status sg_cross_far_grid(sg_plan *plan, int nsm)
 }
 
 sg_status sg_cross_solve(sg_plan *plan, const sg_workspace *ws, const void *sigma, const void *dx, const void *dy,
-                         void *fx, void *fy, cudaStream_t st)
+                         void *fx, void *fy, void *fz, cudaStream_t st)
 {
     if (plan->ntiles == 0 || plan->ntargets == 0) return SG_OK;
+    if (plan->geom.z != 0.0) {
+        if (plan->prec == SG_FP64)
+            return cross_solve_z<double>(plan, ws, (const double *)sigma, (const double *)dx, (const double *)dy,
+                                         (double *)fx, (double *)fy, (double *)fz, st);
+        return cross_solve_z<float>(plan, ws, (const float *)sigma, (const float *)dx, (const float *)dy, (float *)fx,
+                                    (float *)fy, (float *)fz, st);
+    }
     if (plan->prec == SG_FP64)
         return cross_solve_f64(plan, ws, (const double *)sigma, (const double *)dx, (const double *)dy, (double *)fx,
                                (double *)fy, st);

@@ -123,5 +123,5 @@ def test_masked_patch_rules(lib):
     assert "absent parent" in sg.last_error()
     # central slopes on a masked patch: the neighbour-leaf rule (absent cells count as outside)
     assert sg.sg_geom_validate([base], masks=[hole], slope_mode=sg.SG_SLOPES_CENTRAL) == sg.SG_OK
-    assert sg.sg_geom_validate([base], masks=[hole], z=0.1) == sg.SG_EINVAL
+    assert sg.sg_geom_validate([base], masks=[hole], z=0.1) == sg.SG_OK  # off the plane: the direct path
     assert sg.sg_geom_validate([base], masks=[np.zeros((8, 8))]) == sg.SG_EINVAL  # no leaf at all
