@@ -17,8 +17,11 @@
  * a uniform grid; several patches on refinement levels 0, 1, 2, ... (ratio 2,
  * Section 3 and Fig. 1) form an AMR hierarchy whose leaves are the cells not
  * covered by a patch of the next level. Pairs of cells in the same patch are
- * summed as a zero-padded FFT convolution; pairs in different patches by a
- * direct sum over cell corners. Both give the sum above to rounding.
+ * summed as a zero-padded FFT convolution; pairs in different patches either
+ * by level convolutions (every level on the finest lattice, fractional-offset
+ * kernel tables) or by a direct sum (the corner form in FP64; in FP32 plans
+ * FP64 near cells and a cell-centred expansion of far cells). All give the sum
+ * above to rounding.
  *
  * Conventions
  *  - Every entry point returns an sg_status; no exception or signal crosses
@@ -86,28 +89,33 @@ typedef struct {
     double G;                   /* gravitational constant */
     int slope_mode;             /* an sg_slope_mode */
     double z;                   /* height of the targets above the disk plane; 0 = in the plane.
-                                   z != 0 (off-plane forces, Section 2 with the arctan terms)
-                                   needs a single patch and sg_force3 */
+                                   z != 0 (off-plane forces, Section 2 with the arctan terms;
+                                   sg_force3): one patch, or a hierarchy on the direct-sum path
+                                   (level convolutions are for z == 0) */
     const uint8_t *const *masks; /* NULL, or one entry per patch: NULL (every cell of the patch
                                    exists) or nx*ny bytes, row-major, nonzero where the cell
                                    exists. Cells that do not exist carry no density and get no
                                    force (quadtree hierarchies, where a refined region is not a
                                    rectangle). Rules: on a refined patch existing cells come in
                                    whole 2 x 2 blocks over an existing parent cell; a parent
-                                   cell with children is not a leaf. Not with z != 0 or
-                                   SG_SLOPES_CENTRAL. Read during sg_plan_create only. */
+                                   cell with children is not a leaf. With SG_SLOPES_CENTRAL the
+                                   neighbour-leaf rule applies (absent cells count as outside).
+                                   Read during sg_plan_create only. */
     int cross_mode;             /* an sg_cross_mode: how pairs of cells in different patches
                                    (and, with level convolutions, all pairs) are summed */
 } sg_geom;
 
 typedef enum {
     SG_CROSS_AUTO = 0,          /* level convolutions when the hierarchy fits, else direct */
-    SG_CROSS_DIRECT = 1,        /* per-patch FFT convolutions + corner-form direct sum across patches */
+    SG_CROSS_DIRECT = 1,        /* per-patch FFT convolutions + the direct sum across patches (corner
+                                   form in FP64 plans and off the plane; FP64 near cells and a
+                                   far-field expansion in FP32 plans) */
     SG_CROSS_LEVELS = 2         /* level convolutions (SG_EINVAL if the hierarchy does not fit):
                                    every level's composite source on the finest lattice, every
                                    ordered pair of levels one zero-padded FFT convolution with
                                    fractional-offset kernel tables; needs a finest-lattice
-                                   extent of at most 2048 cells per axis and z == 0 */
+                                   extent of at most 4096 cells per axis (2048 in FP64 plans)
+                                   and z == 0 */
 } sg_cross_mode;
 
 typedef struct {
@@ -198,10 +206,13 @@ sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const v
 
 /*
  * Fx, Fy and Fz (enqueued on `stream`, buffers as for sg_force plus fz).
- * For a plan with z != 0 (one patch) the targets are the points (xc, yc, z)
- * above the cell centres and all three components come from the off-plane cell
+ * For a plan with z != 0 the targets are the points (xc, yc, z) above the leaf
+ * cell centres and all three components come from the off-plane cell
  * integrals (Section 2): K^{z,0} = integral of (zbar - z)/r^3 = -dd atan(uv/(z r)),
- * K^{z,x} = (x - xc) K^{z,0} - z K^{x,0}, K^{z,y} = (y - yc) K^{z,0} - z K^{y,0}.
+ * K^{z,x} = (x - xc) K^{z,0} - z K^{x,0}, K^{z,y} = (y - yc) K^{z,0} - z K^{y,0};
+ * a hierarchy (or masked patch) takes each patch's own convolution with its
+ * height-z tables plus the cross-patch sum in the corner form of the off-plane
+ * antiderivatives, evaluated in FP64 for plans of either precision.
  * For a z = 0 plan Fx, Fy are those of sg_force and Fz is the limit from
  * above the plane, -2 pi G sigma0 of the target's own cell (the other cells'
  * normal forces vanish in the plane). Errors: as sg_force.

@@ -637,7 +637,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         use_lv = lv_params(g, gi, prec, lva, lvmaps, lv_bytes);
         if (!use_lv) lv_bytes = -1;
         if (!use_lv && g->cross_mode == SG_CROSS_LEVELS)
-            return fail("level convolutions need z == 0, no central slopes and a finest-lattice extent of at most "
+            return fail("level convolutions need z == 0 and a finest-lattice extent of at most "
                         "4096 cells per axis (2048 for FP64 plans)");
     }
     std::vector<sg_tile_desc> tiles;
