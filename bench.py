@@ -187,6 +187,18 @@ def workload_offplane():
     return wl
 
 
+def workload_offplane_amr3():
+    """The config-3 hierarchy (3 x 256^2) with the targets one finest cell
+    width above the plane (Fx, Fy, Fz): each patch's own convolution with its
+    height-z tables plus the FP64 corner-form cross sum."""
+    wl = workload_amr3()
+    h = min(p[5] for p in wl["patches"])
+    wl["z"] = h
+    wl["name"] = wl["name"] + ", targets at z = finest h above the plane"
+    wl["config"] = dict(wl["config"], workload="amr3_exponential_offplane", z=h, outputs="Fx Fy Fz")
+    return wl
+
+
 def workload_nested(base, levels, r0=0.1):
     """Centred nested ratio-2 patches of base^2 cells each (the largest AMR
     request of the serving mix at base 512, 4 levels), sigma = exp(-R/r0)."""
@@ -228,6 +240,7 @@ def workload_ilr(n=512, levels=3, rule="ilr", disk="d2"):
 
 
 WORKLOADS = {"spiral1024": workload_spiral, "amr3": workload_amr3, "offplane": workload_offplane,
+             "offplane_amr3": workload_offplane_amr3,
              "ilr512": lambda: workload_ilr(512, 3, "ilr", "d2"), "ilr1024": lambda: workload_ilr(1024, 3, "ilr", "d2"),
              "ilr2048": lambda: workload_ilr(2048, 3, "ilr", "d2"),
              "amr4_512": lambda: workload_nested(512, 4)}
@@ -969,6 +982,10 @@ def run_gpu(args):
     stage_mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(stage_mean, key=stage_mean.get)
     hbm_peak, hbm_src, fp32_peak, fp32_src = _peaks()
+    alu_peak, alu_src = fp32_peak, fp32_src
+    if wl.get("precision", "fp32") == "fp64" and dom == "cross_direct":
+        alu_peak = _alu_peaks()["fp64_tflops"]
+        alu_src = "measured (sg_alu_peak: FP64 FMA on every SM, best of 5): an FP64 plan's cross sum"
     info = plan.info
     alg = algorithmic_bytes(wl, info, dom, nout=1 if pot else 2)
     flops = algorithmic_flops(wl, info, dom, nout=1 if pot else 2)
@@ -992,9 +1009,9 @@ def run_gpu(args):
                        "cross_mode": fp64_path, "note": fp64_note},
         "rel_err_vs_fp64": rel_err,
         "stage_ms": stage_mean,
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": tflops / fp32_peak, "traffic": TRAFFIC.get((args.workload, dom)),
-                     "algorithmic_flops": flops, "peak_source": fp32_src, "alu_peaks": _alu_peaks(),
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": tflops / alu_peak, "traffic": TRAFFIC.get((args.workload, dom)),
+                     "algorithmic_flops": flops, "peak_source": alu_src, "alu_peaks": _alu_peaks(),
                      "hbm": {"algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": hbm_peak,
                              "frac": gbs / hbm_peak, "peak_source": hbm_src}},
         "e2e": ({"value": args.steps * world / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -1153,6 +1170,10 @@ def algorithmic_flops(wl, info, stage, nout=2):
         # through p^3); FP64 plans: 28 per target-corner pair
         fp32 = wl.get("precision", "fp32") == "fp32"
         total = (30.0 if nout == 2 else 16.0) if fp32 else 28.0
+        if wl.get("z"):
+            # off the plane: FP32 plans 2 x 2 Gauss nodes per far pair at 16 flops each
+            # (3 x 3 within SG_FAR_R4 cells); FP64 plans the corner form, 36 per target-corner pair
+            total = 64.0 if fp32 else 36.0
         total *= info["cross_pairs"]
     return total
 

@@ -538,10 +538,11 @@ sizes plan_sizes(const sg_geom *g, const geom_info &gi, sg_precision prec, int n
     if (gi.n > 1 || gi.masked) s.direct = 3 * gi.ncells * (int64_t)es + gi.ncells * (int64_t)sizeof(int);
     if ((gi.n > 1 || gi.masked) && g->slope_mode == SG_SLOPES_CENTRAL) s.direct += 40 * gi.ncells;  // links, centres
     if (gi.n > 1 && lv_bytes < 0) {
-        // off the plane: FP64 corner weights and three partial components per split
+        // off the plane: three partial components per split (and the near field in FP32 plans)
         const bool off = g->z != 0.0;
-        const int64_t slices = off ? (int64_t)nsplit * 3 / 2 + 1 : (prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1);
-        s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)(off ? 8 : es)) +
+        const int64_t slices = off ? ((int64_t)nsplit + (prec == SG_FP32 ? 1 : 0)) * 3 / 2 + 1
+                                   : (prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1);
+        s.direct += (int64_t)ntiles * ((int64_t)sizeof(sg_tile_desc) + SG_TILE_N * 4 * (int64_t)es) +
                     gi.nleaves * (int64_t)sizeof(int4) + (int64_t)nblocks * (int64_t)sizeof(sg_target_block) +
                     slices * gi.nleaves * 16;
     }
@@ -642,8 +643,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
     }
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tfirst, tcount;
-    // corner tiles for the corner form (FP64 plans, and every plan off the plane), cell tiles otherwise
-    const bool corner_form = prec == SG_FP64 || g->z != 0.0;
+    // corner tiles for the corner form (FP64 plans), cell tiles for the FP32 far field
+    const bool corner_form = prec == SG_FP64;
     if (gi.n > 1 && !use_lv) build_tiles(g, gi, !corner_form, tiles, tfirst, tcount);
     int dev = 0, nsm = 152;
     SG_CUDA_TRY(cudaGetDevice(&dev));
@@ -790,8 +791,8 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
             st = cudaMemcpy(plan->tiles, tiles.data(), tiles.size() * sizeof(sg_tile_desc), cudaMemcpyHostToDevice) ==
                          cudaSuccess ? SG_OK : SG_ECUDA;
         const size_t nw = (size_t)plan->ntiles * SG_TILE_N;
-        // FP64 corner weights (FP64 plans, and every plan off the plane), FP32 cell coefficients otherwise
-        const bool wide = prec == SG_FP64 || g->z != 0.0;
+        // FP64 corner weights (FP64 plans), FP32 cell coefficients (FP32 plans)
+        const bool wide = prec == SG_FP64;
         plan->ws_tile_bytes = (int64_t)nw * (wide ? (int64_t)sizeof(sg_dvec4) : (int64_t)sizeof(float4));
         // targets: every leaf, in blocks of the leaves of 16 x 16 cells
         std::vector<int4> tg;
@@ -809,9 +810,10 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
                             cudaMemcpyHostToDevice) == cudaSuccess ? SG_OK : SG_ECUDA;
         const int64_t slices = prec == SG_FP64 ? (nsplit > 1 ? nsplit : 0) : nsplit + 1;
         plan->ws_partial_bytes = slices * (int64_t)tg.size() * 2 * (int64_t)sizeof(double);
-        if (g->z != 0.0)  // off the plane: three components per split, both precisions
-            plan->ws_partial_bytes = (int64_t)nsplit * (int64_t)tg.size() * 3 * (int64_t)sizeof(double);
-        if (st == SG_OK && prec == SG_FP32 && g->z == 0.0) st = sg_cross_far_grid(plan, nsm);
+        if (g->z != 0.0)  // off the plane: three components per split (FP32: and one slice for the near field)
+            plan->ws_partial_bytes =
+                ((int64_t)nsplit + (prec == SG_FP32 ? 1 : 0)) * (int64_t)tg.size() * 3 * (int64_t)sizeof(double);
+        if (st == SG_OK && prec == SG_FP32) st = sg_cross_far_grid(plan, nsm);
     }
     if (st == SG_OK) st = sg_twiddles_build(plan);
     if (st == SG_OK) st = sg_phase_build(plan);
@@ -1014,7 +1016,7 @@ sg_status sg_plan_bytes(const sg_geom *geom, sg_precision prec, int64_t *bytes)
         lv_bytes = -1;
     std::vector<sg_tile_desc> tiles;
     std::vector<int> tf, tc;
-    const bool corner_form = prec == SG_FP64 || geom->z != 0.0;
+    const bool corner_form = prec == SG_FP64;
     if (gi.n > 1 && lv_bytes < 0) build_tiles(geom, gi, !corner_form, tiles, tf, tc);
     const int nblocks = lv_bytes < 0 ? count_blocks(geom, gi) : 0;
     const int nsplit = choose_nsplit(nblocks, (int)tiles.size(), 152, corner_form ? SG_FP64 : prec);

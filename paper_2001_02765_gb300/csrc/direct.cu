@@ -981,9 +981,10 @@ sg_status cross_potential_f32(sg_plan *plan, const sg_workspace *ws, const float
 // ============================================================ off plane ====
 //
 // Targets at height z != 0 above the plane of the sources (Section 2's kernels
-// with R = sqrt(u^2 + v^2 + z^2)): the corner form with the off-plane
-// antiderivatives, in FP64 for plans of either precision. With the corner
-// weights A_c(t), X_c, Y_c as in the plane,
+// with R = sqrt(u^2 + v^2 + z^2)): FP64 plans sum every pair in the corner form
+// with the off-plane antiderivatives; FP32 plans use it for the near cells and
+// Gauss-Legendre quadrature of the cell integrals for the far cells (below).
+// With the corner weights A_c(t), X_c, Y_c as in the plane,
 //   Fx(t) = G sum_c [ -A_c G0 + X_c (v G0y - |z| T) - Y_c R ]
 //   Fy(t) = G sum_c [ -A_c G0y + Y_c (u G0 - |z| T) - X_c R ]
 //   Fz(t) = G sum_c [ -sgn(z) A_c T + z (X_c G0 + Y_c G0y) ]
@@ -1080,6 +1081,275 @@ __global__ void k_cross_reduce_z(const int4 *__restrict__ targets, int ntargets,
     }
 }
 
+// FP32 plans off the plane: near cells (k_cross_far's near box) in the FP64
+// corner form above, far cells by tensor Gauss-Legendre quadrature of the cell
+// integrals of (m + deltax H xi + deltay H eta) (a + xi, b + eta, -zeta) / R^3
+// over the unit cell (a, b = centre minus target, zeta = z, in cell widths):
+// 3 x 3 nodes from SG_NEAR_R cell widths on (relative error below 3e-7 there,
+// from the sixth derivative of the kernel), 2 x 2 from SG_FAR_R4 on (below 1e-6),
+// in FP32 per tile and FP64 across tiles like the in-plane far field.
+template <int NG>
+__device__ __forceinline__ void cell_far_z(float a, float b, float zeta2, float4 c, float &qx, float &qy, float &qz)
+{
+    // nodes on [-1/2, 1/2] and weights summing to 1
+    constexpr float X3 = 0.387298334620742f, W3a = 5.f / 18.f, W3b = 8.f / 18.f;
+    constexpr float X2 = 0.288675134594813f;
+    float sx = 0.f, sy = 0.f, s0 = 0.f;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const float xi = NG == 3 ? (i == 0 ? -X3 : (i == 1 ? 0.f : X3)) : (i == 0 ? -X2 : X2);
+        const float wi = NG == 3 ? (i == 1 ? W3b : W3a) : 0.5f;
+        const float da = a + xi;
+        const float da2z = fmaf(da, da, zeta2);
+#pragma unroll
+        for (int j = 0; j < NG; ++j) {
+            const float eta = NG == 3 ? (j == 0 ? -X3 : (j == 1 ? 0.f : X3)) : (j == 0 ? -X2 : X2);
+            const float wj = NG == 3 ? (j == 1 ? W3b : W3a) : 0.5f;
+            const float db = b + eta;
+            const float ir = rsqrtf(fmaf(db, db, da2z));
+            // density at the node (c.y, c.z = deltax H / 8, deltay H / 8) times weight / R^3
+            const float w = wi * wj * fmaf(8.f * c.y, xi, fmaf(8.f * c.z, eta, c.x)) * (ir * ir * ir);
+            sx = fmaf(w, da, sx);
+            sy = fmaf(w, db, sy);
+            s0 += w;
+        }
+    }
+    qx += sx;
+    qy += sy;
+    qz += s0;  // times -zeta by the caller
+}
+
+template <int NG, bool MASK>
+__device__ __forceinline__ void tile_far_z(const float4 *__restrict__ w, float a0, float b0, float zeta, double &ax,
+                                           double &ay, double &az)
+{
+    float qx = 0.f, qy = 0.f, qz = 0.f;
+    const float zeta2 = zeta * zeta;
+#pragma unroll 1
+    for (int r = 0; r < SG_TILE_Y; ++r) {
+        const float b = b0 + (float)r;
+        const bool bnear = fabsf(b) < (float)SG_NEAR_R;
+#pragma unroll 2
+        for (int c = 0; c < SG_TILE_X; ++c) {
+            const float a = a0 + (float)c;
+            if (MASK && bnear && fabsf(a) < (float)SG_NEAR_R) continue;
+            cell_far_z<NG>(a, b, zeta2, w[r * SG_TILE_X + c], qx, qy, qz);
+        }
+    }
+    ax += qx;
+    ay += qy;
+    az += (double)(-zeta) * (double)qz;
+}
+
+// Persistent far field off the plane (k_cross_far's items, staging, waits);
+// partial[(split, target)][3].
+__global__ void __launch_bounds__(SG_DIRECT_THREADS) k_cross_far_z(
+    const sg_target_block *__restrict__ blocks, int nblocks, const int4 *__restrict__ targets,
+    const sg_tile_desc *__restrict__ tiles, const sg_patch_dev *__restrict__ pd, int ntiles,
+    const float4 *__restrict__ coefs, int nsplit, double G, double zl, double *__restrict__ partial, int ntargets,
+    int *__restrict__ words, int tries)
+{
+    __shared__ __align__(128) float4 buf[FAR_STAGES][SG_TILE_N];
+    __shared__ uint64_t full[FAR_STAGES];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        for (int s = 0; s < FAR_STAGES; ++s) mbar_init(&full[s], 1);
+    __syncthreads();
+    uint32_t used = 0, issued = 0;
+    const int nitems = nblocks * nsplit;
+    bool failed = false;
+    while (!failed) {
+        if (tid == 0) s_item = atomicAdd(&words[1], 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int bi = item / nsplit, split = item - bi * nsplit;
+        const sg_target_block blk = blocks[bi];
+        const int t0 = (int)((int64_t)ntiles * split / nsplit), t1 = (int)((int64_t)ntiles * (split + 1) / nsplit);
+        const int own0 = pd[blk.patch].tile_first, own1 = own0 + pd[blk.patch].tile_count;
+        const int n1 = max(0, min(t1, own0) - t0), s2 = max(t0, own1);
+        const int n = n1 + max(0, t1 - s2);
+        const bool active = tid < blk.count;
+        const int4 tg = targets[blk.first + (active ? tid : 0)];
+        if (tid == 0) {
+            for (int k = 0; k < n && k < FAR_STAGES; ++k, ++issued) {
+                const int stg = issued % FAR_STAGES;
+                const int t = k < n1 ? t0 + k : s2 + (k - n1);
+                mbar_arrive_expect_tx(&full[stg], TILE_BYTES);
+                bulk_copy_g2s(buf[stg], coefs + (int64_t)t * SG_TILE_N, TILE_BYTES, &full[stg]);
+            }
+        }
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int k = 0; k < n; ++k, ++used) {
+            const int stg = used % FAR_STAGES;
+            const int t = k < n1 ? t0 + k : s2 + (k - n1);
+            const bool ok = mbar_wait_bounded(&full[stg], (used / FAR_STAGES) & 1, tries);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const sg_tile_desc td = tiles[t];
+            const int cx0 = td.ox + td.step / 2, cx1 = cx0 + (SG_TILE_X - 1) * td.step;
+            const int cy0 = td.oy + td.step / 2, cy1 = cy0 + (SG_TILE_Y - 1) * td.step;
+            const int gx = max(0, max(cx0 - blk.tx1, blk.tx0 - cx1));
+            const int gy = max(0, max(cy0 - blk.ty1, blk.ty0 - cy1));
+            const int gap = max(gx, gy);
+            const float inv = 1.0f / (float)td.step;
+            const float a0 = (float)(td.ox - tg.x) * inv + 0.5f, b0 = (float)(td.oy - tg.y) * inv + 0.5f;
+            const float zeta = (float)(zl / (double)td.step);  // the height in the tile's cell widths
+            if (gap >= SG_FAR_R4 * td.step) tile_far_z<2, false>(buf[stg], a0, b0, zeta, ax, ay, az);
+            else if (gap >= SG_NEAR_R * td.step) tile_far_z<3, false>(buf[stg], a0, b0, zeta, ax, ay, az);
+            else tile_far_z<3, true>(buf[stg], a0, b0, zeta, ax, ay, az);
+            __syncthreads();
+            if (tid == 0 && k + FAR_STAGES < n) {
+                const int kk = k + FAR_STAGES;
+                const int tn = kk < n1 ? t0 + kk : s2 + (kk - n1);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_expect_tx(&full[stg], TILE_BYTES);
+                bulk_copy_g2s(buf[stg], coefs + (int64_t)tn * SG_TILE_N, TILE_BYTES, &full[stg]);
+                ++issued;
+            }
+        }
+        if (failed) break;
+        if (active) {
+            double *o = partial + ((int64_t)split * ntargets + blk.first + tid) * 3;
+            o[0] = G * ax;
+            o[1] = G * ay;
+            o[2] = G * az;
+        }
+    }
+    if (failed && tid == 0) {
+        atomicExch(&words[0], 1);
+        for (uint32_t g = used; g < issued; ++g) mbar_wait_bounded(&full[g % FAR_STAGES], (g / FAR_STAGES) & 1, SG_MBAR_MAX_TRIES);
+    }
+}
+
+// Near cells off the plane in FP64: k_cross_near's boxes and warp reduction
+// with the off-plane corner form; writes slice nsplit of partial[.][3].
+__global__ void __launch_bounds__(NEAR_WARPS * 32) k_cross_near_z(const int4 *__restrict__ targets, int ntargets,
+                                                                 const sg_patch_dev *__restrict__ pd, int npatches,
+                                                                 const float *__restrict__ sigma,
+                                                                 const float *__restrict__ dx,
+                                                                 const float *__restrict__ dy, double lambda,
+                                                                 double G, double z, double *__restrict__ near_out)
+{
+    __shared__ double cellv[NEAR_WARPS][3][NEAR_SLOTS];
+    const int lane = threadIdx.x & 31;
+    double *cl = cellv[threadIdx.x >> 5][0], *cx = cellv[threadIdx.x >> 5][1], *cy = cellv[threadIdx.x >> 5][2];
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+    const double az = fabs(z), z2 = z * z, sz = z > 0.0 ? 1.0 : -1.0;
+    for (int t = warp; t < ntargets; t += nwarps) {
+        const int4 tg = targets[t];
+        double fx = 0.0, fy = 0.0, fzs = 0.0;
+        for (int q = 0; q < npatches; ++q) {
+            if (q == tg.w) continue;
+            const sg_patch_dev &p = pd[q];
+            const int64_t L = p.step, RL = (int64_t)SG_NEAR_R * L;
+            const int64_t ex = (int64_t)tg.x - p.ox - L / 2, ey = (int64_t)tg.y - p.oy - L / 2;
+            const int i0 = max(0, floor_div(ex - RL, L) + 1), j0 = max(0, floor_div(ey - RL, L) + 1);
+            const int i1 = min(p.nx - 1, -floor_div(-(ex + RL), L) - 1);
+            const int j1 = min(p.ny - 1, -floor_div(-(ey + RL), L) - 1);
+            if (i0 > i1 || j0 > j1) continue;
+            const int nbx = i1 - i0 + 1, nby = j1 - j0 + 1, W = nbx + 2;
+            __syncwarp();  // the previous box's values have been read
+            for (int k = lane; k < W * (nby + 2); k += 32) {
+                const int bi = k % W - 1, bj = k / W - 1;
+                double l = 0.0, X = 0.0, Y = 0.0;
+                if (bi >= 0 && bi < nbx && bj >= 0 && bj < nby) {
+                    const int i = i0 + bi, j = j0 + bj;
+                    const int64_t o = p.cell_off + (int64_t)j * p.nx + i;
+                    X = dx[o];
+                    Y = dy[o];
+                    const double ux = ((double)tg.x - ((double)p.ox + (i + 0.5) * (double)L)) * lambda;
+                    const double uy = ((double)tg.y - ((double)p.oy + (j + 0.5) * (double)L)) * lambda;
+                    l = fma(X, ux, fma(Y, uy, (double)sigma[o]));
+                }
+                cl[k] = l;
+                cx[k] = X;
+                cy[k] = Y;
+            }
+            // ln rho_u of corner column ci and ln rho_v of corner row cj in lanes
+            const double uc = ((double)p.ox + (double)(i0 + lane) * L - tg.x) * lambda;
+            const double vc = ((double)p.oy + (double)(j0 + lane) * L - tg.y) * lambda;
+            const double lnu = lane <= nbx ? 0.5 * log(fma(uc, uc, z2)) : 0.0;
+            const double lnv = lane <= nby ? 0.5 * log(fma(vc, vc, z2)) : 0.0;
+            __syncwarp();
+            const int nci = nbx + 1, ncorner = nci * (nby + 1);
+            for (int base = 0; base < ncorner; base += 32) {
+                const int k = base + lane;
+                const bool valid = k < ncorner;
+                const int kk = valid ? k : 0;
+                const int ci = kk % nci, cj = kk / nci;
+                const double Lu = __shfl_sync(0xffffffffu, lnu, ci);
+                const double Lv = __shfl_sync(0xffffffffu, lnv, cj);
+                if (!valid) continue;
+                const int s00 = cj * W + ci, s10 = s00 + 1, s01 = s00 + W, s11 = s01 + 1;
+                const double A = (cl[s00] - cl[s10]) - (cl[s01] - cl[s11]);
+                const double X = (cx[s00] - cx[s10]) - (cx[s01] - cx[s11]);
+                const double Y = (cy[s00] - cy[s10]) - (cy[s01] - cy[s11]);
+                const double u = ((double)p.ox + (double)(i0 + ci) * L - tg.x) * lambda;
+                const double v = ((double)p.oy + (double)(j0 + cj) * L - tg.y) * lambda;
+                const double R = sqrt(fma(u, u, fma(v, v, z2)));
+                const double ta = log(fabs(v) + R) - Lu, tb = log(fabs(u) + R) - Lv;
+                const double g0 = v > 0.0 ? ta : (v < 0.0 ? -ta : 0.0);
+                const double g0y = u > 0.0 ? tb : (u < 0.0 ? -tb : 0.0);
+                const double T = atan(u * v / (az * R));
+                fx += fma(-A, g0, fma(X, fma(v, g0y, -az * T), -Y * R));
+                fy += fma(-A, g0y, fma(Y, fma(u, g0, -az * T), -X * R));
+                fzs += fma(-sz * A, T, z * fma(X, g0, Y * g0y));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, off);
+            fy += __shfl_xor_sync(0xffffffffu, fy, off);
+            fzs += __shfl_xor_sync(0xffffffffu, fzs, off);
+        }
+        if (lane == 0) {
+            near_out[(int64_t)t * 3 + 0] = G * fx;
+            near_out[(int64_t)t * 3 + 1] = G * fy;
+            near_out[(int64_t)t * 3 + 2] = G * fzs;
+        }
+    }
+}
+
+sg_status cross_solve_z_f32(sg_plan *plan, const sg_workspace *ws, const float *sigma, const float *dx,
+                            const float *dy, float *fx, float *fy, float *fz, cudaStream_t st)
+{
+    float4 *w = (float4 *)ws->tile_w;
+    const int64_t nw = (int64_t)plan->ntiles * SG_TILE_N;
+    int grid_w = (int)((nw + 255) / 256);
+    if (grid_w > 65535) grid_w = 65535;
+    sg_timing_begin(ws, SG_STAGE_WEIGHTS, st);
+    k_cell_coefs<<<grid_w, 256, 0, st>>>(plan->tiles, plan->ntiles, plan->patch_dev, sigma, dx, dy,
+                                         plan->lattice_unit, w, ws->err + 1);
+    SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_WEIGHTS, st);
+    sg_timing_begin(ws, SG_STAGE_DIRECT, st);
+    k_cross_far_z<<<plan->far_grid, SG_DIRECT_THREADS, 0, st>>>(plan->blocks, plan->nblocks, plan->targets, plan->tiles,
+                                                                plan->patch_dev, plan->ntiles, w, plan->nsplit,
+                                                                plan->geom.G, plan->geom.z / plan->lattice_unit,
+                                                                ws->partial, plan->ntargets, ws->err,
+                                                                plan->wait_tries);
+    SG_CUDA_TRY(cudaGetLastError());
+    double *near = ws->partial + (int64_t)plan->nsplit * plan->ntargets * 3;
+    const int64_t nblk = ((int64_t)plan->ntargets + NEAR_WARPS - 1) / NEAR_WARPS;
+    const int grid_n = (int)(nblk < (1 << 20) ? nblk : (1 << 20));
+    k_cross_near_z<<<grid_n, NEAR_WARPS * 32, 0, st>>>(plan->targets, plan->ntargets, plan->patch_dev,
+                                                       plan->npatches, sigma, dx, dy, plan->lattice_unit,
+                                                       plan->geom.G, plan->geom.z, near);
+    SG_CUDA_TRY(cudaGetLastError());
+    // the splits and the near slice, in a fixed order
+    k_cross_reduce_z<float><<<(plan->ntargets + 255) / 256, 256, 0, st>>>(plan->targets, plan->ntargets,
+                                                                           plan->nsplit + 1, ws->partial, fx, fy, fz);
+    SG_CUDA_TRY(cudaGetLastError());
+    sg_timing_end(ws, SG_STAGE_DIRECT, st);
+    return SG_OK;
+}
+
 template <typename T>
 sg_status cross_solve_z(sg_plan *plan, const sg_workspace *ws, const T *sigma, const T *dx, const T *dy, T *fx,
                         T *fy, T *fz, cudaStream_t st)
@@ -1111,7 +1381,10 @@ sg_status cross_solve_z(sg_plan *plan, const sg_workspace *ws, const T *sigma, c
 sg_status sg_cross_far_grid(sg_plan *plan, int nsm)
 {
     int per_sm = 0;
-    SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cross_far, SG_DIRECT_THREADS, 0));
+    if (plan->geom.z != 0.0)
+        SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cross_far_z, SG_DIRECT_THREADS, 0));
+    else
+        SG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cross_far, SG_DIRECT_THREADS, 0));
     if (per_sm < 1) per_sm = 1;
     const int64_t items = (int64_t)plan->nblocks * plan->nsplit;
     int64_t g = (int64_t)nsm * per_sm;
@@ -1128,8 +1401,8 @@ sg_status sg_cross_solve(sg_plan *plan, const sg_workspace *ws, const void *sigm
         if (plan->prec == SG_FP64)
             return cross_solve_z<double>(plan, ws, (const double *)sigma, (const double *)dx, (const double *)dy,
                                          (double *)fx, (double *)fy, (double *)fz, st);
-        return cross_solve_z<float>(plan, ws, (const float *)sigma, (const float *)dx, (const float *)dy, (float *)fx,
-                                    (float *)fy, (float *)fz, st);
+        return cross_solve_z_f32(plan, ws, (const float *)sigma, (const float *)dx, (const float *)dy, (float *)fx,
+                                 (float *)fy, (float *)fz, st);
     }
     if (plan->prec == SG_FP64)
         return cross_solve_f64(plan, ws, (const double *)sigma, (const double *)dx, (const double *)dy, (double *)fx,
