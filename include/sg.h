@@ -108,8 +108,8 @@ typedef struct {
 typedef enum {
     SG_CROSS_AUTO = 0,          /* level convolutions when the hierarchy fits, else direct */
     SG_CROSS_DIRECT = 1,        /* per-patch FFT convolutions + the direct sum across patches (corner
-                                   form in FP64 plans and off the plane; FP64 near cells and a
-                                   far-field expansion in FP32 plans) */
+                                   form in FP64 plans; FP64 near cells and a far-field expansion,
+                                   or quadrature off the plane, in FP32 plans) */
     SG_CROSS_LEVELS = 2         /* level convolutions (SG_EINVAL if the hierarchy does not fit):
                                    every level's composite source on the finest lattice, every
                                    ordered pair of levels one zero-padded FFT convolution with
@@ -211,8 +211,9 @@ sg_status sg_force(sg_plan *plan, const void *sigma, const void *deltax, const v
  * integrals (Section 2): K^{z,0} = integral of (zbar - z)/r^3 = -dd atan(uv/(z r)),
  * K^{z,x} = (x - xc) K^{z,0} - z K^{x,0}, K^{z,y} = (y - yc) K^{z,0} - z K^{y,0};
  * a hierarchy (or masked patch) takes each patch's own convolution with its
- * height-z tables plus the cross-patch sum in the corner form of the off-plane
- * antiderivatives, evaluated in FP64 for plans of either precision.
+ * height-z tables plus the cross-patch sum: the corner form of the off-plane
+ * antiderivatives in FP64 (every pair in FP64 plans; the near cells in FP32
+ * plans, whose far cells take Gauss-Legendre quadrature of the cell integrals).
  * For a z = 0 plan Fx, Fy are those of sg_force and Fz is the limit from
  * above the plane, -2 pi G sigma0 of the target's own cell (the other cells'
  * normal forces vanish in the plane). Errors: as sg_force.
