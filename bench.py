@@ -648,6 +648,9 @@ def run_serve(args):
                        "mean": stats["latency_mean_ms"]},
         "capacity_solves_per_s": capacity, "offered_rate": rate, "load_sweep": sweep,
         "peak_bytes": stats["peak_bytes"],
+        "grouped": {"groups": stats["groups_started"], "requests": stats["grouped_requests"],
+                    "note": "queued single-patch requests of one padded length, precision and slope handling "
+                            "admitted together (one launch per pass over the group)"},
         "fp64_plain": {"solves_per_s": done64 / t64 if t64 else None, "requests": done64,
                        "left_out": left_out,
                        "note": "one solve at a time on a %.0f s prefix of the same stream; requests whose FP64 plan "

@@ -535,8 +535,13 @@ sg_status sg_batch_layout(const sg_batch *batch, int *mode, double *ms_persisten
  * (0 = no limit); each admitted request gets its own workspace from the
  * server's stream-ordered memory pool and runs on its slot's stream, so
  * requests arriving while others run start as slots and memory free up and
- * overlap on the device. Plans stay resident and may be shared by many
- * requests; a result is bit-for-bit the same alone and in any mix. Completion
+ * overlap on the device. When the head of the queue is a single in-plane
+ * patch, queued requests with the same padded lengths, precision and slope
+ * handling that fit the budget join it (up to the group limit, 16 by default):
+ * they run on its slot, each with its own workspace, and each pass of the
+ * convolution is one launch over all of them (the batches' grouped launches).
+ * Plans stay resident and may be shared by many requests; a result is
+ * bit-for-bit the same alone, grouped and in any mix. Completion
  * is observed on the host (a stream host function); nothing waits on the GPU.
  * The caller keeps the plan and the buffers alive until the request finished,
  * and must not destroy a plan with requests in flight. The server is
@@ -551,6 +556,8 @@ typedef struct {
     int64_t bytes_in_use, peak_bytes;
     int64_t latency_count;          /* completed requests the latencies cover */
     double latency_p50_ms, latency_p99_ms, latency_mean_ms;
+    uint64_t groups_started;        /* grouped admissions so far */
+    uint64_t grouped_requests;      /* requests run in them */
 } sg_server_stats;
 
 /* Create a server on the current device. max_inflight: 1..256 concurrent
@@ -559,6 +566,10 @@ sg_status sg_server_create(size_t hbm_budget, int max_inflight, sg_server **out)
 
 /* Cancel queued requests, wait for running ones, release everything. NULL is a no-op. */
 sg_status sg_server_destroy(sg_server *server);
+
+/* Most requests admitted together as one group (1..16; 1 admits every request
+ * alone). Applies to admissions from then on. Errors: SG_EINVAL. */
+sg_status sg_server_set_group_limit(sg_server *server, int max_members);
 
 /* Queue one solve; *ticket identifies it. SG_EBUDGET (rejected) if its workspace
  * alone exceeds the budget; SG_EINVAL for null pointers, missing caller slopes or

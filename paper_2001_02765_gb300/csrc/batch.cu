@@ -19,6 +19,7 @@
 // results bit for bit in either layout.
 #include "common.cuh"
 #include "batch_run.cuh"
+#include "group.cuh"
 
 #include <algorithm>
 #include <map>
@@ -153,27 +154,10 @@ sg_status persistent_upload(sg_batch *b, batch_graph &g, const std::vector<int> 
     return SG_OK;
 }
 
-// A member of a group: one in-plane patch (any length), no composite source.
-bool groupable(const sg_plan *p)
-{
-    return p->npatches == 1 && !p->composite && !p->lv && p->geom.z == 0.0;
-}
-
-// A group's passes: the members' arguments in one device array per pass.
-template <typename T>
-struct group_passes {
-    sgk::uniform_passes<T> u;  // lengths, shapes and twiddles are common to the group
-    const sgk::row_fwd_args<T> *rf = nullptr;
-    const sgk::edge_args<T> *ed = nullptr;
-    const sgk::col_args<T> *col = nullptr;
-    const sgk::row_inv_args<T> *ri = nullptr;
-    sgk::batch_shape bs = {0, 0};
-    int *err = nullptr;
-};
-
 // Upload the argument arrays of a group (owned by the layout); before capture.
 template <typename T>
-sg_status group_upload(batch_graph &bg, const std::vector<sgk::uniform_passes<T>> &us, int *err, group_passes<T> &g)
+sg_status group_upload(batch_graph &bg, const std::vector<sgk::uniform_passes<T>> &us, int *err,
+                       sgk::group_passes<T> &g)
 {
     const int m = (int)us.size();
     std::vector<sgk::row_fwd_args<T>> rf(m);
@@ -207,19 +191,6 @@ sg_status group_upload(batch_graph &bg, const std::vector<sgk::uniform_passes<T>
     return SG_OK;
 }
 
-// One launch per pass for all the group's members.
-template <typename T>
-sg_status group_enqueue(const group_passes<T> &g, cudaStream_t st)
-{
-    const sgk::uniform_passes<T> &u = g.u;
-    SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, g.rf, g.bs));
-    if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st, g.ed, g.bs));
-    if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, g.err, st, g.col, g.bs));
-    else SG_TRY(sgk::cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, g.err, st, g.col, g.bs));
-    SG_TRY(sgk::rows_inv<T>(u.px, u.shx[1], u.ri, u.nout, u.twx, st, g.ri, g.bs));
-    return SG_OK;
-}
-
 // The inputs of one batch creation.
 struct batch_inputs {
     int n;
@@ -248,12 +219,8 @@ sg_status capture_layout(sg_batch *b, const batch_inputs &in, bool persistent, i
             if (!persistent_member(p)) rest.push_back(i);
             else if (p->prec == SG_FP64) mem64.push_back(i);
             else mem32.push_back(i);
-        } else if (groupable(p)) {
-            // (precision, Px, Py, central slopes formed in the spectrum, fields of the row pass)
-            const bool central = p->geom.slope_mode == SG_SLOPES_CENTRAL && p->pp[0].phase;
-            groups[std::make_tuple((int)p->prec, p->pp[0].d.px, p->pp[0].d.py, central ? 1 : 0,
-                                   p->geom.slope_mode == SG_SLOPES_NONE ? 1 : 3)]
-                .push_back(i);
+        } else if (sgk::groupable(p)) {
+            groups[sgk::group_key(p)].push_back(i);
         } else {
             rest.push_back(i);
         }
@@ -261,8 +228,8 @@ sg_status capture_layout(sg_batch *b, const batch_inputs &in, bool persistent, i
     sg_status st = SG_OK;
     persistent_run<float> r32;
     persistent_run<double> r64;
-    std::vector<group_passes<float>> g32;
-    std::vector<group_passes<double>> g64;
+    std::vector<sgk::group_passes<float>> g32;
+    std::vector<sgk::group_passes<double>> g64;
     if (persistent) {
         if (!mem32.empty())
             st = persistent_upload<float>(b, bg, mem32, in.plans, in.sigma, in.deltax, in.deltay, in.fx, in.fy, r32);
@@ -341,10 +308,10 @@ sg_status capture_layout(sg_batch *b, const batch_inputs &in, bool persistent, i
             return sgk::batch_run_launch<double>(r64.items, r64.nitems, r64.members, r64.nmem, r64.ctl, r64.err,
                                                  r64.tries, r64.smem, nsm, bs);
         }, 1);
-    for (const group_passes<float> &g : g32)
-        run_branch([&](cudaStream_t bs) { return group_enqueue<float>(g, bs); }, g.u.central ? 4 : 3);
-    for (const group_passes<double> &g : g64)
-        run_branch([&](cudaStream_t bs) { return group_enqueue<double>(g, bs); }, g.u.central ? 4 : 3);
+    for (const sgk::group_passes<float> &g : g32)
+        run_branch([&](cudaStream_t bs) { return sgk::group_enqueue<float>(g, bs); }, g.u.central ? 4 : 3);
+    for (const sgk::group_passes<double> &g : g64)
+        run_branch([&](cudaStream_t bs) { return sgk::group_enqueue<double>(g, bs); }, g.u.central ? 4 : 3);
     for (int i : rest)
         run_branch([&](cudaStream_t bs) {
             return sg_force_ws(in.plans[i], &b->ws[i], in.sigma[i], in.dx(i), in.dy(i), in.fx[i], in.fy[i], bs);

@@ -213,10 +213,14 @@ __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const 
 // which one thread fetches with one 1-D bulk copy (TMA) per plane at kernel
 // start so that they arrive while the forward transform runs.
 // Column kernels keep each column in registers between transform stages and
-// exchange through COL_NBUF shared buffers (fft_regs in fft.cuh).
-constexpr int COL_NBUF = 2;
+// exchange through col_nbuf shared buffers (fft_regs in fft.cuh): two (one
+// barrier per exchange), except FP64 columns of 4096 points, whose two buffers
+// and six spectrum planes would exceed a CTA's 227 KB: one buffer there (a
+// barrier before each transform's first exchange).
+template <typename T, int PY>
+__host__ __device__ constexpr int col_nbuf() { return sizeof(T) == 8 && PY >= 4096 ? 1 : 2; }
 template <typename T, int PY, int CB>
-__host__ __device__ constexpr int col_buf_bytes() { return COL_NBUF * ((spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15); }
+__host__ __device__ constexpr int col_buf_bytes() { return col_nbuf<T, PY>() * ((spad_size<cplx_t<T>>(CB * PY) * (int)sizeof(cplx_t<T>) + 15) & ~15); }
 template <typename T, int PY, int CB, int NPL = 6>
 __host__ __device__ constexpr int col_smem_bytes() { return col_buf_bytes<T, PY, CB>() + CB * NPL * ((PY / 2 + 1 + 3) & ~3) * (int)sizeof(T); }
 
@@ -309,8 +313,8 @@ __device__ __forceinline__ void col_body(const col_args<T> &args, int bx, int qx
             v[m] = (m < 4 && j < ny && kx < qx) ? ld_plain<CO>(&work_fwd[((int64_t)f * qx + kx) * ny + j])
                                                 : cmake<C>((T)0, (T)0);
         }
-        if (COL_NBUF == 1 && f > 0) __syncthreads();
-        fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
+        if (col_nbuf<T, PY>() == 1 && f > 0) __syncthreads();
+        fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), false>(v, bufs, par, tw);
         if (f == 0) {
             if (!spectra_ready(&bar, err, args.tries)) return;
             if (CO && threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait; the body runs again
@@ -378,8 +382,8 @@ __device__ __forceinline__ void col_body(const col_args<T> &args, int bx, int qx
                 if (o == 2) v[q] = accz[q];
             }
         }
-        if (COL_NBUF == 1) __syncthreads();
-        fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(v, bufs, par, tw);
+        if (col_nbuf<T, PY>() == 1) __syncthreads();
+        fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), true>(v, bufs, par, tw);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int j = jt + m * STEP;
@@ -543,7 +547,7 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
     for (int m = 0; m < 4; ++m)
         if (jt + m * STEP == ny - 1) rows[c][1] = v[m];
     int par = 0;
-    fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
+    fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), false>(v, bufs, par, tw);
     if (!spectra_ready(&bar, err, args.tries)) return;
     if (CO && threadIdx.x == 0) mbar_inval(&bar);  // every thread has passed its wait; the body runs again
 
@@ -581,15 +585,15 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
     }
 
     // inverse transforms: the products are already in the transform's input pattern
-    if (COL_NBUF == 1) __syncthreads();
-    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accx, bufs, par, tw);
+    if (col_nbuf<T, PY>() == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), true>(accx, bufs, par, tw);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int j = jt + m * STEP;
         if (j < ny && kx < qx) work_inv[(int64_t)kx * ny + j] = accx[m];
     }
-    if (COL_NBUF == 1) __syncthreads();
-    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accy, bufs, par, tw);
+    if (col_nbuf<T, PY>() == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), true>(accy, bufs, par, tw);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int j = jt + m * STEP;
@@ -647,7 +651,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     for (int m = 0; m < 4; ++m)
         if (jt + m * STEP == ny - 1) rows[c][1] = v[m];
     int par = 0;
-    fft_regs<C, PY, CB, THREADS, COL_NBUF, false>(v, bufs, par, tw);
+    fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), false>(v, bufs, par, tw);
     if (!spectra_ready(&bar, err, args.tries)) return;
 
     C accx[8], accy[8];
@@ -684,15 +688,15 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     }
 
     // inverse transforms: the products are already in the transform's input pattern
-    if (COL_NBUF == 1) __syncthreads();
-    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accx, bufs, par, tw);
+    if (col_nbuf<T, PY>() == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), true>(accx, bufs, par, tw);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int j = jt + m * STEP;
         if (j < ny && kx < qx) work_inv[(int64_t)kx * ny + j] = accx[m];
     }
-    if (COL_NBUF == 1) __syncthreads();
-    fft_regs<C, PY, CB, THREADS, COL_NBUF, true>(accy, bufs, par, tw);
+    if (col_nbuf<T, PY>() == 1) __syncthreads();
+    fft_regs<C, PY, CB, THREADS, col_nbuf<T, PY>(), true>(accy, bufs, par, tw);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int j = jt + m * STEP;

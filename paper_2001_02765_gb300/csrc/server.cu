@@ -12,8 +12,18 @@
 // by all requests that use them; the work split of a solve depends only on its
 // plan, so a result is bit-for-bit the same alone and in any mix.
 //
+// Requests of single in-plane patches with equal padded lengths, precision and
+// slope handling that are queued together are admitted together as a group
+// (up to the server's group limit, 16 by default) on one slot: each keeps its
+// own workspace, and each pass of the convolution is one launch over all of
+// them (group.cuh, the batches' grouped launches), with the same arithmetic
+// per member, so a result is still bit-for-bit that of the request alone. The
+// head of the queue is always admitted first; queued requests of its group
+// join it out of arrival order.
+//
 // Nothing on the device waits for anything: completion is observed on the host.
 #include "common.cuh"
+#include "group.cuh"
 
 #include <string.h>
 
@@ -32,6 +42,9 @@ namespace {
 
 enum { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_GPU_DONE = 2, RQ_FINISHED = 3 };
 
+constexpr int GROUP_MAX = 16;   // members of one grouped admission (upper bound of the limit)
+constexpr int GROUP_SCAN = 256; // queued requests looked at for the head's group
+
 double now_s()
 {
     using namespace std::chrono;
@@ -39,6 +52,8 @@ double now_s()
 }
 
 }  // namespace
+
+struct sg_group_run;
 
 struct sg_request {
     uint64_t ticket = 0;
@@ -52,6 +67,16 @@ struct sg_request {
     sg_status result = SG_OK;
     double t_submit = 0, t_start = 0, t_done = 0;
     struct sg_server *server = nullptr;
+    sg_group_run *group = nullptr;  // the grouped admission it runs in (NULL: alone)
+};
+
+// Requests admitted together on one slot; the slot and the device argument
+// arrays are released when the last member has finished.
+struct sg_group_run {
+    int slot = -1;
+    std::vector<sg_request *> members;
+    void *dargs = nullptr;
+    int pending = 0;
 };
 
 struct sg_server {
@@ -61,6 +86,10 @@ struct sg_server {
     cudaMemPool_t pool = nullptr;
     std::vector<cudaStream_t> streams;
     int *err_host = nullptr;            // per slot: the request's device error word, copied after its solve (pinned)
+    char *arg_host = nullptr;           // per slot: staging of a group's pass arguments (pinned)
+    size_t arg_bytes = 0;               // per slot
+    int group_limit = GROUP_MAX;        // 1: no grouping
+    uint64_t groups_started = 0, grouped_requests = 0;
     std::vector<int> free_slots;
     std::deque<sg_request *> queue;
     std::vector<sg_request *> running;
@@ -91,9 +120,19 @@ void finalize(sg_server *s, sg_request *r)
 {
     sg_workspace_free(&r->ws, s->streams[r->slot], true);
     s->bytes_in_use -= r->bytes;
-    // a bounded wait that ran out in one of the request's kernels (device error word)
+    // a bounded wait that ran out in one of the request's kernels (device error word;
+    // a group's kernels report into its first member's word, copied to the slot's)
     if (r->result == SG_OK && s->err_host[r->slot] != 0) r->result = SG_ETIMEOUT;
-    s->free_slots.push_back(r->slot);
+    if (sg_group_run *g = r->group) {
+        r->group = nullptr;
+        if (--g->pending == 0) {
+            if (g->dargs) cudaFreeAsync(g->dargs, s->streams[g->slot]);
+            s->free_slots.push_back(g->slot);
+            delete g;
+        }
+    } else {
+        s->free_slots.push_back(r->slot);
+    }
     r->slot = -1;
     if (r->result == SG_OK) {
         s->completed++;
@@ -106,12 +145,11 @@ void finalize(sg_server *s, sg_request *r)
 
 // Start a queued request on a free slot (lock held). Returns false when its
 // workspace cannot be allocated now (it stays queued).
-bool start(sg_server *s, sg_request *r)
+// The request's workspace, stream-ordered from the server's pool on `st`, its
+// error word cleared; false (nothing held) when it cannot be allocated now.
+bool alloc_ws(sg_server *s, sg_request *r, cudaStream_t st)
 {
-    const int slot = s->free_slots.back();
-    cudaStream_t st = s->streams[slot];
     memset(&r->ws, 0, sizeof(r->ws));
-    // stream-ordered allocation from the server's pool
     sg_status a = SG_OK;
     {
         const sg_plan *p = r->plan;
@@ -133,6 +171,14 @@ bool start(sg_server *s, sg_request *r)
         sg_workspace_free(&r->ws, st, true);
         return false;
     }
+    return true;
+}
+
+bool start(sg_server *s, sg_request *r)
+{
+    const int slot = s->free_slots.back();
+    cudaStream_t st = s->streams[slot];
+    if (!alloc_ws(s, r, st)) return false;
     s->free_slots.pop_back();
     r->slot = slot;
     s->bytes_in_use += r->bytes;
@@ -155,6 +201,133 @@ bool start(sg_server *s, sg_request *r)
     return true;
 }
 
+void CUDART_CB on_group_done(void *p)
+{
+    sg_group_run *g = (sg_group_run *)p;
+    const double t = now_s();
+    sg_server *s = g->members[0]->server;
+    for (sg_request *r : g->members) {
+        r->t_done = t;
+        r->state.store(RQ_GPU_DONE);
+    }
+    s->wake.notify_one();
+}
+
+// Pack the members' pass arguments into the slot's pinned staging, copy them
+// to a pool allocation and enqueue the grouped launches (lock held).
+template <typename T>
+sg_status group_launch(sg_server *s, sg_group_run *g, cudaStream_t st)
+{
+    const int m = (int)g->members.size();
+    std::vector<sgk::uniform_passes<T>> us(m);
+    int maxny = 0;
+    for (int k = 0; k < m; ++k) {
+        sg_request *r = g->members[k];
+        const bool caller = r->plan->geom.slope_mode == SG_SLOPES_CALLER;
+        us[k] = sgk::uniform_setup<T>(r->plan, &r->ws, 0, r->sigma, caller ? r->dx : nullptr,
+                                      caller ? r->dy : nullptr, r->fx, r->fy, nullptr);
+        if (us[k].rf.src.ny > maxny) maxny = us[k].rf.src.ny;
+    }
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t s0 = m * sizeof(sgk::row_fwd_args<T>), s1 = m * sizeof(sgk::edge_args<T>);
+    const size_t s2 = m * sizeof(sgk::col_args<T>), s3 = m * sizeof(sgk::row_inv_args<T>);
+    const size_t total = up(s0) + up(s1) + up(s2) + up(s3);
+    if (total > s->arg_bytes) return SG_EINVAL;  // sized for GROUP_MAX members at creation
+    char *h = s->arg_host + (size_t)g->slot * s->arg_bytes;
+    for (int k = 0; k < m; ++k) {
+        ((sgk::row_fwd_args<T> *)h)[k] = us[k].rf;
+        ((sgk::edge_args<T> *)(h + up(s0)))[k] = us[k].ed;
+        ((sgk::col_args<T> *)(h + up(s0) + up(s1)))[k] = us[k].col;
+        ((sgk::row_inv_args<T> *)(h + up(s0) + up(s1) + up(s2)))[k] = us[k].ri;
+    }
+    char *d = nullptr;
+    if (cudaMallocFromPoolAsync((void **)&d, total, s->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ENOMEM;
+    }
+    g->dargs = d;
+    SG_CUDA_TRY(cudaMemcpyAsync(d, h, total, cudaMemcpyHostToDevice, st));
+    sgk::group_passes<T> gp;
+    gp.u = us[0];
+    gp.rf = (const sgk::row_fwd_args<T> *)d;
+    gp.ed = (const sgk::edge_args<T> *)(d + up(s0));
+    gp.col = (const sgk::col_args<T> *)(d + up(s0) + up(s1));
+    gp.ri = (const sgk::row_inv_args<T> *)(d + up(s0) + up(s1) + up(s2));
+    gp.bs = {m, maxny};
+    gp.err = g->members[0]->ws.err;
+    return sgk::group_enqueue<T>(gp, st);
+}
+
+// Start the requests `mem` (same group key; the queue's head first) together on
+// a free slot (lock held). Returns false, holding nothing, when some member's
+// workspace cannot be allocated now.
+bool start_group(sg_server *s, const std::vector<sg_request *> &mem)
+{
+    const int slot = s->free_slots.back();
+    cudaStream_t st = s->streams[slot];
+    for (size_t k = 0; k < mem.size(); ++k) {
+        if (!alloc_ws(s, mem[k], st)) {
+            for (size_t q = 0; q < k; ++q) sg_workspace_free(&mem[q]->ws, st, true);
+            return false;
+        }
+    }
+    s->free_slots.pop_back();
+    sg_group_run *g = new sg_group_run();
+    g->slot = slot;
+    g->members = mem;
+    g->pending = (int)mem.size();
+    const double t = now_s();
+    for (sg_request *r : mem) {
+        r->slot = slot;
+        r->group = g;
+        s->bytes_in_use += r->bytes;
+        r->t_start = t;
+        r->state.store(RQ_RUNNING);
+        s->running.push_back(r);
+    }
+    s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
+    s->err_host[slot] = 0;
+    s->groups_started++;
+    s->grouped_requests += mem.size();
+    sg_status res = mem[0]->plan->prec == SG_FP64 ? group_launch<double>(s, g, st) : group_launch<float>(s, g, st);
+    if (res == SG_OK &&
+        cudaMemcpyAsync(&s->err_host[slot], mem[0]->ws.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        res = SG_ECUDA;
+    if (res != SG_OK || cudaLaunchHostFunc(st, on_group_done, g) != cudaSuccess) {
+        if (res == SG_OK) res = SG_ECUDA;
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        const double td = now_s();
+        for (sg_request *r : mem) {
+            r->result = res;
+            r->t_done = td;
+            r->state.store(RQ_GPU_DONE);
+        }
+    }
+    return true;
+}
+
+// The head's group: queued requests with its key that fit the budget alongside
+// it, in queue order, up to the group limit (lock held).
+std::vector<sg_request *> collect_group(sg_server *s)
+{
+    std::vector<sg_request *> mem;
+    sg_request *head = s->queue.front();
+    mem.push_back(head);
+    if (s->group_limit < 2 || !sgk::groupable(head->plan)) return mem;
+    const auto key = sgk::group_key(head->plan);
+    int64_t need = s->bytes_in_use + head->bytes;
+    const size_t n = std::min(s->queue.size(), (size_t)GROUP_SCAN);
+    for (size_t i = 1; i < n && (int)mem.size() < s->group_limit; ++i) {
+        sg_request *q = s->queue[i];
+        if (!sgk::groupable(q->plan) || sgk::group_key(q->plan) != key) continue;
+        if (need + q->bytes > s->budget) continue;
+        need += q->bytes;
+        mem.push_back(q);
+    }
+    return mem;
+}
+
 void worker_main(sg_server *s)
 {
     cudaSetDevice(s->device);
@@ -174,10 +347,15 @@ void worker_main(sg_server *s)
             }
         }
         if (progressed) s->finished.notify_all();
-        // admissions, in arrival order
+        // admissions, in arrival order (a head with queued requests of its group: together)
         while (!s->queue.empty() && !s->free_slots.empty() && !s->stop) {
             sg_request *r = s->queue.front();
             if (s->bytes_in_use + r->bytes > s->budget) break;
+            const std::vector<sg_request *> grp = collect_group(s);
+            if (grp.size() > 1 && start_group(s, grp)) {
+                for (sg_request *q : grp) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), q));
+                continue;
+            }
             if (!start(s, r)) {
                 if (!s->running.empty()) break;  // memory frees up when a running request ends
                 // nothing running and still no memory: fail this request rather than wait forever
@@ -219,6 +397,13 @@ sg_status sg_server_create(size_t hbm_budget, int max_inflight, sg_server **out)
     }
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->err_host, sizeof(int) * max_inflight, cudaHostAllocDefault);
     if (e == cudaSuccess) memset(s->err_host, 0, sizeof(int) * max_inflight);
+    {
+        // a group's four argument arrays (FP64, the larger), each padded to 256 bytes
+        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        s->arg_bytes = up(GROUP_MAX * sizeof(sgk::row_fwd_args<double>)) + up(GROUP_MAX * sizeof(sgk::edge_args<double>)) +
+                       up(GROUP_MAX * sizeof(sgk::col_args<double>)) + up(GROUP_MAX * sizeof(sgk::row_inv_args<double>));
+    }
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->arg_host, s->arg_bytes * max_inflight, cudaHostAllocDefault);
     for (int k = 0; k < max_inflight && e == cudaSuccess; ++k) {
         cudaStream_t st;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -232,6 +417,7 @@ sg_status sg_server_create(size_t hbm_budget, int max_inflight, sg_server **out)
         for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
         if (s->pool) cudaMemPoolDestroy(s->pool);
         if (s->err_host) cudaFreeHost(s->err_host);
+        if (s->arg_host) cudaFreeHost(s->arg_host);
         delete s;
         return SG_ECUDA;
     }
@@ -263,7 +449,16 @@ sg_status sg_server_destroy(sg_server *s)
     }
     cudaMemPoolDestroy(s->pool);
     cudaFreeHost(s->err_host);
+    cudaFreeHost(s->arg_host);
     delete s;
+    return SG_OK;
+}
+
+sg_status sg_server_set_group_limit(sg_server *s, int max_members)
+{
+    if (!s || max_members < 1 || max_members > GROUP_MAX) return SG_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->group_limit = max_members;
     return SG_OK;
 }
 
@@ -386,6 +581,8 @@ sg_status sg_server_get_stats(sg_server *s, sg_server_stats *out, int reset_late
     double sum = 0;
     for (double x : v) sum += x;
     out->latency_mean_ms = v.empty() ? 0.0 : sum / (double)v.size();
+    out->groups_started = s->groups_started;
+    out->grouped_requests = s->grouped_requests;
     if (reset_latencies) s->latency_ms.clear();
     return SG_OK;
 }

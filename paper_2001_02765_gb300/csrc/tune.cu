@@ -45,7 +45,8 @@ int64_t col_smem(int pad, int cb, int npl, bool fp64)
     const int64_t cs = fp64 ? 16 : 8, rs = fp64 ? 8 : 4;
     const int64_t n = (int64_t)cb * pad;
     const int64_t padded = fp64 ? (n - 1) + ((n - 1) >> 3) + 1 : (n - 1) + ((n - 1) >> 4) + 1;
-    return sgk::COL_NBUF * ((padded * cs + 15) & ~15LL) + (int64_t)cb * npl * (((pad / 2 + 1) + 3) & ~3) * rs;
+    const int64_t nbuf = fp64 && pad >= 4096 ? 1 : 2;  // col_nbuf
+    return nbuf * ((padded * cs + 15) & ~15LL) + (int64_t)cb * npl * (((pad / 2 + 1) + 3) & ~3) * rs;
 }
 
 bool knob_feasible(int knob, int pad, int v, bool fp64)

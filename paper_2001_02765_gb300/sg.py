@@ -69,7 +69,8 @@ class sg_server_stats(ctypes.Structure):
                 ("cancelled", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("queued", ctypes.c_int64),
                 ("running", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
                 ("latency_count", ctypes.c_int64), ("latency_p50_ms", ctypes.c_double),
-                ("latency_p99_ms", ctypes.c_double), ("latency_mean_ms", ctypes.c_double)]
+                ("latency_p99_ms", ctypes.c_double), ("latency_mean_ms", ctypes.c_double),
+                ("groups_started", ctypes.c_uint64), ("grouped_requests", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes)
@@ -112,6 +113,7 @@ _SIGNATURES = {
                                ctypes.POINTER(ctypes.c_double)]),
     "sg_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sg_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sg_server_stats), ctypes.c_int]),
+    "sg_server_set_group_limit": (ctypes.c_int, [_VP, ctypes.c_int]),
     "sg_plan_create_zones": (ctypes.c_int, [ctypes.POINTER(sg_zones), ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)]),
     "sg_force_zones": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -387,6 +389,11 @@ def sg_server_get_stats(server, reset_latencies=False):
     out = sg_server_stats()
     _check(load().sg_server_get_stats(server, ctypes.byref(out), int(bool(reset_latencies))), "sg_server_get_stats")
     return {k: getattr(out, k) for k, _ in sg_server_stats._fields_}
+
+
+def sg_server_set_group_limit(server, max_members):
+    """Most requests admitted together as one group (1 admits every request alone)."""
+    _check(load().sg_server_set_group_limit(server, int(max_members)), "sg_server_set_group_limit")
 
 
 SG_PEAK_FP64_FMA, SG_PEAK_FP32_FMA, SG_PEAK_FP32_LG2 = 0, 1, 2

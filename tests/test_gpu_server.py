@@ -115,6 +115,7 @@ def test_poll_cancel_timeout_and_unknown_tickets(sg):
     s = torch.rand(n * n, dtype=torch.float64, device="cuda")
     outs = [(torch.empty_like(s), torch.empty_like(s)) for _ in range(3)]
     server = sg.sg_server_create(0, 1)  # one slot: the second and third requests queue
+    sg.sg_server_set_group_limit(server, 1)  # and are not admitted together with the first
     try:
         assert sg.sg_poll(server, 12345)[0] == sg.SG_ENOTFOUND
         t1 = sg.sg_submit(server, plan.handle, s.data_ptr(), 0, 0, outs[0][0].data_ptr(), outs[0][1].data_ptr())
@@ -157,3 +158,58 @@ def test_destroy_cancels_queued_requests(sg):
     sg.sg_server_destroy(server)  # waits for the running one, cancels the rest
     torch.cuda.synchronize()
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_queued_requests_of_one_length_run_grouped(sg, prec):
+    """Requests of one padded length queued behind a long one are admitted
+    together (one grouped launch per pass); each result equals its solo
+    sg_force bit for bit, with ragged row counts and two slope modes; with a
+    group limit of 1 nothing is grouped."""
+    import torch
+    dt = np.float32 if prec == "fp32" else np.float64
+    big = sg.Plan([(0,) + W.unit_grid(1024)], precision=prec, slope_mode=sg.SG_SLOPES_CENTRAL)
+    bs = concat_dev([np.random.Generator(np.random.PCG64(3)).uniform(0, 1, (1024, 1024))], dt)
+    shapes = [(100, 100), (120, 96), (110, 90)]  # padded 256 x 256 each
+    reqs = []
+    for k in range(9):
+        nx, ny = shapes[k % 3]
+        mode = sg.SG_SLOPES_CALLER if k % 2 == 0 else sg.SG_SLOPES_CENTRAL
+        plan = sg.Plan([(0, nx, ny, -1.0, -1.0, 2.0 / nx)], precision=prec, slope_mode=mode)
+        s, sx, sy = W.random_fields(ny, nx, seed=60 + k)
+        ins = [concat_dev([a], dt) for a in (s, sx, sy)]
+        if mode != sg.SG_SLOPES_CALLER:
+            ins = [ins[0], None, None]
+        fx, fy = plan.force(*ins)
+        torch.cuda.synchronize()
+        reqs.append((plan, ins, fx.clone(), fy.clone()))
+    ptr = lambda t: 0 if t is None else t.data_ptr()
+    for limit in (16, 1):
+        server = sg.sg_server_create(0, 1)  # one slot: everything queues behind the first request
+        try:
+            sg.sg_server_set_group_limit(server, limit)
+            bfx, bfy = torch.empty_like(bs), torch.empty_like(bs)
+            tickets = [sg.sg_submit(server, big.handle, bs.data_ptr(), 0, 0, bfx.data_ptr(), bfy.data_ptr())]
+            outs = []
+            for plan, ins, rx, ry in reqs:
+                fx = torch.full_like(ins[0], float("nan"))
+                fy = torch.full_like(ins[0], float("nan"))
+                tickets.append(sg.sg_submit(server, plan.handle, *(ptr(a) for a in ins), fx.data_ptr(), fy.data_ptr()))
+                outs.append((fx, fy, rx, ry))
+            for t in tickets:
+                st, res, _ = sg.sg_wait(server, t, 60000.0)
+                assert st == sg.SG_OK and res == sg.SG_OK
+            for fx, fy, rx, ry in outs:
+                assert torch.equal(fx, rx) and torch.equal(fy, ry)
+            stats = sg.sg_server_get_stats(server)
+            if limit == 1:
+                assert stats["groups_started"] == 0
+            else:
+                # the caller-slope and central-slope requests form one group each
+                assert stats["groups_started"] >= 2 and stats["grouped_requests"] >= 4
+            assert stats["bytes_in_use"] == 0 and stats["running"] == 0
+        finally:
+            sg.sg_server_destroy(server)
+    for plan, *_ in reqs:
+        plan.close()
+    big.close()

@@ -169,6 +169,30 @@ def test_largest_patch_2048_fp32_sampled(sg):
     assert rel_l2(fx[tj, ti], fy[tj, ti], rx, ry) < F32_TOL
 
 
+@pytest.mark.parametrize("mode", ["central", "caller"])
+def test_fp64_4096_point_columns_sampled(sg, mode):
+    """FP64 plans whose padded length is 4096 (sides 1100 x 1030; one exchange
+    buffer in the column pass there, the shared-memory limit): 24 sampled
+    cells vs the plain sum."""
+    nx, ny = 1100, 1030
+    geom = (nx, ny, -1.0, -0.95, 2.0 / nx)
+    h = geom[4]
+    X, Y = W.cell_centres(*geom)
+    s, sx, sy = W.kuzmin_sigma(X, Y, 0.15)
+    if mode == "central":
+        fx, fy = _solve(sg, geom, "fp64", sg.SG_SLOPES_CENTRAL, s)
+        sx, sy = central_slopes(s, h)
+    else:
+        fx, fy = _solve(sg, geom, "fp64", sg.SG_SLOPES_CALLER, s, sx, sy)
+    rng = np.random.Generator(np.random.PCG64(14))
+    tj = rng.integers(0, ny, 24)
+    ti = rng.integers(0, nx, 24)
+    rx, ry = uniform_direct_force(s, sx, sy, h, x0=geom[2], y0=geom[3], targets=(tj, ti))
+    err = rel_l2(fx[tj, ti], fy[tj, ti], rx, ry)
+    print("rel L2 fp64 4096-point %s: %.3e" % (mode, err))
+    assert err < 1e-11
+
+
 def test_host_entry_point_equals_device_entry_point(sg):
     import torch
     ny, nx = 96, 80
