@@ -779,6 +779,15 @@ def run_gpu(args):
         pads = sorted({_pad(p[1]) for p in wl["patches"]} | {_pad(p[2]) for p in wl["patches"]})
         res = sg.sg_autotune(sg.SG_FP32, pads[0], pads[-1], reps=15)
         tuned = {"seconds": time.perf_counter() - t0, "shapes": {str(p): res[p][0] for p in pads}}
+    # the cross-patch direct sum's split and far-field grid (skipped where one
+    # solve takes seconds: the candidates would take minutes)
+    if not args.no_autotune and plan.info["cross_mode"] == 1 and plan.info["cross_pairs"] < 1e11:
+        t0 = time.perf_counter()
+        before = sg.sg_plan_direct_shape(plan.handle)
+        best = sg.sg_plan_autotune(plan.handle, 3)
+        after = sg.sg_plan_direct_shape(plan.handle)
+        tuned = dict(tuned or {}, direct={"seconds": time.perf_counter() - t0, "split_and_far_grid_built": before,
+                                          "split_and_far_grid_chosen": after, "best_ms": best})
     stream = torch.cuda.Stream()
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     sigma, dxs, dys = dev(wl["sigma"]), dev(wl["dx"]), dev(wl["dy"])

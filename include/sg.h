@@ -466,6 +466,20 @@ sg_status sg_tune_set(int precision, int pad, const int *shape);
  * plans and buffers. Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
 sg_status sg_autotune(int precision, int min_pad, int max_pad, int reps, double *best_ms);
 
+/* Tune the cross-patch direct sum of one plan (hierarchies on the direct
+ * path; a no-op returning *best_ms = 0 for other plans): the source-tile
+ * ranges per target block (the plan's value, a half or a quarter of it) and,
+ * for FP32 plans, the CTAs of the persistent far-field launch (1, 2, 3, 4, 6
+ * or 8 per SM), each timed as the median of `reps` solves on zero fields with
+ * the plan's own workspace; the fastest pair stays in the plan. The split only
+ * regroups the FP64 partial sums of the far field (results agree to FP64
+ * rounding; the far-field grid changes nothing). Synchronous; call with no
+ * solve of the plan in flight and before capturing the plan into a batch.
+ * sg_plan_direct_shape reads the pair. best_ms may be NULL. Errors: SG_EINVAL,
+ * SG_ENOMEM, SG_ECUDA. */
+sg_status sg_plan_autotune(sg_plan *plan, int reps, double *best_ms);
+sg_status sg_plan_direct_shape(const sg_plan *plan, int *nsplit, int *far_grid);
+
 /* ------------------------------------------------------------------------
  * Batches (not in the paper): n independent solves bound to their plans and
  * caller-owned device buffers at creation and captured once into a CUDA graph,

@@ -1,4 +1,5 @@
-// Launch-shape tuning of the uniform-patch passes (not in the paper).
+// Launch-shape tuning of the uniform-patch passes and of a plan's cross-patch
+// direct sum (not in the paper).
 //
 // For every padded length and precision a process-wide table holds the launch
 // shape of each pass: row sequences per CTA of the forward and inverse row
@@ -198,6 +199,102 @@ sg_status sg_autotune(int precision, int min_pad, int max_pad, int reps, double 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+// The cross-patch direct sum of one plan: source-tile ranges per target block
+// (the plan's value, a half and a quarter of it: the partial-sum buffers were
+// sized for the plan's value) and, for FP32 plans, the CTAs of the persistent
+// far-field launch (1, 2, 3, 4, 6 or 8 per SM), timed on the plan's own
+// workspace with zero fields, the fastest kept.
+sg_status sg_plan_autotune(sg_plan *plan, int reps, double *best_ms)
+{
+    if (!plan || reps < 1) {
+        sg_set_last_error_message("sg_plan_autotune: null plan or repetitions below 1");
+        return SG_EINVAL;
+    }
+    if (plan->ntiles == 0 || plan->ntargets == 0) {  // no direct sum to tune
+        if (best_ms) *best_ms = 0.0;
+        return SG_OK;
+    }
+    int dev = 0, nsm = 0;
+    SG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device) return SG_EINVAL;
+    SG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t es = plan->prec == SG_FP64 ? 8 : 4, n = plan->ncells;
+    char *buf = nullptr;
+    SG_CUDA_TRY(cudaMalloc(&buf, (size_t)(6 * n * es)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sg_status st = cudaMemset(buf, 0, (size_t)(6 * n * es)) == cudaSuccess ? SG_OK : SG_ECUDA;
+    if (st == SG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = SG_ECUDA;
+    auto solve = [&]() -> sg_status {
+        if (plan->geom.z != 0.0) return sg_force3(plan, buf, buf + n * es, buf + 2 * n * es, buf + 3 * n * es,
+                                                  buf + 4 * n * es, buf + 5 * n * es, nullptr);
+        return sg_force(plan, buf, buf + n * es, buf + 2 * n * es, buf + 3 * n * es, buf + 4 * n * es, nullptr);
+    };
+    auto time_it = [&](double &ms) -> sg_status {
+        SG_TRY(solve());  // warm-up
+        std::vector<float> t;
+        for (int r = 0; r < reps; ++r) {
+            SG_CUDA_TRY(cudaEventRecord(e0, nullptr));
+            SG_TRY(solve());
+            SG_CUDA_TRY(cudaEventRecord(e1, nullptr));
+            SG_CUDA_TRY(cudaEventSynchronize(e1));
+            float x = 0;
+            SG_CUDA_TRY(cudaEventElapsedTime(&x, e0, e1));
+            t.push_back(x);
+        }
+        std::nth_element(t.begin(), t.begin() + t.size() / 2, t.end());
+        ms = t[t.size() / 2];
+        return SG_OK;
+    };
+    const bool fp32 = plan->prec == SG_FP32;
+    const int built = plan->nsplit;
+    int per_sm = fp32 ? std::max(1, (plan->far_grid + nsm - 1) / nsm) : 0;
+    auto set_shape = [&](int ns, int psm) {
+        plan->nsplit = ns;
+        if (fp32) {
+            const int64_t items = (int64_t)plan->nblocks * ns;
+            plan->far_grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)nsm * psm));
+        }
+    };
+    double best = 1e300;
+    int best_ns = built, best_psm = per_sm;
+    for (int ns : {built, built / 2, built / 4}) {
+        if (st != SG_OK || ns < 1 || (ns != built && ns == best_ns)) continue;
+        set_shape(ns, per_sm);
+        double ms = 0;
+        st = time_it(ms);
+        if (st == SG_OK && ms < best) {
+            best = ms;
+            best_ns = ns;
+        }
+    }
+    if (fp32)
+        for (int psm : {1, 2, 3, 4, 6, 8}) {
+            if (st != SG_OK || psm == per_sm) continue;
+            set_shape(best_ns, psm);
+            double ms = 0;
+            st = time_it(ms);
+            if (st == SG_OK && ms < best) {
+                best = ms;
+                best_psm = psm;
+            }
+        }
+    set_shape(best_ns, best_psm);
+    if (st == SG_OK && best_ms) *best_ms = best;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaDeviceSynchronize();
+    cudaFree(buf);
+    return st;
+}
+
+sg_status sg_plan_direct_shape(const sg_plan *plan, int *nsplit, int *far_grid)
+{
+    if (!plan || !nsplit || !far_grid) return SG_EINVAL;
+    *nsplit = plan->nsplit;
+    *far_grid = plan->far_grid;
+    return SG_OK;
 }
 
 }  // extern "C"

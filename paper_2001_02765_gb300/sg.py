@@ -114,6 +114,8 @@ _SIGNATURES = {
     "sg_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "sg_server_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(sg_server_stats), ctypes.c_int]),
     "sg_server_set_group_limit": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "sg_plan_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "sg_plan_direct_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sg_plan_create_zones": (ctypes.c_int, [ctypes.POINTER(sg_zones), ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)]),
     "sg_force_zones": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -389,6 +391,20 @@ def sg_server_get_stats(server, reset_latencies=False):
     out = sg_server_stats()
     _check(load().sg_server_get_stats(server, ctypes.byref(out), int(bool(reset_latencies))), "sg_server_get_stats")
     return {k: getattr(out, k) for k, _ in sg_server_stats._fields_}
+
+
+def sg_plan_autotune(handle, reps=5):
+    """Tune a plan's cross-patch direct sum; returns the best median solve time (ms)."""
+    ms = ctypes.c_double()
+    _check(load().sg_plan_autotune(handle, int(reps), ctypes.byref(ms)), "sg_plan_autotune")
+    return ms.value
+
+
+def sg_plan_direct_shape(handle):
+    """(source-tile ranges per target block, CTAs of the FP32 far-field launch)."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().sg_plan_direct_shape(handle, ctypes.byref(a), ctypes.byref(b)), "sg_plan_direct_shape")
+    return a.value, b.value
 
 
 def sg_server_set_group_limit(server, max_members):

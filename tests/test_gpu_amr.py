@@ -342,3 +342,30 @@ def test_central_slopes_fp32_config3_sampled(sg):
     plan.close()
     print("rel L2 fp32 central config 3: %.3e" % err)
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_plan_autotune_direct_sum(sg, prec):
+    """sg_plan_autotune picks the direct sum's split and far-field grid among
+    its candidates; the solve afterwards agrees with the solve before to FP64
+    rounding of the regrouped partial sums (FP32 plans: to FP32 rounding) and
+    still matches the oracle."""
+    import torch
+    patches = [(lev,) + p for lev, p in enumerate(W.centred_nested_patches(64, 3))]
+    sig, sx, sy = _fields(patches, 9, positive=True)
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan, fx0, fy0 = _run(sg, patches, prec, 2, sig, sx, sy, cross=1)
+    ns0, fg0 = sg.sg_plan_direct_shape(plan.handle)
+    ms = sg.sg_plan_autotune(plan.handle, 3)
+    ns1, fg1 = sg.sg_plan_direct_shape(plan.handle)
+    assert ms > 0 and ns1 in (ns0, ns0 // 2, ns0 // 4) and ns1 >= 1
+    if prec == "fp32":
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        assert 1 <= fg1 <= 8 * nsm
+    fx, fy = plan.force(concat_dev(sig, dt), concat_dev(sx, dt), concat_dev(sy, dt))
+    torch.cuda.synchronize()
+    fx, fy = fx.cpu().numpy(), fy.cpu().numpy()
+    scale = max(np.abs(fx0).max(), np.abs(fy0).max())
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    assert np.abs(fx - fx0).max() <= tol * scale and np.abs(fy - fy0).max() <= tol * scale
+    plan.close()
