@@ -716,7 +716,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         const int nplanes = g->z != 0.0 ? 9 : 6;
         if (!use_lv) st = dev_alloc(plan, &pp.spectra, nplanes * (size_t)(d.px / 2 + 1) * sg_spec_stride(d.py) * es);
         if (st == SG_OK && g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0 && !(gi.n > 1 || gi.masked))
-            st = dev_alloc(plan, &pp.phase, (5 * (size_t)(d.px / 2 + 1) + 5 * (size_t)d.py) * es);
+            st = dev_alloc(plan, &pp.phase, (4 * (size_t)(d.px / 2 + 1) + 4 * (size_t)d.py) * es);
     }
     if (plan->composite) {
         plan->ws_sfield_bytes = 6 * gi.ncells * (int64_t)es;  // composite sources S, filled values F

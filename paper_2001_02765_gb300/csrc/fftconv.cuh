@@ -27,8 +27,8 @@
 // transform i sin(2 pi k / P) / h times sigma's, except that it also puts
 // s[0] / 2h at i = -1 and -s[nx-1] / 2h at i = nx, outside the patch, whose
 // transforms are removed again:
-//   deltax^(kx, ky) = i csin(kx) S - e^{+2 pi i kx/Px}/2h C0(ky) + e^{-2 pi i nx kx/Px}/2h C1(ky)
-//   deltay^(kx, ky) = i rsin(ky) S - e^{+2 pi i ky/Py}/2h R0(kx) + e^{-2 pi i ny ky/Py}/2h R1(kx)
+//   deltax^(kx, ky) = i sin(2 pi kx/Px)/h S - e^{+2 pi i kx/Px}/2h C0(ky) + e^{-2 pi i nx kx/Px}/2h C1(ky)
+//   deltay^(kx, ky) = i sin(2 pi ky/Py)/h S - e^{+2 pi i ky/Py}/2h R0(kx) + e^{-2 pi i ny ky/Py}/2h R1(kx)
 // with S = sigma^(kx, ky), C0 / C1 the y-transforms of sigma's first / last
 // column (k_edge_cols), R0 / R1 the x-transforms of its first / last row (the
 // column pass reads them from its own input). So only sigma is transformed:
@@ -531,8 +531,8 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB, 6, CO>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
-    const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
-    const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
+    const C *ce1 = reinterpret_cast<const C *>(phase), *ce2 = ce1 + qx;
+    const C *re1 = ce2 + qx, *re2 = re1 + PY;
 
     // the lower half of the column straight into registers (the upper half is zero)
     C v[8];
@@ -563,11 +563,9 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
         const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
         const C S = v[q];
         // slope spectra
-        const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
-        const C e1 = cmake<C>(__ldg(&ce1[2 * kx]), __ldg(&ce1[2 * kx + 1]));
-        const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
-        const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
-        const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
+        const C e1 = __ldg(&ce1[kx]), e2 = __ldg(&ce2[kx]);
+        const C f1 = __ldg(&re1[ky]), f2 = __ldg(&re2[ky]);
+        const T cs = (T)2 * e1.y, rs = (T)2 * f1.y;  // sin(2 pi k / P) / h, exactly
         const C c0 = ld_table<CO>(&edge[ky]), c1 = ld_table<CO>(&edge[PY + ky]);
         // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
         const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
@@ -635,8 +633,8 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
-    const T *csin = phase, *ce1 = phase + qx, *ce2 = phase + 3 * qx;
-    const T *rsin = phase + 5 * qx, *re1 = rsin + PY, *re2 = rsin + 3 * PY;
+    const C *ce1 = reinterpret_cast<const C *>(phase), *ce2 = ce1 + qx;
+    const C *re1 = ce2 + qx, *re2 = re1 + PY;
 
     // the lower half of the column straight into registers (the upper half is zero)
     C v[8];
@@ -666,11 +664,9 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
         const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
         const C S = v[q];
         // slope spectra
-        const T cs = __ldg(&csin[kx]), rs = __ldg(&rsin[ky]);
-        const C e1 = cmake<C>(__ldg(&ce1[2 * kx]), __ldg(&ce1[2 * kx + 1]));
-        const C e2 = cmake<C>(__ldg(&ce2[2 * kx]), __ldg(&ce2[2 * kx + 1]));
-        const C f1 = cmake<C>(__ldg(&re1[2 * ky]), __ldg(&re1[2 * ky + 1]));
-        const C f2 = cmake<C>(__ldg(&re2[2 * ky]), __ldg(&re2[2 * ky + 1]));
+        const C e1 = __ldg(&ce1[kx]), e2 = __ldg(&ce2[kx]);
+        const C f1 = __ldg(&re1[ky]), f2 = __ldg(&re2[ky]);
+        const T cs = (T)2 * e1.y, rs = (T)2 * f1.y;  // sin(2 pi k / P) / h, exactly
         const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
         // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
         const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);

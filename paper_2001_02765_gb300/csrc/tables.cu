@@ -389,16 +389,20 @@ sg_status sg_tables_build(sg_plan *plan)
     return SG_OK;
 }
 
-// Central-slope factors of a patch (see fftconv.cu), in the plan precision:
-//   csin[kx] = sin(2 pi kx / Px) / h,  ce1[kx] = e^{+2 pi i kx / Px} / 2h,  ce2[kx] = e^{-2 pi i nx kx / Px} / 2h
-// for kx in [0, Px/2], and the same along y for ky in [0, Py) (rsin, re1, re2).
-// Layout: csin[qx] ce1[qx] ce2[qx] rsin[py] re1[py] re2[py], complex entries as (re, im).
+// Central-slope factors of a patch (see fftconv.cuh), in the plan precision:
+//   ce1[kx] = e^{+2 pi i kx / Px} / 2h,  ce2[kx] = e^{-2 pi i nx kx / Px} / 2h
+// for kx in [0, Px/2], and the same along y for ky in [0, Py) (re1, re2).
+// Layout: ce1[qx] ce2[qx] re1[py] re2[py] of complex entries (re, im), each
+// array starting at an even element so that an entry is one aligned vector
+// load. The sine factor sin(2 pi k / P) / h of the spectral difference is twice
+// the imaginary part of e1 (a power-of-two scaling of the same rounded value,
+// so the kernels form it exactly).
 template <typename T>
 __global__ void k_phase(T *out, int nx, int ny, int px, int py, double h)
 {
     const int qx = px / 2 + 1;
-    T *csin = out, *ce1 = out + qx, *ce2 = out + 3 * qx;
-    T *rsin = out + 5 * qx, *re1 = rsin + py, *re2 = rsin + 3 * py;
+    T *ce1 = out, *ce2 = out + 2 * qx;
+    T *re1 = out + 4 * qx, *re2 = re1 + 2 * py;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < qx + py; k += gridDim.x * blockDim.x) {
         const bool col = k < qx;
         const int kk = col ? k : k - qx;
@@ -407,8 +411,7 @@ __global__ void k_phase(T *out, int nx, int ny, int px, int py, double h)
         sincospi(2.0 * (double)kk / (double)P, &s1, &c1);
         // e^{-2 pi i n k / P}: reduce n k mod P first so the argument stays small
         sincospi(-2.0 * (double)(((long long)n * kk) % P) / (double)P, &s2, &c2);
-        T *sn = col ? csin : rsin, *e1 = col ? ce1 : re1, *e2 = col ? ce2 : re2;
-        sn[kk] = (T)(s1 / h);
+        T *e1 = col ? ce1 : re1, *e2 = col ? ce2 : re2;
         e1[2 * kk] = (T)(c1 / (2.0 * h));
         e1[2 * kk + 1] = (T)(s1 / (2.0 * h));
         e2[2 * kk] = (T)(c2 / (2.0 * h));
