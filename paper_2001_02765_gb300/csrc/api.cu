@@ -776,7 +776,7 @@ sg_status plan_build(const sg_geom *g, sg_precision prec, size_t budget, sg_plan
         // central slopes of a single unmasked patch (in the plane) transform sigma only, plus the
         // two edge columns (2 x py complex); hierarchies transform three composite fields
         const bool central = g->slope_mode == SG_SLOPES_CENTRAL && g->z == 0.0 && !(gi.n > 1 || gi.masked);
-        const int64_t f = central ? q + 2LL * pdev[k].py * (int64_t)(2 * es) : 3 * q;
+        const int64_t f = central ? q + (2LL * pdev[k].py + 1) * (int64_t)(2 * es) : 3 * q;  // edge pairs, even start
         const int nout = g->z != 0.0 ? 3 : 2;
         if (f > wf) wf = f;
         if (nout * q > wi) wi = nout * q;

@@ -14,7 +14,7 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
     const sgk::uniform_passes<T> u = sgk::uniform_setup<T>(plan, ws, p, sigma, dx, dy, fx, fy, fz, pot_spec, wf_pot);
     // the passes' scratch must hold what they write (checked before any launch)
     const int64_t q = (int64_t)u.qx * plan->pp[p].d.ny * (int64_t)sizeof(cplx_t<T>);
-    const int64_t need_f = u.nf_rows * q + (u.central ? 2LL * u.py * (int64_t)sizeof(cplx_t<T>) : 0);
+    const int64_t need_f = u.nf_rows * q + (u.central ? (2LL * u.py + 1) * (int64_t)sizeof(cplx_t<T>) : 0);
     const int64_t have_f = pot_spec && wf_pot != ws->work_fwd ? plan->pot_fwd_bytes : plan->ws_fwd_bytes;
     if (need_f > have_f || u.nout * q > plan->ws_inv_bytes) {
         sg_set_last_error_message("internal: a transform pass needs more scratch than the plan sized");

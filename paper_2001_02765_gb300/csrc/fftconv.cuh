@@ -143,6 +143,20 @@ __device__ __forceinline__ X ld_table(const X *p)
     if constexpr (CO) return __ldca(p);
     return __ldg(p);
 }
+// The pair (a, b) at index k of an array of interleaved complex pairs: one
+// 16-byte load in FP32 (the array 16-byte aligned), two in FP64.
+template <bool CO, typename C>
+__device__ __forceinline__ void ld_pair(const C *p, int k, C &a, C &b)
+{
+    if constexpr (sizeof(C) == 8) {
+        const float4 q = ld_table<CO>(reinterpret_cast<const float4 *>(p) + k);
+        a = make_float2(q.x, q.y);
+        b = make_float2(q.z, q.w);
+    } else {
+        a = ld_table<CO>(p + 2 * k);
+        b = ld_table<CO>(p + 2 * k + 1);
+    }
+}
 template <typename T, int PX, int NB, int THREADS>
 __device__ __forceinline__ void row_fwd_body(const row_fwd_args<T> &args, int bx, int f,
                                              const cplx_t<T> *__restrict__ tw)
@@ -464,7 +478,7 @@ __global__ void __launch_bounds__(THREADS) k_row_inv(row_inv_args<T> one, const 
 }
 
 // y-transforms of sigma's first and last columns, packed as z = c0 + i c1:
-// edge[k] = C0(k), edge[PY + k] = C1(k), k < PY.
+// edge[2k] = C0(k), edge[2k + 1] = C1(k), k < PY (pairs: one load per bin).
 template <typename T, int PY, int THREADS>
 __device__ __forceinline__ void edge_body(const edge_args<T> &args, const cplx_t<T> *__restrict__ tw)
 {
@@ -485,8 +499,8 @@ __device__ __forceinline__ void edge_body(const edge_args<T> &args, const cplx_t
     for (int k = threadIdx.x; k < PY; k += THREADS) {
         const C z = buf[spad<C>(k)];
         const C w = buf[spad<C>((PY - k) & (PY - 1))];
-        edge[k] = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
-        edge[PY + k] = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
+        edge[2 * k] = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
+        edge[2 * k + 1] = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
     }
     sg_dep_wait();
 }
@@ -531,8 +545,7 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB, 6, CO>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
-    const C *ce1 = reinterpret_cast<const C *>(phase), *ce2 = ce1 + qx;
-    const C *re1 = ce2 + qx, *re2 = re1 + PY;
+    const C *cpair = reinterpret_cast<const C *>(phase), *rpair = cpair + 2 * qx;  // (e1, e2) per kx, per ky
 
     // the lower half of the column straight into registers (the upper half is zero)
     C v[8];
@@ -563,10 +576,12 @@ __device__ __forceinline__ void col_central_body(const col_args<T> &args, int bx
         const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
         const C S = v[q];
         // slope spectra
-        const C e1 = __ldg(&ce1[kx]), e2 = __ldg(&ce2[kx]);
-        const C f1 = __ldg(&re1[ky]), f2 = __ldg(&re2[ky]);
+        C e1, e2, f1, f2;
+        ld_pair<false>(cpair, kx, e1, e2);
+        ld_pair<false>(rpair, ky, f1, f2);
         const T cs = (T)2 * e1.y, rs = (T)2 * f1.y;  // sin(2 pi k / P) / h, exactly
-        const C c0 = ld_table<CO>(&edge[ky]), c1 = ld_table<CO>(&edge[PY + ky]);
+        C c0, c1;
+        ld_pair<CO>(edge, ky, c0, c1);
         // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
         const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
         const C q2 = cmul_rn(f2, rows[c][1]), q1 = cmul_rn(f1, rows[c][0]);
@@ -633,8 +648,7 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
     __syncthreads();
     if (threadIdx.x == 0) fetch_spectra<T, PY, CB>(ssp, spec, kx0, qx, &bar);
     sg_dep_wait();  // the row pass's output (the kernel spectra are the plan's own)
-    const C *ce1 = reinterpret_cast<const C *>(phase), *ce2 = ce1 + qx;
-    const C *re1 = ce2 + qx, *re2 = re1 + PY;
+    const C *cpair = reinterpret_cast<const C *>(phase), *rpair = cpair + 2 * qx;  // (e1, e2) per kx, per ky
 
     // the lower half of the column straight into registers (the upper half is zero)
     C v[8];
@@ -664,10 +678,12 @@ __global__ void __launch_bounds__(THREADS, (col_min_blocks<T, PY, THREADS>())) k
         const T *sp = ssp + c * QS + kq;  // plane p at sp[p * CB * QS]
         const C S = v[q];
         // slope spectra
-        const C e1 = __ldg(&ce1[kx]), e2 = __ldg(&ce2[kx]);
-        const C f1 = __ldg(&re1[ky]), f2 = __ldg(&re2[ky]);
+        C e1, e2, f1, f2;
+        ld_pair<false>(cpair, kx, e1, e2);
+        ld_pair<false>(rpair, ky, f1, f2);
         const T cs = (T)2 * e1.y, rs = (T)2 * f1.y;  // sin(2 pi k / P) / h, exactly
-        const C c0 = __ldg(&edge[ky]), c1 = __ldg(&edge[PY + ky]);
+        C c0, c1;
+        ld_pair<false>(edge, ky, c0, c1);
         // every operation explicitly rounded (see mul_rn): the result must not depend on the launch shape
         const C p2 = cmul_rn(e2, c1), p1 = cmul_rn(e1, c0);
         const C q2 = cmul_rn(f2, rows[c][1]), q1 = cmul_rn(f1, rows[c][0]);
@@ -812,7 +828,8 @@ inline uniform_passes<T> uniform_setup(const sg_plan *plan, const sg_workspace *
     u.nf_cols = nf;
     u.nout = pot_spec ? 1 : (fz ? 3 : 2);
     u.rf.work = wf;
-    C *edge = wf + (int64_t)u.qx * d.ny;  // after sigma's row transforms (central slopes)
+    // after sigma's row transforms (central slopes), at an even element: 16-byte pairs
+    C *edge = wf + (((int64_t)u.qx * d.ny + 1) & ~(int64_t)1);
     u.ed = {src.sigma, d.nx, d.ny, edge};
     u.col = {wf, wi, pot_spec ? pot_spec : (const T *)pp.spectra, edge, (const T *)pp.phase, d.ny, plan->wait_tries};
     u.ri = {wi, (T *)fx + off, pot_spec ? nullptr : (T *)fy + off, fz ? (T *)fz + off : nullptr, d.nx, d.ny};

@@ -392,17 +392,17 @@ sg_status sg_tables_build(sg_plan *plan)
 // Central-slope factors of a patch (see fftconv.cuh), in the plan precision:
 //   ce1[kx] = e^{+2 pi i kx / Px} / 2h,  ce2[kx] = e^{-2 pi i nx kx / Px} / 2h
 // for kx in [0, Px/2], and the same along y for ky in [0, Py) (re1, re2).
-// Layout: ce1[qx] ce2[qx] re1[py] re2[py] of complex entries (re, im), each
-// array starting at an even element so that an entry is one aligned vector
-// load. The sine factor sin(2 pi k / P) / h of the spectral difference is twice
-// the imaginary part of e1 (a power-of-two scaling of the same rounded value,
-// so the kernels form it exactly).
+// Layout: pairs (e1, e2) per kx, then pairs (e1, e2) per ky, each entry
+// complex (re, im): 4 T per index, so that a pair is one aligned 16-byte load
+// in FP32 (the y pairs start at 4 qx T). The sine factor sin(2 pi k / P) / h of
+// the spectral difference is twice the imaginary part of e1 (a power-of-two
+// scaling of the same rounded value, so the kernels form it exactly).
 template <typename T>
 __global__ void k_phase(T *out, int nx, int ny, int px, int py, double h)
 {
     const int qx = px / 2 + 1;
-    T *ce1 = out, *ce2 = out + 2 * qx;
-    T *re1 = out + 4 * qx, *re2 = re1 + 2 * py;
+    T *ce1 = out, *ce2 = out + 2;
+    T *re1 = out + 4 * qx, *re2 = re1 + 2;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < qx + py; k += gridDim.x * blockDim.x) {
         const bool col = k < qx;
         const int kk = col ? k : k - qx;
@@ -412,10 +412,10 @@ __global__ void k_phase(T *out, int nx, int ny, int px, int py, double h)
         // e^{-2 pi i n k / P}: reduce n k mod P first so the argument stays small
         sincospi(-2.0 * (double)(((long long)n * kk) % P) / (double)P, &s2, &c2);
         T *e1 = col ? ce1 : re1, *e2 = col ? ce2 : re2;
-        e1[2 * kk] = (T)(c1 / (2.0 * h));
-        e1[2 * kk + 1] = (T)(s1 / (2.0 * h));
-        e2[2 * kk] = (T)(c2 / (2.0 * h));
-        e2[2 * kk + 1] = (T)(s2 / (2.0 * h));
+        e1[4 * kk] = (T)(c1 / (2.0 * h));
+        e1[4 * kk + 1] = (T)(s1 / (2.0 * h));
+        e2[4 * kk] = (T)(c2 / (2.0 * h));
+        e2[4 * kk + 1] = (T)(s2 / (2.0 * h));
     }
 }
 
