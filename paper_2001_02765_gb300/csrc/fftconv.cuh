@@ -143,6 +143,20 @@ __device__ __forceinline__ X ld_table(const X *p)
     if constexpr (CO) return __ldca(p);
     return __ldg(p);
 }
+// Two adjacent FP32 complex values (16-byte aligned) in one load, through the
+// same path as ld_plain; FP64 (not used there): two loads.
+template <bool CO, typename C>
+__device__ __forceinline__ void ld_pair_plain(const C *p, C &a, C &b)
+{
+    if constexpr (sizeof(C) == 8) {
+        const float4 q = ld_plain<CO>(reinterpret_cast<const float4 *>(p));
+        a = make_float2(q.x, q.y);
+        b = make_float2(q.z, q.w);
+    } else {
+        a = ld_plain<CO>(p);
+        b = ld_plain<CO>(p + 1);
+    }
+}
 // The pair (a, b) at index k of an array of interleaved complex pairs: one
 // 16-byte load in FP32 (the array 16-byte aligned), two in FP64.
 template <bool CO, typename C>
@@ -433,15 +447,23 @@ __device__ __forceinline__ void row_inv_body(const row_inv_args<T> &args, int bx
     const C *w = work_inv + (int64_t)o * QX * ny;
     T *out = o == 0 ? fx : (o == 1 ? fy : fz);
 
-    // Z[k] = A[k] + i B[k] over the full length, from the half spectra of rows 2s, 2s+1
+    // Z[k] = A[k] + i B[k] over the full length, from the half spectra of rows 2s, 2s+1.
+    // In FP32 with an even row count the two rows' values of a column are one
+    // aligned 16-byte pair (ja is even): one load instead of two.
     constexpr int NE = NB * QX;
+    const bool pairs = sizeof(C) == 8 && (ny & 1) == 0;
     for (int e0 = threadIdx.x; e0 < NE; e0 += LOAD_UNROLL * THREADS) {
         C av[LOAD_UNROLL], bv[LOAD_UNROLL];
 #pragma unroll
         for (int u = 0; u < LOAD_UNROLL; ++u) {
             const int e = e0 + u * THREADS, s = e % NB, k = e / NB, ja = j0 + 2 * s;
-            av[u] = (e < NE && ja < ny) ? ld_plain<CO>(&w[(int64_t)k * ny + ja]) : cmake<C>((T)0, (T)0);
-            bv[u] = (e < NE && ja + 1 < ny) ? ld_plain<CO>(&w[(int64_t)k * ny + ja + 1]) : cmake<C>((T)0, (T)0);
+            if (pairs) {
+                av[u] = bv[u] = cmake<C>((T)0, (T)0);
+                if (e < NE && ja < ny) ld_pair_plain<CO>(&w[(int64_t)k * ny + ja], av[u], bv[u]);
+            } else {
+                av[u] = (e < NE && ja < ny) ? ld_plain<CO>(&w[(int64_t)k * ny + ja]) : cmake<C>((T)0, (T)0);
+                bv[u] = (e < NE && ja + 1 < ny) ? ld_plain<CO>(&w[(int64_t)k * ny + ja + 1]) : cmake<C>((T)0, (T)0);
+            }
         }
 #pragma unroll
         for (int u = 0; u < LOAD_UNROLL; ++u) {
