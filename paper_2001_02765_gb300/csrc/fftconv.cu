@@ -21,10 +21,10 @@ sg_status uniform_solve_t(sg_plan *plan, const sg_workspace *ws, int p, const vo
         return SG_EINVAL;
     }
     sg_timing_begin(ws, SG_STAGE_ROW_FWD, st);
-    SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st));
-    // the edge-column transform runs beside the row pass (a dependent launch that
-    // does not wait for it; see k_edge_cols)
+    // central slopes: the one-CTA edge-column transform first, the row pass
+    // beside it as a dependent launch that waits for it at its end (k_edge_cols)
     if (u.central) SG_TRY(sgk::edge_cols<T>(u.py, u.ed, u.twy, st));
+    SG_TRY(sgk::rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, nullptr, {0, 0}, u.central));
     sg_timing_end(ws, SG_STAGE_ROW_FWD, st);
     sg_timing_begin(ws, SG_STAGE_COL_CONV, st);
     if (u.central) SG_TRY(sgk::cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, ws->err, st));

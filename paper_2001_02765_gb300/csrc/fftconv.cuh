@@ -171,7 +171,7 @@ __device__ __forceinline__ void ld_pair(const C *p, int k, C &a, C &b)
         b = ld_table<CO>(p + 2 * k + 1);
     }
 }
-template <typename T, int PX, int NB, int THREADS>
+template <typename T, int PX, int NB, int THREADS, bool WAIT_AT_END = false>
 __device__ __forceinline__ void row_fwd_body(const row_fwd_args<T> &args, int bx, int f,
                                              const cplx_t<T> *__restrict__ tw)
 {
@@ -185,7 +185,11 @@ __device__ __forceinline__ void row_fwd_body(const row_fwd_args<T> &args, int bx
     const int j0 = bx * RB;
     const int ny = src.ny;
     if (j0 >= ny) return;
-    sg_dep_wait();
+    // WAIT_AT_END: launched after the edge-column transform, which waited for the
+    // previous solve before letting this kernel start, so the scratch is free
+    // now; the wait at the end makes this kernel's completion imply the edge
+    // transform's (CTA 0 always reaches it)
+    if constexpr (!WAIT_AT_END) sg_dep_wait();
 
     // two rows per complex sequence: z = row(2s) + i row(2s+1); positions >= PX/2 are zero
     constexpr int NE = NB * (PX / 2);
@@ -225,15 +229,16 @@ __device__ __forceinline__ void row_fwd_body(const row_fwd_args<T> &args, int bx
         else out = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
         work[((int64_t)f * QX + kx) * ny + j] = out;
     }
+    if constexpr (WAIT_AT_END) sg_dep_wait();
 }
 
-template <typename T, int PX, int NB, int THREADS, bool BATCH = false>
+template <typename T, int PX, int NB, int THREADS, bool BATCH = false, bool WAIT_AT_END = false>
 __global__ void __launch_bounds__(THREADS) k_row_fwd(row_fwd_args<T> one, const row_fwd_args<T> *__restrict__ many,
                                                      const cplx_t<T> *__restrict__ tw)
 {
     sg_dep_trigger();
     const row_fwd_args<T> args = pass_args<BATCH>(one, many);
-    row_fwd_body<T, PX, NB, THREADS>(args, blockIdx.x, blockIdx.y, tw);
+    row_fwd_body<T, PX, NB, THREADS, WAIT_AT_END>(args, blockIdx.x, blockIdx.y, tw);
 }
 
 // Shared-memory layout of the column kernels: the padded FFT buffer, then the
@@ -524,16 +529,17 @@ __device__ __forceinline__ void edge_body(const edge_args<T> &args, const cplx_t
         edge[2 * k] = cmake<C>(half * (z.x + w.x), half * (z.y - w.y));
         edge[2 * k + 1] = cmake<C>(half * (z.y + w.y), half * (w.x - z.x));
     }
-    sg_dep_wait();
 }
 
 template <typename T, int PY, int THREADS, bool BATCH = false>
 __global__ void __launch_bounds__(THREADS) k_edge_cols(edge_args<T> one, const edge_args<T> *__restrict__ many,
                                                        const cplx_t<T> *__restrict__ tw)
 {
-    // launched after the row pass, beside it: sigma is the caller's (ready
-    // before the row pass started); the wait at the end of the body makes this
-    // kernel's completion imply the row pass's, for the column pass after it
+    // the first kernel of a central-slope solve: it waits for the previous
+    // kernel of the stream (its scratch is the solve's scratch), then lets the
+    // row pass start beside it (k_row_fwd with WAIT_AT_END), whose completion
+    // then implies this kernel's for the column pass after them
+    sg_dep_wait();
     sg_dep_trigger();
     const edge_args<T> args = pass_args<BATCH>(one, many);
     edge_body<T, PY, THREADS>(args, tw);
@@ -774,7 +780,7 @@ struct batch_shape {
 };
 template <typename T>
 sg_status rows_fwd(int px, int nb, const row_fwd_args<T> &one, int nf, const cplx_t<T> *tw, cudaStream_t st,
-                   const row_fwd_args<T> *many = nullptr, batch_shape bs = {0, 0});
+                   const row_fwd_args<T> *many = nullptr, batch_shape bs = {0, 0}, bool after_edge = false);
 // The column and inverse-row passes are launched as dependent launches
 // (sg_launch_dep) on the pass before them in the stream; dep = false launches a
 // column pass normally (when its stream waits on an event just before it).

@@ -43,8 +43,8 @@ template <typename T>
 inline sg_status group_enqueue(const group_passes<T> &g, cudaStream_t st)
 {
     const uniform_passes<T> &u = g.u;
-    SG_TRY(rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, g.rf, g.bs));
     if (u.central) SG_TRY(edge_cols<T>(u.py, u.ed, u.twy, st, g.ed, g.bs));
+    SG_TRY(rows_fwd<T>(u.px, u.shx[0], u.rf, u.nf_rows, u.twx, st, g.rf, g.bs, u.central));
     if (u.central) SG_TRY(cols_central<T>(u.py, u.shy[3], u.col, u.qx, u.twy, g.err, st, g.col, g.bs));
     else SG_TRY(cols<T>(u.py, u.shy[2], u.nout, u.col, u.qx, u.nf_cols, u.twy, g.err, st, g.col, g.bs));
     SG_TRY(rows_inv<T>(u.px, u.shx[1], u.ri, u.nout, u.twx, st, g.ri, g.bs));
