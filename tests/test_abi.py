@@ -102,3 +102,32 @@ def test_tune_table_host_rules(lib):
     sg.sg_tune_set(sg.SG_FP32, 2048, [0, 0, 0, 0])
     assert sg.sg_tune_get(sg.SG_FP32, 2048) == d
     assert sg.sg_tune_get(sg.SG_FP64, 4096)["col"] == 1
+
+
+def test_host_side_argument_errors(lib):
+    """Entry points reject null handles and bad arguments on the host, before
+    touching the device (no GPU needed)."""
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_server_set_group_limit(None, 4)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_plan_autotune(None, 3)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_plan_direct_shape(None)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_plan_wait(None)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_force_host_async(None, 1, 0, 0, 1, 1)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_potential_zones(None, 1, 0, 0, 1)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_batch_create([], [], [], [], [], [], mode=sg.SG_BATCH_PERSISTENT)
+    assert e.value.status == sg.SG_EINVAL
+    with pytest.raises(sg.SgError) as e:
+        sg.sg_batch_layout(None)
+    assert e.value.status == sg.SG_EINVAL
