@@ -40,9 +40,10 @@
 //                 - D w^2/8 - conj(D) s/24
 //                 + 7 conj(D) w^4/384 + D s (conj(w)^2 - 7 w^2)/384 - 7 conj(D) s^2/640 }
 //    (terms through H^6; through H^4: m w (1 + s/8) - D w^2/8 - conj(D) s/24).
-//    Relative to 1/rho^2 the truncation is below 5e-7 from 6 cell widths on
-//    (through H^6) and below 1e-6 for the slope terms, 1e-7 for sigma0, from
-//    32 on (through H^4), both far under the 1e-5 the FP32 path is held to;
+//    Relative to 1/rho^2, per unit sigma0 or unit slope times H, the
+//    truncation is at most 1.3e-7 (sigma0) and 1.02e-6 (slopes) from 6 cell
+//    widths on (through H^6), 3e-8 and 7.6e-7 from 32 on (through H^4), all
+//    far under the 1e-5 the FP32 path is held to;
 //    every term is a small positive-scale product, so FP32 rounding stays
 //    relative to the cell's own contribution.
 //  * Near cells (both |a|, |b| < SG_NEAR_R): the closed forms in FP64, as the
