@@ -979,15 +979,19 @@ def run_gpu(args):
                 for pl, st in pair:
                     pl.wait(st)
 
-            pipelined(4)
+            # warm-up over every buffer set; at least 200 timed solves, since
+            # 50 pipelined solves last only a few ms and one host stall there
+            # halves the figure
+            e2e_steps = max(args.steps, 200)
+            pipelined(sets + 2)
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            pipelined(args.steps)
-            e2e_ms = 1e3 * (time.perf_counter() - t0)
+            pipelined(e2e_steps)
+            e2e_ms = 1e3 * (time.perf_counter() - t0) * args.steps / e2e_steps
             e2e_mode = ("pipelined: sg_force_host_async on two plans and two streams, each solve waited for one "
-                        "step later; %d rotating pinned host buffer sets (%.0f MB, more than L2)"
-                        % (sets, sets * (h2d + d2h) / 2**20))
+                        "step later; %d rotating pinned host buffer sets (%.0f MB, more than L2), warmed up over "
+                        "every set; %d solves timed" % (sets, sets * (h2d + d2h) / 2**20, e2e_steps))
             plan2.close()
 
     # roofline of the dominant kernel
