@@ -11,7 +11,7 @@ sg_status launch_cols_central(const col_args<T> &one, const col_args<T> *many, b
                               const cplx_t<T> *tw, int *err, cudaStream_t st, bool dep)
 {
     constexpr int THREADS = CB * PY / 8;
-    const size_t smem = (size_t)col_smem_bytes<T, PY, CB>();
+    const size_t smem = (size_t)col_smem_bytes<T, PY, CB, 6, col_central_nbuf<T, PY, CB>()>();
     auto kern = k_col_conv_central<T, PY, CB, THREADS, BATCH>;
     SG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((qx + CB - 1) / CB, 1, BATCH ? bs.nmem : 1);
