@@ -256,7 +256,7 @@ __host__ __device__ constexpr int col_nbuf() { return sizeof(T) == 8 && PY >= 40
 // runs four CTAs per SM instead of three (1025 columns in 1.7 waves instead of
 // 2.25): 64 registers (one spilled) and one exchange buffer, so that four CTAs'
 // buffers and spectrum planes (41 KB each) fit in an SM's shared memory.
-// Measured 28.3 -> 27.1 us per pass at 2048 x 2048; the caller-slope pass
+// Measured 28.3 -> 27.2 us per pass at 2048 x 2048; the caller-slope pass
 // spills 100 bytes at 64 registers and keeps three.
 template <typename T, int PY, int CB>
 __host__ __device__ constexpr bool col_central_four() { return sizeof(T) == 4 && PY == 2048 && CB == 1; }
@@ -300,7 +300,8 @@ __device__ __forceinline__ bool spectra_ready(uint64_t *bar, int *err, int tries
 // resident CTAs per SM asked of the register allocator (spill-free choices at
 // the default shapes, scaled by the CTA size for the other candidates). FP32
 // 2048-point columns: the two exchange buffers and six spectrum planes take
-// 59.5 KB of shared memory, so three CTAs fit per SM: 80 registers each.
+// 59.5 KB of shared memory, so three CTAs fit per SM: 80 registers each (the
+// central-slope pass kernel's four-CTA form, above, overrides this).
 template <typename T, int PY, int NOUT>
 constexpr int col_min_blocks_def()
 {
