@@ -741,6 +741,98 @@ class OracleSample:
                 "%d seeded leaf targets of the full workload, plain FP64 direct sum over all sources" % sample_targets)
 
 
+# ------------------------------------------------------- cuFFT comparison --
+
+class TorchFFTConv:
+    """The uniform-grid convolution through torch.fft (cuFFT on a GPU), timed
+    beside the library's own transforms as a comparison only; no path of the
+    library uses it.
+
+    F_x[t] = G sum_s sigma0[s] K^{x,0}[s - t] + deltax[s] K^{x,x}[s - t]
+    + deltay[s] K^{x,y}[s - t] (and F_y with K^{y,.}) is a correlation of the
+    fields with the kernel tables; zero padding to P >= 2N - 1 per axis makes
+    the circular form equal to the linear one. tables: the six tables K^{x,0},
+    K^{x,x}, K^{x,y}, K^{y,0}, K^{y,x}, K^{y,y}, each (2 ny - 1) x (2 nx - 1)
+    with entry [n + ny - 1][m + nx - 1] for a source offset (m h, n h). Their
+    spectra are formed once, in FP64, and held in `dtype`'s complex type. Per
+    call: central slopes by elementwise ops (slope_mode 1; sigma = 0 beyond the
+    grid), R2C of the fields, six spectral products, two C2R, crop.
+    """
+
+    def __init__(self, tables, nx, ny, h, G, slope_mode, pad, dtype, device):
+        import torch
+        self.nx, self.ny, self.h, self.G, self.slope_mode = nx, ny, h, G, slope_mode
+        self.py, self.px = pad
+        self.dtype = dtype
+        m = torch.arange(-(nx - 1), nx)
+        n = torch.arange(-(ny - 1), ny)
+        rows = ((-n) % self.py).to(device)
+        cols = ((-m) % self.px).to(device)
+        cdt = torch.complex64 if dtype == torch.float32 else torch.complex128
+        self.spec = []
+        for t in tables:
+            w = torch.zeros(self.py, self.px, dtype=torch.float64, device=device)
+            w[rows[:, None], cols[None, :]] = torch.as_tensor(np.asarray(t, np.float64), device=device)
+            self.spec.append(torch.fft.rfft2(w).to(cdt))
+
+    def __call__(self, sigma, dx=None, dy=None):
+        import torch
+        import torch.nn.functional as F
+        s = sigma.reshape(self.ny, self.nx)
+        if self.slope_mode == 1:
+            p = F.pad(s, (1, 1, 1, 1))
+            dx = (p[1:-1, 2:] - p[1:-1, :-2]) * (0.5 / self.h)
+            dy = (p[2:, 1:-1] - p[:-2, 1:-1]) * (0.5 / self.h)
+        elif self.slope_mode == 2:
+            dx, dy = dx.reshape(self.ny, self.nx), dy.reshape(self.ny, self.nx)
+        else:
+            dx = dy = None
+        size = (self.py, self.px)
+        sh = torch.fft.rfft2(s, s=size)
+        kx0, kxx, kxy, ky0, kyx, kyy = self.spec
+        fxh, fyh = sh * kx0, sh * ky0
+        if dx is not None:
+            ah = torch.fft.rfft2(dx, s=size)
+            bh = torch.fft.rfft2(dy, s=size)
+            fxh = fxh + ah * kxx + bh * kxy
+            fyh = fyh + ah * kyx + bh * kyy
+        fx = torch.fft.irfft2(fxh, s=size)[: self.ny, : self.nx]
+        fy = torch.fft.irfft2(fyh, s=size)[: self.ny, : self.nx]
+        return self.G * fx, self.G * fy
+
+
+def cufft_compare(plan, wl, steps, flush, ref):
+    """Time TorchFFTConv on the workload (FP32, tables from the plan, L2 flushed
+    before each solve, CUDA events on the current stream) and its relative L2
+    error against `ref`, the FP64 plan's (Fx, Fy)."""
+    import torch
+    _, nx, ny, _, _, h = wl["patches"][0]
+    tabs = [plan.kernel_table(0, w) for w in range(6)]
+    conv = TorchFFTConv(tabs, nx, ny, h, plan.G, wl["slope_mode"], (_pad(ny), _pad(nx)), torch.float32, "cuda")
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    s, dx, dy = dev(wl["sigma"]), dev(wl["dx"]), dev(wl["dy"])
+    for _ in range(3):  # cuFFT plans are made on first use
+        fx, fy = conv(s, dx, dy)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        fx, fy = conv(s, dx, dy)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    rx, ry = ref[0].ravel(), ref[1].ravel()
+    num = torch.sum((fx.double().ravel() - rx) ** 2) + torch.sum((fy.double().ravel() - ry) ** 2)
+    den = torch.sum(rx ** 2) + torch.sum(ry ** 2)
+    return {"solves_per_s": 1e3 * steps / sum(per), "ms_per_solve": sum(per) / steps,
+            "p50_ms": float(np.percentile(per, 50)), "rel_err_vs_fp64": float(torch.sqrt(num / den)),
+            "note": "torch.fft (cuFFT) in FP32, a comparison only: %s, R2C of the fields, products with the "
+                    "spectra of the plan's six kernel tables (formed once, untimed), two C2R, crop; L2 flushed "
+                    "before each solve" % ("central slopes by elementwise ops" if wl["slope_mode"] == 1 else
+                                           "caller slopes" if wl["slope_mode"] == 2 else "order 0")}
+
+
 # -------------------------------------------------------------- GPU arm --
 
 def run_gpu(args):
@@ -893,6 +985,15 @@ def run_gpu(args):
     fp64_path = plan64.info["cross_mode"]
     plan64.close()
 
+    # the same convolution through torch.fft (cuFFT) in FP32, timed as a
+    # comparison only (single in-plane patch force workloads)
+    cufft = None
+    if not pot and not zt and zones is None and len(wl["patches"]) == 1 and fp64_ms is not None:
+        try:
+            cufft = cufft_compare(plan, wl, args.steps, flush, g64)
+        except Exception as e:  # the comparison never fails the benchmark
+            cufft = {"unavailable": "%s: %s" % (type(e).__name__, e)}
+
     # end to end through the host-buffer entry point (pinned buffers)
     hs = torch.from_numpy(np.ascontiguousarray(wl["sigma"], np.float32)).pin_memory()
     hdx = torch.from_numpy(np.ascontiguousarray(wl["dx"], np.float32)).pin_memory() if wl["dx"] is not None else None
@@ -1024,6 +1125,7 @@ def run_gpu(args):
         "fp64_plain": {"solves_per_s": 1e3 / fp64_ms * world if fp64_ms else None, "ms_per_solve": fp64_ms,
                        "cross_mode": fp64_path, "note": fp64_note},
         "rel_err_vs_fp64": rel_err,
+        **({"cufft_comparison": cufft} if cufft is not None else {}),
         "stage_ms": stage_mean,
         "roofline": {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": tflops / alu_peak, "traffic": TRAFFIC.get((args.workload, dom)),
